@@ -1,0 +1,567 @@
+/*
+ * CPU oracle for the bottleneck-adaptive CSR SpMV method of Elafrou, Goumas and Koziris,
+ * "Performance Analysis and Optimization of Sparse Matrix-Vector Multiplication on Modern
+ * Multi- and Many-Core Processors" (arXiv 1711.05487).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the slow, plain, obviously-correct reference that
+ * the GPU library is checked against. It shares no code, header, table or constant
+ * generator with the CUDA library; only the tests, the package entry point's smoke check
+ * and the benchmark's CPU-baseline leg may load it. Every loop runs in the order the paper
+ * states, in FP64 unless noted. Build flags must keep floating-point contraction off
+ * (-ffp-contract=off) so that the FP32 selector inference below performs exactly the
+ * operations it spells out.
+ *
+ * Contents (each function cites the passage it follows):
+ *   - CSR validation                         (Section II, CSR definition)
+ *   - y = A x in FP64, plus sum |a_ij x_j|    (Section II, Fig. 1)
+ *   - multi-RHS y = A X                       (Fig. 1 applied column by column)
+ *   - FP64 -> FP32 / BF16 round-to-nearest-even value storage
+ *   - 16-bit delta column-index format       (Section III-E, MB optimization)
+ *   - merge-path coordinates of a CSR matrix (Section III-E, IMB optimization: the
+ *     nnz-balanced work split)
+ *   - Table I matrix features                (Section III-D)
+ *   - P_MB and P_peak bounds                 (Section III-B)
+ *   - Classify rule set                      (Section III-C, Fig. 3)
+ *   - class -> optimization map              (Section III-E, Table II)
+ *   - amortization iterations                (Section IV-D, N_iters,min)
+ *   - MLP selector: FP64 loss and gradient, FP32 inference, log2(1+v) normalisation
+ *     (the learned selector that stands in for the decision tree of Section III-D)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef unsigned __int128 u128;
+
+/* ---------------------------------------------------------------------------------- */
+/* CSR validation (Section II: rowptr indexes the start of each row within the arrays of
+ * nonzeros; colind holds each nonzero's column).                                       */
+/* Return codes: 0 valid, 1 rowptr[0] != 0, 2 rowptr decreases, 3 rowptr[N] != nnz,
+ *               4 column out of [0, n_cols), 5 columns not strictly increasing in a row,
+ *               6 negative sizes.                                                       */
+int oracle_validate_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t *rowptr,
+                        const int32_t *colind) {
+  if (n_rows < 0 || n_cols < 0 || nnz < 0) return 6;
+  if (rowptr[0] != 0) return 1;
+  for (int64_t i = 0; i < n_rows; ++i)
+    if (rowptr[i + 1] < rowptr[i]) return 2;
+  if ((int64_t)rowptr[n_rows] != nnz) return 3;
+  for (int64_t i = 0; i < n_rows; ++i) {
+    for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) {
+      if (colind[j] < 0 || (int64_t)colind[j] >= n_cols) return 4;
+      if (j > rowptr[i] && colind[j] <= colind[j - 1]) return 5;
+    }
+  }
+  return 0;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* y = A x (Fig. 1). The statement inside the inner loop accumulates into y[i], which
+ * starts at zero: the caption and Section II call this the y = A.x kernel, so the
+ * assignment printed in the figure is read as y[i] <- y[i] + val[j] * x[colind[j]].
+ * s[i] = sum_j |val[j] * x[colind[j]]| is the scale that the accuracy bound of each
+ * result row is stated against. Empty rows give y[i] = s[i] = 0.                       */
+void oracle_spmv_f64(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                     const double *val, const double *x, double *y, double *s) {
+  for (int64_t i = 0; i < n_rows; ++i) {
+    double acc = 0.0, mag = 0.0;
+    for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) {
+      double p = val[j] * x[colind[j]];
+      acc += p;
+      mag += fabs(p);
+    }
+    y[i] = acc;
+    if (s) s[i] = mag;
+  }
+}
+
+/* The same sum for a list of rows only (used to check sampled rows of large matrices). */
+void oracle_spmv_rows_f64(const int64_t *rows, int64_t n_sample, const int32_t *rowptr,
+                          const int32_t *colind, const double *val, const double *x,
+                          double *y, double *s) {
+  for (int64_t r = 0; r < n_sample; ++r) {
+    int64_t i = rows[r];
+    double acc = 0.0, mag = 0.0;
+    for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) {
+      double p = val[j] * x[colind[j]];
+      acc += p;
+      mag += fabs(p);
+    }
+    y[r] = acc;
+    s[r] = mag;
+  }
+}
+
+/* Y = A X for k right-hand sides, X and Y row-major (N x k): Fig. 1 for every column. */
+void oracle_spmm_f64(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                     const double *val, const double *X, int64_t k, double *Y, double *S) {
+  for (int64_t i = 0; i < n_rows; ++i) {
+    for (int64_t c = 0; c < k; ++c) {
+      double acc = 0.0, mag = 0.0;
+      for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) {
+        double p = val[j] * X[(int64_t)colind[j] * k + c];
+        acc += p;
+        mag += fabs(p);
+      }
+      Y[i * k + c] = acc;
+      S[i * k + c] = mag;
+    }
+  }
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Reduced-precision value storage: round-to-nearest-even straight from the FP64 value.
+ * FP32: C's double -> float conversion rounds to nearest even in the default mode.       */
+void oracle_round_f32(const double *in, float *out, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) out[i] = (float)in[i];
+}
+
+/* BF16 (1 sign, 8 exponent, 7 fraction bits; same exponent range as FP32). For finite v:
+ * the quantum is 2^(max(e, -126) - 7) with v = m 2^e, 1 <= |m| < 2; v / quantum is exact
+ * (power-of-two scaling) and rint() rounds it to the nearest integer, ties to even.
+ * Magnitudes that round to 2^128 or more become infinity. NaN stays NaN (quiet).        */
+static uint16_t bf16_bits_of_exact(double r) {
+  /* r is exactly representable in bf16: its float image is exact, take the top half. */
+  float f = (float)r;
+  uint32_t u;
+  memcpy(&u, &f, sizeof u);
+  return (uint16_t)(u >> 16);
+}
+
+void oracle_round_bf16(const double *in, uint16_t *out, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) {
+    double v = in[i];
+    if (isnan(v)) {
+      out[i] = signbit(v) ? 0xFFC0u : 0x7FC0u;
+      continue;
+    }
+    if (isinf(v) || v == 0.0) {
+      out[i] = bf16_bits_of_exact(v);
+      continue;
+    }
+    int e;
+    (void)frexp(v, &e);          /* v = f 2^e with 0.5 <= |f| < 1, so |v| in [2^(e-1), 2^e) */
+    int ex = e - 1;              /* v = m 2^ex with 1 <= |m| < 2                            */
+    if (ex < -126) ex = -126;    /* subnormal range keeps the smallest normal's quantum     */
+    double q = ldexp(1.0, ex - 7);
+    double r = rint(v / q) * q;
+    if (fabs(r) >= ldexp(1.0, 128)) r = signbit(v) ? -INFINITY : INFINITY;
+    out[i] = bf16_bits_of_exact(r);
+  }
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Delta-indexed column indices (Section III-E, MB row of Table II): each column index is
+ * stored as its distance to the previous column of the same row, in 16 bits wherever
+ * possible. Read per row: a row whose every consecutive distance fits 16 bits keeps its
+ * first column in base[i] and stores delta[j] = colind[j] - colind[j-1] (delta of the
+ * row's first element = 0). A row with a distance above 65535 is an escape row: its
+ * deltas are 0, its columns go to esc_col in row order, and base[i] = -(1 + offset of the
+ * row in esc_col). An empty row has base[i] = 0. Returns the number of escaped columns. */
+int64_t oracle_delta16_encode(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                              int32_t *base, uint16_t *delta, int32_t *esc_col) {
+  int64_t n_esc = 0;
+  for (int64_t i = 0; i < n_rows; ++i) {
+    int64_t b = rowptr[i], e = rowptr[i + 1];
+    if (b == e) {
+      base[i] = 0;
+      continue;
+    }
+    int fits = 1;
+    for (int64_t j = b + 1; j < e; ++j)
+      if ((int64_t)colind[j] - (int64_t)colind[j - 1] > 65535) fits = 0;
+    if (fits) {
+      base[i] = colind[b];
+      delta[b] = 0;
+      for (int64_t j = b + 1; j < e; ++j) delta[j] = (uint16_t)(colind[j] - colind[j - 1]);
+    } else {
+      base[i] = (int32_t)(-(1 + n_esc));
+      for (int64_t j = b; j < e; ++j) {
+        delta[j] = 0;
+        esc_col[n_esc++] = colind[j];
+      }
+    }
+  }
+  return n_esc;
+}
+
+/* Inverse of the above: rebuild colind from (base, delta, esc_col). */
+void oracle_delta16_decode(int64_t n_rows, const int32_t *rowptr, const int32_t *base,
+                           const uint16_t *delta, const int32_t *esc_col, int32_t *colind) {
+  for (int64_t i = 0; i < n_rows; ++i) {
+    int64_t b = rowptr[i], e = rowptr[i + 1];
+    if (b == e) continue;
+    if (base[i] < 0) {
+      int64_t off = -(int64_t)base[i] - 1;
+      for (int64_t j = b; j < e; ++j) colind[j] = esc_col[off + (j - b)];
+    } else {
+      int64_t c = base[i];
+      for (int64_t j = b; j < e; ++j) {
+        c += delta[j];
+        colind[j] = (int32_t)c;
+      }
+    }
+  }
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Merge-path coordinates (IMB optimization, Section III-E: spread the nonzeros evenly
+ * over the workers and let long rows be shared). The work of a CSR SpMV is the merged
+ * sequence of the N row-end events (row i ends at rowptr[i+1]) and the NNZ nonzeros
+ * 0..NNZ-1, where nonzero j comes before the end of row i exactly when j < rowptr[i+1].
+ * Walking that sequence item by item, coord[2t], coord[2t+1] record (rows ended,
+ * nonzeros consumed) after t * items_per_tile items, for t = 0..n_tiles; the last entry
+ * is (N, NNZ).                                                                           */
+void oracle_merge_path(int64_t n_rows, int64_t nnz, const int32_t *rowptr,
+                       int64_t items_per_tile, int32_t *coord) {
+  int64_t total = n_rows + nnz;
+  int64_t n_tiles = (total + items_per_tile - 1) / items_per_tile;
+  int64_t a = 0, b = 0, t = 0;
+  coord[0] = 0;
+  coord[1] = 0;
+  for (int64_t d = 1; d <= total; ++d) {
+    if (a < n_rows && !(b < nnz && b < (int64_t)rowptr[a + 1])) {
+      ++a;        /* the end of row a comes next */
+    } else {
+      ++b;        /* nonzero b comes next        */
+    }
+    if (d % items_per_tile == 0 || d == total) {
+      ++t;
+      coord[2 * t] = (int32_t)a;
+      coord[2 * t + 1] = (int32_t)b;
+    }
+  }
+  (void)n_tiles;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Table I features (Section III-D). Per row i:
+ *   nnz_i        number of nonzeros;
+ *   bw_i         column distance between first and last nonzero, read as the inclusive
+ *                span last - first + 1 (so that a one-element row has bw = 1 and
+ *                scatter = 1); 0 for an empty row;
+ *   scatter_i    nnz_i / bw_i (0 for an empty row);
+ *   clustering_i ngroups_i / nnz_i, a group being a maximal run of consecutive columns
+ *                (0 for an empty row);
+ *   misses_i     elements whose distance from the previous element of the row exceeds
+ *                the number of x elements in a cache line; a row's first element counts.
+ * The two ratio features are kept as fixed-point numbers q_i = round(2^24 * ratio), the
+ * rational rounded half up; their mean and deviation are taken over the q_i and scaled
+ * back by 2^-24. Means are sum / N; deviations are population deviations (divide by N),
+ * evaluated from exact 128-bit integer moments: sd = sqrt((N sum f^2 - (sum f)^2) / N^2).
+ *
+ * out[0..13] = size, density, nnz_min, nnz_max, nnz_avg, nnz_sd, bw_min, bw_max, bw_avg,
+ *              bw_sd, scatter_avg, scatter_sd, clustering_avg, misses_avg
+ * size is 1 when ws_bytes <= llc_bytes. density = NNZ / (n_rows * n_cols).
+ * isum[0..11] (exact sums, for bit-level comparison): sum nnz, sum bw, sum q_scatter,
+ * sum q_clustering, sum misses, sum ngroups, nnz_min, nnz_max, bw_min, bw_max,
+ * and the low 64 bits of sum nnz^2 and sum bw^2.                                          */
+static double finalize_sd(u128 s1, u128 s2, int64_t n, double scale) {
+  u128 nn = (u128)(uint64_t)n;
+  u128 num = nn * s2 - s1 * s1;
+  double var = (double)num / ((double)n * (double)n);
+  return sqrt(var) * scale;
+}
+
+static uint64_t ratio_q24(uint64_t num, uint64_t den) {
+  /* round(num * 2^24 / den), halves rounded up, in exact integer arithmetic */
+  return (uint64_t)((((u128)num << 25) + den) / ((u128)den * 2));
+}
+
+void oracle_features(int64_t n_rows, int64_t n_cols, const int32_t *rowptr,
+                     const int32_t *colind, int64_t line_elems, int64_t ws_bytes,
+                     int64_t llc_bytes, double *out, uint64_t *isum) {
+  int64_t nnz = rowptr[n_rows];
+  u128 s_nnz = 0, s_nnz2 = 0, s_bw = 0, s_bw2 = 0, s_sc = 0, s_sc2 = 0, s_cl = 0;
+  uint64_t s_miss = 0, s_grp = 0;
+  int64_t nnz_min = INT64_MAX, nnz_max = 0, bw_min = INT64_MAX, bw_max = 0;
+  for (int64_t i = 0; i < n_rows; ++i) {
+    int64_t b = rowptr[i], e = rowptr[i + 1];
+    int64_t k = e - b;
+    int64_t bw = 0, groups = 0, misses = 0;
+    if (k > 0) {
+      bw = (int64_t)colind[e - 1] - (int64_t)colind[b] + 1;
+      for (int64_t j = b; j < e; ++j) {
+        if (j == b) {
+          groups += 1;
+          misses += 1;
+        } else {
+          int64_t d = (int64_t)colind[j] - (int64_t)colind[j - 1];
+          if (d != 1) groups += 1;
+          if (d > line_elems) misses += 1;
+        }
+      }
+    }
+    uint64_t q_sc = k > 0 ? ratio_q24((uint64_t)k, (uint64_t)bw) : 0;
+    uint64_t q_cl = k > 0 ? ratio_q24((uint64_t)groups, (uint64_t)k) : 0;
+    s_nnz += (u128)k;
+    s_nnz2 += (u128)k * (u128)k;
+    s_bw += (u128)bw;
+    s_bw2 += (u128)bw * (u128)bw;
+    s_sc += q_sc;
+    s_sc2 += (u128)q_sc * (u128)q_sc;
+    s_cl += q_cl;
+    s_miss += (uint64_t)misses;
+    s_grp += (uint64_t)groups;
+    if (k < nnz_min) nnz_min = k;
+    if (k > nnz_max) nnz_max = k;
+    if (bw < bw_min) bw_min = bw;
+    if (bw > bw_max) bw_max = bw;
+  }
+  if (n_rows == 0) {
+    nnz_min = nnz_max = bw_min = bw_max = 0;
+  }
+  const double N = (double)n_rows;
+  const double q = 1.0 / 16777216.0; /* 2^-24 */
+  out[0] = ws_bytes <= llc_bytes ? 1.0 : 0.0;
+  out[1] = n_rows > 0 && n_cols > 0 ? (double)nnz / ((double)n_rows * (double)n_cols) : 0.0;
+  out[2] = (double)nnz_min;
+  out[3] = (double)nnz_max;
+  out[4] = n_rows ? (double)s_nnz / N : 0.0;
+  out[5] = n_rows ? finalize_sd(s_nnz, s_nnz2, n_rows, 1.0) : 0.0;
+  out[6] = (double)bw_min;
+  out[7] = (double)bw_max;
+  out[8] = n_rows ? (double)s_bw / N : 0.0;
+  out[9] = n_rows ? finalize_sd(s_bw, s_bw2, n_rows, 1.0) : 0.0;
+  out[10] = n_rows ? ((double)s_sc / N) * q : 0.0;
+  out[11] = n_rows ? finalize_sd(s_sc, s_sc2, n_rows, q) : 0.0;
+  out[12] = n_rows ? ((double)s_cl / N) * q : 0.0;
+  out[13] = n_rows ? (double)s_miss / N : 0.0;
+  if (isum) {
+    isum[0] = (uint64_t)s_nnz;
+    isum[1] = (uint64_t)s_bw;
+    isum[2] = (uint64_t)s_sc;
+    isum[3] = (uint64_t)s_cl;
+    isum[4] = s_miss;
+    isum[5] = s_grp;
+    isum[6] = (uint64_t)nnz_min;
+    isum[7] = (uint64_t)nnz_max;
+    isum[8] = (uint64_t)bw_min;
+    isum[9] = (uint64_t)bw_max;
+    isum[10] = (uint64_t)s_nnz2;
+    isum[11] = (uint64_t)s_bw2;
+  }
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Section III-B bounds, in GFLOP/s with bandwidth in GB/s (1 GB = 1e9 bytes):
+ *   P_MB   = 2 NNZ / ((S_format + S_x + S_y) / B_max),
+ *   P_peak = 2 NNZ / ((S_values + S_x + S_y) / B_max),
+ * with S_format = 4 (N + 1) + (idx_bytes + val_bytes) NNZ for CSR (int32 row pointers),
+ * S_values = val_bytes NNZ, S_x = S_y = vec_bytes N. out[0] = P_MB, out[1] = P_peak,
+ * out[2] = S_format + S_x + S_y (the working set, in bytes).                             */
+void oracle_bounds(int64_t n_rows, int64_t n_cols, int64_t nnz, int64_t idx_bytes,
+                   int64_t val_bytes, int64_t vec_bytes, double b_max_gbs, double *out) {
+  double s_format = 4.0 * (double)(n_rows + 1) + (double)(idx_bytes + val_bytes) * (double)nnz;
+  double s_xy = (double)vec_bytes * (double)n_cols + (double)vec_bytes * (double)n_rows;
+  double s_values = (double)val_bytes * (double)nnz;
+  double flops = 2.0 * (double)nnz;
+  out[0] = flops / ((s_format + s_xy) / b_max_gbs);
+  out[1] = flops / ((s_values + s_xy) / b_max_gbs);
+  out[2] = s_format + s_xy;
+}
+
+/* B_max is raised for working sets that fit the cache hierarchy (Section III-B footnote):
+ * the cache-resident bandwidth applies when the working set is at most the LLC size.   */
+double oracle_select_bmax(int64_t ws_bytes, int64_t llc_bytes, double b_main, double b_llc) {
+  return ws_bytes <= llc_bytes ? b_llc : b_main;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Classify (Section III-C, Fig. 3). Class bits: MB = 1, ML = 2, IMB = 4, CMP = 8.
+ * The paper leaves "P_CSR is close to P_MB" without a tolerance; it is read as
+ * P_CSR / P_MB >= t_mb.                                                                  */
+uint32_t oracle_classify(const double *p /* csr, mb, ml, imb, cmp, peak */, double t_imb,
+                         double t_ml, double t_mb) {
+  double p_csr = p[0], p_mb = p[1], p_ml = p[2], p_imb = p[3], p_cmp = p[4], p_peak = p[5];
+  uint32_t cls = 0;
+  if (p_imb / p_csr > t_imb) cls |= 4u;
+  if (p_ml / p_csr > t_ml) cls |= 2u;
+  if (p_csr / p_mb >= t_mb && p_mb < p_cmp && p_cmp < p_peak) cls |= 1u;
+  if (p_mb > p_cmp || p_cmp > p_peak) cls |= 8u;
+  return cls;
+}
+
+/* Table II: class -> optimization, applied jointly when several classes are detected.
+ * Knobs returned in out[0..3]:
+ *   out[0] partition: 0 = one sub-warp per row (rows dealt to CTAs by the hardware
+ *          scheduler, the GPU's counterpart of a runtime-chosen loop schedule),
+ *          1 = merge-path tiles with long rows split across tiles (matrix decomposition);
+ *   out[1] column index: 0 = int32, 1 = 16-bit deltas (MB);
+ *   out[2] x path: 0 = default, 1 = x kept resident in L2 and gathered through the
+ *          read-only path (ML; the counterpart of software prefetching of x);
+ *   out[3] vector loads and unrolling: 1 for MB (delta encoding + vectorization) and CMP
+ *          (unrolling + vectorization).
+ * IMB picks between its two sub-optimizations with nnz_max versus nnz_avg: highly uneven
+ * row lengths (nnz_max > long_ratio * nnz_avg) take the decomposition (merge-path),
+ * otherwise the dynamic schedule (sub-warp rows). The 16-bit delta index is only built for
+ * the sub-warp row partition, so MB together with the merge-path keeps int32 columns.    */
+void oracle_variant_for_classes(uint32_t cls, double nnz_avg, double nnz_max,
+                                double long_ratio, int32_t *out) {
+  int32_t part = 0, idx = 0, xp = 0, vec = 0;
+  if ((cls & 4u) && nnz_max > long_ratio * nnz_avg) part = 1;
+  if ((cls & 1u) && part == 0) idx = 1;
+  if (cls & 2u) xp = 1;
+  if (cls & (1u | 8u)) vec = 1;
+  out[0] = part;
+  out[1] = idx;
+  out[2] = xp;
+  out[3] = vec;
+}
+
+/* Section IV-D: N_iters,min = t_pre / (t_base - t_opt); returns +inf when the optimized
+ * kernel is not faster.                                                                  */
+double oracle_amortization_iters(double t_pre, double t_base, double t_opt) {
+  if (t_base <= t_opt) return INFINITY;
+  return t_pre / (t_base - t_opt);
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* MLP selector. Layers sizes[0] -> sizes[1] -> sizes[2] -> sizes[3], ReLU after the two
+ * hidden layers, one sigmoid output per bottleneck class, binary cross-entropy averaged
+ * over batch and outputs. Parameters are packed W1 (sizes[1] x sizes[0], row-major), b1,
+ * W2, b2, W3, b3.                                                                        */
+static int64_t mlp_nparams(const int32_t *s) {
+  return (int64_t)s[1] * s[0] + s[1] + (int64_t)s[2] * s[1] + s[2] + (int64_t)s[3] * s[2] +
+         s[3];
+}
+
+int64_t oracle_mlp_nparams(const int32_t *sizes) { return mlp_nparams(sizes); }
+
+/* FP64 loss; when grad is non-null also the gradient of the loss (backpropagation). */
+double oracle_mlp_loss_grad_f64(const int32_t *sizes, const double *params, int64_t batch,
+                                const double *X, const double *Y, double *grad,
+                                double *probs) {
+  int n0 = sizes[0], n1 = sizes[1], n2 = sizes[2], n3 = sizes[3];
+  const double *W1 = params, *b1 = W1 + (int64_t)n1 * n0, *W2 = b1 + n1,
+               *b2 = W2 + (int64_t)n2 * n1, *W3 = b2 + n2, *b3 = W3 + (int64_t)n3 * n2;
+  double *h1 = (double *)malloc(sizeof(double) * (size_t)n1);
+  double *h2 = (double *)malloc(sizeof(double) * (size_t)n2);
+  double *g1 = (double *)malloc(sizeof(double) * (size_t)n1);
+  double *g2 = (double *)malloc(sizeof(double) * (size_t)n2);
+  double *g3 = (double *)malloc(sizeof(double) * (size_t)n3);
+  int64_t np = mlp_nparams(sizes);
+  if (grad) memset(grad, 0, sizeof(double) * (size_t)np);
+  double *dW1 = grad, *db1 = grad ? dW1 + (int64_t)n1 * n0 : 0,
+         *dW2 = grad ? db1 + n1 : 0, *db2 = grad ? dW2 + (int64_t)n2 * n1 : 0,
+         *dW3 = grad ? db2 + n2 : 0, *db3 = grad ? dW3 + (int64_t)n3 * n2 : 0;
+  double loss = 0.0;
+  double inv = 1.0 / ((double)batch * (double)n3);
+  for (int64_t b = 0; b < batch; ++b) {
+    const double *x = X + b * n0;
+    const double *y = Y + b * n3;
+    for (int i = 0; i < n1; ++i) {
+      double a = b1[i];
+      for (int k = 0; k < n0; ++k) a += W1[(int64_t)i * n0 + k] * x[k];
+      h1[i] = a > 0.0 ? a : 0.0;
+    }
+    for (int i = 0; i < n2; ++i) {
+      double a = b2[i];
+      for (int k = 0; k < n1; ++k) a += W2[(int64_t)i * n1 + k] * h1[k];
+      h2[i] = a > 0.0 ? a : 0.0;
+    }
+    for (int i = 0; i < n3; ++i) {
+      double z = b3[i];
+      for (int k = 0; k < n2; ++k) z += W3[(int64_t)i * n2 + k] * h2[k];
+      double p = 1.0 / (1.0 + exp(-z));
+      if (probs) probs[b * n3 + i] = p;
+      /* -[y log p + (1 - y) log(1 - p)] written stably in terms of z */
+      loss += (z > 0.0 ? z : 0.0) - y[i] * z + log1p(exp(-fabs(z)));
+      g3[i] = (p - y[i]) * inv;
+    }
+    if (!grad) continue;
+    for (int i = 0; i < n3; ++i) {
+      db3[i] += g3[i];
+      for (int k = 0; k < n2; ++k) dW3[(int64_t)i * n2 + k] += g3[i] * h2[k];
+    }
+    for (int k = 0; k < n2; ++k) {
+      double a = 0.0;
+      for (int i = 0; i < n3; ++i) a += W3[(int64_t)i * n2 + k] * g3[i];
+      g2[k] = h2[k] > 0.0 ? a : 0.0;
+    }
+    for (int i = 0; i < n2; ++i) {
+      db2[i] += g2[i];
+      for (int k = 0; k < n1; ++k) dW2[(int64_t)i * n1 + k] += g2[i] * h1[k];
+    }
+    for (int k = 0; k < n1; ++k) {
+      double a = 0.0;
+      for (int i = 0; i < n2; ++i) a += W2[(int64_t)i * n1 + k] * g2[i];
+      g1[k] = h1[k] > 0.0 ? a : 0.0;
+    }
+    for (int i = 0; i < n1; ++i) {
+      db1[i] += g1[i];
+      for (int k = 0; k < n0; ++k) dW1[(int64_t)i * n0 + k] += g1[i] * x[k];
+    }
+  }
+  free(h1);
+  free(h2);
+  free(g1);
+  free(g2);
+  free(g3);
+  return loss * inv;
+}
+
+/* FP32 inference with the exact operation order the selector decision is defined by:
+ * each unit starts from its bias and adds w_k * in_k for k = 0, 1, ... with one fused
+ * multiply-add per term; ReLU on hidden units; the outputs are the class logits.         */
+void oracle_mlp_logits_f32(const int32_t *sizes, const float *params, int64_t batch,
+                           const float *X, float *logits) {
+  int n0 = sizes[0], n1 = sizes[1], n2 = sizes[2], n3 = sizes[3];
+  const float *W1 = params, *b1 = W1 + (int64_t)n1 * n0, *W2 = b1 + n1,
+              *b2 = W2 + (int64_t)n2 * n1, *W3 = b2 + n2, *b3 = W3 + (int64_t)n3 * n2;
+  float h1[1024], h2[1024];
+  if (n1 > 1024 || n2 > 1024) return;
+  for (int64_t b = 0; b < batch; ++b) {
+    const float *x = X + b * n0;
+    for (int i = 0; i < n1; ++i) {
+      float a = b1[i];
+      for (int k = 0; k < n0; ++k) a = fmaf(W1[(int64_t)i * n0 + k], x[k], a);
+      h1[i] = a > 0.0f ? a : 0.0f;
+    }
+    for (int i = 0; i < n2; ++i) {
+      float a = b2[i];
+      for (int k = 0; k < n1; ++k) a = fmaf(W2[(int64_t)i * n1 + k], h1[k], a);
+      h2[i] = a > 0.0f ? a : 0.0f;
+    }
+    for (int i = 0; i < n3; ++i) {
+      float a = b3[i];
+      for (int k = 0; k < n2; ++k) a = fmaf(W3[(int64_t)i * n2 + k], h2[k], a);
+      logits[b * n3 + i] = a;
+    }
+  }
+}
+
+/* log2(1 + v) for v >= 0 in FP32, used to compress the heavy-tailed features before the
+ * MLP. w = 1 + v = m 2^e with m in [sqrt(2)/2, sqrt(2)) taken from the bits of w, then
+ * log2(m) = (2 / ln 2) atanh(t), t = (m - 1) / (m + 1), |t| < 0.1716, with the atanh
+ * Taylor series t + t^3/3 + ... + t^11/11 evaluated by Horner's rule in t^2 using fmaf.
+ * Inputs below 0 or NaN return 0.                                                         */
+float oracle_log2p1_f32(float v) {
+  if (!(v > 0.0f)) return 0.0f;
+  float w = 1.0f + v;
+  uint32_t u;
+  memcpy(&u, &w, sizeof u);
+  int e = (int)((u >> 23) & 0xFFu) - 127;
+  uint32_t mb = (u & 0x007FFFFFu) | 0x3F800000u;
+  float m;
+  memcpy(&m, &mb, sizeof m);
+  if (m > 1.41421356f) {
+    m = m * 0.5f;
+    e += 1;
+  }
+  float t = (m - 1.0f) / (m + 1.0f);
+  float t2 = t * t;
+  float p = 1.0f / 11.0f;
+  p = fmaf(p, t2, 1.0f / 9.0f);
+  p = fmaf(p, t2, 1.0f / 7.0f);
+  p = fmaf(p, t2, 1.0f / 5.0f);
+  p = fmaf(p, t2, 1.0f / 3.0f);
+  p = fmaf(p, t2, 1.0f);
+  float l = (t * p) * 2.88539008f; /* 2 / ln 2 */
+  return (float)e + l;
+}
+
+void oracle_log2p1_f32_array(const float *in, float *out, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) out[i] = oracle_log2p1_f32(in[i]);
+}
