@@ -1,0 +1,342 @@
+"""Benchmark: adaptive CSR SpMV GFLOP/s and HBM-roofline fraction on one GB300.
+
+Default workload: the bandwidth-bound 27-point stencil on a 160^3 grid (N = 4,096,000,
+NNZ = 109,215,352), FP64 values, FP64 x. A step is one y = A x through the tuned handle
+(the amortized hot loop); tuning and preprocessing happen once before the timed region and
+are reported as t_pre. The plain CSR-vector baseline and the FP32 / BF16 storage variants
+are timed beside it. Inputs (about 1.2 GB) are larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank runs an independent replica (the method does not shard: one
+matrix, one GPU); rank 0 prints one JSON line with the whole-job throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 8000.0
+
+
+def _peaks():
+    try:
+        with open(MEASURED) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------------ clocks -----
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ---------------------------------------------------------------------- workloads ----
+WORKLOADS = {
+    "stencil27_160": dict(desc="27-point 3-D stencil, 160^3 grid, natural order, FP64 values "
+                               "U[-1,1] off-diagonal with a dominant diagonal, FP64 x",
+                          make=lambda: synth.stencil_27pt(160), x_seed=synth.SEED_BASE + 12),
+    "laplacian_256": dict(desc="5-point 2-D Laplacian 256x256, FP64", make=lambda: synth.laplacian_2d(256),
+                          x_seed=synth.SEED_BASE + 11),
+    "powerlaw_4m": dict(desc="power-law rows Zipf(1.8) clipped at 200,000, N=4,000,000, FP32",
+                        make=lambda: synth.power_law(4_000_000), x_seed=synth.SEED_BASE + 13),
+    "scattered_16m": dict(desc="16,000,000 rows x 8 uniform random columns, FP64",
+                          make=lambda: synth.scattered(16_000_000, 8), x_seed=synth.SEED_BASE + 14),
+}
+
+
+def dtype_bytes(code):
+    return {0: 8, 1: 4, 2: 2}[code]
+
+
+def alg_bytes(n_rows, n_cols, nnz, variant, storage, vec):
+    """Compulsory traffic of one SpMV with the variant's own format (P_MB's M_min):
+    row pointers, column indices (int32 or 16-bit deltas + per-row base), values, x, y."""
+    idx = 2 if variant[1] == 1 else 4
+    extra = 4 * n_rows if variant[1] == 1 else 0
+    return (4 * (n_rows + 1) + (idx + dtype_bytes(storage)) * nnz + extra
+            + dtype_bytes(vec) * (n_rows + n_cols))
+
+
+# --------------------------------------------------------------------------- ours ----
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_1711_05487_gb300 import api
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    wl = WORKLOADS[args.workload]
+    t0 = time.time()
+    m = wl["make"]()
+    gen_s = time.time() - t0
+    x_host = synth.uniform_vector(m.n_cols, wl["x_seed"])
+    stream = torch.cuda.Stream()
+    A = api.SpmvMatrix.from_csr(m, stream=stream)
+    vec_t = torch.float64 if m.val.dtype == np.float64 else torch.float32
+    if m.val.dtype != np.float64:
+        A.set_precision("f32", "f32", "f32", stream=stream)
+    x = torch.from_numpy(x_host).to(vec_t).cuda()
+    y = torch.empty(m.n_rows, dtype=vec_t, device="cuda")
+    flops = 2.0 * m.nnz
+
+    def timed(K, W):
+        with torch.cuda.stream(stream):
+            for _ in range(W):
+                A.run(x, y, stream=stream)
+            stream.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(K):
+                A.run(x, y, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / K
+
+    # plain CSR-vector baseline
+    A.set_variant(stream=stream)
+    base_ms = timed(args.steps, args.warmup)
+    # adaptive: profile-guided classification + Table II variant + autotuned width
+    rep = A.tune("profile", stream=stream)
+    peak, peak_kind = _peaks()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ms = timed(args.steps, args.warmup)
+    clocks.stop()
+    storage = A.storage
+    ab = alg_bytes(m.n_rows, m.n_cols, m.nnz, rep.variant, storage, A.vec)
+    achieved = ab / (ms * 1e-3) / 1e9
+    csr_bytes = alg_bytes(m.n_rows, m.n_cols, m.nnz, (0, 0, 0, 0, 0), storage, A.vec)
+    value = world * flops / (ms * 1e-3) / 1e9
+    # end to end through the C ABI with host buffers (x in, y out, copies inside the timing)
+    xh = torch.from_numpy(x_host).to(vec_t).pin_memory()
+    yh = torch.empty(m.n_rows, dtype=vec_t).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        A.run_host(xh, yh, stream=stream)
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        A.run_host(xh, yh, stream=stream)
+    e2e_ms = (time.perf_counter() - te) * 1e3 / args.steps
+    # reduced-precision value storage on the same matrix (FP64 originals rounded once)
+    extra = {}
+    if m.val.dtype == np.float64 and not args.quick:
+        for st, vt, at in (("f32", "f64", "f64"), ("f32", "f32", "f32"), ("bf16", "f32", "f32")):
+            A.set_precision(st, vt, at, stream=stream)
+            r2 = A.tune("profile", stream=stream)
+            xv = x.to(torch.float64 if vt == "f64" else torch.float32)
+            yv = torch.empty(m.n_rows, dtype=xv.dtype, device="cuda")
+            x_old, y_old = x, y
+            x, y = xv, yv
+            t2 = timed(args.steps, args.warmup)
+            x, y = x_old, y_old
+            b2 = alg_bytes(m.n_rows, m.n_cols, m.nnz, r2.variant, A.storage, A.vec)
+            extra[f"{st}/{vt}/{at}"] = {
+                "gflops": round(flops / (t2 * 1e-3) / 1e9, 1),
+                "variant": list(r2.variant), "classes": r2.class_names,
+                "frac_hbm": round(b2 / (t2 * 1e-3) / 1e9 / peak, 3)}
+        A.set_precision("f64", "f64", "f64", stream=stream)
+    out = {
+        "metric": "SpMV GFLOP/s (2*nnz/t), adaptive (profile-guided) vs plain CSR-vector",
+        "value": round(value, 2),
+        "unit": "GFLOP/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {0: "f64", 1: "f32", 2: "bf16"}[storage],
+        "data": "synthetic (seeded)",
+        "config": {"workload": args.workload, "desc": wl["desc"], "n_rows": m.n_rows,
+                   "nnz": m.nnz, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (no flush needed)" if csr_bytes > 200e6
+                   else "L2-resident working set"},
+        "baseline_csr_vector": {"gflops": round(flops / (base_ms * 1e-3) / 1e9, 2),
+                                "ms": round(base_ms, 5),
+                                "frac_hbm": round(csr_bytes / (base_ms * 1e-3) / 1e9 / peak, 3)},
+        "speedup_vs_csr_vector": round(base_ms / ms, 3),
+        "tune": {"classes": rep.class_names, "variant": list(rep.variant),
+                 "p_gflops": {k: round(v, 1) for k, v in rep.p.items()},
+                 "b_max_gbs": round(rep.b_max_gbs, 1), "t_pre_ms": round(rep.t_pre_ms, 2)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_kind": peak_kind, "alg_bytes": ab,
+                     "frac_of_nominal_8tbs": round(achieved / NOMINAL_HBM_GBS, 4),
+                     "csr_fp64_bytes_frac": round(csr_bytes / (ms * 1e-3) / 1e9 / peak, 4)},
+        "e2e": {"value": round(world * flops / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+                "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
+                "d2h_bytes_per_step": int(yh.numel() * yh.element_size()),
+                "ms_per_step": round(e2e_ms, 4)},
+        "gpu_launches": args.steps * (2 if rep.variant[0] == 1 else 1),
+        "precision_variants": extra,
+        "clocks": clocks.summary(),
+        "gen_s": round(gen_s, 1),
+    }
+    return out, m
+
+
+def cpu_baseline(m, x_host, budget_s=10.0):
+    """The oracle's single-threaded FP64 CSR SpMV timed on the host on the same matrix."""
+    import oracle
+    oracle.lib()
+    t = time.perf_counter()
+    oracle.spmv(m.rowptr, m.colind, m.val, x_host)
+    one = time.perf_counter() - t
+    reps = max(1, min(20, int(budget_s / max(one, 1e-6))))
+    rates = []
+    for _ in range(reps):
+        t = time.perf_counter()
+        oracle.spmv(m.rowptr, m.colind, m.val, x_host)
+        rates.append(2.0 * m.nnz / (time.perf_counter() - t) / 1e9)
+    return {"value": round(oracle.harmonic_mean(rates), 4), "unit": "GFLOP/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"full matrix, {reps} SpMVs, harmonic mean of per-SpMV rates"}
+
+
+# ---------------------------------------------------------------------- reference ----
+def run_reference(args):
+    """The oracle (plain FP64 CPU CSR SpMV), timed on the host cores: --steps SpMVs of the
+    same workload after --warmup untimed ones."""
+    import oracle
+    oracle.lib()
+    wl = WORKLOADS[args.workload]
+    m = wl["make"]()
+    x = synth.uniform_vector(m.n_cols, wl["x_seed"]).astype(np.float64)
+    for _ in range(args.warmup):
+        oracle.spmv(m.rowptr, m.colind, m.val, x)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.spmv(m.rowptr, m.colind, m.val, x)
+    dt = (time.perf_counter() - t) / args.steps
+    v = 2.0 * m.nnz / dt / 1e9
+    return {
+        "impl": "reference", "metric": "SpMV GFLOP/s (2*nnz/t), adaptive (profile-guided) vs "
+        "plain CSR-vector", "value": round(v, 4), "unit": "GFLOP/s", "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)",
+        "config": {"workload": args.workload, "desc": wl["desc"], "n_rows": m.n_rows,
+                   "nnz": m.nnz},
+        "cpu_baseline": {"value": round(v, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": f"full matrix, {args.steps} SpMVs"},
+        "e2e": {"value": round(v, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=128)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="stencil27_160")
+    ap.add_argument("--quick", action="store_true", help="skip the precision variants")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            if args.steps > 20:
+                args.steps = 20
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    out, m = run_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            wl = WORKLOADS[args.workload]
+            out["cpu_baseline"] = cpu_baseline(m, synth.uniform_vector(m.n_cols, wl["x_seed"]))
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

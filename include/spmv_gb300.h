@@ -1,0 +1,307 @@
+/*
+ * spmv_gb300.h -- C ABI of a GB300 (sm_103a) bottleneck-adaptive CSR SpMV library.
+ *
+ * The library implements the method of Elafrou, Goumas and Koziris, "Performance Analysis
+ * and Optimization of Sparse Matrix-Vector Multiplication on Modern Multi- and Many-Core
+ * Processors" (arXiv 1711.05487): y = A x for a CSR matrix (Section II, Fig. 1), a
+ * classifier that finds the matrix's SpMV bottleneck classes -- memory bandwidth (MB),
+ * memory latency (ML), thread imbalance (IMB), computation (CMP) -- by profiling
+ * (Section III-B/C, Fig. 3) or from matrix features (Section III-D, Table I), and a pool of
+ * low-preprocessing CSR optimizations applied jointly per detected class (Section III-E,
+ * Table II). A learned selector (a small MLP trained on the GPU) stands in for the paper's
+ * decision tree.
+ *
+ * Conventions for every entry point:
+ *   - Plain C types only. A stream argument is a cudaStream_t passed as void*; NULL is the
+ *     legacy default stream. A "device pointer" is CUDA global memory of the current device.
+ *   - Every call returns spmv_status and never throws or aborts. On error nothing is
+ *     written to the caller's outputs unless stated.
+ *   - Index arrays are int32 (n_rows, n_cols, nnz < 2^31). CSR columns must be sorted and
+ *     unique within each row.
+ *   - Calls are not thread-safe on the same handle; different handles are independent.
+ */
+#ifndef SPMV_GB300_H
+#define SPMV_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spmv_matrix *spmv_handle_t;
+typedef struct spmv_batch *spmv_batch_t;
+typedef struct spmv_selector *spmv_selector_t;
+typedef void *spmv_stream_t; /* cudaStream_t */
+
+typedef enum {
+  SPMV_OK = 0,
+  SPMV_ERR_INVALID_CSR = 1,       /* rowptr/colind violate the CSR definition           */
+  SPMV_ERR_UNSUPPORTED_DTYPE = 2, /* dtype combination not offered                      */
+  SPMV_ERR_OOM = 3,               /* device allocation failed                           */
+  SPMV_ERR_NOT_TUNED = 4,         /* spmv_run before spmv_tune / spmv_set_variant        */
+  SPMV_ERR_CUDA = 5,              /* a CUDA runtime call failed                         */
+  SPMV_ERR_TIMEOUT = 6,           /* a bounded device-side wait gave up                 */
+  SPMV_ERR_ARG = 7,               /* invalid argument (null pointer, size, k ...)       */
+  SPMV_ERR_NO_SELECTOR = 8        /* learned mode without a selector                    */
+} spmv_status;
+
+typedef enum { SPMV_F64 = 0, SPMV_F32 = 1, SPMV_BF16 = 2 } spmv_dtype;
+
+typedef enum {
+  SPMV_TUNE_PROFILE = 0,  /* Section III-C: micro-benchmarks + Fig. 3 rules            */
+  SPMV_TUNE_FEATURES = 1, /* Section III-D: Table I features + fixed rules              */
+  SPMV_TUNE_LEARNED = 2,  /* features + MLP selector, profiling as fallback             */
+  SPMV_TUNE_FIXED = 3     /* use opts->fixed                                            */
+} spmv_mode;
+
+/* Bottleneck classes (Section III-A); a class set is a bitmask, 0 = not worth optimizing. */
+enum { SPMV_CLASS_MB = 1, SPMV_CLASS_ML = 2, SPMV_CLASS_IMB = 4, SPMV_CLASS_CMP = 8 };
+
+/* One point of the optimization pool (Table II, applied jointly). */
+typedef struct {
+  int32_t partition; /* 0: one sub-warp per row, rows handed to CTAs by the hardware
+                        scheduler; 1: merge-path tiles, long rows split across tiles
+                        (the matrix decomposition of Fig. 4/5)                            */
+  int32_t index;     /* 0: int32 columns; 1: 16-bit column deltas with escape rows (MB)   */
+  int32_t xpath;     /* 0: default; 1: x kept L2-resident (evict-last gathers through the
+                        read-only path, evict-first streams) (ML)                         */
+  int32_t vec;       /* 0: scalar loads; 1: 128-bit loads of val/colind, unrolled (MB/CMP) */
+  int32_t vs;        /* sub-warp width for partition 0: 2,4,8,16,32; 0 = heuristic       */
+} spmv_variant;
+
+#define SPMV_NUM_FEATURES 14
+/* Feature order (Table I): size, density, nnz_min, nnz_max, nnz_avg, nnz_sd, bw_min,
+ * bw_max, bw_avg, bw_sd, scatter_avg, scatter_sd, clustering_avg, misses_avg.          */
+
+typedef struct {
+  double t_imb;          /* Fig. 3 T_IMB, default 1.24                                   */
+  double t_ml;           /* Fig. 3 T_ML, default 1.25                                    */
+  double t_mb;           /* "P_CSR close to P_MB" read as P_CSR/P_MB >= t_mb, default 0.75 */
+  double long_row_ratio; /* IMB sub-choice: nnz_max > ratio * nnz_avg -> decomposition (32) */
+  int32_t autotune;      /* 1: pick the sub-warp width by timing (default 1)             */
+  int32_t reps;          /* timed repetitions per probe (default 20)                     */
+  spmv_variant fixed;    /* SPMV_TUNE_FIXED only                                         */
+  spmv_selector_t selector; /* SPMV_TUNE_LEARNED only                                    */
+  double min_margin;     /* learned: smallest |logit| accepted, else profile (default 0) */
+} spmv_tune_opts;
+
+typedef struct {
+  uint32_t classes;      /* detected class set                                           */
+  int32_t mode_used;     /* route that decided (LEARNED may fall back to PROFILE)        */
+  spmv_variant variant;  /* variant installed on the handle                              */
+  double p[6];           /* P_CSR, P_MB, P_ML, P_IMB, P_CMP, P_peak in GFLOP/s (profile) */
+  double b_max_gbs;      /* bandwidth used for P_MB / P_peak                             */
+  double features[SPMV_NUM_FEATURES];
+  double margin;         /* learned: smallest |logit| of the MLP decision                */
+  double t_pre_ms;       /* whole spmv_tune wall time                                    */
+  double t_classify_ms;  /* probes or features (+ inference)                             */
+  double t_prep_ms;      /* format conversion / partitioning                             */
+  double t_autotune_ms;  /* sub-warp width sweep                                         */
+} spmv_tune_report;
+
+/* ---------------------------------------------------------------- matrix handles ---- */
+
+/* Fills opts with the defaults listed above. */
+spmv_status spmv_tune_opts_default(spmv_tune_opts *opts);
+
+/* Section II (CSR): copies the matrix into library-owned device memory and validates it
+ * on the device. row_ptr[n_rows + 1], col_ind[nnz], val[nnz] in dtype val_type are host
+ * pointers (device_ptrs = 0) or device pointers (device_ptrs = 1); the caller keeps
+ * ownership and may free them when the call returns. Storage, x/y and accumulation
+ * dtypes start as val_type / F64 / F64 (F32 / F32 / F32 for F32 and BF16 input).
+ * Errors: SPMV_ERR_ARG (null out or arrays, negative sizes), SPMV_ERR_INVALID_CSR,
+ * SPMV_ERR_OOM, SPMV_ERR_CUDA. The call synchronizes the stream. */
+spmv_status spmv_create(spmv_handle_t *out, int64_t n_rows, int64_t n_cols, int64_t nnz,
+                        const int32_t *row_ptr, const int32_t *col_ind, const void *val,
+                        spmv_dtype val_type, int32_t device_ptrs, spmv_stream_t stream);
+
+/* Frees every device buffer of the handle (synchronizes the device first). */
+spmv_status spmv_destroy(spmv_handle_t h);
+
+/* Value storage precision (build addition): storage in F64 / F32 / BF16, x and y in
+ * vec_type (F64 or F32), products accumulated in acc_type (F64 or F32). Conversion is
+ * round-to-nearest-even straight from the input values. Offered: storage F64 with
+ * vec = acc = F64; storage F32 or BF16 with (vec, acc) in {(F64,F64),(F32,F32),(F32,F64)}.
+ * Invalidates the tuned variant (spmv_tune or spmv_set_variant must follow). */
+spmv_status spmv_set_precision(spmv_handle_t h, spmv_dtype storage, spmv_dtype vec_type,
+                               spmv_dtype acc_type, spmv_stream_t stream);
+
+/* Section III: classify the matrix with the given route, map classes to optimizations
+ * (Table II), build the variant's data (delta index, merge-path table) and, if
+ * opts->autotune, pick the sub-warp width by timing. opts and report may be NULL
+ * (defaults / no report). Synchronizes the stream (the profile route times kernels).
+ * Errors: SPMV_ERR_NO_SELECTOR (learned without opts->selector), SPMV_ERR_OOM, CUDA. */
+spmv_status spmv_tune(spmv_handle_t h, spmv_mode mode, const spmv_tune_opts *opts,
+                      spmv_tune_report *report, spmv_stream_t stream);
+
+/* Installs a variant directly (same preprocessing as spmv_tune, no classification). */
+spmv_status spmv_set_variant(spmv_handle_t h, const spmv_variant *v, spmv_stream_t stream);
+
+/* Fig. 1: y = A x (y overwritten), asynchronous on stream, no host synchronization.
+ * x[n_cols], y[n_rows] are caller-owned device pointers in the handle's vec_type; they
+ * must stay valid until the stream work completes and must not overlap.
+ * Errors: SPMV_ERR_NOT_TUNED, SPMV_ERR_ARG, SPMV_ERR_CUDA (launch failure). */
+spmv_status spmv_run(spmv_handle_t h, const void *x, void *y, spmv_stream_t stream);
+
+/* y = A x with HOST buffers: copies x to a handle-owned device buffer, runs, copies y
+ * back, on stream; returns after the stream has finished (the end-to-end path).
+ * Pinned host memory gives asynchronous, full-speed copies. */
+spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
+                          spmv_stream_t stream);
+
+/* Y = A X for k right-hand sides (SpMM), X (n_cols x k) and Y (n_rows x k) row-major
+ * device arrays in vec_type. Uses the sub-warp row kernel with int32 columns whatever
+ * the tuned variant; k >= 1. */
+spmv_status spmv_run_spmm(spmv_handle_t h, const void *X, void *Y, int32_t k,
+                          spmv_stream_t stream);
+
+/* Copies the handle's CSR back (device pointers: row_ptr[n_rows+1], col_ind[nnz],
+ * val[nnz] in the storage dtype). Columns are decoded from the 16-bit delta index when
+ * that variant is installed, so this is the format round-trip check. Synchronizes. */
+spmv_status spmv_export_csr(spmv_handle_t h, int32_t *row_ptr, int32_t *col_ind, void *val,
+                            spmv_stream_t stream);
+
+/* Copies the 16-bit delta index (Section III-E, MB) into caller device buffers:
+ * base[n_rows], delta[nnz], esc_col[*n_esc]; pass esc_col = NULL to query *n_esc.
+ * SPMV_ERR_NOT_TUNED if the installed variant has no delta index. */
+spmv_status spmv_get_delta16(spmv_handle_t h, int32_t *base, uint16_t *delta,
+                             int32_t *esc_col, int64_t *n_esc, spmv_stream_t stream);
+
+/* Copies the merge-path tile table (rows ended, nonzeros consumed) for tile boundaries
+ * 0..n_tiles into coord (device, int32[2 * (n_tiles + 1)]); pass coord = NULL to query
+ * *n_tiles and *items_per_tile. */
+spmv_status spmv_get_merge_path(spmv_handle_t h, int32_t *coord, int64_t *n_tiles,
+                                int64_t *items_per_tile, spmv_stream_t stream);
+
+/* Section III-D, Table I features computed on the device (exact integer moments, host
+ * finalization); line_bytes is the cache-line size for misses_i (128 = GPU L2 line,
+ * divided by the x element size). features[14] host, isum[12] host (may be NULL):
+ * sum nnz, sum bw, sum q_scatter, sum q_clustering, sum misses, sum ngroups, nnz_min,
+ * nnz_max, bw_min, bw_max, low 64 bits of sum nnz^2 and of sum bw^2. Synchronizes. */
+spmv_status spmv_features(spmv_handle_t h, int32_t line_bytes, double *features,
+                          uint64_t *isum, spmv_stream_t stream);
+
+/* Section III-B profile: runs the static-partition baseline (P_CSR, per-CTA timers for
+ * P_IMB), the P_ML kernel (colind'[j] = row of j) and the P_CMP kernel (x[i] only), and
+ * computes P_MB, P_peak from byte counts and the measured B_max. p[6] host =
+ * P_CSR, P_MB, P_ML, P_IMB, P_CMP, P_peak (GFLOP/s); b_max_gbs host. Synchronizes. */
+spmv_status spmv_profile(spmv_handle_t h, int32_t reps, double *p, double *b_max_gbs,
+                         spmv_stream_t stream);
+
+/* Runs one profiling kernel once into y (device, vec_type): which = 0 the static-partition
+ * baseline, 1 the P_ML kernel, 2 the P_CMP kernel. For tests of their construction. */
+spmv_status spmv_profile_kernel(spmv_handle_t h, int32_t which, const void *x, void *y,
+                                spmv_stream_t stream);
+
+/* Sustained read bandwidth of the current device (GB/s, 1e9 B/s) for a buffer far larger
+ * than L2 (hbm_gbs) and one resident in L2 (l2_gbs): the B_max of Section III-B and of its
+ * footnote. Measured once per device and cached. */
+spmv_status spmv_probe_bandwidth(double *hbm_gbs, double *l2_gbs);
+
+/* Fig. 3 on a P-vector (csr, mb, ml, imb, cmp, peak); pure function. */
+uint32_t spmv_classify(const double *p, double t_imb, double t_ml, double t_mb);
+
+/* Table II (jointly applied) for a class set; vs is left 0 (heuristic). Pure function. */
+void spmv_variant_for_classes(uint32_t classes, double nnz_avg, double nnz_max,
+                              double long_row_ratio, spmv_variant *out);
+
+/* Section III-B closed forms: out[0] = P_MB, out[1] = P_peak (GFLOP/s, b_max in GB/s),
+ * out[2] = S_format + S_x + S_y (bytes) for int32 CSR with the given element sizes. */
+void spmv_bounds(int64_t n_rows, int64_t n_cols, int64_t nnz, int32_t idx_bytes,
+                 int32_t val_bytes, int32_t vec_bytes, double b_max_gbs, double *out);
+
+/* Feature route rules (Section III-D, fixed rules standing in for the trained tree) on
+ * the 14 Table I features: IMB if nnz_max > long_row_ratio * nnz_avg; ML if
+ * misses_avg >= nnz_avg / 2 and vec_bytes * n_cols > l2_bytes / 2; CMP if size = 1 or
+ * nnz_avg < 4; MB if none of these and size = 0. Pure function. */
+uint32_t spmv_feature_rules(const double *features, int64_t n_cols, int32_t vec_bytes,
+                            int64_t l2_bytes, double long_row_ratio);
+
+/* Validates a CSR held in device memory; *code = 0 valid, 1 rowptr[0] != 0, 2 rowptr
+ * decreases, 3 rowptr[n_rows] != nnz, 4 column out of range, 5 columns not strictly
+ * increasing (the first offending element in storage order decides 4 vs 5). */
+spmv_status spmv_validate_csr(int64_t n_rows, int64_t n_cols, int64_t nnz,
+                              const int32_t *row_ptr, const int32_t *col_ind, int32_t *code,
+                              spmv_stream_t stream);
+
+/* FP64 -> storage dtype conversion (round to nearest even, no double rounding for BF16)
+ * of n device values into out (device). */
+spmv_status spmv_round_values(const double *in, void *out, int64_t n, spmv_dtype to,
+                              spmv_stream_t stream);
+
+/* Reads (and clears) the handle's device error word: 0 none, 1 a bounded wait expired. */
+spmv_status spmv_get_last_device_error(spmv_handle_t h, int32_t *code);
+
+/* Device bytes held by the handle. */
+spmv_status spmv_get_device_bytes(spmv_handle_t h, int64_t *bytes);
+
+const char *spmv_status_string(spmv_status s);
+
+/* ------------------------------------------------------------- learned selector ---- */
+/* The MLP has layer sizes n_in -> h1 -> h2 -> 4 (ReLU hidden units, one logit per class
+ * MB, ML, IMB, CMP); parameters packed W1 (h1 x n_in, row-major), b1, W2, b2, W3, b3, FP32.
+ * Its inputs are SPMV_MLP_INPUTS numbers derived from the Table I features.             */
+#define SPMV_MLP_INPUTS 12
+
+/* Derived inputs on the device: feat (batch x 16 doubles: the 14 Table I features, then
+ * n_rows and nnz), mu / inv_sigma (SPMV_MLP_INPUTS floats each, standardization; NULL =
+ * none) -> X (batch x SPMV_MLP_INPUTS floats). All pointers device. */
+spmv_status spmv_mlp_inputs(const double *feat, int64_t batch, const float *mu,
+                            const float *inv_sigma, float *X, spmv_stream_t stream);
+
+/* FP32 logits (batch x sizes[3]) with the fixed multiply-add order that defines the
+ * decision: each unit starts from its bias and adds w_k * in_k in k order (fmaf). */
+spmv_status spmv_mlp_logits(const int32_t *sizes, const float *params, int64_t batch,
+                            const float *X, float *logits, spmv_stream_t stream);
+
+/* Mean binary cross-entropy of sigmoid(logits) against Y (batch x sizes[3], 0/1) and
+ * its gradient w.r.t. the packed parameters (backpropagation, FP32 with FP64 sums over
+ * the batch, fixed order). grad and loss are device pointers. */
+spmv_status spmv_mlp_loss_grad(const int32_t *sizes, const float *params, int64_t batch,
+                               const float *X, const float *Y, float *grad, float *loss,
+                               spmv_stream_t stream);
+
+/* Runs `steps` full-batch Adam steps (lr, beta1, beta2, eps) on params in place; m and v
+ * are the Adam moments (device, zero at step 0), t0 the number of steps already taken.
+ * loss_hist (device, may be NULL) receives the loss before each step. */
+spmv_status spmv_mlp_train(const int32_t *sizes, float *params, float *m, float *v,
+                           int64_t batch, const float *X, const float *Y, int32_t steps,
+                           int32_t t0, float lr, float beta1, float beta2, float eps,
+                           float *loss_hist, spmv_stream_t stream);
+
+/* A selector: host copies of sizes[4], params, mu and inv_sigma (SPMV_MLP_INPUTS floats
+ * each) are uploaded to the current device. */
+spmv_status spmv_selector_create(spmv_selector_t *out, const int32_t *sizes,
+                                 const float *params, const float *mu,
+                                 const float *inv_sigma);
+spmv_status spmv_selector_destroy(spmv_selector_t s);
+
+/* Class set predicted for a feature vector (16 doubles, host): logit > 0 per class.
+ * *margin = smallest |logit|. */
+spmv_status spmv_selector_predict(spmv_selector_t s, const double *feat16, uint32_t *classes,
+                                  double *margin, spmv_stream_t stream);
+
+/* ----------------------------------------------------------------- batched SpMM ---- */
+/* A batch of `count` tuned handles with FP32 storage, FP32 x/y and FP32 accumulation;
+ * X[i] (n_cols_i x k[i]) and Y[i] (n_rows_i x k[i]) are row-major device arrays, k[i] in
+ * {1, 4, 16}. The batch plans row-block work items (long rows split, partials summed in
+ * FP64) and owns a CUDA graph of its launches. */
+spmv_status spmv_batch_create(spmv_batch_t *out, const spmv_handle_t *handles, int32_t count,
+                              const void *const *X, void *const *Y, const int32_t *k,
+                              spmv_stream_t stream);
+
+/* All products of the batch in one persistent launch (CTAs take work items from a device
+ * counter) plus a fixup launch, replayed from a CUDA graph captured on the first call. */
+spmv_status spmv_run_batched(spmv_batch_t b, spmv_stream_t stream);
+
+/* The same work as plain per-matrix launches (no graph, no persistence), for comparison. */
+spmv_status spmv_run_batched_sequential(spmv_batch_t b, spmv_stream_t stream);
+
+spmv_status spmv_batch_destroy(spmv_batch_t b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPMV_GB300_H */

@@ -101,6 +101,10 @@ def _declare(L):
     L.oracle_log2p1_f32.restype = ctypes.c_float
     L.oracle_log2p1_f32_array.argtypes = [_P, _P, _I64]
     L.oracle_log2p1_f32_array.restype = None
+    L.oracle_feature_rules.argtypes = [_P, _I64, _I64, _I64, _D]
+    L.oracle_feature_rules.restype = ctypes.c_uint32
+    L.oracle_mlp_inputs.argtypes = [_P, _I64, _P, _P, _P]
+    L.oracle_mlp_inputs.restype = None
 
 
 def _p(a: np.ndarray):
@@ -237,7 +241,27 @@ def amortization_iters(t_pre, t_base, t_opt) -> float:
     return float(lib().oracle_amortization_iters(t_pre, t_base, t_opt))
 
 
+def feature_rules(features14, n_cols, vec_bytes, llc_bytes, long_ratio=32.0) -> int:
+    f = _c(features14, np.float64)
+    return int(lib().oracle_feature_rules(_p(f), int(n_cols), int(vec_bytes), int(llc_bytes),
+                                          float(long_ratio)))
+
+
 # ------------------------------------------------------------------------------ MLP
+MLP_INPUTS = 12
+
+
+def mlp_inputs(feat16, mu=None, inv_sigma=None) -> np.ndarray:
+    """FP32 selector inputs from rows of 16 doubles (14 features, n_rows, nnz)."""
+    f = _c(np.atleast_2d(feat16), np.float64)
+    out = np.empty((f.shape[0], MLP_INPUTS), dtype=np.float32)
+    m = None if mu is None else _c(mu, np.float32)
+    s = None if inv_sigma is None else _c(inv_sigma, np.float32)
+    lib().oracle_mlp_inputs(_p(f), f.shape[0], None if m is None else _p(m),
+                            None if s is None else _p(s), _p(out))
+    return out
+
+
 def mlp_nparams(sizes) -> int:
     s = _c(sizes, np.int32)
     return int(lib().oracle_mlp_nparams(_p(s)))

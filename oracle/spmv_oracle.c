@@ -565,3 +565,59 @@ float oracle_log2p1_f32(float v) {
 void oracle_log2p1_f32_array(const float *in, float *out, int64_t n) {
   for (int64_t i = 0; i < n; ++i) out[i] = oracle_log2p1_f32(in[i]);
 }
+
+/* ---------------------------------------------------------------------------------- */
+/* Feature route (Section III-D). The paper trains a decision tree on Table I features;
+ * this build reads the route as fixed rules over the same features:
+ *   IMB  highly uneven rows, nnz_max > long_ratio * nnz_avg (the IMB sub-class test of
+ *        Section III-E);
+ *   ML   most elements open a new cache line (misses_avg >= nnz_avg / 2) and x does not
+ *        fit in half of the last-level cache (vec_bytes * n_cols > llc_bytes / 2);
+ *   CMP  the working set fits the cache (size = 1) or rows are very short (nnz_avg < 4);
+ *   MB   none of the above while the working set exceeds the cache.
+ * f[] is the 14-feature vector of oracle_features.                                       */
+uint32_t oracle_feature_rules(const double *f, int64_t n_cols, int64_t vec_bytes,
+                              int64_t llc_bytes, double long_ratio) {
+  double size = f[0], nnz_max = f[3], nnz_avg = f[4], misses_avg = f[13];
+  uint32_t cls = 0;
+  if (nnz_avg > 0.0 && nnz_max > long_ratio * nnz_avg) cls |= 4u;
+  if (misses_avg >= 0.5 * nnz_avg && (double)vec_bytes * (double)n_cols > 0.5 * (double)llc_bytes)
+    cls |= 2u;
+  if (size != 0.0 || nnz_avg < 4.0) cls |= 8u;
+  if (cls == 0 && size == 0.0) cls |= 1u;
+  return cls;
+}
+
+/* Inputs of the MLP selector, from the 14 features f[0..13] plus n_rows (f[14]) and nnz
+ * (f[15]): twelve numbers, each a feature, a ratio of two features (0 when the
+ * denominator is 0), or log2(1 + that) for the heavy-tailed ones, converted to FP32:
+ *   log2p1(n_rows), log2p1(nnz_avg), log2p1(nnz_sd / nnz_avg), log2p1(nnz_max),
+ *   log2p1(nnz_max / nnz_avg), log2p1(bw_avg), log2p1(bw_sd), scatter_avg, scatter_sd,
+ *   clustering_avg, misses_avg / nnz_avg, size.
+ * With mu and inv_sigma (non-null) every input becomes (v - mu_k) * inv_sigma_k in FP32.  */
+static double ratio_or_zero(double a, double b) { return b > 0.0 ? a / b : 0.0; }
+
+void oracle_mlp_inputs(const double *feat, int64_t batch, const float *mu,
+                       const float *inv_sigma, float *X) {
+  for (int64_t b = 0; b < batch; ++b) {
+    const double *f = feat + b * 16;
+    float r[12];
+    r[0] = oracle_log2p1_f32((float)f[14]);
+    r[1] = oracle_log2p1_f32((float)f[4]);
+    r[2] = oracle_log2p1_f32((float)ratio_or_zero(f[5], f[4]));
+    r[3] = oracle_log2p1_f32((float)f[3]);
+    r[4] = oracle_log2p1_f32((float)ratio_or_zero(f[3], f[4]));
+    r[5] = oracle_log2p1_f32((float)f[8]);
+    r[6] = oracle_log2p1_f32((float)f[9]);
+    r[7] = (float)f[10];
+    r[8] = (float)f[11];
+    r[9] = (float)f[12];
+    r[10] = (float)ratio_or_zero(f[13], f[4]);
+    r[11] = (float)f[0];
+    for (int k = 0; k < 12; ++k) {
+      float z = r[k];
+      if (mu) z = (z - mu[k]) * inv_sigma[k];
+      X[b * 12 + k] = z;
+    }
+  }
+}

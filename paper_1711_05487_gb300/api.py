@@ -1,0 +1,282 @@
+"""Python convenience layer over the C ABI: torch tensors for device memory and streams.
+
+The classes below only marshal arguments (data_ptr(), dtypes, streams) into the C entry
+points of _abi; every step of the SpMV path runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import (SPMV_BF16, SPMV_F32, SPMV_F64, TUNE_FEATURES, TUNE_FIXED, TUNE_LEARNED,
+                   TUNE_PROFILE, spmv_variant)
+
+DTYPE_CODE = {torch.float64: SPMV_F64, torch.float32: SPMV_F32, torch.bfloat16: SPMV_BF16,
+              "f64": SPMV_F64, "f32": SPMV_F32, "bf16": SPMV_BF16}
+TORCH_DTYPE = {SPMV_F64: torch.float64, SPMV_F32: torch.float32, SPMV_BF16: torch.bfloat16}
+MODES = {"profile": TUNE_PROFILE, "features": TUNE_FEATURES, "learned": TUNE_LEARNED,
+         "fixed": TUNE_FIXED}
+CLASS_NAMES = ((1, "MB"), (2, "ML"), (4, "IMB"), (8, "CMP"))
+P_NAMES = ("P_CSR", "P_MB", "P_ML", "P_IMB", "P_CMP", "P_peak")
+FEATURE_NAMES = ("size", "density", "nnz_min", "nnz_max", "nnz_avg", "nnz_sd", "bw_min",
+                 "bw_max", "bw_avg", "bw_sd", "scatter_avg", "scatter_sd",
+                 "clustering_avg", "misses_avg")
+
+
+def class_names(mask: int) -> list[str]:
+    return [n for b, n in CLASS_NAMES if mask & b]
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def variant(partition=0, index=0, xpath=0, vec=0, vs=0) -> spmv_variant:
+    return spmv_variant(partition, index, xpath, vec, vs)
+
+
+BASELINE = dict(partition=0, index=0, xpath=0, vec=0, vs=0)
+
+
+def _as_torch(a, dtype=None) -> torch.Tensor:
+    if isinstance(a, torch.Tensor):
+        return a if dtype is None else a.to(dtype)
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return t if dtype is None else t.to(dtype)
+
+
+@dataclasses.dataclass
+class TuneResult:
+    classes: int
+    mode_used: int
+    variant: tuple
+    p: dict
+    b_max_gbs: float
+    features: dict
+    margin: float
+    t_pre_ms: float
+    t_classify_ms: float
+    t_prep_ms: float
+    t_autotune_ms: float
+
+    @property
+    def class_names(self):
+        return class_names(self.classes)
+
+    @staticmethod
+    def from_report(r: _abi.spmv_tune_report) -> "TuneResult":
+        return TuneResult(int(r.classes), int(r.mode_used), r.variant.as_tuple(),
+                          dict(zip(P_NAMES, list(r.p))), float(r.b_max_gbs),
+                          dict(zip(FEATURE_NAMES, list(r.features))), float(r.margin),
+                          float(r.t_pre_ms), float(r.t_classify_ms), float(r.t_prep_ms),
+                          float(r.t_autotune_ms))
+
+
+class SpmvMatrix:
+    """A CSR matrix owned by the library on the current CUDA device."""
+
+    def __init__(self, n_rows, n_cols, rowptr, colind, val, stream=None):
+        rp = _as_torch(rowptr, torch.int32).contiguous()
+        ci = _as_torch(colind, torch.int32).contiguous()
+        v = _as_torch(val).contiguous()
+        if v.dtype not in DTYPE_CODE:
+            raise TypeError(f"unsupported value dtype {v.dtype}")
+        dev = rp.is_cuda
+        if dev != ci.is_cuda or dev != v.is_cuda:
+            raise ValueError("rowptr, colind and val must all be host or all be device tensors")
+        self.n_rows, self.n_cols, self.nnz = int(n_rows), int(n_cols), int(ci.numel())
+        self._h = None
+        self._h = _abi.spmv_create(self.n_rows, self.n_cols, self.nnz, rp.data_ptr(),
+                                   ci.data_ptr() if self.nnz else None,
+                                   v.data_ptr() if self.nnz else None, DTYPE_CODE[v.dtype],
+                                   1 if dev else 0, _stream(stream))
+        self.in_type = DTYPE_CODE[v.dtype]
+        self.storage = self.in_type
+        self.vec = SPMV_F64 if self.in_type == SPMV_F64 else SPMV_F32
+        self.acc = self.vec
+        self.report: TuneResult | None = None
+
+    @classmethod
+    def from_csr(cls, m, stream=None) -> "SpmvMatrix":
+        return cls(m.n_rows, m.n_cols, m.rowptr, m.colind, m.val, stream)
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def close(self):
+        if self._h:
+            _abi.spmv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----------------------------------------------------------------- configuration
+    def set_precision(self, storage="f64", vec="f64", acc="f64", stream=None):
+        s, v, a = DTYPE_CODE[storage], DTYPE_CODE[vec], DTYPE_CODE[acc]
+        _abi.spmv_set_precision(self._h, s, v, a, _stream(stream))
+        self.storage, self.vec, self.acc = s, v, a
+
+    @property
+    def vec_dtype(self) -> torch.dtype:
+        return TORCH_DTYPE[self.vec]
+
+    def tune(self, mode="profile", stream=None, selector=None, fixed=None, **kw) -> TuneResult:
+        opts = _abi.spmv_tune_opts_default()
+        for k, val in kw.items():
+            setattr(opts, k, val)
+        if selector is not None:
+            opts.selector = selector.handle if hasattr(selector, "handle") else selector
+        if fixed is not None:
+            opts.fixed = fixed if isinstance(fixed, spmv_variant) else variant(**fixed)
+        rep = _abi.spmv_tune(self._h, MODES[mode] if isinstance(mode, str) else mode, opts,
+                             _stream(stream))
+        self.report = TuneResult.from_report(rep)
+        return self.report
+
+    def set_variant(self, stream=None, **knobs):
+        v = variant(**{**BASELINE, **knobs})
+        _abi.spmv_set_variant(self._h, v, _stream(stream))
+
+    # ----------------------------------------------------------------------- running
+    def run(self, x: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if y is None:
+            y = torch.empty(self.n_rows, dtype=self.vec_dtype, device=x.device)
+        _abi.spmv_run(self._h, x.data_ptr(), y.data_ptr(), _stream(stream))
+        return y
+
+    def run_host(self, x: torch.Tensor, y: torch.Tensor, stream=None) -> torch.Tensor:
+        _abi.spmv_run_host(self._h, x.data_ptr(), y.data_ptr(), _stream(stream))
+        return y
+
+    def spmm(self, X: torch.Tensor, Y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        k = X.shape[1]
+        if Y is None:
+            Y = torch.empty((self.n_rows, k), dtype=self.vec_dtype, device=X.device)
+        _abi.spmv_run_spmm(self._h, X.data_ptr(), Y.data_ptr(), k, _stream(stream))
+        return Y
+
+    # ---------------------------------------------------------------- inspection
+    def features(self, line_bytes=128, stream=None):
+        f = np.zeros(14)
+        isum = np.zeros(12, dtype=np.uint64)
+        _abi.spmv_features(self._h, line_bytes, f.ctypes.data, isum.ctypes.data, _stream(stream))
+        return f, isum
+
+    def profile(self, reps=20, stream=None):
+        p = np.zeros(6)
+        b = _abi.spmv_profile(self._h, reps, p.ctypes.data, None, _stream(stream))
+        return p, b
+
+    def profile_kernel(self, which: int, x: torch.Tensor, y: torch.Tensor, stream=None):
+        _abi.spmv_profile_kernel(self._h, which, x.data_ptr(), y.data_ptr(), _stream(stream))
+        return y
+
+    def export_csr(self, device="cuda", stream=None):
+        rp = torch.empty(self.n_rows + 1, dtype=torch.int32, device=device)
+        ci = torch.empty(max(self.nnz, 1), dtype=torch.int32, device=device)
+        v = torch.empty(max(self.nnz, 1), dtype=TORCH_DTYPE[self.storage], device=device)
+        _abi.spmv_export_csr(self._h, rp.data_ptr(), ci.data_ptr(), v.data_ptr(), _stream(stream))
+        return rp, ci[:self.nnz], v[:self.nnz]
+
+    def delta16(self, device="cuda", stream=None):
+        n_esc = _abi.spmv_get_delta16(self._h)
+        base = torch.empty(max(self.n_rows, 1), dtype=torch.int32, device=device)
+        delta = torch.empty(max(self.nnz, 1), dtype=torch.int16, device=device)
+        esc = torch.empty(max(n_esc, 1), dtype=torch.int32, device=device)
+        _abi.spmv_get_delta16(self._h, base.data_ptr(), delta.data_ptr(), esc.data_ptr(),
+                              _stream(stream))
+        return base[:self.n_rows], delta[:self.nnz], esc[:n_esc]
+
+    def merge_path(self, device="cuda", stream=None):
+        n_tiles, items = _abi.spmv_get_merge_path(self._h)
+        c = torch.empty((n_tiles + 1, 2), dtype=torch.int32, device=device)
+        _abi.spmv_get_merge_path(self._h, c.data_ptr(), _stream(stream))
+        return c, items
+
+    def device_bytes(self) -> int:
+        return _abi.spmv_get_device_bytes(self._h)
+
+
+class Selector:
+    """A learned selector (MLP weights + input standardization) on the current device."""
+
+    def __init__(self, sizes, params, mu=None, inv_sigma=None):
+        self.sizes = np.ascontiguousarray(sizes, dtype=np.int32)
+        self.params = np.ascontiguousarray(params, dtype=np.float32)
+        self.mu = None if mu is None else np.ascontiguousarray(mu, dtype=np.float32)
+        self.inv_sigma = None if inv_sigma is None else np.ascontiguousarray(inv_sigma,
+                                                                             dtype=np.float32)
+        self.handle = _abi.spmv_selector_create(
+            self.sizes.ctypes.data, self.params.ctypes.data,
+            None if self.mu is None else self.mu.ctypes.data,
+            None if self.inv_sigma is None else self.inv_sigma.ctypes.data)
+
+    def predict(self, feat16, stream=None):
+        f = np.ascontiguousarray(feat16, dtype=np.float64)
+        return _abi.spmv_selector_predict(self.handle, f.ctypes.data, _stream(stream))
+
+    def close(self):
+        if self.handle:
+            _abi.spmv_selector_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def save(self, path: str):
+        np.savez(path, sizes=self.sizes, params=self.params,
+                 mu=self.mu if self.mu is not None else np.zeros(0, np.float32),
+                 inv_sigma=self.inv_sigma if self.inv_sigma is not None else np.zeros(0, np.float32),
+                 version=np.array([1]))
+
+    @classmethod
+    def load(cls, path: str) -> "Selector":
+        z = np.load(path)
+        mu = z["mu"] if z["mu"].size else None
+        inv = z["inv_sigma"] if z["inv_sigma"].size else None
+        return cls(z["sizes"], z["params"], mu, inv)
+
+
+class Batch:
+    """Many FP32 matrices with k in {1, 4, 16} right-hand sides, one persistent launch."""
+
+    def __init__(self, mats, Xs, Ys, ks, stream=None):
+        self.mats = list(mats)
+        self.Xs, self.Ys = list(Xs), list(Ys)
+        self.handle = _abi.spmv_batch_create([m.handle for m in self.mats],
+                                             [x.data_ptr() for x in self.Xs],
+                                             [y.data_ptr() for y in self.Ys], list(ks),
+                                             _stream(stream))
+
+    def run(self, stream=None):
+        _abi.spmv_run_batched(self.handle, _stream(stream))
+
+    def run_sequential(self, stream=None):
+        _abi.spmv_run_batched_sequential(self.handle, _stream(stream))
+
+    def close(self):
+        if self.handle:
+            _abi.spmv_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

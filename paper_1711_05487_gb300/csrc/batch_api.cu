@@ -1,0 +1,211 @@
+// C ABI of the batched SpMM: work-item planning, the persistent launch captured into a
+// CUDA graph, and the per-matrix sequential path it is compared with.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace spmv;
+
+namespace {
+// Target nonzeros per row-block item; rows longer than this are split into chunks of
+// this many nonzeros (the matrix decomposition applied per item).
+constexpr int32_t kItemNnz = 4096;
+constexpr int32_t kItemRowsMax = 4096;
+
+struct Fail {
+  cudaError_t e;
+};
+#define BK(expr)                               \
+  do {                                         \
+    cudaError_t _e = (expr);                   \
+    if (_e != cudaSuccess) throw Fail{_e};     \
+  } while (0)
+
+int heuristic_vs(double nnz_avg) {
+  int p = 2;
+  while (p < 32 && (double)p < nnz_avg) p <<= 1;
+  return p;
+}
+}  // namespace
+
+struct spmv_batch {
+  int device = 0;
+  int32_t count = 0;
+  std::vector<spmv_handle_t> handles;
+  std::vector<const void *> X;
+  std::vector<void *> Y;
+  std::vector<int32_t> k;
+  BatchMat *d_mats = nullptr;
+  BatchItem *d_items = nullptr;
+  BatchFix *d_fix = nullptr;
+  double *d_partials = nullptr;
+  int32_t *d_counter = nullptr;
+  int32_t n_items = 0, n_fix = 0, n_chunks = 0;
+  int grid = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+static void batch_free(spmv_batch *b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  cudaFree(b->d_mats);
+  cudaFree(b->d_items);
+  cudaFree(b->d_fix);
+  cudaFree(b->d_partials);
+  cudaFree(b->d_counter);
+  delete b;
+}
+
+extern "C" {
+
+spmv_status spmv_batch_create(spmv_batch_t *out, const spmv_handle_t *handles, int32_t count,
+                              const void *const *X, void *const *Y, const int32_t *k,
+                              spmv_stream_t stream) {
+  if (!out || !handles || !X || !Y || !k || count <= 0) return SPMV_ERR_ARG;
+  *out = nullptr;
+  spmv_batch *b = new (std::nothrow) spmv_batch();
+  if (!b) return SPMV_ERR_OOM;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  try {
+    BK(cudaGetDevice(&b->device));
+    b->count = count;
+    std::vector<BatchMat> mats((size_t)count);
+    std::vector<BatchItem> items;
+    std::vector<BatchFix> fix;
+    int32_t chunks = 0;
+    for (int32_t m = 0; m < count; ++m) {
+      if (!handles[m] || k[m] < 1 || (k[m] != 1 && k[m] != 4 && k[m] != 16)) throw Fail{cudaErrorInvalidValue};
+      const int32_t *rp = nullptr, *ci = nullptr;
+      const void *v = nullptr;
+      int64_t n_rows = 0;
+      int32_t st = 0, ve = 0, ac = 0, vs = 0;
+      spmv_status q = handle_info(handles[m], &rp, &ci, &v, &n_rows, &st, &ve, &ac, &vs);
+      if (q != SPMV_OK) {
+        batch_free(b);
+        return q;
+      }
+      if (st != SPMV_F32 || ve != SPMV_F32 || ac != SPMV_F32) {
+        batch_free(b);
+        return SPMV_ERR_UNSUPPORTED_DTYPE;
+      }
+      std::vector<int32_t> hrp((size_t)n_rows + 1);
+      BK(cudaMemcpyAsync(hrp.data(), rp, 4 * ((size_t)n_rows + 1), cudaMemcpyDeviceToHost, s));
+      BK(cudaStreamSynchronize(s));
+      const double avg = n_rows ? (double)hrp[(size_t)n_rows] / (double)n_rows : 0.0;
+      mats[(size_t)m] = BatchMat{rp, ci, static_cast<const float *>(v),
+                                 static_cast<const float *>(X[m]), static_cast<float *>(Y[m]),
+                                 k[m], vs > 0 ? vs : heuristic_vs(avg)};
+      b->handles.push_back(handles[m]);
+      b->X.push_back(X[m]);
+      b->Y.push_back(Y[m]);
+      b->k.push_back(k[m]);
+      // row blocks of about kItemNnz nonzeros; long rows split into chunks
+      int32_t r = 0;
+      while (r < (int32_t)n_rows) {
+        const int32_t len = hrp[(size_t)r + 1] - hrp[(size_t)r];
+        if (len > kItemNnz) {
+          const int32_t first = chunks;
+          int32_t cnt = 0;
+          for (int32_t z = hrp[(size_t)r]; z < hrp[(size_t)r + 1]; z += kItemNnz) {
+            const int32_t ze = std::min(z + kItemNnz, hrp[(size_t)r + 1]);
+            items.push_back(BatchItem{m, r, r + 1, z, ze, chunks++});
+            ++cnt;
+          }
+          fix.push_back(BatchFix{m, r, first, cnt});
+          ++r;
+          continue;
+        }
+        int32_t e = r;
+        int64_t acc = 0;
+        while (e < (int32_t)n_rows && e - r < kItemRowsMax) {
+          const int32_t l = hrp[(size_t)e + 1] - hrp[(size_t)e];
+          if (l > kItemNnz || (acc + l > kItemNnz && e > r)) break;
+          acc += l;
+          ++e;
+        }
+        items.push_back(BatchItem{m, r, e, 0, 0, -1});
+        r = e;
+      }
+    }
+    b->n_items = (int32_t)items.size();
+    b->n_fix = (int32_t)fix.size();
+    b->n_chunks = chunks;
+    BK(cudaMalloc(&b->d_mats, sizeof(BatchMat) * mats.size()));
+    BK(cudaMalloc(&b->d_items, sizeof(BatchItem) * std::max<size_t>(items.size(), 1)));
+    BK(cudaMalloc(&b->d_fix, sizeof(BatchFix) * std::max<size_t>(fix.size(), 1)));
+    BK(cudaMalloc(&b->d_partials, sizeof(double) * 16 * (size_t)std::max(chunks, 1)));
+    BK(cudaMalloc(&b->d_counter, sizeof(int32_t)));
+    BK(cudaMemcpyAsync(b->d_mats, mats.data(), sizeof(BatchMat) * mats.size(), cudaMemcpyHostToDevice, s));
+    if (!items.empty())
+      BK(cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, s));
+    if (!fix.empty())
+      BK(cudaMemcpyAsync(b->d_fix, fix.data(), sizeof(BatchFix) * fix.size(), cudaMemcpyHostToDevice, s));
+    BK(cudaStreamSynchronize(s));
+    int sms = 0;
+    BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    b->grid = std::max(1, std::min(sms * batch_blocks_per_sm(), b->n_items));
+    BK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  } catch (const Fail &f) {
+    cudaGetLastError();
+    batch_free(b);
+    return f.e == cudaErrorMemoryAllocation ? SPMV_ERR_OOM
+           : f.e == cudaErrorInvalidValue  ? SPMV_ERR_ARG
+                                           : SPMV_ERR_CUDA;
+  }
+  *out = b;
+  return SPMV_OK;
+}
+
+spmv_status spmv_run_batched(spmv_batch_t b, spmv_stream_t stream) {
+  if (!b) return SPMV_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  try {
+    if (!b->exec) {
+      // capture on the batch's own stream (the legacy default stream cannot be captured)
+      BK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e1 = launch_batch_persistent(b->d_mats, b->d_items, b->n_items, b->d_counter,
+                                               b->d_partials, b->grid, b->cap);
+      cudaError_t e2 = launch_batch_fixup(b->d_mats, b->d_fix, b->n_fix, b->d_partials, b->cap);
+      cudaGraph_t g = nullptr;
+      cudaError_t e3 = cudaStreamEndCapture(b->cap, &g);
+      BK(e1);
+      BK(e2);
+      BK(e3);
+      b->graph = g;
+      BK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    }
+    BK(cudaGraphLaunch(b->exec, s));
+  } catch (const Fail &f) {
+    cudaGetLastError();
+    return f.e == cudaErrorMemoryAllocation ? SPMV_ERR_OOM : SPMV_ERR_CUDA;
+  }
+  return SPMV_OK;
+}
+
+spmv_status spmv_run_batched_sequential(spmv_batch_t b, spmv_stream_t stream) {
+  if (!b) return SPMV_ERR_ARG;
+  for (int32_t m = 0; m < b->count; ++m) {
+    spmv_status q = b->k[(size_t)m] == 1
+                        ? spmv_run(b->handles[(size_t)m], b->X[(size_t)m], b->Y[(size_t)m], stream)
+                        : spmv_run_spmm(b->handles[(size_t)m], b->X[(size_t)m], b->Y[(size_t)m],
+                                        b->k[(size_t)m], stream);
+    if (q != SPMV_OK) return q;
+  }
+  return SPMV_OK;
+}
+
+spmv_status spmv_batch_destroy(spmv_batch_t b) {
+  if (!b) return SPMV_ERR_ARG;
+  batch_free(b);
+  return SPMV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,173 @@
+// Device-side helpers shared by the SpMV kernels: dtype conversion, cache-hinted loads
+// (inline PTX), sub-warp reductions and scans.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace spmv {
+
+// ------------------------------------------------------------------ dtype traits ------
+template <typename T> struct DT;
+template <> struct DT<double> { static constexpr spmv_dtype id = SPMV_F64; };
+template <> struct DT<float> { static constexpr spmv_dtype id = SPMV_F32; };
+template <> struct DT<__nv_bfloat16> { static constexpr spmv_dtype id = SPMV_BF16; };
+
+template <typename AccT> __device__ __forceinline__ AccT widen(double v) { return (AccT)v; }
+template <typename AccT> __device__ __forceinline__ AccT widen(float v) { return (AccT)v; }
+template <typename AccT> __device__ __forceinline__ AccT widen(__nv_bfloat16 v) {
+  return (AccT)__bfloat162float(v);
+}
+
+// bf16 held in the low / high half of a 32-bit word -> float (exact)
+__device__ __forceinline__ float bf16lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+
+// ---------------------------------------------------------------- L2 cache policies ---
+// createpolicy gives a 64-bit L2 eviction policy for the .L2::cache_hint loads below.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// Streamed, read-once data: read-only path, not kept in L1, evict-first in L2.
+__device__ __forceinline__ uint4 ld_stream_u4(const void *p, uint64_t pol) {
+  uint4 r;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ uint2 ld_stream_u2(const void *p, uint64_t pol) {
+  uint2 r;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;"
+               : "=r"(r.x), "=r"(r.y)
+               : "l"(p), "l"(pol));
+  return r;
+}
+// Plain 128-bit read-only load.
+__device__ __forceinline__ uint4 ld_nc_u4(const void *p) {
+  uint4 r;
+  asm volatile("ld.global.nc.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "l"(p));
+  return r;
+}
+__device__ __forceinline__ uint2 ld_nc_u2(const void *p) {
+  uint2 r;
+  asm volatile("ld.global.nc.v2.u32 {%0,%1}, [%2];" : "=r"(r.x), "=r"(r.y) : "l"(p));
+  return r;
+}
+
+template <bool HINT> __device__ __forceinline__ uint4 ld16(const void *p, uint64_t pol) {
+  if constexpr (HINT) return ld_stream_u4(p, pol);
+  else return ld_nc_u4(p);
+}
+template <bool HINT> __device__ __forceinline__ uint2 ld8(const void *p, uint64_t pol) {
+  if constexpr (HINT) return ld_stream_u2(p, pol);
+  else return ld_nc_u2(p);
+}
+
+// x gathers: evict-last keeps x resident in L2 while the matrix streams past it.
+template <bool XL2> __device__ __forceinline__ double ldx(const double *p, uint64_t pol) {
+  if constexpr (XL2) {
+    double r;
+    asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(p), "l"(pol));
+    return r;
+  } else {
+    return __ldg(p);
+  }
+}
+template <bool XL2> __device__ __forceinline__ float ldx(const float *p, uint64_t pol) {
+  if constexpr (XL2) {
+    float r;
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(pol));
+    return r;
+  } else {
+    return __ldg(p);
+  }
+}
+
+// ---------------------------------------------------- vector loads of E values --------
+// Loads E consecutive values starting at an E-aligned index into AccT registers.
+template <typename AccT, bool HINT, int E> struct VLoad;
+
+template <typename AccT, bool HINT> struct VLoad<AccT, HINT, 4> {
+  __device__ __forceinline__ static void run(const double *p, AccT *o, uint64_t pol) {
+    uint4 a = ld16<HINT>(p, pol), b = ld16<HINT>(p + 2, pol);
+    o[0] = (AccT)__hiloint2double(a.y, a.x);
+    o[1] = (AccT)__hiloint2double(a.w, a.z);
+    o[2] = (AccT)__hiloint2double(b.y, b.x);
+    o[3] = (AccT)__hiloint2double(b.w, b.z);
+  }
+  __device__ __forceinline__ static void run(const float *p, AccT *o, uint64_t pol) {
+    uint4 a = ld16<HINT>(p, pol);
+    o[0] = (AccT)__uint_as_float(a.x);
+    o[1] = (AccT)__uint_as_float(a.y);
+    o[2] = (AccT)__uint_as_float(a.z);
+    o[3] = (AccT)__uint_as_float(a.w);
+  }
+  __device__ __forceinline__ static void run(const __nv_bfloat16 *p, AccT *o, uint64_t pol) {
+    uint2 a = ld8<HINT>(p, pol);
+    o[0] = (AccT)bf16lo(a.x);
+    o[1] = (AccT)bf16hi(a.x);
+    o[2] = (AccT)bf16lo(a.y);
+    o[3] = (AccT)bf16hi(a.y);
+  }
+};
+
+template <typename AccT, bool HINT> struct VLoad<AccT, HINT, 8> {
+  template <typename ValT>
+  __device__ __forceinline__ static void run(const ValT *p, AccT *o, uint64_t pol) {
+    if constexpr (sizeof(ValT) == 2) {
+      uint4 a = ld16<HINT>(p, pol);
+      o[0] = (AccT)bf16lo(a.x); o[1] = (AccT)bf16hi(a.x);
+      o[2] = (AccT)bf16lo(a.y); o[3] = (AccT)bf16hi(a.y);
+      o[4] = (AccT)bf16lo(a.z); o[5] = (AccT)bf16hi(a.z);
+      o[6] = (AccT)bf16lo(a.w); o[7] = (AccT)bf16hi(a.w);
+    } else {
+      VLoad<AccT, HINT, 4>::run(p, o, pol);
+      VLoad<AccT, HINT, 4>::run(p + 4, o + 4, pol);
+    }
+  }
+};
+
+// ------------------------------------------------------------ sub-warp collectives ----
+// Lanes [g*VS, (g+1)*VS) of a warp form sub-warp g; mask selects exactly those lanes.
+template <int VS> __device__ __forceinline__ unsigned group_mask() {
+  if constexpr (VS == 32) return 0xffffffffu;
+  else return ((1u << VS) - 1u) << ((threadIdx.x & 31) & ~(VS - 1));
+}
+
+template <int VS, typename T> __device__ __forceinline__ T group_sum(T v, unsigned mask) {
+#pragma unroll
+  for (int off = VS / 2; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off, VS);
+  return v;
+}
+
+// Inclusive scan over the sub-warp (Hillis-Steele with shuffles).
+template <int VS> __device__ __forceinline__ int group_incl_scan(int v, int lane, unsigned mask) {
+#pragma unroll
+  for (int off = 1; off < VS; off <<= 1) {
+    int t = __shfl_up_sync(mask, v, off, VS);
+    if (lane >= off) v += t;
+  }
+  return v;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+}  // namespace spmv

@@ -1,0 +1,184 @@
+// Host-side declarations shared by the translation units of the library (not part of
+// the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/spmv_gb300.h"
+
+namespace spmv {
+
+// Every device array the kernels read past its logical end (128-bit chunk loads of the
+// last row) is allocated with this many zeroed elements of slack.
+constexpr int64_t kPadElems = 32;
+
+// Merge-path tile geometry.
+constexpr int kMergeThreads = 256;
+constexpr int kMergeIpt = 8;                       // merge items per thread
+constexpr int kMergeItems = kMergeThreads * kMergeIpt;
+
+// Everything a SpMV launch needs; unused pointers are null.
+struct RunArgs {
+  int64_t n_rows = 0, n_cols = 0, nnz = 0;
+  const int32_t *rowptr = nullptr;
+  const int32_t *colind = nullptr;
+  const uint16_t *delta = nullptr;   // 16-bit column deltas
+  const int32_t *dbase = nullptr;    // per-row base column / escape offset
+  const int32_t *esc = nullptr;      // columns of escape rows
+  const void *val = nullptr;         // storage dtype
+  const void *x = nullptr;           // vec dtype
+  void *y = nullptr;                 // vec dtype
+  const int2 *coord = nullptr;       // merge-path tile table [n_tiles + 1]
+  int64_t n_tiles = 0;
+  int32_t *tail_row = nullptr;       // [n_tiles]
+  double *tail_val = nullptr;        // [n_tiles]
+  double *head_val = nullptr;        // [n_tiles]
+  int32_t k = 1;                     // right-hand sides (SpMM)
+};
+
+// Static-partition profiling launch (Section III-B micro-benchmarks).
+struct ProfileArgs {
+  int64_t n_rows = 0, n_cols = 0;
+  const int32_t *part = nullptr;     // [n_ctas + 1] row boundaries
+  int32_t n_ctas = 0;
+  const int32_t *rowptr = nullptr;
+  const int32_t *colind = nullptr;   // colind, or colind' for P_ML
+  const void *val = nullptr;
+  const void *x = nullptr;
+  void *y = nullptr;
+  unsigned long long *t_start = nullptr;
+  unsigned long long *t_end = nullptr;
+  int32_t cmp_mode = 0;              // 1: P_CMP kernel (x[i], no colind)
+  int32_t vs = 8;
+};
+
+// One work item of the batched kernel: rows [row_begin, row_end) of matrix `mat`, or,
+// when chunk >= 0, nonzeros [nz_begin, nz_end) of the single long row row_begin whose
+// partial sums go to partial slot `chunk`.
+struct BatchItem {
+  int32_t mat;
+  int32_t row_begin;
+  int32_t row_end;
+  int32_t nz_begin;
+  int32_t nz_end;
+  int32_t chunk;
+};
+
+struct BatchMat {
+  const int32_t *rowptr;
+  const int32_t *colind;
+  const float *val;
+  const float *X;
+  float *Y;
+  int32_t k;
+  int32_t vs;
+};
+
+// A long row split over several items: partial slots [first, first + count), each k wide.
+struct BatchFix {
+  int32_t mat;
+  int32_t row;
+  int32_t first;
+  int32_t count;
+};
+
+// Launchers, one set per (storage, vec, acc) dtype combination.
+typedef cudaError_t (*spmv_launch_fn)(const spmv_variant &v, const RunArgs &a, cudaStream_t s);
+typedef cudaError_t (*spmm_launch_fn)(const RunArgs &a, int vs, cudaStream_t s);
+typedef cudaError_t (*profile_launch_fn)(const ProfileArgs &a, cudaStream_t s);
+
+struct KernelSet {
+  spmv_launch_fn spmv;
+  spmm_launch_fn spmm;
+  profile_launch_fn profile;
+  int profile_blocks_per_sm;   // occupancy of the profiling kernel (for a resident grid)
+};
+
+// Returns null for combinations that are not offered.
+const KernelSet *kernel_set(spmv_dtype val, spmv_dtype vec, spmv_dtype acc);
+
+#define SPMV_DECLARE_SET(tag) const KernelSet *kernel_set_##tag();
+SPMV_DECLARE_SET(f64_dd)
+SPMV_DECLARE_SET(f32_dd)
+SPMV_DECLARE_SET(f32_ff)
+SPMV_DECLARE_SET(f32_fd)
+SPMV_DECLARE_SET(bf16_dd)
+SPMV_DECLARE_SET(bf16_ff)
+SPMV_DECLARE_SET(bf16_fd)
+#undef SPMV_DECLARE_SET
+
+// ------------------------------------------------------------- preprocessing (prep.cu)
+cudaError_t launch_validate(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t *rowptr,
+                            const int32_t *colind, int32_t *d_code, cudaStream_t s);
+cudaError_t launch_round_values(const double *in, void *out, int64_t n, spmv_dtype to,
+                                cudaStream_t s);
+cudaError_t launch_convert_values(const void *in, spmv_dtype from, void *out, spmv_dtype to,
+                                  int64_t n, cudaStream_t s);
+cudaError_t launch_delta16_flags(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                                 int64_t *esc_count, cudaStream_t s);
+cudaError_t launch_delta16_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                                const int64_t *esc_off, int32_t *dbase, uint16_t *delta,
+                                int32_t *esc, cudaStream_t s);
+cudaError_t launch_delta16_decode(int64_t n_rows, const int32_t *rowptr, const int32_t *dbase,
+                                  const uint16_t *delta, const int32_t *esc, int32_t *colind,
+                                  cudaStream_t s);
+// exclusive scan of n int64 values in place; total (device, 1 value) receives the sum
+cudaError_t launch_scan_i64(int64_t *data, int64_t n, int64_t *total, int64_t *scratch,
+                            int64_t scratch_elems, cudaStream_t s);
+int64_t scan_scratch_elems(int64_t n);
+cudaError_t launch_merge_coords(int64_t n_rows, int64_t nnz, const int32_t *rowptr,
+                                int64_t items, int64_t n_tiles, int2 *coord, cudaStream_t s);
+cudaError_t launch_static_partition(int64_t n_rows, int64_t nnz, const int32_t *rowptr,
+                                    int32_t n_parts, int32_t *part, cudaStream_t s);
+cudaError_t launch_fill_row_index(int64_t n_rows, int64_t n_cols, const int32_t *rowptr,
+                                  int32_t *out, cudaStream_t s);
+cudaError_t launch_fill_const(void *p, spmv_dtype t, int64_t n, double v, cudaStream_t s);
+
+// Features: per-block partial sums, then a final reduction into FeatSums (device).
+struct FeatSums {
+  unsigned long long s_nnz, s_sc, s_cl, s_miss, s_grp;
+  unsigned long long s_nnz2_lo, s_nnz2_hi, s_bw_lo, s_bw_hi, s_bw2_lo, s_bw2_hi, s_sc2_lo,
+      s_sc2_hi;
+  long long nnz_min, nnz_max, bw_min, bw_max;
+};
+int feature_blocks(int64_t n_rows);
+cudaError_t launch_features(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                            int32_t line_elems, FeatSums *partials, int n_blocks,
+                            FeatSums *out, cudaStream_t s);
+cudaError_t launch_row_len_max(int64_t n_rows, const int32_t *rowptr, int32_t *out,
+                               cudaStream_t s);
+
+// Bandwidth probe
+cudaError_t launch_read_probe(const void *buf, int64_t bytes, int reps,
+                              unsigned long long *sink, cudaStream_t s);
+
+// MLP (mlp.cu)
+cudaError_t launch_mlp_inputs(const double *feat, int64_t batch, const float *mu,
+                              const float *inv_sigma, float *X, cudaStream_t s);
+cudaError_t launch_mlp_logits(const int32_t *sizes, const float *params, int64_t batch,
+                              const float *X, float *logits, cudaStream_t s);
+cudaError_t launch_mlp_loss_grad(const int32_t *sizes, const float *params, int64_t batch,
+                                 const float *X, const float *Y, float *grad, float *loss,
+                                 float *work, cudaStream_t s);
+int64_t mlp_work_floats(const int32_t *sizes, int64_t batch);
+int64_t mlp_param_count(const int32_t *sizes);
+cudaError_t launch_adam(int64_t n, float *p, const float *g, float *m, float *v, float lr,
+                        float b1, float b2, float eps, int32_t t, cudaStream_t s);
+
+// Batched (batch.cu)
+cudaError_t launch_batch_persistent(const BatchMat *mats, const BatchItem *items,
+                                    int32_t n_items, int32_t *counter, double *partials,
+                                    int grid, cudaStream_t s);
+cudaError_t launch_batch_fixup(const BatchMat *mats, const BatchFix *fix, int32_t n_fix,
+                               const double *partials, cudaStream_t s);
+cudaError_t launch_batch_items(const BatchMat *mats, const BatchItem *items, int32_t n_items,
+                               double *partials, cudaStream_t s);
+int batch_blocks_per_sm();
+
+// Device arrays and dtypes of a handle (vs = tuned sub-warp width, 0 if none).
+spmv_status handle_info(spmv_handle_t h, const int32_t **rowptr, const int32_t **colind,
+                        const void **val, int64_t *n_rows, int32_t *storage, int32_t *vec,
+                        int32_t *acc, int32_t *vs);
+
+}  // namespace spmv

@@ -1,0 +1,588 @@
+// Preprocessing kernels: CSR validation, value precision conversion, the 16-bit delta
+// column index, merge-path tile table, static profiling partition, Table I feature
+// extraction and the read-bandwidth probe.
+#include <climits>
+
+#include "common.cuh"
+
+namespace spmv {
+
+namespace {
+constexpr int kT = 256;
+
+inline unsigned blocks_for(int64_t n, int per_block = kT) {
+  int64_t b = (n + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > 2147483647LL) b = 2147483647LL;
+  return (unsigned)b;
+}
+}  // namespace
+
+// ----------------------------------------------------------------- CSR validation -----
+// Codes follow the CSR definition (Section II): 1 rowptr[0] != 0, 2 rowptr decreases,
+// 3 rowptr[n] != nnz, 4 column out of range, 5 columns not strictly increasing. For the
+// element checks the first offending element in storage order decides between 4 and 5.
+__global__ void k_validate_rowptr(int64_t n_rows, int64_t nnz, const int32_t *rowptr,
+                                  int32_t *flags) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    if (rowptr[0] != 0) atomicOr(flags, 1);
+    if ((int64_t)rowptr[n_rows] != nnz) atomicOr(flags, 4);
+  }
+  if (i < n_rows && rowptr[i + 1] < rowptr[i]) atomicOr(flags, 2);
+}
+
+__global__ void k_validate_finish(const int32_t *flags, const unsigned long long *first_bad,
+                                  int32_t *code) {
+  const int f = *flags;
+  int c = 0;
+  if (f & 1) c = 1;
+  else if (f & 2) c = 2;
+  else if (f & 4) c = 3;
+  else if (*first_bad != ~0ull) c = (int)(*first_bad & 7ull);
+  *code = c;
+}
+
+__global__ void k_init_validate(int32_t *flags, unsigned long long *first_bad) {
+  *flags = 0;
+  *first_bad = ~0ull;
+}
+
+__global__ void k_validate_cols_guarded(int64_t n_rows, int64_t n_cols, const int32_t *rowptr,
+                                        const int32_t *colind, const int32_t *flags,
+                                        unsigned long long *first_bad) {
+  if (*flags != 0) return;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (i >= n_rows) return;
+  const int s = rowptr[i], e = rowptr[i + 1];
+  for (int j = s + lane; j < e; j += 32) {
+    const int c = colind[j];
+    int code = 0;
+    if (c < 0 || (int64_t)c >= n_cols) code = 4;
+    else if (j > s && c <= colind[j - 1]) code = 5;
+    if (code) atomicMin(first_bad, ((unsigned long long)j << 3) | (unsigned long long)code);
+  }
+}
+
+// d_code points at 16 bytes of device scratch: [code, flags, first_bad (8 bytes)].
+// The element pass reads colind only when every rowptr check passed (then all offsets lie
+// in [0, nnz]).
+cudaError_t launch_validate(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t *rowptr,
+                            const int32_t *colind, int32_t *d_code, cudaStream_t s) {
+  int32_t *flags = d_code + 1;
+  unsigned long long *first_bad = reinterpret_cast<unsigned long long *>(d_code + 2);
+  k_init_validate<<<1, 1, 0, s>>>(flags, first_bad);
+  k_validate_rowptr<<<blocks_for(n_rows + 1), kT, 0, s>>>(n_rows, nnz, rowptr, flags);
+  if (n_rows > 0)
+    k_validate_cols_guarded<<<blocks_for(n_rows, kT / 32), kT, 0, s>>>(n_rows, n_cols, rowptr,
+                                                                       colind, flags, first_bad);
+  k_validate_finish<<<1, 1, 0, s>>>(flags, first_bad, d_code);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- value precision codec -----
+// FP64 -> BF16, round to nearest even without double rounding: the value is first
+// rounded to FP32 with round-to-odd (truncate, then set the last bit if anything was
+// cut off; Boldo & Melquiond, "When double rounding is odd", 2005), which keeps enough
+// bits (24 >= 8 + 2) for the second, round-to-nearest-even step to FP32 -> BF16 to give
+// the correctly rounded result.
+__device__ __forceinline__ uint16_t f64_to_bf16_rne(double v) {
+  if (isnan(v)) return signbit(v) ? (uint16_t)0xFFC0u : (uint16_t)0x7FC0u;
+  float f = __double2float_rz(v);
+  uint32_t u = __float_as_uint(f);
+  if ((double)f != v && !isinf(v)) u |= 1u;   // round to odd
+  if ((u & 0x7F800000u) == 0x7F800000u) return (uint16_t)(u >> 16);  // +-inf
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7FFFu + lsb;                          // nearest, ties to even
+  return (uint16_t)(u >> 16);
+}
+
+__global__ void k_round_values(const double *in, void *out, int64_t n, int to) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = in[i];
+    if (to == SPMV_F64) static_cast<double *>(out)[i] = v;
+    else if (to == SPMV_F32) static_cast<float *>(out)[i] = __double2float_rn(v);
+    else static_cast<uint16_t *>(out)[i] = f64_to_bf16_rne(v);
+  }
+}
+
+cudaError_t launch_round_values(const double *in, void *out, int64_t n, spmv_dtype to,
+                                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  unsigned g = blocks_for(n);
+  if (g > 65536u) g = 65536u;
+  k_round_values<<<g, kT, 0, s>>>(in, out, n, (int)to);
+  return cudaGetLastError();
+}
+
+__device__ __forceinline__ double load_as_f64(const void *p, int t, int64_t i) {
+  if (t == SPMV_F64) return static_cast<const double *>(p)[i];
+  if (t == SPMV_F32) return (double)static_cast<const float *>(p)[i];
+  return (double)__uint_as_float(((uint32_t) static_cast<const uint16_t *>(p)[i]) << 16);
+}
+
+__global__ void k_convert_values(const void *in, int from, void *out, int to, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = load_as_f64(in, from, i);
+    if (to == SPMV_F64) static_cast<double *>(out)[i] = v;
+    else if (to == SPMV_F32) static_cast<float *>(out)[i] = __double2float_rn(v);
+    else static_cast<uint16_t *>(out)[i] = f64_to_bf16_rne(v);
+  }
+}
+
+cudaError_t launch_convert_values(const void *in, spmv_dtype from, void *out, spmv_dtype to,
+                                  int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  unsigned g = blocks_for(n);
+  if (g > 65536u) g = 65536u;
+  k_convert_values<<<g, kT, 0, s>>>(in, (int)from, out, (int)to, n);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- delta16 index --------
+// Per row: escape row iff some consecutive column distance exceeds 65535; esc_count[i]
+// is the row's length for escape rows, 0 otherwise (a scan turns it into offsets).
+__global__ void k_delta16_flags(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                                int64_t *esc_count) {
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (i >= n_rows) return;
+  const int s = rowptr[i], e = rowptr[i + 1];
+  int big = 0;
+  for (int j = s + 1 + lane; j < e; j += 32)
+    if ((int64_t)colind[j] - (int64_t)colind[j - 1] > 65535) big = 1;
+  big = __any_sync(0xffffffffu, big);
+  if (lane == 0) esc_count[i] = big ? (int64_t)(e - s) : 0;
+}
+
+__global__ void k_delta16_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                               const int64_t *esc_off, int32_t *dbase, uint16_t *delta,
+                               int32_t *esc) {
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (i >= n_rows) return;
+  const int s = rowptr[i], e = rowptr[i + 1];
+  if (s == e) {
+    if (lane == 0) dbase[i] = 0;
+    return;
+  }
+  const bool escape = esc_off[i + 1] != esc_off[i];
+  if (escape) {
+    const int64_t off = esc_off[i];
+    if (lane == 0) dbase[i] = (int32_t)(-(1 + off));
+    for (int j = s + lane; j < e; j += 32) {
+      delta[j] = 0;
+      esc[off + (j - s)] = colind[j];
+    }
+  } else {
+    if (lane == 0) dbase[i] = colind[s];
+    for (int j = s + lane; j < e; j += 32)
+      delta[j] = (j == s) ? (uint16_t)0 : (uint16_t)(colind[j] - colind[j - 1]);
+  }
+}
+
+cudaError_t launch_delta16_flags(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                                 int64_t *esc_count, cudaStream_t s) {
+  if (n_rows == 0) return cudaSuccess;
+  k_delta16_flags<<<blocks_for(n_rows, kT / 32), kT, 0, s>>>(n_rows, rowptr, colind, esc_count);
+  return cudaGetLastError();
+}
+
+// esc_off has n_rows + 1 entries (exclusive scan of esc_count, total last).
+cudaError_t launch_delta16_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                                const int64_t *esc_off, int32_t *dbase, uint16_t *delta,
+                                int32_t *esc, cudaStream_t s) {
+  if (n_rows == 0) return cudaSuccess;
+  k_delta16_fill<<<blocks_for(n_rows, kT / 32), kT, 0, s>>>(n_rows, rowptr, colind, esc_off,
+                                                            dbase, delta, esc);
+  return cudaGetLastError();
+}
+
+__global__ void k_delta16_decode(int64_t n_rows, const int32_t *rowptr, const int32_t *dbase,
+                                 const uint16_t *delta, const int32_t *esc, int32_t *colind) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_rows) return;
+  const int s = rowptr[i], e = rowptr[i + 1];
+  if (s == e) return;
+  const int32_t b = dbase[i];
+  if (b < 0) {
+    const int64_t off = -(int64_t)b - 1;
+    for (int j = s; j < e; ++j) colind[j] = esc[off + (j - s)];
+  } else {
+    int c = b;
+    for (int j = s; j < e; ++j) {
+      c += delta[j];
+      colind[j] = c;
+    }
+  }
+}
+
+cudaError_t launch_delta16_decode(int64_t n_rows, const int32_t *rowptr, const int32_t *dbase,
+                                  const uint16_t *delta, const int32_t *esc, int32_t *colind,
+                                  cudaStream_t s) {
+  if (n_rows == 0) return cudaSuccess;
+  k_delta16_decode<<<blocks_for(n_rows), kT, 0, s>>>(n_rows, rowptr, dbase, delta, esc, colind);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- exclusive scan (i64) ---
+// Three passes: per-block sums, a single-block scan of the block sums, then per-block
+// scans with the block offset added. Deterministic (integer).
+constexpr int kScanBlock = 1024;   // elements per block (256 threads x 4)
+
+__global__ void k_scan_block_sums(const int64_t *data, int64_t n, int64_t *sums) {
+  __shared__ int64_t sh[kT];
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+  int64_t acc = 0;
+  for (int q = 0; q < 4; ++q) {
+    const int64_t i = base + threadIdx.x * 4 + q;
+    if (i < n) acc += data[i];
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = kT / 2; off > 0; off >>= 1) {
+    if ((int)threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) sums[blockIdx.x] = sh[0];
+}
+
+__global__ void k_scan_sums_serial(int64_t *sums, int64_t nb, int64_t *total) {
+  // single thread block: chunked scan of up to a few hundred thousand block sums
+  __shared__ int64_t sh[kT];
+  int64_t carry = 0;
+  for (int64_t base = 0; base < nb; base += kT) {
+    const int64_t i = base + threadIdx.x;
+    const int64_t v = i < nb ? sums[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < kT; off <<= 1) {
+      int64_t t = (int)threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < nb) sums[i] = carry + sh[threadIdx.x] - v;
+    carry += sh[kT - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void k_scan_apply(int64_t *data, int64_t n, const int64_t *sums) {
+  __shared__ int64_t sh[kT];
+  const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+  int64_t v[4];
+  int64_t acc = 0;
+  for (int q = 0; q < 4; ++q) {
+    const int64_t i = base + threadIdx.x * 4 + q;
+    v[q] = i < n ? data[i] : 0;
+    acc += v[q];
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = 1; off < kT; off <<= 1) {
+    int64_t t = (int)threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  int64_t run = sums[blockIdx.x] + sh[threadIdx.x] - acc;
+  for (int q = 0; q < 4; ++q) {
+    const int64_t i = base + threadIdx.x * 4 + q;
+    if (i < n) data[i] = run;
+    run += v[q];
+  }
+}
+
+int64_t scan_scratch_elems(int64_t n) { return (n + kScanBlock - 1) / kScanBlock + 1; }
+
+cudaError_t launch_scan_i64(int64_t *data, int64_t n, int64_t *total, int64_t *scratch,
+                            int64_t scratch_elems, cudaStream_t s) {
+  const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+  if (nb + 1 > scratch_elems) return cudaErrorInvalidValue;
+  if (n == 0) {
+    return cudaMemsetAsync(total, 0, sizeof(int64_t), s);
+  }
+  k_scan_block_sums<<<(unsigned)nb, kT, 0, s>>>(data, n, scratch);
+  k_scan_sums_serial<<<1, kT, 0, s>>>(scratch, nb, total);
+  k_scan_apply<<<(unsigned)nb, kT, 0, s>>>(data, n, scratch);
+  return cudaGetLastError();
+}
+
+// -------------------------------------------------------------- merge-path table ------
+// coord[t] = (rows ended, nonzeros consumed) after min(t * items, n_rows + nnz) items of
+// the merge of row ends (row i ends at rowptr[i+1]) with nonzeros 0..nnz-1, where a row
+// end goes first when rowptr[i+1] <= the nonzero's index.
+__global__ void k_merge_coords(int64_t n_rows, int64_t nnz, const int32_t *rowptr,
+                               int64_t items, int64_t n_tiles, int2 *coord) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > n_tiles) return;
+  int64_t d = t * items;
+  const int64_t total = n_rows + nnz;
+  if (d > total) d = total;
+  int64_t lo = d - nnz > 0 ? d - nnz : 0;
+  int64_t hi = d < n_rows ? d : n_rows;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)rowptr[mid + 1] <= d - 1 - mid) lo = mid + 1;
+    else hi = mid;
+  }
+  coord[t] = make_int2((int)lo, (int)(d - lo));
+}
+
+cudaError_t launch_merge_coords(int64_t n_rows, int64_t nnz, const int32_t *rowptr,
+                                int64_t items, int64_t n_tiles, int2 *coord, cudaStream_t s) {
+  k_merge_coords<<<blocks_for(n_tiles + 1), kT, 0, s>>>(n_rows, nnz, rowptr, items, n_tiles, coord);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------ static profiling partition ----
+// part[c] = first row whose start offset is >= round(c * nnz / n_parts): contiguous row
+// ranges of about equal nonzero counts, rows never split (the paper's baseline
+// partitioning, Section IV-A).
+__global__ void k_static_partition(int64_t n_rows, int64_t nnz, const int32_t *rowptr,
+                                   int32_t n_parts, int32_t *part) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c > n_parts) return;
+  if (c == 0) { part[0] = 0; return; }
+  if (c == n_parts) { part[n_parts] = (int32_t)n_rows; return; }
+  const int64_t target = (c * nnz + n_parts / 2) / n_parts;
+  int64_t lo = 0, hi = n_rows;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)rowptr[mid] < target) lo = mid + 1;
+    else hi = mid;
+  }
+  part[c] = (int32_t)lo;
+}
+
+cudaError_t launch_static_partition(int64_t n_rows, int64_t nnz, const int32_t *rowptr,
+                                    int32_t n_parts, int32_t *part, cudaStream_t s) {
+  k_static_partition<<<blocks_for((int64_t)n_parts + 1), kT, 0, s>>>(n_rows, nnz, rowptr, n_parts, part);
+  return cudaGetLastError();
+}
+
+// colind'[j] = i for every nonzero j of row i (P_ML micro-benchmark, Section III-B);
+// for a matrix with more rows than columns the index is clamped to the last column so
+// that x stays in bounds.
+__global__ void k_fill_row_index(int64_t n_rows, int64_t n_cols, const int32_t *rowptr,
+                                 int32_t *out) {
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (i >= n_rows) return;
+  const int s = rowptr[i], e = rowptr[i + 1];
+  const int32_t v = (int32_t)(i < n_cols ? i : n_cols - 1);
+  for (int j = s + lane; j < e; j += 32) out[j] = v;
+}
+
+cudaError_t launch_fill_row_index(int64_t n_rows, int64_t n_cols, const int32_t *rowptr,
+                                  int32_t *out, cudaStream_t s) {
+  if (n_rows == 0) return cudaSuccess;
+  k_fill_row_index<<<blocks_for(n_rows, kT / 32), kT, 0, s>>>(n_rows, n_cols, rowptr, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_fill_const(void *p, int t, int64_t n, double v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (t == SPMV_F64) static_cast<double *>(p)[i] = v;
+    else static_cast<float *>(p)[i] = (float)v;
+  }
+}
+
+cudaError_t launch_fill_const(void *p, spmv_dtype t, int64_t n, double v, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  unsigned g = blocks_for(n);
+  if (g > 65536u) g = 65536u;
+  k_fill_const<<<g, kT, 0, s>>>(p, (int)t, n, v);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------- features ---------
+// Table I per-row quantities, one warp per row; integer sums are exact in any order, so
+// the per-block partials and their final reduction give the same bits as a serial sum.
+typedef unsigned __int128 u128;
+
+struct FeatAcc {
+  u128 s_nnz2, s_bw, s_bw2, s_sc2;
+  unsigned long long s_nnz, s_sc, s_cl, s_miss, s_grp;
+  long long nnz_min, nnz_max, bw_min, bw_max;
+};
+
+__device__ __forceinline__ void feat_init(FeatAcc &f) {
+  f.s_nnz2 = f.s_bw = f.s_bw2 = f.s_sc2 = 0;
+  f.s_nnz = f.s_sc = f.s_cl = f.s_miss = f.s_grp = 0;
+  f.nnz_min = LLONG_MAX;
+  f.nnz_max = 0;
+  f.bw_min = LLONG_MAX;
+  f.bw_max = 0;
+}
+
+__device__ __forceinline__ void feat_merge(FeatAcc &a, const FeatAcc &b) {
+  a.s_nnz2 += b.s_nnz2; a.s_bw += b.s_bw; a.s_bw2 += b.s_bw2; a.s_sc2 += b.s_sc2;
+  a.s_nnz += b.s_nnz; a.s_sc += b.s_sc; a.s_cl += b.s_cl; a.s_miss += b.s_miss;
+  a.s_grp += b.s_grp;
+  a.nnz_min = min(a.nnz_min, b.nnz_min); a.nnz_max = max(a.nnz_max, b.nnz_max);
+  a.bw_min = min(a.bw_min, b.bw_min); a.bw_max = max(a.bw_max, b.bw_max);
+}
+
+__device__ __forceinline__ void feat_store(FeatSums *o, const FeatAcc &f) {
+  o->s_nnz = f.s_nnz; o->s_sc = f.s_sc; o->s_cl = f.s_cl; o->s_miss = f.s_miss;
+  o->s_grp = f.s_grp;
+  o->s_nnz2_lo = (unsigned long long)f.s_nnz2; o->s_nnz2_hi = (unsigned long long)(f.s_nnz2 >> 64);
+  o->s_bw_lo = (unsigned long long)f.s_bw; o->s_bw_hi = (unsigned long long)(f.s_bw >> 64);
+  o->s_bw2_lo = (unsigned long long)f.s_bw2; o->s_bw2_hi = (unsigned long long)(f.s_bw2 >> 64);
+  o->s_sc2_lo = (unsigned long long)f.s_sc2; o->s_sc2_hi = (unsigned long long)(f.s_sc2 >> 64);
+  o->nnz_min = f.nnz_min; o->nnz_max = f.nnz_max; o->bw_min = f.bw_min; o->bw_max = f.bw_max;
+}
+
+__device__ __forceinline__ FeatAcc feat_load(const FeatSums *o) {
+  FeatAcc f;
+  f.s_nnz = o->s_nnz; f.s_sc = o->s_sc; f.s_cl = o->s_cl; f.s_miss = o->s_miss; f.s_grp = o->s_grp;
+  f.s_nnz2 = ((u128)o->s_nnz2_hi << 64) | o->s_nnz2_lo;
+  f.s_bw = ((u128)o->s_bw_hi << 64) | o->s_bw_lo;
+  f.s_bw2 = ((u128)o->s_bw2_hi << 64) | o->s_bw2_lo;
+  f.s_sc2 = ((u128)o->s_sc2_hi << 64) | o->s_sc2_lo;
+  f.nnz_min = o->nnz_min; f.nnz_max = o->nnz_max; f.bw_min = o->bw_min; f.bw_max = o->bw_max;
+  return f;
+}
+
+// round(num * 2^24 / den), halves up, exact (num, den < 2^31)
+__device__ __forceinline__ unsigned long long q24(unsigned long long num, unsigned long long den) {
+  return ((num << 25) + den) / (2ull * den);
+}
+
+constexpr int kFeatThreads = 256;
+constexpr int kFeatWarps = kFeatThreads / 32;
+
+__global__ void __launch_bounds__(kFeatThreads)
+k_features(int64_t n_rows, const int32_t *rowptr, const int32_t *colind, int32_t line_elems,
+           FeatSums *partials) {
+  __shared__ FeatSums sh[kFeatWarps];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  FeatAcc acc;
+  feat_init(acc);
+  for (int64_t i = (int64_t)blockIdx.x * kFeatWarps + warp; i < n_rows;
+       i += (int64_t)gridDim.x * kFeatWarps) {
+    const int s = rowptr[i], e = rowptr[i + 1];
+    const long long k = e - s;
+    unsigned grp = 0, miss = 0;
+    for (int j = s + lane; j < e; j += 32) {
+      if (j == s) {
+        grp += 1;
+        miss += 1;
+      } else {
+        const long long d = (long long)colind[j] - (long long)colind[j - 1];
+        grp += (d != 1);
+        miss += (d > line_elems);
+      }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      grp += __shfl_xor_sync(0xffffffffu, grp, off);
+      miss += __shfl_xor_sync(0xffffffffu, miss, off);
+    }
+    if (lane == 0) {
+      const long long bw = k > 0 ? (long long)colind[e - 1] - (long long)colind[s] + 1 : 0;
+      const unsigned long long qs = k > 0 ? q24((unsigned long long)k, (unsigned long long)bw) : 0;
+      const unsigned long long qc = k > 0 ? q24(grp, (unsigned long long)k) : 0;
+      acc.s_nnz += (unsigned long long)k;
+      acc.s_nnz2 += (u128)k * (u128)k;
+      acc.s_bw += (u128)bw;
+      acc.s_bw2 += (u128)bw * (u128)bw;
+      acc.s_sc += qs;
+      acc.s_sc2 += (u128)qs * (u128)qs;
+      acc.s_cl += qc;
+      acc.s_miss += miss;
+      acc.s_grp += grp;
+      acc.nnz_min = min(acc.nnz_min, k);
+      acc.nnz_max = max(acc.nnz_max, k);
+      acc.bw_min = min(acc.bw_min, bw);
+      acc.bw_max = max(acc.bw_max, bw);
+    }
+  }
+  if (lane == 0) feat_store(&sh[warp], acc);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    FeatAcc tot = feat_load(&sh[0]);
+    for (int w = 1; w < kFeatWarps; ++w) feat_merge(tot, feat_load(&sh[w]));
+    feat_store(&partials[blockIdx.x], tot);
+  }
+}
+
+__global__ void k_features_final(const FeatSums *partials, int n, FeatSums *out) {
+  if (threadIdx.x != 0) return;
+  FeatAcc tot = feat_load(&partials[0]);
+  for (int b = 1; b < n; ++b) feat_merge(tot, feat_load(&partials[b]));
+  feat_store(out, tot);
+}
+
+int feature_blocks(int64_t n_rows) {
+  int64_t b = (n_rows + kFeatWarps * 16 - 1) / (kFeatWarps * 16);
+  if (b < 1) b = 1;
+  if (b > 4096) b = 4096;
+  return (int)b;
+}
+
+cudaError_t launch_features(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                            int32_t line_elems, FeatSums *partials, int n_blocks,
+                            FeatSums *out, cudaStream_t s) {
+  k_features<<<n_blocks, kFeatThreads, 0, s>>>(n_rows, rowptr, colind, line_elems, partials);
+  k_features_final<<<1, 32, 0, s>>>(partials, n_blocks, out);
+  return cudaGetLastError();
+}
+
+__global__ void k_row_len_max(int64_t n_rows, const int32_t *rowptr, int32_t *out) {
+  int m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rows;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, rowptr[i + 1] - rowptr[i]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+cudaError_t launch_row_len_max(int64_t n_rows, const int32_t *rowptr, int32_t *out,
+                               cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess || n_rows == 0) return e;
+  unsigned g = blocks_for(n_rows);
+  if (g > 4096u) g = 4096u;
+  k_row_len_max<<<g, kT, 0, s>>>(n_rows, rowptr, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- bandwidth probe -----
+// Reads `bytes` (a multiple of 16) reps times with 128-bit streaming loads; the XOR of
+// everything read is stored only if it equals an impossible value, so the loads stay.
+__global__ void k_read_probe(const uint4 *buf, int64_t n16, int reps, unsigned long long *sink) {
+  uint32_t acc = 0;
+  for (int r = 0; r < reps; ++r) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const uint4 v = ld_nc_u4(buf + i);
+      acc ^= v.x ^ v.y ^ v.z ^ v.w;
+    }
+  }
+  if (acc == 0x9E3779B9u) *sink = acc;
+}
+
+cudaError_t launch_read_probe(const void *buf, int64_t bytes, int reps,
+                              unsigned long long *sink, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t n16 = bytes / 16;
+  int64_t g = (int64_t)sms * 8;
+  const int64_t need = (n16 + kT - 1) / kT;
+  if (g > need) g = need;
+  if (g < 1) g = 1;
+  k_read_probe<<<(unsigned)g, kT, 0, s>>>(static_cast<const uint4 *>(buf), n16, reps, sink);
+  return cudaGetLastError();
+}
+
+}  // namespace spmv

@@ -1,0 +1,442 @@
+// SpMV kernel templates (one instantiation set per storage / vector / accumulator dtype).
+//
+//  k_rowvec  - a sub-warp of VS lanes per row (Fig. 1's inner loop spread over lanes);
+//              rows go to CTAs through the hardware block scheduler. Knobs from Table II:
+//              VEC  128-bit loads of val / colind, unrolled (CMP, MB "vectorization"),
+//              D16  16-bit column deltas decoded with a sub-warp prefix sum (MB),
+//              XL2  x gathered with an L2 evict-last policy while val / colind stream with
+//                   evict-first (ML: the GPU counterpart of software prefetching into cache).
+//  k_merge   - merge-path tiles of equal (rows + nonzeros) work; rows longer than a tile
+//              are split over tiles and finished by k_merge_fixup (IMB: the decomposition
+//              of Fig. 4/5, long rows computed by many workers with a reduction).
+//  k_static  - the profiling baseline of Section III-B: one resident CTA per static
+//              nnz-balanced row range with %globaltimer stamps (P_CSR, P_IMB, P_ML) or
+//              unit-stride x[i] accesses without colind (P_CMP).
+//  k_spmm    - Y = A X for row-major X with K columns per gather.
+#pragma once
+
+#include <climits>
+
+#include "common.cuh"
+
+namespace spmv {
+
+constexpr int kRowThreads = 256;
+
+// ------------------------------------------------------------------------ k_rowvec ----
+template <typename ValT, typename VecT, typename AccT, int VS, bool VEC, bool D16, bool XL2>
+__global__ void __launch_bounds__(kRowThreads) k_rowvec(const RunArgs a) {
+  constexpr int GROUPS = kRowThreads / VS;
+  const int lane = threadIdx.x & (VS - 1);
+  const int64_t row = (int64_t)blockIdx.x * GROUPS + threadIdx.x / VS;
+  if (row >= a.n_rows) return;  // the whole sub-warp leaves together
+  const unsigned mask = group_mask<VS>();
+  const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
+  const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
+  uint64_t pol_s = 0, pol_x = 0;
+  if constexpr (VEC) pol_s = policy_evict_first();
+  if constexpr (XL2) pol_x = policy_evict_last();
+  const int s = __ldg(a.rowptr + row), e = __ldg(a.rowptr + row + 1);
+  AccT sum = 0;
+  if constexpr (!VEC) {
+    const int32_t *__restrict__ col = a.colind;
+    for (int j = s + lane; j < e; j += VS)
+      sum += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(col + j), pol_x);
+  } else if constexpr (!D16) {
+    // 4 elements per lane per step: colind as one 16-byte load, val as 8..32 bytes.
+    const int32_t *__restrict__ col = a.colind;
+    const int a0 = s & ~3;
+#pragma unroll 2
+    for (int b = a0 + lane * 4; b < e; b += VS * 4) {
+      const uint4 c4 = ld16<true>(col + b, pol_s);
+      AccT v[4];
+      VLoad<AccT, true, 4>::run(val + b, v, pol_s);
+      const int cc[4] = {(int)c4.x, (int)c4.y, (int)c4.z, (int)c4.w};
+      AccT xv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = b + q;
+        xv[q] = (j >= s && j < e) ? (AccT)ldx<XL2>(x + cc[q], pol_x) : (AccT)0;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = b + q;
+        if (j >= s && j < e) sum += v[q] * xv[q];
+      }
+    }
+  } else {
+    const int32_t base = __ldg(a.dbase + row);
+    if (base < 0) {
+      // escape row: its columns are stored in full, in row order
+      const int64_t off = -(int64_t)base - 1 - s;
+      for (int j = s + lane; j < e; j += VS)
+        sum += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(a.esc + off + j), pol_x);
+    } else {
+      // 8 deltas (16 bytes) per lane per step; column = base + running prefix sum
+      const uint16_t *__restrict__ dl = a.delta;
+      const int a0 = s & ~7;
+      const int n_it = (e - a0 + VS * 8 - 1) / (VS * 8);
+      int running = base;
+      for (int it = 0; it < n_it; ++it) {
+        const int b = a0 + it * (VS * 8) + lane * 8;
+        // lanes whose 8 elements start past the row end load nothing (reads stay below
+        // e + 8, inside the arrays' slack)
+        const bool live = b < e;
+        const uint4 d4 = live ? ld16<true>(dl + b, pol_s) : make_uint4(0u, 0u, 0u, 0u);
+        AccT v[8];
+        if (live) {
+          VLoad<AccT, true, 8>::run(val + b, v, pol_s);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) v[q] = (AccT)0;
+        }
+        const uint32_t w[4] = {d4.x, d4.y, d4.z, d4.w};
+        int p[8];
+        int acc = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int j = b + q;
+          int d = (q & 1) ? (int)(w[q >> 1] >> 16) : (int)(w[q >> 1] & 0xFFFFu);
+          d = (j >= s && j < e) ? d : 0;
+          acc += d;
+          p[q] = acc;
+        }
+        const int incl = group_incl_scan<VS>(acc, lane, mask);
+        const int excl = incl - acc;
+        const int tot = __shfl_sync(mask, incl, VS - 1, VS);
+        AccT xv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int j = b + q;
+          xv[q] = (j >= s && j < e) ? (AccT)ldx<XL2>(x + (running + excl + p[q]), pol_x)
+                                    : (AccT)0;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int j = b + q;
+          if (j >= s && j < e) sum += v[q] * xv[q];
+        }
+        running += tot;
+      }
+    }
+  }
+  sum = group_sum<VS>(sum, mask);
+  if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)sum;
+}
+
+// ------------------------------------------------------------------------- k_merge ----
+// Tile t covers merge items [t*D, (t+1)*D): the row-end events and nonzeros between the
+// table entries coord[t] and coord[t+1] (rows ended, nonzeros consumed).
+//  1. stage the tile's row ends and the products val[j] * x[colind[j]] in shared memory
+//     (coalesced loads, all gathers of the tile in flight at once);
+//  2. every thread takes IPT consecutive merge items (found by a merge-path search in
+//     shared memory) and sums each row it sees;
+//  3. a row that began in an earlier thread gets those threads' carries added in thread
+//     order; a row that began in an earlier tile is finished by k_merge_fixup, which adds
+//     the earlier tiles' carries in tile order (no atomics: results are reproducible).
+template <typename ValT, typename VecT, typename AccT, bool XL2>
+__global__ void __launch_bounds__(kMergeThreads) k_merge(const RunArgs a) {
+  constexpr int D = kMergeItems;
+  __shared__ int s_rowend[D + 1];
+  __shared__ AccT s_prod[D];
+  __shared__ int s_crow[kMergeThreads];
+  __shared__ AccT s_cval[kMergeThreads];
+  const int t = blockIdx.x;
+  const int2 c0 = a.coord[t], c1 = a.coord[t + 1];
+  const int row0 = c0.x, nz0 = c0.y;
+  const int nrows_t = c1.x - c0.x, nnz_t = c1.y - c0.y;
+  const int total = nrows_t + nnz_t;
+  const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
+  const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
+  const int32_t *__restrict__ col = a.colind;
+  uint64_t pol_s = 0, pol_x = 0;
+  if constexpr (XL2) {
+    pol_s = policy_evict_first();
+    pol_x = policy_evict_last();
+  }
+  for (int k = threadIdx.x; k < nrows_t; k += kMergeThreads)
+    s_rowend[k] = __ldg(a.rowptr + row0 + 1 + k);
+  if (threadIdx.x == 0) s_rowend[nrows_t] = INT_MAX;
+#pragma unroll 4
+  for (int k = threadIdx.x; k < nnz_t; k += kMergeThreads) {
+    const int j = nz0 + k;
+    s_prod[k] = widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(col + j), pol_x);
+  }
+  __syncthreads();
+
+  const int d0 = min((int)threadIdx.x * kMergeIpt, total);
+  const int d1 = min(d0 + kMergeIpt, total);
+  int lo = max(0, d0 - nnz_t), hi = min(d0, nrows_t);
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (s_rowend[mid] <= nz0 + d0 - 1 - mid) lo = mid + 1;
+    else hi = mid;
+  }
+  int ra = lo, nb = d0 - lo;
+  AccT acc = 0;
+  bool has_first = false;
+  int first_row = 0;
+  AccT first_val = 0;
+  VecT *__restrict__ y = static_cast<VecT *>(a.y);
+  for (int d = d0; d < d1; ++d) {
+    if (nz0 + nb < s_rowend[ra]) {
+      acc += s_prod[nb];
+      ++nb;
+    } else {
+      const int r = row0 + ra;
+      if (!has_first) {
+        has_first = true;
+        first_row = r;
+        first_val = acc;
+      } else {
+        y[r] = (VecT)acc;
+      }
+      acc = 0;
+      ++ra;
+    }
+  }
+  s_crow[threadIdx.x] = row0 + ra;
+  s_cval[threadIdx.x] = acc;
+  __syncthreads();
+  if (has_first) {
+    AccT tot = first_val;
+    for (int q = (int)threadIdx.x - 1; q >= 0 && s_crow[q] == first_row; --q) tot += s_cval[q];
+    const bool continued = (first_row == row0) && (__ldg(a.rowptr + row0) < nz0);
+    if (continued) a.head_val[t] = (double)tot;
+    else y[first_row] = (VecT)tot;
+  }
+  if (threadIdx.x == kMergeThreads - 1) {
+    const int tr = c1.x;
+    double tv = 0.0;
+    for (int q = kMergeThreads - 1; q >= 0 && s_crow[q] == tr; --q) tv += (double)s_cval[q];
+    a.tail_row[t] = tr;
+    a.tail_val[t] = tv;
+  }
+}
+
+// Rows that began in an earlier tile: y[row] = (carries of earlier tiles, nearest first)
+// + the part summed in the tile that ends the row. FP64 throughout.
+template <typename VecT>
+__global__ void k_merge_fixup(const RunArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1;
+  if (t >= a.n_tiles) return;
+  const int2 c0 = a.coord[t], c1 = a.coord[t + 1];
+  const int row0 = c0.x;
+  if (c1.x - c0.x <= 0) return;                  // the tile ends no row
+  if (!(__ldg(a.rowptr + row0) < c0.y)) return;  // its first row starts inside it
+  double tot = 0.0;
+  for (int64_t q = t - 1; q >= 0 && a.tail_row[q] == row0; --q) tot += a.tail_val[q];
+  tot += a.head_val[t];
+  static_cast<VecT *>(a.y)[row0] = (VecT)tot;
+}
+
+// ------------------------------------------------------------------------ k_static ----
+template <typename ValT, typename VecT, typename AccT, int VS, bool CMP>
+__global__ void __launch_bounds__(kRowThreads) k_static(const ProfileArgs a) {
+  __shared__ unsigned long long t0;
+  if (threadIdx.x == 0) t0 = globaltimer_ns();
+  __syncthreads();
+  constexpr int GROUPS = kRowThreads / VS;
+  const int lane = threadIdx.x & (VS - 1);
+  const unsigned mask = group_mask<VS>();
+  const int r0 = a.part[blockIdx.x], r1 = a.part[blockIdx.x + 1];
+  const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
+  const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
+  VecT *__restrict__ y = static_cast<VecT *>(a.y);
+  const int32_t *__restrict__ col = a.colind;
+  const int64_t xmax = a.n_cols - 1;
+  for (int row = r0 + (int)threadIdx.x / VS; row < r1; row += GROUPS) {
+    const int s = __ldg(a.rowptr + row), e = __ldg(a.rowptr + row + 1);
+    AccT sum = 0;
+    if constexpr (CMP) {
+      if (s < e) {   // a matrix without columns has only empty rows: x is never read
+        const VecT xi = __ldg(x + (row < xmax ? row : xmax));
+        for (int j = s + lane; j < e; j += VS) sum += widen<AccT>(val[j]) * (AccT)xi;
+      }
+    } else {
+      for (int j = s + lane; j < e; j += VS)
+        sum += widen<AccT>(val[j]) * (AccT)__ldg(x + __ldg(col + j));
+    }
+    sum = group_sum<VS>(sum, mask);
+    if (lane == 0) y[row] = (VecT)sum;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a.t_start[blockIdx.x] = t0;
+    a.t_end[blockIdx.x] = globaltimer_ns();
+  }
+}
+
+// -------------------------------------------------------------------------- k_spmm ----
+// K consecutive right-hand-side columns [off, off + K) of row-major X / Y (leading
+// dimension ldk). For K > 1 the K values of one X row are fetched as 16-byte loads
+// (launcher guarantees alignment: ldk and off multiples of the vector width).
+template <typename VecT, int K> struct XRow {
+  __device__ __forceinline__ static void load(const VecT *p, VecT *o) {
+    if constexpr (K == 1) {
+      o[0] = __ldg(p);
+    } else {
+      constexpr int PER = 16 / (int)sizeof(VecT);
+#pragma unroll
+      for (int q = 0; q < K; q += PER) {
+        const uint4 u = ld_nc_u4(p + q);
+        if constexpr (sizeof(VecT) == 8) {
+          o[q] = (VecT)__hiloint2double(u.y, u.x);
+          o[q + 1] = (VecT)__hiloint2double(u.w, u.z);
+        } else {
+          o[q] = (VecT)__uint_as_float(u.x);
+          o[q + 1] = (VecT)__uint_as_float(u.y);
+          o[q + 2] = (VecT)__uint_as_float(u.z);
+          o[q + 3] = (VecT)__uint_as_float(u.w);
+        }
+      }
+    }
+  }
+};
+
+template <typename ValT, typename VecT, typename AccT, int VS, int K>
+__global__ void __launch_bounds__(kRowThreads) k_spmm(const RunArgs a, int off, int ldk) {
+  constexpr int GROUPS = kRowThreads / VS;
+  const int lane = threadIdx.x & (VS - 1);
+  const int64_t row = (int64_t)blockIdx.x * GROUPS + threadIdx.x / VS;
+  if (row >= a.n_rows) return;
+  const unsigned mask = group_mask<VS>();
+  const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
+  const VecT *__restrict__ X = static_cast<const VecT *>(a.x);
+  const int s = __ldg(a.rowptr + row), e = __ldg(a.rowptr + row + 1);
+  AccT acc[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) acc[q] = 0;
+  for (int j = s + lane; j < e; j += VS) {
+    const AccT v = widen<AccT>(val[j]);
+    VecT xr[K];
+    XRow<VecT, K>::load(X + (int64_t)__ldg(a.colind + j) * ldk + off, xr);
+#pragma unroll
+    for (int q = 0; q < K; ++q) acc[q] += v * (AccT)xr[q];
+  }
+  VecT *__restrict__ Y = static_cast<VecT *>(a.y) + row * ldk + off;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const AccT r = group_sum<VS>(acc[q], mask);
+    if (lane == 0) Y[q] = (VecT)r;
+  }
+}
+
+// ------------------------------------------------------------------------ launchers ---
+inline unsigned grid_for_rows(int64_t n_rows, int vs) {
+  const int64_t groups = kRowThreads / vs;
+  return (unsigned)((n_rows + groups - 1) / groups);
+}
+
+template <typename ValT, typename VecT, typename AccT, int VS>
+cudaError_t launch_rowvec_vs(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
+  const unsigned g = grid_for_rows(a.n_rows, VS);
+  const bool d16 = v.index == 1, vec = v.vec != 0 || d16, xl2 = v.xpath != 0;
+  if (!vec) {
+    if (xl2) k_rowvec<ValT, VecT, AccT, VS, false, false, true><<<g, kRowThreads, 0, s>>>(a);
+    else k_rowvec<ValT, VecT, AccT, VS, false, false, false><<<g, kRowThreads, 0, s>>>(a);
+  } else if (!d16) {
+    if (xl2) k_rowvec<ValT, VecT, AccT, VS, true, false, true><<<g, kRowThreads, 0, s>>>(a);
+    else k_rowvec<ValT, VecT, AccT, VS, true, false, false><<<g, kRowThreads, 0, s>>>(a);
+  } else {
+    if (xl2) k_rowvec<ValT, VecT, AccT, VS, true, true, true><<<g, kRowThreads, 0, s>>>(a);
+    else k_rowvec<ValT, VecT, AccT, VS, true, true, false><<<g, kRowThreads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <typename ValT, typename VecT, typename AccT>
+cudaError_t launch_spmv_impl(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
+  if (a.n_rows == 0) return cudaSuccess;
+  if (v.partition == 1) {
+    if (a.n_tiles == 0) return cudaSuccess;
+    if (v.xpath) k_merge<ValT, VecT, AccT, true><<<(unsigned)a.n_tiles, kMergeThreads, 0, s>>>(a);
+    else k_merge<ValT, VecT, AccT, false><<<(unsigned)a.n_tiles, kMergeThreads, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (a.n_tiles > 1) {
+      const unsigned g = (unsigned)((a.n_tiles - 1 + 255) / 256);
+      k_merge_fixup<VecT><<<g, 256, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+  }
+  switch (v.vs) {
+    case 2: return launch_rowvec_vs<ValT, VecT, AccT, 2>(v, a, s);
+    case 4: return launch_rowvec_vs<ValT, VecT, AccT, 4>(v, a, s);
+    case 8: return launch_rowvec_vs<ValT, VecT, AccT, 8>(v, a, s);
+    case 16: return launch_rowvec_vs<ValT, VecT, AccT, 16>(v, a, s);
+    case 32: return launch_rowvec_vs<ValT, VecT, AccT, 32>(v, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename ValT, typename VecT, typename AccT, int VS>
+cudaError_t launch_spmm_vs(const RunArgs &a, cudaStream_t s) {
+  const unsigned g = grid_for_rows(a.n_rows, VS);
+  const int k = a.k;
+  constexpr int PER = 16 / (int)sizeof(VecT);
+  int off = 0;
+  if (k % PER == 0) {
+    for (; off + 16 <= k; off += 16) k_spmm<ValT, VecT, AccT, VS, 16><<<g, kRowThreads, 0, s>>>(a, off, k);
+    for (; off + 4 <= k; off += 4) k_spmm<ValT, VecT, AccT, VS, 4><<<g, kRowThreads, 0, s>>>(a, off, k);
+  }
+  for (; off < k; ++off) k_spmm<ValT, VecT, AccT, VS, 1><<<g, kRowThreads, 0, s>>>(a, off, k);
+  return cudaGetLastError();
+}
+
+template <typename ValT, typename VecT, typename AccT>
+cudaError_t launch_spmm_impl(const RunArgs &a, int vs, cudaStream_t s) {
+  if (a.n_rows == 0) return cudaSuccess;
+  switch (vs) {
+    case 2: return launch_spmm_vs<ValT, VecT, AccT, 2>(a, s);
+    case 4: return launch_spmm_vs<ValT, VecT, AccT, 4>(a, s);
+    case 8: return launch_spmm_vs<ValT, VecT, AccT, 8>(a, s);
+    case 16: return launch_spmm_vs<ValT, VecT, AccT, 16>(a, s);
+    case 32: return launch_spmm_vs<ValT, VecT, AccT, 32>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename ValT, typename VecT, typename AccT, int VS>
+cudaError_t launch_static_vs(const ProfileArgs &a, cudaStream_t s) {
+  if (a.cmp_mode) k_static<ValT, VecT, AccT, VS, true><<<a.n_ctas, kRowThreads, 0, s>>>(a);
+  else k_static<ValT, VecT, AccT, VS, false><<<a.n_ctas, kRowThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename ValT, typename VecT, typename AccT>
+cudaError_t launch_profile_impl(const ProfileArgs &a, cudaStream_t s) {
+  if (a.n_ctas <= 0) return cudaSuccess;
+  switch (a.vs) {
+    case 2: return launch_static_vs<ValT, VecT, AccT, 2>(a, s);
+    case 4: return launch_static_vs<ValT, VecT, AccT, 4>(a, s);
+    case 8: return launch_static_vs<ValT, VecT, AccT, 8>(a, s);
+    case 16: return launch_static_vs<ValT, VecT, AccT, 16>(a, s);
+    case 32: return launch_static_vs<ValT, VecT, AccT, 32>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename ValT, typename VecT, typename AccT>
+int profile_occupancy() {
+  int blocks = 0;
+  // all VS share the same resource footprint closely; take the largest-register one
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_static<ValT, VecT, AccT, 2, false>,
+                                                kRowThreads, 0);
+  return blocks > 0 ? blocks : 1;
+}
+
+}  // namespace spmv
+
+// Defines kernel_set_<TAG>() for one dtype combination.
+#define SPMV_DEFINE_SET(TAG, VALT, VECT, ACCT)                                          \
+  namespace spmv {                                                                      \
+  const KernelSet *kernel_set_##TAG() {                                                 \
+    static KernelSet ks = {&launch_spmv_impl<VALT, VECT, ACCT>,                         \
+                           &launch_spmm_impl<VALT, VECT, ACCT>,                         \
+                           &launch_profile_impl<VALT, VECT, ACCT>, 0};                  \
+    if (ks.profile_blocks_per_sm == 0)                                                  \
+      ks.profile_blocks_per_sm = profile_occupancy<VALT, VECT, ACCT>();                 \
+    return &ks;                                                                         \
+  }                                                                                     \
+  }

@@ -1,0 +1,137 @@
+"""Bit-exact GPU parity of the integer and byte work: CSR validation, value rounding, the
+16-bit delta index, merge-path table, Table I features and the selector's pure rules."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return torch_cuda()
+
+
+@pytest.fixture(scope="module")
+def api(torch):
+    from paper_1711_05487_gb300 import api as _api
+    return _api
+
+
+@pytest.fixture(scope="module")
+def abi(torch):
+    from paper_1711_05487_gb300 import _abi
+    return _abi
+
+
+FORMAT_MATS = {
+    "st27_14": lambda: synth.stencil_27pt(14),
+    "scattered_escape": lambda: synth.scattered(300_000, 4, seed=21),
+    "powerlaw": lambda: synth.power_law(50_000, seed=22, dtype=np.float64),
+    "ragged_empty": lambda: synth.uniform_random(7001, 80, seed=23, min_per_row=0),
+    "banded_wide": lambda: synth.banded(200_000, 70_000, 0.0005, seed=24),
+    "identity1": lambda: synth.identity(1),
+}
+
+
+@pytest.mark.parametrize("name", list(FORMAT_MATS))
+def test_delta16_bit_exact_and_round_trip(api, name):
+    m = FORMAT_MATS[name]()
+    A = api.SpmvMatrix.from_csr(m)
+    A.set_variant(index=1, vec=1)
+    base, delta, esc = A.delta16()
+    ob, od, oe = oracle.delta16_encode(m.rowptr, m.colind)
+    assert np.array_equal(base.cpu().numpy(), ob)
+    assert np.array_equal(delta.cpu().numpy().view(np.uint16), od)
+    assert np.array_equal(esc.cpu().numpy(), oe)
+    rp, ci, v = A.export_csr()
+    assert np.array_equal(rp.cpu().numpy(), m.rowptr)
+    assert np.array_equal(ci.cpu().numpy(), m.colind)
+    assert np.array_equal(v.cpu().numpy().view(np.uint64), m.val.view(np.uint64))
+
+
+@pytest.mark.parametrize("name", list(FORMAT_MATS))
+def test_merge_path_table_bit_exact(api, name):
+    m = FORMAT_MATS[name]()
+    A = api.SpmvMatrix.from_csr(m)
+    A.set_variant(partition=1)
+    c, items = A.merge_path()
+    assert np.array_equal(c.cpu().numpy(), oracle.merge_path(m.rowptr, items))
+
+
+def test_value_rounding_bit_exact(abi, torch):
+    rng = np.random.default_rng(3)
+    v = np.concatenate([rng.standard_normal(200_000) * 2.0 ** rng.integers(-150, 130, 200_000),
+                        [0.0, -0.0, 1 + 2 ** -8, 1 + 3 * 2 ** -8, (2 - 2 ** -8) * 2.0 ** 127,
+                         2.0 ** -133, 2.0 ** -134, 3 * 2.0 ** -134, 1e-300, 3.5e38, 1e308,
+                         np.inf, -np.inf, np.nan]])
+    vin = torch.from_numpy(v).cuda()
+    o32 = torch.empty(v.size, dtype=torch.float32, device="cuda")
+    o16 = torch.empty(v.size, dtype=torch.int16, device="cuda")
+    abi.spmv_round_values(vin.data_ptr(), o32.data_ptr(), v.size, abi.SPMV_F32, 0)
+    abi.spmv_round_values(vin.data_ptr(), o16.data_ptr(), v.size, abi.SPMV_BF16, 0)
+    torch.cuda.synchronize()
+    with np.errstate(over="ignore"):
+        assert np.array_equal(o32.cpu().numpy().view(np.uint32),
+                              oracle.round_f32(v).view(np.uint32))
+    assert np.array_equal(o16.cpu().numpy().view(np.uint16), oracle.round_bf16_bits(v))
+
+
+def test_validation_codes_match_oracle(abi, torch):
+    cases = [
+        (2, 4, [0, 2, 3], [0, 3, 1]),
+        (2, 4, [1, 2, 3], [0, 3, 1]),
+        (2, 4, [0, 3, 2], [0, 3]),
+        (2, 4, [0, 2, 2], [0, 3, 1]),
+        (2, 3, [0, 2, 3], [0, 3, 1]),
+        (2, 4, [0, 2, 3], [0, 3, -1]),
+        (2, 4, [0, 2, 3], [3, 0, 1]),
+        (2, 4, [0, 2, 3], [3, 3, 1]),
+        (3, 9, [0, 3, 3, 6], [0, 4, 2, 5, 8, 9]),
+        (3, 9, [0, 3, 3, 6], [0, 4, 9, 5, 5, 8]),
+    ]
+    for n_rows, n_cols, rp, ci in cases:
+        rp_d = torch.tensor(rp, dtype=torch.int32, device="cuda")
+        ci_d = torch.tensor(ci + [0], dtype=torch.int32, device="cuda")
+        code = abi.spmv_validate_csr(n_rows, n_cols, len(ci), rp_d.data_ptr(), ci_d.data_ptr(), 0)
+        want = oracle.validate_csr(n_rows, n_cols, np.array(rp, np.int32), np.array(ci, np.int32))
+        assert code == want, (rp, ci, code, want)
+
+
+def test_create_rejects_invalid_csr(api):
+    from paper_1711_05487_gb300._abi import SpmvError
+    with pytest.raises(SpmvError) as e:
+        api.SpmvMatrix(2, 4, np.array([0, 2, 3], np.int32), np.array([3, 0, 1], np.int32),
+                       np.ones(3))
+    assert e.value.status == 1
+
+
+FEATURE_MATS = {
+    "lap256": lambda: synth.laplacian_2d(256),
+    "st27_20": lambda: synth.stencil_27pt(20),
+    "powerlaw": lambda: synth.power_law(100_000, seed=31, dtype=np.float64),
+    "scattered": lambda: synth.scattered(200_000, 8, seed=32),
+    "ragged_empty": lambda: synth.uniform_random(9001, 100, seed=33, min_per_row=0),
+    "banded": lambda: synth.banded(50_000, 2000, 0.05, seed=34),
+}
+
+
+@pytest.mark.parametrize("name", list(FEATURE_MATS))
+@pytest.mark.parametrize("vec", ["f64", "f32"])
+def test_features_bit_exact(api, torch, name, vec):
+    m = FEATURE_MATS[name]()
+    A = api.SpmvMatrix.from_csr(m)
+    if vec == "f32":
+        A.set_precision("f32", "f32", "f32")
+    f, isum = A.features(line_bytes=128)
+    vb = 8 if vec == "f64" else 4
+    sb = 8 if vec == "f64" else 4
+    ws = 4 * (m.n_rows + 1) + (4 + sb) * m.nnz + vb * (m.n_rows + m.n_cols)
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    of, oi = oracle.features(m.n_rows, m.n_cols, m.rowptr, m.colind, line_elems=128 // vb,
+                             ws_bytes=ws, llc_bytes=l2)
+    assert np.array_equal(f.view(np.uint64), of.view(np.uint64)), (f, of)
+    assert np.array_equal(isum, oi)

@@ -216,3 +216,34 @@ def test_log2p1_accuracy_and_exact_powers():
         assert oracle.log2p1_f32(np.float32(2 ** k - 1))[0] == float(k)
     assert oracle.log2p1_f32(np.float32(0.0))[0] == 0.0
     assert oracle.log2p1_f32(np.float32(-3.0))[0] == 0.0
+
+
+def test_feature_rules_each_branch():
+    base = np.zeros(14)
+    def f(size=0.0, nnz_max=10.0, nnz_avg=10.0, misses=1.0):
+        v = base.copy()
+        v[0], v[3], v[4], v[13] = size, nnz_max, nnz_avg, misses
+        return v
+    l2 = 100 << 20
+    assert oracle.feature_rules(f(), 10 ** 6, 8, l2) == 1                    # MB
+    assert oracle.feature_rules(f(nnz_max=400), 10 ** 6, 8, l2) == 4         # IMB
+    assert oracle.feature_rules(f(misses=6.0), 10 ** 8, 8, l2) == 2          # ML: big x
+    assert oracle.feature_rules(f(misses=6.0), 10 ** 6, 8, l2) == 1          # x fits: MB
+    assert oracle.feature_rules(f(size=1.0), 10 ** 6, 8, l2) == 8            # CMP
+    assert oracle.feature_rules(f(nnz_avg=3.0, nnz_max=3.0), 10 ** 6, 8, l2) == 8
+    assert oracle.feature_rules(f(nnz_max=400, misses=6.0), 10 ** 8, 8, l2) == 6
+
+
+def test_mlp_inputs_definition():
+    feat = np.zeros(16)
+    feat[:14] = [1, 0.5, 1, 63, 1, 3, 3, 255, 15, 3, 0.25, 0.125, 0.75, 0.5]
+    feat[14], feat[15] = 1023.0, 1023.0
+    x = oracle.mlp_inputs(feat)[0]
+    # log2(1 + v) is exact at v = 2^k - 1; the other entries are exact FP32 values
+    assert x.tolist() == [10.0, 1.0, 2.0, 6.0, 6.0, 4.0, 2.0, 0.25, 0.125, 0.75, 0.5, 1.0]
+    mu = np.full(12, 1.0, np.float32)
+    inv = np.full(12, 0.5, np.float32)
+    y = oracle.mlp_inputs(feat, mu, inv)[0]
+    assert np.array_equal(y, (x - 1.0) * 0.5)
+    z = np.zeros(16)
+    assert oracle.mlp_inputs(z)[0].tolist() == [0.0] * 12
