@@ -68,7 +68,8 @@ typedef struct {
   int32_t xpath;     /* 0: default; 1: x kept L2-resident (evict-last gathers through the
                         read-only path, evict-first streams) (ML)                         */
   int32_t vec;       /* 0: scalar loads; 1: 128-bit loads of val/colind, unrolled (MB/CMP) */
-  int32_t vs;        /* sub-warp width for partition 0: 2,4,8,16,32; 0 = heuristic       */
+  int32_t vs;        /* sub-warp width for partition 0: 1 (thread per row over a tile
+                        staged in shared memory by bulk copies), 2,4,8,16,32; 0 = heuristic */
 } spmv_variant;
 
 #define SPMV_NUM_FEATURES 14

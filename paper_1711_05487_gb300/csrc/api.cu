@@ -84,6 +84,13 @@ int heuristic_vs(double nnz_avg, int elems_per_lane) {
   return pow2_ceil_clamped(nnz_avg / (double)elems_per_lane, 2, 32);
 }
 
+// Width for the pool's sub-warp-row variants: rows of up to 64 nonzeros on average go to
+// the thread-per-row tile kernel (width 1: one FMA per nonzero, no lane reduction);
+// longer rows to sub-warps wide enough to cover them.
+int pool_vs(double nnz_avg, int elems_per_lane) {
+  return nnz_avg <= 64.0 ? 1 : heuristic_vs(nnz_avg, elems_per_lane);
+}
+
 struct DeviceInfo {
   int sms = 0;
   int64_t l2_bytes = 0;
@@ -124,6 +131,8 @@ struct spmv_matrix {
   // run state
   spmv_variant variant{};
   bool tuned = false;
+  int32_t tile_cap = 0;        // staged elements per tile of the thread-per-row kernel
+  DevBuf d_err;                // device error word of bounded waits
   DevBuf x_stage, y_stage, scratch;
   int32_t last_error = 0;
   double nnz_avg() const { return n_rows ? (double)nnz / (double)n_rows : 0.0; }
@@ -159,6 +168,8 @@ RunArgs run_args(const spmv_matrix *h, const void *x, void *y) {
   a.tail_row = h->tail_row.as<int32_t>();
   a.tail_val = h->tail_val.as<double>();
   a.head_val = h->head_val.as<double>();
+  a.tile_cap = h->tile_cap;
+  a.err = h->d_err.as<int32_t>();
   return a;
 }
 
@@ -200,6 +211,21 @@ void build_merge(spmv_matrix *h, cudaStream_t s) {
   h->has_merge = true;
 }
 
+// Staged elements per tile of the thread-per-row kernel: the largest tile of the matrix,
+// capped so that a CTA's shared memory stays within 48 KB (tiles above the cap are
+// computed from global memory).
+void compute_tile_cap(spmv_matrix *h, const spmv_variant &v, cudaStream_t s) {
+  const int eb = (int)dtype_bytes(h->storage) + (v.index == 1 ? 2 : 4);
+  const int limit = (((48 * 1024 - 16) / eb) / 8) * 8;
+  DevBuf mx;
+  mx.alloc(4, 4, s);
+  CK(launch_tile_max(h->n_rows, h->rowptr.as<int32_t>(), kTileRows, mx.as<int32_t>(), s));
+  int32_t m = 0;
+  CK(cudaMemcpyAsync(&m, mx.p, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  h->tile_cap = std::min(m, limit);
+}
+
 void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
   if (v.partition == 1) {
     v.index = 0;                 // the delta index is built for sub-warp rows only
@@ -209,7 +235,11 @@ void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
       v.vec = 1;
       build_delta16(h, s);
     }
-    if (v.vs == 0) v.vs = heuristic_vs(h->nnz_avg(), v.index == 1 ? 8 : (v.vec ? 4 : 1));
+    if (v.vs == 0) {
+      v.vs = (v.vec || v.index == 1) ? pool_vs(h->nnz_avg(), v.index == 1 ? 8 : 4)
+                                     : heuristic_vs(h->nnz_avg(), 1);
+    }
+    compute_tile_cap(h, v, s);
   }
 }
 
@@ -218,8 +248,8 @@ bool valid_variant(const spmv_variant &v) {
   if (v.index != 0 && v.index != 1) return false;
   if (v.xpath != 0 && v.xpath != 1) return false;
   if (v.vec != 0 && v.vec != 1) return false;
-  if (v.partition == 0 && v.vs != 0 && v.vs != 2 && v.vs != 4 && v.vs != 8 && v.vs != 16 &&
-      v.vs != 32)
+  if (v.partition == 0 && v.vs != 0 && v.vs != 1 && v.vs != 2 && v.vs != 4 && v.vs != 8 &&
+      v.vs != 16 && v.vs != 32)
     return false;
   return true;
 }
@@ -500,7 +530,7 @@ void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, cudaStream_t s) {
   CK(launch_fill_const(x.p, h->vec, h->n_cols, 1.0, s));
   float best = 1e30f;
   int best_vs = v.vs;
-  const int widths[5] = {2, 4, 8, 16, 32};
+  const int widths[6] = {1, 2, 4, 8, 16, 32};
   for (int w : widths) {
     spmv_variant t = v;
     t.vs = w;
@@ -604,6 +634,7 @@ spmv_status spmv_create(spmv_handle_t *out, int64_t n_rows, int64_t n_cols, int6
     h->in_type = val_type;
     default_types(val_type, &h->storage, &h->vec, &h->acc);
     const size_t eb = dtype_bytes(val_type);
+    h->d_err.alloc(4, 4, s, true);
     h->rowptr.alloc(4 * (size_t)(n_rows + 1), 4, s);
     h->colind.alloc(4 * (size_t)nnz, 4, s);
     h->val_in.alloc(eb * (size_t)nnz, eb, s);
@@ -636,7 +667,7 @@ spmv_status spmv_destroy(spmv_handle_t h) {
   cudaDeviceSynchronize();
   for (DevBuf *b : {&h->rowptr, &h->colind, &h->val_in, &h->val_store, &h->dbase, &h->delta,
                     &h->esc, &h->coord, &h->tail_row, &h->tail_val, &h->head_val, &h->x_stage,
-                    &h->y_stage, &h->scratch})
+                    &h->y_stage, &h->scratch, &h->d_err})
     b->release();
   delete h;
   return SPMV_OK;
@@ -976,9 +1007,15 @@ spmv_status spmv_round_values(const double *in, void *out, int64_t n, spmv_dtype
 
 spmv_status spmv_get_last_device_error(spmv_handle_t h, int32_t *code) {
   if (!h || !code) return SPMV_ERR_ARG;
-  *code = h->last_error;
-  h->last_error = 0;
-  return SPMV_OK;
+  return guarded([&]() -> spmv_status {
+    CK(cudaDeviceSynchronize());
+    int32_t c = 0;
+    CK(cudaMemcpy(&c, h->d_err.p, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemset(h->d_err.p, 0, 4));
+    *code = c ? c : h->last_error;
+    h->last_error = 0;
+    return SPMV_OK;
+  });
 }
 
 spmv_status spmv_get_device_bytes(spmv_handle_t h, int64_t *bytes) {

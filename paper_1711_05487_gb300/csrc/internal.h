@@ -35,7 +35,14 @@ struct RunArgs {
   double *tail_val = nullptr;        // [n_tiles]
   double *head_val = nullptr;        // [n_tiles]
   int32_t k = 1;                     // right-hand sides (SpMM)
+  int32_t tile_cap = 0;              // staged elements per row tile (thread-per-row kernel)
+  int32_t *err = nullptr;            // device error word (bounded waits)
 };
+
+// Thread-per-row tile kernel geometry: rows (= threads) per CTA.
+constexpr int kTileRows = 128;
+// A bounded device wait gives up after this many nanoseconds.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
 // Static-partition profiling launch (Section III-B micro-benchmarks).
 struct ProfileArgs {
@@ -148,6 +155,9 @@ cudaError_t launch_features(int64_t n_rows, const int32_t *rowptr, const int32_t
                             FeatSums *out, cudaStream_t s);
 cudaError_t launch_row_len_max(int64_t n_rows, const int32_t *rowptr, int32_t *out,
                                cudaStream_t s);
+// max over tiles of `tile_rows` rows of the 8-aligned staged element count
+cudaError_t launch_tile_max(int64_t n_rows, const int32_t *rowptr, int tile_rows, int32_t *out,
+                            cudaStream_t s);
 
 // Bandwidth probe
 cudaError_t launch_read_probe(const void *buf, int64_t bytes, int reps,

@@ -556,6 +556,34 @@ cudaError_t launch_row_len_max(int64_t n_rows, const int32_t *rowptr, int32_t *o
   return cudaGetLastError();
 }
 
+// Staged size of a thread-per-row tile: elements from the tile's first nonzero rounded
+// down to a multiple of 8 to its last nonzero, rounded up to a multiple of 8.
+__global__ void k_tile_max(int64_t n_rows, const int32_t *rowptr, int tile_rows, int32_t *out) {
+  int m = 0;
+  const int64_t n_tiles = (n_rows + tile_rows - 1) / tile_rows;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r0 = t * tile_rows;
+    const int64_t r1 = r0 + tile_rows < n_rows ? r0 + tile_rows : n_rows;
+    const int a0 = rowptr[r0] & ~7;
+    m = max(m, ((rowptr[r1] - a0) + 7) & ~7);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+cudaError_t launch_tile_max(int64_t n_rows, const int32_t *rowptr, int tile_rows, int32_t *out,
+                            cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int32_t), s);
+  if (e != cudaSuccess || n_rows == 0) return e;
+  const int64_t n_tiles = (n_rows + tile_rows - 1) / tile_rows;
+  unsigned g = blocks_for(n_tiles);
+  if (g > 4096u) g = 4096u;
+  k_tile_max<<<g, kT, 0, s>>>(n_rows, rowptr, tile_rows, out);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- bandwidth probe -----
 // Reads `bytes` (a multiple of 16) reps times with 128-bit streaming loads; the XOR of
 // everything read is stored only if it equals an impossible value, so the loads stay.

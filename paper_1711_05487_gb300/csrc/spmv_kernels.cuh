@@ -16,6 +16,7 @@
 #pragma once
 
 #include <climits>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -124,13 +125,132 @@ __global__ void __launch_bounds__(kRowThreads) k_rowvec(const RunArgs a) {
   if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)sum;
 }
 
+// ----------------------------------------------------------------------- k_rowtile ----
+// One thread per row over a tile of kTileRows consecutive rows (sub-warp width 1). The
+// tile's values and column indices (int32 or 16-bit deltas) are staged into shared memory
+// by two bulk asynchronous copies (TMA) completing on an mbarrier, so the DRAM stream is
+// fully coalesced whatever the row lengths; then each thread walks its own row with one
+// fused multiply-add per nonzero and no cross-lane reduction. On GB300 the FP64 pipe
+// retires only ~2 FMA lanes per clock per SM, so spending exactly one FP64 instruction per
+// nonzero is what lets FP64 SpMV reach the memory roofline. A tile whose staged size
+// exceeds tile_cap is computed from global memory instead (a warp per row).
+template <typename ValT, typename IdxT>
+__host__ __device__ constexpr int tile_elem_bytes() {
+  return (int)(sizeof(ValT) + sizeof(IdxT));
+}
+
+template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2>
+__global__ void __launch_bounds__(kTileRows) k_rowtile(const RunArgs a) {
+  using IdxT = typename std::conditional<D16, uint16_t, int32_t>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  const int64_t r0 = (int64_t)blockIdx.x * kTileRows;
+  const int64_t r1 = min(r0 + (int64_t)kTileRows, a.n_rows);
+  const int s0 = __ldg(a.rowptr + r0), s1 = __ldg(a.rowptr + r1);
+  const int a0 = s0 & ~7;                        // 8-element (>= 16-byte) aligned start
+  const int nc = ((s1 - a0) + 7) & ~7;           // staged elements
+  const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
+  const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
+  VecT *__restrict__ y = static_cast<VecT *>(a.y);
+  uint64_t pol_x = 0;
+  if constexpr (XL2) pol_x = policy_evict_last();
+  const int64_t row = r0 + threadIdx.x;
+  if (nc <= a.tile_cap) {
+    ValT *sval = reinterpret_cast<ValT *>(smem + 16);
+    IdxT *sidx = reinterpret_cast<IdxT *>(smem + 16 + (size_t)a.tile_cap * sizeof(ValT));
+    const IdxT *gidx;
+    if constexpr (D16) gidx = a.delta;
+    else gidx = a.colind;
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      if (nc > 0) {
+        const uint64_t pol = policy_evict_first();
+        const uint32_t bv = (uint32_t)nc * (uint32_t)sizeof(ValT);
+        const uint32_t bi = (uint32_t)nc * (uint32_t)sizeof(IdxT);
+        mbar_expect_tx(bar, bv + bi);
+        bulk_g2s(sval, val + a0, bv, bar, pol);
+        bulk_g2s(sidx, gidx + a0, bi, bar, pol);
+      }
+    }
+    // row bounds while the copies are in flight
+    int s = 0, e = 0;
+    int32_t base = 0;
+    if (row < r1) {
+      s = __ldg(a.rowptr + row);
+      e = __ldg(a.rowptr + row + 1);
+      if constexpr (D16) base = __ldg(a.dbase + row);
+    }
+    __syncthreads();   // the barrier is initialised before anyone waits on it
+    if (nc > 0) {
+      if (!mbar_wait_bounded(bar, 0, kWaitLimitNs)) {
+        if (threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
+        mbar_wait_bounded(bar, 0, kWaitLimitNs);   // let the copies land before exiting
+        return;
+      }
+    }
+    if (row >= r1) return;
+    AccT acc = 0;
+    const int o = s - a0, len = e - s;
+    if constexpr (D16) {
+      if (base < 0) {
+        const int32_t *ec = a.esc + (-(int64_t)base - 1);
+#pragma unroll 4
+        for (int k = 0; k < len; ++k)
+          acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2>(x + __ldg(ec + k), pol_x), acc);
+      } else {
+        int c = base;
+#pragma unroll 4
+        for (int k = 0; k < len; ++k) {
+          c += (int)sidx[o + k];
+          acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2>(x + c, pol_x), acc);
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int k = 0; k < len; ++k)
+        acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2>(x + sidx[o + k], pol_x), acc);
+    }
+    y[row] = (VecT)acc;
+  } else {
+    // oversize tile: a warp per row straight from global memory
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t r = r0 + warp; r < r1; r += kTileRows / 32) {
+      const int s = __ldg(a.rowptr + r), e = __ldg(a.rowptr + r + 1);
+      AccT acc = 0;
+      if constexpr (D16) {
+        const int32_t base = __ldg(a.dbase + r);
+        if (base < 0) {
+          const int32_t *ec = a.esc + (-(int64_t)base - 1) - s;
+          for (int j = s + lane; j < e; j += 32)
+            acc += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(ec + j), pol_x);
+        } else {
+          // decode the row's deltas: the lane sums its own and its predecessors' deltas
+          int run = base;
+          for (int j0 = s; j0 < e; j0 += 32) {
+            const int j = j0 + lane;
+            const int d = j < e ? (int)a.delta[j] : 0;
+            const int incl = group_incl_scan<32>(d, lane, 0xffffffffu);
+            if (j < e) acc += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + (run + incl), pol_x);
+            run += __shfl_sync(0xffffffffu, incl, 31);
+          }
+        }
+      } else {
+        for (int j = s + lane; j < e; j += 32)
+          acc += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(a.colind + j), pol_x);
+      }
+      acc = group_sum<32>(acc, 0xffffffffu);
+      if (lane == 0) y[r] = (VecT)acc;
+    }
+  }
+}
+
 // ------------------------------------------------------------------------- k_merge ----
 // Tile t covers merge items [t*D, (t+1)*D): the row-end events and nonzeros between the
 // table entries coord[t] and coord[t+1] (rows ended, nonzeros consumed).
-//  1. stage the tile's row ends and the products val[j] * x[colind[j]] in shared memory
+//  1. stage the tile's row ends, values and gathered x[colind[j]] in shared memory
 //     (coalesced loads, all gathers of the tile in flight at once);
 //  2. every thread takes IPT consecutive merge items (found by a merge-path search in
-//     shared memory) and sums each row it sees;
+//     shared memory) and sums each row it sees with one fused multiply-add per nonzero;
 //  3. a row that began in an earlier thread gets those threads' carries added in thread
 //     order; a row that began in an earlier tile is finished by k_merge_fixup, which adds
 //     the earlier tiles' carries in tile order (no atomics: results are reproducible).
@@ -138,7 +258,8 @@ template <typename ValT, typename VecT, typename AccT, bool XL2>
 __global__ void __launch_bounds__(kMergeThreads) k_merge(const RunArgs a) {
   constexpr int D = kMergeItems;
   __shared__ int s_rowend[D + 1];
-  __shared__ AccT s_prod[D];
+  __shared__ AccT s_val[D];
+  __shared__ AccT s_x[D];
   __shared__ int s_crow[kMergeThreads];
   __shared__ AccT s_cval[kMergeThreads];
   const int t = blockIdx.x;
@@ -160,7 +281,8 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const RunArgs a) {
 #pragma unroll 4
   for (int k = threadIdx.x; k < nnz_t; k += kMergeThreads) {
     const int j = nz0 + k;
-    s_prod[k] = widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(col + j), pol_x);
+    s_val[k] = widen<AccT>(val[j]);
+    s_x[k] = (AccT)ldx<XL2>(x + __ldg(col + j), pol_x);
   }
   __syncthreads();
 
@@ -180,7 +302,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const RunArgs a) {
   VecT *__restrict__ y = static_cast<VecT *>(a.y);
   for (int d = d0; d < d1; ++d) {
     if (nz0 + nb < s_rowend[ra]) {
-      acc += s_prod[nb];
+      acc = fma(s_val[nb], s_x[nb], acc);   // one FP64 instruction per nonzero
       ++nb;
     } else {
       const int r = row0 + ra;
@@ -345,6 +467,31 @@ cudaError_t launch_rowvec_vs(const spmv_variant &v, const RunArgs &a, cudaStream
   return cudaGetLastError();
 }
 
+template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2>
+cudaError_t launch_rowtile_k(const RunArgs &a, cudaStream_t s) {
+  using IdxT = typename std::conditional<D16, uint16_t, int32_t>::type;
+  static int configured = 0;
+  const size_t smem = 16 + (size_t)a.tile_cap * (sizeof(ValT) + sizeof(IdxT));
+  if (smem > 48 * 1024 && configured < (int)smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_rowtile<ValT, VecT, AccT, D16, XL2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = (int)smem;
+  }
+  const unsigned g = (unsigned)((a.n_rows + kTileRows - 1) / kTileRows);
+  k_rowtile<ValT, VecT, AccT, D16, XL2><<<g, kTileRows, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename ValT, typename VecT, typename AccT>
+cudaError_t launch_rowtile(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
+  const bool d16 = v.index == 1, xl2 = v.xpath != 0;
+  if (d16) return xl2 ? launch_rowtile_k<ValT, VecT, AccT, true, true>(a, s)
+                      : launch_rowtile_k<ValT, VecT, AccT, true, false>(a, s);
+  return xl2 ? launch_rowtile_k<ValT, VecT, AccT, false, true>(a, s)
+             : launch_rowtile_k<ValT, VecT, AccT, false, false>(a, s);
+}
+
 template <typename ValT, typename VecT, typename AccT>
 cudaError_t launch_spmv_impl(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
@@ -361,6 +508,7 @@ cudaError_t launch_spmv_impl(const spmv_variant &v, const RunArgs &a, cudaStream
     return cudaGetLastError();
   }
   switch (v.vs) {
+    case 1: return launch_rowtile<ValT, VecT, AccT>(v, a, s);
     case 2: return launch_rowvec_vs<ValT, VecT, AccT, 2>(v, a, s);
     case 4: return launch_rowvec_vs<ValT, VecT, AccT, 4>(v, a, s);
     case 8: return launch_rowvec_vs<ValT, VecT, AccT, 8>(v, a, s);
