@@ -184,12 +184,36 @@ spmv_status spmv_get_merge_path(spmv_handle_t h, int32_t *coord, int64_t *n_tile
 spmv_status spmv_features(spmv_handle_t h, int32_t line_bytes, double *features,
                           uint64_t *isum, spmv_stream_t stream);
 
+/* Section III-B profile of the matrix. */
+typedef struct {
+  double p[6];           /* P_CSR, P_MB, P_ML, P_IMB, P_CMP, P_peak (GFLOP/s)             */
+  double b_max_gbs;      /* B_max used for P_MB / P_peak (HBM or L2-resident, footnote)   */
+  double b_hbm_gbs;      /* measured read bandwidth, buffer much larger than L2           */
+  double b_l2_gbs;       /* measured read bandwidth, L2-resident buffer                   */
+  double t_csr_ms;       /* static-partition baseline, event time per launch              */
+  double t_ml_ms;        /* P_ML kernel (colind'[j] = row of j), per launch               */
+  double t_cmp_ms;       /* P_CMP kernel (x[i], no colind), per launch                    */
+  double t_median_ms;    /* lower median over SMs of each SM's span (first start to last
+                            end of its CTAs): the SM is the worker of the static partition */
+  double t_span_ms;      /* last CTA end - first CTA start                                */
+  double t_imb_ms;       /* t_median + launch overhead (t_csr - t_span, if positive)      */
+  int32_t n_ctas;        /* resident CTAs = workers of the static partition               */
+  int32_t vs;            /* sub-warp width of the profiling kernels                       */
+} spmv_profile_report;
+
 /* Section III-B profile: runs the static-partition baseline (P_CSR, per-CTA timers for
- * P_IMB), the P_ML kernel (colind'[j] = row of j) and the P_CMP kernel (x[i] only), and
- * computes P_MB, P_peak from byte counts and the measured B_max. p[6] host =
- * P_CSR, P_MB, P_ML, P_IMB, P_CMP, P_peak (GFLOP/s); b_max_gbs host. Synchronizes. */
-spmv_status spmv_profile(spmv_handle_t h, int32_t reps, double *p, double *b_max_gbs,
+ * P_IMB: P_IMB = 2 NNZ / t_imb), the P_ML kernel (colind'[j] = row of j) and the P_CMP
+ * kernel (x[i] only), and computes P_MB, P_peak from byte counts and the measured B_max
+ * (the L2-resident bandwidth when S_format + S_x + S_y fits in L2). reps = timed launches
+ * per kernel. out is a host pointer. Synchronizes. */
+spmv_status spmv_profile(spmv_handle_t h, int32_t reps, spmv_profile_report *out,
                          spmv_stream_t stream);
+
+/* One launch of the static-partition baseline with per-CTA timers: elapsed_ms[c] and
+ * sm_id[c] (host arrays of at least *n_ctas entries; pass NULL to query *n_ctas). CTAs
+ * whose row range is empty report elapsed 0. Synchronizes. */
+spmv_status spmv_profile_cta_times(spmv_handle_t h, double *elapsed_ms, int32_t *sm_id,
+                                   int32_t *n_ctas, spmv_stream_t stream);
 
 /* Runs one profiling kernel once into y (device, vec_type): which = 0 the static-partition
  * baseline, 1 the P_ML kernel, 2 the P_CMP kernel. For tests of their construction. */

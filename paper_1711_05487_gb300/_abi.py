@@ -61,6 +61,17 @@ class spmv_tune_report(ctypes.Structure):
                 ("t_autotune_ms", _D)]
 
 
+class spmv_profile_report(ctypes.Structure):
+    _fields_ = [("p", _D * 6), ("b_max_gbs", _D), ("b_hbm_gbs", _D), ("b_l2_gbs", _D),
+                ("t_csr_ms", _D), ("t_ml_ms", _D), ("t_cmp_ms", _D), ("t_median_ms", _D),
+                ("t_span_ms", _D), ("t_imb_ms", _D), ("n_ctas", _I32), ("vs", _I32)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "p"}
+        d["p"] = list(self.p)
+        return d
+
+
 _lib = None
 
 # name -> (restype, argtypes); status-returning entries raise on error
@@ -79,7 +90,8 @@ _DECL = {
     "spmv_get_delta16": (_I32, [_P, _P, _P, _P, ctypes.POINTER(_I64), _P]),
     "spmv_get_merge_path": (_I32, [_P, _P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P]),
     "spmv_features": (_I32, [_P, _I32, _P, _P, _P]),
-    "spmv_profile": (_I32, [_P, _I32, _P, _P, _P]),
+    "spmv_profile": (_I32, [_P, _I32, ctypes.POINTER(spmv_profile_report), _P]),
+    "spmv_profile_cta_times": (_I32, [_P, _P, _P, ctypes.POINTER(_I32), _P]),
     "spmv_profile_kernel": (_I32, [_P, _I32, _P, _P, _P]),
     "spmv_probe_bandwidth": (_I32, [ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "spmv_classify": (_U32, [_P, _D, _D, _D]),
@@ -206,10 +218,16 @@ def spmv_features(h, line_bytes, features_host, isum_host=None, stream=0):
     _call("spmv_features", h, line_bytes, features_host, isum_host, stream)
 
 
-def spmv_profile(h, reps, p_host, bmax=None, stream=0):
-    b = _D()
-    _call("spmv_profile", h, reps, p_host, ctypes.byref(b), stream)
-    return b.value
+def spmv_profile(h, reps, stream=0) -> spmv_profile_report:
+    r = spmv_profile_report()
+    _call("spmv_profile", h, reps, ctypes.byref(r), stream)
+    return r
+
+
+def spmv_profile_cta_times(h, elapsed_host=None, smid_host=None, n=0, stream=0) -> int:
+    c = _I32(n)
+    _call("spmv_profile_cta_times", h, elapsed_host, smid_host, ctypes.byref(c), stream)
+    return c.value
 
 
 def spmv_profile_kernel(h, which, x, y, stream=0):

@@ -175,10 +175,19 @@ class SpmvMatrix:
         _abi.spmv_features(self._h, line_bytes, f.ctypes.data, isum.ctypes.data, _stream(stream))
         return f, isum
 
-    def profile(self, reps=20, stream=None):
-        p = np.zeros(6)
-        b = _abi.spmv_profile(self._h, reps, p.ctypes.data, None, _stream(stream))
-        return p, b
+    def profile(self, reps=20, stream=None) -> dict:
+        """Section III-B profile: P-vector, bandwidths and the timings behind them."""
+        r = _abi.spmv_profile(self._h, reps, _stream(stream)).as_dict()
+        r["p"] = dict(zip(P_NAMES, r["p"]))
+        return r
+
+    def profile_cta_times(self, stream=None):
+        """Per-CTA elapsed ms and SM id of one static-partition baseline launch."""
+        n = _abi.spmv_profile_cta_times(self._h, None, None, 0, _stream(stream))
+        el = np.zeros(n)
+        sm = np.zeros(n, dtype=np.int32)
+        _abi.spmv_profile_cta_times(self._h, el.ctypes.data, sm.ctypes.data, n, _stream(stream))
+        return el, sm
 
     def profile_kernel(self, which: int, x: torch.Tensor, y: torch.Tensor, stream=None):
         _abi.spmv_profile_kernel(self._h, which, x.data_ptr(), y.data_ptr(), _stream(stream))

@@ -437,65 +437,124 @@ void compute_features(spmv_matrix *h, int line_bytes, double *out, uint64_t *isu
 }
 
 // ------------------------------------------------------------------ profiling --------
-struct ProfileOut {
-  double p[6];
-  double b_max;
+// The static-partition profiling setup shared by the profile route and its diagnostics:
+// a resident grid of n_ctas CTAs over nnz-balanced contiguous row ranges (rows never
+// split), the paper's baseline partitioning (Section IV-A) with one CTA per worker.
+struct StaticSetup {
+  DevBuf part, t0, t1, smid;
+  ProfileArgs pa;
 };
 
-void run_profile(spmv_matrix *h, int reps, ProfileOut &o, cudaStream_t s) {
+void static_setup(spmv_matrix *h, StaticSetup &st, const void *x, void *y, cudaStream_t s) {
   const KernelSet *ks = set_for(h);
   DeviceInfo &d = device_info(h->device);
-  double b_hbm = 0, b_l2 = 0;
-  probe_bandwidth(h->device, &b_hbm, &b_l2);
   const int n_ctas = std::max(1, d.sms * ks->profile_blocks_per_sm);
-  DevBuf part, x, y, t0, t1, colp;
-  part.alloc(sizeof(int32_t) * (size_t)(n_ctas + 1), 4, s);
-  CK(launch_static_partition(h->n_rows, h->nnz, h->rowptr.as<int32_t>(), n_ctas, part.as<int32_t>(), s));
-  const size_t vb = dtype_bytes(h->vec);
-  x.alloc(vb * (size_t)std::max<int64_t>(h->n_cols, 1), vb, s);
-  y.alloc(vb * (size_t)std::max<int64_t>(h->n_rows, 1), vb, s);
-  CK(launch_fill_const(x.p, h->vec, h->n_cols, 1.0, s));
-  t0.alloc(8 * (size_t)n_ctas, 8, s, true);
-  t1.alloc(8 * (size_t)n_ctas, 8, s, true);
-  colp.alloc(sizeof(int32_t) * (size_t)h->nnz, 4, s);
-  CK(launch_fill_row_index(h->n_rows, h->n_cols, h->rowptr.as<int32_t>(), colp.as<int32_t>(), s));
-  ProfileArgs pa;
+  st.part.alloc(sizeof(int32_t) * (size_t)(n_ctas + 1), 4, s);
+  CK(launch_static_partition(h->n_rows, h->nnz, h->rowptr.as<int32_t>(), n_ctas,
+                             st.part.as<int32_t>(), s));
+  st.t0.alloc(8 * (size_t)n_ctas, 8, s, true);
+  st.t1.alloc(8 * (size_t)n_ctas, 8, s, true);
+  st.smid.alloc(4 * (size_t)n_ctas, 4, s, true);
+  ProfileArgs &pa = st.pa;
   pa.n_rows = h->n_rows;
   pa.n_cols = h->n_cols;
-  pa.part = part.as<int32_t>();
+  pa.part = st.part.as<int32_t>();
   pa.n_ctas = n_ctas;
   pa.rowptr = h->rowptr.as<int32_t>();
   pa.colind = h->colind.as<int32_t>();
   pa.val = h->val_ptr();
-  pa.x = x.p;
-  pa.y = y.p;
-  pa.t_start = t0.as<unsigned long long>();
-  pa.t_end = t1.as<unsigned long long>();
+  pa.x = x;
+  pa.y = y;
+  pa.t_start = st.t0.as<unsigned long long>();
+  pa.t_end = st.t1.as<unsigned long long>();
+  pa.smid = st.smid.as<int32_t>();
   pa.vs = heuristic_vs(h->nnz_avg(), 1);
-  const double flops = 2.0 * (double)h->nnz;
-  // P_CSR and the per-CTA times of the last timed launch (P_IMB)
   pa.cmp_mode = 0;
-  const float t_csr = time_launches([&]() { return ks->profile(pa, s); }, reps, s);
-  std::vector<unsigned long long> ts((size_t)n_ctas), te((size_t)n_ctas);
-  std::vector<int32_t> hp((size_t)n_ctas + 1);
-  CK(cudaMemcpyAsync(ts.data(), t0.p, 8 * (size_t)n_ctas, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(te.data(), t1.p, 8 * (size_t)n_ctas, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(hp.data(), part.p, 4 * ((size_t)n_ctas + 1), cudaMemcpyDeviceToHost, s));
+}
+
+// Per-CTA elapsed times (ms) of the last launch; CTAs with an empty row range get -1.
+void read_cta_times(const StaticSetup &st, std::vector<double> &el, std::vector<int32_t> &sm,
+                    double *span_ms, cudaStream_t s) {
+  const int n = st.pa.n_ctas;
+  std::vector<unsigned long long> ts((size_t)n), te((size_t)n);
+  std::vector<int32_t> hp((size_t)n + 1);
+  sm.assign((size_t)n, 0);
+  CK(cudaMemcpyAsync(ts.data(), st.t0.p, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(te.data(), st.t1.p, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(sm.data(), st.smid.p, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hp.data(), st.part.p, 4 * ((size_t)n + 1), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  std::vector<double> el;
+  el.assign((size_t)n, -1.0);
   unsigned long long tmin = ~0ull, tmax = 0;
-  for (int c = 0; c < n_ctas; ++c) {
-    if (hp[(size_t)c + 1] <= hp[(size_t)c]) continue;   // CTAs without rows did no work
-    el.push_back((double)(te[(size_t)c] - ts[(size_t)c]) * 1e-6);  // ms
+  for (int c = 0; c < n; ++c) {
+    if (hp[(size_t)c + 1] <= hp[(size_t)c]) continue;   // no rows: no work
+    el[(size_t)c] = (double)(te[(size_t)c] - ts[(size_t)c]) * 1e-6;
     tmin = std::min(tmin, ts[(size_t)c]);
     tmax = std::max(tmax, te[(size_t)c]);
   }
+  *span_ms = tmax >= tmin ? (double)(tmax - tmin) * 1e-6 : 0.0;
+}
+
+// Span (ms) of every SM that ran at least one CTA with rows: last end - first start.
+std::vector<double> sm_spans(const StaticSetup &st, cudaStream_t s, double *global_span_ms) {
+  const int n = st.pa.n_ctas;
+  std::vector<unsigned long long> ts((size_t)n), te((size_t)n);
+  std::vector<int32_t> hp((size_t)n + 1), sm((size_t)n);
+  CK(cudaMemcpyAsync(ts.data(), st.t0.p, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(te.data(), st.t1.p, 8 * (size_t)n, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(sm.data(), st.smid.p, 4 * (size_t)n, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(hp.data(), st.part.p, 4 * ((size_t)n + 1), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int max_sm = 0;
+  for (int c = 0; c < n; ++c) max_sm = std::max(max_sm, sm[(size_t)c]);
+  std::vector<unsigned long long> lo((size_t)max_sm + 1, ~0ull), hi((size_t)max_sm + 1, 0);
+  unsigned long long gmin = ~0ull, gmax = 0;
+  for (int c = 0; c < n; ++c) {
+    if (hp[(size_t)c + 1] <= hp[(size_t)c]) continue;
+    const size_t k = (size_t)sm[(size_t)c];
+    lo[k] = std::min(lo[k], ts[(size_t)c]);
+    hi[k] = std::max(hi[k], te[(size_t)c]);
+    gmin = std::min(gmin, ts[(size_t)c]);
+    gmax = std::max(gmax, te[(size_t)c]);
+  }
+  std::vector<double> spans;
+  for (size_t k = 0; k < lo.size(); ++k)
+    if (hi[k] >= lo[k] && lo[k] != ~0ull) spans.push_back((double)(hi[k] - lo[k]) * 1e-6);
+  *global_span_ms = gmax >= gmin && gmin != ~0ull ? (double)(gmax - gmin) * 1e-6 : 0.0;
+  return spans;
+}
+
+void run_profile(spmv_matrix *h, int reps, spmv_profile_report &o, cudaStream_t s) {
+  std::memset(&o, 0, sizeof o);
+  const KernelSet *ks = set_for(h);
+  DeviceInfo &d = device_info(h->device);
+  double b_hbm = 0, b_l2 = 0;
+  probe_bandwidth(h->device, &b_hbm, &b_l2);
+  const size_t vb = dtype_bytes(h->vec);
+  DevBuf x, y, colp;
+  x.alloc(vb * (size_t)std::max<int64_t>(h->n_cols, 1), vb, s);
+  y.alloc(vb * (size_t)std::max<int64_t>(h->n_rows, 1), vb, s);
+  CK(launch_fill_const(x.p, h->vec, h->n_cols, 1.0, s));
+  StaticSetup st;
+  static_setup(h, st, x.p, y.p, s);
+  colp.alloc(sizeof(int32_t) * (size_t)h->nnz, 4, s);
+  CK(launch_fill_row_index(h->n_rows, h->n_cols, h->rowptr.as<int32_t>(), colp.as<int32_t>(), s));
+  ProfileArgs pa = st.pa;
+  const double flops = 2.0 * (double)h->nnz;
+  // P_CSR, and the per-CTA times of the last timed launch (P_IMB)
+  const float t_csr = time_launches([&]() { return ks->profile(pa, s); }, reps, s);
+  // A worker of the paper's static partition is an SM: the CTAs resident on one SM share
+  // its pipes, so their individual times reflect the warp scheduler's fairness rather than
+  // the partition. Each SM's time is the span of its CTAs (first start to last end); the
+  // median is taken over SMs.
+  double t_span = 0.0;
+  std::vector<double> work = sm_spans(st, s, &t_span);
   double t_median = t_csr;
-  double t_span = t_csr;
-  if (!el.empty()) {
-    std::sort(el.begin(), el.end());
-    t_median = el[(el.size() - 1) / 2];             // lower median
-    t_span = (double)(tmax - tmin) * 1e-6;
+  if (!work.empty()) {
+    std::sort(work.begin(), work.end());
+    t_median = work[(work.size() - 1) / 2];           // lower median
+  } else {
+    t_span = t_csr;
   }
   // the median worker time plus the launch cost that no worker sees
   const double t_imb = t_median + std::max(0.0, (double)t_csr - t_span);
@@ -509,8 +568,8 @@ void run_profile(spmv_matrix *h, int reps, ProfileOut &o, cudaStream_t s) {
   double bo[3];
   bounds(h->n_rows, h->n_cols, h->nnz, 4, (int)dtype_bytes(h->storage), (int)vb, 1.0, bo);
   const double ws = bo[2];
-  o.b_max = ws <= (double)d.l2_bytes ? b_l2 : b_hbm;
-  bounds(h->n_rows, h->n_cols, h->nnz, 4, (int)dtype_bytes(h->storage), (int)vb, o.b_max, bo);
+  o.b_max_gbs = ws <= (double)d.l2_bytes ? b_l2 : b_hbm;
+  bounds(h->n_rows, h->n_cols, h->nnz, 4, (int)dtype_bytes(h->storage), (int)vb, o.b_max_gbs, bo);
   auto gf = [&](double ms) { return ms > 0 ? flops / (ms * 1e-3) / 1e9 : 0.0; };
   o.p[0] = gf(t_csr);
   o.p[1] = bo[0];
@@ -518,6 +577,16 @@ void run_profile(spmv_matrix *h, int reps, ProfileOut &o, cudaStream_t s) {
   o.p[3] = gf(t_imb);
   o.p[4] = gf(t_cmp);
   o.p[5] = bo[1];
+  o.b_hbm_gbs = b_hbm;
+  o.b_l2_gbs = b_l2;
+  o.t_csr_ms = t_csr;
+  o.t_ml_ms = t_ml;
+  o.t_cmp_ms = t_cmp;
+  o.t_median_ms = t_median;
+  o.t_span_ms = t_span;
+  o.t_imb_ms = t_imb;
+  o.n_ctas = st.pa.n_ctas;
+  o.vs = st.pa.vs;
 }
 
 // Sub-warp width sweep by timing (Section III-E "parameter tuning"; build addition).
@@ -761,10 +830,10 @@ spmv_status spmv_tune(spmv_handle_t h, spmv_mode mode, const spmv_tune_opts *opt
         }
       }
       if (!done) {
-        ProfileOut po;
+        spmv_profile_report po;
         run_profile(h, opts.reps, po, s);
         std::memcpy(rep.p, po.p, sizeof po.p);
-        rep.b_max_gbs = po.b_max;
+        rep.b_max_gbs = po.b_max_gbs;
         cls = classify(po.p, opts.t_imb, opts.t_ml, opts.t_mb);
         if (nnz_max < 0) {
           DevBuf mx;
@@ -903,14 +972,47 @@ spmv_status spmv_features(spmv_handle_t h, int32_t line_bytes, double *features,
   });
 }
 
-spmv_status spmv_profile(spmv_handle_t h, int32_t reps, double *p, double *b_max_gbs,
+spmv_status spmv_profile(spmv_handle_t h, int32_t reps, spmv_profile_report *out,
                          spmv_stream_t stream) {
-  if (!h || !p) return SPMV_ERR_ARG;
+  if (!h || !out) return SPMV_ERR_ARG;
   return guarded([&]() -> spmv_status {
-    ProfileOut o;
+    spmv_profile_report o;
     run_profile(h, reps > 0 ? reps : 20, o, static_cast<cudaStream_t>(stream));
-    std::memcpy(p, o.p, sizeof o.p);
-    if (b_max_gbs) *b_max_gbs = o.b_max;
+    *out = o;
+    return SPMV_OK;
+  });
+}
+
+spmv_status spmv_profile_cta_times(spmv_handle_t h, double *elapsed_ms, int32_t *sm_id,
+                                   int32_t *n_ctas, spmv_stream_t stream) {
+  if (!h || !n_ctas) return SPMV_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return guarded([&]() -> spmv_status {
+    const KernelSet *ks = set_for(h);
+    const int n = std::max(1, device_info(h->device).sms * ks->profile_blocks_per_sm);
+    if (!elapsed_ms && !sm_id) {
+      *n_ctas = n;
+      return SPMV_OK;
+    }
+    if (*n_ctas < n) return SPMV_ERR_ARG;
+    const size_t vb = dtype_bytes(h->vec);
+    DevBuf x, y;
+    x.alloc(vb * (size_t)std::max<int64_t>(h->n_cols, 1), vb, s);
+    y.alloc(vb * (size_t)std::max<int64_t>(h->n_rows, 1), vb, s);
+    CK(launch_fill_const(x.p, h->vec, h->n_cols, 1.0, s));
+    StaticSetup st;
+    static_setup(h, st, x.p, y.p, s);
+    for (int w = 0; w < 2; ++w) CK(ks->profile(st.pa, s));   // warm
+    CK(ks->profile(st.pa, s));
+    std::vector<double> el;
+    std::vector<int32_t> sm;
+    double span = 0;
+    read_cta_times(st, el, sm, &span, s);
+    for (int c = 0; c < n; ++c) {
+      if (elapsed_ms) elapsed_ms[c] = el[(size_t)c] < 0 ? 0.0 : el[(size_t)c];
+      if (sm_id) sm_id[c] = sm[(size_t)c];
+    }
+    *n_ctas = n;
     return SPMV_OK;
   });
 }
@@ -921,33 +1023,16 @@ spmv_status spmv_profile_kernel(spmv_handle_t h, int32_t which, const void *x, v
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return guarded([&]() -> spmv_status {
     const KernelSet *ks = set_for(h);
-    DeviceInfo &d = device_info(h->device);
-    const int n_ctas = std::max(1, d.sms * ks->profile_blocks_per_sm);
-    DevBuf part, t0, t1, colp;
-    part.alloc(sizeof(int32_t) * (size_t)(n_ctas + 1), 4, s);
-    CK(launch_static_partition(h->n_rows, h->nnz, h->rowptr.as<int32_t>(), n_ctas, part.as<int32_t>(), s));
-    t0.alloc(8 * (size_t)n_ctas, 8, s, true);
-    t1.alloc(8 * (size_t)n_ctas, 8, s, true);
-    ProfileArgs pa;
-    pa.n_rows = h->n_rows;
-    pa.n_cols = h->n_cols;
-    pa.part = part.as<int32_t>();
-    pa.n_ctas = n_ctas;
-    pa.rowptr = h->rowptr.as<int32_t>();
-    pa.colind = h->colind.as<int32_t>();
-    pa.val = h->val_ptr();
-    pa.x = x;
-    pa.y = y;
-    pa.t_start = t0.as<unsigned long long>();
-    pa.t_end = t1.as<unsigned long long>();
-    pa.vs = heuristic_vs(h->nnz_avg(), 1);
+    StaticSetup st;
+    static_setup(h, st, x, y, s);
+    DevBuf colp;
     if (which == 1) {
       colp.alloc(sizeof(int32_t) * (size_t)h->nnz, 4, s);
       CK(launch_fill_row_index(h->n_rows, h->n_cols, h->rowptr.as<int32_t>(), colp.as<int32_t>(), s));
-      pa.colind = colp.as<int32_t>();
+      st.pa.colind = colp.as<int32_t>();
     }
-    pa.cmp_mode = which == 2 ? 1 : 0;
-    CK(ks->profile(pa, s));
+    st.pa.cmp_mode = which == 2 ? 1 : 0;
+    CK(ks->profile(st.pa, s));
     CK(cudaStreamSynchronize(s));
     return SPMV_OK;
   });

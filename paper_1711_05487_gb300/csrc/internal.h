@@ -56,6 +56,7 @@ struct ProfileArgs {
   void *y = nullptr;
   unsigned long long *t_start = nullptr;
   unsigned long long *t_end = nullptr;
+  int32_t *smid = nullptr;            // SM that ran each CTA (may be null)
   int32_t cmp_mode = 0;              // 1: P_CMP kernel (x[i], no colind)
   int32_t vs = 8;
 };

@@ -191,25 +191,33 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile(const RunArgs a) {
     if (row >= r1) return;
     AccT acc = 0;
     const int o = s - a0, len = e - s;
+    // Column of element k: int32 from shared memory, or the running sum of 16-bit deltas
+    // from the row's base column, or (escape rows) the full column kept in global memory.
+    const int32_t *ec = nullptr;
+    int c = base;
     if constexpr (D16) {
-      if (base < 0) {
-        const int32_t *ec = a.esc + (-(int64_t)base - 1);
-#pragma unroll 4
-        for (int k = 0; k < len; ++k)
-          acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2>(x + __ldg(ec + k), pol_x), acc);
-      } else {
-        int c = base;
-#pragma unroll 4
-        for (int k = 0; k < len; ++k) {
-          c += (int)sidx[o + k];
-          acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2>(x + c, pol_x), acc);
-        }
-      }
-    } else {
-#pragma unroll 4
-      for (int k = 0; k < len; ++k)
-        acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2>(x + sidx[o + k], pol_x), acc);
+      if (base < 0) ec = a.esc + (-(int64_t)base - 1);
     }
+    auto column = [&](int k) -> int {
+      if constexpr (D16) {
+        if (ec) return __ldg(ec + k);
+        c += (int)sidx[o + k];
+        return c;
+      } else {
+        return (int)sidx[o + k];
+      }
+    };
+    // 8 gathers of x in flight per thread, then 8 FMAs: the exact trip count keeps the FP64
+    // pipe free of masked-off work (rows in a warp have different lengths).
+    int k = 0;
+    for (; k + 8 <= len; k += 8) {
+      AccT xv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) xv[q] = (AccT)ldx<XL2>(x + column(k + q), pol_x);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc = fma(widen<AccT>(sval[o + k + q]), xv[q], acc);
+    }
+    for (; k < len; ++k) acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2>(x + column(k), pol_x), acc);
     y[row] = (VecT)acc;
   } else {
     // oversize tile: a warp per row straight from global memory
@@ -386,6 +394,11 @@ __global__ void __launch_bounds__(kRowThreads) k_static(const ProfileArgs a) {
   if (threadIdx.x == 0) {
     a.t_start[blockIdx.x] = t0;
     a.t_end[blockIdx.x] = globaltimer_ns();
+    if (a.smid) {
+      uint32_t sm;
+      asm volatile("mov.u32 %0, %smid;" : "=r"(sm));
+      a.smid[blockIdx.x] = (int32_t)sm;
+    }
   }
 }
 
