@@ -44,7 +44,8 @@ typedef enum {
   SPMV_ERR_CUDA = 5,              /* a CUDA runtime call failed                         */
   SPMV_ERR_TIMEOUT = 6,           /* a bounded device-side wait gave up                 */
   SPMV_ERR_ARG = 7,               /* invalid argument (null pointer, size, k ...)       */
-  SPMV_ERR_NO_SELECTOR = 8        /* learned mode without a selector                    */
+  SPMV_ERR_NO_SELECTOR = 8,       /* learned mode without a selector                    */
+  SPMV_ERR_TOO_LARGE = 9          /* problem larger than a fixed-size buffer allows     */
 } spmv_status;
 
 typedef enum { SPMV_F64 = 0, SPMV_F32 = 1, SPMV_BF16 = 2 } spmv_dtype;
@@ -263,6 +264,34 @@ spmv_status spmv_get_last_device_error(spmv_handle_t h, int32_t *code);
 spmv_status spmv_get_device_bytes(spmv_handle_t h, int64_t *bytes);
 
 const char *spmv_status_string(spmv_status s);
+
+/* ----------------------------------------------------- allocation-free SpMV -------- */
+/* y = A x (FP64 values, x and y) with the merge-path variant, for callers that must not
+ * allocate device memory: for example an application whose own allocator owns the device
+ * memory budget and forbids libraries from allocating behind its back, code that runs while
+ * the device is nearly full, or latency-critical code that cannot afford cudaMalloc /
+ * cudaFree (which can synchronize the device). The paper has no counterpart; this is a
+ * property of the library, not of the method.
+ *
+ * The caller passes the CSR (row_ptr[n_rows+1], col_ind[nnz], val[nnz]), x[n_cols] and
+ * y[n_rows] as device pointers; the CSR is used as given (not validated: it must satisfy
+ * the CSR definition). The call allocates nothing: its scratch (merge-path tile table and
+ * per-tile carries) lives in one fixed 16 MiB array in device global memory, created when
+ * the library's kernels are loaded on a device and held by every GPU that loads them until
+ * the process exits. Sizes with n_rows + nnz above about 1.2e9 (599,158 tiles of 2048 merge
+ * items) are rejected with SPMV_ERR_TOO_LARGE before any work is queued.
+ *
+ * The first call on each device looks up the array's device address (a runtime call that
+ * may synchronize); make that first call before any stream capture. Asynchronous on
+ * stream otherwise. All calls share the one array and each call's scratch contents stay
+ * there until the next call overwrites them, so calls whose work overlaps on the GPU (on
+ * different streams, or from different host threads, without ordering between them) race
+ * and give wrong results; serialize them on one stream or with events. Errors:
+ * SPMV_ERR_ARG (negative or oversized int32 sizes, null pointers), SPMV_ERR_TOO_LARGE,
+ * SPMV_ERR_CUDA (launch failure). */
+spmv_status spmv_run_noalloc(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t *row_ptr,
+                             const int32_t *col_ind, const double *val, const double *x,
+                             double *y, spmv_stream_t stream);
 
 /* ------------------------------------------------------------- learned selector ---- */
 /* The MLP has layer sizes n_in -> h1 -> h2 -> 4 (ReLU hidden units, one logit per class

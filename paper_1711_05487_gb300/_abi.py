@@ -27,7 +27,8 @@ MLP_INPUTS = 12
 
 STATUS = {0: "SPMV_OK", 1: "SPMV_ERR_INVALID_CSR", 2: "SPMV_ERR_UNSUPPORTED_DTYPE",
           3: "SPMV_ERR_OOM", 4: "SPMV_ERR_NOT_TUNED", 5: "SPMV_ERR_CUDA",
-          6: "SPMV_ERR_TIMEOUT", 7: "SPMV_ERR_ARG", 8: "SPMV_ERR_NO_SELECTOR"}
+          6: "SPMV_ERR_TIMEOUT", 7: "SPMV_ERR_ARG", 8: "SPMV_ERR_NO_SELECTOR",
+          9: "SPMV_ERR_TOO_LARGE"}
 
 
 class SpmvError(RuntimeError):
@@ -115,6 +116,7 @@ _DECL = {
     "spmv_run_batched": (_I32, [_P, _P]),
     "spmv_run_batched_sequential": (_I32, [_P, _P]),
     "spmv_batch_destroy": (_I32, [_P]),
+    "spmv_run_noalloc": (_I32, [_I64, _I64, _I64, _P, _P, _P, _P, _P, _P]),
 }
 
 DECLARED = tuple(_DECL)
@@ -341,3 +343,8 @@ def spmv_run_batched_sequential(b, stream=0):
 
 def spmv_batch_destroy(b):
     _call("spmv_batch_destroy", b)
+
+
+def spmv_run_noalloc(n_rows, n_cols, nnz, row_ptr, col_ind, val, x, y, stream=0):
+    """y = A x (FP64) without any device allocation; see the header for the scratch limit."""
+    _call("spmv_run_noalloc", n_rows, n_cols, nnz, row_ptr, col_ind, val, x, y, stream)

@@ -665,6 +665,7 @@ const char *spmv_status_string(spmv_status s) {
     case SPMV_ERR_TIMEOUT: return "bounded device wait expired";
     case SPMV_ERR_ARG: return "invalid argument";
     case SPMV_ERR_NO_SELECTOR: return "learned mode needs a selector";
+    case SPMV_ERR_TOO_LARGE: return "problem larger than the fixed scratch buffer allows";
   }
   return "unknown status";
 }

@@ -47,7 +47,7 @@ def test_library_exports_every_declared_symbol(abi):
 
 
 def test_status_strings(abi):
-    for s in range(9):
+    for s in range(10):
         assert abi.spmv_status_string(s)
     assert "invalid argument" in abi.spmv_status_string(7)
 
