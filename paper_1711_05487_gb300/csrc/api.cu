@@ -133,6 +133,8 @@ struct spmv_matrix {
   bool tuned = false;
   int32_t tile_cap = 0;        // staged elements per tile of the thread-per-row kernel
   DevBuf d_err;                // device error word of bounded waits
+  DevBuf small;                // 256 bytes for single-value reductions (maxima, codes)
+  DevBuf feat_part, feat_fin;  // feature partial sums, kept between calls
   DevBuf x_stage, y_stage, scratch;
   int32_t last_error = 0;
   double nnz_avg() const { return n_rows ? (double)nnz / (double)n_rows : 0.0; }
@@ -143,6 +145,7 @@ struct spmv_selector {
   int device = 0;
   int32_t sizes[4] = {0, 0, 0, 0};
   DevBuf params, mu, inv_sigma;
+  DevBuf ws;                   // one sample: 16 features, inputs, hidden layers, logits
   bool has_norm = false;
 };
 
@@ -217,11 +220,9 @@ void build_merge(spmv_matrix *h, cudaStream_t s) {
 void compute_tile_cap(spmv_matrix *h, const spmv_variant &v, cudaStream_t s) {
   const int eb = (int)dtype_bytes(h->storage) + (v.index == 1 ? 2 : 4);
   const int limit = (((48 * 1024 - 16) / eb) / 8) * 8;
-  DevBuf mx;
-  mx.alloc(4, 4, s);
-  CK(launch_tile_max(h->n_rows, h->rowptr.as<int32_t>(), kTileRows, mx.as<int32_t>(), s));
+  CK(launch_tile_max(h->n_rows, h->rowptr.as<int32_t>(), kTileRows, h->small.as<int32_t>(), s));
   int32_t m = 0;
-  CK(cudaMemcpyAsync(&m, mx.p, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&m, h->small.p, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   h->tile_cap = std::min(m, limit);
 }
@@ -384,13 +385,14 @@ void compute_features(spmv_matrix *h, int line_bytes, double *out, uint64_t *isu
                       cudaStream_t s) {
   const int line_elems = std::max(1, line_bytes / (int)dtype_bytes(h->vec));
   const int nb = feature_blocks(h->n_rows);
-  DevBuf part, fin;
-  part.alloc(sizeof(FeatSums) * (size_t)nb, 8, s);
-  fin.alloc(sizeof(FeatSums), 8, s);
+  if (!h->feat_part.p) {
+    h->feat_part.alloc(sizeof(FeatSums) * (size_t)nb, 8, s);
+    h->feat_fin.alloc(sizeof(FeatSums), 8, s);
+  }
   CK(launch_features(h->n_rows, h->rowptr.as<int32_t>(), h->colind.as<int32_t>(), line_elems,
-                     part.as<FeatSums>(), nb, fin.as<FeatSums>(), s));
+                     h->feat_part.as<FeatSums>(), nb, h->feat_fin.as<FeatSums>(), s));
   FeatSums fs;
-  CK(cudaMemcpyAsync(&fs, fin.p, sizeof fs, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&fs, h->feat_fin.p, sizeof fs, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const int64_t n = h->n_rows;
   const u128 s_nnz = fs.s_nnz, s_nnz2 = ((u128)fs.s_nnz2_hi << 64) | fs.s_nnz2_lo;
@@ -705,6 +707,7 @@ spmv_status spmv_create(spmv_handle_t *out, int64_t n_rows, int64_t n_cols, int6
     default_types(val_type, &h->storage, &h->vec, &h->acc);
     const size_t eb = dtype_bytes(val_type);
     h->d_err.alloc(4, 4, s, true);
+    h->small.alloc(256, 4, s, true);
     h->rowptr.alloc(4 * (size_t)(n_rows + 1), 4, s);
     h->colind.alloc(4 * (size_t)nnz, 4, s);
     h->val_in.alloc(eb * (size_t)nnz, eb, s);
@@ -737,7 +740,8 @@ spmv_status spmv_destroy(spmv_handle_t h) {
   cudaDeviceSynchronize();
   for (DevBuf *b : {&h->rowptr, &h->colind, &h->val_in, &h->val_store, &h->dbase, &h->delta,
                     &h->esc, &h->coord, &h->tail_row, &h->tail_val, &h->head_val, &h->x_stage,
-                    &h->y_stage, &h->scratch, &h->d_err})
+                    &h->y_stage, &h->scratch, &h->d_err, &h->small, &h->feat_part,
+                    &h->feat_fin})
     b->release();
   delete h;
   return SPMV_OK;
@@ -837,11 +841,9 @@ spmv_status spmv_tune(spmv_handle_t h, spmv_mode mode, const spmv_tune_opts *opt
         rep.b_max_gbs = po.b_max_gbs;
         cls = classify(po.p, opts.t_imb, opts.t_ml, opts.t_mb);
         if (nnz_max < 0) {
-          DevBuf mx;
-          mx.alloc(4, 4, s);
-          CK(launch_row_len_max(h->n_rows, h->rowptr.as<int32_t>(), mx.as<int32_t>(), s));
+          CK(launch_row_len_max(h->n_rows, h->rowptr.as<int32_t>(), h->small.as<int32_t>(), s));
           int32_t m = 0;
-          CK(cudaMemcpyAsync(&m, mx.p, 4, cudaMemcpyDeviceToHost, s));
+          CK(cudaMemcpyAsync(&m, h->small.p, 4, cudaMemcpyDeviceToHost, s));
           CK(cudaStreamSynchronize(s));
           nnz_max = (double)m;
         }
@@ -1191,6 +1193,9 @@ spmv_status spmv_selector_create(spmv_selector_t *out, const int32_t *sizes, con
       CK(cudaMemcpy(sel->inv_sigma.p, inv_sigma, sizeof(float) * SPMV_MLP_INPUTS, cudaMemcpyHostToDevice));
       sel->has_norm = true;
     }
+    // per-call workspace: 16 doubles of features, then inputs, hidden layers and logits
+    const int64_t wf = SPMV_MLP_INPUTS + mlp_logits_work_floats(sizes, 1) + sizes[3];
+    sel->ws.alloc(sizeof(double) * 16 + sizeof(float) * (size_t)wf, 8, 0, true);
     CK(cudaDeviceSynchronize());
     return SPMV_OK;
   });
@@ -1208,6 +1213,7 @@ spmv_status spmv_selector_destroy(spmv_selector_t sel) {
   sel->params.release();
   sel->mu.release();
   sel->inv_sigma.release();
+  sel->ws.release();
   delete sel;
   return SPMV_OK;
 }
@@ -1217,23 +1223,23 @@ spmv_status spmv_selector_predict(spmv_selector_t sel, const double *feat16, uin
   if (!sel || !feat16 || !classes) return SPMV_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return guarded([&]() -> spmv_status {
-    DevBuf f, x, lg;
-    f.alloc(sizeof(double) * 16, 8, s);
-    x.alloc(sizeof(float) * SPMV_MLP_INPUTS, 4, s);
     const int n3 = sel->sizes[3];
-    lg.alloc(sizeof(float) * (size_t)n3, 4, s);
-    CK(cudaMemcpyAsync(f.p, feat16, sizeof(double) * 16, cudaMemcpyHostToDevice, s));
-    CK(launch_mlp_inputs(f.as<double>(), 1, sel->has_norm ? sel->mu.as<float>() : nullptr,
-                         sel->has_norm ? sel->inv_sigma.as<float>() : nullptr, x.as<float>(), s));
-    CK(launch_mlp_logits(sel->sizes, sel->params.as<float>(), 1, x.as<float>(), lg.as<float>(), s));
-    std::vector<float> h((size_t)n3);
-    CK(cudaMemcpyAsync(h.data(), lg.p, sizeof(float) * (size_t)n3, cudaMemcpyDeviceToHost, s));
+    double *f = sel->ws.as<double>();
+    float *x = reinterpret_cast<float *>(f + 16);
+    float *hid = x + SPMV_MLP_INPUTS;
+    float *lg = hid + mlp_logits_work_floats(sel->sizes, 1);
+    CK(cudaMemcpyAsync(f, feat16, sizeof(double) * 16, cudaMemcpyHostToDevice, s));
+    CK(launch_mlp_inputs(f, 1, sel->has_norm ? sel->mu.as<float>() : nullptr,
+                         sel->has_norm ? sel->inv_sigma.as<float>() : nullptr, x, s));
+    CK(launch_mlp_logits_ws(sel->sizes, sel->params.as<float>(), 1, x, lg, hid, s));
+    float h[64];
+    CK(cudaMemcpyAsync(h, lg, sizeof(float) * (size_t)std::min(n3, 64), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     uint32_t c = 0;
     double mg = 1e300;
     for (int o = 0; o < n3 && o < 4; ++o) {
-      if (h[(size_t)o] > 0.0f) c |= (1u << o);
-      mg = std::min(mg, (double)std::fabs(h[(size_t)o]));
+      if (h[o] > 0.0f) c |= (1u << o);
+      mg = std::min(mg, (double)std::fabs(h[o]));
     }
     *classes = c;
     if (margin) *margin = mg;

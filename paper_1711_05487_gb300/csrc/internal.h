@@ -173,6 +173,9 @@ cudaError_t launch_mlp_loss_grad(const int32_t *sizes, const float *params, int6
                                  const float *X, const float *Y, float *grad, float *loss,
                                  float *work, cudaStream_t s);
 int64_t mlp_work_floats(const int32_t *sizes, int64_t batch);
+int64_t mlp_logits_work_floats(const int32_t *sizes, int64_t batch);
+cudaError_t launch_mlp_logits_ws(const int32_t *sizes, const float *params, int64_t batch,
+                                 const float *X, float *logits, float *work, cudaStream_t s);
 int64_t mlp_param_count(const int32_t *sizes);
 cudaError_t launch_adam(int64_t n, float *p, const float *g, float *m, float *v, float lr,
                         float b1, float b2, float eps, int32_t t, cudaStream_t s);

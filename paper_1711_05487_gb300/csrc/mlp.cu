@@ -167,22 +167,32 @@ __global__ void k_loss_reduce(const double *term, int64_t batch, int n3, float *
   *loss = (float)(acc / ((double)batch * (double)n3));
 }
 
-cudaError_t launch_mlp_logits(const int32_t *sizes, const float *params, int64_t batch,
-                              const float *X, float *logits, cudaStream_t s) {
-  // inference uses a small work area carved from the logits' neighbour: allocate locally
+int64_t mlp_logits_work_floats(const int32_t *sizes, int64_t batch) {
   const Layout L = layout(sizes);
-  float *h1 = nullptr, *h2 = nullptr;
-  cudaError_t e = cudaMallocAsync(&h1, sizeof(float) * (size_t)(batch * L.n1 + batch * L.n2), s);
-  if (e != cudaSuccess) return e;
-  h2 = h1 + batch * L.n1;
+  return batch * ((int64_t)L.n1 + L.n2);
+}
+
+// work: mlp_logits_work_floats(sizes, batch) floats of device memory for the hidden layers.
+cudaError_t launch_mlp_logits_ws(const int32_t *sizes, const float *params, int64_t batch,
+                                 const float *X, float *logits, float *work, cudaStream_t s) {
+  const Layout L = layout(sizes);
+  float *h1 = work, *h2 = work + batch * L.n1;
   k_dense_fwd<<<nblk(batch * L.n1), kT, 0, s>>>(X, batch, L.n0, params + L.w1, params + L.b1,
                                                 L.n1, 1, h1);
   k_dense_fwd<<<nblk(batch * L.n2), kT, 0, s>>>(h1, batch, L.n1, params + L.w2, params + L.b2,
                                                 L.n2, 1, h2);
   k_dense_fwd<<<nblk(batch * L.n3), kT, 0, s>>>(h2, batch, L.n2, params + L.w3, params + L.b3,
                                                 L.n3, 0, logits);
-  e = cudaGetLastError();
-  cudaFreeAsync(h1, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_logits(const int32_t *sizes, const float *params, int64_t batch,
+                              const float *X, float *logits, cudaStream_t s) {
+  float *work = nullptr;
+  cudaError_t e = cudaMallocAsync(&work, sizeof(float) * (size_t)mlp_logits_work_floats(sizes, batch), s);
+  if (e != cudaSuccess) return e;
+  e = launch_mlp_logits_ws(sizes, params, batch, X, logits, work, s);
+  cudaFreeAsync(work, s);
   return e;
 }
 

@@ -304,10 +304,12 @@ def mixed_spec(index: int, seed: int = SEED_BASE + 40, n_lo: int = 10_000,
             side = max(3, int(round(n ** (1 / 3))))
             spec.update(kind="st27", side=side)
     elif fam == "powerlaw":
-        spec.update(n=n, alpha=float(rng.uniform(1.6, 2.6)))
+        spec.update(n=n, alpha=float(rng.uniform(1.6, 2.6)), clip=min(n, 20_000))
     elif fam == "banded":
-        hb = int(round(math.exp(rng.uniform(0.0, math.log(max(2.0, n / 10))))))
-        spec.update(n=n, half_bw=max(1, hb), density=float(rng.uniform(0.05, 1.0)))
+        hb = max(1, int(round(math.exp(rng.uniform(0.0, math.log(max(2.0, n / 10)))))))
+        # density per band U(0.05, 1), capped so that a row holds about 64 nonzeros at most
+        dens = min(float(rng.uniform(0.05, 1.0)), 64.0 / (2 * hb + 1))
+        spec.update(n=n, half_bw=hb, density=dens)
     else:
         spec.update(n=n, max_per_row=int(rng.integers(1, 65)))
     return spec
@@ -324,7 +326,8 @@ def make_from_spec(spec: dict, dtype=np.float64) -> Csr:
         else:
             m = stencil_27pt(spec["side"], seed)
     elif fam == "powerlaw":
-        m = power_law(spec["n"], spec["alpha"], clip=spec["n"], seed=seed, dtype=np.float64)
+        m = power_law(spec["n"], spec["alpha"], clip=spec.get("clip", spec["n"]), seed=seed,
+                      dtype=np.float64)
     elif fam == "banded":
         m = banded(spec["n"], spec["half_bw"], spec["density"], seed)
     else:
