@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 8000.0
 
@@ -114,6 +115,20 @@ WORKLOADS = {
 }
 
 
+def measured_traffic(workload: str, variant) -> dict | None:
+    """DRAM bytes per launch of the dominant kernel from an ncu capture (profiles/), valid only
+    for the same variant and the same library sources."""
+    try:
+        from paper_1711_05487_gb300.buildlib import source_digest
+        with open(TRAFFIC) as fh:
+            t = json.load(fh).get(workload)
+        if t and list(t["variant"]) == list(variant) and t["source_digest"] == source_digest():
+            return t
+    except Exception:
+        return None
+    return None
+
+
 def dtype_bytes(code):
     return {0: 8, 1: 4, 2: 2}[code]
 
@@ -178,7 +193,13 @@ def run_ours(args, rank, world):
     A.set_variant(stream=stream)
     base_ms = timed(args.steps, args.warmup)
     # adaptive: profile-guided classification + Table II variant + autotuned width
-    rep = A.tune("profile", stream=stream)
+    # (--fixed-variant installs a given variant instead, so that a run under a profiler, whose
+    # inflated timings would steer the tuner elsewhere, executes the kernel a plain run picks)
+    if args.fixed_variant:
+        knobs = [int(v) for v in args.fixed_variant.split(",")]
+        rep = A.tune("fixed", stream=stream, fixed=api.variant(*knobs))
+    else:
+        rep = A.tune("profile", stream=stream)
     peak, peak_kind = _peaks()
     clocks = ClockSampler(dev)
     clocks.start()
@@ -193,6 +214,7 @@ def run_ours(args, rank, world):
     ms = timed(args.steps, args.warmup, tag="bench_timed")
     clocks.stop()
     storage = A.storage
+    traffic = measured_traffic(args.workload, rep.variant)
     ab = alg_bytes(m.n_rows, m.n_cols, m.nnz, rep.variant, storage, A.vec)
     achieved = ab / (ms * 1e-3) / 1e9
     csr_bytes = alg_bytes(m.n_rows, m.n_cols, m.nnz, (0, 0, 0, 0, 0), storage, A.vec)
@@ -264,7 +286,9 @@ def run_ours(args, rank, world):
                  "p_gflops": {k: round(v, 1) for k, v in rep.p.items()},
                  "b_max_gbs": round(rep.b_max_gbs, 1), "t_pre_ms": round(rep.t_pre_ms, 2)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                     "traffic_source": traffic["source"] if traffic else None,
                      "peak_kind": peak_kind, "alg_bytes": ab,
                      "frac_of_nominal_8tbs": round(achieved / NOMINAL_HBM_GBS, 4),
                      "csr_fp64_bytes_frac": round(csr_bytes / (ms * 1e-3) / 1e9 / peak, 4)},
@@ -342,6 +366,9 @@ def main():
     ap.add_argument("--workload", choices=list(WORKLOADS), default="stencil27_160")
     ap.add_argument("--quick", action="store_true", help="skip the precision variants")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fixed-variant", default=None,
+                    help="install this variant instead of tuning: partition,index,xpath,vec,"
+                         "vs,tile_rows,tile_pipe")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     world = int(os.environ.get("WORLD_SIZE", "1"))

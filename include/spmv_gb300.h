@@ -71,6 +71,9 @@ typedef struct {
   int32_t vec;       /* 0: scalar loads; 1: 128-bit loads of val/colind, unrolled (MB/CMP) */
   int32_t vs;        /* sub-warp width for partition 0: 1 (thread per row over a tile
                         staged in shared memory by bulk copies), 2,4,8,16,32; 0 = heuristic */
+  int32_t tile_rows; /* width 1: rows per staged tile, 32 / 64 / 128; 0 = automatic       */
+  int32_t tile_pipe; /* width 1: 0 = one tile per CTA, 1 = persistent CTAs keeping the next
+                        tile's bulk copy in flight (two shared-memory stages)               */
 } spmv_variant;
 
 #define SPMV_NUM_FEATURES 14
@@ -87,6 +90,7 @@ typedef struct {
   spmv_variant fixed;    /* SPMV_TUNE_FIXED only                                         */
   spmv_selector_t selector; /* SPMV_TUNE_LEARNED only                                    */
   double min_margin;     /* learned: smallest |logit| accepted, else profile (default 0) */
+  int32_t second_pass;   /* profile: re-profile after the CMP optimization (default 1)   */
 } spmv_tune_opts;
 
 typedef struct {
@@ -94,13 +98,14 @@ typedef struct {
   int32_t mode_used;     /* route that decided (LEARNED may fall back to PROFILE)        */
   spmv_variant variant;  /* variant installed on the handle                              */
   double p[6];           /* P_CSR, P_MB, P_ML, P_IMB, P_CMP, P_peak in GFLOP/s (profile) */
+  double p2[2];          /* second pass: P_CSR', P_ML' of the CMP-optimized kernel (0 if none) */
   double b_max_gbs;      /* bandwidth used for P_MB / P_peak                             */
   double features[SPMV_NUM_FEATURES];
   double margin;         /* learned: smallest |logit| of the MLP decision                */
   double t_pre_ms;       /* whole spmv_tune wall time                                    */
   double t_classify_ms;  /* probes or features (+ inference)                             */
   double t_prep_ms;      /* format conversion / partitioning                             */
-  double t_autotune_ms;  /* sub-warp width sweep                                         */
+  double t_autotune_ms;  /* sub-warp width and tile geometry sweep                       */
 } spmv_tune_report;
 
 /* ---------------------------------------------------------------- matrix handles ---- */
@@ -200,6 +205,9 @@ typedef struct {
   double t_imb_ms;       /* t_median + launch overhead (t_csr - t_span, if positive)      */
   int32_t n_ctas;        /* resident CTAs = workers of the static partition               */
   int32_t vs;            /* sub-warp width of the profiling kernels                       */
+  double p2[2];          /* second pass with the CMP-optimized kernel (thread per row over
+                            shared-memory tiles) as baseline: P_CSR', and P_ML' of the same
+                            kernel on colind'                                             */
 } spmv_profile_report;
 
 /* Section III-B profile: runs the static-partition baseline (P_CSR, per-CTA timers for
@@ -228,6 +236,13 @@ spmv_status spmv_probe_bandwidth(double *hbm_gbs, double *l2_gbs);
 
 /* Fig. 3 on a P-vector (csr, mb, ml, imb, cmp, peak); pure function. */
 uint32_t spmv_classify(const double *p, double t_imb, double t_ml, double t_mb);
+
+/* Fig. 3 followed by the second pass (a GB300 reading of Section III-C): when CMP is
+ * detected and p2 (P_CSR', P_ML' of the CMP-optimized kernel) is given, ML is added if
+ * P_ML' / P_CSR' > t_ml and MB if P_CSR' / P_MB >= t_mb. p2 may be NULL (= spmv_classify).
+ * Pure function. */
+uint32_t spmv_classify2(const double *p, const double *p2, double t_imb, double t_ml,
+                        double t_mb);
 
 /* Table II (jointly applied) for a class set; vs is left 0 (heuristic). Pure function. */
 void spmv_variant_for_classes(uint32_t classes, double nnz_avg, double nnz_max,

@@ -87,6 +87,8 @@ def _declare(L):
     L.oracle_select_bmax.restype = _D
     L.oracle_classify.argtypes = [_P, _D, _D, _D]
     L.oracle_classify.restype = ctypes.c_uint32
+    L.oracle_classify2.argtypes = [_P, _P, _D, _D, _D]
+    L.oracle_classify2.restype = ctypes.c_uint32
     L.oracle_variant_for_classes.argtypes = [ctypes.c_uint32, _D, _D, _D, _P]
     L.oracle_variant_for_classes.restype = None
     L.oracle_amortization_iters.argtypes = [_D, _D, _D]
@@ -228,6 +230,12 @@ def select_bmax(ws_bytes, llc_bytes, b_main, b_llc) -> float:
 def classify(p_csr, p_mb, p_ml, p_imb, p_cmp, p_peak, t_imb=1.24, t_ml=1.25, t_mb=0.75):
     p = np.array([p_csr, p_mb, p_ml, p_imb, p_cmp, p_peak], dtype=np.float64)
     return int(lib().oracle_classify(_p(p), t_imb, t_ml, t_mb))
+
+
+def classify2(p6, p2=None, t_imb=1.24, t_ml=1.25, t_mb=0.75):
+    p = np.ascontiguousarray(p6, dtype=np.float64)
+    q = None if p2 is None else np.ascontiguousarray(p2, dtype=np.float64)
+    return int(lib().oracle_classify2(_p(p), None if q is None else _p(q), t_imb, t_ml, t_mb))
 
 
 def variant_for_classes(cls, nnz_avg, nnz_max, long_ratio=32.0):

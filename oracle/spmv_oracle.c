@@ -383,6 +383,21 @@ uint32_t oracle_classify(const double *p /* csr, mb, ml, imb, cmp, peak */, doub
   return cls;
 }
 
+/* Second profiling pass, this build's GB300 reading of Section III-C: a compute-bound
+ * baseline (CMP) hides the memory bottlenecks, so after the CMP optimization the profile is
+ * repeated with the optimized kernel as the baseline, p2 = (P_CSR', P_ML'): ML joins the
+ * class set when P_ML' / P_CSR' > t_ml and MB when P_CSR' / P_MB >= t_mb. Without p2, or
+ * when pass one found no CMP, the result is Fig. 3's.                                   */
+uint32_t oracle_classify2(const double *p, const double *p2, double t_imb, double t_ml,
+                          double t_mb) {
+  uint32_t cls = oracle_classify(p, t_imb, t_ml, t_mb);
+  if (p2 != NULL && (cls & 8u) && p2[0] > 0.0) {
+    if (p2[1] / p2[0] > t_ml) cls |= 2u;
+    if (p2[0] / p[1] >= t_mb) cls |= 1u;
+  }
+  return cls;
+}
+
 /* Table II: class -> optimization, applied jointly when several classes are detected.
  * Knobs returned in out[0..3]:
  *   out[0] partition: 0 = one sub-warp per row (rows dealt to CTAs by the hardware

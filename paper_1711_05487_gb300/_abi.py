@@ -39,25 +39,28 @@ class SpmvError(RuntimeError):
 
 class spmv_variant(ctypes.Structure):
     _fields_ = [("partition", _I32), ("index", _I32), ("xpath", _I32), ("vec", _I32),
-                ("vs", _I32)]
+                ("vs", _I32), ("tile_rows", _I32), ("tile_pipe", _I32)]
 
     def as_tuple(self):
-        return (self.partition, self.index, self.xpath, self.vec, self.vs)
+        return (self.partition, self.index, self.xpath, self.vec, self.vs, self.tile_rows,
+                self.tile_pipe)
 
     def __repr__(self):
         return (f"spmv_variant(partition={self.partition}, index={self.index}, "
-                f"xpath={self.xpath}, vec={self.vec}, vs={self.vs})")
+                f"xpath={self.xpath}, vec={self.vec}, vs={self.vs}, "
+                f"tile_rows={self.tile_rows}, tile_pipe={self.tile_pipe})")
 
 
 class spmv_tune_opts(ctypes.Structure):
     _fields_ = [("t_imb", _D), ("t_ml", _D), ("t_mb", _D), ("long_row_ratio", _D),
                 ("autotune", _I32), ("reps", _I32), ("fixed", spmv_variant),
-                ("selector", _P), ("min_margin", _D)]
+                ("selector", _P), ("min_margin", _D), ("second_pass", _I32)]
 
 
 class spmv_tune_report(ctypes.Structure):
     _fields_ = [("classes", _U32), ("mode_used", _I32), ("variant", spmv_variant),
-                ("p", _D * 6), ("b_max_gbs", _D), ("features", _D * NUM_FEATURES),
+                ("p", _D * 6), ("p2", _D * 2), ("b_max_gbs", _D),
+                ("features", _D * NUM_FEATURES),
                 ("margin", _D), ("t_pre_ms", _D), ("t_classify_ms", _D), ("t_prep_ms", _D),
                 ("t_autotune_ms", _D)]
 
@@ -65,11 +68,13 @@ class spmv_tune_report(ctypes.Structure):
 class spmv_profile_report(ctypes.Structure):
     _fields_ = [("p", _D * 6), ("b_max_gbs", _D), ("b_hbm_gbs", _D), ("b_l2_gbs", _D),
                 ("t_csr_ms", _D), ("t_ml_ms", _D), ("t_cmp_ms", _D), ("t_median_ms", _D),
-                ("t_span_ms", _D), ("t_imb_ms", _D), ("n_ctas", _I32), ("vs", _I32)]
+                ("t_span_ms", _D), ("t_imb_ms", _D), ("n_ctas", _I32), ("vs", _I32),
+                ("p2", _D * 2)]
 
     def as_dict(self):
-        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "p"}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("p", "p2")}
         d["p"] = list(self.p)
+        d["p2"] = list(self.p2)
         return d
 
 
@@ -96,6 +101,7 @@ _DECL = {
     "spmv_profile_kernel": (_I32, [_P, _I32, _P, _P, _P]),
     "spmv_probe_bandwidth": (_I32, [ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "spmv_classify": (_U32, [_P, _D, _D, _D]),
+    "spmv_classify2": (_U32, [_P, _P, _D, _D, _D]),
     "spmv_variant_for_classes": (None, [_U32, _D, _D, _D, ctypes.POINTER(spmv_variant)]),
     "spmv_bounds": (None, [_I64, _I64, _I64, _I32, _I32, _I32, _D, _P]),
     "spmv_feature_rules": (_U32, [_P, _I64, _I32, _I64, _D]),
@@ -244,6 +250,10 @@ def spmv_probe_bandwidth():
 
 def spmv_classify(p_host, t_imb=1.24, t_ml=1.25, t_mb=0.75) -> int:
     return int(lib().spmv_classify(p_host, t_imb, t_ml, t_mb))
+
+
+def spmv_classify2(p_host, p2_host=None, t_imb=1.24, t_ml=1.25, t_mb=0.75) -> int:
+    return int(lib().spmv_classify2(p_host, p2_host, t_imb, t_ml, t_mb))
 
 
 def spmv_variant_for_classes(classes, nnz_avg, nnz_max, long_row_ratio=32.0) -> spmv_variant:

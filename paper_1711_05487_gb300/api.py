@@ -39,11 +39,11 @@ def _stream(stream) -> int:
     return int(stream)
 
 
-def variant(partition=0, index=0, xpath=0, vec=0, vs=0) -> spmv_variant:
-    return spmv_variant(partition, index, xpath, vec, vs)
+def variant(partition=0, index=0, xpath=0, vec=0, vs=0, tile_rows=0, tile_pipe=0) -> spmv_variant:
+    return spmv_variant(partition, index, xpath, vec, vs, tile_rows, tile_pipe)
 
 
-BASELINE = dict(partition=0, index=0, xpath=0, vec=0, vs=0)
+BASELINE = dict(partition=0, index=0, xpath=0, vec=0, vs=0, tile_rows=0, tile_pipe=0)
 
 
 def _as_torch(a, dtype=None) -> torch.Tensor:
@@ -59,6 +59,7 @@ class TuneResult:
     mode_used: int
     variant: tuple
     p: dict
+    p2: list
     b_max_gbs: float
     features: dict
     margin: float
@@ -74,7 +75,7 @@ class TuneResult:
     @staticmethod
     def from_report(r: _abi.spmv_tune_report) -> "TuneResult":
         return TuneResult(int(r.classes), int(r.mode_used), r.variant.as_tuple(),
-                          dict(zip(P_NAMES, list(r.p))), float(r.b_max_gbs),
+                          dict(zip(P_NAMES, list(r.p))), list(r.p2), float(r.b_max_gbs),
                           dict(zip(FEATURE_NAMES, list(r.features))), float(r.margin),
                           float(r.t_pre_ms), float(r.t_classify_ms), float(r.t_prep_ms),
                           float(r.t_autotune_ms))

@@ -32,16 +32,30 @@ def _sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _digest() -> str:
+def _hash_files(files) -> str:
     h = hashlib.sha256()
-    files = _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + \
-        sorted(glob.glob(os.path.join(CSRC, "*.h"))) + \
-        [os.path.join(ROOT, "include", "spmv_gb300.h"), os.path.abspath(__file__)]
     for f in files:
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
+
+
+def _kernel_files() -> list[str]:
+    return _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + \
+        sorted(glob.glob(os.path.join(CSRC, "*.h"))) + \
+        [os.path.join(ROOT, "include", "spmv_gb300.h")]
+
+
+def _digest() -> str:
+    # the build stamp also covers this file (flags)
+    return _hash_files(_kernel_files() + [os.path.abspath(__file__)])
+
+
+def source_digest() -> str:
+    """SHA-256 of the library's CUDA/C++ sources and header: identifies the kernels a
+    measurement was taken on."""
+    return _hash_files(_kernel_files())
 
 
 def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:

@@ -132,6 +132,8 @@ struct spmv_matrix {
   spmv_variant variant{};
   bool tuned = false;
   int32_t tile_cap = 0;        // staged elements per tile of the thread-per-row kernel
+  int32_t tile_rows = kTileRows;  // rows per tile of the thread-per-row kernel
+  int32_t tile_pipe = 0;       // 1: persistent CTAs with two tiles in flight
   DevBuf d_err;                // device error word of bounded waits
   DevBuf small;                // 256 bytes for single-value reductions (maxima, codes)
   DevBuf feat_part, feat_fin;  // feature partial sums, kept between calls
@@ -172,6 +174,8 @@ RunArgs run_args(const spmv_matrix *h, const void *x, void *y) {
   a.tail_val = h->tail_val.as<double>();
   a.head_val = h->head_val.as<double>();
   a.tile_cap = h->tile_cap;
+  a.tile_rows = h->tile_rows;
+  a.tile_pipe = h->tile_pipe;
   a.err = h->d_err.as<int32_t>();
   return a;
 }
@@ -214,17 +218,45 @@ void build_merge(spmv_matrix *h, cudaStream_t s) {
   h->has_merge = true;
 }
 
-// Staged elements per tile of the thread-per-row kernel: the largest tile of the matrix,
-// capped so that a CTA's shared memory stays within 48 KB (tiles above the cap are
-// computed from global memory).
-void compute_tile_cap(spmv_matrix *h, const spmv_variant &v, cudaStream_t s) {
-  const int eb = (int)dtype_bytes(h->storage) + (v.index == 1 ? 2 : 4);
-  const int limit = (((48 * 1024 - 16) / eb) / 8) * 8;
-  CK(launch_tile_max(h->n_rows, h->rowptr.as<int32_t>(), kTileRows, h->small.as<int32_t>(), s));
+// Geometry of the thread-per-row kernel. A staged tile holds the values and columns of
+// `rows` consecutive rows; the staged capacity is the matrix's largest such tile, capped by
+// the shared-memory budget of one stage (48 KB for one tile per CTA, 56 KB per stage for
+// the persistent two-stage kernel). Tiles above the cap are computed from global memory.
+int32_t max_tile_elems(spmv_matrix *h, int rows, cudaStream_t s) {
+  CK(launch_tile_max(h->n_rows, h->rowptr.as<int32_t>(), rows, h->small.as<int32_t>(), s));
   int32_t m = 0;
   CK(cudaMemcpyAsync(&m, h->small.p, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  h->tile_cap = std::min(m, limit);
+  return m;
+}
+
+int32_t tile_limit(const spmv_matrix *h, const spmv_variant &v, bool pipe) {
+  const int eb = (int)dtype_bytes(h->storage) + (v.index == 1 ? 2 : 4);
+  const int budget = (pipe ? 56 : 48) * 1024 - 32;
+  return ((budget / eb) / 8) * 8;
+}
+
+void set_tile_geometry(spmv_matrix *h, const spmv_variant &v, int rows, bool pipe,
+                       cudaStream_t s) {
+  h->tile_rows = rows;
+  h->tile_pipe = pipe ? 1 : 0;
+  h->tile_cap = std::min(max_tile_elems(h, rows, s), tile_limit(h, v, pipe));
+}
+
+// Default geometry: the largest of 128, 64, 32 rows per tile whose largest tile fits one
+// 48 KB stage, one tile per CTA; 128-row tiles when none fits.
+void compute_tile_cap(spmv_matrix *h, const spmv_variant &v, cudaStream_t s) {
+  const int32_t limit = tile_limit(h, v, false);
+  for (int rows = kTileRows; rows >= 32; rows /= 2) {
+    const int32_t m = max_tile_elems(h, rows, s);
+    if (m <= limit) {
+      h->tile_rows = rows;
+      h->tile_pipe = 0;
+      h->tile_cap = m;
+      return;
+    }
+  }
+  set_tile_geometry(h, v, kTileRows, false, s);
 }
 
 void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
@@ -240,7 +272,19 @@ void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
       v.vs = (v.vec || v.index == 1) ? pool_vs(h->nnz_avg(), v.index == 1 ? 8 : 4)
                                      : heuristic_vs(h->nnz_avg(), 1);
     }
-    compute_tile_cap(h, v, s);
+    if (v.vs == 1 && v.tile_rows != 0) {
+      set_tile_geometry(h, v, v.tile_rows, v.tile_pipe != 0, s);
+    } else {
+      compute_tile_cap(h, v, s);
+      if (v.vs == 1) {
+        v.tile_rows = h->tile_rows;
+        v.tile_pipe = h->tile_pipe;
+      }
+    }
+    if (v.vs != 1) {
+      v.tile_rows = 0;
+      v.tile_pipe = 0;
+    }
   }
 }
 
@@ -252,6 +296,9 @@ bool valid_variant(const spmv_variant &v) {
   if (v.partition == 0 && v.vs != 0 && v.vs != 1 && v.vs != 2 && v.vs != 4 && v.vs != 8 &&
       v.vs != 16 && v.vs != 32)
     return false;
+  if (v.tile_rows != 0 && v.tile_rows != 32 && v.tile_rows != 64 && v.tile_rows != 128)
+    return false;
+  if (v.tile_pipe != 0 && v.tile_pipe != 1) return false;
   return true;
 }
 
@@ -342,6 +389,19 @@ uint32_t classify(const double *p, double t_imb, double t_ml, double t_mb) {
   if (p_ml / p_csr > t_ml) c |= SPMV_CLASS_ML;
   if (p_csr / p_mb >= t_mb && p_mb < p_cmp && p_cmp < p_peak) c |= SPMV_CLASS_MB;
   if (p_mb > p_cmp || p_cmp > p_peak) c |= SPMV_CLASS_CMP;
+  return c;
+}
+
+// Second profiling pass (GB300 reading of Section III-C): when the baseline is compute
+// bound (CMP), the compute bottleneck hides the memory ones. After the CMP optimization
+// (one FMA per nonzero) the profile is repeated with that kernel as the baseline:
+// p2 = {P_CSR', P_ML'}; ML if P_ML' / P_CSR' > t_ml, MB if P_CSR' / P_MB >= t_mb.
+uint32_t classify2(const double *p, const double *p2, double t_imb, double t_ml, double t_mb) {
+  uint32_t c = classify(p, t_imb, t_ml, t_mb);
+  if (p2 && (c & SPMV_CLASS_CMP) && p2[0] > 0.0) {
+    if (p2[1] / p2[0] > t_ml) c |= SPMV_CLASS_ML;
+    if (p2[0] / p[1] >= t_mb) c |= SPMV_CLASS_MB;
+  }
   return c;
 }
 
@@ -526,7 +586,8 @@ std::vector<double> sm_spans(const StaticSetup &st, cudaStream_t s, double *glob
   return spans;
 }
 
-void run_profile(spmv_matrix *h, int reps, spmv_profile_report &o, cudaStream_t s) {
+void run_profile(spmv_matrix *h, int reps, spmv_profile_report &o, cudaStream_t s,
+                 bool second_pass = false) {
   std::memset(&o, 0, sizeof o);
   const KernelSet *ks = set_for(h);
   DeviceInfo &d = device_info(h->device);
@@ -589,11 +650,28 @@ void run_profile(spmv_matrix *h, int reps, spmv_profile_report &o, cudaStream_t 
   o.t_imb_ms = t_imb;
   o.n_ctas = st.pa.n_ctas;
   o.vs = st.pa.vs;
+  if (second_pass && h->n_rows > 0) {
+    // the CMP optimization as the new baseline: thread-per-row tiles, int32 columns
+    spmv_variant v2{};
+    v2.vec = 1;
+    v2.vs = 1;
+    compute_tile_cap(h, v2, s);
+    const float t2 = time_launches([&]() { return launch_run(h, v2, x.p, y.p, s); }, reps, s);
+    RunArgs a2 = run_args(h, x.p, y.p);
+    a2.colind = colp.as<int32_t>();
+    const KernelSet *k2 = set_for(h);
+    const float t2ml = time_launches([&]() { return k2->spmv(v2, a2, s); }, reps, s);
+    o.p2[0] = gf(t2);
+    o.p2[1] = gf(t2ml);
+  }
 }
 
-// Sub-warp width sweep by timing (Section III-E "parameter tuning"; build addition).
+// Sub-warp width sweep by timing (Section III-E "parameter tuning"; build addition). When
+// the thread-per-row kernel (width 1) wins, its geometry is swept too: 128 / 64 / 32 rows
+// per tile, one tile per CTA or persistent CTAs with two tiles in flight.
 void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, cudaStream_t s) {
   if (v.partition != 0 || h->n_rows == 0) return;
+  const bool fixed_geometry = v.tile_rows != 0;
   const size_t vb = dtype_bytes(h->vec);
   DevBuf x, y;
   x.alloc(vb * (size_t)std::max<int64_t>(h->n_cols, 1), vb, s);
@@ -602,6 +680,7 @@ void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, cudaStream_t s) {
   float best = 1e30f;
   int best_vs = v.vs;
   const int widths[6] = {1, 2, 4, 8, 16, 32};
+  compute_tile_cap(h, v, s);
   for (int w : widths) {
     spmv_variant t = v;
     t.vs = w;
@@ -612,6 +691,33 @@ void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, cudaStream_t s) {
     }
   }
   v.vs = best_vs;
+  if (best_vs != 1) {
+    v.tile_rows = 0;
+    v.tile_pipe = 0;
+    return;
+  }
+  if (fixed_geometry) {
+    set_tile_geometry(h, v, v.tile_rows, v.tile_pipe != 0, s);
+    return;
+  }
+  int best_rows = h->tile_rows, best_pipe = h->tile_pipe, best_cap = h->tile_cap;
+  for (int pipe = 0; pipe <= 1; ++pipe) {
+    for (int rows = kTileRows; rows >= 32; rows /= 2) {
+      set_tile_geometry(h, v, rows, pipe != 0, s);
+      const float ms = time_launches([&]() { return launch_run(h, v, x.p, y.p, s); }, reps, s);
+      if (ms < best) {
+        best = ms;
+        best_rows = rows;
+        best_pipe = pipe;
+        best_cap = h->tile_cap;
+      }
+    }
+  }
+  h->tile_rows = best_rows;
+  h->tile_pipe = best_pipe;
+  h->tile_cap = best_cap;
+  v.tile_rows = best_rows;
+  v.tile_pipe = best_pipe;
 }
 
 bool combo_offered(spmv_dtype storage, spmv_dtype vec, spmv_dtype acc) {
@@ -681,6 +787,7 @@ spmv_status spmv_tune_opts_default(spmv_tune_opts *o) {
   o->long_row_ratio = 32.0;
   o->autotune = 1;
   o->reps = 20;
+  o->second_pass = 1;
   o->min_margin = 0.0;
   return SPMV_OK;
 }
@@ -836,10 +943,12 @@ spmv_status spmv_tune(spmv_handle_t h, spmv_mode mode, const spmv_tune_opts *opt
       }
       if (!done) {
         spmv_profile_report po;
-        run_profile(h, opts.reps, po, s);
+        run_profile(h, opts.reps, po, s, opts.second_pass != 0);
         std::memcpy(rep.p, po.p, sizeof po.p);
+        std::memcpy(rep.p2, po.p2, sizeof po.p2);
         rep.b_max_gbs = po.b_max_gbs;
-        cls = classify(po.p, opts.t_imb, opts.t_ml, opts.t_mb);
+        cls = classify2(po.p, opts.second_pass ? po.p2 : nullptr, opts.t_imb, opts.t_ml,
+                        opts.t_mb);
         if (nnz_max < 0) {
           CK(launch_row_len_max(h->n_rows, h->rowptr.as<int32_t>(), h->small.as<int32_t>(), s));
           int32_t m = 0;
@@ -865,6 +974,7 @@ spmv_status spmv_tune(spmv_handle_t h, spmv_mode mode, const spmv_tune_opts *opt
     rep.t_classify_ms = t1 - t0;
     rep.t_prep_ms = t2 - t1;
     rep.t_autotune_ms = t3 - t2;
+
     rep.t_pre_ms = t3 - t0;
     return SPMV_OK;
   });
@@ -980,7 +1090,7 @@ spmv_status spmv_profile(spmv_handle_t h, int32_t reps, spmv_profile_report *out
   if (!h || !out) return SPMV_ERR_ARG;
   return guarded([&]() -> spmv_status {
     spmv_profile_report o;
-    run_profile(h, reps > 0 ? reps : 20, o, static_cast<cudaStream_t>(stream));
+    run_profile(h, reps > 0 ? reps : 20, o, static_cast<cudaStream_t>(stream), true);
     *out = o;
     return SPMV_OK;
   });
@@ -1054,6 +1164,11 @@ spmv_status spmv_probe_bandwidth(double *hbm_gbs, double *l2_gbs) {
 uint32_t spmv_classify(const double *p, double t_imb, double t_ml, double t_mb) {
   if (!p) return 0;
   return classify(p, t_imb, t_ml, t_mb);
+}
+
+uint32_t spmv_classify2(const double *p, const double *p2, double t_imb, double t_ml, double t_mb) {
+  if (!p) return 0;
+  return classify2(p, p2, t_imb, t_ml, t_mb);
 }
 
 void spmv_variant_for_classes(uint32_t classes, double nnz_avg, double nnz_max,

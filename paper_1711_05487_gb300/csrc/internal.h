@@ -36,10 +36,12 @@ struct RunArgs {
   double *head_val = nullptr;        // [n_tiles]
   int32_t k = 1;                     // right-hand sides (SpMM)
   int32_t tile_cap = 0;              // staged elements per row tile (thread-per-row kernel)
+  int32_t tile_rows = 0;             // rows (= threads) per tile: 32, 64 or 128
+  int32_t tile_pipe = 0;             // 1: persistent CTAs with two staged tiles in flight
   int32_t *err = nullptr;            // device error word (bounded waits)
 };
 
-// Thread-per-row tile kernel geometry: rows (= threads) per CTA.
+// Thread-per-row tile kernel geometry: at most this many rows (= threads) per CTA.
 constexpr int kTileRows = 128;
 // A bounded device wait gives up after this many nanoseconds.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;

@@ -69,7 +69,7 @@ def measure_matrix(m, reps: int = 5) -> dict:
     feat16 = np.concatenate([f, [float(m.n_rows), float(m.nnz)]])
     lens = np.diff(m.rowptr)
     out = {"feat16": feat16, "classes": rep.classes, "p": [rep.p[k] for k in rep.p],
-           "times": times, "t_pre_profile_ms": rep.t_pre_ms, "t_features_ms": t_feat,
+           "p2": list(rep.p2), "times": times, "t_pre_profile_ms": rep.t_pre_ms, "t_features_ms": t_feat,
            "nnz_avg": float(lens.mean()) if lens.size else 0.0,
            "nnz_max": float(lens.max()) if lens.size else 0.0, "name": m.name}
     A.close()
@@ -102,6 +102,7 @@ def build_dataset(count: int, seed: int, n_lo: int, n_hi: int, reps: int = 5,
         "feat16": np.stack([r["feat16"] for r in rows]),
         "classes": np.array([r["classes"] for r in rows], dtype=np.int32),
         "p": np.array([r["p"] for r in rows]),
+        "p2": np.array([r["p2"] for r in rows]),
         "times": np.array([r["times"] for r in rows]),
         "t_pre_profile_ms": np.array([r["t_pre_profile_ms"] for r in rows]),
         "t_features_ms": np.array([r["t_features_ms"] for r in rows]),
@@ -236,18 +237,36 @@ def main():
     # split by seed order: the first train_frac of the indices train, the rest test
     n_tr = int(round(args.train_frac * n))
     tr, te = np.arange(n_tr), np.arange(n_tr, n)
+    # thresholds of the profile route calibrated on the training split (Section III-C grid
+    # search), then the labels the network learns are the calibrated route's class sets
+    cal = None
+    if "p2" in ds:
+        from . import calibrate
+        cal = calibrate.grid_search(ds, tr)
+        ds = dict(ds)
+        ds["classes_paper"] = ds["classes"]
+        ds["classes"] = calibrate.classes_for(ds, np.arange(n), cal["best"])
     t1 = time.time()
     params, mu, inv, hist = train(ds["feat16"][tr], ds["classes"][tr], steps=args.steps)
     t_train = time.time() - t1
     pred_te, _ = predict(params, mu, inv, ds["feat16"][te])
     pred_tr, _ = predict(params, mu, inv, ds["feat16"][tr])
     res = {"train": evaluate(ds, tr, pred_tr), "test": evaluate(ds, te, pred_te),
+           "calibration": None if cal is None else {
+               "thresholds": cal["best"], "train_mean_gain": cal["best_gain"],
+               "paper_thresholds_train_mean_gain": cal["paper_gain"],
+               "test_mean_gain": calibrate.mean_gain(ds, te, cal["best"]),
+               "paper_thresholds_test_mean_gain": calibrate.mean_gain(ds, te, calibrate.PAPER)},
            "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
            "t_dataset_s": t_data, "t_train_s": t_train, "count": int(n),
            "t_pre_profile_ms_median": float(np.median(ds["t_pre_profile_ms"])),
            "t_features_ms_median": float(np.median(ds["t_features_ms"]))}
     sel = Selector(SIZES, params, mu, inv)
     sel.save(os.path.join(args.out, "selector_gb300.npz"))
+    if cal is not None:
+        with open(os.path.join(args.out, "calibration_gb300.json"), "w") as fh:
+            json.dump({"t_imb": cal["best"][0], "t_ml": cal["best"][1], "t_mb": cal["best"][2],
+                       "second_pass": 1}, fh, indent=1)
     with open(os.path.join(args.out, "selector_metrics.json"), "w") as fh:
         json.dump(res, fh, indent=1)
     print(json.dumps(res))

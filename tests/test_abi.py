@@ -76,6 +76,16 @@ def test_classify_matches_oracle(abi):
             assert abi.spmv_classify(p.ctypes.data, *t) == oracle.classify(*p, *t)
 
 
+def test_classify2_matches_oracle(abi):
+    rng = np.random.default_rng(2)
+    for _ in range(3000):
+        p = np.ascontiguousarray(rng.uniform(10, 1000, 6))
+        p2 = np.ascontiguousarray(rng.uniform(10, 1500, 2))
+        for q in (p2, None):
+            got = abi.spmv_classify2(p.ctypes.data, None if q is None else q.ctypes.data)
+            assert got == oracle.classify2(p, q)
+
+
 def test_variant_map_matches_oracle(abi):
     for cls in range(16):
         for avg, mx in [(10, 1000), (10, 100), (1, 33), (0, 0)]:

@@ -66,7 +66,7 @@ def test_profile_route_decision_and_result(api, torch, name):
     r = A.tune("profile", reps=5)
     p = [r.p[k] for k in ("P_CSR", "P_MB", "P_ML", "P_IMB", "P_CMP", "P_peak")]
     assert all(v > 0 for v in p)
-    assert r.classes == oracle.classify(*p)
+    assert r.classes == oracle.classify2(p, r.p2)
     lens = np.diff(m.rowptr)
     want = oracle.variant_for_classes(r.classes, lens.mean(), lens.max())
     assert tuple(r.variant[:4]) == want

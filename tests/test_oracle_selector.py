@@ -247,3 +247,17 @@ def test_mlp_inputs_definition():
     assert np.array_equal(y, (x - 1.0) * 0.5)
     z = np.zeros(16)
     assert oracle.mlp_inputs(z)[0].tolist() == [0.0] * 12
+
+
+def test_classify2_second_pass_truth_table():
+    cmp_only = [100.0, 150.0, 110.0, 110.0, 110.0, 300.0]     # Fig. 3 -> {CMP}
+    assert oracle.classify(*cmp_only) == 8
+    assert oracle.classify2(cmp_only) == 8                    # no second pass
+    # P_CSR' = 120 (120 / P_MB 150 = 0.8 >= 0.75 -> MB); P_ML' = 200 (ratio 1.67 -> ML)
+    assert oracle.classify2(cmp_only, [120.0, 200.0]) == 8 | 1 | 2
+    assert oracle.classify2(cmp_only, [100.0, 110.0]) == 8    # 0.667 < 0.75, ratio 1.1
+    assert oracle.classify2(cmp_only, [112.5, 112.5]) == 8 | 1  # exactly 0.75 -> MB
+    assert oracle.classify2(cmp_only, [100.0, 125.0]) == 8    # ML needs a strict excess
+    # without CMP in the first pass the second pass changes nothing
+    mb_only = [100.0, 110.0, 100.0, 100.0, 150.0, 300.0]
+    assert oracle.classify2(mb_only, [1.0, 1000.0]) == oracle.classify(*mb_only) == 1
