@@ -112,6 +112,12 @@ WORKLOADS = {
                         make=lambda: synth.power_law(4_000_000), x_seed=synth.SEED_BASE + 13),
     "scattered_16m": dict(desc="16,000,000 rows x 8 uniform random columns, FP64",
                           make=lambda: synth.scattered(16_000_000, 8), x_seed=synth.SEED_BASE + 14),
+    "powerlaw_1m": dict(desc="power-law rows Zipf(1.8) clipped at 200,000, N=1,000,000, FP32 "
+                             "(profiling-size case)",
+                        make=lambda: synth.power_law(1_000_000), x_seed=synth.SEED_BASE + 13),
+    "scattered_4m": dict(desc="4,000,000 rows x 8 uniform random columns, FP64 (profiling-size "
+                              "case)", make=lambda: synth.scattered(4_000_000, 8),
+                         x_seed=synth.SEED_BASE + 14),
 }
 
 
@@ -308,6 +314,110 @@ def run_ours(args, rank, world):
     return out, m
 
 
+def run_batched(args, rank, world):
+    """512 mixed FP32 matrices (N log-uniform in [1e3, 2e5]) with k in {1, 4, 16} right-hand
+    sides each: one graph-captured persistent launch per step, against the same products
+    launched matrix by matrix."""
+    import concurrent.futures as cf
+
+    import torch
+
+    from paper_1711_05487_gb300 import api
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    specs = synth.batched_specs(args.batch_count)
+    t0 = time.time()
+    with cf.ThreadPoolExecutor(max_workers=max(2, (os.cpu_count() or 4) - 2)) as ex:
+        mats = list(ex.map(lambda sp: synth.make_from_spec(sp, dtype=np.float32), specs))
+    gen_s = time.time() - t0
+    stream = torch.cuda.Stream()
+    sel_path = os.path.join(ROOT, "paper_1711_05487_gb300", "data", "selector_gb300.npz")
+    sel = api.Selector.load(sel_path) if os.path.exists(sel_path) else None
+    As, Xs, Ys, ks = [], [], [], []
+    flops = 0.0
+    nbytes = 0
+    t_tune = 0.0
+    for sp, m in zip(specs, mats):
+        A = api.SpmvMatrix.from_csr(m, stream=stream)
+        A.set_precision("f32", "f32", "f32", stream=stream)
+        if sel is not None:
+            t_tune += A.tune("learned", stream=stream, selector=sel).t_pre_ms
+        else:
+            A.set_variant(stream=stream)
+        k = sp["k"]
+        X = torch.from_numpy(synth.uniform_vector(m.n_cols * k, sp["seed"], np.float32)
+                             ).reshape(m.n_cols, k).cuda()
+        As.append(A)
+        Xs.append(X)
+        Ys.append(torch.empty((m.n_rows, k), dtype=torch.float32, device="cuda"))
+        ks.append(k)
+        flops += 2.0 * m.nnz * k
+        nbytes += 4 * (m.n_rows + 1) + 8 * m.nnz + 4 * k * (m.n_rows + m.n_cols)
+    B = api.Batch(As, Xs, Ys, ks, stream=stream)
+
+    def timed(fn, K, W, tag):
+        with torch.cuda.stream(stream):
+            for _ in range(W):
+                fn(stream=stream)
+            stream.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push(tag)
+            e0.record(stream)
+            for _ in range(K):
+                fn(stream=stream)
+            e1.record(stream)
+            torch.cuda.nvtx.range_pop()
+            e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / K
+
+    peak, peak_kind = _peaks()
+    seq_ms = timed(B.run_sequential, max(4, args.steps // 8), args.warmup, "batched_sequential")
+    clocks = ClockSampler(dev)
+    clocks.start()
+    t_load = time.time()
+    with torch.cuda.stream(stream):
+        while time.time() - t_load < 1.5:
+            B.run(stream=stream)
+            stream.synchronize()
+    ms = timed(B.run, args.steps, args.warmup, "bench_timed")
+    clocks.stop()
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    total_nnz = sum(m.nnz for m in mats)
+    out = {
+        "metric": "batched SpMV/SpMM GFLOP/s (sum of 2*nnz*k / t), one persistent launch",
+        "value": round(world * flops / (ms * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded)",
+        "config": {"workload": f"batched_{len(mats)}", "matrices": len(mats),
+                   "total_nnz": total_nnz,
+                   "k_hist": {str(k): ks.count(k) for k in (1, 4, 16)},
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (no flush needed)"},
+        "sequential_launches": {"gflops": round(flops / (seq_ms * 1e-3) / 1e9, 2),
+                                "ms": round(seq_ms, 4)},
+        "speedup_vs_sequential": round(seq_ms / ms, 3),
+        "tune": {"route": "learned" if sel is not None else "fixed",
+                 "t_pre_ms_total": round(t_tune, 1)},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_kind": peak_kind, "alg_bytes": nbytes},
+        "gpu_launches": args.steps * 2,
+        "clocks": clocks.summary(),
+        "gen_s": round(gen_s, 1),
+    }
+    return out
+
+
 def cpu_baseline(m, x_host, budget_s=10.0):
     """The oracle's single-threaded FP64 CSR SpMV timed on the host on the same matrix."""
     import oracle
@@ -363,7 +473,10 @@ def main():
     ap.add_argument("--steps", type=int, default=128)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=list(WORKLOADS), default="stencil27_160")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batched_512"],
+                    default="stencil27_160")
+    ap.add_argument("--batch-count", type=int, default=512,
+                    help="matrices in the batched workload (512; fewer for profiling)")
     ap.add_argument("--quick", action="store_true", help="skip the precision variants")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fixed-variant", default=None,
@@ -384,6 +497,11 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
+    if args.workload == "batched_512":
+        out = run_batched(args, rank, world)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return
     out, m = run_ours(args, rank, world)
     if rank == 0:
         if not args.no_cpu_baseline:

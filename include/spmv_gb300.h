@@ -153,8 +153,9 @@ spmv_status spmv_set_variant(spmv_handle_t h, const spmv_variant *v, spmv_stream
 spmv_status spmv_run(spmv_handle_t h, const void *x, void *y, spmv_stream_t stream);
 
 /* y = A x with HOST buffers: copies x to a handle-owned device buffer, runs, copies y
- * back, on stream; returns after the stream has finished (the end-to-end path).
- * Pinned host memory gives asynchronous, full-speed copies. */
+ * back; returns when y is on the host (the end-to-end path). Row variants compute in four
+ * row chunks and copy each finished chunk of y back on a handle-owned stream while the next
+ * chunk computes. Pinned host memory gives asynchronous, full-speed copies. */
 spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
                           spmv_stream_t stream);
 
@@ -293,8 +294,8 @@ const char *spmv_status_string(spmv_status s);
  * the CSR definition). The call allocates nothing: its scratch (merge-path tile table and
  * per-tile carries) lives in one fixed 16 MiB array in device global memory, created when
  * the library's kernels are loaded on a device and held by every GPU that loads them until
- * the process exits. Sizes with n_rows + nnz above about 1.2e9 (599,158 tiles of 2048 merge
- * items) are rejected with SPMV_ERR_TOO_LARGE before any work is queued.
+ * the process exits. Sizes with n_rows + nnz above about 1.07e9 (599,158 tiles of 1792
+ * merge items) are rejected with SPMV_ERR_TOO_LARGE before any work is queued.
  *
  * The first call on each device looks up the array's device address (a runtime call that
  * may synchronize); make that first call before any stream capture. Asynchronous on

@@ -23,6 +23,9 @@ using namespace spmv;
 namespace {
 
 typedef unsigned __int128 u128;
+// Host-buffer runs split the rows into this many chunks so that the copy of one chunk of y
+// back to the host overlaps the computation of the next.
+constexpr int kHostChunks = 4;
 
 inline size_t dtype_bytes(spmv_dtype t) { return t == SPMV_F64 ? 8 : (t == SPMV_F32 ? 4 : 2); }
 inline bool valid_dtype(int t) { return t == SPMV_F64 || t == SPMV_F32 || t == SPMV_BF16; }
@@ -136,6 +139,8 @@ struct spmv_matrix {
   int32_t tile_pipe = 0;       // 1: persistent CTAs with two tiles in flight
   DevBuf d_err;                // device error word of bounded waits
   DevBuf small;                // 256 bytes for single-value reductions (maxima, codes)
+  cudaStream_t copy_stream = nullptr;   // host-buffer runs: device-to-host copies of y
+  cudaEvent_t chunk_done[kHostChunks] = {};
   DevBuf feat_part, feat_fin;  // feature partial sums, kept between calls
   DevBuf x_stage, y_stage, scratch;
   int32_t last_error = 0;
@@ -845,6 +850,11 @@ spmv_status spmv_create(spmv_handle_t *out, int64_t n_rows, int64_t n_cols, int6
 spmv_status spmv_destroy(spmv_handle_t h) {
   if (!h) return SPMV_ERR_ARG;
   cudaDeviceSynchronize();
+  if (h->copy_stream) {
+    for (int c = 0; c < kHostChunks; ++c)
+      if (h->chunk_done[c]) cudaEventDestroy(h->chunk_done[c]);
+    cudaStreamDestroy(h->copy_stream);
+  }
   for (DevBuf *b : {&h->rowptr, &h->colind, &h->val_in, &h->val_store, &h->dbase, &h->delta,
                     &h->esc, &h->coord, &h->tail_row, &h->tail_val, &h->head_val, &h->x_stage,
                     &h->y_stage, &h->scratch, &h->d_err, &h->small, &h->feat_part,
@@ -1000,11 +1010,41 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
     const size_t vb = dtype_bytes(h->vec);
     if (!h->x_stage.p) h->x_stage.alloc(vb * (size_t)std::max<int64_t>(h->n_cols, 1), vb, s);
     if (!h->y_stage.p) h->y_stage.alloc(vb * (size_t)std::max<int64_t>(h->n_rows, 1), vb, s);
+    if (!h->copy_stream) {
+      CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+      for (int c = 0; c < kHostChunks; ++c)
+        CK(cudaEventCreateWithFlags(&h->chunk_done[c], cudaEventDisableTiming));
+    }
     if (h->n_cols > 0)
       CK(cudaMemcpyAsync(h->x_stage.p, x_host, vb * (size_t)h->n_cols, cudaMemcpyHostToDevice, s));
-    CK(launch_run(h, h->variant, h->x_stage.p, h->y_stage.p, s));
-    if (h->n_rows > 0)
-      CK(cudaMemcpyAsync(y_host, h->y_stage.p, vb * (size_t)h->n_rows, cudaMemcpyDeviceToHost, s));
+    // Row kernels compute any row range on their own (row pointers are absolute), so the rows
+    // go in chunks (aligned to 128-row tiles) and each chunk of y is copied back on a second
+    // stream while the next chunk computes. Merge-path tiles span the whole matrix: one launch.
+    const bool chunked = h->variant.partition == 0 && h->n_rows >= 4 * kHostChunks * kTileRows;
+    const int nch = chunked ? kHostChunks : 1;
+    int64_t per = (h->n_rows + nch - 1) / nch;
+    per = ((per + kTileRows - 1) / kTileRows) * kTileRows;
+    const KernelSet *ks = set_for(h);
+    for (int c = 0; c < nch; ++c) {
+      const int64_t r0 = std::min<int64_t>(h->n_rows, (int64_t)c * per);
+      const int64_t r1 = std::min<int64_t>(h->n_rows, r0 + per);
+      if (r1 <= r0) continue;
+      if (nch == 1) {
+        CK(launch_run(h, h->variant, h->x_stage.p, h->y_stage.p, s));
+      } else {
+        RunArgs a = run_args(h, h->x_stage.p, static_cast<char *>(h->y_stage.p) + vb * (size_t)r0);
+        a.n_rows = r1 - r0;
+        a.rowptr += r0;
+        if (a.dbase) a.dbase += r0;
+        CK(ks->spmv(h->variant, a, s));
+      }
+      CK(cudaEventRecord(h->chunk_done[c], s));
+      CK(cudaStreamWaitEvent(h->copy_stream, h->chunk_done[c], 0));
+      CK(cudaMemcpyAsync(static_cast<char *>(y_host) + vb * (size_t)r0,
+                         static_cast<char *>(h->y_stage.p) + vb * (size_t)r0,
+                         vb * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, h->copy_stream));
+    }
+    CK(cudaStreamSynchronize(h->copy_stream));
     CK(cudaStreamSynchronize(s));
     return SPMV_OK;
   });

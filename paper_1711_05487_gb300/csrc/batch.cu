@@ -1,11 +1,13 @@
 // Batched SpMV / SpMM over many matrices of uneven sizes in one persistent launch.
 //
 // The host plans work items (row blocks of about equal nonzero counts; rows longer than a
-// chunk are split into nonzero chunks, the matrix decomposition of Fig. 4/5). A grid of
-// resident CTAs takes items from a device counter with atomicAdd -- no CTA ever waits on
-// another -- and k_batch_fixup adds the chunks of split rows in chunk order, in FP64.
-// Storage, x/y and accumulation are FP32; every matrix has k in {1, 4, 16} right-hand
-// sides (row-major X and Y).
+// chunk are split into nonzero chunks, the matrix decomposition of Fig. 4/5) and sorts them
+// by the matrices' right-hand-side count k in {1, 4, 16}. One resident kernel per k walks its
+// items: every warp takes the next item from a device counter with atomicAdd (no warp or CTA
+// ever waits on another), a row-block item is computed by sub-warps of the matrix's width,
+// a chunk of a long row by the whole warp into an FP64 partial slot, and k_batch_fixup adds
+// the chunks of each split row in chunk order, in FP64. Storage, x/y and accumulation are
+// FP32; X and Y are row-major (n x k).
 #include "common.cuh"
 
 namespace spmv {
@@ -30,18 +32,18 @@ __device__ __forceinline__ void load_xrow(const float *p, float *o) {
   }
 }
 
-// Rows [r0, r1) of one matrix, a sub-warp of vs lanes per row.
+// Rows [r0, r1) of one matrix by one warp: sub-warps of VS lanes, one row each.
 template <int K, int VS>
-__device__ void batch_rows(const BatchMat &m, int r0, int r1) {
-  constexpr int GROUPS = kBT / VS;
-  const int lane = threadIdx.x & (VS - 1);
+__device__ void warp_rows(const BatchMat &m, int r0, int r1, int lane) {
+  constexpr int GROUPS = 32 / VS;
+  const int sl = lane & (VS - 1);
   const unsigned mask = group_mask<VS>();
-  for (int row = r0 + (int)threadIdx.x / VS; row < r1; row += GROUPS) {
+  for (int row = r0 + lane / VS; row < r1; row += GROUPS) {
     const int s = __ldg(m.rowptr + row), e = __ldg(m.rowptr + row + 1);
     float acc[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) acc[q] = 0.0f;
-    for (int j = s + lane; j < e; j += VS) {
+    for (int j = s + sl; j < e; j += VS) {
       const float v = __ldg(m.val + j);
       float xr[K];
       load_xrow<K>(m.X + (int64_t)__ldg(m.colind + j) * K, xr);
@@ -51,85 +53,72 @@ __device__ void batch_rows(const BatchMat &m, int r0, int r1) {
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       const float r = group_sum<VS>(acc[q], mask);
-      if (lane == 0) m.Y[(int64_t)row * K + q] = r;
+      if (sl == 0) m.Y[(int64_t)row * K + q] = r;
     }
   }
 }
 
 template <int K>
-__device__ void batch_rows_k(const BatchMat &m, int r0, int r1) {
+__device__ void warp_rows_vs(const BatchMat &m, int r0, int r1, int lane) {
   switch (m.vs) {
-    case 2: batch_rows<K, 2>(m, r0, r1); break;
-    case 4: batch_rows<K, 4>(m, r0, r1); break;
-    case 8: batch_rows<K, 8>(m, r0, r1); break;
-    case 16: batch_rows<K, 16>(m, r0, r1); break;
-    default: batch_rows<K, 32>(m, r0, r1); break;
+    case 2: warp_rows<K, 2>(m, r0, r1, lane); break;
+    case 4: warp_rows<K, 4>(m, r0, r1, lane); break;
+    case 8: warp_rows<K, 8>(m, r0, r1, lane); break;
+    case 16: warp_rows<K, 16>(m, r0, r1, lane); break;
+    default: warp_rows<K, 32>(m, r0, r1, lane); break;
   }
 }
 
-// Nonzeros [z0, z1) of one long row, the whole CTA: FP32 per-thread sums, then a fixed
-// tree reduction in FP64 into partial slot `chunk` (16 doubles per slot, k used).
+// Nonzeros [z0, z1) of one long row by one warp: FP32 lane sums, then a fixed shuffle tree
+// in FP64 into partial slot `chunk` (16 doubles per slot, k used).
 template <int K>
-__device__ void batch_chunk(const BatchMat &m, int z0, int z1, int chunk, double *partials) {
-  __shared__ double red[kBT];
+__device__ void warp_chunk(const BatchMat &m, int z0, int z1, int chunk, double *partials,
+                           int lane) {
   float acc[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) acc[q] = 0.0f;
-  for (int j = z0 + (int)threadIdx.x; j < z1; j += kBT) {
+  for (int j = z0 + lane; j < z1; j += 32) {
     const float v = __ldg(m.val + j);
     float xr[K];
     load_xrow<K>(m.X + (int64_t)__ldg(m.colind + j) * K, xr);
 #pragma unroll
     for (int q = 0; q < K; ++q) acc[q] = fmaf(v, xr[q], acc[q]);
   }
+#pragma unroll
   for (int q = 0; q < K; ++q) {
-    red[threadIdx.x] = (double)acc[q];
-    __syncthreads();
-    for (int off = kBT / 2; off > 0; off >>= 1) {
-      if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) partials[(int64_t)chunk * 16 + q] = red[0];
-    __syncthreads();
+    const double r = group_sum<32>((double)acc[q], 0xffffffffu);
+    if (lane == 0) partials[(int64_t)chunk * 16 + q] = r;
   }
 }
 
-__device__ void batch_item(const BatchMat *mats, const BatchItem &it, double *partials) {
-  const BatchMat m = mats[it.mat];
-  if (it.chunk < 0) {
-    switch (m.k) {
-      case 1: batch_rows_k<1>(m, it.row_begin, it.row_end); break;
-      case 4: batch_rows_k<4>(m, it.row_begin, it.row_end); break;
-      default: batch_rows_k<16>(m, it.row_begin, it.row_end); break;
-    }
-  } else {
-    switch (m.k) {
-      case 1: batch_chunk<1>(m, it.nz_begin, it.nz_end, it.chunk, partials); break;
-      case 4: batch_chunk<4>(m, it.nz_begin, it.nz_end, it.chunk, partials); break;
-      default: batch_chunk<16>(m, it.nz_begin, it.nz_end, it.chunk, partials); break;
-    }
-  }
-}
-
+template <int K>
 __global__ void __launch_bounds__(kBT)
 k_batch_persistent(const BatchMat *mats, const BatchItem *items, int32_t n_items,
                    int32_t *counter, double *partials) {
-  __shared__ int s_item;
+  const int lane = threadIdx.x & 31;
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-    __syncthreads();
-    const int it = s_item;
-    __syncthreads();
+    int it = 0;
+    if (lane == 0) it = atomicAdd(counter, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= n_items) break;
-    batch_item(mats, items[it], partials);
+    const BatchItem item = items[it];
+    const BatchMat m = mats[item.mat];
+    if (item.chunk < 0) warp_rows_vs<K>(m, item.row_begin, item.row_end, lane);
+    else warp_chunk<K>(m, item.nz_begin, item.nz_end, item.chunk, partials, lane);
   }
 }
 
-// One CTA per item (the same work without persistence).
+// One warp per item (the same work without persistence).
+template <int K>
 __global__ void __launch_bounds__(kBT)
 k_batch_items(const BatchMat *mats, const BatchItem *items, int32_t n_items, double *partials) {
-  if ((int)blockIdx.x >= n_items) return;
-  batch_item(mats, items[blockIdx.x], partials);
+  const int lane = threadIdx.x & 31;
+  const int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  if (it >= n_items) return;
+  const BatchItem item = items[it];
+  const BatchMat m = mats[item.mat];
+  if (item.chunk < 0) warp_rows_vs<K>(m, item.row_begin, item.row_end, lane);
+  else warp_chunk<K>(m, item.nz_begin, item.nz_end, item.chunk, partials, lane);
 }
 
 __global__ void k_batch_fixup(const BatchMat *mats, const BatchFix *fix, int32_t n_fix,
@@ -145,26 +134,33 @@ __global__ void k_batch_fixup(const BatchMat *mats, const BatchFix *fix, int32_t
   m.Y[(int64_t)f.row * m.k + q] = (float)tot;
 }
 
-int batch_blocks_per_sm() {
+int batch_blocks_per_sm_k(int k) {
   int b = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_persistent, kBT, 0);
+  if (k == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_persistent<1>, kBT, 0);
+  else if (k == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_persistent<4>, kBT, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_persistent<16>, kBT, 0);
   return b > 0 ? b : 1;
 }
 
-cudaError_t launch_batch_persistent(const BatchMat *mats, const BatchItem *items,
-                                    int32_t n_items, int32_t *counter, double *partials,
-                                    int grid, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
-  if (e != cudaSuccess) return e;
-  if (n_items <= 0) return cudaSuccess;
-  k_batch_persistent<<<grid, kBT, 0, s>>>(mats, items, n_items, counter, partials);
+int batch_blocks_per_sm() { return batch_blocks_per_sm_k(16); }
+
+cudaError_t launch_batch_persistent_k(int k, const BatchMat *mats, const BatchItem *items,
+                                      int32_t n_items, int32_t *counter, double *partials,
+                                      int grid, cudaStream_t s) {
+  if (n_items <= 0 || grid <= 0) return cudaSuccess;
+  if (k == 1) k_batch_persistent<1><<<grid, kBT, 0, s>>>(mats, items, n_items, counter, partials);
+  else if (k == 4) k_batch_persistent<4><<<grid, kBT, 0, s>>>(mats, items, n_items, counter, partials);
+  else k_batch_persistent<16><<<grid, kBT, 0, s>>>(mats, items, n_items, counter, partials);
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_items(const BatchMat *mats, const BatchItem *items, int32_t n_items,
-                               double *partials, cudaStream_t s) {
+cudaError_t launch_batch_items_k(int k, const BatchMat *mats, const BatchItem *items,
+                                 int32_t n_items, double *partials, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  k_batch_items<<<n_items, kBT, 0, s>>>(mats, items, n_items, partials);
+  const unsigned g = (unsigned)(((int64_t)n_items * 32 + kBT - 1) / kBT);
+  if (k == 1) k_batch_items<1><<<g, kBT, 0, s>>>(mats, items, n_items, partials);
+  else if (k == 4) k_batch_items<4><<<g, kBT, 0, s>>>(mats, items, n_items, partials);
+  else k_batch_items<16><<<g, kBT, 0, s>>>(mats, items, n_items, partials);
   return cudaGetLastError();
 }
 

@@ -10,10 +10,13 @@
 using namespace spmv;
 
 namespace {
-// Target nonzeros per row-block item; rows longer than this are split into chunks of
-// this many nonzeros (the matrix decomposition applied per item).
-constexpr int32_t kItemNnz = 4096;
-constexpr int32_t kItemRowsMax = 4096;
+// Target nonzeros per row-block item (a warp's work); rows longer than this are split into
+// chunks of kChunkNnz nonzeros (the matrix decomposition applied per item).
+constexpr int32_t kItemNnz = 1024;
+constexpr int32_t kChunkNnz = 2048;
+constexpr int32_t kItemRowsMax = 1024;
+constexpr int kKs[3] = {1, 4, 16};
+inline int k_slot(int k) { return k == 1 ? 0 : (k == 4 ? 1 : 2); }
 
 struct Fail {
   cudaError_t e;
@@ -39,13 +42,16 @@ struct spmv_batch {
   std::vector<void *> Y;
   std::vector<int32_t> k;
   BatchMat *d_mats = nullptr;
-  BatchItem *d_items = nullptr;
+  BatchItem *d_items = nullptr;          // items of k = 1, then k = 4, then k = 16
   BatchFix *d_fix = nullptr;
   double *d_partials = nullptr;
-  int32_t *d_counter = nullptr;
+  int32_t *d_counter = nullptr;          // one work counter per k
   int32_t n_items = 0, n_fix = 0, n_chunks = 0;
-  int grid = 0;
+  int32_t item_off[4] = {0, 0, 0, 0};    // item range of each k
+  int grid[3] = {0, 0, 0};
   cudaStream_t cap = nullptr;
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -56,6 +62,10 @@ static void batch_free(spmv_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (auto st : b->side)
+    if (st) cudaStreamDestroy(st);
+  for (auto e : b->ev)
+    if (e) cudaEventDestroy(e);
   cudaFree(b->d_mats);
   cudaFree(b->d_items);
   cudaFree(b->d_fix);
@@ -78,7 +88,7 @@ spmv_status spmv_batch_create(spmv_batch_t *out, const spmv_handle_t *handles, i
     BK(cudaGetDevice(&b->device));
     b->count = count;
     std::vector<BatchMat> mats((size_t)count);
-    std::vector<BatchItem> items;
+    std::vector<BatchItem> items_k[3];
     std::vector<BatchFix> fix;
     int32_t chunks = 0;
     for (int32_t m = 0; m < count; ++m) {
@@ -108,14 +118,15 @@ spmv_status spmv_batch_create(spmv_batch_t *out, const spmv_handle_t *handles, i
       b->Y.push_back(Y[m]);
       b->k.push_back(k[m]);
       // row blocks of about kItemNnz nonzeros; long rows split into chunks
+      std::vector<BatchItem> &items = items_k[k_slot(k[m])];
       int32_t r = 0;
       while (r < (int32_t)n_rows) {
         const int32_t len = hrp[(size_t)r + 1] - hrp[(size_t)r];
         if (len > kItemNnz) {
           const int32_t first = chunks;
           int32_t cnt = 0;
-          for (int32_t z = hrp[(size_t)r]; z < hrp[(size_t)r + 1]; z += kItemNnz) {
-            const int32_t ze = std::min(z + kItemNnz, hrp[(size_t)r + 1]);
+          for (int32_t z = hrp[(size_t)r]; z < hrp[(size_t)r + 1]; z += kChunkNnz) {
+            const int32_t ze = std::min(z + kChunkNnz, hrp[(size_t)r + 1]);
             items.push_back(BatchItem{m, r, r + 1, z, ze, chunks++});
             ++cnt;
           }
@@ -135,6 +146,12 @@ spmv_status spmv_batch_create(spmv_batch_t *out, const spmv_handle_t *handles, i
         r = e;
       }
     }
+    std::vector<BatchItem> items;
+    for (int q = 0; q < 3; ++q) {
+      b->item_off[q] = (int32_t)items.size();
+      items.insert(items.end(), items_k[q].begin(), items_k[q].end());
+    }
+    b->item_off[3] = (int32_t)items.size();
     b->n_items = (int32_t)items.size();
     b->n_fix = (int32_t)fix.size();
     b->n_chunks = chunks;
@@ -142,7 +159,7 @@ spmv_status spmv_batch_create(spmv_batch_t *out, const spmv_handle_t *handles, i
     BK(cudaMalloc(&b->d_items, sizeof(BatchItem) * std::max<size_t>(items.size(), 1)));
     BK(cudaMalloc(&b->d_fix, sizeof(BatchFix) * std::max<size_t>(fix.size(), 1)));
     BK(cudaMalloc(&b->d_partials, sizeof(double) * 16 * (size_t)std::max(chunks, 1)));
-    BK(cudaMalloc(&b->d_counter, sizeof(int32_t)));
+    BK(cudaMalloc(&b->d_counter, 3 * sizeof(int32_t)));
     BK(cudaMemcpyAsync(b->d_mats, mats.data(), sizeof(BatchMat) * mats.size(), cudaMemcpyHostToDevice, s));
     if (!items.empty())
       BK(cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, s));
@@ -151,8 +168,14 @@ spmv_status spmv_batch_create(spmv_batch_t *out, const spmv_handle_t *handles, i
     BK(cudaStreamSynchronize(s));
     int sms = 0;
     BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
-    b->grid = std::max(1, std::min(sms * batch_blocks_per_sm(), b->n_items));
+    for (int q = 0; q < 3; ++q) {
+      const int64_t warps = b->item_off[q + 1] - b->item_off[q];
+      const int64_t ctas = (warps + 7) / 8;     // 8 warps per CTA
+      b->grid[q] = (int)std::min<int64_t>((int64_t)sms * batch_blocks_per_sm_k(kKs[q]), ctas);
+    }
     BK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    for (auto &st : b->side) BK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    for (auto &e : b->ev) BK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   } catch (const Fail &f) {
     cudaGetLastError();
     batch_free(b);
@@ -169,15 +192,26 @@ spmv_status spmv_run_batched(spmv_batch_t b, spmv_stream_t stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   try {
     if (!b->exec) {
-      // capture on the batch's own stream (the legacy default stream cannot be captured)
+      // Capture on the batch's own streams (the legacy default stream cannot be captured):
+      // reset the counters, fork the three persistent kernels (k = 1, 4, 16) onto parallel
+      // branches, join, then the fixup of split rows.
       BK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e1 = launch_batch_persistent(b->d_mats, b->d_items, b->n_items, b->d_counter,
-                                               b->d_partials, b->grid, b->cap);
-      cudaError_t e2 = launch_batch_fixup(b->d_mats, b->d_fix, b->n_fix, b->d_partials, b->cap);
+      cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 3 * sizeof(int32_t), b->cap);
+      cudaStream_t st[3] = {b->cap, b->side[0], b->side[1]};
+      if (e == cudaSuccess) e = cudaEventRecord(b->ev[0], b->cap);
+      for (int q = 1; q < 3 && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(st[q], b->ev[0], 0);
+      for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+        e = launch_batch_persistent_k(kKs[q], b->d_mats, b->d_items + b->item_off[q],
+                                      b->item_off[q + 1] - b->item_off[q], b->d_counter + q,
+                                      b->d_partials, b->grid[q], st[q]);
+      for (int q = 1; q < 3 && e == cudaSuccess; ++q) {
+        e = cudaEventRecord(b->ev[q], st[q]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->ev[q], 0);
+      }
+      if (e == cudaSuccess) e = launch_batch_fixup(b->d_mats, b->d_fix, b->n_fix, b->d_partials, b->cap);
       cudaGraph_t g = nullptr;
       cudaError_t e3 = cudaStreamEndCapture(b->cap, &g);
-      BK(e1);
-      BK(e2);
+      BK(e);
       BK(e3);
       b->graph = g;
       BK(cudaGraphInstantiate(&b->exec, b->graph, 0));

@@ -15,7 +15,8 @@ constexpr int64_t kPadElems = 32;
 
 // Merge-path tile geometry.
 constexpr int kMergeThreads = 256;
-constexpr int kMergeIpt = 8;                       // merge items per thread
+constexpr int kMergeIpt = 7;   // merge items per thread: an odd stride between threads keeps
+                               // their shared-memory reads in distinct banks
 constexpr int kMergeItems = kMergeThreads * kMergeIpt;
 
 // Everything a SpMV launch needs; unused pointers are null.
@@ -182,14 +183,15 @@ int64_t mlp_param_count(const int32_t *sizes);
 cudaError_t launch_adam(int64_t n, float *p, const float *g, float *m, float *v, float lr,
                         float b1, float b2, float eps, int32_t t, cudaStream_t s);
 
-// Batched (batch.cu)
-cudaError_t launch_batch_persistent(const BatchMat *mats, const BatchItem *items,
-                                    int32_t n_items, int32_t *counter, double *partials,
-                                    int grid, cudaStream_t s);
+// Batched (batch.cu): one persistent kernel per right-hand-side count k in {1, 4, 16}
+cudaError_t launch_batch_persistent_k(int k, const BatchMat *mats, const BatchItem *items,
+                                      int32_t n_items, int32_t *counter, double *partials,
+                                      int grid, cudaStream_t s);
+cudaError_t launch_batch_items_k(int k, const BatchMat *mats, const BatchItem *items,
+                                 int32_t n_items, double *partials, cudaStream_t s);
 cudaError_t launch_batch_fixup(const BatchMat *mats, const BatchFix *fix, int32_t n_fix,
                                const double *partials, cudaStream_t s);
-cudaError_t launch_batch_items(const BatchMat *mats, const BatchItem *items, int32_t n_items,
-                               double *partials, cudaStream_t s);
+int batch_blocks_per_sm_k(int k);
 int batch_blocks_per_sm();
 
 // Device arrays and dtypes of a handle (vs = tuned sub-warp width, 0 if none).

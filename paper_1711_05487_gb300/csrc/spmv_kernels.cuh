@@ -381,9 +381,10 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_pipe(const RunArgs a) {
 //     (coalesced loads, all gathers of the tile in flight at once);
 //  2. every thread takes IPT consecutive merge items (found by a merge-path search in
 //     shared memory) and sums each row it sees with one fused multiply-add per nonzero;
-//  3. a row that began in an earlier thread gets those threads' carries added in thread
-//     order; a row that began in an earlier tile is finished by k_merge_fixup, which adds
-//     the earlier tiles' carries in tile order (no atomics: results are reproducible).
+//  3. a row that began in an earlier thread gets those threads' carries through a segmented
+//     scan over the threads (keys = open rows); a row that began in an earlier tile is
+//     finished by k_merge_fixup, which adds the earlier tiles' carries in tile order (no
+//     atomics: results are reproducible).
 template <typename ValT, typename VecT, typename AccT, bool XL2>
 __global__ void __launch_bounds__(kMergeThreads) k_merge(const RunArgs a) {
   constexpr int D = kMergeItems;
@@ -447,39 +448,86 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const RunArgs a) {
       ++ra;
     }
   }
-  s_crow[threadIdx.x] = row0 + ra;
-  s_cval[threadIdx.x] = acc;
+  // Carries: thread i ends holding the partial sum `acc` of its open row `key`. Keys are
+  // non-decreasing over the threads, so equal keys form contiguous segments; a segmented
+  // inclusive scan (fixed shuffle tree inside each warp, then warps combined in order) gives
+  // every thread the sum of its segment up to itself.
+  const int key = row0 + ra;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  AccT sc = acc;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const AccT tv = __shfl_up_sync(0xffffffffu, sc, off);
+    const int tk = __shfl_up_sync(0xffffffffu, key, off);
+    if (lane >= off && tk == key) sc += tv;
+  }
+  __shared__ AccT s_wsum[kMergeThreads / 32];
+  __shared__ int s_wkey_first[kMergeThreads / 32], s_wkey_last[kMergeThreads / 32];
+  __shared__ AccT s_win[kMergeThreads / 32];
+  if (lane == 31) {
+    s_wsum[warp] = sc;
+    s_wkey_last[warp] = key;
+  }
+  if (lane == 0) s_wkey_first[warp] = key;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // carry into warp w: the part of its first segment held by earlier warps
+    AccT in = 0;
+    s_win[0] = 0;
+    for (int w = 1; w < kMergeThreads / 32; ++w) {
+      if (s_wkey_last[w - 1] == s_wkey_first[w]) {
+        in = s_wsum[w - 1] + (s_wkey_first[w - 1] == s_wkey_last[w - 1] ? in : (AccT)0);
+      } else {
+        in = 0;
+      }
+      s_win[w] = in;
+    }
+  }
+  __syncthreads();
+  if (key == s_wkey_first[warp]) sc += s_win[warp];
+  s_crow[threadIdx.x] = key;
+  s_cval[threadIdx.x] = sc;
   __syncthreads();
   if (has_first) {
-    AccT tot = first_val;
-    for (int q = (int)threadIdx.x - 1; q >= 0 && s_crow[q] == first_row; --q) tot += s_cval[q];
+    // the row this thread completed began in earlier threads: add their segment
+    const int q = (int)threadIdx.x - 1;
+    const AccT tot = (q >= 0 && s_crow[q] == first_row) ? first_val + s_cval[q] : first_val;
     const bool continued = (first_row == row0) && (__ldg(a.rowptr + row0) < nz0);
     if (continued) a.head_val[t] = (double)tot;
     else y[first_row] = (VecT)tot;
   }
   if (threadIdx.x == kMergeThreads - 1) {
-    const int tr = c1.x;
-    double tv = 0.0;
-    for (int q = kMergeThreads - 1; q >= 0 && s_crow[q] == tr; --q) tv += (double)s_cval[q];
-    a.tail_row[t] = tr;
-    a.tail_val[t] = tv;
+    // the row open at the tile's end (idle threads hold it with a zero carry)
+    a.tail_row[t] = c1.x;
+    a.tail_val[t] = s_crow[threadIdx.x] == c1.x ? (double)s_cval[threadIdx.x] : 0.0;
   }
 }
 
-// Rows that began in an earlier tile: y[row] = (carries of earlier tiles, nearest first)
-// + the part summed in the tile that ends the row. FP64 throughout.
+// Rows that began in an earlier tile: y[row] = (carries of the earlier tiles that hold part
+// of the row) + the part summed in the tile that ends the row. One warp per tile: the lanes
+// read 32 earlier tails at a time, a fixed shuffle tree sums each chunk and the chunks are
+// added nearest first; FP64 throughout.
 template <typename VecT>
 __global__ void k_merge_fixup(const RunArgs a) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x + 1;
-  if (t >= a.n_tiles) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32 + 1;
+  if (t >= a.n_tiles) return;                    // uniform across the warp
   const int2 c0 = a.coord[t], c1 = a.coord[t + 1];
   const int row0 = c0.x;
   if (c1.x - c0.x <= 0) return;                  // the tile ends no row
   if (!(__ldg(a.rowptr + row0) < c0.y)) return;  // its first row starts inside it
   double tot = 0.0;
-  for (int64_t q = t - 1; q >= 0 && a.tail_row[q] == row0; --q) tot += a.tail_val[q];
+  for (int64_t base = t - 1; base >= 0; base -= 32) {
+    const int64_t q = base - lane;
+    const bool mine = q >= 0 && a.tail_row[q] == row0;
+    double v = mine ? a.tail_val[q] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    tot += v;
+    if (!__all_sync(0xffffffffu, mine)) break;   // the row's earlier tiles are contiguous
+  }
   tot += a.head_val[t];
-  static_cast<VecT *>(a.y)[row0] = (VecT)tot;
+  if (lane == 0) static_cast<VecT *>(a.y)[row0] = (VecT)tot;
 }
 
 // ------------------------------------------------------------------------ k_static ----
@@ -662,7 +710,7 @@ cudaError_t launch_spmv_impl(const spmv_variant &v, const RunArgs &a, cudaStream
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (a.n_tiles > 1) {
-      const unsigned g = (unsigned)((a.n_tiles - 1 + 255) / 256);
+      const unsigned g = (unsigned)(((a.n_tiles - 1) * 32 + 255) / 256);   // a warp per tile
       k_merge_fixup<VecT><<<g, 256, 0, s>>>(a);
     }
     return cudaGetLastError();

@@ -166,16 +166,22 @@ def test_spmm(api, torch, name, k):
     check_rows(Y32.ravel(), Yr.ravel(), Sr.ravel(), tau, f"spmm32 {name} k={k}")
 
 
-def test_run_host_equals_device_run(api, torch):
-    m = MATS["st27_12"]
+@pytest.mark.parametrize("gen", [lambda: synth.stencil_27pt(12),       # one launch
+                                 lambda: synth.stencil_27pt(30),       # four row chunks
+                                 lambda: synth.power_law(30_000, seed=14, dtype=np.float64)])
+def test_run_host_equals_device_run(api, torch, gen):
+    m = gen()
     A = api.SpmvMatrix.from_csr(m)
-    A.set_variant(index=1, vec=1)
     x64 = synth.uniform_vector(m.n_cols, 7)
-    yd = A.run(_dev(torch, x64)).cpu()
     xh = torch.from_numpy(x64).pin_memory()
     yh = torch.empty(m.n_rows, dtype=torch.float64).pin_memory()
-    A.run_host(xh, yh)
-    assert torch.equal(yd, yh)
+    for v in (dict(index=1, vec=1), dict(vec=1, vs=1, tile_rows=64, tile_pipe=1),
+              dict(vec=1, vs=4), dict(partition=1)):
+        A.set_variant(**v)
+        yd = A.run(torch.from_numpy(x64).cuda()).cpu()
+        yh.fill_(float("nan"))
+        A.run_host(xh, yh)
+        assert torch.equal(yd, yh), v
 
 
 def test_not_tuned_and_bad_args(api, torch):
