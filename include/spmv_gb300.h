@@ -153,9 +153,11 @@ spmv_status spmv_set_variant(spmv_handle_t h, const spmv_variant *v, spmv_stream
 spmv_status spmv_run(spmv_handle_t h, const void *x, void *y, spmv_stream_t stream);
 
 /* y = A x with HOST buffers: copies x to a handle-owned device buffer, runs, copies y
- * back; returns when y is on the host (the end-to-end path). Row variants compute in four
- * row chunks and copy each finished chunk of y back on a handle-owned stream while the next
- * chunk computes. Pinned host memory gives asynchronous, full-speed copies. */
+ * back; returns when y is on the host (the end-to-end path). Row variants compute in eight
+ * row chunks: chunk c waits only for the prefix of x up to the largest column of chunks
+ * 0..c (uploaded piece by piece on a handle-owned stream) and each finished chunk of y is
+ * downloaded on another while the next computes. Pinned host memory gives asynchronous,
+ * full-speed copies. Host buffers must stay valid until the call returns. */
 spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
                           spmv_stream_t stream);
 

@@ -23,9 +23,9 @@ using namespace spmv;
 namespace {
 
 typedef unsigned __int128 u128;
-// Host-buffer runs split the rows into this many chunks so that the copy of one chunk of y
-// back to the host overlaps the computation of the next.
-constexpr int kHostChunks = 4;
+// Host-buffer runs split the rows into this many chunks so that the upload of the part of x
+// the next chunk needs and the download of the previous chunk's y overlap the computation.
+constexpr int kHostChunks = 8;
 
 inline size_t dtype_bytes(spmv_dtype t) { return t == SPMV_F64 ? 8 : (t == SPMV_F32 ? 4 : 2); }
 inline bool valid_dtype(int t) { return t == SPMV_F64 || t == SPMV_F32 || t == SPMV_BF16; }
@@ -140,7 +140,11 @@ struct spmv_matrix {
   DevBuf d_err;                // device error word of bounded waits
   DevBuf small;                // 256 bytes for single-value reductions (maxima, codes)
   cudaStream_t copy_stream = nullptr;   // host-buffer runs: device-to-host copies of y
+  cudaStream_t upload_stream = nullptr; // host-buffer runs: host-to-device copies of x
   cudaEvent_t chunk_done[kHostChunks] = {};
+  cudaEvent_t x_ready[kHostChunks] = {};
+  int64_t x_need[kHostChunks] = {};     // elements of x (a prefix) chunks 0..c read
+  bool x_need_valid = false;
   DevBuf feat_part, feat_fin;  // feature partial sums, kept between calls
   DevBuf x_stage, y_stage, scratch;
   int32_t last_error = 0;
@@ -851,9 +855,12 @@ spmv_status spmv_destroy(spmv_handle_t h) {
   if (!h) return SPMV_ERR_ARG;
   cudaDeviceSynchronize();
   if (h->copy_stream) {
-    for (int c = 0; c < kHostChunks; ++c)
+    for (int c = 0; c < kHostChunks; ++c) {
       if (h->chunk_done[c]) cudaEventDestroy(h->chunk_done[c]);
+      if (h->x_ready[c]) cudaEventDestroy(h->x_ready[c]);
+    }
     cudaStreamDestroy(h->copy_stream);
+    cudaStreamDestroy(h->upload_stream);
   }
   for (DevBuf *b : {&h->rowptr, &h->colind, &h->val_in, &h->val_store, &h->dbase, &h->delta,
                     &h->esc, &h->coord, &h->tail_row, &h->tail_val, &h->head_val, &h->x_stage,
@@ -1012,22 +1019,57 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
     if (!h->y_stage.p) h->y_stage.alloc(vb * (size_t)std::max<int64_t>(h->n_rows, 1), vb, s);
     if (!h->copy_stream) {
       CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
-      for (int c = 0; c < kHostChunks; ++c)
+      CK(cudaStreamCreateWithFlags(&h->upload_stream, cudaStreamNonBlocking));
+      for (int c = 0; c < kHostChunks; ++c) {
         CK(cudaEventCreateWithFlags(&h->chunk_done[c], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->x_ready[c], cudaEventDisableTiming));
+      }
     }
-    if (h->n_cols > 0)
-      CK(cudaMemcpyAsync(h->x_stage.p, x_host, vb * (size_t)h->n_cols, cudaMemcpyHostToDevice, s));
-    // Row kernels compute any row range on their own (row pointers are absolute), so the rows
-    // go in chunks (aligned to 128-row tiles) and each chunk of y is copied back on a second
-    // stream while the next chunk computes. Merge-path tiles span the whole matrix: one launch.
+    // Row kernels compute any row range on their own (row pointers are absolute), so rows go
+    // in chunks aligned to 128-row tiles. Chunk c reads x only up to the largest column of
+    // chunks 0..c, so x is uploaded in matching pieces on one stream, each chunk waits for
+    // its piece, and each finished chunk of y is downloaded on another stream. Merge-path
+    // tiles span the whole matrix: one upload, one launch, one download.
     const bool chunked = h->variant.partition == 0 && h->n_rows >= 4 * kHostChunks * kTileRows;
     const int nch = chunked ? kHostChunks : 1;
     int64_t per = (h->n_rows + nch - 1) / nch;
     per = ((per + kTileRows - 1) / kTileRows) * kTileRows;
+    if (chunked && !h->x_need_valid) {
+      int64_t bounds[kHostChunks + 1];
+      for (int c = 0; c <= nch; ++c) bounds[c] = std::min<int64_t>(h->n_rows, (int64_t)c * per);
+      DevBuf db;
+      db.alloc(sizeof(bounds), 8, s);
+      CK(cudaMemcpyAsync(db.p, bounds, sizeof(bounds), cudaMemcpyHostToDevice, s));
+      CK(launch_chunk_colmax(h->n_rows, h->rowptr.as<int32_t>(), h->colind.as<int32_t>(),
+                             db.as<int64_t>(), nch, h->small.as<int32_t>(), s));
+      int32_t cm[kHostChunks];
+      CK(cudaMemcpyAsync(cm, h->small.p, sizeof(int32_t) * nch, cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      int64_t run = 0;
+      for (int c = 0; c < nch; ++c) {
+        run = std::max<int64_t>(run, (int64_t)cm[c] + 1);
+        h->x_need[c] = std::min<int64_t>(run, h->n_cols);
+      }
+      h->x_need_valid = true;
+    }
+    // the upload stream starts after work already queued on the caller's stream
+    CK(cudaEventRecord(h->chunk_done[0], s));
+    CK(cudaStreamWaitEvent(h->upload_stream, h->chunk_done[0], 0));
+    int64_t uploaded = 0;
     const KernelSet *ks = set_for(h);
     for (int c = 0; c < nch; ++c) {
+      const int64_t need = chunked ? h->x_need[c] : h->n_cols;
+      if (need > uploaded) {
+        CK(cudaMemcpyAsync(static_cast<char *>(h->x_stage.p) + vb * (size_t)uploaded,
+                           static_cast<const char *>(x_host) + vb * (size_t)uploaded,
+                           vb * (size_t)(need - uploaded), cudaMemcpyHostToDevice,
+                           h->upload_stream));
+        uploaded = need;
+      }
+      CK(cudaEventRecord(h->x_ready[c], h->upload_stream));
+      CK(cudaStreamWaitEvent(s, h->x_ready[c], 0));
       const int64_t r0 = std::min<int64_t>(h->n_rows, (int64_t)c * per);
-      const int64_t r1 = std::min<int64_t>(h->n_rows, r0 + per);
+      const int64_t r1 = nch == 1 ? h->n_rows : std::min<int64_t>(h->n_rows, r0 + per);
       if (r1 <= r0) continue;
       if (nch == 1) {
         CK(launch_run(h, h->variant, h->x_stage.p, h->y_stage.p, s));
@@ -1045,6 +1087,7 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
                          vb * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, h->copy_stream));
     }
     CK(cudaStreamSynchronize(h->copy_stream));
+    CK(cudaStreamSynchronize(h->upload_stream));
     CK(cudaStreamSynchronize(s));
     return SPMV_OK;
   });

@@ -163,6 +163,11 @@ cudaError_t launch_row_len_max(int64_t n_rows, const int32_t *rowptr, int32_t *o
 cudaError_t launch_tile_max(int64_t n_rows, const int32_t *rowptr, int tile_rows, int32_t *out,
                             cudaStream_t s);
 
+// Largest column of each row chunk (host-buffer pipelining)
+cudaError_t launch_chunk_colmax(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                                const int64_t *bounds, int n_chunks, int32_t *out,
+                                cudaStream_t s);
+
 // Bandwidth probe
 cudaError_t launch_read_probe(const void *buf, int64_t bytes, int reps,
                               unsigned long long *sink, cudaStream_t s);

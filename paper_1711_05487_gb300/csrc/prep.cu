@@ -584,6 +584,31 @@ cudaError_t launch_tile_max(int64_t n_rows, const int32_t *rowptr, int tile_rows
   return cudaGetLastError();
 }
 
+// Largest column index used by rows [bounds[c], bounds[c+1]) for each of n_chunks chunks
+// (-1 for a chunk without nonzeros); out must hold n_chunks ints set to -1.
+__global__ void k_chunk_colmax(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                               const int64_t *bounds, int n_chunks, int32_t *out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_rows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int s = rowptr[i], e = rowptr[i + 1];
+    if (e <= s) continue;
+    int c = 0;
+    while (c + 1 < n_chunks && i >= bounds[c + 1]) ++c;
+    atomicMax(out + c, colind[e - 1]);
+  }
+}
+
+cudaError_t launch_chunk_colmax(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                                const int64_t *bounds, int n_chunks, int32_t *out,
+                                cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0xFF, sizeof(int32_t) * (size_t)n_chunks, s);
+  if (e != cudaSuccess || n_rows == 0) return e;
+  unsigned g = blocks_for(n_rows);
+  if (g > 4096u) g = 4096u;
+  k_chunk_colmax<<<g, kT, 0, s>>>(n_rows, rowptr, colind, bounds, n_chunks, out);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- bandwidth probe -----
 // Reads `bytes` (a multiple of 16) reps times with 128-bit streaming loads; the XOR of
 // everything read is stored only if it equals an impossible value, so the loads stay.

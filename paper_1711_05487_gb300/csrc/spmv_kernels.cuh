@@ -409,11 +409,30 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const RunArgs a) {
   for (int k = threadIdx.x; k < nrows_t; k += kMergeThreads)
     s_rowend[k] = __ldg(a.rowptr + row0 + 1 + k);
   if (threadIdx.x == 0) s_rowend[nrows_t] = INT_MAX;
-#pragma unroll 4
-  for (int k = threadIdx.x; k < nnz_t; k += kMergeThreads) {
-    const int j = nz0 + k;
-    s_val[k] = widen<AccT>(val[j]);
-    s_x[k] = (AccT)ldx<XL2>(x + __ldg(col + j), pol_x);
+  // nnz_t <= kMergeIpt * kMergeThreads: every thread stages at most kMergeIpt nonzeros; all
+  // column loads are issued first, then all value loads and x gathers, then the stores
+  {
+    int cj[kMergeIpt];
+#pragma unroll
+    for (int q = 0; q < kMergeIpt; ++q) {
+      const int k = q * kMergeThreads + (int)threadIdx.x;
+      cj[q] = k < nnz_t ? __ldg(col + nz0 + k) : 0;
+    }
+    AccT vv[kMergeIpt], xx[kMergeIpt];
+#pragma unroll
+    for (int q = 0; q < kMergeIpt; ++q) {
+      const int k = q * kMergeThreads + (int)threadIdx.x;
+      vv[q] = k < nnz_t ? widen<AccT>(val[nz0 + k]) : (AccT)0;
+      xx[q] = k < nnz_t ? (AccT)ldx<XL2>(x + cj[q], pol_x) : (AccT)0;
+    }
+#pragma unroll
+    for (int q = 0; q < kMergeIpt; ++q) {
+      const int k = q * kMergeThreads + (int)threadIdx.x;
+      if (k < nnz_t) {
+        s_val[k] = vv[q];
+        s_x[k] = xx[q];
+      }
+    }
   }
   __syncthreads();
 
