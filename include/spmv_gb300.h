@@ -278,6 +278,14 @@ spmv_status spmv_round_values(const double *in, void *out, int64_t n, spmv_dtype
 /* Reads (and clears) the handle's device error word: 0 none, 1 a bounded wait expired. */
 spmv_status spmv_get_last_device_error(spmv_handle_t h, int32_t *code);
 
+/* Failure-path self test of the bounded device waits the tile kernels use: launches one
+ * CTA that waits on an mbarrier phase nothing completes (transaction count armed, no copy
+ * issued) with a limit of limit_ns (1 ns .. 10 s). The wait gives up, the kernel records the
+ * expiry in the handle's error word and exits; the call then reads and clears the word and
+ * returns SPMV_ERR_TIMEOUT (SPMV_OK would mean the wait completed). The CUDA context stays
+ * usable. Synchronizes the stream. */
+spmv_status spmv_selftest_wait_timeout(spmv_handle_t h, int64_t limit_ns, spmv_stream_t stream);
+
 /* Device bytes held by the handle. */
 spmv_status spmv_get_device_bytes(spmv_handle_t h, int64_t *bytes);
 

@@ -109,6 +109,7 @@ _DECL = {
     "spmv_round_values": (_I32, [_P, _P, _I64, _I32, _P]),
     "spmv_get_last_device_error": (_I32, [_P, ctypes.POINTER(_I32)]),
     "spmv_get_device_bytes": (_I32, [_P, ctypes.POINTER(_I64)]),
+    "spmv_selftest_wait_timeout": (_I32, [_P, _I64, _P]),
     "spmv_status_string": (ctypes.c_char_p, [_I32]),
     "spmv_mlp_inputs": (_I32, [_P, _I64, _P, _P, _P, _P]),
     "spmv_mlp_logits": (_I32, [_P, _P, _I64, _P, _P, _P]),
@@ -285,6 +286,11 @@ def spmv_get_last_device_error(h) -> int:
     c = _I32()
     _call("spmv_get_last_device_error", h, ctypes.byref(c))
     return c.value
+
+
+def spmv_selftest_wait_timeout(h, limit_ns, stream=0) -> int:
+    """Returns the raw status: SPMV_ERR_TIMEOUT (6) when the bounded wait expired."""
+    return int(lib().spmv_selftest_wait_timeout(h, limit_ns, stream))
 
 
 def spmv_get_device_bytes(h) -> int:

@@ -1304,6 +1304,20 @@ spmv_status spmv_get_last_device_error(spmv_handle_t h, int32_t *code) {
   });
 }
 
+spmv_status spmv_selftest_wait_timeout(spmv_handle_t h, int64_t limit_ns,
+                                       spmv_stream_t stream) {
+  if (!h || limit_ns <= 0 || limit_ns > 10000000000LL) return SPMV_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return guarded([&]() -> spmv_status {
+    CK(launch_selftest_wait((uint64_t)limit_ns, h->d_err.as<int32_t>(), s));
+    CK(cudaStreamSynchronize(s));
+    int32_t c = 0;
+    CK(cudaMemcpy(&c, h->d_err.p, 4, cudaMemcpyDeviceToHost));
+    CK(cudaMemset(h->d_err.p, 0, 4));
+    return c ? SPMV_ERR_TIMEOUT : SPMV_OK;
+  });
+}
+
 spmv_status spmv_get_device_bytes(spmv_handle_t h, int64_t *bytes) {
   if (!h || !bytes) return SPMV_ERR_ARG;
   int64_t t = 0;

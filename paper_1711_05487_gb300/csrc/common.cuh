@@ -206,14 +206,16 @@ __device__ __forceinline__ uint64_t globaltimer_ns();
 
 // Waits for phase `parity` of the barrier for at most limit_ns of wall time; false when
 // the limit expired (the caller records the error and must not read the staged data).
+// Also bounded by an iteration count, so that the wait ends even if the clock stalled.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
                                                   uint64_t limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
-  for (;;) {
+  for (uint32_t it = 0; it < (1u << 26); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (globaltimer_ns() - t0 > limit_ns) return false;
   }
+  return false;
 }
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {

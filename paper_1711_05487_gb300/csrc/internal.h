@@ -168,6 +168,9 @@ cudaError_t launch_chunk_colmax(int64_t n_rows, const int32_t *rowptr, const int
                                 const int64_t *bounds, int n_chunks, int32_t *out,
                                 cudaStream_t s);
 
+// Failure-path self test (bounded wait that expires)
+cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t *err, cudaStream_t s);
+
 // Bandwidth probe
 cudaError_t launch_read_probe(const void *buf, int64_t bytes, int reps,
                               unsigned long long *sink, cudaStream_t s);

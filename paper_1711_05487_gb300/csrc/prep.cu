@@ -609,6 +609,25 @@ cudaError_t launch_chunk_colmax(int64_t n_rows, const int32_t *rowptr, const int
   return cudaGetLastError();
 }
 
+// Failure-path self test: waits (bounded) on an mbarrier phase that nothing completes -- the
+// transaction count is armed but no copy is issued -- and records the expiry in err exactly
+// as the SpMV kernels do. No asynchronous copy is in flight when the CTA exits.
+__global__ void k_selftest_wait(uint64_t limit_ns, int32_t *err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_expect_tx(&bar, 16);
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_bounded(&bar, 0, limit_ns);
+  if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicExch(err, 1);
+}
+
+cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t *err, cudaStream_t s) {
+  k_selftest_wait<<<1, 32, 0, s>>>(limit_ns, err);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- bandwidth probe -----
 // Reads `bytes` (a multiple of 16) reps times with 128-bit streaming loads; the XOR of
 // everything read is stored only if it equals an impossible value, so the loads stay.

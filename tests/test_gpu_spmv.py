@@ -204,3 +204,16 @@ def test_runs_are_reproducible(api, torch):
         a = A.run(x).clone()
         b = A.run(x)
         assert torch.equal(a, b), v
+
+
+def test_bounded_wait_expires_and_context_survives(api, torch):
+    """A wait on an mbarrier phase nothing completes gives up after its limit, the error is
+    reported to the host, and the next SpMV on the same context is correct."""
+    from paper_1711_05487_gb300 import _abi
+    m = MATS["st27_12"]
+    A = api.SpmvMatrix.from_csr(m)
+    assert _abi.spmv_selftest_wait_timeout(A.handle, 2_000_000) == 6     # 2 ms limit
+    assert _abi.spmv_get_last_device_error(A.handle) == 0                  # cleared
+    A.set_variant(vec=1, vs=1)
+    x64 = synth.uniform_vector(m.n_cols, 15)
+    check_spmv(m, x64, A.run(_dev(torch, x64)).cpu().numpy(), TAU["f64"], "after timeout")
