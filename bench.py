@@ -154,7 +154,7 @@ def measured_traffic(workload: str, variant) -> dict | None:
 
 
 def dtype_bytes(code):
-    return {0: 8, 1: 4, 2: 2}[code]
+    return {0: 8, 1: 4, 2: 2, 3: 8}[code]
 
 
 def alg_bytes(n_rows, n_cols, nnz, variant, storage, vec):
@@ -282,7 +282,8 @@ def run_ours(args, rank, world):
     # reduced-precision value storage on the same matrix (FP64 originals rounded once)
     extra = {}
     if m.val.dtype == np.float64 and not args.quick:
-        for st, vt, at in (("f32", "f64", "f64"), ("f32", "f32", "f32"), ("bf16", "f32", "f32")):
+        for st, vt, at in (("df64", "f64", "df64"), ("f32", "f64", "f64"), ("f32", "f32", "f32"),
+                           ("bf16", "f32", "f32")):
             A.set_precision(st, vt, at, stream=stream)
             r2 = A.tune("profile", stream=stream)
             xv = x.to(torch.float64 if vt == "f64" else torch.float32)
@@ -308,7 +309,7 @@ def run_ours(args, rank, world):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {0: "f64", 1: "f32", 2: "bf16"}[storage],
+        "dtype": {0: "f64", 1: "f32", 2: "bf16", 3: "df64"}[storage],
         "data": "synthetic (seeded)",
         "config": {"workload": args.workload, "desc": wl["desc"], "n_rows": m.n_rows,
                    "nnz": m.nnz, "parallelism": f"replicas x{world}",

@@ -48,7 +48,12 @@ typedef enum {
   SPMV_ERR_TOO_LARGE = 9          /* problem larger than a fixed-size buffer allows     */
 } spmv_status;
 
-typedef enum { SPMV_F64 = 0, SPMV_F32 = 1, SPMV_BF16 = 2 } spmv_dtype;
+/* SPMV_DF64 ("double-float") carries an FP64 number as the unevaluated sum hi + lo of two
+ * FP32 numbers: hi = the top 24 significant bits, lo = the next 23 (both truncated), so
+ * |v - hi - lo| < 2^-46 |v|; zero splits to (+-0, 0), and a nonzero outside [2^-40, 2^41),
+ * an infinity or a NaN to (NaN, 0). As a storage / accumulation type it runs FP64 SpMV on
+ * the FP32 pipe (see spmv_set_precision); it is not an input type of spmv_create. */
+typedef enum { SPMV_F64 = 0, SPMV_F32 = 1, SPMV_BF16 = 2, SPMV_DF64 = 3 } spmv_dtype;
 
 typedef enum {
   SPMV_TUNE_PROFILE = 0,  /* Section III-C: micro-benchmarks + Fig. 3 rules            */
@@ -130,7 +135,17 @@ spmv_status spmv_destroy(spmv_handle_t h);
 /* Value storage precision (build addition): storage in F64 / F32 / BF16, x and y in
  * vec_type (F64 or F32), products accumulated in acc_type (F64 or F32). Conversion is
  * round-to-nearest-even straight from the input values. Offered: storage F64 with
- * vec = acc = F64; storage F32 or BF16 with (vec, acc) in {(F64,F64),(F32,F32),(F32,F64)}.
+ * vec = acc = F64; storage F32 or BF16 with (vec, acc) in {(F64,F64),(F32,F32),(F32,F64)};
+ * storage DF64 with vec = F64, acc = DF64 (FP64 input values only).
+ * DF64 (a GB300 answer to the CMP class, not in the paper): GB300's FP64 pipe is about 1/64
+ * of its FP32 pipe, so width-1 row variants (vs = 1) compute each product and the row sum
+ * in double-float FP32 arithmetic from value pairs split once here and x split on every
+ * call: each row ends within about 8e-13 of sum_j |a_ij x_j| (inside the FP64 bound of
+ * 1e-12), not bit-identical to FP64 FMAs. Rows longer than 32 nonzeros, or meeting a value
+ * or x element that does not split (see SPMV_DF64), are recomputed with FP64 FMAs; every
+ * other variant runs the FP64 kernels on the FP64 values. The handle keeps the pairs
+ * (8 bytes per nonzero) and an 8-byte-per-column split x beside the FP64 values, so runs
+ * of one DF64 handle must not overlap in time (one stream, or ordered streams).
  * Invalidates the tuned variant (spmv_tune or spmv_set_variant must follow). */
 spmv_status spmv_set_precision(spmv_handle_t h, spmv_dtype storage, spmv_dtype vec_type,
                                spmv_dtype acc_type, spmv_stream_t stream);
@@ -271,7 +286,8 @@ spmv_status spmv_validate_csr(int64_t n_rows, int64_t n_cols, int64_t nnz,
                               spmv_stream_t stream);
 
 /* FP64 -> storage dtype conversion (round to nearest even, no double rounding for BF16)
- * of n device values into out (device). */
+ * of n device values into out (device). to = SPMV_DF64 writes n (hi, lo) FP32 pairs
+ * (8 bytes each) split as SPMV_DF64 describes. */
 spmv_status spmv_round_values(const double *in, void *out, int64_t n, spmv_dtype to,
                               spmv_stream_t stream);
 

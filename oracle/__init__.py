@@ -73,6 +73,8 @@ def _declare(L):
     L.oracle_round_f32.restype = None
     L.oracle_round_bf16.argtypes = [_P, _P, _I64]
     L.oracle_round_bf16.restype = None
+    L.oracle_df_split.argtypes = [_P, _P, _I64]
+    L.oracle_df_split.restype = None
     L.oracle_delta16_encode.argtypes = [_I64, _P, _P, _P, _P, _P]
     L.oracle_delta16_encode.restype = _I64
     L.oracle_delta16_decode.argtypes = [_I64, _P, _P, _P, _P, _P]
@@ -164,6 +166,14 @@ def round_bf16_bits(v) -> np.ndarray:
     a = _c(v, np.float64)
     out = np.empty(a.shape[0], dtype=np.uint16)
     lib().oracle_round_bf16(_p(a), _p(out), a.shape[0])
+    return out
+
+
+def df_split_bits(v) -> np.ndarray:
+    """Double-float split: uint32 array (n, 2) of FP32 bit patterns (hi, lo)."""
+    a = _c(v, np.float64)
+    out = np.empty((a.shape[0], 2), dtype=np.uint32)
+    lib().oracle_df_split(_p(a), _p(out), a.shape[0])
     return out
 
 

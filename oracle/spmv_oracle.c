@@ -151,6 +151,49 @@ void oracle_round_bf16(const double *in, uint16_t *out, int64_t n) {
   }
 }
 
+/* Double-float split of FP64 values (the library's DF64 storage; no counterpart in the
+ * paper): v = hi + lo + r with hi = v truncated toward zero to 24 significant bits and
+ * lo = (v - hi) truncated toward zero at the quantum 2^(e - 46), e = floor(log2 |v|), so
+ * |r| < 2^(e - 46). Both are FP32 numbers, returned as bit patterns; a zero lo is +0.
+ * Zero gives (+-0, 0);
+ * a nonzero with e outside [-40, 40], an infinity or a NaN gives (0x7FC00000, 0). The
+ * subtractions below are exact: each operand and result is a multiple of the quantum and
+ * below 2^53 quanta.                                                                     */
+static uint32_t f32_bits(float f) {
+  uint32_t u;
+  memcpy(&u, &f, sizeof u);
+  return u;
+}
+
+void oracle_df_split(const double *in, uint32_t *out, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) {
+    const double v = in[i];
+    uint32_t hi_bits, lo_bits = 0;
+    if (v == 0.0) {
+      hi_bits = signbit(v) ? 0x80000000u : 0u;
+    } else if (!isfinite(v)) {
+      hi_bits = 0x7FC00000u;
+    } else {
+      int e2;
+      (void)frexp(v, &e2);
+      const int e = e2 - 1;                        /* 2^e <= |v| < 2^(e+1) */
+      if (e < -40 || e > 40) {
+        hi_bits = 0x7FC00000u;
+      } else {
+        const double q_hi = ldexp(1.0, e - 23);    /* 24 significant bits */
+        const double hi = trunc(v / q_hi) * q_hi;
+        const double q_lo = ldexp(1.0, e - 46);    /* 23 more bits */
+        double lo = trunc((v - hi) / q_lo) * q_lo;
+        if (lo == 0.0) lo = 0.0;                   /* a zero low part is +0 */
+        hi_bits = f32_bits((float)hi);             /* exact: hi, lo fit FP32 */
+        lo_bits = f32_bits((float)lo);
+      }
+    }
+    out[2 * i] = hi_bits;
+    out[2 * i + 1] = lo_bits;
+  }
+}
+
 /* ---------------------------------------------------------------------------------- */
 /* Delta-indexed column indices (Section III-E, MB row of Table II): each column index is
  * stored as its distance to the previous column of the same row, in 16 bits wherever

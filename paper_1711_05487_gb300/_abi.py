@@ -19,7 +19,7 @@ _U32 = ctypes.c_uint32
 _D = ctypes.c_double
 _F = ctypes.c_float
 
-SPMV_F64, SPMV_F32, SPMV_BF16 = 0, 1, 2
+SPMV_F64, SPMV_F32, SPMV_BF16, SPMV_DF64 = 0, 1, 2, 3
 TUNE_PROFILE, TUNE_FEATURES, TUNE_LEARNED, TUNE_FIXED = 0, 1, 2, 3
 CLASS_MB, CLASS_ML, CLASS_IMB, CLASS_CMP = 1, 2, 4, 8
 NUM_FEATURES = 14

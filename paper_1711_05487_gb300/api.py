@@ -12,12 +12,14 @@ import numpy as np
 import torch
 
 from . import _abi
-from ._abi import (SPMV_BF16, SPMV_F32, SPMV_F64, TUNE_FEATURES, TUNE_FIXED, TUNE_LEARNED,
+from ._abi import (SPMV_BF16, SPMV_DF64, SPMV_F32, SPMV_F64, TUNE_FEATURES, TUNE_FIXED, TUNE_LEARNED,
                    TUNE_PROFILE, spmv_variant)
 
 DTYPE_CODE = {torch.float64: SPMV_F64, torch.float32: SPMV_F32, torch.bfloat16: SPMV_BF16,
-              "f64": SPMV_F64, "f32": SPMV_F32, "bf16": SPMV_BF16}
-TORCH_DTYPE = {SPMV_F64: torch.float64, SPMV_F32: torch.float32, SPMV_BF16: torch.bfloat16}
+              "f64": SPMV_F64, "f32": SPMV_F32, "bf16": SPMV_BF16, "df64": SPMV_DF64}
+# DF64 handles keep and export their FP64 values; x and y are FP64
+TORCH_DTYPE = {SPMV_F64: torch.float64, SPMV_F32: torch.float32, SPMV_BF16: torch.bfloat16,
+               SPMV_DF64: torch.float64}
 MODES = {"profile": TUNE_PROFILE, "features": TUNE_FEATURES, "learned": TUNE_LEARNED,
          "fixed": TUNE_FIXED}
 CLASS_NAMES = ((1, "MB"), (2, "ML"), (4, "IMB"), (8, "CMP"))

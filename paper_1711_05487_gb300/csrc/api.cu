@@ -27,8 +27,12 @@ typedef unsigned __int128 u128;
 // the next chunk needs and the download of the previous chunk's y overlap the computation.
 constexpr int kHostChunks = 8;
 
-inline size_t dtype_bytes(spmv_dtype t) { return t == SPMV_F64 ? 8 : (t == SPMV_F32 ? 4 : 2); }
+inline size_t dtype_bytes(spmv_dtype t) {
+  return (t == SPMV_F64 || t == SPMV_DF64) ? 8 : (t == SPMV_F32 ? 4 : 2);
+}
+// input value types (spmv_create); SPMV_DF64 is a storage / arithmetic choice only
 inline bool valid_dtype(int t) { return t == SPMV_F64 || t == SPMV_F32 || t == SPMV_BF16; }
+inline bool valid_precision_dtype(int t) { return valid_dtype(t) || t == SPMV_DF64; }
 
 struct CudaFail {
   cudaError_t e;
@@ -124,6 +128,7 @@ struct spmv_matrix {
   int64_t n_rows = 0, n_cols = 0, nnz = 0;
   spmv_dtype in_type = SPMV_F64, storage = SPMV_F64, vec = SPMV_F64, acc = SPMV_F64;
   DevBuf rowptr, colind, val_in, val_store;
+  DevBuf val_df, x_df;         // storage SPMV_DF64: value pairs, split x (per call)
   // optimization-pool data
   DevBuf dbase, delta, esc;
   int64_t n_esc = 0;
@@ -186,6 +191,8 @@ RunArgs run_args(const spmv_matrix *h, const void *x, void *y) {
   a.tile_rows = h->tile_rows;
   a.tile_pipe = h->tile_pipe;
   a.err = h->d_err.as<int32_t>();
+  a.val_df = h->val_df.p;
+  a.x_df = h->x_df.p;
   return a;
 }
 
@@ -746,7 +753,14 @@ void default_types(spmv_dtype in, spmv_dtype *st, spmv_dtype *vec, spmv_dtype *a
 
 void install_storage(spmv_matrix *h, cudaStream_t s) {
   h->val_store.release();
-  if (h->storage != h->in_type) {
+  h->val_df.release();
+  h->x_df.release();
+  if (h->storage == SPMV_DF64) {
+    // the FP64 input values stay the values of every non-double-float kernel
+    h->val_df.alloc(8 * (size_t)h->nnz, 8, s);
+    CK(launch_df_split(h->val_in.as<double>(), h->val_df.p, 0, h->nnz, s));
+    h->x_df.alloc(8 * (size_t)std::max<int64_t>(h->n_cols, 1), 8, s);
+  } else if (h->storage != h->in_type) {
     const size_t eb = dtype_bytes(h->storage);
     h->val_store.alloc(eb * (size_t)h->nnz, eb, s);
     CK(launch_convert_values(h->val_in.p, h->in_type, h->val_store.p, h->storage, h->nnz, s));
@@ -874,9 +888,11 @@ spmv_status spmv_destroy(spmv_handle_t h) {
 spmv_status spmv_set_precision(spmv_handle_t h, spmv_dtype storage, spmv_dtype vec_type,
                                spmv_dtype acc_type, spmv_stream_t stream) {
   if (!h) return SPMV_ERR_ARG;
-  if (!valid_dtype(storage) || !valid_dtype(vec_type) || !valid_dtype(acc_type))
+  if (!valid_precision_dtype(storage) || !valid_precision_dtype(vec_type) ||
+      !valid_precision_dtype(acc_type))
     return SPMV_ERR_UNSUPPORTED_DTYPE;
   if (!combo_offered(storage, vec_type, acc_type)) return SPMV_ERR_UNSUPPORTED_DTYPE;
+  if (storage == SPMV_DF64 && h->in_type != SPMV_F64) return SPMV_ERR_UNSUPPORTED_DTYPE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return guarded([&]() -> spmv_status {
     if (storage != h->storage) {
@@ -1075,6 +1091,8 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
         CK(launch_run(h, h->variant, h->x_stage.p, h->y_stage.p, s));
       } else {
         RunArgs a = run_args(h, h->x_stage.p, static_cast<char *>(h->y_stage.p) + vb * (size_t)r0);
+        a.x_split_lo = c == 0 ? 0 : h->x_need[c - 1];   // x elements that arrived for chunk c
+        a.x_split_hi = need;
         a.n_rows = r1 - r0;
         a.rowptr += r0;
         if (a.dbase) a.dbase += r0;
@@ -1287,7 +1305,8 @@ spmv_status spmv_validate_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const
 spmv_status spmv_round_values(const double *in, void *out, int64_t n, spmv_dtype to,
                               spmv_stream_t stream) {
   if ((n > 0 && (!in || !out)) || n < 0) return SPMV_ERR_ARG;
-  if (!valid_dtype(to)) return SPMV_ERR_UNSUPPORTED_DTYPE;
+  if (!valid_precision_dtype(to)) return SPMV_ERR_UNSUPPORTED_DTYPE;
+  if (to == SPMV_DF64) return map_err(launch_df_split(in, out, 0, n, static_cast<cudaStream_t>(stream)));
   return map_err(launch_round_values(in, out, n, to, static_cast<cudaStream_t>(stream)));
 }
 
@@ -1480,6 +1499,7 @@ spmv_status handle_info(spmv_handle_t h, const int32_t **rowptr, const int32_t *
 
 const KernelSet *kernel_set(spmv_dtype val, spmv_dtype vec, spmv_dtype acc) {
   if (val == SPMV_F64) return (vec == SPMV_F64 && acc == SPMV_F64) ? kernel_set_f64_dd() : nullptr;
+  if (val == SPMV_DF64) return (vec == SPMV_F64 && acc == SPMV_DF64) ? kernel_set_f64_df() : nullptr;
   const bool dd = vec == SPMV_F64 && acc == SPMV_F64;
   const bool ff = vec == SPMV_F32 && acc == SPMV_F32;
   const bool fd = vec == SPMV_F32 && acc == SPMV_F64;

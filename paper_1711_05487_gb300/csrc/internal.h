@@ -40,6 +40,11 @@ struct RunArgs {
   int32_t tile_rows = 0;             // rows (= threads) per tile: 32, 64 or 128
   int32_t tile_pipe = 0;             // 1: persistent CTAs with two staged tiles in flight
   int32_t *err = nullptr;            // device error word (bounded waits)
+  // double-float FP64 (storage SPMV_DF64): value pairs, the split x and the range of x
+  // elements to split before the launch ([lo, hi), hi < 0 meaning n_cols)
+  const void *val_df = nullptr;
+  void *x_df = nullptr;
+  int64_t x_split_lo = 0, x_split_hi = -1;
 };
 
 // Thread-per-row tile kernel geometry: at most this many rows (= threads) per CTA.
@@ -117,7 +122,11 @@ SPMV_DECLARE_SET(f32_fd)
 SPMV_DECLARE_SET(bf16_dd)
 SPMV_DECLARE_SET(bf16_ff)
 SPMV_DECLARE_SET(bf16_fd)
+SPMV_DECLARE_SET(f64_df)
 #undef SPMV_DECLARE_SET
+
+// Splits in[lo, hi) into double-float pairs out[lo, hi) (spmv_df.cu).
+cudaError_t launch_df_split(const double *in, void *out, int64_t lo, int64_t hi, cudaStream_t s);
 
 // ------------------------------------------------------------- preprocessing (prep.cu)
 cudaError_t launch_validate(int64_t n_rows, int64_t n_cols, int64_t nnz, const int32_t *rowptr,

@@ -1,0 +1,241 @@
+// FP64 SpMV whose products and sums run in the FP32 pipe as double-float arithmetic.
+//
+// GB300's FP64 pipe retires about 0.5 T FMA/s against 33 T for FP32, so FP64 SpMV with one
+// FMA per nonzero is compute bound (the CMP class of Section III-A) on this GPU. Here every
+// FP64 number is carried as an unevaluated sum hi + lo of two FP32 numbers:
+//   - split: hi holds the top 24 significant bits of v (exact truncation), lo the next 23
+//     (truncated), so |v - hi - lo| < 2^-46 |v|. The split is integer bit work; values are
+//     split once when the precision is installed, x once per call;
+//   - product: hi_v*hi_x is taken exactly as a rounded product and its error (fmaf), plus
+//     the cross terms hi_v*lo_x + lo_v*hi_x; lo_v*lo_x (< 2^-46 |v x|) is dropped. Together
+//     with the split, each product is within about 6 * 2^-46 |v x| of v*x;
+//   - sum: the row accumulator (s, t) is updated with an error-free two-sum of the high parts
+//     (Knuth, TAOCP vol. 2, 4.2.2), the low parts added to its error, and a fast two-sum
+//     renormalisation (Dekker 1971). Each step errs by at most about 6 u^2 (|s| + |p|),
+//     u = 2^-24, so a row of n <= kDfMaxRow products ends within about
+//     6 u^2 (n + 1) + 6 * 2^-46 < 8e-13 of sum_j |a_ij x_j|.
+// Rows longer than kDfMaxRow, and rows that meet a value or an x element outside
+// [2^-40, 2^41) (split to a NaN marker, so the double-float sum is not finite), are
+// recomputed with native FP64 FMAs from the original FP64 values.
+#include "spmv_kernels.cuh"
+
+namespace spmv {
+
+namespace {
+constexpr int kDfMaxRow = 32;
+constexpr uint32_t kDfNanHi = 0x7FC00000u;   // quiet NaN: marks an unsplittable number
+}  // namespace
+
+// Split of one FP64 number into FP32 bit patterns (hi, lo), integer operations only.
+// Zero gives (+-0, 0); a nonzero outside [2^-40, 2^41) (biased exponent outside
+// [983, 1063]), an infinity or a NaN gives (NaN, 0).
+__device__ __forceinline__ uint2 df_split_bits(double d) {
+  const uint32_t H = (uint32_t)((unsigned long long)__double_as_longlong(d) >> 32);
+  const uint32_t L = (uint32_t)(unsigned long long)__double_as_longlong(d);
+  if ((H & 0x7FFFFFFFu) == 0u && L == 0u) return make_uint2(H, 0u);
+  const uint32_t eb = (H >> 20) & 0x7FFu;
+  if (eb - 983u > 80u) return make_uint2(kDfNanHi, 0u);
+  // (H:L) << 3 puts the low 9 exponent bits and the top 23 fraction bits in one word; the
+  // rebias 1023 -> 127 is a subtraction of 896 in the exponent field, taken modulo 2^9
+  // (the result lies in [87, 167], so its ninth bit is zero)
+  const uint32_t hi = (__funnelshift_l(L, H, 3) - (384u << 23)) | (H & 0x80000000u);
+  // lo = next 23 fraction bits scaled by 2^(e - 46): built as (1.m - 1) * 2^(e - 23), an
+  // exact FP32 subtraction of two numbers carrying hi's sign
+  const uint32_t base = (hi & 0xFF800000u) - (23u << 23);
+  const uint32_t m = (L >> 6) & 0x7FFFFFu;
+  const float lo = __fsub_rn(__uint_as_float(base | m), __uint_as_float(base));
+  return make_uint2(hi, __float_as_uint(lo));
+}
+
+__global__ void k_df_split(const double *__restrict__ in, uint2 *__restrict__ out, int64_t lo,
+                           int64_t hi) {
+  for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = df_split_bits(in[i]);
+}
+
+cudaError_t launch_df_split(const double *in, void *out, int64_t lo, int64_t hi,
+                            cudaStream_t s) {
+  if (hi <= lo) return cudaSuccess;
+  int64_t g = (hi - lo + 255) / 256;
+  if (g > 152 * 8) g = 152 * 8;
+  k_df_split<<<(unsigned)g, 256, 0, s>>>(in, static_cast<uint2 *>(out), lo, hi);
+  return cudaGetLastError();
+}
+
+namespace {
+
+template <bool XL2> __device__ __forceinline__ uint2 ldx_pair(const uint2 *p, uint64_t pol) {
+  if constexpr (XL2) {
+    uint2 r;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                 : "=r"(r.x), "=r"(r.y)
+                 : "l"(p), "l"(pol));
+    return r;
+  } else {
+    return __ldg(p);
+  }
+}
+
+// (s, t) += (p, q); the _rn intrinsics keep each operation as written.
+__device__ __forceinline__ void df_add(float &s, float &t, float p, float q) {
+  const float S = __fadd_rn(s, p);
+  const float b = __fsub_rn(S, s);
+  float e = __fadd_rn(__fsub_rn(s, __fsub_rn(S, b)), __fsub_rn(p, b));
+  e = __fadd_rn(e, __fadd_rn(t, q));
+  s = __fadd_rn(S, e);
+  t = __fsub_rn(e, __fsub_rn(s, S));
+}
+
+// v * x as (p, q): p = fl(hi_v hi_x), q = its rounding error + hi_v lo_x + lo_v hi_x.
+__device__ __forceinline__ void df_prod(uint2 v, uint2 xv, float &p, float &q) {
+  const float vh = __uint_as_float(v.x), vl = __uint_as_float(v.y);
+  const float xh = __uint_as_float(xv.x), xl = __uint_as_float(xv.y);
+  p = __fmul_rn(vh, xh);
+  const float pe = __fmaf_rn(vh, xh, -p);
+  q = __fadd_rn(__fmaf_rn(vh, xl, __fmul_rn(vl, xh)), pe);
+}
+
+}  // namespace
+
+// Thread-per-row tiles as in the FP64 kernel: a tile's value pairs and column indices are
+// staged in shared memory by one bulk copy each; each thread then walks its row.
+template <bool D16, bool XL2>
+__global__ void __launch_bounds__(kTileRows) k_rowtile_df(const RunArgs a) {
+  using IdxT = typename std::conditional<D16, uint16_t, int32_t>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  const int rows = (int)blockDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * rows;
+  const int64_t r1 = min(r0 + (int64_t)rows, a.n_rows);
+  const int s0 = __ldg(a.rowptr + r0), s1 = __ldg(a.rowptr + r1);
+  const int a0 = s0 & ~7;
+  const int nc = ((s1 - a0) + 7) & ~7;
+  const double *__restrict__ val = static_cast<const double *>(a.val);
+  const uint2 *__restrict__ vdf = static_cast<const uint2 *>(a.val_df);
+  const double *__restrict__ x = static_cast<const double *>(a.x);
+  const uint2 *__restrict__ xdf = static_cast<const uint2 *>(a.x_df);
+  double *__restrict__ y = static_cast<double *>(a.y);
+  uint64_t pol_x = 0;
+  if constexpr (XL2) pol_x = policy_evict_last();
+  const int64_t row = r0 + threadIdx.x;
+  if (nc > a.tile_cap) {
+    tile_direct<double, double, double, D16, XL2>(a, r0, r1, x, y, pol_x);
+    return;
+  }
+  uint2 *sval = reinterpret_cast<uint2 *>(smem + 16);
+  IdxT *sidx = reinterpret_cast<IdxT *>(smem + 16 + (size_t)a.tile_cap * sizeof(uint2));
+  const IdxT *gidx;
+  if constexpr (D16) gidx = a.delta;
+  else gidx = a.colind;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    if (nc > 0) {
+      const uint64_t pol = policy_evict_first();
+      const uint32_t bv = (uint32_t)nc * 8u;
+      const uint32_t bi = (uint32_t)nc * (uint32_t)sizeof(IdxT);
+      mbar_expect_tx(bar, bv + bi);
+      bulk_g2s(sval, vdf + a0, bv, bar, pol);
+      bulk_g2s(sidx, gidx + a0, bi, bar, pol);
+    }
+  }
+  int s = 0, e = 0;
+  int32_t base = 0;
+  if (row < r1) {
+    s = __ldg(a.rowptr + row);
+    e = __ldg(a.rowptr + row + 1);
+    if constexpr (D16) base = __ldg(a.dbase + row);
+  }
+  __syncthreads();
+  if (nc > 0) {
+    if (!mbar_wait_bounded(bar, 0, kWaitLimitNs)) {
+      if (threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
+      mbar_wait_bounded(bar, 0, kWaitLimitNs);
+      return;
+    }
+  }
+  if (row >= r1) return;
+  const int o = s - a0, len = e - s;
+  const int32_t *ec = nullptr;
+  if constexpr (D16) {
+    if (base < 0) ec = a.esc + (-(int64_t)base - 1);
+  }
+  int c = base;
+  auto column = [&](int k) -> int {
+    if constexpr (D16) {
+      if (ec) return __ldg(ec + k);
+      c += (int)sidx[o + k];
+      return c;
+    } else {
+      return (int)sidx[o + k];
+    }
+  };
+  if (len <= kDfMaxRow) {
+    float sh = 0.0f, sl = 0.0f;
+    int k = 0;
+    for (; k + 8 <= len; k += 8) {
+      uint2 xv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) xv[q] = ldx_pair<XL2>(xdf + column(k + q), pol_x);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float p, pq;
+        df_prod(sval[o + k + q], xv[q], p, pq);
+        df_add(sh, sl, p, pq);
+      }
+    }
+    for (; k < len; ++k) {
+      float p, pq;
+      df_prod(sval[o + k], ldx_pair<XL2>(xdf + column(k), pol_x), p, pq);
+      df_add(sh, sl, p, pq);
+    }
+    if (isfinite(sh)) {
+      y[row] = (double)sh + (double)sl;
+      return;
+    }
+    c = base;   // restart the delta decode for the FP64 pass
+  }
+  double acc = 0.0;
+  for (int k = 0; k < len; ++k) acc = fma(__ldg(val + s + k), ldx<XL2>(x + column(k), pol_x), acc);
+  y[row] = acc;
+}
+
+namespace {
+
+template <bool D16, bool XL2> cudaError_t launch_rowtile_df_k(const RunArgs &a, cudaStream_t s) {
+  static int configured = 0;
+  const int rows = a.tile_rows > 0 ? a.tile_rows : kTileRows;
+  const size_t smem = 16 + (size_t)a.tile_cap * (8 + (D16 ? 2 : 4));
+  cudaError_t e = ensure_smem(k_rowtile_df<D16, XL2>, smem, configured);
+  if (e != cudaSuccess) return e;
+  const unsigned g = (unsigned)((a.n_rows + rows - 1) / rows);
+  k_rowtile_df<D16, XL2><<<g, rows, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Width-1 row variants run the double-float tile kernel (one tile per CTA, whatever
+// tile_pipe says); every other variant runs the native FP64 kernels on the FP64 values.
+cudaError_t launch_spmv_df(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
+  if (a.n_rows == 0) return cudaSuccess;
+  if (v.partition != 0 || v.vs != 1) return kernel_set_f64_dd()->spmv(v, a, s);
+  const int64_t hi = a.x_split_hi >= 0 ? a.x_split_hi : a.n_cols;
+  cudaError_t e = launch_df_split(static_cast<const double *>(a.x), a.x_df, a.x_split_lo, hi, s);
+  if (e != cudaSuccess) return e;
+  const bool d16 = v.index == 1, xl2 = v.xpath != 0;
+  if (d16) return xl2 ? launch_rowtile_df_k<true, true>(a, s) : launch_rowtile_df_k<true, false>(a, s);
+  return xl2 ? launch_rowtile_df_k<false, true>(a, s) : launch_rowtile_df_k<false, false>(a, s);
+}
+
+}  // namespace
+
+const KernelSet *kernel_set_f64_df() {
+  static const KernelSet ks = [] {
+    const KernelSet *f64 = kernel_set_f64_dd();
+    KernelSet k = *f64;
+    k.spmv = &launch_spmv_df;
+    return k;
+  }();
+  return &ks;
+}
+
+}  // namespace spmv

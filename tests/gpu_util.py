@@ -5,7 +5,7 @@ import pytest
 import oracle
 
 # Tolerances on |y_gpu - y_oracle| <= tau * sum_j |a_ij x_j| per row, by value storage
-TAU = {"f64": 1e-12, "f32": 2e-6, "bf16": 8e-3}
+TAU = {"f64": 1e-12, "df64": 1e-12, "f32": 2e-6, "bf16": 8e-3}
 
 
 def torch_cuda():
@@ -17,7 +17,7 @@ def torch_cuda():
 
 def stored_values(val64: np.ndarray, storage: str) -> np.ndarray:
     """The values the GPU multiplies with, widened exactly to FP64 (oracle rounding)."""
-    if storage == "f64":
+    if storage in ("f64", "df64"):
         return val64.astype(np.float64)
     if storage == "f32":
         return oracle.round_f32(val64).astype(np.float64)

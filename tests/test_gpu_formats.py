@@ -80,6 +80,20 @@ def test_value_rounding_bit_exact(abi, torch):
     assert np.array_equal(o16.cpu().numpy().view(np.uint16), oracle.round_bf16_bits(v))
 
 
+def test_df_split_bit_exact(abi, torch):
+    """Double-float value pairs (DF64 storage) equal the oracle's split bit for bit."""
+    rng = np.random.default_rng(31)
+    v = np.concatenate([rng.standard_normal(200_000) * 2.0 ** rng.integers(-48, 48, 200_000),
+                        [0.0, -0.0, 1.0, 1 + 2 ** -30, 1 + 2 ** -52, -3.75, 2.0 ** -40,
+                         2.0 ** 41, 2.0 ** 41 - 2.0 ** -12, 2.0 ** -41, 1e-310, 1e308,
+                         np.inf, -np.inf, np.nan, -(1 + 2 ** -46)]])
+    vin = torch.from_numpy(v).cuda()
+    out = torch.empty((v.size, 2), dtype=torch.int32, device="cuda")
+    abi.spmv_round_values(vin.data_ptr(), out.data_ptr(), v.size, abi.SPMV_DF64, 0)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), oracle.df_split_bits(v))
+
+
 def test_validation_codes_match_oracle(abi, torch):
     cases = [
         (2, 4, [0, 2, 3], [0, 3, 1]),

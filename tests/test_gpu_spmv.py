@@ -112,7 +112,8 @@ def test_empty_matrix_and_zero_rows(api, torch):
 
 
 PRECISIONS = [("f32", "f64", "f64"), ("f32", "f32", "f64"), ("bf16", "f64", "f64"),
-              ("bf16", "f32", "f64"), ("bf16", "f32", "f32"), ("f32", "f32", "f32")]
+              ("bf16", "f32", "f64"), ("bf16", "f32", "f32"), ("f32", "f32", "f32"),
+              ("df64", "f64", "df64")]
 
 
 @pytest.mark.parametrize("storage,vec,acc", PRECISIONS)
@@ -131,7 +132,8 @@ def test_precisions(api, torch, name, storage, vec, acc):
     x = _dev(torch, x64, torch.float64 if vec == "f64" else torch.float32)
     variants = [dict(), dict(vec=1, vs=4), dict(index=1, vec=1, vs=4), dict(partition=1),
                 dict(vec=1, xpath=1, vs=8), dict(vec=1, vs=1),
-                dict(index=1, vec=1, vs=1, tile_rows=64, tile_pipe=1)]
+                dict(index=1, vec=1, vs=1, tile_rows=64, tile_pipe=1),
+                dict(vec=1, vs=1, tile_rows=32, xpath=1)]
     for v in variants:
         A.set_variant(**v)
         y = A.run(x).double().cpu().numpy()
@@ -217,3 +219,91 @@ def test_bounded_wait_expires_and_context_survives(api, torch):
     A.set_variant(vec=1, vs=1)
     x64 = synth.uniform_vector(m.n_cols, 15)
     check_spmv(m, x64, A.run(_dev(torch, x64)).cpu().numpy(), TAU["f64"], "after timeout")
+
+
+def _df_runs(api, torch, m, x64, variants):
+    """(double-float y, FP64 y) per width-1 variant on the same matrix and x."""
+    A = api.SpmvMatrix.from_csr(m)
+    D = api.SpmvMatrix.from_csr(m)
+    D.set_precision("df64", "f64", "df64")
+    x = _dev(torch, x64)
+    out = []
+    for v in variants:
+        A.set_variant(**v)
+        D.set_variant(**v)
+        out.append((D.run(x).cpu().numpy(), A.run(x).cpu().numpy()))
+    return out
+
+
+DF_VARIANTS = [dict(vec=1, vs=1, tile_rows=r, xpath=xp) for r in (32, 128) for xp in (0, 1)] + \
+              [dict(index=1, vec=1, vs=1, tile_rows=r) for r in (32, 64, 128)]
+
+
+def test_df64_rows_that_do_not_split_fall_back_to_fp64(api, torch):
+    """Rows that meet a value or x element outside [2^-40, 2^41) are recomputed with FP64
+    FMAs, bit-identical to the FP64 tile kernel; zeros in x split exactly; every row stays
+    within the FP64 bound of the oracle."""
+    m = synth.uniform_random(20_000, 20, seed=21, min_per_row=0, n_cols=30_000)
+    rng = np.random.default_rng(22)
+    val = m.val.copy()
+    bad_rows = rng.choice(m.n_rows, 300, replace=False)
+    for r in bad_rows[:150]:                     # tiny and huge values
+        s, e = m.rowptr[r], m.rowptr[r + 1]
+        if e > s:
+            val[s] = 1e-14 if r % 2 else 3e13
+    m = synth.Csr(m.n_rows, m.n_cols, m.rowptr, m.colind, val, "df_edges")
+    x64 = synth.uniform_vector(m.n_cols, 23)
+    x64[rng.choice(m.n_cols, 200, replace=False)] = 0.0
+    x64[rng.choice(m.n_cols, 50, replace=False)] = 1e-13
+    x64[rng.choice(m.n_cols, 50, replace=False)] = -5e12
+    xb = (x64 != 0) & ((np.abs(x64) < 2.0 ** -40) | (np.abs(x64) >= 2.0 ** 41))
+    vb = (val != 0) & ((np.abs(val) < 2.0 ** -40) | (np.abs(val) >= 2.0 ** 41))
+    bad = np.zeros(m.n_rows, bool)
+    row_of = np.repeat(np.arange(m.n_rows), np.diff(m.rowptr))
+    bad[row_of[vb | xb[m.colind]]] = True
+    assert bad.sum() > 100
+    for (yd, y64), v in zip(_df_runs(api, torch, m, x64, DF_VARIANTS), DF_VARIANTS):
+        assert np.array_equal(yd[bad].view(np.uint64), y64[bad].view(np.uint64)), v
+        check_spmv(m, x64, yd, TAU["df64"], f"df64 {v}")
+
+
+def test_df64_long_rows_and_ragged(api, torch):
+    for m in (MATS["ragged_empty"], MATS["powerlaw"], MATS["one_long_row"], MATS["banded"]):
+        x64 = synth.uniform_vector(m.n_cols, 24)
+        long_rows = np.diff(m.rowptr) > 32
+        for (yd, y64), v in zip(_df_runs(api, torch, m, x64, DF_VARIANTS), DF_VARIANTS):
+            check_spmv(m, x64, yd, TAU["df64"], f"df64 {m.name} {v}")
+            # rows above 32 nonzeros: FP64 FMAs in the FP64 tile kernel's order (oversize
+            # tiles run the same warp-per-row code in both)
+            assert np.array_equal(yd[long_rows], y64[long_rows]), (m.name, v)
+
+
+def test_df64_run_host_equals_device_run(api, torch):
+    m = synth.stencil_27pt(30)
+    A = api.SpmvMatrix.from_csr(m)
+    A.set_precision("df64", "f64", "df64")
+    x64 = synth.uniform_vector(m.n_cols, 25)
+    xh = torch.from_numpy(x64).pin_memory()
+    yh = torch.empty(m.n_rows, dtype=torch.float64).pin_memory()
+    for v in (dict(index=1, vec=1, vs=1), dict(vec=1, vs=1, tile_rows=64)):
+        A.set_variant(**v)
+        yd = A.run(torch.from_numpy(x64).cuda()).cpu()
+        yh.fill_(float("nan"))
+        A.run_host(xh, yh)
+        assert torch.equal(yd, yh), v
+        check_spmv(m, x64, yh.numpy(), TAU["df64"], f"df64 host {v}")
+
+
+def test_df64_tune_and_reject_non_f64_input(api, torch):
+    from paper_1711_05487_gb300._abi import SpmvError
+    m = MATS["st27_12"]
+    A = api.SpmvMatrix.from_csr(m)
+    A.set_precision("df64", "f64", "df64")
+    rep = A.tune("profile")
+    x64 = synth.uniform_vector(m.n_cols, 26)
+    check_spmv(m, x64, A.run(_dev(torch, x64)).cpu().numpy(), TAU["df64"], f"df64 tuned {rep.variant}")
+    B = api.SpmvMatrix.from_csr(m.astype(np.float32))
+    with pytest.raises(SpmvError):
+        B.set_precision("df64", "f64", "df64")
+    with pytest.raises(SpmvError):
+        A.set_precision("df64", "f32", "df64")

@@ -128,3 +128,59 @@ def test_merge_path_splits_characterised(gen, d):
 def test_merge_path_empty_matrix():
     c = oracle.merge_path(np.zeros(1, np.int32), 16)
     assert c.tolist() == [[0, 0]]
+
+
+# ------------------------------------------------------------------ double-float split
+def _f32_bits(x: float) -> int:
+    return int(np.array([x], dtype=np.float32).view(np.uint32)[0])
+
+
+def _df_exact(v: float) -> tuple[int, int]:
+    """The split from the 53-bit integer significand M of v: hi = the top 24 bits of M,
+    lo = the next 23, each scaled back to v's exponent (exact rational arithmetic)."""
+    import math
+    if v == 0.0:
+        return (0x80000000 if math.copysign(1.0, v) < 0 else 0, 0)
+    if not math.isfinite(v):
+        return (0x7FC00000, 0)
+    _, e2 = math.frexp(abs(v))
+    e = e2 - 1
+    if e < -40 or e > 40:
+        return (0x7FC00000, 0)
+    M = Fraction(abs(v)) / Fraction(2) ** (e - 52)
+    assert M.denominator == 1 and 2 ** 52 <= M < 2 ** 53
+    M = int(M)
+    sign = -1 if v < 0 else 1
+    hi = sign * Fraction(M >> 29) * Fraction(2) ** (e - 23)
+    lo_int = (M >> 6) & (2 ** 23 - 1)
+    lo = sign * Fraction(lo_int) * Fraction(2) ** (e - 46)
+    return (_f32_bits(float(hi)), _f32_bits(float(lo)) if lo_int else 0)
+
+
+def test_df_split_against_integer_significand():
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(4000) * 2.0 ** rng.integers(-45, 46, 4000)
+    edge = [1.0, -1.0, 1 + 2 ** -30, 1 + 2 ** -52, -3.75, 2.0 ** -40, 2.0 ** 41,
+            2.0 ** 41 - 2.0 ** -12, 2.0 ** -41, (2 - 2 ** -52) * 2.0 ** -41, 0.0, -0.0,
+            np.inf, -np.inf, np.nan, 1 + 2 ** -23 + 2 ** -24 + 2 ** -47, -(1 + 2 ** -46)]
+    v = np.concatenate([v, edge])
+    got = oracle.df_split_bits(v)
+    want = np.array([_df_exact(float(t)) for t in v], dtype=np.uint32)
+    assert np.array_equal(got, want)
+
+
+def test_df_split_known_bits_and_error_bound():
+    got = oracle.df_split_bits(np.array([1.0, 1 + 2 ** -30, 1 + 2 ** -52, -3.75, 2.0 ** -40,
+                                         2.0 ** 41, 0.0, -0.0, np.nan]))
+    assert [tuple(hex(int(b)) for b in r) for r in got] == [
+        ("0x3f800000", "0x0"), ("0x3f800000", "0x30800000"), ("0x3f800000", "0x0"),
+        ("0xc0700000", "0x0"), ("0x2b800000", "0x0"), ("0x7fc00000", "0x0"),
+        ("0x0", "0x0"), ("0x80000000", "0x0"), ("0x7fc00000", "0x0")]
+    rng = np.random.default_rng(4)
+    v = rng.uniform(-1, 1, 20000) * 2.0 ** rng.integers(-39, 40, 20000)
+    v = v[(np.abs(v) >= 2.0 ** -40) & (np.abs(v) < 2.0 ** 41)]
+    pair = oracle.df_split_bits(v).view(np.float32).astype(np.float64)
+    hi, lo = pair[:, 0], pair[:, 1]
+    r = np.array([float(Fraction(a) - Fraction(b) - Fraction(c)) for a, b, c in zip(v, hi, lo)])
+    assert np.all(np.abs(r) < 2.0 ** -46 * np.abs(v))
+    assert np.all(np.sign(r) * np.sign(v) >= 0)          # truncation toward zero
