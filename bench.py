@@ -184,6 +184,8 @@ def run_ours(args, rank, world):
     vec_t = torch.float64 if m.val.dtype == np.float64 else torch.float32
     if m.val.dtype != np.float64:
         A.set_precision("f32", "f32", "f32", stream=stream)
+    elif args.precision == "df64":
+        A.set_precision("df64", "f64", "df64", stream=stream)
     x = torch.from_numpy(x_host).to(vec_t).cuda()
     y = torch.empty(m.n_rows, dtype=vec_t, device="cuda")
     flops = 2.0 * m.nnz
@@ -233,7 +235,7 @@ def run_ours(args, rank, world):
     ms = timed(args.steps, args.warmup, tag="bench_timed")
     clocks.stop()
     storage = A.storage
-    traffic = measured_traffic(args.workload, rep.variant)
+    traffic = measured_traffic(args.workload + ("/df64" if storage == 3 else ""), rep.variant)
     ab = alg_bytes(m.n_rows, m.n_cols, m.nnz, rep.variant, storage, A.vec)
     achieved = ab / (ms * 1e-3) / 1e9
     csr_bytes = alg_bytes(m.n_rows, m.n_cols, m.nnz, (0, 0, 0, 0, 0), storage, A.vec)
@@ -505,6 +507,9 @@ def main():
     ap.add_argument("--batch-count", type=int, default=512,
                     help="matrices in the batched workload (512; fewer for profiling)")
     ap.add_argument("--quick", action="store_true", help="skip the precision variants")
+    ap.add_argument("--precision", choices=["native", "df64"], default="native",
+                    help="FP64 workloads: native FP64 arithmetic, or double-float (df64) "
+                         "storage and arithmetic for the timed line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fixed-variant", default=None,
                     help="install this variant instead of tuning: partition,index,xpath,vec,"

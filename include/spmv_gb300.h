@@ -139,13 +139,12 @@ spmv_status spmv_destroy(spmv_handle_t h);
  * storage DF64 with vec = F64, acc = DF64 (FP64 input values only).
  * DF64 (a GB300 answer to the CMP class, not in the paper): GB300's FP64 pipe is about 1/64
  * of its FP32 pipe, so width-1 row variants (vs = 1) compute each product and the row sum
- * in double-float FP32 arithmetic from value pairs split once here and x split on every
- * call: each row ends within about 8e-13 of sum_j |a_ij x_j| (inside the FP64 bound of
- * 1e-12), not bit-identical to FP64 FMAs. Rows longer than 32 nonzeros, or meeting a value
- * or x element that does not split (see SPMV_DF64), are recomputed with FP64 FMAs; every
- * other variant runs the FP64 kernels on the FP64 values. The handle keeps the pairs
- * (8 bytes per nonzero) and an 8-byte-per-column split x beside the FP64 values, so runs
- * of one DF64 handle must not overlap in time (one stream, or ordered streams).
+ * in double-float FP32 arithmetic from value pairs split once here and x elements split as
+ * they are gathered: each row ends within about 8e-13 of sum_j |a_ij x_j| (inside the FP64
+ * bound of 1e-12), not bit-identical to FP64 FMAs. Rows longer than 32 nonzeros, or meeting
+ * a value or x element that does not split (see SPMV_DF64), are recomputed with FP64 FMAs;
+ * every other variant runs the FP64 kernels on the FP64 values. The handle keeps the pairs
+ * (8 bytes per nonzero) beside the FP64 values.
  * Invalidates the tuned variant (spmv_tune or spmv_set_variant must follow). */
 spmv_status spmv_set_precision(spmv_handle_t h, spmv_dtype storage, spmv_dtype vec_type,
                                spmv_dtype acc_type, spmv_stream_t stream);

@@ -128,7 +128,7 @@ struct spmv_matrix {
   int64_t n_rows = 0, n_cols = 0, nnz = 0;
   spmv_dtype in_type = SPMV_F64, storage = SPMV_F64, vec = SPMV_F64, acc = SPMV_F64;
   DevBuf rowptr, colind, val_in, val_store;
-  DevBuf val_df, x_df;         // storage SPMV_DF64: value pairs, split x (per call)
+  DevBuf val_df;               // storage SPMV_DF64: double-float value pairs
   // optimization-pool data
   DevBuf dbase, delta, esc;
   int64_t n_esc = 0;
@@ -192,7 +192,6 @@ RunArgs run_args(const spmv_matrix *h, const void *x, void *y) {
   a.tile_pipe = h->tile_pipe;
   a.err = h->d_err.as<int32_t>();
   a.val_df = h->val_df.p;
-  a.x_df = h->x_df.p;
   return a;
 }
 
@@ -685,9 +684,10 @@ void run_profile(spmv_matrix *h, int reps, spmv_profile_report &o, cudaStream_t 
 // Sub-warp width sweep by timing (Section III-E "parameter tuning"; build addition). When
 // the thread-per-row kernel (width 1) wins, its geometry is swept too: 128 / 64 / 32 rows
 // per tile, one tile per CTA or persistent CTAs with two tiles in flight.
+// Called by spmv_tune for the routes that choose a variant (never for SPMV_TUNE_FIXED), so
+// the sub-warp width and, for width 1, the tile geometry are always swept.
 void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, cudaStream_t s) {
   if (v.partition != 0 || h->n_rows == 0) return;
-  const bool fixed_geometry = v.tile_rows != 0;
   const size_t vb = dtype_bytes(h->vec);
   DevBuf x, y;
   x.alloc(vb * (size_t)std::max<int64_t>(h->n_cols, 1), vb, s);
@@ -710,10 +710,6 @@ void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, cudaStream_t s) {
   if (best_vs != 1) {
     v.tile_rows = 0;
     v.tile_pipe = 0;
-    return;
-  }
-  if (fixed_geometry) {
-    set_tile_geometry(h, v, v.tile_rows, v.tile_pipe != 0, s);
     return;
   }
   int best_rows = h->tile_rows, best_pipe = h->tile_pipe, best_cap = h->tile_cap;
@@ -754,12 +750,10 @@ void default_types(spmv_dtype in, spmv_dtype *st, spmv_dtype *vec, spmv_dtype *a
 void install_storage(spmv_matrix *h, cudaStream_t s) {
   h->val_store.release();
   h->val_df.release();
-  h->x_df.release();
   if (h->storage == SPMV_DF64) {
     // the FP64 input values stay the values of every non-double-float kernel
     h->val_df.alloc(8 * (size_t)h->nnz, 8, s);
     CK(launch_df_split(h->val_in.as<double>(), h->val_df.p, 0, h->nnz, s));
-    h->x_df.alloc(8 * (size_t)std::max<int64_t>(h->n_cols, 1), 8, s);
   } else if (h->storage != h->in_type) {
     const size_t eb = dtype_bytes(h->storage);
     h->val_store.alloc(eb * (size_t)h->nnz, eb, s);
@@ -1091,8 +1085,6 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
         CK(launch_run(h, h->variant, h->x_stage.p, h->y_stage.p, s));
       } else {
         RunArgs a = run_args(h, h->x_stage.p, static_cast<char *>(h->y_stage.p) + vb * (size_t)r0);
-        a.x_split_lo = c == 0 ? 0 : h->x_need[c - 1];   // x elements that arrived for chunk c
-        a.x_split_hi = need;
         a.n_rows = r1 - r0;
         a.rowptr += r0;
         if (a.dbase) a.dbase += r0;

@@ -40,11 +40,7 @@ struct RunArgs {
   int32_t tile_rows = 0;             // rows (= threads) per tile: 32, 64 or 128
   int32_t tile_pipe = 0;             // 1: persistent CTAs with two staged tiles in flight
   int32_t *err = nullptr;            // device error word (bounded waits)
-  // double-float FP64 (storage SPMV_DF64): value pairs, the split x and the range of x
-  // elements to split before the launch ([lo, hi), hi < 0 meaning n_cols)
-  const void *val_df = nullptr;
-  void *x_df = nullptr;
-  int64_t x_split_lo = 0, x_split_hi = -1;
+  const void *val_df = nullptr;      // storage SPMV_DF64: double-float value pairs
 };
 
 // Thread-per-row tile kernel geometry: at most this many rows (= threads) per CTA.

@@ -5,7 +5,7 @@
 // FP64 number is carried as an unevaluated sum hi + lo of two FP32 numbers:
 //   - split: hi holds the top 24 significant bits of v (exact truncation), lo the next 23
 //     (truncated), so |v - hi - lo| < 2^-46 |v|. The split is integer bit work; values are
-//     split once when the precision is installed, x once per call;
+//     split once when the precision is installed, x elements as they are gathered;
 //   - product: hi_v*hi_x is taken exactly as a rounded product and its error (fmaf), plus
 //     the cross terms hi_v*lo_x + lo_v*hi_x; lo_v*lo_x (< 2^-46 |v x|) is dropped. Together
 //     with the split, each product is within about 6 * 2^-46 |v x| of v*x;
@@ -26,24 +26,26 @@ constexpr int kDfMaxRow = 32;
 constexpr uint32_t kDfNanHi = 0x7FC00000u;   // quiet NaN: marks an unsplittable number
 }  // namespace
 
-// Split of one FP64 number into FP32 bit patterns (hi, lo), integer operations only.
-// Zero gives (+-0, 0); a nonzero outside [2^-40, 2^41) (biased exponent outside
-// [983, 1063]), an infinity or a NaN gives (NaN, 0).
-__device__ __forceinline__ uint2 df_split_bits(double d) {
+// Split of one FP64 number into FP32 bit patterns (hi, lo), integer operations and one
+// exact FP32 subtraction, without branches. Zero gives (+-0, 0); a nonzero outside
+// [2^-40, 2^41) (biased exponent outside [983, 1063]), an infinity or a NaN gives (NaN, 0).
+__device__ __forceinline__ uint2 df_split(double d) {
   const uint32_t H = (uint32_t)((unsigned long long)__double_as_longlong(d) >> 32);
   const uint32_t L = (uint32_t)(unsigned long long)__double_as_longlong(d);
-  if ((H & 0x7FFFFFFFu) == 0u && L == 0u) return make_uint2(H, 0u);
   const uint32_t eb = (H >> 20) & 0x7FFu;
-  if (eb - 983u > 80u) return make_uint2(kDfNanHi, 0u);
   // (H:L) << 3 puts the low 9 exponent bits and the top 23 fraction bits in one word; the
   // rebias 1023 -> 127 is a subtraction of 896 in the exponent field, taken modulo 2^9
-  // (the result lies in [87, 167], so its ninth bit is zero)
-  const uint32_t hi = (__funnelshift_l(L, H, 3) - (384u << 23)) | (H & 0x80000000u);
-  // lo = next 23 fraction bits scaled by 2^(e - 46): built as (1.m - 1) * 2^(e - 23), an
-  // exact FP32 subtraction of two numbers carrying hi's sign
+  // (in range the result lies in [87, 167], so its ninth bit is zero)
+  uint32_t hi = (__funnelshift_l(L, H, 3) - (384u << 23)) | (H & 0x80000000u);
+  // lo = the next 23 fraction bits scaled by 2^(e - 46): (1.m - 1) * 2^(e - 23), an exact
+  // FP32 subtraction of two numbers carrying hi's sign
   const uint32_t base = (hi & 0xFF800000u) - (23u << 23);
   const uint32_t m = (L >> 6) & 0x7FFFFFu;
-  const float lo = __fsub_rn(__uint_as_float(base | m), __uint_as_float(base));
+  float lo = __fsub_rn(__uint_as_float(base | m), __uint_as_float(base));
+  const bool out = eb - 983u > 80u;                  // also zero, subnormal, inf, NaN
+  const bool zero = ((H & 0x7FFFFFFFu) | L) == 0u;
+  hi = out ? (zero ? (H & 0x80000000u) : kDfNanHi) : hi;
+  lo = out ? 0.0f : lo;
   return make_uint2(hi, __float_as_uint(lo));
 }
 
@@ -51,7 +53,7 @@ __global__ void k_df_split(const double *__restrict__ in, uint2 *__restrict__ ou
                            int64_t hi) {
   for (int64_t i = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < hi;
        i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = df_split_bits(in[i]);
+    out[i] = df_split(in[i]);
 }
 
 cudaError_t launch_df_split(const double *in, void *out, int64_t lo, int64_t hi,
@@ -114,7 +116,6 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_df(const RunArgs a) {
   const double *__restrict__ val = static_cast<const double *>(a.val);
   const uint2 *__restrict__ vdf = static_cast<const uint2 *>(a.val_df);
   const double *__restrict__ x = static_cast<const double *>(a.x);
-  const uint2 *__restrict__ xdf = static_cast<const uint2 *>(a.x_df);
   double *__restrict__ y = static_cast<double *>(a.y);
   uint64_t pol_x = 0;
   if constexpr (XL2) pol_x = policy_evict_last();
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_df(const RunArgs a) {
     for (; k + 8 <= len; k += 8) {
       uint2 xv[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) xv[q] = ldx_pair<XL2>(xdf + column(k + q), pol_x);
+      for (int q = 0; q < 8; ++q) xv[q] = df_split(ldx<XL2>(x + column(k + q), pol_x));
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         float p, pq;
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_df(const RunArgs a) {
     }
     for (; k < len; ++k) {
       float p, pq;
-      df_prod(sval[o + k], ldx_pair<XL2>(xdf + column(k), pol_x), p, pq);
+      df_prod(sval[o + k], df_split(ldx<XL2>(x + column(k), pol_x)), p, pq);
       df_add(sh, sl, p, pq);
     }
     if (isfinite(sh)) {
@@ -218,9 +219,6 @@ template <bool D16, bool XL2> cudaError_t launch_rowtile_df_k(const RunArgs &a, 
 cudaError_t launch_spmv_df(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
   if (v.partition != 0 || v.vs != 1) return kernel_set_f64_dd()->spmv(v, a, s);
-  const int64_t hi = a.x_split_hi >= 0 ? a.x_split_hi : a.n_cols;
-  cudaError_t e = launch_df_split(static_cast<const double *>(a.x), a.x_df, a.x_split_lo, hi, s);
-  if (e != cudaSuccess) return e;
   const bool d16 = v.index == 1, xl2 = v.xpath != 0;
   if (d16) return xl2 ? launch_rowtile_df_k<true, true>(a, s) : launch_rowtile_df_k<true, false>(a, s);
   return xl2 ? launch_rowtile_df_k<false, true>(a, s) : launch_rowtile_df_k<false, false>(a, s);
