@@ -143,8 +143,9 @@ spmv_status spmv_destroy(spmv_handle_t h);
  * they are gathered: each row ends within about 8e-13 of sum_j |a_ij x_j| (inside the FP64
  * bound of 1e-12), not bit-identical to FP64 FMAs. Rows longer than 32 nonzeros, or meeting
  * a value or x element that does not split (see SPMV_DF64), are recomputed with FP64 FMAs;
- * every other variant runs the FP64 kernels on the FP64 values. The handle keeps the pairs
- * (8 bytes per nonzero) beside the FP64 values.
+ * every other variant runs the FP64 kernels on the FP64 values. Width-1 variants run one
+ * tile per CTA (tile_pipe is set to 0). The handle keeps the pairs (8 bytes per nonzero)
+ * beside the FP64 values.
  * Invalidates the tuned variant (spmv_tune or spmv_set_variant must follow). */
 spmv_status spmv_set_precision(spmv_handle_t h, spmv_dtype storage, spmv_dtype vec_type,
                                spmv_dtype acc_type, spmv_stream_t stream);

@@ -287,6 +287,7 @@ void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
       v.vs = (v.vec || v.index == 1) ? pool_vs(h->nnz_avg(), v.index == 1 ? 8 : 4)
                                      : heuristic_vs(h->nnz_avg(), 1);
     }
+    if (h->storage == SPMV_DF64) v.tile_pipe = 0;   // the double-float kernel: one tile per CTA
     if (v.vs == 1 && v.tile_rows != 0) {
       set_tile_geometry(h, v, v.tile_rows, v.tile_pipe != 0, s);
     } else {
@@ -713,7 +714,8 @@ void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, cudaStream_t s) {
     return;
   }
   int best_rows = h->tile_rows, best_pipe = h->tile_pipe, best_cap = h->tile_cap;
-  for (int pipe = 0; pipe <= 1; ++pipe) {
+  const int max_pipe = h->storage == SPMV_DF64 ? 0 : 1;
+  for (int pipe = 0; pipe <= max_pipe; ++pipe) {
     for (int rows = kTileRows; rows >= 32; rows /= 2) {
       set_tile_geometry(h, v, rows, pipe != 0, s);
       const float ms = time_launches([&]() { return launch_run(h, v, x.p, y.p, s); }, reps, s);
