@@ -75,6 +75,8 @@ def _declare(L):
     L.oracle_round_bf16.restype = None
     L.oracle_df_split.argtypes = [_P, _P, _I64]
     L.oracle_df_split.restype = None
+    L.oracle_cg.argtypes = [_I64, _P, _P, _P, _P, _P, _I64, _D, _P, _P]
+    L.oracle_cg.restype = _I64
     L.oracle_delta16_encode.argtypes = [_I64, _P, _P, _P, _P, _P]
     L.oracle_delta16_encode.restype = _I64
     L.oracle_delta16_decode.argtypes = [_I64, _P, _P, _P, _P, _P]
@@ -175,6 +177,19 @@ def df_split_bits(v) -> np.ndarray:
     out = np.empty((a.shape[0], 2), dtype=np.uint32)
     lib().oracle_df_split(_p(a), _p(out), a.shape[0])
     return out
+
+
+def cg(rowptr, colind, val, b, x0=None, max_iters=1000, rtol=1e-10):
+    """Conjugate gradients; returns (x, iterations, converged, ||r_k|| for k = 0..iterations)."""
+    rp, ci, v = _c(rowptr, np.int32), _c(colind, np.int32), _c(val, np.float64)
+    bb = _c(b, np.float64)
+    n = bb.shape[0]
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    hist = np.zeros(max_iters + 1)
+    conv = np.zeros(1, dtype=np.int32)
+    k = lib().oracle_cg(n, _p(rp), _p(ci), _p(v), _p(bb), _p(x), max_iters, float(rtol),
+                        _p(hist), _p(conv))
+    return x, int(k), bool(conv[0]), hist[:k + 1]
 
 
 def bf16_bits_to_f64(bits) -> np.ndarray:

@@ -24,6 +24,9 @@
  *   - Classify rule set                      (Section III-C, Fig. 3)
  *   - class -> optimization map              (Section III-E, Table II)
  *   - amortization iterations                (Section IV-D, N_iters,min)
+ *   - conjugate gradients on y = A x         (Section IV-D's iterative-solver setting;
+ *     Hestenes and Stiefel's method)
+ *   - double-float split of FP64 values      (the library's DF64 storage)
  *   - MLP selector: FP64 loss and gradient, FP32 inference, log2(1+v) normalisation
  *     (the learned selector that stands in for the decision tree of Section III-D)
  */
@@ -192,6 +195,60 @@ void oracle_df_split(const double *in, uint32_t *out, int64_t n) {
     out[2 * i] = hi_bits;
     out[2 * i + 1] = lo_bits;
   }
+}
+
+/* Conjugate gradients (Hestenes and Stiefel 1952), the solver setting of Section IV-D in
+ * which the tuned SpMV is applied once per iteration. In the textbook order:
+ *   r_0 = b - A x_0, p_0 = r_0;
+ *   for k = 0, 1, ...: alpha_k = (r_k, r_k) / (p_k, A p_k); x_{k+1} = x_k + alpha_k p_k;
+ *     r_{k+1} = r_k - alpha_k A p_k; beta_k = (r_{k+1}, r_{k+1}) / (r_k, r_k);
+ *     p_{k+1} = r_{k+1} + beta_k p_k,
+ * stopping when ||r_k|| <= rtol ||b|| or after max_iters iterations. alpha (beta) is 0 when
+ * its denominator is 0. x holds x_0 on entry and the last iterate on return; hist (may be
+ * NULL) receives ||r_k|| for k = 0 .. iterations. Dot products are plain sequential FP64
+ * sums. Returns the number of iterations; *converged tells whether the test was met. */
+static double dot_f64(int64_t n, const double *a, const double *b) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+int64_t oracle_cg(int64_t n, const int32_t *rowptr, const int32_t *colind, const double *val,
+                  const double *b, double *x, int64_t max_iters, double rtol, double *hist,
+                  int32_t *converged) {
+  double *r = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double *p = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double *ap = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  oracle_spmv_f64(n, rowptr, colind, val, x, ap, NULL);
+  for (int64_t i = 0; i < n; ++i) {
+    r[i] = b[i] - ap[i];
+    p[i] = r[i];
+  }
+  const double b_norm = sqrt(dot_f64(n, b, b));
+  double rr = dot_f64(n, r, r);
+  if (hist) hist[0] = sqrt(rr);
+  int64_t k = 0;
+  *converged = sqrt(rr) <= rtol * b_norm;
+  while (!*converged && k < max_iters) {
+    oracle_spmv_f64(n, rowptr, colind, val, p, ap, NULL);
+    const double pap = dot_f64(n, p, ap);
+    const double alpha = pap != 0.0 ? rr / pap : 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      x[i] += alpha * p[i];
+      r[i] -= alpha * ap[i];
+    }
+    const double rr_new = dot_f64(n, r, r);
+    const double beta = rr != 0.0 ? rr_new / rr : 0.0;
+    for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+    rr = rr_new;
+    ++k;
+    if (hist) hist[k] = sqrt(rr);
+    *converged = sqrt(rr) <= rtol * b_norm;
+  }
+  free(r);
+  free(p);
+  free(ap);
+  return k;
 }
 
 /* ---------------------------------------------------------------------------------- */

@@ -184,6 +184,16 @@ def stencil_27pt(n: int, seed: int = SEED_BASE + 2) -> Csr:
     return _stencil_3d(n, offs, seed, f"stencil27_{n}^3")
 
 
+def laplacian_27pt(n: int) -> Csr:
+    """Symmetric 27-point operator on an n^3 grid (Dirichlet boundary): 26 on the diagonal,
+    -1 for each neighbour. Symmetric with a positive diagonal and irreducibly diagonally
+    dominant, hence positive definite: the SPD system of the conjugate-gradient solves."""
+    m = stencil_27pt(n)
+    row_of = np.repeat(np.arange(m.n_rows, dtype=np.int64), np.diff(m.rowptr))
+    val = np.where(m.colind == row_of, 26.0, -1.0)
+    return Csr(m.n_rows, m.n_cols, m.rowptr, m.colind, val, f"laplacian27_{n}^3")
+
+
 def stencil_7pt(n: int, seed: int) -> Csr:
     offs = [(0, 0, -1), (0, -1, 0), (-1, 0, 0), (0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)]
     return _stencil_3d(n, offs, seed, f"stencil7_{n}^3")
