@@ -447,38 +447,135 @@ def run_batched(args, rank, world):
     return out
 
 
-def cpu_baseline(m, x_host, budget_s=10.0):
-    """The oracle's single-threaded FP64 CSR SpMV timed on the host on the same matrix."""
-    import oracle
-    oracle.lib()
+def run_cg(args, rank, world):
+    """Conjugate gradients on the SPD 27-point operator 160^3 (Section IV-D's solver setting):
+    time to rtol with the plain CSR-vector handle and with tuned handles, and the iterations
+    after which tuning pays for itself."""
+    import torch
+
+    from paper_1711_05487_gb300 import api
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    t0 = time.time()
+    m = synth.laplacian_27pt(160)
+    gen_s = time.time() - t0
+    b = torch.from_numpy(synth.uniform_vector(m.n_rows, synth.SEED_BASE + 15)).cuda()
+    rtol, max_iters, check = 1e-8, 5000, 25
+    solves = max(1, min(args.steps, 5))
+    peak, peak_kind = _peaks()
+
+    def solve_runs(A):
+        A.cg(b, max_iters=max_iters, rtol=rtol, check_every=check)       # warm-up
+        times, rep = [], None
+        for _ in range(solves):
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            _, rep = A.cg(b, max_iters=max_iters, rtol=rtol, check_every=check)
+            times.append(max_over_ranks(rep["t_ms"], world))
+        return float(np.median(times)), rep
+
+    res = {}
+    A = api.SpmvMatrix.from_csr(m)
+    A.set_variant()
+    t_plain, rep_plain = solve_runs(A)
+    res["csr_vector"] = {"ms": round(t_plain, 3), "iters": rep_plain["iters"],
+                         "ms_per_iter": round(t_plain / max(1, rep_plain["iters"]), 5),
+                         "t_pre_ms": 0.0}
+    clocks = ClockSampler(dev)
+    clocks.start()
+    tuned = None
+    for name, prec in (("tuned_f64", None), ("tuned_df64", "df64")):
+        if prec:
+            A.set_precision(prec, "f64", prec)
+        tr = A.tune("profile")
+        t, rep = solve_runs(A)
+        it = max(1, rep["iters"])
+        gain = t_plain / max(1, rep_plain["iters"]) - t / it
+        res[name] = {"ms": round(t, 3), "iters": rep["iters"], "ms_per_iter": round(t / it, 5),
+                     "t_pre_ms": round(tr.t_pre_ms, 2), "variant": list(tr.variant),
+                     "classes": tr.class_names, "converged": rep["converged"],
+                     "breakeven_iters": round(tr.t_pre_ms / gain, 1) if gain > 0 else None,
+                     "ms_with_tuning": round(t + tr.t_pre_ms, 3)}
+        if tuned is None:
+            tuned = (t, rep, tr)
+    clocks.stop()
+    t, rep, tr = tuned
+    it = max(1, rep["iters"])
+    spmv_b = alg_bytes(m.n_rows, m.n_cols, m.nnz, tr.variant, 0, 0)
+    iter_b = spmv_b + 88 * m.n_rows     # + dot(p,Ap) 16N, x/r update 48N, p update 24N
+    achieved = iter_b / (t / it * 1e-3) / 1e9
+    return {
+        "metric": "CG solve time to rtol 1e-8, SPD 27-point operator 160^3, tuned handle",
+        "value": round(t, 3), "unit": "ms", "n_gpus": world, "steps": solves,
+        "warmup": 1, "ms_per_step": round(t, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+        "config": {"workload": "cg27_160", "n_rows": m.n_rows, "nnz": m.nnz, "rtol": rtol,
+                   "check_every": check, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (no flush needed)"},
+        "solves": res,
+        "speedup_vs_csr_vector": round(t_plain / t, 3),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_kind": peak_kind, "alg_bytes_per_iter": iter_b},
+        "gpu_launches": solves * (it * 6 + 5),
+        "clocks": clocks.summary(),
+        "gen_s": round(gen_s, 1),
+    }
+
+
+def _time_rates(fn, nnz, budget_s):
     t = time.perf_counter()
-    oracle.spmv(m.rowptr, m.colind, m.val, x_host)
+    fn()
     one = time.perf_counter() - t
     reps = max(1, min(20, int(budget_s / max(one, 1e-6))))
     rates = []
     for _ in range(reps):
         t = time.perf_counter()
-        oracle.spmv(m.rowptr, m.colind, m.val, x_host)
-        rates.append(2.0 * m.nnz / (time.perf_counter() - t) / 1e9)
-    return {"value": round(oracle.harmonic_mean(rates), 4), "unit": "GFLOP/s", "cores": 1,
-            "kind": "oracle",
-            "sample": f"full matrix, {reps} SpMVs, harmonic mean of per-SpMV rates"}
+        fn()
+        rates.append(2.0 * nnz / (time.perf_counter() - t) / 1e9)
+    return rates
+
+
+def cpu_baseline(m, x_host, budget_s=8.0):
+    """The oracle's FP64 CSR SpMV on the host: the paper's static nnz-balanced baseline on all
+    host cores (the headline), and the single-threaded loop."""
+    import oracle
+    oracle.lib()
+    cores = os.cpu_count() or 1
+    used = [1]
+
+    def par():
+        used[0] = oracle.spmv_static(m.rowptr, m.colind, m.val, x_host, cores)[1]
+
+    rates = _time_rates(par, m.nnz, budget_s)
+    rates1 = _time_rates(lambda: oracle.spmv(m.rowptr, m.colind, m.val, x_host), m.nnz, budget_s)
+    return {"value": round(oracle.harmonic_mean(rates), 4), "unit": "GFLOP/s",
+            "cores": used[0], "kind": "oracle",
+            "sample": f"full matrix, {len(rates)} SpMVs, harmonic mean of per-SpMV rates; "
+                      "static nnz-balanced row partition, one range per thread",
+            "single_thread": {"value": round(oracle.harmonic_mean(rates1), 4), "cores": 1,
+                              "sample": f"full matrix, {len(rates1)} SpMVs"}}
 
 
 # ---------------------------------------------------------------------- reference ----
 def run_reference(args):
-    """The oracle (plain FP64 CPU CSR SpMV), timed on the host cores: --steps SpMVs of the
-    same workload after --warmup untimed ones."""
+    """The oracle (plain FP64 CPU CSR SpMV over the paper's static nnz-balanced row
+    partition, one range per host core), timed on the host: --steps SpMVs of the same
+    workload after --warmup untimed ones."""
     import oracle
     oracle.lib()
     wl = WORKLOADS[args.workload]
     m = wl["make"]()
     x = synth.uniform_vector(m.n_cols, wl["x_seed"]).astype(np.float64)
+    cores = os.cpu_count() or 1
+    used = 1
     for _ in range(args.warmup):
-        oracle.spmv(m.rowptr, m.colind, m.val, x)
+        used = oracle.spmv_static(m.rowptr, m.colind, m.val, x, cores)[1]
     t = time.perf_counter()
     for _ in range(args.steps):
-        oracle.spmv(m.rowptr, m.colind, m.val, x)
+        oracle.spmv_static(m.rowptr, m.colind, m.val, x, cores)
     dt = (time.perf_counter() - t) / args.steps
     v = 2.0 * m.nnz / dt / 1e9
     return {
@@ -489,8 +586,10 @@ def run_reference(args):
         "data": "synthetic (seeded)",
         "config": {"workload": args.workload, "desc": wl["desc"], "n_rows": m.n_rows,
                    "nnz": m.nnz},
-        "cpu_baseline": {"value": round(v, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                         "sample": f"full matrix, {args.steps} SpMVs"},
+        "cpu_baseline": {"value": round(v, 4), "unit": "GFLOP/s", "cores": used,
+                         "kind": "oracle",
+                         "sample": f"full matrix, {args.steps} SpMVs, static nnz-balanced "
+                                   "row partition, one range per thread"},
         "e2e": {"value": round(v, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -502,7 +601,7 @@ def main():
     ap.add_argument("--steps", type=int, default=128)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batched_512"],
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["batched_512", "cg27_160"],
                     default="stencil27_160")
     ap.add_argument("--batch-count", type=int, default=512,
                     help="matrices in the batched workload (512; fewer for profiling)")
@@ -529,8 +628,8 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
-    if args.workload == "batched_512":
-        out = run_batched(args, rank, world)
+    if args.workload in ("batched_512", "cg27_160"):
+        out = (run_batched if args.workload == "batched_512" else run_cg)(args, rank, world)
         if rank == 0:
             print(json.dumps(out), flush=True)
         return

@@ -335,6 +335,39 @@ spmv_status spmv_run_noalloc(int64_t n_rows, int64_t n_cols, int64_t nnz, const 
                              const int32_t *col_ind, const double *val, const double *x,
                              double *y, spmv_stream_t stream);
 
+/* ------------------------------------------------------------ iterative solver ---- */
+/* Conjugate gradients (Hestenes and Stiefel) for A x = b with A symmetric positive definite
+ * (square handle, vec_type F64): the iterative-solver setting in which Section IV-D weighs
+ * the optimizer's preprocessing against the SpMV time it saves. Every iteration applies the
+ * handle's tuned variant once (spmv_tune or spmv_set_variant must come first); the dot
+ * products and vector updates are the library's own FP64 kernels with fixed reduction
+ * order, so a solve repeats bit for bit. Textbook order: r0 = b - A x0, p0 = r0;
+ * alpha = (r,r)/(p,Ap), x += alpha p, r -= alpha Ap, beta = (r',r')/(r,r), p = r' + beta p;
+ * alpha (beta) is 0 when its denominator is 0.
+ *   b[n], x[n]: device FP64; x holds x0 on entry and the last iterate on return.
+ *   The solve stops when ||r_k|| <= rtol ||b|| (||r_k|| from the recurrence) or after
+ *   max_iters iterations; the host reads ||r_k|| every check_every iterations (each read
+ *   synchronizes the stream), so up to check_every - 1 iterations may run past the point
+ *   where the test was first met.
+ *   res_hist: NULL or device FP64[max_iters + 1], receives ||r_k|| for k = 0 .. iterations.
+ *   report: NULL or receives the iteration count, whether the test was met, the final
+ *   ||r_k||, ||b|| and the wall time.
+ * The handle keeps a workspace of 3 n doubles (+ a few KB) between calls. Synchronizes the
+ * stream. Errors: SPMV_ERR_ARG (non-square, null vectors, max_iters < 0, rtol < 0 or NaN,
+ * check_every < 1), SPMV_ERR_NOT_TUNED, SPMV_ERR_UNSUPPORTED_DTYPE (vec_type not F64),
+ * SPMV_ERR_OOM, SPMV_ERR_CUDA. */
+typedef struct {
+  int32_t iters;      /* iterations run                                   */
+  int32_t converged;  /* 1 if ||r_k|| <= rtol ||b|| at the last check      */
+  double res_norm;    /* ||r_k|| (recurrence) at the end                   */
+  double b_norm;      /* ||b||                                             */
+  double t_ms;        /* wall time of the call                             */
+} spmv_cg_report;
+
+spmv_status spmv_cg(spmv_handle_t h, const double *b, double *x, int32_t max_iters,
+                    double rtol, int32_t check_every, double *res_hist,
+                    spmv_cg_report *report, spmv_stream_t stream);
+
 /* ------------------------------------------------------------- learned selector ---- */
 /* The MLP has layer sizes n_in -> h1 -> h2 -> 4 (ReLU hidden units, one logit per class
  * MB, ML, IMB, CMP); parameters packed W1 (h1 x n_in, row-major), b1, W2, b2, W3, b3, FP32.

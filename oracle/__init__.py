@@ -41,7 +41,9 @@ def build(force: bool = False) -> str:
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared",
            "-fPIC", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    # OpenMP only serves the static-partition baseline; without it that runs on one thread
+    if subprocess.run(cmd[:-1] + ["-fopenmp", "-lm"], capture_output=True).returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -75,6 +77,8 @@ def _declare(L):
     L.oracle_round_bf16.restype = None
     L.oracle_df_split.argtypes = [_P, _P, _I64]
     L.oracle_df_split.restype = None
+    L.oracle_spmv_f64_static.argtypes = [_I64, _P, _P, _P, _P, _P, ctypes.c_int32]
+    L.oracle_spmv_f64_static.restype = ctypes.c_int32
     L.oracle_cg.argtypes = [_I64, _P, _P, _P, _P, _P, _I64, _D, _P, _P]
     L.oracle_cg.restype = _I64
     L.oracle_delta16_encode.argtypes = [_I64, _P, _P, _P, _P, _P]
@@ -177,6 +181,17 @@ def df_split_bits(v) -> np.ndarray:
     out = np.empty((a.shape[0], 2), dtype=np.uint32)
     lib().oracle_df_split(_p(a), _p(out), a.shape[0])
     return out
+
+
+def spmv_static(rowptr, colind, val, x, n_threads: int):
+    """The paper's static nnz-balanced baseline on n_threads OpenMP threads; returns
+    (y, threads used). y equals spmv()'s bit for bit."""
+    rp, ci, v, xx = (_c(rowptr, np.int32), _c(colind, np.int32), _c(val, np.float64),
+                     _c(x, np.float64))
+    n = rp.shape[0] - 1
+    y = np.empty(n, dtype=np.float64)
+    used = lib().oracle_spmv_f64_static(n, _p(rp), _p(ci), _p(v), _p(xx), _p(y), int(n_threads))
+    return y, int(used)
 
 
 def cg(rowptr, colind, val, b, x0=None, max_iters=1000, rtol=1e-10):

@@ -31,6 +31,9 @@
  *     (the learned selector that stands in for the decision tree of Section III-D)
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -77,6 +80,48 @@ void oracle_spmv_f64(int64_t n_rows, const int32_t *rowptr, const int32_t *colin
     y[i] = acc;
     if (s) s[i] = mag;
   }
+}
+
+/* The paper's baseline CSR scheme (Section IV-A): rows are split into n_threads contiguous
+ * ranges of about NNZ / n_threads nonzeros each (static, nnz-balanced; range t starts at the
+ * first row whose rowptr reaches t NNZ / n_threads) and each range is one OpenMP thread's.
+ * Every row is the same sequential sum as in oracle_spmv_f64, so y is bit-identical to it.
+ * Returns the number of threads that ran (1 when built without OpenMP). */
+int32_t oracle_spmv_f64_static(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                               const double *val, const double *x, double *y,
+                               int32_t n_threads) {
+  if (n_threads < 1) n_threads = 1;
+  const int64_t nnz = n_rows > 0 ? rowptr[n_rows] : 0;
+  int32_t used = 1;
+#ifdef _OPENMP
+#pragma omp parallel num_threads(n_threads)
+  {
+    const int32_t T = (int32_t)omp_get_num_threads();
+    const int32_t t = (int32_t)omp_get_thread_num();
+    if (t == 0) used = T;
+#else
+  {
+    const int32_t T = 1, t = 0;
+#endif
+    /* first row of a range: lower bound of the target nonzero count in rowptr */
+    int64_t bounds[2];
+    for (int q = 0; q < 2; ++q) {
+      const int64_t target = (int64_t)(((__int128)nnz * (t + q)) / T);
+      int64_t lo = 0, hi = n_rows;
+      while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (rowptr[mid] < target) lo = mid + 1;
+        else hi = mid;
+      }
+      bounds[q] = (t + q == T) ? n_rows : lo;
+    }
+    for (int64_t i = bounds[0]; i < bounds[1]; ++i) {
+      double acc = 0.0;
+      for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) acc += val[j] * x[colind[j]];
+      y[i] = acc;
+    }
+  }
+  return used;
 }
 
 /* The same sum for a list of rows only (used to check sampled rows of large matrices). */

@@ -78,6 +78,14 @@ class spmv_profile_report(ctypes.Structure):
         return d
 
 
+class spmv_cg_report(ctypes.Structure):
+    _fields_ = [("iters", _I32), ("converged", _I32), ("res_norm", _D), ("b_norm", _D),
+                ("t_ms", _D)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lib = None
 
 # name -> (restype, argtypes); status-returning entries raise on error
@@ -92,6 +100,7 @@ _DECL = {
     "spmv_run": (_I32, [_P, _P, _P, _P]),
     "spmv_run_host": (_I32, [_P, _P, _P, _P]),
     "spmv_run_spmm": (_I32, [_P, _P, _P, _I32, _P]),
+    "spmv_cg": (_I32, [_P, _P, _P, _I32, _D, _I32, _P, ctypes.POINTER(spmv_cg_report), _P]),
     "spmv_export_csr": (_I32, [_P, _P, _P, _P, _P]),
     "spmv_get_delta16": (_I32, [_P, _P, _P, _P, ctypes.POINTER(_I64), _P]),
     "spmv_get_merge_path": (_I32, [_P, _P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P]),
@@ -205,6 +214,12 @@ def spmv_run_host(h, x_host, y_host, stream=0):
 
 def spmv_run_spmm(h, X, Y, k, stream=0):
     _call("spmv_run_spmm", h, X, Y, k, stream)
+
+
+def spmv_cg(h, b, x, max_iters, rtol, check_every=1, res_hist=None, stream=0) -> dict:
+    rep = spmv_cg_report()
+    _call("spmv_cg", h, b, x, max_iters, rtol, check_every, res_hist, ctypes.byref(rep), stream)
+    return rep.as_dict()
 
 
 def spmv_export_csr(h, row_ptr, col_ind, val, stream=0):

@@ -196,6 +196,18 @@ class SpmvMatrix:
         _abi.spmv_profile_kernel(self._h, which, x.data_ptr(), y.data_ptr(), _stream(stream))
         return y
 
+    def cg(self, b: torch.Tensor, x0: torch.Tensor | None = None, max_iters: int = 1000,
+           rtol: float = 1e-10, check_every: int = 10, history: bool = False, stream=None):
+        """Conjugate gradients on the tuned handle (SPD matrix, FP64 vectors). Returns
+        (x, report dict[, ||r_k|| history as a device tensor])."""
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        hist = torch.zeros(max_iters + 1, dtype=torch.float64, device=b.device) if history else None
+        rep = _abi.spmv_cg(self._h, b.data_ptr(), x.data_ptr(), max_iters, rtol, check_every,
+                           None if hist is None else hist.data_ptr(), _stream(stream))
+        if history:
+            return x, rep, hist[:rep["iters"] + 1]
+        return x, rep
+
     def export_csr(self, device="cuda", stream=None):
         rp = torch.empty(self.n_rows + 1, dtype=torch.int32, device=device)
         ci = torch.empty(max(self.nnz, 1), dtype=torch.int32, device=device)

@@ -207,6 +207,19 @@ cudaError_t launch_batch_fixup(const BatchMat *mats, const BatchFix *fix, int32_
 int batch_blocks_per_sm_k(int k);
 int batch_blocks_per_sm();
 
+// Conjugate gradients (cg.cu): deterministic FP64 vector kernels; each reduction writes
+// fixed-grid block partials to `part` (cg_reduce_blocks() doubles) and then one scalar.
+int cg_reduce_blocks();
+cudaError_t launch_dot(const double *a, const double *b, int64_t n, double *part, double *out,
+                       double *hist, cudaStream_t s);
+cudaError_t launch_cg_start(const double *b, const double *ax, double *r, double *p, int64_t n,
+                            double *part, double *rr, double *hist, cudaStream_t s);
+cudaError_t launch_cg_xr(const double *p, const double *ap, double *x, double *r, int64_t n,
+                         const double *rr, const double *pap, double *part, double *rr_new,
+                         double *hist, cudaStream_t s);
+cudaError_t launch_cg_p(const double *r, double *p, int64_t n, const double *rr,
+                        const double *rr_new, cudaStream_t s);
+
 // Device arrays and dtypes of a handle (vs = tuned sub-warp width, 0 if none).
 spmv_status handle_info(spmv_handle_t h, const int32_t **rowptr, const int32_t **colind,
                         const void **val, int64_t *n_rows, int32_t *storage, int32_t *vec,

@@ -110,3 +110,17 @@ def test_generators_produce_valid_csr():
               synth.scattered(3000, 8, seed=2), synth.banded(3000, 40, 0.3, 3),
               synth.uniform_random(3000, 64, 4)):
         assert oracle.validate_csr(m.n_rows, m.n_cols, m.rowptr, m.colind) == 0, m.name
+
+
+def test_static_partition_baseline_equals_sequential_bit_for_bit():
+    """The paper's static nnz-balanced baseline computes every row with the same sum."""
+    mats = [synth.power_law(5000, seed=31, dtype=np.float64),
+            synth.uniform_random(777, 9, seed=32, min_per_row=0),
+            synth.identity(3)]
+    for m in mats:
+        x = synth.uniform_vector(m.n_cols, 33)
+        y1, _ = oracle.spmv(m.rowptr, m.colind, m.val, x)
+        for T in (1, 2, 5, 16):
+            y, used = oracle.spmv_static(m.rowptr, m.colind, m.val, x, T)
+            assert 1 <= used <= T
+            assert np.array_equal(y.view(np.uint64), y1.view(np.uint64)), (m.name, T)
