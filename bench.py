@@ -141,12 +141,13 @@ def whole_job_rate(units_per_replica: float, ms_max: float, world: int) -> float
 
 def measured_traffic(workload: str, variant) -> dict | None:
     """DRAM bytes per launch of the dominant kernel from an ncu capture (profiles/), valid only
-    for the same variant and the same library sources."""
+    for the same variant and unchanged kernel sources (the files the entry lists)."""
     try:
         from paper_1711_05487_gb300.buildlib import source_digest
         with open(TRAFFIC) as fh:
             t = json.load(fh).get(workload)
-        if t and list(t["variant"]) == list(variant) and t["source_digest"] == source_digest():
+        if (t and list(t["variant"]) == list(variant)
+                and t["source_digest"] == source_digest(t.get("sources"))):
             return t
     except Exception:
         return None

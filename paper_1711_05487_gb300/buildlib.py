@@ -52,9 +52,12 @@ def _digest() -> str:
     return _hash_files(_kernel_files() + [os.path.abspath(__file__)])
 
 
-def source_digest() -> str:
-    """SHA-256 of the library's CUDA/C++ sources and header: identifies the kernels a
-    measurement was taken on."""
+def source_digest(files=None) -> str:
+    """SHA-256 of the library's CUDA/C++ sources and header, or of the named files of the
+    source folder (a kernel's own sources): identifies the kernels a measurement was taken
+    on."""
+    if files:
+        return _hash_files([os.path.join(CSRC, f) for f in files])
     return _hash_files(_kernel_files())
 
 
