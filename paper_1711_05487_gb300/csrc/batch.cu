@@ -32,40 +32,86 @@ __device__ __forceinline__ void load_xrow(const float *p, float *o) {
   }
 }
 
-// Rows [r0, r1) of one matrix by one warp: sub-warps of VS lanes, one row each.
-template <int K, int VS>
+// Rows [r0, r1) of one matrix by one warp: sub-warps of VS lanes, one row each, U rows per
+// sub-warp at a time. The U rows' bounds, values, columns and x rows are loaded together
+// before any multiply-add, so U chains of dependent loads are in flight per lane instead of
+// one. Each row's lane sums and their reduction keep the order of a single-row walk.
+template <int K, int VS, int U>
 __device__ void warp_rows(const BatchMat &m, int r0, int r1, int lane) {
   constexpr int GROUPS = 32 / VS;
   const int sl = lane & (VS - 1);
   const unsigned mask = group_mask<VS>();
-  for (int row = r0 + lane / VS; row < r1; row += GROUPS) {
-    const int s = __ldg(m.rowptr + row), e = __ldg(m.rowptr + row + 1);
-    float acc[K];
+  for (int row0 = r0 + lane / VS; row0 < r1; row0 += GROUPS * U) {
+    int s[U], e[U];
+    int maxlen = 0;
 #pragma unroll
-    for (int q = 0; q < K; ++q) acc[q] = 0.0f;
-    for (int j = s + sl; j < e; j += VS) {
-      const float v = __ldg(m.val + j);
-      float xr[K];
-      load_xrow<K>(m.X + (int64_t)__ldg(m.colind + j) * K, xr);
+    for (int u = 0; u < U; ++u) {
+      const int row = row0 + u * GROUPS;
+      s[u] = 0;
+      e[u] = 0;
+      if (row < r1) {
+        s[u] = __ldg(m.rowptr + row);
+        e[u] = __ldg(m.rowptr + row + 1);
+      }
+      maxlen = max(maxlen, e[u] - s[u]);
+    }
+    float acc[U][K];
 #pragma unroll
-      for (int q = 0; q < K; ++q) acc[q] = fmaf(v, xr[q], acc[q]);
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int q = 0; q < K; ++q) acc[u][q] = 0.0f;
+    for (int off = sl; off < maxlen; off += VS) {
+      float v[U];
+      int c[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = s[u] + off;
+        const bool ok = j < e[u];
+        v[u] = ok ? __ldg(m.val + j) : 0.0f;
+        c[u] = ok ? __ldg(m.colind + j) : -1;
+      }
+      float xr[U][K];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (c[u] >= 0) {
+          load_xrow<K>(m.X + (int64_t)c[u] * K, xr[u]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < K; ++q) xr[u][q] = 0.0f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int q = 0; q < K; ++q) acc[u][q] = fmaf(v[u], xr[u][q], acc[u][q]);
     }
 #pragma unroll
-    for (int q = 0; q < K; ++q) {
-      const float r = group_sum<VS>(acc[q], mask);
-      if (sl == 0) m.Y[(int64_t)row * K + q] = r;
+    for (int u = 0; u < U; ++u) {
+      const int row = row0 + u * GROUPS;
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        const float r = group_sum<VS>(acc[u][q], mask);
+        if (sl == 0 && row < r1) m.Y[(int64_t)row * K + q] = r;
+      }
     }
   }
 }
 
+// rows in flight per lane: more for narrow right-hand sides (registers: U * K accumulators)
+template <int K> struct RowsInFlight {
+  static constexpr int value = K == 1 ? 4 : (K == 4 ? 2 : 1);
+};
+
 template <int K>
 __device__ void warp_rows_vs(const BatchMat &m, int r0, int r1, int lane) {
+  constexpr int U = RowsInFlight<K>::value;
   switch (m.vs) {
-    case 2: warp_rows<K, 2>(m, r0, r1, lane); break;
-    case 4: warp_rows<K, 4>(m, r0, r1, lane); break;
-    case 8: warp_rows<K, 8>(m, r0, r1, lane); break;
-    case 16: warp_rows<K, 16>(m, r0, r1, lane); break;
-    default: warp_rows<K, 32>(m, r0, r1, lane); break;
+    case 1: warp_rows<K, 1, U>(m, r0, r1, lane); break;
+    case 2: warp_rows<K, 2, U>(m, r0, r1, lane); break;
+    case 4: warp_rows<K, 4, U>(m, r0, r1, lane); break;
+    case 8: warp_rows<K, 8, U>(m, r0, r1, lane); break;
+    case 16: warp_rows<K, 16, U>(m, r0, r1, lane); break;
+    default: warp_rows<K, 32, U>(m, r0, r1, lane); break;
   }
 }
 
@@ -77,7 +123,19 @@ __device__ void warp_chunk(const BatchMat &m, int z0, int z1, int chunk, double 
   float acc[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) acc[q] = 0.0f;
-  for (int j = z0 + lane; j < z1; j += 32) {
+  // two elements per lane per step: both loads issue before the multiply-adds, which then
+  // run in element order
+  int j = z0 + lane;
+  for (; j + 32 < z1; j += 64) {
+    const float v0 = __ldg(m.val + j), v1 = __ldg(m.val + j + 32);
+    const int c0 = __ldg(m.colind + j), c1 = __ldg(m.colind + j + 32);
+    float x0[K], x1[K];
+    load_xrow<K>(m.X + (int64_t)c0 * K, x0);
+    load_xrow<K>(m.X + (int64_t)c1 * K, x1);
+#pragma unroll
+    for (int q = 0; q < K; ++q) acc[q] = fmaf(v1, x1[q], fmaf(v0, x0[q], acc[q]));
+  }
+  if (j < z1) {
     const float v = __ldg(m.val + j);
     float xr[K];
     load_xrow<K>(m.X + (int64_t)__ldg(m.colind + j) * K, xr);

@@ -142,12 +142,23 @@ spmv_status spmv_batch_create(spmv_batch_t *out, const spmv_handle_t *handles, i
           acc += l;
           ++e;
         }
-        items.push_back(BatchItem{m, r, e, 0, 0, -1});
+        items.push_back(BatchItem{m, r, e, 0, (int32_t)acc, -1});   // nz_end: the block's nnz
         r = e;
       }
     }
+    // Longest items first (chunks of split rows, then full row blocks, then the short
+    // remainders), so that the last items the warps take are the cheapest; the sort is
+    // stable, so items of one matrix stay together within a class (x rows stay L2-hot).
+    auto item_class = [&](const BatchItem &it) -> int {
+      if (it.chunk >= 0) return 0;
+      return it.nz_end >= kItemNnz / 2 ? 1 : 2;
+    };
     std::vector<BatchItem> items;
     for (int q = 0; q < 3; ++q) {
+      std::stable_sort(items_k[q].begin(), items_k[q].end(),
+                       [&](const BatchItem &a, const BatchItem &c) {
+                         return item_class(a) < item_class(c);
+                       });
       b->item_off[q] = (int32_t)items.size();
       items.insert(items.end(), items_k[q].begin(), items_k[q].end());
     }

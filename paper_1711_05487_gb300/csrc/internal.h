@@ -65,9 +65,10 @@ struct ProfileArgs {
   int32_t vs = 8;
 };
 
-// One work item of the batched kernel: rows [row_begin, row_end) of matrix `mat`, or,
-// when chunk >= 0, nonzeros [nz_begin, nz_end) of the single long row row_begin whose
-// partial sums go to partial slot `chunk`.
+// One work item of the batched kernel: rows [row_begin, row_end) of matrix `mat` (nz_end
+// then holds the block's nonzero count, used only to order items), or, when chunk >= 0,
+// nonzeros [nz_begin, nz_end) of the single long row row_begin whose partial sums go to
+// partial slot `chunk`.
 struct BatchItem {
   int32_t mat;
   int32_t row_begin;
