@@ -385,12 +385,16 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_pipe(const RunArgs a) {
 //     scan over the threads (keys = open rows); a row that began in an earlier tile is
 //     finished by k_merge_fixup, which adds the earlier tiles' carries in tile order (no
 //     atomics: results are reproducible).
+// With FP32 accumulation the tile stages each product a_j x_j (one shared-memory store and
+// load per nonzero, the multiply done while staging); with FP64 accumulation it stages a_j
+// and x_j and the walk keeps one FMA per nonzero (GB300's FP64 pipe is the scarce unit).
 template <typename ValT, typename VecT, typename AccT, bool XL2>
 __global__ void __launch_bounds__(kMergeThreads) k_merge(const RunArgs a) {
   constexpr int D = kMergeItems;
+  constexpr bool PROD = std::is_same<AccT, float>::value;
   __shared__ int s_rowend[D + 1];
   __shared__ AccT s_val[D];
-  __shared__ AccT s_x[D];
+  __shared__ AccT s_x[PROD ? 1 : D];
   __shared__ int s_crow[kMergeThreads];
   __shared__ AccT s_cval[kMergeThreads];
   const int t = blockIdx.x;
@@ -429,8 +433,12 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const RunArgs a) {
     for (int q = 0; q < kMergeIpt; ++q) {
       const int k = q * kMergeThreads + (int)threadIdx.x;
       if (k < nnz_t) {
-        s_val[k] = vv[q];
-        s_x[k] = xx[q];
+        if constexpr (PROD) {
+          s_val[k] = vv[q] * xx[q];
+        } else {
+          s_val[k] = vv[q];
+          s_x[k] = xx[q];
+        }
       }
     }
   }
@@ -450,9 +458,11 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const RunArgs a) {
   int first_row = 0;
   AccT first_val = 0;
   VecT *__restrict__ y = static_cast<VecT *>(a.y);
+  int re = s_rowend[ra];   // end of the current row (s_rowend[nrows_t] is a sentinel)
   for (int d = d0; d < d1; ++d) {
-    if (nz0 + nb < s_rowend[ra]) {
-      acc = fma(s_val[nb], s_x[nb], acc);   // one FP64 instruction per nonzero
+    if (nz0 + nb < re) {
+      if constexpr (PROD) acc += s_val[nb];
+      else acc = fma(s_val[nb], s_x[nb], acc);   // one FP64 instruction per nonzero
       ++nb;
     } else {
       const int r = row0 + ra;
@@ -465,6 +475,7 @@ __global__ void __launch_bounds__(kMergeThreads) k_merge(const RunArgs a) {
       }
       acc = 0;
       ++ra;
+      re = s_rowend[ra];
     }
   }
   // Carries: thread i ends holding the partial sum `acc` of its open row `key`. Keys are
