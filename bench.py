@@ -266,6 +266,31 @@ def run_ours(args, rank, world):
             amort[route] = {"t_pre_ms": round(r_l.t_pre_ms, 2), "t_spmv_ms": round(t_l, 5),
                             "classes": r_l.class_names, "variant": list(r_l.variant),
                             "n_iters_min": n_iters(r_l.t_pre_ms, t_l)}
+        # Section IV-D's trivial optimizers: try every single optimization (5) or also every
+        # pair of them (15 in all), 64 timed SpMVs each, keep the fastest; t_pre is the whole
+        # search including each candidate's preprocessing
+        singles = {"delta16": dict(index=1, vec=1), "xl2": dict(xpath=1),
+                   "merge": dict(partition=1), "vector": dict(vec=1), "tile": dict(vec=1, vs=1)}
+        names = list(singles)
+        pairs = [(a, b) for i, a in enumerate(names) for b in names[i + 1:]]
+
+        def trivial(cands):
+            t0 = time.perf_counter()
+            best = None
+            for knobs in cands:
+                A.set_variant(stream=stream, **knobs)
+                t_c = timed(64, 2)
+                if best is None or t_c < best[0]:
+                    best = (t_c, knobs)
+            t_pre = (time.perf_counter() - t0) * 1e3
+            return {"t_pre_ms": round(t_pre, 2), "t_spmv_ms": round(best[0], 5),
+                    "candidates": len(cands), "best": best[1],
+                    "n_iters_min": n_iters(t_pre, best[0])}
+
+        single_c = [singles[n] for n in names]
+        amort["trivial_single"] = trivial(single_c)
+        amort["trivial_combined"] = trivial(single_c + [{**singles[a], **singles[b]}
+                                                       for a, b in pairs])
         A.tune("fixed", stream=stream, fixed=api.variant(*rep.variant))
     # every pool variant timed on this matrix: the paper's "oracle" (perfect optimizer)
     sweep = {}

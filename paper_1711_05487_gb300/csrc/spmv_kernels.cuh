@@ -281,8 +281,7 @@ template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2>
 __global__ void __launch_bounds__(kTileRows) k_rowtile_pipe(const RunArgs a) {
   using IdxT = typename std::conditional<D16, uint16_t, int32_t>::type;
   constexpr int S = 2;
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);           // S barriers, 16 B apart
+  extern __shared__ __align__(16) unsigned char smem[];   // S mbarriers 16 B apart, then stages
   const int rows = (int)blockDim.x;
   const int64_t n_tiles = (a.n_rows + rows - 1) / rows;
   const size_t vbytes = (size_t)a.tile_cap * sizeof(ValT);
