@@ -146,6 +146,15 @@ struct spmv_matrix {
   DevBuf small;                // 256 bytes for single-value reductions (maxima, codes)
   cudaStream_t copy_stream = nullptr;   // host-buffer runs: device-to-host copies of y
   cudaStream_t upload_stream = nullptr; // host-buffer runs: host-to-device copies of x
+  cudaStream_t capture_stream = nullptr;  // host-buffer runs: graph capture
+  cudaStream_t chunk_stream[2] = {};    // host-buffer runs: alternate chunks' kernels
+  cudaEvent_t joined[5] = {};           // host-buffer runs: fork from / rejoin the origin
+  cudaGraph_t host_graph = nullptr;     // host-buffer pipeline for (host_x, host_y, epoch)
+  cudaGraphExec_t host_exec = nullptr;
+  const void *host_x = nullptr;
+  void *host_y = nullptr;
+  uint64_t host_epoch = 0;
+  uint64_t epoch = 1;                   // bumped whenever precision or variant changes
   cudaEvent_t chunk_done[kHostChunks] = {};
   cudaEvent_t x_ready[kHostChunks] = {};
   int64_t x_need[kHostChunks] = {};     // elements of x (a prefix) chunks 0..c read
@@ -777,6 +786,25 @@ template <typename F> spmv_status guarded(F fn) {
   }
 }
 
+// True for page-locked (pinned or registered) host memory.
+bool is_page_locked(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
+void drop_host_graph(spmv_matrix *h) {
+  if (h->host_exec) cudaGraphExecDestroy(h->host_exec);
+  if (h->host_graph) cudaGraphDestroy(h->host_graph);
+  h->host_exec = nullptr;
+  h->host_graph = nullptr;
+  h->host_x = nullptr;
+  h->host_y = nullptr;
+}
+
 }  // namespace
 
 // ================================================================= C ABI ============
@@ -865,13 +893,19 @@ spmv_status spmv_create(spmv_handle_t *out, int64_t n_rows, int64_t n_cols, int6
 spmv_status spmv_destroy(spmv_handle_t h) {
   if (!h) return SPMV_ERR_ARG;
   cudaDeviceSynchronize();
+  drop_host_graph(h);
   if (h->copy_stream) {
     for (int c = 0; c < kHostChunks; ++c) {
       if (h->chunk_done[c]) cudaEventDestroy(h->chunk_done[c]);
       if (h->x_ready[c]) cudaEventDestroy(h->x_ready[c]);
     }
+    for (auto e : h->joined)
+      if (e) cudaEventDestroy(e);
     cudaStreamDestroy(h->copy_stream);
     cudaStreamDestroy(h->upload_stream);
+    cudaStreamDestroy(h->capture_stream);
+    for (auto st : h->chunk_stream)
+      if (st) cudaStreamDestroy(st);
   }
   for (DevBuf *b : {&h->rowptr, &h->colind, &h->val_in, &h->val_store, &h->dbase, &h->delta,
                     &h->esc, &h->coord, &h->tail_row, &h->tail_val, &h->head_val, &h->x_stage,
@@ -903,6 +937,7 @@ spmv_status spmv_set_precision(spmv_handle_t h, spmv_dtype storage, spmv_dtype v
     }
     h->vec = vec_type;
     h->acc = acc_type;
+    ++h->epoch;
     h->tuned = false;
     return SPMV_OK;
   });
@@ -915,6 +950,7 @@ spmv_status spmv_set_variant(spmv_handle_t h, const spmv_variant *v, spmv_stream
     spmv_variant w = *v;
     prepare_variant(h, w, s);
     h->variant = w;
+    ++h->epoch;
     h->tuned = true;
     return SPMV_OK;
   });
@@ -997,6 +1033,7 @@ spmv_status spmv_tune(spmv_handle_t h, spmv_mode mode, const spmv_tune_opts *opt
     CK(cudaStreamSynchronize(s));
     const double t3 = now_ms();
     h->variant = v;
+    ++h->epoch;
     h->tuned = true;
     rep.classes = cls;
     rep.mode_used = used;
@@ -1033,23 +1070,23 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
     if (!h->copy_stream) {
       CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
       CK(cudaStreamCreateWithFlags(&h->upload_stream, cudaStreamNonBlocking));
+      CK(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+      for (auto &st : h->chunk_stream) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
       for (int c = 0; c < kHostChunks; ++c) {
         CK(cudaEventCreateWithFlags(&h->chunk_done[c], cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&h->x_ready[c], cudaEventDisableTiming));
       }
+      for (auto &e : h->joined) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    // Row kernels compute any row range on their own (row pointers are absolute), so rows go
-    // in chunks aligned to 128-row tiles. Chunk c reads x only up to the largest column of
-    // chunks 0..c, so x is uploaded in matching pieces on one stream, each chunk waits for
-    // its piece, and each finished chunk of y is downloaded on another stream. Merge-path
-    // tiles span the whole matrix: one upload, one launch, one download.
     const bool chunked = h->variant.partition == 0 && h->n_rows >= 4 * kHostChunks * kTileRows;
     const int nch = chunked ? kHostChunks : 1;
+    // chunk row boundaries: equal parts aligned to 128 rows
     int64_t per = (h->n_rows + nch - 1) / nch;
     per = ((per + kTileRows - 1) / kTileRows) * kTileRows;
+    int64_t bounds[kHostChunks + 1];
+    for (int c = 0; c < nch; ++c) bounds[c] = std::min<int64_t>(h->n_rows, (int64_t)c * per);
+    bounds[nch] = h->n_rows;
     if (chunked && !h->x_need_valid) {
-      int64_t bounds[kHostChunks + 1];
-      for (int c = 0; c <= nch; ++c) bounds[c] = std::min<int64_t>(h->n_rows, (int64_t)c * per);
       DevBuf db;
       db.alloc(sizeof(bounds), 8, s);
       CK(cudaMemcpyAsync(db.p, bounds, sizeof(bounds), cudaMemcpyHostToDevice, s));
@@ -1065,42 +1102,80 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
       }
       h->x_need_valid = true;
     }
-    // the upload stream starts after work already queued on the caller's stream
-    CK(cudaEventRecord(h->chunk_done[0], s));
-    CK(cudaStreamWaitEvent(h->upload_stream, h->chunk_done[0], 0));
-    int64_t uploaded = 0;
+    // Row kernels compute any row range on their own (row pointers are absolute), so rows go
+    // in chunks aligned to 128-row tiles. Chunk c reads x only up to the largest column of
+    // chunks 0..c, so x is uploaded in matching pieces on one stream, each chunk waits for
+    // its piece, and each finished chunk of y is downloaded on another stream. Consecutive
+    // chunks' kernels go to two alternating streams, so one chunk's last partial wave of CTAs
+    // overlaps the next chunk's first; all side streams join back into `origin` at the end.
+    // Merge-path tiles span the whole matrix: one upload, one launch, one download.
     const KernelSet *ks = set_for(h);
-    for (int c = 0; c < nch; ++c) {
-      const int64_t need = chunked ? h->x_need[c] : h->n_cols;
-      if (need > uploaded) {
-        CK(cudaMemcpyAsync(static_cast<char *>(h->x_stage.p) + vb * (size_t)uploaded,
-                           static_cast<const char *>(x_host) + vb * (size_t)uploaded,
-                           vb * (size_t)(need - uploaded), cudaMemcpyHostToDevice,
-                           h->upload_stream));
-        uploaded = need;
+    auto enqueue = [&](cudaStream_t origin) {
+      cudaStream_t side[4] = {h->upload_stream, h->copy_stream, h->chunk_stream[0],
+                              h->chunk_stream[1]};
+      CK(cudaEventRecord(h->joined[4], origin));
+      for (cudaStream_t st : side) CK(cudaStreamWaitEvent(st, h->joined[4], 0));
+      int64_t uploaded = 0;
+      for (int c = 0; c < nch; ++c) {
+        const int64_t need = chunked ? h->x_need[c] : h->n_cols;
+        if (need > uploaded) {
+          CK(cudaMemcpyAsync(static_cast<char *>(h->x_stage.p) + vb * (size_t)uploaded,
+                             static_cast<const char *>(x_host) + vb * (size_t)uploaded,
+                             vb * (size_t)(need - uploaded), cudaMemcpyHostToDevice,
+                             h->upload_stream));
+          uploaded = need;
+        }
+        CK(cudaEventRecord(h->x_ready[c], h->upload_stream));
+        cudaStream_t cs = h->chunk_stream[c & 1];
+        CK(cudaStreamWaitEvent(cs, h->x_ready[c], 0));
+        const int64_t r0 = bounds[c], r1 = bounds[c + 1];
+        if (r1 <= r0) continue;
+        if (nch == 1) {
+          CK(launch_run(h, h->variant, h->x_stage.p, h->y_stage.p, cs));
+        } else {
+          RunArgs a = run_args(h, h->x_stage.p, static_cast<char *>(h->y_stage.p) + vb * (size_t)r0);
+          a.n_rows = r1 - r0;
+          a.rowptr += r0;
+          if (a.dbase) a.dbase += r0;
+          CK(ks->spmv(h->variant, a, cs));
+        }
+        CK(cudaEventRecord(h->chunk_done[c], cs));
+        CK(cudaStreamWaitEvent(h->copy_stream, h->chunk_done[c], 0));
+        CK(cudaMemcpyAsync(static_cast<char *>(y_host) + vb * (size_t)r0,
+                           static_cast<char *>(h->y_stage.p) + vb * (size_t)r0,
+                           vb * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, h->copy_stream));
       }
-      CK(cudaEventRecord(h->x_ready[c], h->upload_stream));
-      CK(cudaStreamWaitEvent(s, h->x_ready[c], 0));
-      const int64_t r0 = std::min<int64_t>(h->n_rows, (int64_t)c * per);
-      const int64_t r1 = nch == 1 ? h->n_rows : std::min<int64_t>(h->n_rows, r0 + per);
-      if (r1 <= r0) continue;
-      if (nch == 1) {
-        CK(launch_run(h, h->variant, h->x_stage.p, h->y_stage.p, s));
-      } else {
-        RunArgs a = run_args(h, h->x_stage.p, static_cast<char *>(h->y_stage.p) + vb * (size_t)r0);
-        a.n_rows = r1 - r0;
-        a.rowptr += r0;
-        if (a.dbase) a.dbase += r0;
-        CK(ks->spmv(h->variant, a, s));
+      for (int k = 0; k < 4; ++k) {
+        CK(cudaEventRecord(h->joined[k], side[k]));
+        CK(cudaStreamWaitEvent(origin, h->joined[k], 0));
       }
-      CK(cudaEventRecord(h->chunk_done[c], s));
-      CK(cudaStreamWaitEvent(h->copy_stream, h->chunk_done[c], 0));
-      CK(cudaMemcpyAsync(static_cast<char *>(y_host) + vb * (size_t)r0,
-                         static_cast<char *>(h->y_stage.p) + vb * (size_t)r0,
-                         vb * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, h->copy_stream));
+    };
+    if (is_page_locked(x_host) && is_page_locked(y_host)) {
+      // Page-locked buffers: the whole pipeline (uploads, chunk kernels, downloads and the
+      // events between the three streams) is captured once into a CUDA graph per pair of
+      // host buffers and tuning state, then replayed with one launch per call.
+      if (!h->host_exec || h->host_x != x_host || h->host_y != y_host ||
+          h->host_epoch != h->epoch) {
+        drop_host_graph(h);
+        CK(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeRelaxed));
+        try {
+          enqueue(h->capture_stream);
+        } catch (...) {
+          cudaGraph_t g = nullptr;
+          cudaStreamEndCapture(h->capture_stream, &g);
+          if (g) cudaGraphDestroy(g);
+          throw;
+        }
+        CK(cudaStreamEndCapture(h->capture_stream, &h->host_graph));
+        CK(cudaGraphInstantiate(&h->host_exec, h->host_graph, 0));
+        h->host_x = x_host;
+        h->host_y = y_host;
+        h->host_epoch = h->epoch;
+      }
+      CK(cudaGraphLaunch(h->host_exec, s));
+    } else {
+      enqueue(s);
     }
-    CK(cudaStreamSynchronize(h->copy_stream));
-    CK(cudaStreamSynchronize(h->upload_stream));
     CK(cudaStreamSynchronize(s));
     return SPMV_OK;
   });

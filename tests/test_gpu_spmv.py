@@ -307,3 +307,26 @@ def test_df64_tune_and_reject_non_f64_input(api, torch):
         B.set_precision("df64", "f64", "df64")
     with pytest.raises(SpmvError):
         A.set_precision("df64", "f32", "df64")
+
+
+def test_run_host_graph_replays_follow_buffers_and_variants(api, torch):
+    """Page-locked buffers take the captured-graph path: a new buffer pair or a new variant
+    is re-captured, and pageable buffers take the eager path; all equal the device run."""
+    m = synth.stencil_27pt(30)
+    A = api.SpmvMatrix.from_csr(m)
+    xs = [synth.uniform_vector(m.n_cols, s) for s in (71, 72)]
+    outs = {}
+    for v in (dict(index=1, vec=1, vs=1, tile_rows=32), dict(vec=1, vs=4), dict(partition=1)):
+        A.set_variant(**v)
+        for pin in (True, False):
+            for k, x64 in enumerate(xs):
+                xh = torch.from_numpy(x64)
+                yh = torch.full((m.n_rows,), float("nan"), dtype=torch.float64)
+                if pin:
+                    xh, yh = xh.pin_memory(), yh.pin_memory()
+                for _ in range(2):                       # capture, then replay
+                    A.run_host(xh, yh)
+                    want = A.run(torch.from_numpy(x64).cuda()).cpu()
+                    assert torch.equal(want, yh), (v, pin, k)
+                outs[(str(v), pin, k)] = yh.clone()
+        assert torch.equal(outs[(str(v), True, 0)], outs[(str(v), False, 0)])
