@@ -1,0 +1,315 @@
+// Thread-per-row tile kernels (sub-warp width 1) and their launchers: a tile of 32, 64 or
+// 128 consecutive rows is staged into shared memory by bulk asynchronous copies (TMA) and
+// each thread walks its own row with one fused multiply-add per nonzero (CMP on GB300's
+// FP64 pipe; MB with 16-bit column deltas).
+//  k_rowtile       - one tile per CTA;
+//  k_rowtile_pipe  - persistent CTAs keeping the next tile's bulk copy in flight.
+// Included by spmv_kernels.cuh; kept apart so that a measurement of these kernels can name
+// exactly the sources it was taken on.
+#pragma once
+
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace spmv {
+
+// ----------------------------------------------------------------------- k_rowtile ----
+// One thread per row over a tile of blockDim.x (32, 64 or 128) consecutive rows (sub-warp
+// width 1). The
+// tile's values and column indices (int32 or 16-bit deltas) are staged into shared memory
+// by two bulk asynchronous copies (TMA) completing on an mbarrier, so the DRAM stream is
+// fully coalesced whatever the row lengths; then each thread walks its own row with one
+// fused multiply-add per nonzero and no cross-lane reduction. On GB300 the FP64 pipe
+// retires only ~2 FMA lanes per clock per SM, so spending exactly one FP64 instruction per
+// nonzero is what lets FP64 SpMV reach the memory roofline. A tile whose staged size
+// exceeds tile_cap is computed from global memory instead (a warp per row).
+template <typename ValT, typename IdxT>
+__host__ __device__ constexpr int tile_elem_bytes() {
+  return (int)(sizeof(ValT) + sizeof(IdxT));
+}
+
+// Dot product of one row whose values and columns sit in shared memory at offset o (the
+// row's first element) of a staged tile: 8 gathers of x in flight per thread, then 8 FMAs;
+// the exact trip count keeps the FP64 pipe free of masked-off work.
+template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2, typename IdxT>
+__device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
+                                             const IdxT *sidx, int o, int len, int32_t base,
+                                             const VecT *__restrict__ x, uint64_t pol_x) {
+  AccT acc = 0;
+  // Column of element k: int32 from shared memory, or the running sum of 16-bit deltas
+  // from the row's base column, or (escape rows) the full column kept in global memory.
+  const int32_t *ec = nullptr;
+  int c = base;
+  if constexpr (D16) {
+    if (base < 0) ec = a.esc + (-(int64_t)base - 1);
+  }
+  auto column = [&](int k) -> int {
+    if constexpr (D16) {
+      if (ec) return __ldg(ec + k);
+      c += (int)sidx[o + k];
+      return c;
+    } else {
+      return (int)sidx[o + k];
+    }
+  };
+  int k = 0;
+  for (; k + 8 <= len; k += 8) {
+    AccT xv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) xv[q] = (AccT)ldx<XL2>(x + column(k + q), pol_x);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc = fma(widen<AccT>(sval[o + k + q]), xv[q], acc);
+  }
+  for (; k < len; ++k) acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2>(x + column(k), pol_x), acc);
+  return acc;
+}
+
+// Rows [r0, r1) straight from global memory, a warp per row (tiles larger than the staged
+// capacity).
+template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2>
+__device__ __forceinline__ void tile_direct(const RunArgs &a, int64_t r0, int64_t r1,
+                                            const VecT *__restrict__ x, VecT *__restrict__ y,
+                                            uint64_t pol_x) {
+  const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t r = r0 + warp; r < r1; r += blockDim.x / 32) {
+    const int s = __ldg(a.rowptr + r), e = __ldg(a.rowptr + r + 1);
+    AccT acc = 0;
+    if constexpr (D16) {
+      const int32_t base = __ldg(a.dbase + r);
+      if (base < 0) {
+        const int32_t *ec = a.esc + (-(int64_t)base - 1) - s;
+        for (int j = s + lane; j < e; j += 32)
+          acc += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(ec + j), pol_x);
+      } else {
+        // decode the row's deltas: the lane sums its own and its predecessors' deltas
+        int run = base;
+        for (int j0 = s; j0 < e; j0 += 32) {
+          const int j = j0 + lane;
+          const int d = j < e ? (int)a.delta[j] : 0;
+          const int incl = group_incl_scan<32>(d, lane, 0xffffffffu);
+          if (j < e) acc += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + (run + incl), pol_x);
+          run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+      }
+    } else {
+      for (int j = s + lane; j < e; j += 32)
+        acc += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(a.colind + j), pol_x);
+    }
+    acc = group_sum<32>(acc, 0xffffffffu);
+    if (lane == 0) y[r] = (VecT)acc;
+  }
+}
+
+template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2>
+__global__ void __launch_bounds__(kTileRows) k_rowtile(const RunArgs a) {
+  using IdxT = typename std::conditional<D16, uint16_t, int32_t>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+  const int rows = (int)blockDim.x;
+  const int64_t r0 = (int64_t)blockIdx.x * rows;
+  const int64_t r1 = min(r0 + (int64_t)rows, a.n_rows);
+  const int s0 = __ldg(a.rowptr + r0), s1 = __ldg(a.rowptr + r1);
+  const int a0 = s0 & ~7;                        // 8-element (>= 16-byte) aligned start
+  const int nc = ((s1 - a0) + 7) & ~7;           // staged elements
+  const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
+  const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
+  VecT *__restrict__ y = static_cast<VecT *>(a.y);
+  uint64_t pol_x = 0;
+  if constexpr (XL2) pol_x = policy_evict_last();
+  const int64_t row = r0 + threadIdx.x;
+  if (nc <= a.tile_cap) {
+    ValT *sval = reinterpret_cast<ValT *>(smem + 16);
+    IdxT *sidx = reinterpret_cast<IdxT *>(smem + 16 + (size_t)a.tile_cap * sizeof(ValT));
+    const IdxT *gidx;
+    if constexpr (D16) gidx = a.delta;
+    else gidx = a.colind;
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      if (nc > 0) {
+        const uint64_t pol = policy_evict_first();
+        const uint32_t bv = (uint32_t)nc * (uint32_t)sizeof(ValT);
+        const uint32_t bi = (uint32_t)nc * (uint32_t)sizeof(IdxT);
+        mbar_expect_tx(bar, bv + bi);
+        bulk_g2s(sval, val + a0, bv, bar, pol);
+        bulk_g2s(sidx, gidx + a0, bi, bar, pol);
+      }
+    }
+    // row bounds while the copies are in flight
+    int s = 0, e = 0;
+    int32_t base = 0;
+    if (row < r1) {
+      s = __ldg(a.rowptr + row);
+      e = __ldg(a.rowptr + row + 1);
+      if constexpr (D16) base = __ldg(a.dbase + row);
+    }
+    __syncthreads();   // the barrier is initialised before anyone waits on it
+    if (nc > 0) {
+      if (!mbar_wait_bounded(bar, 0, kWaitLimitNs)) {
+        if (threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
+        mbar_wait_bounded(bar, 0, kWaitLimitNs);   // let the copies land before exiting
+        return;
+      }
+    }
+    if (row >= r1) return;
+    y[row] = (VecT)tile_row_dot<ValT, VecT, AccT, D16, XL2>(a, sval, sidx, s - a0, e - s, base,
+                                                           x, pol_x);
+  } else {
+    // oversize tile: a warp per row straight from global memory
+    tile_direct<ValT, VecT, AccT, D16, XL2>(a, r0, r1, x, y, pol_x);
+  }
+}
+
+
+// Persistent variant: a resident grid in which every CTA walks tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ... with two shared-memory stages, so that the bulk copy of its
+// next tile is in flight while it computes the current one. Stage s is refilled only after
+// all threads passed the barrier that ends their reads of it.
+template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2>
+__global__ void __launch_bounds__(kTileRows) k_rowtile_pipe(const RunArgs a) {
+  using IdxT = typename std::conditional<D16, uint16_t, int32_t>::type;
+  constexpr int S = 2;
+  extern __shared__ __align__(16) unsigned char smem[];   // S mbarriers 16 B apart, then stages
+  const int rows = (int)blockDim.x;
+  const int64_t n_tiles = (a.n_rows + rows - 1) / rows;
+  const size_t vbytes = (size_t)a.tile_cap * sizeof(ValT);
+  const size_t stage_bytes = vbytes + (size_t)a.tile_cap * sizeof(IdxT);
+  unsigned char *stage0 = smem + 16 * S;
+  const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
+  const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
+  VecT *__restrict__ y = static_cast<VecT *>(a.y);
+  const IdxT *gidx;
+  if constexpr (D16) gidx = a.delta;
+  else gidx = a.colind;
+  uint64_t pol_x = 0;
+  if constexpr (XL2) pol_x = policy_evict_last();
+  auto tile_span = [&](int64_t t, int64_t &r0, int64_t &r1, int &a0, int &nc) {
+    r0 = t * rows;
+    r1 = min(r0 + (int64_t)rows, a.n_rows);
+    const int s0 = __ldg(a.rowptr + r0), s1 = __ldg(a.rowptr + r1);
+    a0 = s0 & ~7;
+    nc = ((s1 - a0) + 7) & ~7;
+  };
+  auto issue = [&](int64_t t, int st) {   // one thread
+    int64_t r0, r1;
+    int a0, nc;
+    tile_span(t, r0, r1, a0, nc);
+    uint64_t *b = reinterpret_cast<uint64_t *>(smem + 16 * st);
+    if (nc > 0 && nc <= a.tile_cap) {
+      const uint64_t pol = policy_evict_first();
+      const uint32_t bv = (uint32_t)nc * (uint32_t)sizeof(ValT);
+      const uint32_t bi = (uint32_t)nc * (uint32_t)sizeof(IdxT);
+      unsigned char *dst = stage0 + (size_t)st * stage_bytes;
+      mbar_expect_tx(b, bv + bi);
+      bulk_g2s(dst, val + a0, bv, b, pol);
+      bulk_g2s(dst + vbytes, gidx + a0, bi, b, pol);
+    } else {
+      mbar_arrive(b);                      // nothing staged: complete the phase now
+    }
+  };
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < S; ++st) mbar_init(reinterpret_cast<uint64_t *>(smem + 16 * st), 1);
+    for (int st = 0; st < S; ++st) {
+      const int64_t t = (int64_t)blockIdx.x + (int64_t)st * gridDim.x;
+      if (t < n_tiles) issue(t, st);
+    }
+  }
+  __syncthreads();
+  for (int64_t i = 0;; ++i) {
+    const int64_t t = (int64_t)blockIdx.x + i * gridDim.x;
+    if (t >= n_tiles) break;
+    const int st = (int)(i % S);
+    const uint32_t parity = (uint32_t)((i / S) & 1);
+    int64_t r0, r1;
+    int a0, nc;
+    tile_span(t, r0, r1, a0, nc);
+    const int64_t row = r0 + threadIdx.x;
+    int s = 0, e = 0;
+    int32_t base = 0;
+    if (row < r1) {
+      s = __ldg(a.rowptr + row);
+      e = __ldg(a.rowptr + row + 1);
+      if constexpr (D16) base = __ldg(a.dbase + row);
+    }
+    uint64_t *b = reinterpret_cast<uint64_t *>(smem + 16 * st);
+    const bool ok = mbar_wait_bounded(b, parity, kWaitLimitNs);
+    if (!__syncthreads_and(ok)) {
+      // give up: record the error and let every copy in flight land before exiting
+      if (threadIdx.x == 0 && a.err) atomicExch(a.err, 1);
+      for (int q = 0; q < S; ++q) {
+        const int64_t tq = (int64_t)blockIdx.x + (i + q) * gridDim.x;
+        if (tq < n_tiles)
+          mbar_wait_bounded(reinterpret_cast<uint64_t *>(smem + 16 * ((i + q) % S)),
+                            (uint32_t)(((i + q) / S) & 1), kWaitLimitNs);
+      }
+      return;
+    }
+    if (nc <= a.tile_cap) {
+      const ValT *sval = reinterpret_cast<const ValT *>(stage0 + (size_t)st * stage_bytes);
+      const IdxT *sidx = reinterpret_cast<const IdxT *>(stage0 + (size_t)st * stage_bytes + vbytes);
+      if (row < r1)
+        y[row] = (VecT)tile_row_dot<ValT, VecT, AccT, D16, XL2>(a, sval, sidx, s - a0, e - s,
+                                                               base, x, pol_x);
+    } else {
+      tile_direct<ValT, VecT, AccT, D16, XL2>(a, r0, r1, x, y, pol_x);
+    }
+    __syncthreads();                       // every thread is done with stage st
+    if (threadIdx.x == 0) {
+      const int64_t t2 = (int64_t)blockIdx.x + (i + S) * gridDim.x;
+      if (t2 < n_tiles) issue(t2, st);
+    }
+  }
+}
+
+template <typename K>
+cudaError_t ensure_smem(K kernel, size_t smem, int &configured) {
+  if (smem > 48 * 1024 && configured < (int)smem) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = (int)smem;
+  }
+  return cudaSuccess;
+}
+
+template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2>
+cudaError_t launch_rowtile_k(const RunArgs &a, cudaStream_t s) {
+  using IdxT = typename std::conditional<D16, uint16_t, int32_t>::type;
+  const int rows = a.tile_rows > 0 ? a.tile_rows : kTileRows;
+  const size_t per_stage = (size_t)a.tile_cap * (sizeof(ValT) + sizeof(IdxT));
+  if (a.tile_pipe) {
+    static int configured = 0;
+    auto kern = k_rowtile_pipe<ValT, VecT, AccT, D16, XL2>;
+    const size_t smem = 32 + 2 * per_stage;
+    cudaError_t e = ensure_smem(kern, smem, configured);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, rows, smem);
+    const int64_t n_tiles = (a.n_rows + rows - 1) / rows;
+    int64_t g = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    if (g > n_tiles) g = n_tiles;
+    kern<<<(unsigned)g, rows, smem, s>>>(a);
+    return cudaGetLastError();
+  }
+  static int configured = 0;
+  const size_t smem = 16 + per_stage;
+  cudaError_t e = ensure_smem(k_rowtile<ValT, VecT, AccT, D16, XL2>, smem, configured);
+  if (e != cudaSuccess) return e;
+  const unsigned g = (unsigned)((a.n_rows + rows - 1) / rows);
+  k_rowtile<ValT, VecT, AccT, D16, XL2><<<g, rows, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename ValT, typename VecT, typename AccT>
+cudaError_t launch_rowtile(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
+  const bool d16 = v.index == 1, xl2 = v.xpath != 0;
+  if (d16) return xl2 ? launch_rowtile_k<ValT, VecT, AccT, true, true>(a, s)
+                      : launch_rowtile_k<ValT, VecT, AccT, true, false>(a, s);
+  return xl2 ? launch_rowtile_k<ValT, VecT, AccT, false, true>(a, s)
+             : launch_rowtile_k<ValT, VecT, AccT, false, false>(a, s);
+}
+
+}  // namespace spmv
