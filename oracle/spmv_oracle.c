@@ -19,6 +19,8 @@
  *   - 16-bit delta column-index format       (Section III-E, MB optimization)
  *   - merge-path coordinates of a CSR matrix (Section III-E, IMB optimization: the
  *     nnz-balanced work split)
+ *   - row decomposition into short, medium and chunked long rows (Section III-E, IMB:
+ *     the matrix decomposition of Fig. 5)
  *   - Table I matrix features                (Section III-D)
  *   - P_MB and P_peak bounds                 (Section III-B)
  *   - Classify rule set                      (Section III-C, Fig. 3)
@@ -294,6 +296,40 @@ int64_t oracle_cg(int64_t n, const int32_t *rowptr, const int32_t *colind, const
   free(p);
   free(ap);
   return k;
+}
+
+/* Row decomposition for thread imbalance (Section III-E, IMB: A = A_short + A_long, Fig. 5):
+ * a row of length len is long when len >= chunk, medium when l_med <= len < chunk, short
+ * otherwise. Long row r is cut into chunks [z, min(z + chunk, rowptr[r+1])) for
+ * z = rowptr[r], rowptr[r] + chunk, ... . Outputs in row order: med_rows[], long_rows[],
+ * long_first[] (first chunk of each long row, then the chunk count), chunks[] as
+ * (row, begin, end, 0). counts[0..2] = medium rows, long rows, chunks.                   */
+void oracle_row_bins(int64_t n_rows, const int32_t *rowptr, int32_t l_med, int32_t chunk,
+                     int32_t *med_rows, int32_t *long_rows, int32_t *long_first,
+                     int32_t *chunks, int64_t *counts) {
+  int64_t n_med = 0, n_long = 0, n_ch = 0;
+  for (int64_t r = 0; r < n_rows; ++r) {
+    const int32_t b = rowptr[r], e = rowptr[r + 1];
+    const int32_t len = e - b;
+    if (len >= chunk) {
+      long_rows[n_long] = (int32_t)r;
+      long_first[n_long] = (int32_t)n_ch;
+      ++n_long;
+      for (int32_t z = b; z < e; z += chunk) {
+        chunks[4 * n_ch] = (int32_t)r;
+        chunks[4 * n_ch + 1] = z;
+        chunks[4 * n_ch + 2] = (z + chunk < e) ? z + chunk : e;
+        chunks[4 * n_ch + 3] = 0;
+        ++n_ch;
+      }
+    } else if (len >= l_med) {
+      med_rows[n_med++] = (int32_t)r;
+    }
+  }
+  long_first[n_long] = (int32_t)n_ch;
+  counts[0] = n_med;
+  counts[1] = n_long;
+  counts[2] = n_ch;
 }
 
 /* ---------------------------------------------------------------------------------- */

@@ -184,3 +184,50 @@ def test_df_split_known_bits_and_error_bound():
     r = np.array([float(Fraction(a) - Fraction(b) - Fraction(c)) for a, b, c in zip(v, hi, lo)])
     assert np.all(np.abs(r) < 2.0 ** -46 * np.abs(v))
     assert np.all(np.sign(r) * np.sign(v) >= 0)          # truncation toward zero
+
+
+# ------------------------------------------------------------------ row decomposition
+def test_row_bins_hand_example():
+    # row lengths 1, 5, 0, 12, 3, 9 with l_med = 3 and chunk = 5: rows 0 and 2 are short,
+    # row 4 (length 3) is medium, rows 1, 3 and 5 are long and cut into chunks of 5
+    lens = [1, 5, 0, 12, 3, 9]
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    med, lng, first, ch = oracle.row_bins(rp, l_med=3, chunk=5)
+    assert list(med) == [4]
+    assert list(lng) == [1, 3, 5]
+    assert list(first) == [0, 1, 4, 6]
+    assert [tuple(c) for c in ch] == [(1, 1, 6, 0), (3, 6, 11, 0), (3, 11, 16, 0),
+                                      (3, 16, 18, 0), (5, 21, 26, 0), (5, 26, 30, 0)]
+
+
+def test_row_bins_partition_the_matrix_exactly():
+    """A_short + A_medium + A_long = A: every nonzero belongs to exactly one short row,
+    medium row or chunk, and rebuilding the product from the pieces gives the oracle's y."""
+    m = synth.power_law(30_000, alpha=1.4, clip=30_000, seed=17, dtype=np.float64)
+    med, lng, first, ch = oracle.row_bins(m.rowptr, l_med=64, chunk=4096)
+    lens = np.diff(m.rowptr)
+    owner = np.full(m.nnz, -1, np.int64)
+    for r in np.where(lens < 64)[0]:
+        owner[m.rowptr[r]:m.rowptr[r + 1]] = 0
+    for r in med:
+        assert 64 <= lens[r] < 4096
+        assert np.all(owner[m.rowptr[r]:m.rowptr[r + 1]] == -1)
+        owner[m.rowptr[r]:m.rowptr[r + 1]] = 1
+    assert len(lng) > 0 and np.all(lens[lng] >= 4096)
+    for i, r in enumerate(lng):
+        cs = ch[first[i]:first[i + 1]]
+        assert np.all(cs[:, 0] == r)
+        assert cs[0, 1] == m.rowptr[r] and cs[-1, 2] == m.rowptr[r + 1]
+        assert np.all(cs[1:, 1] == cs[:-1, 2])
+        assert np.all(cs[:-1, 2] - cs[:-1, 1] == 4096) and 0 < cs[-1, 2] - cs[-1, 1] <= 4096
+        for _, b, e, _ in cs:
+            assert np.all(owner[b:e] == -1)
+            owner[b:e] = 2
+    assert np.all(owner >= 0)
+    x = synth.uniform_vector(m.n_cols, 18)
+    y, _ = oracle.spmv(m.rowptr, m.colind, m.val, x)
+    prod = m.val * x[m.colind]
+    y2 = np.zeros(m.n_rows)
+    rows_of = np.repeat(np.arange(m.n_rows), lens)
+    np.add.at(y2, rows_of, prod)
+    assert np.allclose(y2, y, rtol=0, atol=1e-9)
