@@ -68,8 +68,12 @@ enum { SPMV_CLASS_MB = 1, SPMV_CLASS_ML = 2, SPMV_CLASS_IMB = 4, SPMV_CLASS_CMP 
 /* One point of the optimization pool (Table II, applied jointly). */
 typedef struct {
   int32_t partition; /* 0: one sub-warp per row, rows handed to CTAs by the hardware
-                        scheduler; 1: merge-path tiles, long rows split across tiles
-                        (the matrix decomposition of Fig. 4/5)                            */
+                        scheduler; 1: merge-path tiles, long rows split across tiles;
+                        2: row decomposition (A = A_short + A_long, Fig. 5): rows under
+                        64 nonzeros on sub-warps of vs lanes (2, 4 or 8), rows under
+                        4096 on one warp each, longer rows in 4096-nonzero chunks summed
+                        in FP64 in chunk order. 1 and 2 are the decompositions of
+                        Section III-E (IMB); the autotuner picks between them         */
   int32_t index;     /* 0: int32 columns; 1: 16-bit column deltas with escape rows (MB)   */
   int32_t xpath;     /* 0: default; 1: x kept L2-resident (evict-last gathers through the
                         read-only path, evict-first streams) (ML)                         */
@@ -204,6 +208,16 @@ spmv_status spmv_get_delta16(spmv_handle_t h, int32_t *base, uint16_t *delta,
  * *n_tiles and *items_per_tile. */
 spmv_status spmv_get_merge_path(spmv_handle_t h, int32_t *coord, int64_t *n_tiles,
                                 int64_t *items_per_tile, spmv_stream_t stream);
+
+/* Copies the row decomposition of partition 2 (device arrays, int32): med_rows[n_med] the
+ * rows of 64..4095 nonzeros, long_rows[n_long] the rows of 4096 or more, long_first
+ * [n_long + 1] each long row's first chunk (the last entry is n_chunks), chunks[4 * n_chunks]
+ * as (row, first nonzero, end nonzero, 0), all in row order. counts (host, int64[3])
+ * receives n_med, n_long, n_chunks; pass med_rows = NULL to query counts only.
+ * SPMV_ERR_NOT_TUNED if no decomposition has been built. */
+spmv_status spmv_get_row_bins(spmv_handle_t h, int32_t *med_rows, int32_t *long_rows,
+                              int32_t *long_first, int32_t *chunks, int64_t *counts,
+                              spmv_stream_t stream);
 
 /* Section III-D, Table I features computed on the device (exact integer moments, host
  * finalization); line_bytes is the cache-line size for misses_i (128 = GPU L2 line,

@@ -104,6 +104,7 @@ _DECL = {
     "spmv_export_csr": (_I32, [_P, _P, _P, _P, _P]),
     "spmv_get_delta16": (_I32, [_P, _P, _P, _P, ctypes.POINTER(_I64), _P]),
     "spmv_get_merge_path": (_I32, [_P, _P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P]),
+    "spmv_get_row_bins": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
     "spmv_features": (_I32, [_P, _I32, _P, _P, _P]),
     "spmv_profile": (_I32, [_P, _I32, ctypes.POINTER(spmv_profile_report), _P]),
     "spmv_profile_cta_times": (_I32, [_P, _P, _P, ctypes.POINTER(_I32), _P]),
@@ -230,6 +231,15 @@ def spmv_get_delta16(h, base=None, delta=None, esc_col=None, stream=0) -> int:
     n = _I64()
     _call("spmv_get_delta16", h, base, delta, esc_col, ctypes.byref(n), stream)
     return n.value
+
+
+def spmv_get_row_bins(h, med_rows=None, long_rows=None, long_first=None, chunks=None,
+                      stream=0):
+    """Returns (n_med, n_long, n_chunks); copies the lists when the pointers are given."""
+    counts = (_I64 * 3)()
+    _call("spmv_get_row_bins", h, med_rows, long_rows, long_first, chunks,
+          ctypes.cast(counts, _P), stream)
+    return int(counts[0]), int(counts[1]), int(counts[2])
 
 
 def spmv_get_merge_path(h, coord=None, stream=0):

@@ -224,6 +224,18 @@ class SpmvMatrix:
                               _stream(stream))
         return base[:self.n_rows], delta[:self.nnz], esc[:n_esc]
 
+    def row_bins(self, device="cuda", stream=None):
+        """The row decomposition (partition 2): medium rows, long rows, each long row's first
+        chunk, and the chunk table (row, first nonzero, end nonzero, 0)."""
+        n_med, n_long, n_ch = _abi.spmv_get_row_bins(self._h)
+        med = torch.empty(max(n_med, 1), dtype=torch.int32, device=device)
+        lng = torch.empty(max(n_long, 1), dtype=torch.int32, device=device)
+        first = torch.empty(n_long + 1, dtype=torch.int32, device=device)
+        ch = torch.empty((max(n_ch, 1), 4), dtype=torch.int32, device=device)
+        _abi.spmv_get_row_bins(self._h, med.data_ptr(), lng.data_ptr(), first.data_ptr(),
+                               ch.data_ptr(), _stream(stream))
+        return med[:n_med], lng[:n_long], first, ch[:n_ch]
+
     def merge_path(self, device="cuda", stream=None):
         n_tiles, items = _abi.spmv_get_merge_path(self._h)
         c = torch.empty((n_tiles + 1, 2), dtype=torch.int32, device=device)

@@ -43,7 +43,8 @@ def mean_gain(ds: dict, idx, thr) -> float:
     cls = classes_for(ds, idx, thr)
     ch = np.array([_candidate(c, a, m) for c, a, m in
                    zip(cls, ds["nnz_avg"][idx], ds["nnz_max"][idx])])
-    t = ds["times"][idx]
+    from .selector_train import family_times
+    t = family_times(ds["times"][idx])
     return float(np.mean(t[:, 0] / t[np.arange(len(idx)), ch]))
 
 

@@ -136,6 +136,10 @@ struct spmv_matrix {
   DevBuf coord, tail_row, tail_val, head_val;
   int64_t n_tiles = 0;
   bool has_merge = false;
+  DevBuf bin_rows, bin_long_rows, bin_long_first, bin_chunks, bin_partials;
+  int64_t bin_n_med = 0, bin_n_long = 0, bin_n_chunks = 0;
+  int32_t bin_vs_short = 4;
+  bool has_bins = false;
   // run state
   spmv_variant variant{};
   bool tuned = false;
@@ -202,6 +206,16 @@ RunArgs run_args(const spmv_matrix *h, const void *x, void *y) {
   a.tile_pipe = h->tile_pipe;
   a.err = h->d_err.as<int32_t>();
   a.val_df = h->val_df.p;
+  a.bin_l_med = kBinMed;
+  a.bin_vs_short = h->bin_vs_short;
+  a.bin_rows = h->bin_rows.as<int32_t>();
+  a.bin_n_med = h->bin_n_med;
+  a.bin_chunks = h->bin_chunks.as<int4>();
+  a.bin_n_chunks = h->bin_n_chunks;
+  a.bin_long_rows = h->bin_long_rows.as<int32_t>();
+  a.bin_long_first = h->bin_long_first.as<int32_t>();
+  a.bin_n_long = h->bin_n_long;
+  a.bin_partials = h->bin_partials.as<double>();
   return a;
 }
 
@@ -241,6 +255,41 @@ void build_merge(spmv_matrix *h, cudaStream_t s) {
   CK(cudaStreamSynchronize(s));
   h->n_tiles = n_tiles;
   h->has_merge = true;
+}
+
+// Row decomposition tables (partition 2): three exclusive scans over per-row counts place
+// each medium row in the row list and each long row's chunks in the chunk table.
+void build_bins(spmv_matrix *h, cudaStream_t s) {
+  if (h->has_bins) return;
+  const int64_t n = h->n_rows;
+  DevBuf cnt;
+  cnt.alloc(sizeof(int64_t) * 3 * (size_t)(n + 1), 8, s, true);
+  int64_t *med = cnt.as<int64_t>(), *lng = med + (n + 1), *nch = lng + (n + 1);
+  CK(launch_bin_counts(n, h->rowptr.as<int32_t>(), kBinMed, kBinChunk, med, lng, nch, s));
+  const int64_t se = scan_scratch_elems(n);
+  DevBuf scr;
+  scr.alloc(sizeof(int64_t) * (size_t)se, 8, s);
+  for (int64_t *p : {med, lng, nch}) CK(launch_scan_i64(p, n, p + n, scr.as<int64_t>(), se, s));
+  int64_t tot[3];
+  for (int q = 0; q < 3; ++q)
+    CK(cudaMemcpyAsync(tot + q, med + (int64_t)q * (n + 1) + n, sizeof(int64_t),
+                       cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  h->bin_rows.alloc(4 * (size_t)std::max<int64_t>(tot[0], 1), 4, s);
+  h->bin_long_rows.alloc(4 * (size_t)std::max<int64_t>(tot[1], 1), 4, s);
+  h->bin_long_first.alloc(4 * (size_t)(tot[1] + 1), 4, s);
+  h->bin_chunks.alloc(16 * (size_t)std::max<int64_t>(tot[2], 1), 16, s);
+  h->bin_partials.alloc(8 * (size_t)std::max<int64_t>(tot[2], 1), 8, s);
+  const int32_t last = (int32_t)tot[2];
+  CK(cudaMemcpyAsync(h->bin_long_first.as<int32_t>() + tot[1], &last, 4, cudaMemcpyHostToDevice, s));
+  CK(launch_bin_fill(n, h->rowptr.as<int32_t>(), kBinMed, kBinChunk, med, lng, nch,
+                     h->bin_rows.as<int32_t>(), h->bin_long_rows.as<int32_t>(),
+                     h->bin_long_first.as<int32_t>(), h->bin_chunks.as<int4>(), s));
+  CK(cudaStreamSynchronize(s));
+  h->bin_n_med = tot[0];
+  h->bin_n_long = tot[1];
+  h->bin_n_chunks = tot[2];
+  h->has_bins = true;
 }
 
 // Geometry of the thread-per-row kernel. A staged tile holds the values and columns of
@@ -288,6 +337,14 @@ void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
   if (v.partition == 1) {
     v.index = 0;                 // the delta index is built for sub-warp rows only
     build_merge(h, s);
+  } else if (v.partition == 2) {
+    v.index = 0;
+    v.vec = 1;
+    if (v.vs != 2 && v.vs != 4 && v.vs != 8) v.vs = 4;   // short rows' sub-warp width
+    v.tile_rows = 0;
+    v.tile_pipe = 0;
+    h->bin_vs_short = v.vs;
+    build_bins(h, s);
   } else {
     if (v.index == 1) {
       v.vec = 1;
@@ -315,7 +372,8 @@ void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
 }
 
 bool valid_variant(const spmv_variant &v) {
-  if (v.partition != 0 && v.partition != 1) return false;
+  if (v.partition < 0 || v.partition > 2) return false;
+  if (v.partition == 2 && v.vs != 0 && v.vs != 2 && v.vs != 4 && v.vs != 8) return false;
   if (v.index != 0 && v.index != 1) return false;
   if (v.xpath != 0 && v.xpath != 1) return false;
   if (v.vec != 0 && v.vec != 1) return false;
@@ -698,12 +756,33 @@ void run_profile(spmv_matrix *h, int reps, spmv_profile_report &o, cudaStream_t 
 // Called by spmv_tune for the routes that choose a variant (never for SPMV_TUNE_FIXED), so
 // the sub-warp width and, for width 1, the tile geometry are always swept.
 void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, cudaStream_t s) {
-  if (v.partition != 0 || h->n_rows == 0) return;
+  if (h->n_rows == 0) return;
   const size_t vb = dtype_bytes(h->vec);
   DevBuf x, y;
   x.alloc(vb * (size_t)std::max<int64_t>(h->n_cols, 1), vb, s);
   y.alloc(vb * (size_t)std::max<int64_t>(h->n_rows, 1), vb, s);
   CK(launch_fill_const(x.p, h->vec, h->n_cols, 1.0, s));
+  if (v.partition != 0) {
+    // IMB's decomposition family: merge-path tiles, or the row decomposition with short
+    // rows on sub-warps of 2, 4 or 8 lanes; the fastest is kept
+    spmv_variant best_v = v;
+    float best_t = 1e30f;
+    const int cand[4][2] = {{1, 0}, {2, 2}, {2, 4}, {2, 8}};
+    for (const auto &c : cand) {
+      spmv_variant t = v;
+      t.partition = c[0];
+      t.vs = c[1];
+      prepare_variant(h, t, s);
+      const float ms = time_launches([&]() { return launch_run(h, t, x.p, y.p, s); }, reps, s);
+      if (ms < best_t) {
+        best_t = ms;
+        best_v = t;
+      }
+    }
+    v = best_v;
+    prepare_variant(h, v, s);
+    return;
+  }
   float best = 1e30f;
   int best_vs = v.vs;
   const int widths[6] = {1, 2, 4, 8, 16, 32};
@@ -910,7 +989,8 @@ spmv_status spmv_destroy(spmv_handle_t h) {
   for (DevBuf *b : {&h->rowptr, &h->colind, &h->val_in, &h->val_store, &h->dbase, &h->delta,
                     &h->esc, &h->coord, &h->tail_row, &h->tail_val, &h->head_val, &h->x_stage,
                     &h->y_stage, &h->scratch, &h->d_err, &h->small, &h->feat_part,
-                    &h->feat_fin, &h->val_df, &h->cg_ws})
+                    &h->feat_fin, &h->val_df, &h->cg_ws, &h->bin_rows, &h->bin_long_rows,
+                    &h->bin_long_first, &h->bin_chunks, &h->bin_partials})
     b->release();
   delete h;
   return SPMV_OK;
@@ -1289,6 +1369,28 @@ spmv_status spmv_get_delta16(spmv_handle_t h, int32_t *base, uint16_t *delta, in
       CK(cudaMemcpyAsync(delta, h->delta.p, 2 * (size_t)h->nnz, cudaMemcpyDeviceToDevice, s));
     if (esc_col && h->n_esc)
       CK(cudaMemcpyAsync(esc_col, h->esc.p, 4 * (size_t)h->n_esc, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return SPMV_OK;
+  });
+}
+
+spmv_status spmv_get_row_bins(spmv_handle_t h, int32_t *med_rows, int32_t *long_rows,
+                              int32_t *long_first, int32_t *chunks, int64_t *counts,
+                              spmv_stream_t stream) {
+  if (!h || !counts) return SPMV_ERR_ARG;
+  if (!h->has_bins) return SPMV_ERR_NOT_TUNED;
+  counts[0] = h->bin_n_med;
+  counts[1] = h->bin_n_long;
+  counts[2] = h->bin_n_chunks;
+  if (!med_rows) return SPMV_OK;
+  if (!long_rows || !long_first || !chunks) return SPMV_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return guarded([&]() -> spmv_status {
+    CK(cudaMemcpyAsync(med_rows, h->bin_rows.p, 4 * (size_t)h->bin_n_med, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(long_rows, h->bin_long_rows.p, 4 * (size_t)h->bin_n_long, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(long_first, h->bin_long_first.p, 4 * (size_t)(h->bin_n_long + 1),
+                       cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(chunks, h->bin_chunks.p, 16 * (size_t)h->bin_n_chunks, cudaMemcpyDeviceToDevice, s));
     CK(cudaStreamSynchronize(s));
     return SPMV_OK;
   });

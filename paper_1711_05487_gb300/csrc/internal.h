@@ -41,7 +41,25 @@ struct RunArgs {
   int32_t tile_pipe = 0;             // 1: persistent CTAs with two staged tiles in flight
   int32_t *err = nullptr;            // device error word (bounded waits)
   const void *val_df = nullptr;      // storage SPMV_DF64: double-float value pairs
+  // row decomposition (partition 2): rows with length < bin_l_med go to sub-warps of
+  // bin_vs_short lanes; medium rows (bin_rows) to a warp each; long rows (bin_long_rows,
+  // length >= kBinChunk) in chunks (row, first, end nonzero) whose FP64 partials are added
+  // per long row over [bin_long_first[i], bin_long_first[i + 1])
+  int32_t bin_l_med = 0, bin_vs_short = 4;
+  const int32_t *bin_rows = nullptr;
+  int64_t bin_n_med = 0;
+  const int4 *bin_chunks = nullptr;
+  int64_t bin_n_chunks = 0;
+  const int32_t *bin_long_rows = nullptr;
+  const int32_t *bin_long_first = nullptr;
+  int64_t bin_n_long = 0;
+  double *bin_partials = nullptr;
 };
+
+// Row decomposition thresholds: rows of at least kBinMed nonzeros get a warp; rows of at
+// least kBinChunk nonzeros are split into chunks of kBinChunk nonzeros.
+constexpr int kBinMed = 64;
+constexpr int kBinChunk = 4096;
 
 // Thread-per-row tile kernel geometry: at most this many rows (= threads) per CTA.
 constexpr int kTileRows = 128;
@@ -168,6 +186,16 @@ cudaError_t launch_row_len_max(int64_t n_rows, const int32_t *rowptr, int32_t *o
 // max over tiles of `tile_rows` rows of the 8-aligned staged element count
 cudaError_t launch_tile_max(int64_t n_rows, const int32_t *rowptr, int tile_rows, int32_t *out,
                             cudaStream_t s);
+
+// Row decomposition tables: per-row counts (medium flag, long flag, chunks) for the scans,
+// then the lists (bin_rows, long rows, their first chunk, chunk table).
+cudaError_t launch_bin_counts(int64_t n_rows, const int32_t *rowptr, int32_t l_med,
+                              int32_t chunk, int64_t *med, int64_t *lng, int64_t *nch,
+                              cudaStream_t s);
+cudaError_t launch_bin_fill(int64_t n_rows, const int32_t *rowptr, int32_t l_med, int32_t chunk,
+                            const int64_t *med_off, const int64_t *lng_off,
+                            const int64_t *nch_off, int32_t *bin_rows, int32_t *long_rows,
+                            int32_t *long_first, int4 *chunks, cudaStream_t s);
 
 // Largest column of each row chunk (host-buffer pipelining)
 cudaError_t launch_chunk_colmax(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,

@@ -657,4 +657,55 @@ cudaError_t launch_read_probe(const void *buf, int64_t bytes, int reps,
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------ row decomposition ------
+// Per row: med = 1 if l_med <= length < chunk, lng = 1 if length >= chunk, nch = the long
+// row's chunk count. Exclusive scans of the three give each row's place in the lists.
+__global__ void k_bin_counts(int64_t n_rows, const int32_t *rowptr, int32_t l_med,
+                             int32_t chunk, int64_t *med, int64_t *lng, int64_t *nch) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  const int len = rowptr[r + 1] - rowptr[r];
+  const bool is_long = len >= chunk;
+  med[r] = (len >= l_med && !is_long) ? 1 : 0;
+  lng[r] = is_long ? 1 : 0;
+  nch[r] = is_long ? (len + chunk - 1) / chunk : 0;
+}
+
+__global__ void k_bin_fill(int64_t n_rows, const int32_t *rowptr, int32_t l_med, int32_t chunk,
+                           const int64_t *med_off, const int64_t *lng_off,
+                           const int64_t *nch_off, int32_t *bin_rows, int32_t *long_rows,
+                           int32_t *long_first, int4 *chunks) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  const int s = rowptr[r], e = rowptr[r + 1], len = e - s;
+  if (len >= chunk) {
+    const int64_t k = lng_off[r];
+    const int64_t c0 = nch_off[r];
+    long_rows[k] = (int32_t)r;
+    long_first[k] = (int32_t)c0;
+    int64_t c = c0;
+    for (int z = s; z < e; z += chunk, ++c) chunks[c] = make_int4((int)r, z, min(z + chunk, e), 0);
+  } else if (len >= l_med) {
+    bin_rows[med_off[r]] = (int32_t)r;
+  }
+}
+
+cudaError_t launch_bin_counts(int64_t n_rows, const int32_t *rowptr, int32_t l_med,
+                              int32_t chunk, int64_t *med, int64_t *lng, int64_t *nch,
+                              cudaStream_t s) {
+  if (n_rows <= 0) return cudaSuccess;
+  k_bin_counts<<<blocks_for(n_rows), kT, 0, s>>>(n_rows, rowptr, l_med, chunk, med, lng, nch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_fill(int64_t n_rows, const int32_t *rowptr, int32_t l_med, int32_t chunk,
+                            const int64_t *med_off, const int64_t *lng_off,
+                            const int64_t *nch_off, int32_t *bin_rows, int32_t *long_rows,
+                            int32_t *long_first, int4 *chunks, cudaStream_t s) {
+  if (n_rows <= 0) return cudaSuccess;
+  k_bin_fill<<<blocks_for(n_rows), kT, 0, s>>>(n_rows, rowptr, l_med, chunk, med_off, lng_off,
+                                                nch_off, bin_rows, long_rows, long_first, chunks);
+  return cudaGetLastError();
+}
+
 }  // namespace spmv

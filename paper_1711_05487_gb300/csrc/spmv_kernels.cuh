@@ -7,6 +7,8 @@
 //              XL2  x gathered with an L2 evict-last policy while val / colind stream with
 //                   evict-first (ML: the GPU counterpart of software prefetching into cache).
 //  k_rowtile - thread-per-row tiles staged by TMA bulk copies (spmv_tile.cuh).
+//  k_bins_*  - row decomposition: short rows by sub-warps, medium rows by warps, long rows
+//              split into chunks with a fixed-order FP64 fixup (IMB).
 //  k_merge   - merge-path tiles of equal (rows + nonzeros) work; rows longer than a tile
 //              are split over tiles and finished by k_merge_fixup (IMB: the decomposition
 //              of Fig. 4/5, long rows computed by many workers with a reduction).
@@ -25,6 +27,51 @@
 namespace spmv {
 
 constexpr int kRowThreads = 256;
+
+// ------------------------------------------------------------ vector-load range dot ----
+// One lane's share of sum_{j in [s, e)} val[j] x[colind[j]] for a sub-warp of VS lanes: 4
+// elements per lane per step, colind as one 16-byte load and val as 8..32 bytes (the chunks
+// start at s rounded down to 4 elements; elements outside [s, e) are masked off). With a
+// wider SumT than AccT (FP32 accumulation over a long-row chunk), each step's four products
+// are summed in AccT and the step sums in SumT.
+template <typename ValT, typename VecT, typename AccT, int VS, bool XL2, typename SumT = AccT>
+__device__ __forceinline__ SumT vec_range_dot(const RunArgs &a, int s, int e, int lane,
+                                              uint64_t pol_s, uint64_t pol_x) {
+  const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
+  const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
+  const int32_t *__restrict__ col = a.colind;
+  SumT sum = 0;
+  const int a0 = s & ~3;
+#pragma unroll 2
+  for (int b = a0 + lane * 4; b < e; b += VS * 4) {
+    const uint4 c4 = ld16<true>(col + b, pol_s);
+    AccT v[4];
+    VLoad<AccT, true, 4>::run(val + b, v, pol_s);
+    const int cc[4] = {(int)c4.x, (int)c4.y, (int)c4.z, (int)c4.w};
+    AccT xv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = b + q;
+      xv[q] = (j >= s && j < e) ? (AccT)ldx<XL2>(x + cc[q], pol_x) : (AccT)0;
+    }
+    if constexpr (std::is_same<SumT, AccT>::value) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = b + q;
+        if (j >= s && j < e) sum += v[q] * xv[q];
+      }
+    } else {
+      AccT part = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = b + q;
+        if (j >= s && j < e) part += v[q] * xv[q];
+      }
+      sum += (SumT)part;
+    }
+  }
+  return sum;
+}
 
 // ------------------------------------------------------------------------ k_rowvec ----
 template <typename ValT, typename VecT, typename AccT, int VS, bool VEC, bool D16, bool XL2>
@@ -46,27 +93,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rowvec(const RunArgs a) {
     for (int j = s + lane; j < e; j += VS)
       sum += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(col + j), pol_x);
   } else if constexpr (!D16) {
-    // 4 elements per lane per step: colind as one 16-byte load, val as 8..32 bytes.
-    const int32_t *__restrict__ col = a.colind;
-    const int a0 = s & ~3;
-#pragma unroll 2
-    for (int b = a0 + lane * 4; b < e; b += VS * 4) {
-      const uint4 c4 = ld16<true>(col + b, pol_s);
-      AccT v[4];
-      VLoad<AccT, true, 4>::run(val + b, v, pol_s);
-      const int cc[4] = {(int)c4.x, (int)c4.y, (int)c4.z, (int)c4.w};
-      AccT xv[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int j = b + q;
-        xv[q] = (j >= s && j < e) ? (AccT)ldx<XL2>(x + cc[q], pol_x) : (AccT)0;
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int j = b + q;
-        if (j >= s && j < e) sum += v[q] * xv[q];
-      }
-    }
+    sum = vec_range_dot<ValT, VecT, AccT, VS, XL2>(a, s, e, lane, pol_s, pol_x);
   } else {
     const int32_t base = __ldg(a.dbase + row);
     if (base < 0) {
@@ -410,6 +437,87 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm(const RunArgs a, int off, 
   }
 }
 
+// -------------------------------------------------------------------- k_bins_* ------
+// Row decomposition (IMB, Section III-E's matrix decomposition A = A_short + A_long; Fig. 5):
+//  k_bins_short  - rows shorter than l_med, a sub-warp of VS lanes each, over all rows
+//                  (longer rows are skipped: the sub-warp reads their bounds only);
+//  k_bins_warp   - one warp per work item: a medium row (l_med <= length < kBinChunk, from
+//                  the row list) written directly, or a chunk of at most kBinChunk nonzeros
+//                  of a long row whose sum goes to an FP64 partial slot; the lanes add
+//                  their steps' sums in FP64 (FP32 accumulation stays within 4 products);
+//  k_bins_fixup  - each long row's partials added in chunk order (reproducible, no atomics).
+template <typename ValT, typename VecT, typename AccT, int VS, bool XL2>
+__global__ void __launch_bounds__(kRowThreads) k_bins_short(const RunArgs a) {
+  constexpr int GROUPS = kRowThreads / VS;
+  const int lane = threadIdx.x & (VS - 1);
+  const int64_t row = (int64_t)blockIdx.x * GROUPS + threadIdx.x / VS;
+  if (row >= a.n_rows) return;
+  const int s = __ldg(a.rowptr + row), e = __ldg(a.rowptr + row + 1);
+  if (e - s >= a.bin_l_med) return;
+  uint64_t pol_s = policy_evict_first(), pol_x = 0;
+  if constexpr (XL2) pol_x = policy_evict_last();
+  AccT sum = vec_range_dot<ValT, VecT, AccT, VS, XL2>(a, s, e, lane, pol_s, pol_x);
+  sum = group_sum<VS>(sum, group_mask<VS>());
+  if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)sum;
+}
+
+template <typename ValT, typename VecT, typename AccT, bool XL2>
+__global__ void __launch_bounds__(kRowThreads) k_bins_warp(const RunArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t item = ((int64_t)blockIdx.x * kRowThreads + threadIdx.x) / 32;
+  if (item >= a.bin_n_med + a.bin_n_chunks) return;
+  uint64_t pol_s = policy_evict_first(), pol_x = 0;
+  if constexpr (XL2) pol_x = policy_evict_last();
+  if (item < a.bin_n_chunks) {
+    const int4 c = a.bin_chunks[item];   // (row, first nonzero, end nonzero, unused)
+    const double sum = vec_range_dot<ValT, VecT, AccT, 32, XL2, double>(a, c.y, c.z, lane,
+                                                                       pol_s, pol_x);
+    const double t = group_sum<32>(sum, 0xffffffffu);
+    if (lane == 0) a.bin_partials[item] = t;
+  } else {
+    const int row = __ldg(a.bin_rows + (item - a.bin_n_chunks));
+    const int s = __ldg(a.rowptr + row), e = __ldg(a.rowptr + row + 1);
+    double sum = vec_range_dot<ValT, VecT, AccT, 32, XL2, double>(a, s, e, lane, pol_s, pol_x);
+    sum = group_sum<32>(sum, 0xffffffffu);
+    if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)sum;
+  }
+}
+
+template <typename VecT>
+__global__ void k_bins_fixup(const RunArgs a) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.bin_n_long) return;
+  double t = 0.0;
+  for (int c = a.bin_long_first[i]; c < a.bin_long_first[i + 1]; ++c) t += a.bin_partials[c];
+  static_cast<VecT *>(a.y)[a.bin_long_rows[i]] = (VecT)t;
+}
+
+template <typename ValT, typename VecT, typename AccT, int VS>
+void launch_bins_short(bool xl2, const RunArgs &a, cudaStream_t s) {
+  const unsigned g = (unsigned)((a.n_rows + (kRowThreads / VS) - 1) / (kRowThreads / VS));
+  if (xl2) k_bins_short<ValT, VecT, AccT, VS, true><<<g, kRowThreads, 0, s>>>(a);
+  else k_bins_short<ValT, VecT, AccT, VS, false><<<g, kRowThreads, 0, s>>>(a);
+}
+
+template <typename ValT, typename VecT, typename AccT>
+cudaError_t launch_bins(bool xl2, const RunArgs &a, cudaStream_t s) {
+  if (a.n_rows == 0) return cudaSuccess;
+  switch (a.bin_vs_short) {
+    case 2: launch_bins_short<ValT, VecT, AccT, 2>(xl2, a, s); break;
+    case 8: launch_bins_short<ValT, VecT, AccT, 8>(xl2, a, s); break;
+    default: launch_bins_short<ValT, VecT, AccT, 4>(xl2, a, s); break;
+  }
+  const int64_t items = a.bin_n_med + a.bin_n_chunks;
+  if (items > 0) {
+    const unsigned g = (unsigned)((items * 32 + kRowThreads - 1) / kRowThreads);
+    if (xl2) k_bins_warp<ValT, VecT, AccT, true><<<g, kRowThreads, 0, s>>>(a);
+    else k_bins_warp<ValT, VecT, AccT, false><<<g, kRowThreads, 0, s>>>(a);
+  }
+  if (a.bin_n_long > 0)
+    k_bins_fixup<VecT><<<(unsigned)((a.bin_n_long + 255) / 256), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------ launchers ---
 inline unsigned grid_for_rows(int64_t n_rows, int vs) {
   const int64_t groups = kRowThreads / vs;
@@ -436,6 +544,7 @@ cudaError_t launch_rowvec_vs(const spmv_variant &v, const RunArgs &a, cudaStream
 template <typename ValT, typename VecT, typename AccT>
 cudaError_t launch_spmv_impl(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
+  if (v.partition == 2) return launch_bins<ValT, VecT, AccT>(v.xpath != 0, a, s);
   if (v.partition == 1) {
     if (a.n_tiles == 0) return cudaSuccess;
     if (v.xpath) k_merge<ValT, VecT, AccT, true><<<(unsigned)a.n_tiles, kMergeThreads, 0, s>>>(a);

@@ -37,7 +37,7 @@ from .api import Selector, SpmvMatrix
 # Every variant a class set can select (partition, index, xpath, vec) with the pool's
 # sub-warp width heuristic; index 0 is the plain CSR-vector.
 CANDIDATES = ((0, 0, 0, 0), (0, 0, 0, 1), (0, 1, 0, 1), (0, 0, 1, 0), (0, 0, 1, 1),
-              (0, 1, 1, 1), (1, 0, 0, 0), (1, 0, 1, 0))
+              (0, 1, 1, 1), (1, 0, 0, 0), (1, 0, 1, 0), (2, 0, 0, 1), (2, 0, 1, 1))
 SIZES = (12, 32, 32, 4)
 
 
@@ -177,6 +177,19 @@ def predict(params, mu, inv, feat16, sizes=SIZES) -> tuple[np.ndarray, np.ndarra
 
 
 # --------------------------------------------------------------------- evaluation ----
+def family_times(t: np.ndarray) -> np.ndarray:
+    """Times with each merge-path candidate replaced by the faster of it and the row
+    decomposition with the same x path: the autotuner picks between the two decompositions
+    for IMB matrices."""
+    t = np.array(t, dtype=np.float64, copy=True)
+    if t.shape[1] < len(CANDIDATES):
+        return t
+    for xp in (0, 1):
+        m, b = CANDIDATES.index((1, 0, xp, 0)), CANDIDATES.index((2, 0, xp, 1))
+        t[:, m] = np.minimum(t[:, m], t[:, b])
+    return t
+
+
 def candidate_of(classes: int, nnz_avg: float, nnz_max: float) -> int:
     v = _abi.spmv_variant_for_classes(int(classes), nnz_avg, nnz_max, 32.0)
     if v.partition == 1:          # merge-path tiles use neither the delta index nor widths
@@ -194,7 +207,7 @@ def evaluate(ds: dict, idx: np.ndarray, pred: np.ndarray) -> dict:
     lab = ds["classes"][idx]
     emr = float(np.mean(pred == lab))
     pmr = float(np.mean(((pred & lab) != 0) | ((pred == 0) & (lab == 0))))
-    t = ds["times"][idx]
+    t = family_times(ds["times"][idx])
     ch_ml = np.array([candidate_of(c, a, mx) for c, a, mx in
                       zip(pred, ds["nnz_avg"][idx], ds["nnz_max"][idx])])
     ch_pr = np.array([candidate_of(c, a, mx) for c, a, mx in

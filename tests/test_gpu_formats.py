@@ -80,6 +80,19 @@ def test_value_rounding_bit_exact(abi, torch):
     assert np.array_equal(o16.cpu().numpy().view(np.uint16), oracle.round_bf16_bits(v))
 
 
+def test_row_bins_bit_exact(api, torch):
+    """The row decomposition tables equal the oracle's, for a matrix with short, medium and
+    long rows and for one with none of the latter two."""
+    for m in (synth.power_law(60_000, alpha=1.4, clip=60_000, seed=19, dtype=np.float64),
+              synth.laplacian_2d(40)):
+        A = api.SpmvMatrix.from_csr(m)
+        A.set_variant(partition=2)
+        med, lng, first, ch = (t.cpu().numpy() for t in A.row_bins())
+        om, ol, of, oc = oracle.row_bins(m.rowptr, l_med=64, chunk=4096)
+        assert np.array_equal(med, om) and np.array_equal(lng, ol)
+        assert np.array_equal(first, of) and np.array_equal(ch, oc)
+
+
 def test_df_split_bit_exact(abi, torch):
     """Double-float value pairs (DF64 storage) equal the oracle's split bit for bit."""
     rng = np.random.default_rng(31)
