@@ -172,8 +172,8 @@ spmv_status spmv_set_variant(spmv_handle_t h, const spmv_variant *v, spmv_stream
 spmv_status spmv_run(spmv_handle_t h, const void *x, void *y, spmv_stream_t stream);
 
 /* y = A x with HOST buffers: copies x to a handle-owned device buffer, runs, copies y
- * back; returns when y is on the host (the end-to-end path). Row variants compute in eight
- * row chunks: chunk c waits only for the prefix of x up to the largest column of chunks
+ * back; returns when y is on the host (the end-to-end path). Row variants whose x and y
+ * together reach 8 MB compute in eight row chunks: chunk c waits only for the prefix of x up to the largest column of chunks
  * 0..c (uploaded piece by piece on a handle-owned stream), consecutive chunks' kernels run
  * on two alternating handle-owned streams, and each finished chunk of y is downloaded on
  * another while the next computes. With page-locked x and y the whole pipeline is captured

@@ -1158,7 +1158,10 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
       }
       for (auto &e : h->joined) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    const bool chunked = h->variant.partition == 0 && h->n_rows >= 4 * kHostChunks * kTileRows;
+    // pipelining pays once the copies take longer than a few chunk launches (x and y of at
+    // least 8 MB together)
+    const bool chunked = h->variant.partition == 0 && h->n_rows >= 4 * kHostChunks * kTileRows &&
+                         (int64_t)vb * (h->n_rows + h->n_cols) >= 8000000;
     const int nch = chunked ? kHostChunks : 1;
     // chunk row boundaries: equal parts aligned to 128 rows
     int64_t per = (h->n_rows + nch - 1) / nch;

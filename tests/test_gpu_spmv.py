@@ -170,8 +170,8 @@ def test_spmm(api, torch, name, k):
     check_rows(Y32.ravel(), Yr.ravel(), Sr.ravel(), tau, f"spmm32 {name} k={k}")
 
 
-@pytest.mark.parametrize("gen", [lambda: synth.stencil_27pt(12),       # one launch
-                                 lambda: synth.stencil_27pt(30),       # four row chunks
+@pytest.mark.parametrize("gen", [lambda: synth.stencil_27pt(30),       # one launch
+                                 lambda: synth.stencil_27pt(80),       # eight row chunks
                                  lambda: synth.power_law(30_000, seed=14, dtype=np.float64)])
 def test_run_host_equals_device_run(api, torch, gen):
     m = gen()
@@ -281,7 +281,7 @@ def test_df64_long_rows_and_ragged(api, torch):
 
 
 def test_df64_run_host_equals_device_run(api, torch):
-    m = synth.stencil_27pt(30)
+    m = synth.stencil_27pt(80)
     A = api.SpmvMatrix.from_csr(m)
     A.set_precision("df64", "f64", "df64")
     x64 = synth.uniform_vector(m.n_cols, 25)
@@ -314,7 +314,7 @@ def test_df64_tune_and_reject_non_f64_input(api, torch):
 def test_run_host_graph_replays_follow_buffers_and_variants(api, torch):
     """Page-locked buffers take the captured-graph path: a new buffer pair or a new variant
     is re-captured, and pageable buffers take the eager path; all equal the device run."""
-    m = synth.stencil_27pt(30)
+    m = synth.stencil_27pt(80)          # x and y above 8 MB: the chunked pipeline
     A = api.SpmvMatrix.from_csr(m)
     xs = [synth.uniform_vector(m.n_cols, s) for s in (71, 72)]
     outs = {}
