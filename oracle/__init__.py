@@ -79,7 +79,8 @@ def _declare(L):
     L.oracle_df_split.restype = None
     L.oracle_spmv_f64_static.argtypes = [_I64, _P, _P, _P, _P, _P, ctypes.c_int32]
     L.oracle_spmv_f64_static.restype = ctypes.c_int32
-    L.oracle_row_bins.argtypes = [_I64, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P, _P]
+    L.oracle_row_bins.argtypes = [_I64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P, _P,
+                                  _P]
     L.oracle_row_bins.restype = None
     L.oracle_cg.argtypes = [_I64, _P, _P, _P, _P, _P, _I64, _D, _P, _P]
     L.oracle_cg.restype = _I64
@@ -185,9 +186,9 @@ def df_split_bits(v) -> np.ndarray:
     return out
 
 
-def row_bins(rowptr, l_med=64, chunk=4096):
+def row_bins(rowptr, colind, l_med=64, chunk=4096):
     """(med_rows, long_rows, long_first, chunks (n, 4)) of the row decomposition."""
-    rp = _c(rowptr, np.int32)
+    rp, ci = _c(rowptr, np.int32), _c(colind, np.int32)
     n = rp.shape[0] - 1
     lens = np.diff(rp.astype(np.int64))
     max_ch = int(np.sum((lens + chunk - 1) // chunk)) + 1
@@ -196,7 +197,7 @@ def row_bins(rowptr, l_med=64, chunk=4096):
     first = np.empty(n + 1, np.int32)
     ch = np.empty((max_ch, 4), np.int32)
     counts = np.zeros(3, np.int64)
-    lib().oracle_row_bins(n, _p(rp), l_med, chunk, _p(med), _p(lng), _p(first), _p(ch),
+    lib().oracle_row_bins(n, _p(rp), _p(ci), l_med, chunk, _p(med), _p(lng), _p(first), _p(ch),
                           _p(counts))
     a, b, c = (int(v) for v in counts)
     return med[:a], lng[:b], first[:b + 1], ch[:c]

@@ -303,10 +303,12 @@ int64_t oracle_cg(int64_t n, const int32_t *rowptr, const int32_t *colind, const
  * otherwise. Long row r is cut into chunks [z, min(z + chunk, rowptr[r+1])) for
  * z = rowptr[r], rowptr[r] + chunk, ... . Outputs in row order: med_rows[], long_rows[],
  * long_first[] (first chunk of each long row, then the chunk count), chunks[] as
- * (row, begin, end, 0). counts[0..2] = medium rows, long rows, chunks.                   */
-void oracle_row_bins(int64_t n_rows, const int32_t *rowptr, int32_t l_med, int32_t chunk,
-                     int32_t *med_rows, int32_t *long_rows, int32_t *long_first,
-                     int32_t *chunks, int64_t *counts) {
+ * (row, begin z, end, start column) where the start column is the column a delta decode
+ * of the chunk starts from: colind[z - 1] inside the row, colind[z] (whose delta is 0) for
+ * the row's first chunk. counts[0..2] = medium rows, long rows, chunks.                  */
+void oracle_row_bins(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                     int32_t l_med, int32_t chunk, int32_t *med_rows, int32_t *long_rows,
+                     int32_t *long_first, int32_t *chunks, int64_t *counts) {
   int64_t n_med = 0, n_long = 0, n_ch = 0;
   for (int64_t r = 0; r < n_rows; ++r) {
     const int32_t b = rowptr[r], e = rowptr[r + 1];
@@ -319,7 +321,7 @@ void oracle_row_bins(int64_t n_rows, const int32_t *rowptr, int32_t l_med, int32
         chunks[4 * n_ch] = (int32_t)r;
         chunks[4 * n_ch + 1] = z;
         chunks[4 * n_ch + 2] = (z + chunk < e) ? z + chunk : e;
-        chunks[4 * n_ch + 3] = 0;
+        chunks[4 * n_ch + 3] = z > b ? colind[z - 1] : colind[z];
         ++n_ch;
       }
     } else if (len >= l_med) {
@@ -590,14 +592,16 @@ uint32_t oracle_classify2(const double *p, const double *p2, double t_imb, doubl
  *   out[3] vector loads and unrolling: 1 for MB (delta encoding + vectorization) and CMP
  *          (unrolling + vectorization).
  * IMB picks between its two sub-optimizations with nnz_max versus nnz_avg: highly uneven
- * row lengths (nnz_max > long_ratio * nnz_avg) take the decomposition (merge-path),
- * otherwise the dynamic schedule (sub-warp rows). The 16-bit delta index is only built for
- * the sub-warp row partition, so MB together with the merge-path keeps int32 columns.    */
+ * row lengths (nnz_max > long_ratio * nnz_avg) take the decomposition (out[0] = 1; the
+ * library's autotuner then runs it as merge-path tiles or as row bins), otherwise the
+ * dynamic schedule (sub-warp rows). MB sets the 16-bit delta index in every case: the
+ * optimizations of Table II apply jointly, and the row-bin decomposition decodes deltas
+ * (merge-path tiles keep int32 columns).                                                */
 void oracle_variant_for_classes(uint32_t cls, double nnz_avg, double nnz_max,
                                 double long_ratio, int32_t *out) {
   int32_t part = 0, idx = 0, xp = 0, vec = 0;
   if ((cls & 4u) && nnz_max > long_ratio * nnz_avg) part = 1;
-  if ((cls & 1u) && part == 0) idx = 1;
+  if (cls & 1u) idx = 1;   /* the delta index composes with the row decomposition */
   if (cls & 2u) xp = 1;
   if (cls & (1u | 8u)) vec = 1;
   out[0] = part;

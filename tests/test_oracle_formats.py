@@ -192,19 +192,21 @@ def test_row_bins_hand_example():
     # row 4 (length 3) is medium, rows 1, 3 and 5 are long and cut into chunks of 5
     lens = [1, 5, 0, 12, 3, 9]
     rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
-    med, lng, first, ch = oracle.row_bins(rp, l_med=3, chunk=5)
+    ci = np.concatenate([np.arange(n) * 3 + 7 for n in lens]).astype(np.int32)
+    med, lng, first, ch = oracle.row_bins(rp, ci, l_med=3, chunk=5)
     assert list(med) == [4]
     assert list(lng) == [1, 3, 5]
     assert list(first) == [0, 1, 4, 6]
-    assert [tuple(c) for c in ch] == [(1, 1, 6, 0), (3, 6, 11, 0), (3, 11, 16, 0),
-                                      (3, 16, 18, 0), (5, 21, 26, 0), (5, 26, 30, 0)]
+    # start column: the row's first column for a first chunk, else the previous column
+    assert [tuple(c) for c in ch] == [(1, 1, 6, 7), (3, 6, 11, 7), (3, 11, 16, 19),
+                                      (3, 16, 18, 34), (5, 21, 26, 7), (5, 26, 30, 19)]
 
 
 def test_row_bins_partition_the_matrix_exactly():
     """A_short + A_medium + A_long = A: every nonzero belongs to exactly one short row,
     medium row or chunk, and rebuilding the product from the pieces gives the oracle's y."""
     m = synth.power_law(30_000, alpha=1.4, clip=30_000, seed=17, dtype=np.float64)
-    med, lng, first, ch = oracle.row_bins(m.rowptr, l_med=64, chunk=4096)
+    med, lng, first, ch = oracle.row_bins(m.rowptr, m.colind, l_med=64, chunk=4096)
     lens = np.diff(m.rowptr)
     owner = np.full(m.nnz, -1, np.int64)
     for r in np.where(lens < 64)[0]:
@@ -220,9 +222,10 @@ def test_row_bins_partition_the_matrix_exactly():
         assert cs[0, 1] == m.rowptr[r] and cs[-1, 2] == m.rowptr[r + 1]
         assert np.all(cs[1:, 1] == cs[:-1, 2])
         assert np.all(cs[:-1, 2] - cs[:-1, 1] == 4096) and 0 < cs[-1, 2] - cs[-1, 1] <= 4096
-        for _, b, e, _ in cs:
+        for _, b, e, c0 in cs:
             assert np.all(owner[b:e] == -1)
             owner[b:e] = 2
+            assert c0 == m.colind[b - 1 if b > m.rowptr[r] else b]
     assert np.all(owner >= 0)
     x = synth.uniform_vector(m.n_cols, 18)
     y, _ = oracle.spmv(m.rowptr, m.colind, m.val, x)

@@ -114,7 +114,7 @@ def test_variant_map_table2():
     for cls in range(16):
         part, idx, xp, vec = oracle.variant_for_classes(cls, nnz_avg=10, nnz_max=1000)
         assert part == (1 if cls & 4 else 0)
-        assert idx == (1 if (cls & 1 and not cls & 4) else 0)
+        assert idx == (1 if cls & 1 else 0)
         assert xp == (1 if cls & 2 else 0)
         assert vec == (1 if cls & 9 else 0)
     # IMB without highly uneven rows keeps the dynamic (sub-warp row) schedule
