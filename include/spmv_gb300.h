@@ -74,7 +74,8 @@ typedef struct {
                         4096 on one warp each, longer rows in 4096-nonzero chunks summed
                         in FP64 in chunk order. 1 and 2 are the decompositions of
                         Section III-E (IMB); the autotuner picks between them         */
-  int32_t index;     /* 0: int32 columns; 1: 16-bit column deltas with escape rows (MB)   */
+  int32_t index;     /* 0: int32 columns; 1: 16-bit column deltas with escape rows (MB);
+                        merge-path tiles (partition 1) always read int32 columns          */
   int32_t xpath;     /* 0: default; 1: x kept L2-resident (evict-last gathers through the
                         read-only path, evict-first streams) (ML)                         */
   int32_t vec;       /* 0: scalar loads; 1: 128-bit loads of val/colind, unrolled (MB/CMP) */
@@ -212,7 +213,9 @@ spmv_status spmv_get_merge_path(spmv_handle_t h, int32_t *coord, int64_t *n_tile
 /* Copies the row decomposition of partition 2 (device arrays, int32): med_rows[n_med] the
  * rows of 64..4095 nonzeros, long_rows[n_long] the rows of 4096 or more, long_first
  * [n_long + 1] each long row's first chunk (the last entry is n_chunks), chunks[4 * n_chunks]
- * as (row, first nonzero, end nonzero, 0), all in row order. counts (host, int64[3])
+ * as (row, first nonzero z, end nonzero, start column: colind[z - 1] for a chunk that starts
+ * inside its row, colind[z] for a row's first chunk -- where a 16-bit delta decode of the
+ * chunk starts), all in row order. counts (host, int64[3])
  * receives n_med, n_long, n_chunks; pass med_rows = NULL to query counts only.
  * SPMV_ERR_NOT_TUNED if no decomposition has been built. */
 spmv_status spmv_get_row_bins(spmv_handle_t h, int32_t *med_rows, int32_t *long_rows,

@@ -282,7 +282,8 @@ void build_bins(spmv_matrix *h, cudaStream_t s) {
   h->bin_partials.alloc(8 * (size_t)std::max<int64_t>(tot[2], 1), 8, s);
   const int32_t last = (int32_t)tot[2];
   CK(cudaMemcpyAsync(h->bin_long_first.as<int32_t>() + tot[1], &last, 4, cudaMemcpyHostToDevice, s));
-  CK(launch_bin_fill(n, h->rowptr.as<int32_t>(), kBinMed, kBinChunk, med, lng, nch,
+  CK(launch_bin_fill(n, h->rowptr.as<int32_t>(), h->colind.as<int32_t>(), kBinMed, kBinChunk,
+                     med, lng, nch,
                      h->bin_rows.as<int32_t>(), h->bin_long_rows.as<int32_t>(),
                      h->bin_long_first.as<int32_t>(), h->bin_chunks.as<int4>(), s));
   CK(cudaStreamSynchronize(s));
@@ -338,7 +339,7 @@ void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
     v.index = 0;                 // the delta index is built for sub-warp rows only
     build_merge(h, s);
   } else if (v.partition == 2) {
-    v.index = 0;
+    if (v.index == 1) build_delta16(h, s);
     v.vec = 1;
     if (v.vs != 2 && v.vs != 4 && v.vs != 8) v.vs = 4;   // short rows' sub-warp width
     v.tile_rows = 0;
@@ -492,7 +493,7 @@ uint32_t classify2(const double *p, const double *p2, double t_imb, double t_ml,
 spmv_variant variant_for_classes(uint32_t cls, double nnz_avg, double nnz_max, double long_ratio) {
   spmv_variant v{};
   if ((cls & SPMV_CLASS_IMB) && nnz_max > long_ratio * nnz_avg) v.partition = 1;
-  if ((cls & SPMV_CLASS_MB) && v.partition == 0) v.index = 1;
+  if (cls & SPMV_CLASS_MB) v.index = 1;   // merge-path tiles keep int32 columns
   if (cls & SPMV_CLASS_ML) v.xpath = 1;
   if (cls & (SPMV_CLASS_MB | SPMV_CLASS_CMP)) v.vec = 1;
   v.vs = 0;

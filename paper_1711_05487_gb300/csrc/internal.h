@@ -43,8 +43,9 @@ struct RunArgs {
   const void *val_df = nullptr;      // storage SPMV_DF64: double-float value pairs
   // row decomposition (partition 2): rows with length < bin_l_med go to sub-warps of
   // bin_vs_short lanes; medium rows (bin_rows) to a warp each; long rows (bin_long_rows,
-  // length >= kBinChunk) in chunks (row, first, end nonzero) whose FP64 partials are added
-  // per long row over [bin_long_first[i], bin_long_first[i + 1])
+  // length >= kBinChunk) in chunks (row, first, end nonzero, the column a delta decode of
+  // the chunk starts from) whose FP64 partials are added per long row over
+  // [bin_long_first[i], bin_long_first[i + 1])
   int32_t bin_l_med = 0, bin_vs_short = 4;
   const int32_t *bin_rows = nullptr;
   int64_t bin_n_med = 0;
@@ -192,10 +193,11 @@ cudaError_t launch_tile_max(int64_t n_rows, const int32_t *rowptr, int tile_rows
 cudaError_t launch_bin_counts(int64_t n_rows, const int32_t *rowptr, int32_t l_med,
                               int32_t chunk, int64_t *med, int64_t *lng, int64_t *nch,
                               cudaStream_t s);
-cudaError_t launch_bin_fill(int64_t n_rows, const int32_t *rowptr, int32_t l_med, int32_t chunk,
-                            const int64_t *med_off, const int64_t *lng_off,
-                            const int64_t *nch_off, int32_t *bin_rows, int32_t *long_rows,
-                            int32_t *long_first, int4 *chunks, cudaStream_t s);
+cudaError_t launch_bin_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                            int32_t l_med, int32_t chunk, const int64_t *med_off,
+                            const int64_t *lng_off, const int64_t *nch_off, int32_t *bin_rows,
+                            int32_t *long_rows, int32_t *long_first, int4 *chunks,
+                            cudaStream_t s);
 
 // Largest column of each row chunk (host-buffer pipelining)
 cudaError_t launch_chunk_colmax(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,

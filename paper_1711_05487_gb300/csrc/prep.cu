@@ -671,10 +671,12 @@ __global__ void k_bin_counts(int64_t n_rows, const int32_t *rowptr, int32_t l_me
   nch[r] = is_long ? (len + chunk - 1) / chunk : 0;
 }
 
-__global__ void k_bin_fill(int64_t n_rows, const int32_t *rowptr, int32_t l_med, int32_t chunk,
-                           const int64_t *med_off, const int64_t *lng_off,
-                           const int64_t *nch_off, int32_t *bin_rows, int32_t *long_rows,
-                           int32_t *long_first, int4 *chunks) {
+// A chunk is (row, first nonzero z, end nonzero, the column its delta decode starts from:
+// colind[z - 1] inside the row, colind[z] for the row's first chunk, whose first delta is 0).
+__global__ void k_bin_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                           int32_t l_med, int32_t chunk, const int64_t *med_off,
+                           const int64_t *lng_off, const int64_t *nch_off, int32_t *bin_rows,
+                           int32_t *long_rows, int32_t *long_first, int4 *chunks) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n_rows) return;
   const int s = rowptr[r], e = rowptr[r + 1], len = e - s;
@@ -684,7 +686,8 @@ __global__ void k_bin_fill(int64_t n_rows, const int32_t *rowptr, int32_t l_med,
     long_rows[k] = (int32_t)r;
     long_first[k] = (int32_t)c0;
     int64_t c = c0;
-    for (int z = s; z < e; z += chunk, ++c) chunks[c] = make_int4((int)r, z, min(z + chunk, e), 0);
+    for (int z = s; z < e; z += chunk, ++c)
+      chunks[c] = make_int4((int)r, z, min(z + chunk, e), colind[z > s ? z - 1 : z]);
   } else if (len >= l_med) {
     bin_rows[med_off[r]] = (int32_t)r;
   }
@@ -698,13 +701,15 @@ cudaError_t launch_bin_counts(int64_t n_rows, const int32_t *rowptr, int32_t l_m
   return cudaGetLastError();
 }
 
-cudaError_t launch_bin_fill(int64_t n_rows, const int32_t *rowptr, int32_t l_med, int32_t chunk,
-                            const int64_t *med_off, const int64_t *lng_off,
-                            const int64_t *nch_off, int32_t *bin_rows, int32_t *long_rows,
-                            int32_t *long_first, int4 *chunks, cudaStream_t s) {
+cudaError_t launch_bin_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                            int32_t l_med, int32_t chunk, const int64_t *med_off,
+                            const int64_t *lng_off, const int64_t *nch_off, int32_t *bin_rows,
+                            int32_t *long_rows, int32_t *long_first, int4 *chunks,
+                            cudaStream_t s) {
   if (n_rows <= 0) return cudaSuccess;
-  k_bin_fill<<<blocks_for(n_rows), kT, 0, s>>>(n_rows, rowptr, l_med, chunk, med_off, lng_off,
-                                                nch_off, bin_rows, long_rows, long_first, chunks);
+  k_bin_fill<<<blocks_for(n_rows), kT, 0, s>>>(n_rows, rowptr, colind, l_med, chunk, med_off,
+                                                lng_off, nch_off, bin_rows, long_rows,
+                                                long_first, chunks);
   return cudaGetLastError();
 }
 

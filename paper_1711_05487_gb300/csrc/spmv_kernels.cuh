@@ -73,6 +73,86 @@ __device__ __forceinline__ SumT vec_range_dot(const RunArgs &a, int s, int e, in
   return sum;
 }
 
+// One lane's share over [s, e) of an escape row, whose columns are stored in full: ec[0] is
+// the column of element s.
+template <typename ValT, typename VecT, typename AccT, int VS, bool XL2, typename SumT = AccT>
+__device__ __forceinline__ SumT esc_range_dot(const RunArgs &a, int s, int e,
+                                              const int32_t *ec, int lane, uint64_t pol_x) {
+  const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
+  const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
+  SumT sum = 0;
+  for (int j = s + lane; j < e; j += VS)
+    sum += (SumT)(widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(ec + (j - s)), pol_x));
+  return sum;
+}
+
+// One lane's share over [s, e) with 16-bit column deltas: 8 deltas (16 bytes) per lane per
+// step, the column of element j = running + the deltas of elements s..j (a sub-warp prefix
+// sum), where running is the column the decode starts from (the row's base for a range that
+// starts the row, whose first delta is 0; the preceding element's column otherwise).
+template <typename ValT, typename VecT, typename AccT, int VS, bool XL2, typename SumT = AccT>
+__device__ __forceinline__ SumT d16_range_dot(const RunArgs &a, int s, int e, int running,
+                                              int lane, unsigned mask, uint64_t pol_s,
+                                              uint64_t pol_x) {
+  const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
+  const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
+  const uint16_t *__restrict__ dl = a.delta;
+  SumT sum = 0;
+  const int a0 = s & ~7;
+  const int n_it = (e - a0 + VS * 8 - 1) / (VS * 8);
+  for (int it = 0; it < n_it; ++it) {
+    const int b = a0 + it * (VS * 8) + lane * 8;
+    // lanes whose 8 elements start past the range end load nothing (reads stay below
+    // e + 8, inside the arrays' slack)
+    const bool live = b < e;
+    const uint4 d4 = live ? ld16<true>(dl + b, pol_s) : make_uint4(0u, 0u, 0u, 0u);
+    AccT v[8];
+    if (live) {
+      VLoad<AccT, true, 8>::run(val + b, v, pol_s);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = (AccT)0;
+    }
+    const uint32_t w[4] = {d4.x, d4.y, d4.z, d4.w};
+    int p[8];
+    int acc = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int j = b + q;
+      int d = (q & 1) ? (int)(w[q >> 1] >> 16) : (int)(w[q >> 1] & 0xFFFFu);
+      d = (j >= s && j < e) ? d : 0;
+      acc += d;
+      p[q] = acc;
+    }
+    const int incl = group_incl_scan<VS>(acc, lane, mask);
+    const int excl = incl - acc;
+    const int tot = __shfl_sync(mask, incl, VS - 1, VS);
+    AccT xv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int j = b + q;
+      xv[q] = (j >= s && j < e) ? (AccT)ldx<XL2>(x + (running + excl + p[q]), pol_x) : (AccT)0;
+    }
+    if constexpr (std::is_same<SumT, AccT>::value) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int j = b + q;
+        if (j >= s && j < e) sum += v[q] * xv[q];
+      }
+    } else {
+      AccT part = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int j = b + q;
+        if (j >= s && j < e) part += v[q] * xv[q];
+      }
+      sum += (SumT)part;
+    }
+    running += tot;
+  }
+  return sum;
+}
+
 // ------------------------------------------------------------------------ k_rowvec ----
 template <typename ValT, typename VecT, typename AccT, int VS, bool VEC, bool D16, bool XL2>
 __global__ void __launch_bounds__(kRowThreads) k_rowvec(const RunArgs a) {
@@ -96,59 +176,11 @@ __global__ void __launch_bounds__(kRowThreads) k_rowvec(const RunArgs a) {
     sum = vec_range_dot<ValT, VecT, AccT, VS, XL2>(a, s, e, lane, pol_s, pol_x);
   } else {
     const int32_t base = __ldg(a.dbase + row);
-    if (base < 0) {
-      // escape row: its columns are stored in full, in row order
-      const int64_t off = -(int64_t)base - 1 - s;
-      for (int j = s + lane; j < e; j += VS)
-        sum += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(a.esc + off + j), pol_x);
-    } else {
-      // 8 deltas (16 bytes) per lane per step; column = base + running prefix sum
-      const uint16_t *__restrict__ dl = a.delta;
-      const int a0 = s & ~7;
-      const int n_it = (e - a0 + VS * 8 - 1) / (VS * 8);
-      int running = base;
-      for (int it = 0; it < n_it; ++it) {
-        const int b = a0 + it * (VS * 8) + lane * 8;
-        // lanes whose 8 elements start past the row end load nothing (reads stay below
-        // e + 8, inside the arrays' slack)
-        const bool live = b < e;
-        const uint4 d4 = live ? ld16<true>(dl + b, pol_s) : make_uint4(0u, 0u, 0u, 0u);
-        AccT v[8];
-        if (live) {
-          VLoad<AccT, true, 8>::run(val + b, v, pol_s);
-        } else {
-#pragma unroll
-          for (int q = 0; q < 8; ++q) v[q] = (AccT)0;
-        }
-        const uint32_t w[4] = {d4.x, d4.y, d4.z, d4.w};
-        int p[8];
-        int acc = 0;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int j = b + q;
-          int d = (q & 1) ? (int)(w[q >> 1] >> 16) : (int)(w[q >> 1] & 0xFFFFu);
-          d = (j >= s && j < e) ? d : 0;
-          acc += d;
-          p[q] = acc;
-        }
-        const int incl = group_incl_scan<VS>(acc, lane, mask);
-        const int excl = incl - acc;
-        const int tot = __shfl_sync(mask, incl, VS - 1, VS);
-        AccT xv[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int j = b + q;
-          xv[q] = (j >= s && j < e) ? (AccT)ldx<XL2>(x + (running + excl + p[q]), pol_x)
-                                    : (AccT)0;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int j = b + q;
-          if (j >= s && j < e) sum += v[q] * xv[q];
-        }
-        running += tot;
-      }
-    }
+    if (base < 0)
+      sum = esc_range_dot<ValT, VecT, AccT, VS, XL2>(a, s, e, a.esc + (-(int64_t)base - 1),
+                                                     lane, pol_x);
+    else
+      sum = d16_range_dot<ValT, VecT, AccT, VS, XL2>(a, s, e, base, lane, mask, pol_s, pol_x);
   }
   sum = group_sum<VS>(sum, mask);
   if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)sum;
@@ -446,7 +478,27 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm(const RunArgs a, int off, 
 //                  of a long row whose sum goes to an FP64 partial slot; the lanes add
 //                  their steps' sums in FP64 (FP32 accumulation stays within 4 products);
 //  k_bins_fixup  - each long row's partials added in chunk order (reproducible, no atomics).
-template <typename ValT, typename VecT, typename AccT, int VS, bool XL2>
+// One sub-warp's share of elements [s, e) of row `row`, whose decode (delta16 columns)
+// starts from column `running`.
+template <typename ValT, typename VecT, typename AccT, int VS, bool D16, bool XL2, typename SumT>
+__device__ __forceinline__ SumT bins_range_dot(const RunArgs &a, int64_t row, int s, int e,
+                                               int running, int lane, uint64_t pol_s,
+                                               uint64_t pol_x) {
+  if constexpr (D16) {
+    const int32_t base = __ldg(a.dbase + row);
+    if (base < 0) {
+      const int rs = __ldg(a.rowptr + row);
+      return esc_range_dot<ValT, VecT, AccT, VS, XL2, SumT>(
+          a, s, e, a.esc + (-(int64_t)base - 1) + (s - rs), lane, pol_x);
+    }
+    return d16_range_dot<ValT, VecT, AccT, VS, XL2, SumT>(a, s, e, running, lane,
+                                                          group_mask<VS>(), pol_s, pol_x);
+  } else {
+    return vec_range_dot<ValT, VecT, AccT, VS, XL2, SumT>(a, s, e, lane, pol_s, pol_x);
+  }
+}
+
+template <typename ValT, typename VecT, typename AccT, int VS, bool D16, bool XL2>
 __global__ void __launch_bounds__(kRowThreads) k_bins_short(const RunArgs a) {
   constexpr int GROUPS = kRowThreads / VS;
   const int lane = threadIdx.x & (VS - 1);
@@ -456,12 +508,14 @@ __global__ void __launch_bounds__(kRowThreads) k_bins_short(const RunArgs a) {
   if (e - s >= a.bin_l_med) return;
   uint64_t pol_s = policy_evict_first(), pol_x = 0;
   if constexpr (XL2) pol_x = policy_evict_last();
-  AccT sum = vec_range_dot<ValT, VecT, AccT, VS, XL2>(a, s, e, lane, pol_s, pol_x);
+  const int running = D16 ? __ldg(a.dbase + row) : 0;
+  AccT sum = bins_range_dot<ValT, VecT, AccT, VS, D16, XL2, AccT>(a, row, s, e, running, lane,
+                                                                  pol_s, pol_x);
   sum = group_sum<VS>(sum, group_mask<VS>());
   if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)sum;
 }
 
-template <typename ValT, typename VecT, typename AccT, bool XL2>
+template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2>
 __global__ void __launch_bounds__(kRowThreads) k_bins_warp(const RunArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t item = ((int64_t)blockIdx.x * kRowThreads + threadIdx.x) / 32;
@@ -469,15 +523,18 @@ __global__ void __launch_bounds__(kRowThreads) k_bins_warp(const RunArgs a) {
   uint64_t pol_s = policy_evict_first(), pol_x = 0;
   if constexpr (XL2) pol_x = policy_evict_last();
   if (item < a.bin_n_chunks) {
-    const int4 c = a.bin_chunks[item];   // (row, first nonzero, end nonzero, unused)
-    const double sum = vec_range_dot<ValT, VecT, AccT, 32, XL2, double>(a, c.y, c.z, lane,
-                                                                       pol_s, pol_x);
+    // (row, first nonzero, end nonzero, the column the delta decode starts from)
+    const int4 c = a.bin_chunks[item];
+    const double sum = bins_range_dot<ValT, VecT, AccT, 32, D16, XL2, double>(
+        a, c.x, c.y, c.z, c.w, lane, pol_s, pol_x);
     const double t = group_sum<32>(sum, 0xffffffffu);
     if (lane == 0) a.bin_partials[item] = t;
   } else {
     const int row = __ldg(a.bin_rows + (item - a.bin_n_chunks));
     const int s = __ldg(a.rowptr + row), e = __ldg(a.rowptr + row + 1);
-    double sum = vec_range_dot<ValT, VecT, AccT, 32, XL2, double>(a, s, e, lane, pol_s, pol_x);
+    const int running = D16 ? __ldg(a.dbase + row) : 0;
+    double sum = bins_range_dot<ValT, VecT, AccT, 32, D16, XL2, double>(a, row, s, e, running,
+                                                                        lane, pol_s, pol_x);
     sum = group_sum<32>(sum, 0xffffffffu);
     if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)sum;
   }
@@ -492,26 +549,32 @@ __global__ void k_bins_fixup(const RunArgs a) {
   static_cast<VecT *>(a.y)[a.bin_long_rows[i]] = (VecT)t;
 }
 
-template <typename ValT, typename VecT, typename AccT, int VS>
-void launch_bins_short(bool xl2, const RunArgs &a, cudaStream_t s) {
-  const unsigned g = (unsigned)((a.n_rows + (kRowThreads / VS) - 1) / (kRowThreads / VS));
-  if (xl2) k_bins_short<ValT, VecT, AccT, VS, true><<<g, kRowThreads, 0, s>>>(a);
-  else k_bins_short<ValT, VecT, AccT, VS, false><<<g, kRowThreads, 0, s>>>(a);
-}
-
-template <typename ValT, typename VecT, typename AccT>
-cudaError_t launch_bins(bool xl2, const RunArgs &a, cudaStream_t s) {
-  if (a.n_rows == 0) return cudaSuccess;
+template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2>
+void launch_bins_k(const RunArgs &a, cudaStream_t s) {
   switch (a.bin_vs_short) {
-    case 2: launch_bins_short<ValT, VecT, AccT, 2>(xl2, a, s); break;
-    case 8: launch_bins_short<ValT, VecT, AccT, 8>(xl2, a, s); break;
-    default: launch_bins_short<ValT, VecT, AccT, 4>(xl2, a, s); break;
+    case 2: k_bins_short<ValT, VecT, AccT, 2, D16, XL2><<<(unsigned)((a.n_rows + 127) / 128),
+                                                         kRowThreads, 0, s>>>(a); break;
+    case 8: k_bins_short<ValT, VecT, AccT, 8, D16, XL2><<<(unsigned)((a.n_rows + 31) / 32),
+                                                         kRowThreads, 0, s>>>(a); break;
+    default: k_bins_short<ValT, VecT, AccT, 4, D16, XL2><<<(unsigned)((a.n_rows + 63) / 64),
+                                                          kRowThreads, 0, s>>>(a); break;
   }
   const int64_t items = a.bin_n_med + a.bin_n_chunks;
   if (items > 0) {
     const unsigned g = (unsigned)((items * 32 + kRowThreads - 1) / kRowThreads);
-    if (xl2) k_bins_warp<ValT, VecT, AccT, true><<<g, kRowThreads, 0, s>>>(a);
-    else k_bins_warp<ValT, VecT, AccT, false><<<g, kRowThreads, 0, s>>>(a);
+    k_bins_warp<ValT, VecT, AccT, D16, XL2><<<g, kRowThreads, 0, s>>>(a);
+  }
+}
+
+template <typename ValT, typename VecT, typename AccT>
+cudaError_t launch_bins(bool d16, bool xl2, const RunArgs &a, cudaStream_t s) {
+  if (a.n_rows == 0) return cudaSuccess;
+  if (d16) {
+    if (xl2) launch_bins_k<ValT, VecT, AccT, true, true>(a, s);
+    else launch_bins_k<ValT, VecT, AccT, true, false>(a, s);
+  } else {
+    if (xl2) launch_bins_k<ValT, VecT, AccT, false, true>(a, s);
+    else launch_bins_k<ValT, VecT, AccT, false, false>(a, s);
   }
   if (a.bin_n_long > 0)
     k_bins_fixup<VecT><<<(unsigned)((a.bin_n_long + 255) / 256), 256, 0, s>>>(a);
@@ -544,7 +607,7 @@ cudaError_t launch_rowvec_vs(const spmv_variant &v, const RunArgs &a, cudaStream
 template <typename ValT, typename VecT, typename AccT>
 cudaError_t launch_spmv_impl(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
-  if (v.partition == 2) return launch_bins<ValT, VecT, AccT>(v.xpath != 0, a, s);
+  if (v.partition == 2) return launch_bins<ValT, VecT, AccT>(v.index == 1, v.xpath != 0, a, s);
   if (v.partition == 1) {
     if (a.n_tiles == 0) return cudaSuccess;
     if (v.xpath) k_merge<ValT, VecT, AccT, true><<<(unsigned)a.n_tiles, kMergeThreads, 0, s>>>(a);

@@ -86,9 +86,9 @@ def test_row_bins_bit_exact(api, torch):
     for m in (synth.power_law(60_000, alpha=1.4, clip=60_000, seed=19, dtype=np.float64),
               synth.laplacian_2d(40)):
         A = api.SpmvMatrix.from_csr(m)
-        A.set_variant(partition=2)
+        A.set_variant(partition=2, index=1)
         med, lng, first, ch = (t.cpu().numpy() for t in A.row_bins())
-        om, ol, of, oc = oracle.row_bins(m.rowptr, l_med=64, chunk=4096)
+        om, ol, of, oc = oracle.row_bins(m.rowptr, m.colind, l_med=64, chunk=4096)
         assert np.array_equal(med, om) and np.array_equal(lng, ol)
         assert np.array_equal(first, of) and np.array_equal(ch, oc)
 

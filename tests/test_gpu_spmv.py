@@ -46,6 +46,8 @@ VARIANTS = (
        dict(index=1, vec=1, xpath=1, vs=4)]                            # ML (+ joint)
     + [dict(partition=1), dict(partition=1, xpath=1)]                  # IMB
     + [dict(partition=2, vs=w) for w in (2, 4, 8)] + [dict(partition=2, xpath=1)]
+    + [dict(partition=2, index=1, vs=w) for w in (2, 8)]                # MB + IMB
+    + [dict(partition=2, index=1, xpath=1)]
     + [dict(vec=1, vs=1, tile_rows=r, tile_pipe=p) for r in (32, 64, 128) for p in (0, 1)]
     + [dict(index=1, vec=1, vs=1, tile_rows=r, tile_pipe=p, xpath=p) for r in (32, 128)
        for p in (0, 1)]                                                # width-1 tiles
@@ -132,7 +134,7 @@ def test_precisions(api, torch, name, storage, vec, acc):
         x64 = x64.astype(np.float32).astype(np.float64)    # the x the GPU sees
     x = _dev(torch, x64, torch.float64 if vec == "f64" else torch.float32)
     variants = [dict(), dict(vec=1, vs=4), dict(index=1, vec=1, vs=4), dict(partition=1),
-                dict(partition=2),
+                dict(partition=2), dict(partition=2, index=1),
                 dict(vec=1, xpath=1, vs=8), dict(vec=1, vs=1),
                 dict(index=1, vec=1, vs=1, tile_rows=64, tile_pipe=1),
                 dict(vec=1, vs=1, tile_rows=32, xpath=1)]
