@@ -88,6 +88,12 @@ def _declare(L):
     L.oracle_delta16_encode.restype = _I64
     L.oracle_delta16_decode.argtypes = [_I64, _P, _P, _P, _P, _P]
     L.oracle_delta16_decode.restype = None
+    L.oracle_delta8_encode.argtypes = [_I64, _P, _P, _P, _P, _P]
+    L.oracle_delta8_encode.restype = _I64
+    L.oracle_delta8_decode.argtypes = [_I64, _P, _P, _P, _P, _P]
+    L.oracle_delta8_decode.restype = None
+    L.oracle_delta_width.argtypes = [_I64, _P, _P]
+    L.oracle_delta_width.restype = ctypes.c_int32
     L.oracle_merge_path.argtypes = [_I64, _I64, _P, _I64, _P]
     L.oracle_merge_path.restype = None
     L.oracle_features.argtypes = [_I64, _I64, _P, _P, _I64, _I64, _I64, _P, _P]
@@ -242,6 +248,32 @@ def delta16_encode(rowptr, colind):
     esc = np.empty(max(1, ci.shape[0]), dtype=np.int32)
     n_esc = lib().oracle_delta16_encode(n, _p(rp), _p(ci), _p(base), _p(delta), _p(esc))
     return base, delta, esc[:n_esc].copy()
+
+
+def delta8_encode(rowptr, colind):
+    """Returns (base int32[N], delta uint8[NNZ], esc_col int32[n_esc])."""
+    rp, ci = _c(rowptr, np.int32), _c(colind, np.int32)
+    n = rp.shape[0] - 1
+    base = np.empty(n, dtype=np.int32)
+    delta = np.empty(ci.shape[0], dtype=np.uint8)
+    esc = np.empty(max(1, ci.shape[0]), dtype=np.int32)
+    n_esc = lib().oracle_delta8_encode(n, _p(rp), _p(ci), _p(base), _p(delta), _p(esc))
+    return base, delta, esc[:n_esc].copy()
+
+
+def delta8_decode(rowptr, base, delta, esc_col):
+    rp = _c(rowptr, np.int32)
+    b, d = _c(base, np.int32), _c(delta, np.uint8)
+    e = _c(esc_col if len(esc_col) else np.zeros(1, np.int32), np.int32)
+    out = np.empty(d.shape[0], dtype=np.int32)
+    lib().oracle_delta8_decode(rp.shape[0] - 1, _p(rp), _p(b), _p(d), _p(e), _p(out))
+    return out
+
+
+def delta_width(rowptr, colind) -> int:
+    """8 or 16: the per-matrix width of the delta index."""
+    rp, ci = _c(rowptr, np.int32), _c(colind, np.int32)
+    return int(lib().oracle_delta_width(rp.shape[0] - 1, _p(rp), _p(ci)))
 
 
 def delta16_decode(rowptr, base, delta, esc_col):

@@ -16,7 +16,7 @@
  *   - y = A x in FP64, plus sum |a_ij x_j|    (Section II, Fig. 1)
  *   - multi-RHS y = A X                       (Fig. 1 applied column by column)
  *   - FP64 -> FP32 / BF16 round-to-nearest-even value storage
- *   - 16-bit delta column-index format       (Section III-E, MB optimization)
+ *   - 8- and 16-bit delta column-index formats and the width choice (Section III-E, MB)
  *   - merge-path coordinates of a CSR matrix (Section III-E, IMB optimization: the
  *     nnz-balanced work split)
  *   - row decomposition into short, medium and chunked long rows (Section III-E, IMB:
@@ -386,6 +386,72 @@ void oracle_delta16_decode(int64_t n_rows, const int32_t *rowptr, const int32_t 
       }
     }
   }
+}
+
+/* The 8-bit form of the same index: a row whose consecutive column distances all fit 8 bits
+ * stores them as uint8 (first delta 0), any other non-empty row is an escape row.          */
+int64_t oracle_delta8_encode(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                             int32_t *base, uint8_t *delta, int32_t *esc_col) {
+  int64_t n_esc = 0;
+  for (int64_t i = 0; i < n_rows; ++i) {
+    int64_t b = rowptr[i], e = rowptr[i + 1];
+    if (b == e) {
+      base[i] = 0;
+      continue;
+    }
+    int fits = 1;
+    for (int64_t j = b + 1; j < e; ++j)
+      if ((int64_t)colind[j] - (int64_t)colind[j - 1] > 255) fits = 0;
+    if (fits) {
+      base[i] = colind[b];
+      delta[b] = 0;
+      for (int64_t j = b + 1; j < e; ++j) delta[j] = (uint8_t)(colind[j] - colind[j - 1]);
+    } else {
+      base[i] = (int32_t)(-(1 + n_esc));
+      for (int64_t j = b; j < e; ++j) {
+        delta[j] = 0;
+        esc_col[n_esc++] = colind[j];
+      }
+    }
+  }
+  return n_esc;
+}
+
+void oracle_delta8_decode(int64_t n_rows, const int32_t *rowptr, const int32_t *base,
+                          const uint8_t *delta, const int32_t *esc_col, int32_t *colind) {
+  for (int64_t i = 0; i < n_rows; ++i) {
+    int64_t b = rowptr[i], e = rowptr[i + 1];
+    if (b == e) continue;
+    if (base[i] < 0) {
+      int64_t off = -(int64_t)base[i] - 1;
+      for (int64_t j = b; j < e; ++j) colind[j] = esc_col[off + (j - b)];
+    } else {
+      int64_t c = base[i];
+      for (int64_t j = b; j < e; ++j) {
+        c += delta[j];
+        colind[j] = (int32_t)c;
+      }
+    }
+  }
+}
+
+/* "8- or 16-bit deltas wherever possible, never both" (Section III-E, MB): one width per
+ * matrix, the one whose index is smaller. Index bytes of width w: w/8 per nonzero of the
+ * rows that fit w, 4 per nonzero of the escape rows (the per-row base is the same for
+ * both). Returns 8 when that is strictly fewer bytes than 16, else 16.                    */
+int32_t oracle_delta_width(int64_t n_rows, const int32_t *rowptr, const int32_t *colind) {
+  int64_t bytes8 = 0, bytes16 = 0;
+  for (int64_t i = 0; i < n_rows; ++i) {
+    int64_t b = rowptr[i], e = rowptr[i + 1];
+    int64_t maxd = 0;
+    for (int64_t j = b + 1; j < e; ++j) {
+      int64_t d = (int64_t)colind[j] - (int64_t)colind[j - 1];
+      if (d > maxd) maxd = d;
+    }
+    bytes8 += (maxd <= 255 ? 1 : 4) * (e - b);
+    bytes16 += (maxd <= 65535 ? 2 : 4) * (e - b);
+  }
+  return bytes8 < bytes16 ? 8 : 16;
 }
 
 /* ---------------------------------------------------------------------------------- */

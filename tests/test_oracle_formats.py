@@ -93,6 +93,44 @@ def test_delta16_stencil_has_no_escape_rows():
     assert esc.size == 0
 
 
+def test_delta8_hand_example_and_gap_limit():
+    rp = np.array([0, 3, 3, 5, 6, 8], np.int32)
+    ci = np.array([2, 3, 10, 0, 300, 5, 100, 355], np.int32)
+    base, delta, esc = oracle.delta8_encode(rp, ci)
+    assert list(base) == [2, 0, -1, 5, 100]          # row 2's gap 300 escapes, 255 fits
+    assert list(delta) == [0, 1, 7, 0, 0, 0, 0, 255]
+    assert list(esc) == [0, 300]
+    assert np.array_equal(oracle.delta8_decode(rp, base, delta, esc), ci)
+
+
+@pytest.mark.parametrize("gen", [lambda: synth.banded(3000, 40, 0.5, seed=5),
+                                 lambda: synth.laplacian_2d(200),
+                                 lambda: synth.power_law(20_000, seed=6)])
+def test_delta8_round_trip(gen):
+    m = gen()
+    base, delta, esc = oracle.delta8_encode(m.rowptr, m.colind)
+    assert np.array_equal(oracle.delta8_decode(m.rowptr, base, delta, esc), m.colind)
+
+
+def test_delta_width_choice():
+    # every gap of the 2-D Laplacian on a 200-wide grid is 1 or 199: 8 bits fit everywhere
+    assert oracle.delta_width(*_rc(synth.laplacian_2d(200))) == 8
+    # the 27-point stencil's plane gaps (~n^2) escape 8 bits: 16
+    assert oracle.delta_width(*_rc(synth.stencil_27pt(20))) == 16
+    # one row of 4 nonzeros with a 256 gap (16 bytes escaped at 8 bits, 8 at 16 bits) next
+    # to short-gap rows: 8 bits win only when the fitting rows save more than the escape
+    # costs. Rows: [0,1,2,300] and k rows [0,1,2,3]: bytes8 = 16 + 4k, bytes16 = 8 + 8k
+    for k, want in ((1, 16), (2, 16), (3, 8)):
+        rows = [[0, 1, 2, 300]] + [[0, 1, 2, 3]] * k
+        rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+        ci = np.concatenate(rows).astype(np.int32)
+        assert oracle.delta_width(rp, ci) == want, k
+
+
+def _rc(m):
+    return m.rowptr, m.colind
+
+
 # -------------------------------------------------------------------- merge path
 def test_merge_path_hand_example():
     rp = np.array([0, 2, 2, 5], np.int32)
