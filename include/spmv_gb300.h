@@ -74,8 +74,9 @@ typedef struct {
                         4096 on one warp each, longer rows in 4096-nonzero chunks summed
                         in FP64 in chunk order. 1 and 2 are the decompositions of
                         Section III-E (IMB); the autotuner picks between them         */
-  int32_t index;     /* 0: int32 columns; 1: 16-bit column deltas with escape rows (MB);
-                        merge-path tiles (partition 1) always read int32 columns          */
+  int32_t index;     /* 0: int32 columns; 1: 8- or 16-bit column deltas (one width per
+                        matrix, see spmv_get_delta) with escape rows (MB); merge-path
+                        tiles (partition 1) always read int32 columns                     */
   int32_t xpath;     /* 0: default; 1: x kept L2-resident (evict-last gathers through the
                         read-only path, evict-first streams) (ML)                         */
   int32_t vec;       /* 0: scalar loads; 1: 128-bit loads of val/colind, unrolled (MB/CMP) */
@@ -198,11 +199,16 @@ spmv_status spmv_run_spmm(spmv_handle_t h, const void *X, void *Y, int32_t k,
 spmv_status spmv_export_csr(spmv_handle_t h, int32_t *row_ptr, int32_t *col_ind, void *val,
                             spmv_stream_t stream);
 
-/* Copies the 16-bit delta index (Section III-E, MB) into caller device buffers:
- * base[n_rows], delta[nnz], esc_col[*n_esc]; pass esc_col = NULL to query *n_esc.
- * SPMV_ERR_NOT_TUNED if the installed variant has no delta index. */
-spmv_status spmv_get_delta16(spmv_handle_t h, int32_t *base, uint16_t *delta,
-                             int32_t *esc_col, int64_t *n_esc, spmv_stream_t stream);
+/* Copies the delta column index (Section III-E, MB) of the handle: base[n_rows] (a row's
+ * first column, or -(1 + offset) into esc_col for an escape row, 0 for an empty row),
+ * delta[nnz] of *bits (8 or 16) bits each (the first delta of a row is 0) and
+ * esc_col[*n_esc] (escape rows' columns in full, in row order). The width is chosen per
+ * matrix: 8 bits when that index is strictly smaller than the 16-bit one (1 or 2 bytes per
+ * nonzero of the rows whose gaps fit, 4 per nonzero of escape rows), else 16 -- "8- or
+ * 16-bit deltas, never both". Pass base = delta = esc_col = NULL to query *n_esc and
+ * *bits. SPMV_ERR_NOT_TUNED if no delta index has been built. */
+spmv_status spmv_get_delta(spmv_handle_t h, int32_t *base, void *delta, int32_t *esc_col,
+                           int64_t *n_esc, int32_t *bits, spmv_stream_t stream);
 
 /* Copies the merge-path tile table (rows ended, nonzeros consumed) for tile boundaries
  * 0..n_tiles into coord (device, int32[2 * (n_tiles + 1)]); pass coord = NULL to query

@@ -102,7 +102,7 @@ _DECL = {
     "spmv_run_spmm": (_I32, [_P, _P, _P, _I32, _P]),
     "spmv_cg": (_I32, [_P, _P, _P, _I32, _D, _I32, _P, ctypes.POINTER(spmv_cg_report), _P]),
     "spmv_export_csr": (_I32, [_P, _P, _P, _P, _P]),
-    "spmv_get_delta16": (_I32, [_P, _P, _P, _P, ctypes.POINTER(_I64), _P]),
+    "spmv_get_delta": (_I32, [_P, _P, _P, _P, ctypes.POINTER(_I64), ctypes.POINTER(_I32), _P]),
     "spmv_get_merge_path": (_I32, [_P, _P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P]),
     "spmv_get_row_bins": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
     "spmv_features": (_I32, [_P, _I32, _P, _P, _P]),
@@ -227,10 +227,11 @@ def spmv_export_csr(h, row_ptr, col_ind, val, stream=0):
     _call("spmv_export_csr", h, row_ptr, col_ind, val, stream)
 
 
-def spmv_get_delta16(h, base=None, delta=None, esc_col=None, stream=0) -> int:
-    n = _I64()
-    _call("spmv_get_delta16", h, base, delta, esc_col, ctypes.byref(n), stream)
-    return n.value
+def spmv_get_delta(h, base=None, delta=None, esc_col=None, stream=0) -> tuple[int, int]:
+    """Returns (n_esc, bits); copies the index when the pointers are given."""
+    n, bits = _I64(), _I32()
+    _call("spmv_get_delta", h, base, delta, esc_col, ctypes.byref(n), ctypes.byref(bits), stream)
+    return n.value, bits.value
 
 
 def spmv_get_row_bins(h, med_rows=None, long_rows=None, long_first=None, chunks=None,

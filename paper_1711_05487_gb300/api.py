@@ -215,14 +215,16 @@ class SpmvMatrix:
         _abi.spmv_export_csr(self._h, rp.data_ptr(), ci.data_ptr(), v.data_ptr(), _stream(stream))
         return rp, ci[:self.nnz], v[:self.nnz]
 
-    def delta16(self, device="cuda", stream=None):
-        n_esc = _abi.spmv_get_delta16(self._h)
+    def delta(self, device="cuda", stream=None):
+        """The delta column index: (base, delta as uint8/int16 bits, escape columns, width)."""
+        n_esc, bits = _abi.spmv_get_delta(self._h)
         base = torch.empty(max(self.n_rows, 1), dtype=torch.int32, device=device)
-        delta = torch.empty(max(self.nnz, 1), dtype=torch.int16, device=device)
+        delta = torch.empty(max(self.nnz, 1), dtype=torch.uint8 if bits == 8 else torch.int16,
+                            device=device)
         esc = torch.empty(max(n_esc, 1), dtype=torch.int32, device=device)
-        _abi.spmv_get_delta16(self._h, base.data_ptr(), delta.data_ptr(), esc.data_ptr(),
-                              _stream(stream))
-        return base[:self.n_rows], delta[:self.nnz], esc[:n_esc]
+        _abi.spmv_get_delta(self._h, base.data_ptr(), delta.data_ptr(), esc.data_ptr(),
+                            _stream(stream))
+        return base[:self.n_rows], delta[:self.nnz], esc[:n_esc], bits
 
     def row_bins(self, device="cuda", stream=None):
         """The row decomposition (partition 2): medium rows, long rows, each long row's first

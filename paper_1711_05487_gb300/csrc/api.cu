@@ -132,6 +132,7 @@ struct spmv_matrix {
   // optimization-pool data
   DevBuf dbase, delta, esc;
   int64_t n_esc = 0;
+  int32_t delta_bits = 16;     // width of the built delta index: 8 or 16
   bool has_delta = false;
   DevBuf coord, tail_row, tail_val, head_val;
   int64_t n_tiles = 0;
@@ -190,7 +191,8 @@ RunArgs run_args(const spmv_matrix *h, const void *x, void *y) {
   a.nnz = h->nnz;
   a.rowptr = h->rowptr.as<int32_t>();
   a.colind = h->colind.as<int32_t>();
-  a.delta = h->delta.as<uint16_t>();
+  a.delta = h->delta.p;
+  a.delta_bits = h->delta_bits;
   a.dbase = h->dbase.as<int32_t>();
   a.esc = h->esc.as<int32_t>();
   a.val = h->val_ptr();
@@ -219,26 +221,38 @@ RunArgs run_args(const spmv_matrix *h, const void *x, void *y) {
   return a;
 }
 
-void build_delta16(spmv_matrix *h, cudaStream_t s) {
+// The delta index (Section III-E, MB): 8- or 16-bit column deltas, never both; the width
+// is the one whose index is smaller (1 or 2 bytes per nonzero of the rows whose gaps fit,
+// 4 per nonzero of escape rows), 16 on a tie.
+void build_delta(spmv_matrix *h, cudaStream_t s) {
   if (h->has_delta) return;
   const int64_t n = h->n_rows;
   DevBuf cnt;
-  cnt.alloc(sizeof(int64_t) * (size_t)(n + 1), 8, s, true);
-  CK(launch_delta16_flags(n, h->rowptr.as<int32_t>(), h->colind.as<int32_t>(), cnt.as<int64_t>(), s));
+  cnt.alloc(sizeof(int64_t) * 2 * (size_t)(n + 1), 8, s, true);
+  int64_t *e8 = cnt.as<int64_t>(), *e16 = e8 + (n + 1);
+  CK(launch_delta_flags(n, h->rowptr.as<int32_t>(), h->colind.as<int32_t>(), e8, e16, s));
   const int64_t se = scan_scratch_elems(n);
   DevBuf scr;
   scr.alloc(sizeof(int64_t) * (size_t)se, 8, s);
-  CK(launch_scan_i64(cnt.as<int64_t>(), n, cnt.as<int64_t>() + n, scr.as<int64_t>(), se, s));
-  int64_t n_esc = 0;
-  CK(cudaMemcpyAsync(&n_esc, cnt.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(launch_scan_i64(e8, n, e8 + n, scr.as<int64_t>(), se, s));
+  CK(launch_scan_i64(e16, n, e16 + n, scr.as<int64_t>(), se, s));
+  int64_t esc8 = 0, esc16 = 0;
+  CK(cudaMemcpyAsync(&esc8, e8 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&esc16, e16 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  const int64_t bytes8 = (h->nnz - esc8) + 4 * esc8;
+  const int64_t bytes16 = 2 * (h->nnz - esc16) + 4 * esc16;
+  const int bits = bytes8 < bytes16 ? 8 : 16;
+  const int64_t n_esc = bits == 8 ? esc8 : esc16;
   h->dbase.alloc(sizeof(int32_t) * (size_t)n, 4, s);
-  h->delta.alloc(sizeof(uint16_t) * (size_t)h->nnz, 2, s);
+  h->delta.alloc((size_t)(bits / 8) * (size_t)h->nnz, (size_t)(bits / 8), s);
   h->esc.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(n_esc, 1), 4, s);
-  CK(launch_delta16_fill(n, h->rowptr.as<int32_t>(), h->colind.as<int32_t>(), cnt.as<int64_t>(),
-                         h->dbase.as<int32_t>(), h->delta.as<uint16_t>(), h->esc.as<int32_t>(), s));
+  CK(launch_delta_fill(bits, n, h->rowptr.as<int32_t>(), h->colind.as<int32_t>(),
+                       bits == 8 ? e8 : e16, h->dbase.as<int32_t>(), h->delta.p,
+                       h->esc.as<int32_t>(), s));
   CK(cudaStreamSynchronize(s));
   h->n_esc = n_esc;
+  h->delta_bits = bits;
   h->has_delta = true;
 }
 
@@ -297,8 +311,13 @@ void build_bins(spmv_matrix *h, cudaStream_t s) {
 // `rows` consecutive rows; the staged capacity is the matrix's largest such tile, capped by
 // the shared-memory budget of one stage (48 KB for one tile per CTA, 56 KB per stage for
 // the persistent two-stage kernel). Tiles above the cap are computed from global memory.
-int32_t max_tile_elems(spmv_matrix *h, int rows, cudaStream_t s) {
-  CK(launch_tile_max(h->n_rows, h->rowptr.as<int32_t>(), rows, h->small.as<int32_t>(), s));
+// staged-tile alignment of the variant's column representation
+int tile_align(const spmv_matrix *h, const spmv_variant &v) {
+  return v.index == 1 ? stage_align_bits(h->delta_bits) : 8;
+}
+
+int32_t max_tile_elems(spmv_matrix *h, int rows, int align, cudaStream_t s) {
+  CK(launch_tile_max(h->n_rows, h->rowptr.as<int32_t>(), rows, align, h->small.as<int32_t>(), s));
   int32_t m = 0;
   CK(cudaMemcpyAsync(&m, h->small.p, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -306,16 +325,17 @@ int32_t max_tile_elems(spmv_matrix *h, int rows, cudaStream_t s) {
 }
 
 int32_t tile_limit(const spmv_matrix *h, const spmv_variant &v, bool pipe) {
-  const int eb = (int)dtype_bytes(h->storage) + (v.index == 1 ? 2 : 4);
+  const int eb = (int)dtype_bytes(h->storage) + (v.index == 1 ? h->delta_bits / 8 : 4);
   const int budget = (pipe ? 56 : 48) * 1024 - 32;
-  return ((budget / eb) / 8) * 8;
+  const int al = tile_align(h, v);
+  return ((budget / eb) / al) * al;
 }
 
 void set_tile_geometry(spmv_matrix *h, const spmv_variant &v, int rows, bool pipe,
                        cudaStream_t s) {
   h->tile_rows = rows;
   h->tile_pipe = pipe ? 1 : 0;
-  h->tile_cap = std::min(max_tile_elems(h, rows, s), tile_limit(h, v, pipe));
+  h->tile_cap = std::min(max_tile_elems(h, rows, tile_align(h, v), s), tile_limit(h, v, pipe));
 }
 
 // Default geometry: the largest of 128, 64, 32 rows per tile whose largest tile fits one
@@ -323,7 +343,7 @@ void set_tile_geometry(spmv_matrix *h, const spmv_variant &v, int rows, bool pip
 void compute_tile_cap(spmv_matrix *h, const spmv_variant &v, cudaStream_t s) {
   const int32_t limit = tile_limit(h, v, false);
   for (int rows = kTileRows; rows >= 32; rows /= 2) {
-    const int32_t m = max_tile_elems(h, rows, s);
+    const int32_t m = max_tile_elems(h, rows, tile_align(h, v), s);
     if (m <= limit) {
       h->tile_rows = rows;
       h->tile_pipe = 0;
@@ -339,7 +359,7 @@ void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
     v.index = 0;                 // the delta index is built for sub-warp rows only
     build_merge(h, s);
   } else if (v.partition == 2) {
-    if (v.index == 1) build_delta16(h, s);
+    if (v.index == 1) build_delta(h, s);
     v.vec = 1;
     if (v.vs != 2 && v.vs != 4 && v.vs != 8) v.vs = 4;   // short rows' sub-warp width
     v.tile_rows = 0;
@@ -349,7 +369,7 @@ void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
   } else {
     if (v.index == 1) {
       v.vec = 1;
-      build_delta16(h, s);
+      build_delta(h, s);
     }
     if (v.vs == 0) {
       v.vs = (v.vec || v.index == 1) ? pool_vs(h->nnz_avg(), v.index == 1 ? 8 : 4)
@@ -1346,9 +1366,10 @@ spmv_status spmv_export_csr(spmv_handle_t h, int32_t *row_ptr, int32_t *col_ind,
   return guarded([&]() -> spmv_status {
     CK(cudaMemcpyAsync(row_ptr, h->rowptr.p, 4 * (size_t)(h->n_rows + 1), cudaMemcpyDeviceToDevice, s));
     if (h->nnz > 0) {
-      if (h->tuned && h->variant.partition == 0 && h->variant.index == 1 && h->has_delta) {
-        CK(launch_delta16_decode(h->n_rows, h->rowptr.as<int32_t>(), h->dbase.as<int32_t>(),
-                                 h->delta.as<uint16_t>(), h->esc.as<int32_t>(), col_ind, s));
+      if (h->tuned && h->variant.partition != 1 && h->variant.index == 1 && h->has_delta) {
+        CK(launch_delta_decode(h->delta_bits, h->n_rows, h->rowptr.as<int32_t>(),
+                               h->dbase.as<int32_t>(), h->delta.p, h->esc.as<int32_t>(), col_ind,
+                               s));
       } else {
         CK(cudaMemcpyAsync(col_ind, h->colind.p, 4 * (size_t)h->nnz, cudaMemcpyDeviceToDevice, s));
       }
@@ -1360,17 +1381,19 @@ spmv_status spmv_export_csr(spmv_handle_t h, int32_t *row_ptr, int32_t *col_ind,
   });
 }
 
-spmv_status spmv_get_delta16(spmv_handle_t h, int32_t *base, uint16_t *delta, int32_t *esc_col,
-                             int64_t *n_esc, spmv_stream_t stream) {
-  if (!h || !n_esc) return SPMV_ERR_ARG;
+spmv_status spmv_get_delta(spmv_handle_t h, int32_t *base, void *delta, int32_t *esc_col,
+                           int64_t *n_esc, int32_t *bits, spmv_stream_t stream) {
+  if (!h || !n_esc || !bits) return SPMV_ERR_ARG;
   if (!h->has_delta) return SPMV_ERR_NOT_TUNED;
   *n_esc = h->n_esc;
+  *bits = h->delta_bits;
   if (!esc_col && !base && !delta) return SPMV_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return guarded([&]() -> spmv_status {
     if (base) CK(cudaMemcpyAsync(base, h->dbase.p, 4 * (size_t)h->n_rows, cudaMemcpyDeviceToDevice, s));
     if (delta && h->nnz)
-      CK(cudaMemcpyAsync(delta, h->delta.p, 2 * (size_t)h->nnz, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(delta, h->delta.p, (size_t)(h->delta_bits / 8) * (size_t)h->nnz,
+                         cudaMemcpyDeviceToDevice, s));
     if (esc_col && h->n_esc)
       CK(cudaMemcpyAsync(esc_col, h->esc.p, 4 * (size_t)h->n_esc, cudaMemcpyDeviceToDevice, s));
     CK(cudaStreamSynchronize(s));

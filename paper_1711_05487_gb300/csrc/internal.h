@@ -19,12 +19,22 @@ constexpr int kMergeIpt = 7;   // merge items per thread: an odd stride between 
                                // their shared-memory reads in distinct banks
 constexpr int kMergeItems = kMergeThreads * kMergeIpt;
 
+// Column index representation of a kernel instance: DB = 0 for int32 columns, 16 or 8 for
+// column deltas of that width. A staged tile starts and ends on a multiple of
+// stage_align<DB>() elements, so that its index copy is a whole number of 16-byte units.
+template <int DB> struct IdxOf { using type = int32_t; };
+template <> struct IdxOf<16> { using type = uint16_t; };
+template <> struct IdxOf<8> { using type = uint8_t; };
+template <int DB> __host__ __device__ constexpr int stage_align() { return DB == 8 ? 16 : 8; }
+inline int stage_align_bits(int db) { return db == 8 ? 16 : 8; }
+
 // Everything a SpMV launch needs; unused pointers are null.
 struct RunArgs {
   int64_t n_rows = 0, n_cols = 0, nnz = 0;
   const int32_t *rowptr = nullptr;
   const int32_t *colind = nullptr;
-  const uint16_t *delta = nullptr;   // 16-bit column deltas
+  const void *delta = nullptr;       // column deltas, delta_bits (8 or 16) wide
+  int32_t delta_bits = 16;
   const int32_t *dbase = nullptr;    // per-row base column / escape offset
   const int32_t *esc = nullptr;      // columns of escape rows
   const void *val = nullptr;         // storage dtype
@@ -151,14 +161,17 @@ cudaError_t launch_round_values(const double *in, void *out, int64_t n, spmv_dty
                                 cudaStream_t s);
 cudaError_t launch_convert_values(const void *in, spmv_dtype from, void *out, spmv_dtype to,
                                   int64_t n, cudaStream_t s);
-cudaError_t launch_delta16_flags(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
-                                 int64_t *esc_count, cudaStream_t s);
-cudaError_t launch_delta16_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
-                                const int64_t *esc_off, int32_t *dbase, uint16_t *delta,
-                                int32_t *esc, cudaStream_t s);
-cudaError_t launch_delta16_decode(int64_t n_rows, const int32_t *rowptr, const int32_t *dbase,
-                                  const uint16_t *delta, const int32_t *esc, int32_t *colind,
-                                  cudaStream_t s);
+// Delta index: per row, the nonzeros that escape 8-bit and 16-bit deltas (the row's length
+// when some gap exceeds 255, resp. 65535, else 0); then, for the chosen width, the fill and
+// the inverse (decode back to colind).
+cudaError_t launch_delta_flags(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                               int64_t *esc8, int64_t *esc16, cudaStream_t s);
+cudaError_t launch_delta_fill(int bits, int64_t n_rows, const int32_t *rowptr,
+                              const int32_t *colind, const int64_t *esc_off, int32_t *dbase,
+                              void *delta, int32_t *esc, cudaStream_t s);
+cudaError_t launch_delta_decode(int bits, int64_t n_rows, const int32_t *rowptr,
+                                const int32_t *dbase, const void *delta, const int32_t *esc,
+                                int32_t *colind, cudaStream_t s);
 // exclusive scan of n int64 values in place; total (device, 1 value) receives the sum
 cudaError_t launch_scan_i64(int64_t *data, int64_t n, int64_t *total, int64_t *scratch,
                             int64_t scratch_elems, cudaStream_t s);
@@ -184,9 +197,9 @@ cudaError_t launch_features(int64_t n_rows, const int32_t *rowptr, const int32_t
                             FeatSums *out, cudaStream_t s);
 cudaError_t launch_row_len_max(int64_t n_rows, const int32_t *rowptr, int32_t *out,
                                cudaStream_t s);
-// max over tiles of `tile_rows` rows of the 8-aligned staged element count
-cudaError_t launch_tile_max(int64_t n_rows, const int32_t *rowptr, int tile_rows, int32_t *out,
-                            cudaStream_t s);
+// max over tiles of `tile_rows` rows of the staged element count, aligned to `align`
+cudaError_t launch_tile_max(int64_t n_rows, const int32_t *rowptr, int tile_rows, int align,
+                            int32_t *out, cudaStream_t s);
 
 // Row decomposition tables: per-row counts (medium flag, long flag, chunks) for the scans,
 // then the lists (bin_rows, long rows, their first chunk, chunk table).

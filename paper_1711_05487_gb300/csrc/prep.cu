@@ -142,25 +142,29 @@ cudaError_t launch_convert_values(const void *in, spmv_dtype from, void *out, sp
   return cudaGetLastError();
 }
 
-// --------------------------------------------------------------- delta16 index --------
-// Per row: escape row iff some consecutive column distance exceeds 65535; esc_count[i]
-// is the row's length for escape rows, 0 otherwise (a scan turns it into offsets).
-__global__ void k_delta16_flags(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
-                                int64_t *esc_count) {
+// ------------------------------------------------------------------ delta index --------
+// Per row (a warp each): esc8[i] / esc16[i] = the row's length if some consecutive column
+// distance exceeds 255 / 65535, else 0 (scans turn these into escape offsets and totals).
+__global__ void k_delta_flags(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                              int64_t *esc8, int64_t *esc16) {
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (i >= n_rows) return;
   const int s = rowptr[i], e = rowptr[i + 1];
-  int big = 0;
+  int64_t maxd = 0;
   for (int j = s + 1 + lane; j < e; j += 32)
-    if ((int64_t)colind[j] - (int64_t)colind[j - 1] > 65535) big = 1;
-  big = __any_sync(0xffffffffu, big);
-  if (lane == 0) esc_count[i] = big ? (int64_t)(e - s) : 0;
+    maxd = max(maxd, (int64_t)colind[j] - (int64_t)colind[j - 1]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) maxd = max(maxd, __shfl_xor_sync(0xffffffffu, maxd, off));
+  if (lane == 0) {
+    esc8[i] = maxd > 255 ? (int64_t)(e - s) : 0;
+    esc16[i] = maxd > 65535 ? (int64_t)(e - s) : 0;
+  }
 }
 
-__global__ void k_delta16_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
-                               const int64_t *esc_off, int32_t *dbase, uint16_t *delta,
-                               int32_t *esc) {
+template <typename T>
+__global__ void k_delta_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                             const int64_t *esc_off, int32_t *dbase, T *delta, int32_t *esc) {
   const int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (i >= n_rows) return;
@@ -180,29 +184,35 @@ __global__ void k_delta16_fill(int64_t n_rows, const int32_t *rowptr, const int3
   } else {
     if (lane == 0) dbase[i] = colind[s];
     for (int j = s + lane; j < e; j += 32)
-      delta[j] = (j == s) ? (uint16_t)0 : (uint16_t)(colind[j] - colind[j - 1]);
+      delta[j] = (j == s) ? (T)0 : (T)(colind[j] - colind[j - 1]);
   }
 }
 
-cudaError_t launch_delta16_flags(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
-                                 int64_t *esc_count, cudaStream_t s) {
+cudaError_t launch_delta_flags(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                               int64_t *esc8, int64_t *esc16, cudaStream_t s) {
   if (n_rows == 0) return cudaSuccess;
-  k_delta16_flags<<<blocks_for(n_rows, kT / 32), kT, 0, s>>>(n_rows, rowptr, colind, esc_count);
+  k_delta_flags<<<blocks_for(n_rows, kT / 32), kT, 0, s>>>(n_rows, rowptr, colind, esc8, esc16);
   return cudaGetLastError();
 }
 
-// esc_off has n_rows + 1 entries (exclusive scan of esc_count, total last).
-cudaError_t launch_delta16_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
-                                const int64_t *esc_off, int32_t *dbase, uint16_t *delta,
-                                int32_t *esc, cudaStream_t s) {
+// esc_off has n_rows + 1 entries (exclusive scan of the chosen width's counts, total last).
+cudaError_t launch_delta_fill(int bits, int64_t n_rows, const int32_t *rowptr,
+                              const int32_t *colind, const int64_t *esc_off, int32_t *dbase,
+                              void *delta, int32_t *esc, cudaStream_t s) {
   if (n_rows == 0) return cudaSuccess;
-  k_delta16_fill<<<blocks_for(n_rows, kT / 32), kT, 0, s>>>(n_rows, rowptr, colind, esc_off,
-                                                            dbase, delta, esc);
+  const unsigned g = blocks_for(n_rows, kT / 32);
+  if (bits == 8)
+    k_delta_fill<uint8_t><<<g, kT, 0, s>>>(n_rows, rowptr, colind, esc_off, dbase,
+                                           static_cast<uint8_t *>(delta), esc);
+  else
+    k_delta_fill<uint16_t><<<g, kT, 0, s>>>(n_rows, rowptr, colind, esc_off, dbase,
+                                            static_cast<uint16_t *>(delta), esc);
   return cudaGetLastError();
 }
 
-__global__ void k_delta16_decode(int64_t n_rows, const int32_t *rowptr, const int32_t *dbase,
-                                 const uint16_t *delta, const int32_t *esc, int32_t *colind) {
+template <typename T>
+__global__ void k_delta_decode(int64_t n_rows, const int32_t *rowptr, const int32_t *dbase,
+                               const T *delta, const int32_t *esc, int32_t *colind) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_rows) return;
   const int s = rowptr[i], e = rowptr[i + 1];
@@ -220,11 +230,16 @@ __global__ void k_delta16_decode(int64_t n_rows, const int32_t *rowptr, const in
   }
 }
 
-cudaError_t launch_delta16_decode(int64_t n_rows, const int32_t *rowptr, const int32_t *dbase,
-                                  const uint16_t *delta, const int32_t *esc, int32_t *colind,
-                                  cudaStream_t s) {
+cudaError_t launch_delta_decode(int bits, int64_t n_rows, const int32_t *rowptr,
+                                const int32_t *dbase, const void *delta, const int32_t *esc,
+                                int32_t *colind, cudaStream_t s) {
   if (n_rows == 0) return cudaSuccess;
-  k_delta16_decode<<<blocks_for(n_rows), kT, 0, s>>>(n_rows, rowptr, dbase, delta, esc, colind);
+  if (bits == 8)
+    k_delta_decode<uint8_t><<<blocks_for(n_rows), kT, 0, s>>>(
+        n_rows, rowptr, dbase, static_cast<const uint8_t *>(delta), esc, colind);
+  else
+    k_delta_decode<uint16_t><<<blocks_for(n_rows), kT, 0, s>>>(
+        n_rows, rowptr, dbase, static_cast<const uint16_t *>(delta), esc, colind);
   return cudaGetLastError();
 }
 
@@ -558,29 +573,30 @@ cudaError_t launch_row_len_max(int64_t n_rows, const int32_t *rowptr, int32_t *o
 
 // Staged size of a thread-per-row tile: elements from the tile's first nonzero rounded
 // down to a multiple of 8 to its last nonzero, rounded up to a multiple of 8.
-__global__ void k_tile_max(int64_t n_rows, const int32_t *rowptr, int tile_rows, int32_t *out) {
+__global__ void k_tile_max(int64_t n_rows, const int32_t *rowptr, int tile_rows, int align,
+                           int32_t *out) {
   int m = 0;
   const int64_t n_tiles = (n_rows + tile_rows - 1) / tile_rows;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r0 = t * tile_rows;
     const int64_t r1 = r0 + tile_rows < n_rows ? r0 + tile_rows : n_rows;
-    const int a0 = rowptr[r0] & ~7;
-    m = max(m, ((rowptr[r1] - a0) + 7) & ~7);
+    const int a0 = rowptr[r0] & ~(align - 1);
+    m = max(m, ((rowptr[r1] - a0) + align - 1) & ~(align - 1));
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
   if ((threadIdx.x & 31) == 0) atomicMax(out, m);
 }
 
-cudaError_t launch_tile_max(int64_t n_rows, const int32_t *rowptr, int tile_rows, int32_t *out,
-                            cudaStream_t s) {
+cudaError_t launch_tile_max(int64_t n_rows, const int32_t *rowptr, int tile_rows, int align,
+                            int32_t *out, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int32_t), s);
   if (e != cudaSuccess || n_rows == 0) return e;
   const int64_t n_tiles = (n_rows + tile_rows - 1) / tile_rows;
   unsigned g = blocks_for(n_tiles);
   if (g > 4096u) g = 4096u;
-  k_tile_max<<<g, kT, 0, s>>>(n_rows, rowptr, tile_rows, out);
+  k_tile_max<<<g, kT, 0, s>>>(n_rows, rowptr, tile_rows, align, out);
   return cudaGetLastError();
 }
 

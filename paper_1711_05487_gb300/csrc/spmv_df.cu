@@ -102,17 +102,18 @@ __device__ __forceinline__ void df_prod(uint2 v, uint2 xv, float &p, float &q) {
 
 // Thread-per-row tiles as in the FP64 kernel: a tile's value pairs and column indices are
 // staged in shared memory by one bulk copy each; each thread then walks its row.
-template <bool D16, bool XL2>
+template <int DB, bool XL2>
 __global__ void __launch_bounds__(kTileRows) k_rowtile_df(const RunArgs a) {
-  using IdxT = typename std::conditional<D16, uint16_t, int32_t>::type;
+  using IdxT = typename IdxOf<DB>::type;
+  constexpr int AL = stage_align<DB>();
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   const int rows = (int)blockDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * rows;
   const int64_t r1 = min(r0 + (int64_t)rows, a.n_rows);
   const int s0 = __ldg(a.rowptr + r0), s1 = __ldg(a.rowptr + r1);
-  const int a0 = s0 & ~7;
-  const int nc = ((s1 - a0) + 7) & ~7;
+  const int a0 = s0 & ~(AL - 1);
+  const int nc = ((s1 - a0) + AL - 1) & ~(AL - 1);
   const double *__restrict__ val = static_cast<const double *>(a.val);
   const uint2 *__restrict__ vdf = static_cast<const uint2 *>(a.val_df);
   const double *__restrict__ x = static_cast<const double *>(a.x);
@@ -121,13 +122,13 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_df(const RunArgs a) {
   if constexpr (XL2) pol_x = policy_evict_last();
   const int64_t row = r0 + threadIdx.x;
   if (nc > a.tile_cap) {
-    tile_direct<double, double, double, D16, XL2>(a, r0, r1, x, y, pol_x);
+    tile_direct<double, double, double, DB, XL2>(a, r0, r1, x, y, pol_x);
     return;
   }
   uint2 *sval = reinterpret_cast<uint2 *>(smem + 16);
   IdxT *sidx = reinterpret_cast<IdxT *>(smem + 16 + (size_t)a.tile_cap * sizeof(uint2));
   const IdxT *gidx;
-  if constexpr (D16) gidx = a.delta;
+  if constexpr (DB != 0) gidx = static_cast<const IdxT *>(a.delta);
   else gidx = a.colind;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_df(const RunArgs a) {
   if (row < r1) {
     s = __ldg(a.rowptr + row);
     e = __ldg(a.rowptr + row + 1);
-    if constexpr (D16) base = __ldg(a.dbase + row);
+    if constexpr (DB != 0) base = __ldg(a.dbase + row);
   }
   __syncthreads();
   if (nc > 0) {
@@ -158,12 +159,12 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_df(const RunArgs a) {
   if (row >= r1) return;
   const int o = s - a0, len = e - s;
   const int32_t *ec = nullptr;
-  if constexpr (D16) {
+  if constexpr (DB != 0) {
     if (base < 0) ec = a.esc + (-(int64_t)base - 1);
   }
   int c = base;
   auto column = [&](int k) -> int {
-    if constexpr (D16) {
+    if constexpr (DB != 0) {
       if (ec) return __ldg(ec + k);
       c += (int)sidx[o + k];
       return c;
@@ -203,14 +204,14 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_df(const RunArgs a) {
 
 namespace {
 
-template <bool D16, bool XL2> cudaError_t launch_rowtile_df_k(const RunArgs &a, cudaStream_t s) {
+template <int DB, bool XL2> cudaError_t launch_rowtile_df_k(const RunArgs &a, cudaStream_t s) {
   static int configured = 0;
   const int rows = a.tile_rows > 0 ? a.tile_rows : kTileRows;
-  const size_t smem = 16 + (size_t)a.tile_cap * (8 + (D16 ? 2 : 4));
-  cudaError_t e = ensure_smem(k_rowtile_df<D16, XL2>, smem, configured);
+  const size_t smem = 16 + (size_t)a.tile_cap * (8 + sizeof(typename IdxOf<DB>::type));
+  cudaError_t e = ensure_smem(k_rowtile_df<DB, XL2>, smem, configured);
   if (e != cudaSuccess) return e;
   const unsigned g = (unsigned)((a.n_rows + rows - 1) / rows);
-  k_rowtile_df<D16, XL2><<<g, rows, smem, s>>>(a);
+  k_rowtile_df<DB, XL2><<<g, rows, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -219,9 +220,12 @@ template <bool D16, bool XL2> cudaError_t launch_rowtile_df_k(const RunArgs &a, 
 cudaError_t launch_spmv_df(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
   if (v.partition != 0 || v.vs != 1) return kernel_set_f64_dd()->spmv(v, a, s);
-  const bool d16 = v.index == 1, xl2 = v.xpath != 0;
-  if (d16) return xl2 ? launch_rowtile_df_k<true, true>(a, s) : launch_rowtile_df_k<true, false>(a, s);
-  return xl2 ? launch_rowtile_df_k<false, true>(a, s) : launch_rowtile_df_k<false, false>(a, s);
+  const bool xl2 = v.xpath != 0;
+  if (v.index == 1 && a.delta_bits == 8)
+    return xl2 ? launch_rowtile_df_k<8, true>(a, s) : launch_rowtile_df_k<8, false>(a, s);
+  if (v.index == 1)
+    return xl2 ? launch_rowtile_df_k<16, true>(a, s) : launch_rowtile_df_k<16, false>(a, s);
+  return xl2 ? launch_rowtile_df_k<0, true>(a, s) : launch_rowtile_df_k<0, false>(a, s);
 }
 
 }  // namespace

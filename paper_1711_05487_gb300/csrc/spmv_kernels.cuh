@@ -3,7 +3,7 @@
 //  k_rowvec  - a sub-warp of VS lanes per row (Fig. 1's inner loop spread over lanes);
 //              rows go to CTAs through the hardware block scheduler. Knobs from Table II:
 //              VEC  128-bit loads of val / colind, unrolled (CMP, MB "vectorization"),
-//              D16  16-bit column deltas decoded with a sub-warp prefix sum (MB),
+//              DB   8- or 16-bit column deltas decoded with a sub-warp prefix sum (MB),
 //              XL2  x gathered with an L2 evict-last policy while val / colind stream with
 //                   evict-first (ML: the GPU counterpart of software prefetching into cache).
 //  k_rowtile - thread-per-row tiles staged by TMA bulk copies (spmv_tile.cuh).
@@ -86,17 +86,34 @@ __device__ __forceinline__ SumT esc_range_dot(const RunArgs &a, int s, int e,
   return sum;
 }
 
-// One lane's share over [s, e) with 16-bit column deltas: 8 deltas (16 bytes) per lane per
-// step, the column of element j = running + the deltas of elements s..j (a sub-warp prefix
-// sum), where running is the column the decode starts from (the row's base for a range that
-// starts the row, whose first delta is 0; the preceding element's column otherwise).
-template <typename ValT, typename VecT, typename AccT, int VS, bool XL2, typename SumT = AccT>
-__device__ __forceinline__ SumT d16_range_dot(const RunArgs &a, int s, int e, int running,
-                                              int lane, unsigned mask, uint64_t pol_s,
-                                              uint64_t pol_x) {
+// Eight column deltas of DB (8 or 16) bits starting at element b (a multiple of 8): one
+// 8- or 16-byte load.
+template <int DB>
+__device__ __forceinline__ void load_deltas8(const void *delta, int b, uint64_t pol, int d[8]) {
+  if constexpr (DB == 16) {
+    const uint4 w = ld16<true>(static_cast<const uint16_t *>(delta) + b, pol);
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) d[q] = (q & 1) ? (int)(u[q >> 1] >> 16) : (int)(u[q >> 1] & 0xFFFFu);
+  } else {
+    const uint2 w = ld8<true>(static_cast<const uint8_t *>(delta) + b, pol);
+    const uint32_t u[2] = {w.x, w.y};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) d[q] = (int)((u[q >> 2] >> (8 * (q & 3))) & 0xFFu);
+  }
+}
+
+// One lane's share over [s, e) with DB-bit column deltas: 8 deltas per lane per step, the
+// column of element j = running + the deltas of elements s..j (a sub-warp prefix sum), where
+// running is the column the decode starts from (the row's base for a range that starts the
+// row, whose first delta is 0; the preceding element's column otherwise).
+template <typename ValT, typename VecT, typename AccT, int VS, int DB, bool XL2,
+          typename SumT = AccT>
+__device__ __forceinline__ SumT delta_range_dot(const RunArgs &a, int s, int e, int running,
+                                                int lane, unsigned mask, uint64_t pol_s,
+                                                uint64_t pol_x) {
   const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
   const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
-  const uint16_t *__restrict__ dl = a.delta;
   SumT sum = 0;
   const int a0 = s & ~7;
   const int n_it = (e - a0 + VS * 8 - 1) / (VS * 8);
@@ -105,22 +122,21 @@ __device__ __forceinline__ SumT d16_range_dot(const RunArgs &a, int s, int e, in
     // lanes whose 8 elements start past the range end load nothing (reads stay below
     // e + 8, inside the arrays' slack)
     const bool live = b < e;
-    const uint4 d4 = live ? ld16<true>(dl + b, pol_s) : make_uint4(0u, 0u, 0u, 0u);
+    int dd[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     AccT v[8];
     if (live) {
+      load_deltas8<DB>(a.delta, b, pol_s, dd);
       VLoad<AccT, true, 8>::run(val + b, v, pol_s);
     } else {
 #pragma unroll
       for (int q = 0; q < 8; ++q) v[q] = (AccT)0;
     }
-    const uint32_t w[4] = {d4.x, d4.y, d4.z, d4.w};
     int p[8];
     int acc = 0;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int j = b + q;
-      int d = (q & 1) ? (int)(w[q >> 1] >> 16) : (int)(w[q >> 1] & 0xFFFFu);
-      d = (j >= s && j < e) ? d : 0;
+      const int d = (j >= s && j < e) ? dd[q] : 0;
       acc += d;
       p[q] = acc;
     }
@@ -154,7 +170,7 @@ __device__ __forceinline__ SumT d16_range_dot(const RunArgs &a, int s, int e, in
 }
 
 // ------------------------------------------------------------------------ k_rowvec ----
-template <typename ValT, typename VecT, typename AccT, int VS, bool VEC, bool D16, bool XL2>
+template <typename ValT, typename VecT, typename AccT, int VS, bool VEC, int DB, bool XL2>
 __global__ void __launch_bounds__(kRowThreads) k_rowvec(const RunArgs a) {
   constexpr int GROUPS = kRowThreads / VS;
   const int lane = threadIdx.x & (VS - 1);
@@ -172,7 +188,7 @@ __global__ void __launch_bounds__(kRowThreads) k_rowvec(const RunArgs a) {
     const int32_t *__restrict__ col = a.colind;
     for (int j = s + lane; j < e; j += VS)
       sum += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(col + j), pol_x);
-  } else if constexpr (!D16) {
+  } else if constexpr (DB == 0) {
     sum = vec_range_dot<ValT, VecT, AccT, VS, XL2>(a, s, e, lane, pol_s, pol_x);
   } else {
     const int32_t base = __ldg(a.dbase + row);
@@ -180,7 +196,8 @@ __global__ void __launch_bounds__(kRowThreads) k_rowvec(const RunArgs a) {
       sum = esc_range_dot<ValT, VecT, AccT, VS, XL2>(a, s, e, a.esc + (-(int64_t)base - 1),
                                                      lane, pol_x);
     else
-      sum = d16_range_dot<ValT, VecT, AccT, VS, XL2>(a, s, e, base, lane, mask, pol_s, pol_x);
+      sum = delta_range_dot<ValT, VecT, AccT, VS, DB, XL2>(a, s, e, base, lane, mask, pol_s,
+                                                           pol_x);
   }
   sum = group_sum<VS>(sum, mask);
   if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)sum;
@@ -478,27 +495,27 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm(const RunArgs a, int off, 
 //                  of a long row whose sum goes to an FP64 partial slot; the lanes add
 //                  their steps' sums in FP64 (FP32 accumulation stays within 4 products);
 //  k_bins_fixup  - each long row's partials added in chunk order (reproducible, no atomics).
-// One sub-warp's share of elements [s, e) of row `row`, whose decode (delta16 columns)
-// starts from column `running`.
-template <typename ValT, typename VecT, typename AccT, int VS, bool D16, bool XL2, typename SumT>
+// One sub-warp's share of elements [s, e) of row `row`, whose decode (delta columns of DB
+// bits) starts from column `running`.
+template <typename ValT, typename VecT, typename AccT, int VS, int DB, bool XL2, typename SumT>
 __device__ __forceinline__ SumT bins_range_dot(const RunArgs &a, int64_t row, int s, int e,
                                                int running, int lane, uint64_t pol_s,
                                                uint64_t pol_x) {
-  if constexpr (D16) {
+  if constexpr (DB != 0) {
     const int32_t base = __ldg(a.dbase + row);
     if (base < 0) {
       const int rs = __ldg(a.rowptr + row);
       return esc_range_dot<ValT, VecT, AccT, VS, XL2, SumT>(
           a, s, e, a.esc + (-(int64_t)base - 1) + (s - rs), lane, pol_x);
     }
-    return d16_range_dot<ValT, VecT, AccT, VS, XL2, SumT>(a, s, e, running, lane,
-                                                          group_mask<VS>(), pol_s, pol_x);
+    return delta_range_dot<ValT, VecT, AccT, VS, DB, XL2, SumT>(a, s, e, running, lane,
+                                                                group_mask<VS>(), pol_s, pol_x);
   } else {
     return vec_range_dot<ValT, VecT, AccT, VS, XL2, SumT>(a, s, e, lane, pol_s, pol_x);
   }
 }
 
-template <typename ValT, typename VecT, typename AccT, int VS, bool D16, bool XL2>
+template <typename ValT, typename VecT, typename AccT, int VS, int DB, bool XL2>
 __global__ void __launch_bounds__(kRowThreads) k_bins_short(const RunArgs a) {
   constexpr int GROUPS = kRowThreads / VS;
   const int lane = threadIdx.x & (VS - 1);
@@ -508,14 +525,14 @@ __global__ void __launch_bounds__(kRowThreads) k_bins_short(const RunArgs a) {
   if (e - s >= a.bin_l_med) return;
   uint64_t pol_s = policy_evict_first(), pol_x = 0;
   if constexpr (XL2) pol_x = policy_evict_last();
-  const int running = D16 ? __ldg(a.dbase + row) : 0;
-  AccT sum = bins_range_dot<ValT, VecT, AccT, VS, D16, XL2, AccT>(a, row, s, e, running, lane,
+  const int running = DB != 0 ? __ldg(a.dbase + row) : 0;
+  AccT sum = bins_range_dot<ValT, VecT, AccT, VS, DB, XL2, AccT>(a, row, s, e, running, lane,
                                                                   pol_s, pol_x);
   sum = group_sum<VS>(sum, group_mask<VS>());
   if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)sum;
 }
 
-template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2>
+template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
 __global__ void __launch_bounds__(kRowThreads) k_bins_warp(const RunArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t item = ((int64_t)blockIdx.x * kRowThreads + threadIdx.x) / 32;
@@ -525,15 +542,15 @@ __global__ void __launch_bounds__(kRowThreads) k_bins_warp(const RunArgs a) {
   if (item < a.bin_n_chunks) {
     // (row, first nonzero, end nonzero, the column the delta decode starts from)
     const int4 c = a.bin_chunks[item];
-    const double sum = bins_range_dot<ValT, VecT, AccT, 32, D16, XL2, double>(
+    const double sum = bins_range_dot<ValT, VecT, AccT, 32, DB, XL2, double>(
         a, c.x, c.y, c.z, c.w, lane, pol_s, pol_x);
     const double t = group_sum<32>(sum, 0xffffffffu);
     if (lane == 0) a.bin_partials[item] = t;
   } else {
     const int row = __ldg(a.bin_rows + (item - a.bin_n_chunks));
     const int s = __ldg(a.rowptr + row), e = __ldg(a.rowptr + row + 1);
-    const int running = D16 ? __ldg(a.dbase + row) : 0;
-    double sum = bins_range_dot<ValT, VecT, AccT, 32, D16, XL2, double>(a, row, s, e, running,
+    const int running = DB != 0 ? __ldg(a.dbase + row) : 0;
+    double sum = bins_range_dot<ValT, VecT, AccT, 32, DB, XL2, double>(a, row, s, e, running,
                                                                         lane, pol_s, pol_x);
     sum = group_sum<32>(sum, 0xffffffffu);
     if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)sum;
@@ -549,32 +566,35 @@ __global__ void k_bins_fixup(const RunArgs a) {
   static_cast<VecT *>(a.y)[a.bin_long_rows[i]] = (VecT)t;
 }
 
-template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2>
+template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
 void launch_bins_k(const RunArgs &a, cudaStream_t s) {
   switch (a.bin_vs_short) {
-    case 2: k_bins_short<ValT, VecT, AccT, 2, D16, XL2><<<(unsigned)((a.n_rows + 127) / 128),
+    case 2: k_bins_short<ValT, VecT, AccT, 2, DB, XL2><<<(unsigned)((a.n_rows + 127) / 128),
                                                          kRowThreads, 0, s>>>(a); break;
-    case 8: k_bins_short<ValT, VecT, AccT, 8, D16, XL2><<<(unsigned)((a.n_rows + 31) / 32),
+    case 8: k_bins_short<ValT, VecT, AccT, 8, DB, XL2><<<(unsigned)((a.n_rows + 31) / 32),
                                                          kRowThreads, 0, s>>>(a); break;
-    default: k_bins_short<ValT, VecT, AccT, 4, D16, XL2><<<(unsigned)((a.n_rows + 63) / 64),
+    default: k_bins_short<ValT, VecT, AccT, 4, DB, XL2><<<(unsigned)((a.n_rows + 63) / 64),
                                                           kRowThreads, 0, s>>>(a); break;
   }
   const int64_t items = a.bin_n_med + a.bin_n_chunks;
   if (items > 0) {
     const unsigned g = (unsigned)((items * 32 + kRowThreads - 1) / kRowThreads);
-    k_bins_warp<ValT, VecT, AccT, D16, XL2><<<g, kRowThreads, 0, s>>>(a);
+    k_bins_warp<ValT, VecT, AccT, DB, XL2><<<g, kRowThreads, 0, s>>>(a);
   }
 }
 
 template <typename ValT, typename VecT, typename AccT>
-cudaError_t launch_bins(bool d16, bool xl2, const RunArgs &a, cudaStream_t s) {
+cudaError_t launch_bins(int db, bool xl2, const RunArgs &a, cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
-  if (d16) {
-    if (xl2) launch_bins_k<ValT, VecT, AccT, true, true>(a, s);
-    else launch_bins_k<ValT, VecT, AccT, true, false>(a, s);
+  if (db == 16) {
+    if (xl2) launch_bins_k<ValT, VecT, AccT, 16, true>(a, s);
+    else launch_bins_k<ValT, VecT, AccT, 16, false>(a, s);
+  } else if (db == 8) {
+    if (xl2) launch_bins_k<ValT, VecT, AccT, 8, true>(a, s);
+    else launch_bins_k<ValT, VecT, AccT, 8, false>(a, s);
   } else {
-    if (xl2) launch_bins_k<ValT, VecT, AccT, false, true>(a, s);
-    else launch_bins_k<ValT, VecT, AccT, false, false>(a, s);
+    if (xl2) launch_bins_k<ValT, VecT, AccT, 0, true>(a, s);
+    else launch_bins_k<ValT, VecT, AccT, 0, false>(a, s);
   }
   if (a.bin_n_long > 0)
     k_bins_fixup<VecT><<<(unsigned)((a.bin_n_long + 255) / 256), 256, 0, s>>>(a);
@@ -590,16 +610,19 @@ inline unsigned grid_for_rows(int64_t n_rows, int vs) {
 template <typename ValT, typename VecT, typename AccT, int VS>
 cudaError_t launch_rowvec_vs(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
   const unsigned g = grid_for_rows(a.n_rows, VS);
-  const bool d16 = v.index == 1, vec = v.vec != 0 || d16, xl2 = v.xpath != 0;
+  const bool dl = v.index == 1, vec = v.vec != 0 || dl, xl2 = v.xpath != 0;
   if (!vec) {
-    if (xl2) k_rowvec<ValT, VecT, AccT, VS, false, false, true><<<g, kRowThreads, 0, s>>>(a);
-    else k_rowvec<ValT, VecT, AccT, VS, false, false, false><<<g, kRowThreads, 0, s>>>(a);
-  } else if (!d16) {
-    if (xl2) k_rowvec<ValT, VecT, AccT, VS, true, false, true><<<g, kRowThreads, 0, s>>>(a);
-    else k_rowvec<ValT, VecT, AccT, VS, true, false, false><<<g, kRowThreads, 0, s>>>(a);
+    if (xl2) k_rowvec<ValT, VecT, AccT, VS, false, 0, true><<<g, kRowThreads, 0, s>>>(a);
+    else k_rowvec<ValT, VecT, AccT, VS, false, 0, false><<<g, kRowThreads, 0, s>>>(a);
+  } else if (!dl) {
+    if (xl2) k_rowvec<ValT, VecT, AccT, VS, true, 0, true><<<g, kRowThreads, 0, s>>>(a);
+    else k_rowvec<ValT, VecT, AccT, VS, true, 0, false><<<g, kRowThreads, 0, s>>>(a);
+  } else if (a.delta_bits == 8) {
+    if (xl2) k_rowvec<ValT, VecT, AccT, VS, true, 8, true><<<g, kRowThreads, 0, s>>>(a);
+    else k_rowvec<ValT, VecT, AccT, VS, true, 8, false><<<g, kRowThreads, 0, s>>>(a);
   } else {
-    if (xl2) k_rowvec<ValT, VecT, AccT, VS, true, true, true><<<g, kRowThreads, 0, s>>>(a);
-    else k_rowvec<ValT, VecT, AccT, VS, true, true, false><<<g, kRowThreads, 0, s>>>(a);
+    if (xl2) k_rowvec<ValT, VecT, AccT, VS, true, 16, true><<<g, kRowThreads, 0, s>>>(a);
+    else k_rowvec<ValT, VecT, AccT, VS, true, 16, false><<<g, kRowThreads, 0, s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -607,7 +630,8 @@ cudaError_t launch_rowvec_vs(const spmv_variant &v, const RunArgs &a, cudaStream
 template <typename ValT, typename VecT, typename AccT>
 cudaError_t launch_spmv_impl(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
-  if (v.partition == 2) return launch_bins<ValT, VecT, AccT>(v.index == 1, v.xpath != 0, a, s);
+  if (v.partition == 2)
+    return launch_bins<ValT, VecT, AccT>(v.index == 1 ? a.delta_bits : 0, v.xpath != 0, a, s);
   if (v.partition == 1) {
     if (a.n_tiles == 0) return cudaSuccess;
     if (v.xpath) k_merge<ValT, VecT, AccT, true><<<(unsigned)a.n_tiles, kMergeThreads, 0, s>>>(a);

@@ -32,7 +32,7 @@ __host__ __device__ constexpr int tile_elem_bytes() {
 // Dot product of one row whose values and columns sit in shared memory at offset o (the
 // row's first element) of a staged tile: 8 gathers of x in flight per thread, then 8 FMAs;
 // the exact trip count keeps the FP64 pipe free of masked-off work.
-template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2, typename IdxT>
+template <typename ValT, typename VecT, typename AccT, int DB, bool XL2, typename IdxT>
 __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
                                              const IdxT *sidx, int o, int len, int32_t base,
                                              const VecT *__restrict__ x, uint64_t pol_x) {
@@ -41,11 +41,11 @@ __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
   // from the row's base column, or (escape rows) the full column kept in global memory.
   const int32_t *ec = nullptr;
   int c = base;
-  if constexpr (D16) {
+  if constexpr (DB != 0) {
     if (base < 0) ec = a.esc + (-(int64_t)base - 1);
   }
   auto column = [&](int k) -> int {
-    if constexpr (D16) {
+    if constexpr (DB != 0) {
       if (ec) return __ldg(ec + k);
       c += (int)sidx[o + k];
       return c;
@@ -67,7 +67,7 @@ __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
 
 // Rows [r0, r1) straight from global memory, a warp per row (tiles larger than the staged
 // capacity).
-template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2>
+template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
 __device__ __forceinline__ void tile_direct(const RunArgs &a, int64_t r0, int64_t r1,
                                             const VecT *__restrict__ x, VecT *__restrict__ y,
                                             uint64_t pol_x) {
@@ -76,7 +76,7 @@ __device__ __forceinline__ void tile_direct(const RunArgs &a, int64_t r0, int64_
   for (int64_t r = r0 + warp; r < r1; r += blockDim.x / 32) {
     const int s = __ldg(a.rowptr + r), e = __ldg(a.rowptr + r + 1);
     AccT acc = 0;
-    if constexpr (D16) {
+    if constexpr (DB != 0) {
       const int32_t base = __ldg(a.dbase + r);
       if (base < 0) {
         const int32_t *ec = a.esc + (-(int64_t)base - 1) - s;
@@ -84,10 +84,12 @@ __device__ __forceinline__ void tile_direct(const RunArgs &a, int64_t r0, int64_
           acc += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(ec + j), pol_x);
       } else {
         // decode the row's deltas: the lane sums its own and its predecessors' deltas
+        using DT = typename IdxOf<DB>::type;
+        const DT *__restrict__ dl = static_cast<const DT *>(a.delta);
         int run = base;
         for (int j0 = s; j0 < e; j0 += 32) {
           const int j = j0 + lane;
-          const int d = j < e ? (int)a.delta[j] : 0;
+          const int d = j < e ? (int)dl[j] : 0;
           const int incl = group_incl_scan<32>(d, lane, 0xffffffffu);
           if (j < e) acc += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + (run + incl), pol_x);
           run += __shfl_sync(0xffffffffu, incl, 31);
@@ -102,17 +104,18 @@ __device__ __forceinline__ void tile_direct(const RunArgs &a, int64_t r0, int64_
   }
 }
 
-template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2>
+template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
 __global__ void __launch_bounds__(kTileRows) k_rowtile(const RunArgs a) {
-  using IdxT = typename std::conditional<D16, uint16_t, int32_t>::type;
+  using IdxT = typename IdxOf<DB>::type;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   const int rows = (int)blockDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * rows;
   const int64_t r1 = min(r0 + (int64_t)rows, a.n_rows);
   const int s0 = __ldg(a.rowptr + r0), s1 = __ldg(a.rowptr + r1);
-  const int a0 = s0 & ~7;                        // 8-element (>= 16-byte) aligned start
-  const int nc = ((s1 - a0) + 7) & ~7;           // staged elements
+  constexpr int AL = stage_align<DB>();
+  const int a0 = s0 & ~(AL - 1);                 // aligned start: the copies are 16-byte units
+  const int nc = ((s1 - a0) + AL - 1) & ~(AL - 1);   // staged elements
   const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
   const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
   VecT *__restrict__ y = static_cast<VecT *>(a.y);
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile(const RunArgs a) {
     ValT *sval = reinterpret_cast<ValT *>(smem + 16);
     IdxT *sidx = reinterpret_cast<IdxT *>(smem + 16 + (size_t)a.tile_cap * sizeof(ValT));
     const IdxT *gidx;
-    if constexpr (D16) gidx = a.delta;
+    if constexpr (DB != 0) gidx = static_cast<const IdxT *>(a.delta);
     else gidx = a.colind;
     if (threadIdx.x == 0) {
       mbar_init(bar, 1);
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile(const RunArgs a) {
     if (row < r1) {
       s = __ldg(a.rowptr + row);
       e = __ldg(a.rowptr + row + 1);
-      if constexpr (D16) base = __ldg(a.dbase + row);
+      if constexpr (DB != 0) base = __ldg(a.dbase + row);
     }
     __syncthreads();   // the barrier is initialised before anyone waits on it
     if (nc > 0) {
@@ -153,11 +156,11 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile(const RunArgs a) {
       }
     }
     if (row >= r1) return;
-    y[row] = (VecT)tile_row_dot<ValT, VecT, AccT, D16, XL2>(a, sval, sidx, s - a0, e - s, base,
+    y[row] = (VecT)tile_row_dot<ValT, VecT, AccT, DB, XL2>(a, sval, sidx, s - a0, e - s, base,
                                                            x, pol_x);
   } else {
     // oversize tile: a warp per row straight from global memory
-    tile_direct<ValT, VecT, AccT, D16, XL2>(a, r0, r1, x, y, pol_x);
+    tile_direct<ValT, VecT, AccT, DB, XL2>(a, r0, r1, x, y, pol_x);
   }
 }
 
@@ -166,9 +169,9 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile(const RunArgs a) {
 // blockIdx.x + gridDim.x, ... with two shared-memory stages, so that the bulk copy of its
 // next tile is in flight while it computes the current one. Stage s is refilled only after
 // all threads passed the barrier that ends their reads of it.
-template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2>
+template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
 __global__ void __launch_bounds__(kTileRows) k_rowtile_pipe(const RunArgs a) {
-  using IdxT = typename std::conditional<D16, uint16_t, int32_t>::type;
+  using IdxT = typename IdxOf<DB>::type;
   constexpr int S = 2;
   extern __shared__ __align__(16) unsigned char smem[];   // S mbarriers 16 B apart, then stages
   const int rows = (int)blockDim.x;
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_pipe(const RunArgs a) {
   const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
   VecT *__restrict__ y = static_cast<VecT *>(a.y);
   const IdxT *gidx;
-  if constexpr (D16) gidx = a.delta;
+  if constexpr (DB != 0) gidx = static_cast<const IdxT *>(a.delta);
   else gidx = a.colind;
   uint64_t pol_x = 0;
   if constexpr (XL2) pol_x = policy_evict_last();
@@ -188,8 +191,9 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_pipe(const RunArgs a) {
     r0 = t * rows;
     r1 = min(r0 + (int64_t)rows, a.n_rows);
     const int s0 = __ldg(a.rowptr + r0), s1 = __ldg(a.rowptr + r1);
-    a0 = s0 & ~7;
-    nc = ((s1 - a0) + 7) & ~7;
+    constexpr int AL = stage_align<DB>();
+    a0 = s0 & ~(AL - 1);
+    nc = ((s1 - a0) + AL - 1) & ~(AL - 1);
   };
   auto issue = [&](int64_t t, int st) {   // one thread
     int64_t r0, r1;
@@ -230,7 +234,7 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_pipe(const RunArgs a) {
     if (row < r1) {
       s = __ldg(a.rowptr + row);
       e = __ldg(a.rowptr + row + 1);
-      if constexpr (D16) base = __ldg(a.dbase + row);
+      if constexpr (DB != 0) base = __ldg(a.dbase + row);
     }
     uint64_t *b = reinterpret_cast<uint64_t *>(smem + 16 * st);
     const bool ok = mbar_wait_bounded(b, parity, kWaitLimitNs);
@@ -249,10 +253,10 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_pipe(const RunArgs a) {
       const ValT *sval = reinterpret_cast<const ValT *>(stage0 + (size_t)st * stage_bytes);
       const IdxT *sidx = reinterpret_cast<const IdxT *>(stage0 + (size_t)st * stage_bytes + vbytes);
       if (row < r1)
-        y[row] = (VecT)tile_row_dot<ValT, VecT, AccT, D16, XL2>(a, sval, sidx, s - a0, e - s,
+        y[row] = (VecT)tile_row_dot<ValT, VecT, AccT, DB, XL2>(a, sval, sidx, s - a0, e - s,
                                                                base, x, pol_x);
     } else {
-      tile_direct<ValT, VecT, AccT, D16, XL2>(a, r0, r1, x, y, pol_x);
+      tile_direct<ValT, VecT, AccT, DB, XL2>(a, r0, r1, x, y, pol_x);
     }
     __syncthreads();                       // every thread is done with stage st
     if (threadIdx.x == 0) {
@@ -273,14 +277,14 @@ cudaError_t ensure_smem(K kernel, size_t smem, int &configured) {
   return cudaSuccess;
 }
 
-template <typename ValT, typename VecT, typename AccT, bool D16, bool XL2>
+template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
 cudaError_t launch_rowtile_k(const RunArgs &a, cudaStream_t s) {
-  using IdxT = typename std::conditional<D16, uint16_t, int32_t>::type;
+  using IdxT = typename IdxOf<DB>::type;
   const int rows = a.tile_rows > 0 ? a.tile_rows : kTileRows;
   const size_t per_stage = (size_t)a.tile_cap * (sizeof(ValT) + sizeof(IdxT));
   if (a.tile_pipe) {
     static int configured = 0;
-    auto kern = k_rowtile_pipe<ValT, VecT, AccT, D16, XL2>;
+    auto kern = k_rowtile_pipe<ValT, VecT, AccT, DB, XL2>;
     const size_t smem = 32 + 2 * per_stage;
     cudaError_t e = ensure_smem(kern, smem, configured);
     if (e != cudaSuccess) return e;
@@ -296,20 +300,24 @@ cudaError_t launch_rowtile_k(const RunArgs &a, cudaStream_t s) {
   }
   static int configured = 0;
   const size_t smem = 16 + per_stage;
-  cudaError_t e = ensure_smem(k_rowtile<ValT, VecT, AccT, D16, XL2>, smem, configured);
+  cudaError_t e = ensure_smem(k_rowtile<ValT, VecT, AccT, DB, XL2>, smem, configured);
   if (e != cudaSuccess) return e;
   const unsigned g = (unsigned)((a.n_rows + rows - 1) / rows);
-  k_rowtile<ValT, VecT, AccT, D16, XL2><<<g, rows, smem, s>>>(a);
+  k_rowtile<ValT, VecT, AccT, DB, XL2><<<g, rows, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <typename ValT, typename VecT, typename AccT>
 cudaError_t launch_rowtile(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
-  const bool d16 = v.index == 1, xl2 = v.xpath != 0;
-  if (d16) return xl2 ? launch_rowtile_k<ValT, VecT, AccT, true, true>(a, s)
-                      : launch_rowtile_k<ValT, VecT, AccT, true, false>(a, s);
-  return xl2 ? launch_rowtile_k<ValT, VecT, AccT, false, true>(a, s)
-             : launch_rowtile_k<ValT, VecT, AccT, false, false>(a, s);
+  const bool xl2 = v.xpath != 0;
+  if (v.index == 1 && a.delta_bits == 8)
+    return xl2 ? launch_rowtile_k<ValT, VecT, AccT, 8, true>(a, s)
+               : launch_rowtile_k<ValT, VecT, AccT, 8, false>(a, s);
+  if (v.index == 1)
+    return xl2 ? launch_rowtile_k<ValT, VecT, AccT, 16, true>(a, s)
+               : launch_rowtile_k<ValT, VecT, AccT, 16, false>(a, s);
+  return xl2 ? launch_rowtile_k<ValT, VecT, AccT, 0, true>(a, s)
+             : launch_rowtile_k<ValT, VecT, AccT, 0, false>(a, s);
 }
 
 }  // namespace spmv

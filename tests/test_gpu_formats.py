@@ -29,6 +29,8 @@ def abi(torch):
 
 FORMAT_MATS = {
     "st27_14": lambda: synth.stencil_27pt(14),
+    "lap2d_200": lambda: synth.laplacian_2d(200),                       # 8-bit deltas
+    "banded_narrow": lambda: synth.banded(20_000, 60, 0.3, seed=25),     # 8-bit deltas
     "scattered_escape": lambda: synth.scattered(300_000, 4, seed=21),
     "powerlaw": lambda: synth.power_law(50_000, seed=22, dtype=np.float64),
     "ragged_empty": lambda: synth.uniform_random(7001, 80, seed=23, min_per_row=0),
@@ -38,14 +40,18 @@ FORMAT_MATS = {
 
 
 @pytest.mark.parametrize("name", list(FORMAT_MATS))
-def test_delta16_bit_exact_and_round_trip(api, name):
+def test_delta_index_bit_exact_and_round_trip(api, name):
+    """The width (8 or 16 bits, one per matrix) and the index equal the oracle's; the CSR
+    exported from the index equals the input."""
     m = FORMAT_MATS[name]()
     A = api.SpmvMatrix.from_csr(m)
     A.set_variant(index=1, vec=1)
-    base, delta, esc = A.delta16()
-    ob, od, oe = oracle.delta16_encode(m.rowptr, m.colind)
+    base, delta, esc, bits = A.delta()
+    assert bits == oracle.delta_width(m.rowptr, m.colind)
+    enc = oracle.delta8_encode if bits == 8 else oracle.delta16_encode
+    ob, od, oe = enc(m.rowptr, m.colind)
     assert np.array_equal(base.cpu().numpy(), ob)
-    assert np.array_equal(delta.cpu().numpy().view(np.uint16), od)
+    assert np.array_equal(delta.cpu().numpy().view(np.uint8 if bits == 8 else np.uint16), od)
     assert np.array_equal(esc.cpu().numpy(), oe)
     rp, ci, v = A.export_csr()
     assert np.array_equal(rp.cpu().numpy(), m.rowptr)
@@ -162,3 +168,12 @@ def test_features_bit_exact(api, torch, name, vec):
                              ws_bytes=ws, llc_bytes=l2)
     assert np.array_equal(f.view(np.uint64), of.view(np.uint64)), (f, of)
     assert np.array_equal(isum, oi)
+
+
+def test_delta_widths_cover_both_cases():
+    """The matrices above exercise both widths: 8 bits where every gap is at most 255 (the
+    14^3 stencil's plane gap is 196), 16 bits where the plane gap is larger."""
+    widths = {name: oracle.delta_width(m.rowptr, m.colind)
+              for name, m in ((n, g()) for n, g in FORMAT_MATS.items())}
+    assert widths["lap2d_200"] == 8 and widths["st27_14"] == 8
+    assert widths["banded_wide"] == 16 and widths["scattered_escape"] == 16

@@ -33,6 +33,8 @@ def _matrices():
         "one_long_row": synth.uniform_random(1, 9000, seed=11, min_per_row=9000, n_cols=20_000),
         "rect_wide": synth.uniform_random(700, 40, seed=12, n_cols=50_000),
         "rect_tall": synth.uniform_random(5000, 6, seed=13, n_cols=300),
+        "lap2d_8bit": synth.laplacian_2d(150, 170),          # 8-bit deltas
+        "banded_8bit": synth.banded(9000, 50, 0.4, seed=26),  # 8-bit deltas, ragged rows
     }
 
 
