@@ -187,6 +187,9 @@ def run_ours(args, rank, world):
         A.set_precision("f32", "f32", "f32", stream=stream)
     elif args.precision == "df64":
         A.set_precision("df64", "f64", "df64", stream=stream)
+    elif args.precision in ("f32", "bf16"):
+        A.set_precision(args.precision, "f32", "f32", stream=stream)
+        vec_t = torch.float32
     x = torch.from_numpy(x_host).to(vec_t).cuda()
     y = torch.empty(m.n_rows, dtype=vec_t, device="cuda")
     flops = 2.0 * m.nnz
@@ -236,7 +239,8 @@ def run_ours(args, rank, world):
     ms = timed(args.steps, args.warmup, tag="bench_timed")
     clocks.stop()
     storage = A.storage
-    traffic = measured_traffic(args.workload + ("/df64" if storage == 3 else ""), rep.variant)
+    traffic = measured_traffic(args.workload + ("" if args.precision == "native"
+                                                 else "/" + args.precision), rep.variant)
     ab = alg_bytes(m.n_rows, m.n_cols, m.nnz, rep.variant, storage, A.vec)
     achieved = ab / (ms * 1e-3) / 1e9
     csr_bytes = alg_bytes(m.n_rows, m.n_cols, m.nnz, (0, 0, 0, 0, 0), storage, A.vec)
@@ -632,9 +636,10 @@ def main():
     ap.add_argument("--batch-count", type=int, default=512,
                     help="matrices in the batched workload (512; fewer for profiling)")
     ap.add_argument("--quick", action="store_true", help="skip the precision variants")
-    ap.add_argument("--precision", choices=["native", "df64"], default="native",
-                    help="FP64 workloads: native FP64 arithmetic, or double-float (df64) "
-                         "storage and arithmetic for the timed line")
+    ap.add_argument("--precision", choices=["native", "df64", "f32", "bf16"], default="native",
+                    help="FP64 workloads: native FP64 arithmetic, double-float (df64) storage "
+                         "and arithmetic, or FP32 / BF16 value storage with FP32 x and "
+                         "accumulation, for the timed line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fixed-variant", default=None,
                     help="install this variant instead of tuning: partition,index,xpath,vec,"

@@ -32,8 +32,8 @@ constexpr int kRowThreads = 256;
 // One lane's share of sum_{j in [s, e)} val[j] x[colind[j]] for a sub-warp of VS lanes: 4
 // elements per lane per step, colind as one 16-byte load and val as 8..32 bytes (the chunks
 // start at s rounded down to 4 elements; elements outside [s, e) are masked off). With a
-// wider SumT than AccT (FP32 accumulation over a long-row chunk), each step's four products
-// are summed in AccT and the step sums in SumT.
+// wider SumT than AccT (FP32 accumulation over a long range), runs of 16 products (four
+// steps) are summed in AccT and the run sums in SumT: within the FP32 bound, (16 + 1) u.
 template <typename ValT, typename VecT, typename AccT, int VS, bool XL2, typename SumT = AccT>
 __device__ __forceinline__ SumT vec_range_dot(const RunArgs &a, int s, int e, int lane,
                                               uint64_t pol_s, uint64_t pol_x) {
@@ -41,6 +41,8 @@ __device__ __forceinline__ SumT vec_range_dot(const RunArgs &a, int s, int e, in
   const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
   const int32_t *__restrict__ col = a.colind;
   SumT sum = 0;
+  AccT part = 0;
+  int steps = 0;
   const int a0 = s & ~3;
 #pragma unroll 2
   for (int b = a0 + lane * 4; b < e; b += VS * 4) {
@@ -61,15 +63,19 @@ __device__ __forceinline__ SumT vec_range_dot(const RunArgs &a, int s, int e, in
         if (j >= s && j < e) sum += v[q] * xv[q];
       }
     } else {
-      AccT part = 0;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int j = b + q;
         if (j >= s && j < e) part += v[q] * xv[q];
       }
-      sum += (SumT)part;
+      if (++steps == 4) {
+        sum += (SumT)part;
+        part = 0;
+        steps = 0;
+      }
     }
   }
+  if constexpr (!std::is_same<SumT, AccT>::value) sum += (SumT)part;
   return sum;
 }
 
@@ -115,6 +121,7 @@ __device__ __forceinline__ SumT delta_range_dot(const RunArgs &a, int s, int e, 
   const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
   const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
   SumT sum = 0;
+  AccT part = 0;
   const int a0 = s & ~7;
   const int n_it = (e - a0 + VS * 8 - 1) / (VS * 8);
   for (int it = 0; it < n_it; ++it) {
@@ -156,16 +163,19 @@ __device__ __forceinline__ SumT delta_range_dot(const RunArgs &a, int s, int e, 
         if (j >= s && j < e) sum += v[q] * xv[q];
       }
     } else {
-      AccT part = 0;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int j = b + q;
         if (j >= s && j < e) part += v[q] * xv[q];
       }
-      sum += (SumT)part;
+      if (it & 1) {           // runs of 16 products (two steps) summed in AccT
+        sum += (SumT)part;
+        part = 0;
+      }
     }
     running += tot;
   }
+  if constexpr (!std::is_same<SumT, AccT>::value) sum += (SumT)part;
   return sum;
 }
 
@@ -493,7 +503,7 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm(const RunArgs a, int off, 
 //  k_bins_warp   - one warp per work item: a medium row (l_med <= length < kBinChunk, from
 //                  the row list) written directly, or a chunk of at most kBinChunk nonzeros
 //                  of a long row whose sum goes to an FP64 partial slot; the lanes add
-//                  their steps' sums in FP64 (FP32 accumulation stays within 4 products);
+//                  runs of 16 products in FP64 (FP32 accumulation stays within 16);
 //  k_bins_fixup  - each long row's partials added in chunk order (reproducible, no atomics).
 // One sub-warp's share of elements [s, e) of row `row`, whose decode (delta columns of DB
 // bits) starts from column `running`.
