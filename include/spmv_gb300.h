@@ -97,7 +97,7 @@ typedef struct {
   double t_mb;           /* "P_CSR close to P_MB" read as P_CSR/P_MB >= t_mb, default 0.75 */
   double long_row_ratio; /* IMB sub-choice: nnz_max > ratio * nnz_avg -> decomposition (32) */
   int32_t autotune;      /* 1: pick the sub-warp width by timing (default 1)             */
-  int32_t reps;          /* timed repetitions per probe (default 20)                     */
+  int32_t reps;          /* timed repetitions per probe (default 8; the autotuner half) */
   spmv_variant fixed;    /* SPMV_TUNE_FIXED only                                         */
   spmv_selector_t selector; /* SPMV_TUNE_LEARNED only                                    */
   double min_margin;     /* learned: smallest |logit| accepted, else profile (default 0) */

@@ -934,7 +934,7 @@ spmv_status spmv_tune_opts_default(spmv_tune_opts *o) {
   o->t_mb = 0.75;
   o->long_row_ratio = 32.0;
   o->autotune = 1;
-  o->reps = 20;
+  o->reps = 8;
   o->second_pass = 1;
   o->min_margin = 0.0;
   return SPMV_OK;
@@ -1063,7 +1063,7 @@ spmv_status spmv_tune(spmv_handle_t h, spmv_mode mode, const spmv_tune_opts *opt
   spmv_tune_opts opts;
   if (opts_in) opts = *opts_in;
   else spmv_tune_opts_default(&opts);
-  if (opts.reps <= 0) opts.reps = 20;
+  if (opts.reps <= 0) opts.reps = 8;
   if (mode == SPMV_TUNE_LEARNED && !opts.selector) return SPMV_ERR_NO_SELECTOR;
   if (mode < SPMV_TUNE_PROFILE || mode > SPMV_TUNE_FIXED) return SPMV_ERR_ARG;
   if (mode == SPMV_TUNE_FIXED && !valid_variant(opts.fixed)) return SPMV_ERR_ARG;
