@@ -51,9 +51,29 @@ inline spmv_status map_err(cudaError_t e) {
   } while (0)
 
 // Device buffer with zeroed slack past the logical end (see kPadElems).
+// A device allocation owned by exactly one object (move-only; freed on destruction, so
+// temporaries do not leak when a CUDA error unwinds a build step).
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) {
+    o.p = nullptr;
+    o.bytes = 0;
+  }
+  DevBuf &operator=(DevBuf &&o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p;
+      bytes = o.bytes;
+      o.p = nullptr;
+      o.bytes = 0;
+    }
+    return *this;
+  }
+  ~DevBuf() { release(); }
   void alloc(size_t logical_bytes, size_t elem_bytes, cudaStream_t s, bool zero_all = false) {
     release();
     size_t pad = (size_t)kPadElems * elem_bytes;

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_df(const RunArgs a) {
 namespace {
 
 template <int DB, bool XL2> cudaError_t launch_rowtile_df_k(const RunArgs &a, cudaStream_t s) {
-  static int configured = 0;
+  static std::atomic<int> configured{0};
   const int rows = a.tile_rows > 0 ? a.tile_rows : kTileRows;
   const size_t smem = 16 + (size_t)a.tile_cap * (8 + sizeof(typename IdxOf<DB>::type));
   cudaError_t e = ensure_smem(k_rowtile_df<DB, XL2>, smem, configured);

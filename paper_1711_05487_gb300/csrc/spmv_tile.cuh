@@ -8,6 +8,8 @@
 // exactly the sources it was taken on.
 #pragma once
 
+#include <atomic>
+#include <mutex>
 #include <type_traits>
 
 #include "common.cuh"
@@ -266,15 +268,24 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_pipe(const RunArgs a) {
   }
 }
 
+// Raises a kernel's dynamic shared-memory limit the first time a launch needs more than
+// 48 KB. The limit only grows, under one lock, so concurrent callers never lower it below a
+// size another thread is about to launch with.
+inline std::mutex &smem_attr_mutex() {
+  static std::mutex m;
+  return m;
+}
+
 template <typename K>
-cudaError_t ensure_smem(K kernel, size_t smem, int &configured) {
-  if (smem > 48 * 1024 && configured < (int)smem) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = (int)smem;
-  }
-  return cudaSuccess;
+cudaError_t ensure_smem(K kernel, size_t smem, std::atomic<int> &configured) {
+  if (smem <= 48 * 1024 || configured.load(std::memory_order_acquire) >= (int)smem)
+    return cudaSuccess;
+  std::lock_guard<std::mutex> lk(smem_attr_mutex());
+  if (configured.load(std::memory_order_relaxed) >= (int)smem) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) configured.store((int)smem, std::memory_order_release);
+  return e;
 }
 
 template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
@@ -283,7 +294,7 @@ cudaError_t launch_rowtile_k(const RunArgs &a, cudaStream_t s) {
   const int rows = a.tile_rows > 0 ? a.tile_rows : kTileRows;
   const size_t per_stage = (size_t)a.tile_cap * (sizeof(ValT) + sizeof(IdxT));
   if (a.tile_pipe) {
-    static int configured = 0;
+    static std::atomic<int> configured{0};
     auto kern = k_rowtile_pipe<ValT, VecT, AccT, DB, XL2>;
     const size_t smem = 32 + 2 * per_stage;
     cudaError_t e = ensure_smem(kern, smem, configured);
@@ -298,7 +309,7 @@ cudaError_t launch_rowtile_k(const RunArgs &a, cudaStream_t s) {
     kern<<<(unsigned)g, rows, smem, s>>>(a);
     return cudaGetLastError();
   }
-  static int configured = 0;
+  static std::atomic<int> configured{0};
   const size_t smem = 16 + per_stage;
   cudaError_t e = ensure_smem(k_rowtile<ValT, VecT, AccT, DB, XL2>, smem, configured);
   if (e != cudaSuccess) return e;
