@@ -97,6 +97,48 @@ __device__ void warp_rows(const BatchMat &m, int r0, int r1, int lane) {
   }
 }
 
+// K = 16: the four lanes of a quad share a nonzero, each gathering one 16-byte quarter of
+// its x row and keeping 4 accumulators, so a sub-warp of VS lanes has VS / 4 nonzeros of its
+// row in flight (two per quad per step) instead of one 64-byte gather per lane. The quads'
+// sums of one row are added with a fixed shuffle tree; the quad of slot 0 writes the row.
+template <int VS>
+__device__ void warp_rows_k16(const BatchMat &m, int r0, int r1, int lane) {
+  static_assert(VS >= 4, "a quad per nonzero");
+  constexpr int GROUPS = 32 / VS, SLOTS = VS / 4;
+  const int sl = lane & (VS - 1), slot = sl >> 2, quad = sl & 3;
+  const unsigned mask = group_mask<VS>();
+  for (int row = r0 + lane / VS; row < r1; row += GROUPS) {
+    const int s = __ldg(m.rowptr + row), e = __ldg(m.rowptr + row + 1);
+    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    int j = s + slot;
+    for (; j + SLOTS < e; j += 2 * SLOTS) {
+      const float v0 = __ldg(m.val + j), v1 = __ldg(m.val + j + SLOTS);
+      const int c0 = __ldg(m.colind + j), c1 = __ldg(m.colind + j + SLOTS);
+      const uint4 x0 = ld_nc_u4(m.X + (int64_t)c0 * 16 + quad * 4);
+      const uint4 x1 = ld_nc_u4(m.X + (int64_t)c1 * 16 + quad * 4);
+      acc[0] = fmaf(v1, __uint_as_float(x1.x), fmaf(v0, __uint_as_float(x0.x), acc[0]));
+      acc[1] = fmaf(v1, __uint_as_float(x1.y), fmaf(v0, __uint_as_float(x0.y), acc[1]));
+      acc[2] = fmaf(v1, __uint_as_float(x1.z), fmaf(v0, __uint_as_float(x0.z), acc[2]));
+      acc[3] = fmaf(v1, __uint_as_float(x1.w), fmaf(v0, __uint_as_float(x0.w), acc[3]));
+    }
+    if (j < e) {
+      const float v0 = __ldg(m.val + j);
+      const uint4 x0 = ld_nc_u4(m.X + (int64_t)__ldg(m.colind + j) * 16 + quad * 4);
+      acc[0] = fmaf(v0, __uint_as_float(x0.x), acc[0]);
+      acc[1] = fmaf(v0, __uint_as_float(x0.y), acc[1]);
+      acc[2] = fmaf(v0, __uint_as_float(x0.z), acc[2]);
+      acc[3] = fmaf(v0, __uint_as_float(x0.w), acc[3]);
+    }
+#pragma unroll
+    for (int off = 4; off < VS; off <<= 1)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += __shfl_xor_sync(mask, acc[q], off, VS);
+    if (slot == 0)
+      *reinterpret_cast<float4 *>(m.Y + (int64_t)row * 16 + quad * 4) =
+          make_float4(acc[0], acc[1], acc[2], acc[3]);
+  }
+}
+
 // rows in flight per lane: more for narrow right-hand sides (registers: U * K accumulators)
 template <int K> struct RowsInFlight {
   static constexpr int value = K == 1 ? 4 : (K == 4 ? 2 : 1);
@@ -105,6 +147,15 @@ template <int K> struct RowsInFlight {
 template <int K>
 __device__ void warp_rows_vs(const BatchMat &m, int r0, int r1, int lane) {
   constexpr int U = RowsInFlight<K>::value;
+  if constexpr (K == 16) {
+    switch (m.vs) {
+      case 1: case 2: case 4: warp_rows_k16<4>(m, r0, r1, lane); break;
+      case 8: warp_rows_k16<8>(m, r0, r1, lane); break;
+      case 16: warp_rows_k16<16>(m, r0, r1, lane); break;
+      default: warp_rows_k16<32>(m, r0, r1, lane); break;
+    }
+    return;
+  }
   switch (m.vs) {
     case 1: warp_rows<K, 1, U>(m, r0, r1, lane); break;
     case 2: warp_rows<K, 2, U>(m, r0, r1, lane); break;
@@ -117,9 +168,51 @@ __device__ void warp_rows_vs(const BatchMat &m, int r0, int r1, int lane) {
 
 // Nonzeros [z0, z1) of one long row by one warp: FP32 lane sums, then a fixed shuffle tree
 // in FP64 into partial slot `chunk` (16 doubles per slot, k used).
+// K = 16: eight slots of a quad each (as in warp_rows_k16); the slots' sums are added in
+// FP64 with a fixed shuffle tree and the quad of slot 0 writes the 16 partials.
+__device__ void warp_chunk_k16(const BatchMat &m, int z0, int z1, int chunk, double *partials,
+                               int lane) {
+  const int slot = lane >> 2, quad = lane & 3;
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  int j = z0 + slot;
+  for (; j + 8 < z1; j += 16) {
+    const float v0 = __ldg(m.val + j), v1 = __ldg(m.val + j + 8);
+    const int c0 = __ldg(m.colind + j), c1 = __ldg(m.colind + j + 8);
+    const uint4 x0 = ld_nc_u4(m.X + (int64_t)c0 * 16 + quad * 4);
+    const uint4 x1 = ld_nc_u4(m.X + (int64_t)c1 * 16 + quad * 4);
+    acc[0] = fmaf(v1, __uint_as_float(x1.x), fmaf(v0, __uint_as_float(x0.x), acc[0]));
+    acc[1] = fmaf(v1, __uint_as_float(x1.y), fmaf(v0, __uint_as_float(x0.y), acc[1]));
+    acc[2] = fmaf(v1, __uint_as_float(x1.z), fmaf(v0, __uint_as_float(x0.z), acc[2]));
+    acc[3] = fmaf(v1, __uint_as_float(x1.w), fmaf(v0, __uint_as_float(x0.w), acc[3]));
+  }
+  if (j < z1) {
+    const float v0 = __ldg(m.val + j);
+    const uint4 x0 = ld_nc_u4(m.X + (int64_t)__ldg(m.colind + j) * 16 + quad * 4);
+    acc[0] = fmaf(v0, __uint_as_float(x0.x), acc[0]);
+    acc[1] = fmaf(v0, __uint_as_float(x0.y), acc[1]);
+    acc[2] = fmaf(v0, __uint_as_float(x0.z), acc[2]);
+    acc[3] = fmaf(v0, __uint_as_float(x0.w), acc[3]);
+  }
+  double t[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    t[q] = (double)acc[q];
+#pragma unroll
+    for (int off = 4; off < 32; off <<= 1) t[q] += __shfl_xor_sync(0xffffffffu, t[q], off);
+  }
+  if (slot == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) partials[(int64_t)chunk * 16 + quad * 4 + q] = t[q];
+  }
+}
+
 template <int K>
 __device__ void warp_chunk(const BatchMat &m, int z0, int z1, int chunk, double *partials,
                            int lane) {
+  if constexpr (K == 16) {
+    warp_chunk_k16(m, z0, z1, chunk, partials, lane);
+    return;
+  }
   float acc[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) acc[q] = 0.0f;
