@@ -5,6 +5,7 @@
 // so a solve repeats bit for bit. Scalars stay on the device; the host reads the residual
 // only every `check_every` iterations.
 #include "common.cuh"
+#include "handle.h"
 
 namespace spmv {
 
@@ -143,3 +144,72 @@ cudaError_t launch_cg_p(const double *r, double *p, int64_t n, const double *rr,
 }
 
 }  // namespace spmv
+
+using namespace spmv;
+using namespace spmv::rt;
+
+extern "C" {
+
+spmv_status spmv_cg(spmv_handle_t h, const double *b, double *x, int32_t max_iters,
+                    double rtol, int32_t check_every, double *res_hist,
+                    spmv_cg_report *report, spmv_stream_t stream) {
+  if (!h || max_iters < 0 || !(rtol >= 0.0) || check_every < 1) return SPMV_ERR_ARG;
+  if (!h->tuned) return SPMV_ERR_NOT_TUNED;
+  if (h->n_rows != h->n_cols) return SPMV_ERR_ARG;
+  if (h->vec != SPMV_F64) return SPMV_ERR_UNSUPPORTED_DTYPE;
+  if (h->n_rows > 0 && (!b || !x)) return SPMV_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return guarded([&]() -> spmv_status {
+    const double t0 = now_ms();
+    const int64_t n = h->n_rows;
+    const int nb = cg_reduce_blocks();
+    const size_t vec_bytes = ((8 * (size_t)std::max<int64_t>(n, 1) + 255) / 256) * 256;
+    const size_t need = 3 * vec_bytes + 8 * (size_t)nb + 8 * 8;
+    if (h->cg_ws.bytes < need) h->cg_ws.alloc(need, 8, s);
+    char *w = static_cast<char *>(h->cg_ws.p);
+    double *r = reinterpret_cast<double *>(w);
+    double *p = reinterpret_cast<double *>(w + vec_bytes);
+    double *ap = reinterpret_cast<double *>(w + 2 * vec_bytes);
+    double *part = reinterpret_cast<double *>(w + 3 * vec_bytes);
+    double *sc = part + nb;   // sc[0], sc[1]: (r, r) of even / odd iterations; sc[2]: (p, Ap);
+                              // sc[3]: (b, b)
+    // r_0 = b - A x_0, p_0 = r_0
+    CK(launch_run(h, h->variant, x, ap, s));
+    CK(launch_cg_start(b, ap, r, p, n, part, sc, res_hist, s));
+    CK(launch_dot(b, b, n, part, sc + 3, nullptr, s));
+    double host_sc[4];
+    CK(cudaMemcpyAsync(host_sc, sc, sizeof host_sc, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double b_norm = std::sqrt(host_sc[3]);
+    double res = std::sqrt(host_sc[0]);
+    bool conv = res <= rtol * b_norm;
+    int32_t k = 0;
+    while (!conv && k < max_iters) {
+      const int32_t chunk = std::min(check_every, max_iters - k);
+      for (int32_t j = 0; j < chunk; ++j, ++k) {
+        double *rr = sc + (k & 1), *rr_new = sc + ((k + 1) & 1);
+        CK(launch_run(h, h->variant, p, ap, s));
+        CK(launch_dot(p, ap, n, part, sc + 2, nullptr, s));
+        CK(launch_cg_xr(p, ap, x, r, n, rr, sc + 2, part, rr_new,
+                        res_hist ? res_hist + k + 1 : nullptr, s));
+        CK(launch_cg_p(r, p, n, rr, rr_new, s));
+      }
+      double rr_host = 0.0;
+      CK(cudaMemcpyAsync(&rr_host, sc + (k & 1), sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      res = std::sqrt(rr_host);
+      conv = res <= rtol * b_norm;
+    }
+    CK(cudaStreamSynchronize(s));
+    if (report) {
+      report->iters = k;
+      report->converged = conv ? 1 : 0;
+      report->res_norm = res;
+      report->b_norm = b_norm;
+      report->t_ms = now_ms() - t0;
+    }
+    return SPMV_OK;
+  });
+}
+
+}  // extern "C"

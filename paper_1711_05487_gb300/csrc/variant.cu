@@ -1,0 +1,254 @@
+// Optimization-pool data and variant installation (Table II): the delta index, the
+// merge-path tile table, the row decomposition tables and the thread-per-row tile geometry.
+#include "handle.h"
+
+using namespace spmv;
+using namespace spmv::rt;
+
+namespace spmv {
+namespace rt {
+
+const KernelSet *set_for(const spmv_matrix *h) { return kernel_set(h->storage, h->vec, h->acc); }
+
+RunArgs run_args(const spmv_matrix *h, const void *x, void *y) {
+  RunArgs a;
+  a.n_rows = h->n_rows;
+  a.n_cols = h->n_cols;
+  a.nnz = h->nnz;
+  a.rowptr = h->rowptr.as<int32_t>();
+  a.colind = h->colind.as<int32_t>();
+  a.delta = h->delta.p;
+  a.delta_bits = h->delta_bits;
+  a.dbase = h->dbase.as<int32_t>();
+  a.esc = h->esc.as<int32_t>();
+  a.val = h->val_ptr();
+  a.x = x;
+  a.y = y;
+  a.coord = h->coord.as<int2>();
+  a.n_tiles = h->n_tiles;
+  a.tail_row = h->tail_row.as<int32_t>();
+  a.tail_val = h->tail_val.as<double>();
+  a.head_val = h->head_val.as<double>();
+  a.tile_cap = h->tile_cap;
+  a.tile_rows = h->tile_rows;
+  a.tile_pipe = h->tile_pipe;
+  a.err = h->d_err.as<int32_t>();
+  a.val_df = h->val_df.p;
+  a.bin_l_med = kBinMed;
+  a.bin_vs_short = h->bin_vs_short;
+  a.bin_rows = h->bin_rows.as<int32_t>();
+  a.bin_n_med = h->bin_n_med;
+  a.bin_chunks = h->bin_chunks.as<int4>();
+  a.bin_n_chunks = h->bin_n_chunks;
+  a.bin_long_rows = h->bin_long_rows.as<int32_t>();
+  a.bin_long_first = h->bin_long_first.as<int32_t>();
+  a.bin_n_long = h->bin_n_long;
+  a.bin_partials = h->bin_partials.as<double>();
+  return a;
+}
+
+}  // namespace rt
+}  // namespace spmv
+
+namespace {
+
+// The delta index (Section III-E, MB): 8- or 16-bit column deltas, never both; the width
+// is the one whose index is smaller (1 or 2 bytes per nonzero of the rows whose gaps fit,
+// 4 per nonzero of escape rows), 16 on a tie.
+void build_delta(spmv_matrix *h, cudaStream_t s) {
+  if (h->has_delta) return;
+  const int64_t n = h->n_rows;
+  DevBuf cnt;
+  cnt.alloc(sizeof(int64_t) * 2 * (size_t)(n + 1), 8, s, true);
+  int64_t *e8 = cnt.as<int64_t>(), *e16 = e8 + (n + 1);
+  CK(launch_delta_flags(n, h->rowptr.as<int32_t>(), h->colind.as<int32_t>(), e8, e16, s));
+  const int64_t se = scan_scratch_elems(n);
+  DevBuf scr;
+  scr.alloc(sizeof(int64_t) * (size_t)se, 8, s);
+  CK(launch_scan_i64(e8, n, e8 + n, scr.as<int64_t>(), se, s));
+  CK(launch_scan_i64(e16, n, e16 + n, scr.as<int64_t>(), se, s));
+  int64_t esc8 = 0, esc16 = 0;
+  CK(cudaMemcpyAsync(&esc8, e8 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&esc16, e16 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const int64_t bytes8 = (h->nnz - esc8) + 4 * esc8;
+  const int64_t bytes16 = 2 * (h->nnz - esc16) + 4 * esc16;
+  const int bits = bytes8 < bytes16 ? 8 : 16;
+  const int64_t n_esc = bits == 8 ? esc8 : esc16;
+  h->dbase.alloc(sizeof(int32_t) * (size_t)n, 4, s);
+  h->delta.alloc((size_t)(bits / 8) * (size_t)h->nnz, (size_t)(bits / 8), s);
+  h->esc.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(n_esc, 1), 4, s);
+  CK(launch_delta_fill(bits, n, h->rowptr.as<int32_t>(), h->colind.as<int32_t>(),
+                       bits == 8 ? e8 : e16, h->dbase.as<int32_t>(), h->delta.p,
+                       h->esc.as<int32_t>(), s));
+  CK(cudaStreamSynchronize(s));
+  h->n_esc = n_esc;
+  h->delta_bits = bits;
+  h->has_delta = true;
+}
+
+void build_merge(spmv_matrix *h, cudaStream_t s) {
+  if (h->has_merge) return;
+  const int64_t total = h->n_rows + h->nnz;
+  const int64_t n_tiles = (total + kMergeItems - 1) / kMergeItems;
+  h->coord.alloc(sizeof(int2) * (size_t)(n_tiles + 1), 8, s);
+  h->tail_row.alloc(sizeof(int32_t) * (size_t)std::max<int64_t>(n_tiles, 1), 4, s, true);
+  h->tail_val.alloc(sizeof(double) * (size_t)std::max<int64_t>(n_tiles, 1), 8, s, true);
+  h->head_val.alloc(sizeof(double) * (size_t)std::max<int64_t>(n_tiles, 1), 8, s, true);
+  CK(launch_merge_coords(h->n_rows, h->nnz, h->rowptr.as<int32_t>(), kMergeItems, n_tiles,
+                         h->coord.as<int2>(), s));
+  CK(cudaStreamSynchronize(s));
+  h->n_tiles = n_tiles;
+  h->has_merge = true;
+}
+
+// Row decomposition tables (partition 2): three exclusive scans over per-row counts place
+// each medium row in the row list and each long row's chunks in the chunk table.
+void build_bins(spmv_matrix *h, cudaStream_t s) {
+  if (h->has_bins) return;
+  const int64_t n = h->n_rows;
+  DevBuf cnt;
+  cnt.alloc(sizeof(int64_t) * 3 * (size_t)(n + 1), 8, s, true);
+  int64_t *med = cnt.as<int64_t>(), *lng = med + (n + 1), *nch = lng + (n + 1);
+  CK(launch_bin_counts(n, h->rowptr.as<int32_t>(), kBinMed, kBinChunk, med, lng, nch, s));
+  const int64_t se = scan_scratch_elems(n);
+  DevBuf scr;
+  scr.alloc(sizeof(int64_t) * (size_t)se, 8, s);
+  for (int64_t *p : {med, lng, nch}) CK(launch_scan_i64(p, n, p + n, scr.as<int64_t>(), se, s));
+  int64_t tot[3];
+  for (int q = 0; q < 3; ++q)
+    CK(cudaMemcpyAsync(tot + q, med + (int64_t)q * (n + 1) + n, sizeof(int64_t),
+                       cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  h->bin_rows.alloc(4 * (size_t)std::max<int64_t>(tot[0], 1), 4, s);
+  h->bin_long_rows.alloc(4 * (size_t)std::max<int64_t>(tot[1], 1), 4, s);
+  h->bin_long_first.alloc(4 * (size_t)(tot[1] + 1), 4, s);
+  h->bin_chunks.alloc(16 * (size_t)std::max<int64_t>(tot[2], 1), 16, s);
+  h->bin_partials.alloc(8 * (size_t)std::max<int64_t>(tot[2], 1), 8, s);
+  const int32_t last = (int32_t)tot[2];
+  CK(cudaMemcpyAsync(h->bin_long_first.as<int32_t>() + tot[1], &last, 4, cudaMemcpyHostToDevice, s));
+  CK(launch_bin_fill(n, h->rowptr.as<int32_t>(), h->colind.as<int32_t>(), kBinMed, kBinChunk,
+                     med, lng, nch,
+                     h->bin_rows.as<int32_t>(), h->bin_long_rows.as<int32_t>(),
+                     h->bin_long_first.as<int32_t>(), h->bin_chunks.as<int4>(), s));
+  CK(cudaStreamSynchronize(s));
+  h->bin_n_med = tot[0];
+  h->bin_n_long = tot[1];
+  h->bin_n_chunks = tot[2];
+  h->has_bins = true;
+}
+
+// Geometry of the thread-per-row kernel. A staged tile holds the values and columns of
+// `rows` consecutive rows; the staged capacity is the matrix's largest such tile, capped by
+// the shared-memory budget of one stage (48 KB for one tile per CTA, 56 KB per stage for
+// the persistent two-stage kernel). Tiles above the cap are computed from global memory.
+// staged-tile alignment of the variant's column representation
+int tile_align(const spmv_matrix *h, const spmv_variant &v) {
+  return v.index == 1 ? stage_align_bits(h->delta_bits) : 8;
+}
+
+int32_t max_tile_elems(spmv_matrix *h, int rows, int align, cudaStream_t s) {
+  CK(launch_tile_max(h->n_rows, h->rowptr.as<int32_t>(), rows, align, h->small.as<int32_t>(), s));
+  int32_t m = 0;
+  CK(cudaMemcpyAsync(&m, h->small.p, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return m;
+}
+
+int32_t tile_limit(const spmv_matrix *h, const spmv_variant &v, bool pipe) {
+  const int eb = (int)dtype_bytes(h->storage) + (v.index == 1 ? h->delta_bits / 8 : 4);
+  const int budget = (pipe ? 56 : 48) * 1024 - 32;
+  const int al = tile_align(h, v);
+  return ((budget / eb) / al) * al;
+}
+
+}  // namespace
+
+namespace spmv {
+namespace rt {
+
+void set_tile_geometry(spmv_matrix *h, const spmv_variant &v, int rows, bool pipe,
+                       cudaStream_t s) {
+  h->tile_rows = rows;
+  h->tile_pipe = pipe ? 1 : 0;
+  h->tile_cap = std::min(max_tile_elems(h, rows, tile_align(h, v), s), tile_limit(h, v, pipe));
+}
+
+// Default geometry: the largest of 128, 64, 32 rows per tile whose largest tile fits one
+// 48 KB stage, one tile per CTA; 128-row tiles when none fits.
+void compute_tile_cap(spmv_matrix *h, const spmv_variant &v, cudaStream_t s) {
+  const int32_t limit = tile_limit(h, v, false);
+  for (int rows = kTileRows; rows >= 32; rows /= 2) {
+    const int32_t m = max_tile_elems(h, rows, tile_align(h, v), s);
+    if (m <= limit) {
+      h->tile_rows = rows;
+      h->tile_pipe = 0;
+      h->tile_cap = m;
+      return;
+    }
+  }
+  set_tile_geometry(h, v, kTileRows, false, s);
+}
+
+void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
+  if (v.partition == 1) {
+    v.index = 0;                 // the delta index is built for sub-warp rows only
+    build_merge(h, s);
+  } else if (v.partition == 2) {
+    if (v.index == 1) build_delta(h, s);
+    v.vec = 1;
+    if (v.vs != 2 && v.vs != 4 && v.vs != 8) v.vs = 4;   // short rows' sub-warp width
+    v.tile_rows = 0;
+    v.tile_pipe = 0;
+    h->bin_vs_short = v.vs;
+    build_bins(h, s);
+  } else {
+    if (v.index == 1) {
+      v.vec = 1;
+      build_delta(h, s);
+    }
+    if (v.vs == 0) {
+      v.vs = (v.vec || v.index == 1) ? pool_vs(h->nnz_avg(), v.index == 1 ? 8 : 4)
+                                     : heuristic_vs(h->nnz_avg(), 1);
+    }
+    if (h->storage == SPMV_DF64) v.tile_pipe = 0;   // the double-float kernel: one tile per CTA
+    if (v.vs == 1 && v.tile_rows != 0) {
+      set_tile_geometry(h, v, v.tile_rows, v.tile_pipe != 0, s);
+    } else {
+      compute_tile_cap(h, v, s);
+      if (v.vs == 1) {
+        v.tile_rows = h->tile_rows;
+        v.tile_pipe = h->tile_pipe;
+      }
+    }
+    if (v.vs != 1) {
+      v.tile_rows = 0;
+      v.tile_pipe = 0;
+    }
+  }
+}
+
+bool valid_variant(const spmv_variant &v) {
+  if (v.partition < 0 || v.partition > 2) return false;
+  if (v.partition == 2 && v.vs != 0 && v.vs != 2 && v.vs != 4 && v.vs != 8) return false;
+  if (v.index != 0 && v.index != 1) return false;
+  if (v.xpath != 0 && v.xpath != 1) return false;
+  if (v.vec != 0 && v.vec != 1) return false;
+  if (v.partition == 0 && v.vs != 0 && v.vs != 1 && v.vs != 2 && v.vs != 4 && v.vs != 8 &&
+      v.vs != 16 && v.vs != 32)
+    return false;
+  if (v.tile_rows != 0 && v.tile_rows != 32 && v.tile_rows != 64 && v.tile_rows != 128)
+    return false;
+  if (v.tile_pipe != 0 && v.tile_pipe != 1) return false;
+  return true;
+}
+
+cudaError_t launch_run(const spmv_matrix *h, const spmv_variant &v, const void *x, void *y,
+                       cudaStream_t s) {
+  const KernelSet *ks = set_for(h);
+  RunArgs a = run_args(h, x, y);
+  return ks->spmv(v, a, s);
+}
+
+}  // namespace rt
+}  // namespace spmv
