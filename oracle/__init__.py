@@ -94,6 +94,10 @@ def _declare(L):
     L.oracle_delta8_decode.restype = None
     L.oracle_delta_width.argtypes = [_I64, _P, _P]
     L.oracle_delta_width.restype = ctypes.c_int32
+    L.oracle_panel_width.argtypes = [_I64, ctypes.c_int32]
+    L.oracle_panel_width.restype = ctypes.c_int32
+    L.oracle_col_panels.argtypes = [_I64, _I64, _P, _P, ctypes.c_int32, _P, _P]
+    L.oracle_col_panels.restype = None
     L.oracle_merge_path.argtypes = [_I64, _I64, _P, _I64, _P]
     L.oracle_merge_path.restype = None
     L.oracle_features.argtypes = [_I64, _I64, _P, _P, _I64, _I64, _I64, _P, _P]
@@ -207,6 +211,22 @@ def row_bins(rowptr, colind, l_med=64, chunk=4096):
                           _p(counts))
     a, b, c = (int(v) for v in counts)
     return med[:a], lng[:b], first[:b + 1], ch[:c]
+
+
+def panel_width(n_cols: int, n_panels: int) -> int:
+    """Columns per panel: ceil(n_cols / n_panels) rounded up to a multiple of 32."""
+    return int(lib().oracle_panel_width(int(n_cols), int(n_panels)))
+
+
+def col_panels(rowptr, colind, n_cols: int, n_panels: int):
+    """(prow (n_panels, n_rows + 1), perm, width) of the column-panel copy: panel p's rows
+    are prow[p] into the copy, whose columns are colind[perm] and values val[perm]."""
+    rp, ci = _c(rowptr, np.int32), _c(colind, np.int32)
+    n = rp.shape[0] - 1
+    prow = np.empty((n_panels, n + 1), np.int32)
+    perm = np.empty(max(ci.shape[0], 1), np.int32)
+    lib().oracle_col_panels(n, int(n_cols), _p(rp), _p(ci), int(n_panels), _p(prow), _p(perm))
+    return prow, perm[:ci.shape[0]], panel_width(n_cols, n_panels)
 
 
 def spmv_static(rowptr, colind, val, x, n_threads: int):

@@ -335,6 +335,36 @@ void oracle_row_bins(int64_t n_rows, const int32_t *rowptr, const int32_t *colin
 }
 
 /* ---------------------------------------------------------------------------------- */
+/* Column panels (Section III-E, ML: make the irregular accesses to x hit in cache; read on
+ * GB300 as cutting x into P slices that each fit in the L2 and running the SpMV as one pass
+ * per slice). Panel p holds the columns [p*w, (p+1)*w), w = oracle_panel_width(n_cols, P):
+ * ceil(n_cols / P) rounded up to a multiple of 32 (trailing panels may be empty). The
+ * panel-major copy lists panel 0's nonzeros row by row, then panel 1's, and so on; inside a
+ * row the columns keep their order. prow[p*(n_rows+1) + i] is the position in the copy of
+ * row i's first nonzero of panel p, prow[p*(n_rows+1) + n_rows] the end of panel p, and
+ * perm[k] the position in the original CSR of copy element k.                           */
+int32_t oracle_panel_width(int64_t n_cols, int32_t n_panels) {
+  int64_t w = (n_cols + n_panels - 1) / n_panels;
+  w = (w + 31) / 32 * 32;
+  return (int32_t)(w > 0 ? w : 32);
+}
+
+void oracle_col_panels(int64_t n_rows, int64_t n_cols, const int32_t *rowptr,
+                       const int32_t *colind, int32_t n_panels, int32_t *prow, int32_t *perm) {
+  const int64_t w = oracle_panel_width(n_cols, n_panels);
+  int64_t k = 0;
+  for (int32_t p = 0; p < n_panels; ++p) {
+    const int64_t lo = (int64_t)p * w, hi = lo + w;
+    for (int64_t i = 0; i < n_rows; ++i) {
+      prow[(int64_t)p * (n_rows + 1) + i] = (int32_t)k;
+      for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j)
+        if (colind[j] >= lo && colind[j] < hi) perm[k++] = (int32_t)j;
+    }
+    prow[(int64_t)p * (n_rows + 1) + n_rows] = (int32_t)k;
+  }
+}
+
+/* ---------------------------------------------------------------------------------- */
 /* Delta-indexed column indices (Section III-E, MB row of Table II): each column index is
  * stored as its distance to the previous column of the same row, in 16 bits wherever
  * possible. Read per row: a row whose every consecutive distance fits 16 bits keeps its

@@ -272,3 +272,84 @@ def test_row_bins_partition_the_matrix_exactly():
     rows_of = np.repeat(np.arange(m.n_rows), lens)
     np.add.at(y2, rows_of, prod)
     assert np.allclose(y2, y, rtol=0, atol=1e-9)
+
+
+# ------------------------------------------------------------------ column panels
+def test_panel_width_closed_forms():
+    # ceil(n_cols / P) rounded up to a multiple of 32
+    assert oracle.panel_width(100, 1) == 128
+    assert oracle.panel_width(1000, 4) == 256
+    assert oracle.panel_width(64, 2) == 32
+    assert oracle.panel_width(65, 2) == 64
+    assert oracle.panel_width(16_000_000, 2) == 8_000_000
+    assert oracle.panel_width(16_000_000, 3) == 5_333_344
+    assert oracle.panel_width(40, 4) == 32      # panels 2 and 3 are empty
+    assert oracle.panel_width(0, 2) == 32
+
+
+def test_col_panels_hand_example():
+    # 3 rows over 70 columns, 3 panels of 32 columns: [0, 32), [32, 64), [64, 96)
+    rp = np.array([0, 4, 4, 7], np.int32)
+    ci = np.array([1, 31, 32, 69, 5, 40, 63], np.int32)
+    prow, perm, w = oracle.col_panels(rp, ci, 70, 3)
+    assert w == 32
+    assert prow.tolist() == [[0, 2, 2, 3], [3, 4, 4, 6], [6, 7, 7, 7]]
+    assert perm.tolist() == [0, 1, 4, 2, 5, 6, 3]
+
+
+def _dense(n_rows, n_cols, rp, ci, v):
+    d = np.zeros((n_rows, n_cols))
+    for i in range(n_rows):
+        for j in range(rp[i], rp[i + 1]):
+            d[i, ci[j]] += v[j]
+    return d
+
+
+@pytest.mark.parametrize("n_panels", [1, 2, 3, 5, 16])
+@pytest.mark.parametrize("gen", [lambda: synth.uniform_random(300, 40, seed=31),
+                                 lambda: synth.scattered(500, 8, seed=32),
+                                 lambda: synth.banded(400, 30, 0.5, seed=33),
+                                 lambda: synth.dense_random(60, 90, 0.03, seed=36)])
+def test_col_panels_against_dense_masks(gen, n_panels):
+    """Panel p, read as a CSR of its own, is A with every column outside [p*w, (p+1)*w) set
+    to zero; perm is a bijection; columns keep their order inside each row."""
+    m = gen()
+    prow, perm, w = oracle.col_panels(m.rowptr, m.colind, m.n_cols, n_panels)
+    assert prow.shape == (n_panels, m.n_rows + 1)
+    assert np.array_equal(np.sort(perm), np.arange(m.nnz))
+    dense = _dense(m.n_rows, m.n_cols, m.rowptr, m.colind, m.val)
+    pc, pv = m.colind[perm], m.val[perm]
+    cols = np.arange(m.n_cols)
+    total = np.zeros_like(dense)
+    for p in range(n_panels):
+        r = prow[p]
+        assert np.all(np.diff(r) >= 0)
+        if p > 0:
+            assert r[0] == prow[p - 1][-1]
+        for i in range(m.n_rows):
+            assert np.all(np.diff(pc[r[i]:r[i + 1]]) > 0)
+        d = _dense(m.n_rows, m.n_cols, r, pc, pv)
+        inside = (cols >= p * w) & (cols < (p + 1) * w)
+        assert np.array_equal(d, dense * inside[None, :])
+        total += d
+    assert np.array_equal(total, dense)
+    assert prow[0][0] == 0 and prow[-1][-1] == m.nnz
+    if n_panels == 1:
+        assert np.array_equal(prow[0], m.rowptr) and np.array_equal(perm, np.arange(m.nnz))
+
+
+def test_col_panels_spmv_by_passes_is_exact_on_integers():
+    # integer values and x: every partial sum is exact, so summing the passes in order
+    # equals the one-pass product bit for bit
+    m = synth.scattered(2000, 8, seed=34)
+    rng = np.random.default_rng(35)
+    val = rng.integers(-9, 10, m.nnz).astype(np.float64)
+    x = rng.integers(-9, 10, m.n_cols).astype(np.float64)
+    y, _ = oracle.spmv(m.rowptr, m.colind, val, x)
+    prow, perm, _ = oracle.col_panels(m.rowptr, m.colind, m.n_cols, 3)
+    acc = np.zeros(m.n_rows)
+    for p in range(3):
+        yp, _ = oracle.spmv(prow[p] - prow[p][0], m.colind[perm][prow[p][0]:prow[p][-1]],
+                            val[perm][prow[p][0]:prow[p][-1]], x)
+        acc += yp
+    assert np.array_equal(acc, y)
