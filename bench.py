@@ -160,11 +160,32 @@ def dtype_bytes(code):
 
 def alg_bytes(n_rows, n_cols, nnz, variant, storage, vec):
     """Compulsory traffic of one SpMV with the variant's own format (P_MB's M_min):
-    row pointers, column indices (int32 or 16-bit deltas + per-row base), values, x, y."""
+    row pointers, column indices (int32 or 16-bit deltas + per-row base), values, x, y.
+    Column panels (xpath = P >= 2) read P sets of row pointers and pass over y 2P - 1 times
+    (written once, then read and written by every later pass)."""
+    if len(variant) > 2 and variant[2] >= 2:
+        p = variant[2]
+        vb = 8 if storage == 3 else dtype_bytes(storage)
+        return (4 * p * (n_rows + 1) + (4 + vb) * nnz + dtype_bytes(vec) * n_cols
+                + dtype_bytes(vec) * n_rows * (2 * p - 1))
     idx = 2 if variant[1] == 1 else 4
     extra = 4 * n_rows if variant[1] == 1 else 0
     return (4 * (n_rows + 1) + (idx + dtype_bytes(storage)) * nnz + extra
             + dtype_bytes(vec) * (n_rows + n_cols))
+
+
+def launches_per_spmv(A, variant) -> int:
+    """Kernel launches of one SpMV with the installed variant."""
+    from paper_1711_05487_gb300 import _abi
+    if len(variant) > 2 and variant[2] >= 2:
+        return variant[2]                                  # one pass per column panel
+    if variant[0] == 1:
+        n_tiles, _ = _abi.spmv_get_merge_path(A.handle)
+        return 1 + (n_tiles > 1)                           # tiles, then the carry fixup
+    if variant[0] == 2:
+        n_med, n_long, n_ch = _abi.spmv_get_row_bins(A.handle)
+        return 1 + (n_med + n_ch > 0) + (n_long > 0)       # short rows, warps, fixup
+    return 1
 
 
 # --------------------------------------------------------------------------- ours ----
@@ -302,12 +323,14 @@ def run_ours(args, rank, world):
         pool = {"csr_vector": dict(), "vector_w4": dict(vec=1, vs=4),
                 "tile_i32": dict(vec=1, vs=1), "tile_delta16": dict(index=1, vec=1, vs=1),
                 "tile_i32_xl2": dict(vec=1, vs=1, xpath=1),
-                "subwarp_delta16": dict(index=1, vec=1, vs=4), "merge_path": dict(partition=1)}
+                "subwarp_delta16": dict(index=1, vec=1, vs=4), "merge_path": dict(partition=1),
+                "col_panels_2": dict(xpath=2, vs=2)}
         for name, knobs in pool.items():
             A.set_variant(stream=stream, **knobs)
             t_v = timed(max(8, args.steps // 4), args.warmup)
             vb = alg_bytes(m.n_rows, m.n_cols, m.nnz,
-                           (knobs.get("partition", 0), knobs.get("index", 0)), storage, A.vec)
+                           (knobs.get("partition", 0), knobs.get("index", 0),
+                            knobs.get("xpath", 0)), storage, A.vec)
             sweep[name] = {"gflops": round(flops / (t_v * 1e-3) / 1e9, 1),
                            "frac_hbm": round(vb / (t_v * 1e-3) / 1e9 / peak, 3)}
         A.tune("fixed", stream=stream, fixed=api.variant(*rep.variant))
@@ -365,7 +388,7 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
                 "d2h_bytes_per_step": int(yh.numel() * yh.element_size()),
                 "ms_per_step": round(e2e_ms, 4)},
-        "gpu_launches": args.steps * (2 if rep.variant[0] == 1 else 1),
+        "gpu_launches": args.steps * launches_per_spmv(A, rep.variant),
         "precision_variants": extra,
         "variant_sweep": sweep,
         "amortization": amort,

@@ -78,7 +78,12 @@ typedef struct {
                         matrix, see spmv_get_delta) with escape rows (MB); merge-path
                         tiles (partition 1) always read int32 columns                     */
   int32_t xpath;     /* 0: default; 1: x kept L2-resident (evict-last gathers through the
-                        read-only path, evict-first streams) (ML)                         */
+                        read-only path, evict-first streams) (ML); P = 2..16: x cut into P
+                        column panels, the SpMV run as P passes over a panel-major copy of
+                        the matrix, pass p gathering only from slice p of x (ML with x
+                        larger than the L2; see spmv_get_col_panels). Panels run rows on
+                        sub-warps of vs = 1, 2, 4 or 8 lanes with int32 columns (partition
+                        and index are set to 0); vec selects 128-bit loads               */
   int32_t vec;       /* 0: scalar loads; 1: 128-bit loads of val/colind, unrolled (MB/CMP) */
   int32_t vs;        /* sub-warp width for partition 0: 1 (thread per row over a tile
                         staged in shared memory by bulk copies), 2,4,8,16,32; 0 = heuristic */
@@ -209,6 +214,19 @@ spmv_status spmv_export_csr(spmv_handle_t h, int32_t *row_ptr, int32_t *col_ind,
  * *bits. SPMV_ERR_NOT_TUNED if no delta index has been built. */
 spmv_status spmv_get_delta(spmv_handle_t h, int32_t *base, void *delta, int32_t *esc_col,
                            int64_t *n_esc, int32_t *bits, spmv_stream_t stream);
+
+/* Copies the column-panel copy of the matrix (variant xpath = P >= 2; Section III-E, ML,
+ * with x cut into P slices that each fit in the L2): panel p holds the columns
+ * [p * w, (p + 1) * w), w = *panel_cols = ceil(n_cols / P) rounded up to a multiple of 32
+ * (trailing panels may be empty). panel_rowptr (device, int32[P * (n_rows + 1)]) holds
+ * each panel's row pointers, absolute positions into panel_col (device, int32[nnz]) and
+ * panel_val (device, nnz values of the storage dtype; FP64 for SPMV_DF64 storage), which
+ * list panel 0's nonzeros row by row, then panel 1's, and so on, columns in row order.
+ * Any of the three arrays may be NULL; all NULL queries *n_panels and *panel_cols.
+ * SPMV_ERR_NOT_TUNED if no panel copy has been built. */
+spmv_status spmv_get_col_panels(spmv_handle_t h, int32_t *panel_rowptr, int32_t *panel_col,
+                                void *panel_val, int32_t *n_panels, int32_t *panel_cols,
+                                spmv_stream_t stream);
 
 /* Copies the merge-path tile table (rows ended, nonzeros consumed) for tile boundaries
  * 0..n_tiles into coord (device, int32[2 * (n_tiles + 1)]); pass coord = NULL to query

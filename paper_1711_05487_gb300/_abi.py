@@ -105,6 +105,8 @@ _DECL = {
     "spmv_get_delta": (_I32, [_P, _P, _P, _P, ctypes.POINTER(_I64), ctypes.POINTER(_I32), _P]),
     "spmv_get_merge_path": (_I32, [_P, _P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P]),
     "spmv_get_row_bins": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
+    "spmv_get_col_panels": (_I32, [_P, _P, _P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
+                                   _P]),
     "spmv_features": (_I32, [_P, _I32, _P, _P, _P]),
     "spmv_profile": (_I32, [_P, _I32, ctypes.POINTER(spmv_profile_report), _P]),
     "spmv_profile_cta_times": (_I32, [_P, _P, _P, ctypes.POINTER(_I32), _P]),
@@ -241,6 +243,14 @@ def spmv_get_row_bins(h, med_rows=None, long_rows=None, long_first=None, chunks=
     _call("spmv_get_row_bins", h, med_rows, long_rows, long_first, chunks,
           ctypes.cast(counts, _P), stream)
     return int(counts[0]), int(counts[1]), int(counts[2])
+
+
+def spmv_get_col_panels(h, panel_rowptr=None, panel_col=None, panel_val=None, stream=0):
+    """Returns (n_panels, panel_cols); copies the panel copy when the pointers are given."""
+    n, w = _I32(), _I32()
+    _call("spmv_get_col_panels", h, panel_rowptr, panel_col, panel_val, ctypes.byref(n),
+          ctypes.byref(w), stream)
+    return n.value, w.value
 
 
 def spmv_get_merge_path(h, coord=None, stream=0):

@@ -228,7 +228,8 @@ class SpmvMatrix:
 
     def row_bins(self, device="cuda", stream=None):
         """The row decomposition (partition 2): medium rows, long rows, each long row's first
-        chunk, and the chunk table (row, first nonzero, end nonzero, 0)."""
+        chunk, and the chunk table (row, first nonzero, end nonzero, the column a delta
+        decode of the chunk starts from)."""
         n_med, n_long, n_ch = _abi.spmv_get_row_bins(self._h)
         med = torch.empty(max(n_med, 1), dtype=torch.int32, device=device)
         lng = torch.empty(max(n_long, 1), dtype=torch.int32, device=device)
@@ -237,6 +238,17 @@ class SpmvMatrix:
         _abi.spmv_get_row_bins(self._h, med.data_ptr(), lng.data_ptr(), first.data_ptr(),
                                ch.data_ptr(), _stream(stream))
         return med[:n_med], lng[:n_long], first, ch[:n_ch]
+
+    def col_panels(self, device="cuda", stream=None):
+        """The column-panel copy (variant xpath = P >= 2): (row pointers (P, n_rows + 1),
+        columns, values, panel width)."""
+        n_p, w = _abi.spmv_get_col_panels(self._h)
+        rp = torch.empty((n_p, self.n_rows + 1), dtype=torch.int32, device=device)
+        ci = torch.empty(max(self.nnz, 1), dtype=torch.int32, device=device)
+        v = torch.empty(max(self.nnz, 1), dtype=TORCH_DTYPE[self.storage], device=device)
+        _abi.spmv_get_col_panels(self._h, rp.data_ptr(), ci.data_ptr(), v.data_ptr(),
+                                 _stream(stream))
+        return rp, ci[:self.nnz], v[:self.nnz], w
 
     def merge_path(self, device="cuda", stream=None):
         n_tiles, items = _abi.spmv_get_merge_path(self._h)

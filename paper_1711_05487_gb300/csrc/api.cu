@@ -27,6 +27,7 @@ void default_types(spmv_dtype in, spmv_dtype *st, spmv_dtype *vec, spmv_dtype *a
 void install_storage(spmv_matrix *h, cudaStream_t s) {
   h->val_store.release();
   h->val_df.release();
+  drop_panels(h);   // the panel copy holds values of the previous storage dtype
   if (h->storage == SPMV_DF64) {
     // the FP64 input values stay the values of every non-double-float kernel
     h->val_df.alloc(8 * (size_t)h->nnz, 8, s);
@@ -260,6 +261,30 @@ spmv_status spmv_get_row_bins(spmv_handle_t h, int32_t *med_rows, int32_t *long_
   });
 }
 
+spmv_status spmv_get_col_panels(spmv_handle_t h, int32_t *panel_rowptr, int32_t *panel_col,
+                                void *panel_val, int32_t *n_panels, int32_t *panel_cols,
+                                spmv_stream_t stream) {
+  if (!h || !n_panels || !panel_cols) return SPMV_ERR_ARG;
+  if (h->pnl_count == 0) return SPMV_ERR_NOT_TUNED;
+  *n_panels = h->pnl_count;
+  *panel_cols = h->pnl_width;
+  if (!panel_rowptr && !panel_col && !panel_val) return SPMV_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return guarded([&]() -> spmv_status {
+    const size_t vb = h->storage == SPMV_DF64 ? 8 : dtype_bytes(h->storage);
+    if (panel_rowptr)
+      CK(cudaMemcpyAsync(panel_rowptr, h->pnl_rowptr.p,
+                         4 * (size_t)h->pnl_count * (size_t)(h->n_rows + 1),
+                         cudaMemcpyDeviceToDevice, s));
+    if (panel_col && h->nnz)
+      CK(cudaMemcpyAsync(panel_col, h->pnl_col.p, 4 * (size_t)h->nnz, cudaMemcpyDeviceToDevice, s));
+    if (panel_val && h->nnz)
+      CK(cudaMemcpyAsync(panel_val, h->pnl_val.p, vb * (size_t)h->nnz, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return SPMV_OK;
+  });
+}
+
 spmv_status spmv_get_merge_path(spmv_handle_t h, int32_t *coord, int64_t *n_tiles,
                                 int64_t *items_per_tile, spmv_stream_t stream) {
   if (!h || !n_tiles || !items_per_tile) return SPMV_ERR_ARG;
@@ -329,7 +354,9 @@ spmv_status spmv_get_device_bytes(spmv_handle_t h, int64_t *bytes) {
   int64_t t = 0;
   for (const DevBuf *b : {&h->rowptr, &h->colind, &h->val_in, &h->val_store, &h->dbase, &h->delta,
                           &h->esc, &h->coord, &h->tail_row, &h->tail_val, &h->head_val,
-                          &h->x_stage, &h->y_stage, &h->scratch})
+                          &h->x_stage, &h->y_stage, &h->scratch, &h->val_df, &h->bin_rows,
+                          &h->bin_long_rows, &h->bin_long_first, &h->bin_chunks,
+                          &h->bin_partials, &h->pnl_rowptr, &h->pnl_col, &h->pnl_val})
     t += (int64_t)b->bytes;
   *bytes = t;
   return SPMV_OK;

@@ -155,6 +155,9 @@ struct spmv_matrix {
   int64_t bin_n_med = 0, bin_n_long = 0, bin_n_chunks = 0;
   int32_t bin_vs_short = 4;
   bool has_bins = false;
+  DevBuf pnl_rowptr, pnl_col, pnl_val;   // column panels: panel-major copy of the matrix
+  int32_t pnl_count = 0;       // panels of the built copy (0: none)
+  int32_t pnl_width = 0;       // columns per panel
   // run state
   spmv_variant variant{};
   bool tuned = false;
@@ -212,6 +215,8 @@ bool valid_variant(const spmv_variant &v);
 // One launch of variant v on device buffers x and y.
 cudaError_t launch_run(const spmv_matrix *h, const spmv_variant &v, const void *x, void *y,
                        cudaStream_t s);
+// Frees the column-panel copy (its values follow the storage dtype).
+void drop_panels(spmv_matrix *h);
 // Frees the captured host-buffer pipeline.
 void drop_host_graph(spmv_matrix *h);
 

@@ -59,7 +59,8 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
     }
     // pipelining pays once the copies take longer than a few chunk launches (x and y of at
     // least 8 MB together)
-    const bool chunked = h->variant.partition == 0 && h->n_rows >= 4 * kHostChunks * kTileRows &&
+    const bool chunked = h->variant.partition == 0 && h->variant.xpath < 2 &&
+                         h->n_rows >= 4 * kHostChunks * kTileRows &&
                          (int64_t)vb * (h->n_rows + h->n_cols) >= 8000000;
     const int nch = chunked ? kHostChunks : 1;
     // chunk row boundaries: equal parts aligned to 128 rows
@@ -90,7 +91,8 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
     // its piece, and each finished chunk of y is downloaded on another stream. Consecutive
     // chunks' kernels go to two alternating streams, so one chunk's last partial wave of CTAs
     // overlaps the next chunk's first; all side streams join back into `origin` at the end.
-    // Merge-path tiles span the whole matrix: one upload, one launch, one download.
+    // Merge-path tiles and column panels span the whole matrix: one upload, one run, one
+    // download.
     const KernelSet *ks = set_for(h);
     auto enqueue = [&](cudaStream_t origin) {
       cudaStream_t side[4] = {h->upload_stream, h->copy_stream, h->chunk_stream[0],

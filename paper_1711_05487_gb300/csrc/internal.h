@@ -65,7 +65,16 @@ struct RunArgs {
   const int32_t *bin_long_first = nullptr;
   int64_t bin_n_long = 0;
   double *bin_partials = nullptr;
+  // column panels (xpath >= 2): a panel-major copy of the matrix; panel p's row pointers
+  // are pnl_rowptr + p * (n_rows + 1), absolute positions into pnl_col / pnl_val
+  const int32_t *pnl_rowptr = nullptr;
+  const int32_t *pnl_col = nullptr;
+  const void *pnl_val = nullptr;
+  int32_t n_panels = 0;
 };
+
+// Column panels: at most this many slices of x (variant field xpath = panel count).
+constexpr int kMaxPanels = 16;
 
 // Row decomposition thresholds: rows of at least kBinMed nonzeros get a warp; rows of at
 // least kBinChunk nonzeros are split into chunks of kBinChunk nonzeros.
@@ -211,6 +220,17 @@ cudaError_t launch_bin_fill(int64_t n_rows, const int32_t *rowptr, const int32_t
                             const int64_t *lng_off, const int64_t *nch_off, int32_t *bin_rows,
                             int32_t *long_rows, int32_t *long_first, int4 *chunks,
                             cudaStream_t s);
+
+// Column panels of width w (panel p = columns [p*w, (p+1)*w), the last panel takes the rest):
+// the nonzero count of every row in every panel ([n_panels][n_rows + 1] int64, for the
+// scans), then the panel-major copy of the columns and values (val_bytes 2, 4 or 8) and
+// each panel's row pointers ([n_panels][n_rows + 1] int32), from the scanned counts.
+cudaError_t launch_panel_counts(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                                int32_t n_panels, int32_t width, int64_t *cnt, cudaStream_t s);
+cudaError_t launch_panel_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                              const void *val, int val_bytes, int32_t n_panels,
+                              const int64_t *off, int32_t *pnl_rowptr, int32_t *pnl_col,
+                              void *pnl_val, cudaStream_t s);
 
 // Largest column of each row chunk (host-buffer pipelining)
 cudaError_t launch_chunk_colmax(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,

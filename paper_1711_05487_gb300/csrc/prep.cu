@@ -729,4 +729,92 @@ cudaError_t launch_bin_fill(int64_t n_rows, const int32_t *rowptr, const int32_t
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ column panels ----
+// Thread per row: the row's columns are sorted, so its part in panel b starts at the first
+// column >= b * width (binary search between the previous boundary and the row's end).
+__global__ void k_panel_counts(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                               int32_t n_panels, int32_t width, int64_t *cnt) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  const int e = rowptr[r + 1];
+  int prev = rowptr[r];
+  for (int b = 1; b < n_panels; ++b) {
+    const int64_t target = (int64_t)b * width;
+    int lo = prev, hi = e;
+    while (lo < hi) {
+      const int mid = lo + ((hi - lo) >> 1);
+      if ((int64_t)colind[mid] < target) lo = mid + 1;
+      else hi = mid;
+    }
+    cnt[(int64_t)(b - 1) * (n_rows + 1) + r] = lo - prev;
+    prev = lo;
+  }
+  cnt[(int64_t)(n_panels - 1) * (n_rows + 1) + r] = e - prev;
+}
+
+// Warp per row (warp n_rows writes the panels' end pointers): the row's panel-p part is
+// copied to panel p's base (the totals of the panels before it) plus the row's scanned
+// offset in panel p.
+template <typename T>
+__global__ void k_panel_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                             const T *val, int32_t n_panels, const int64_t *off,
+                             int32_t *pnl_rowptr, int32_t *pnl_col, T *pnl_val) {
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r > n_rows) return;
+  const int64_t stride = n_rows + 1;
+  int64_t base = 0;
+  int src = r < n_rows ? rowptr[r] : 0;
+  for (int p = 0; p < n_panels; ++p) {
+    const int64_t *o = off + (int64_t)p * stride;
+    const int64_t dst = base + o[r];
+    if (lane == 0) pnl_rowptr[(int64_t)p * stride + r] = (int32_t)dst;
+    if (r < n_rows) {
+      const int c = (int)(o[r + 1] - o[r]);
+      for (int k = lane; k < c; k += 32) {
+        pnl_col[dst + k] = colind[src + k];
+        pnl_val[dst + k] = val[src + k];
+      }
+      src += c;
+    }
+    base += o[n_rows];
+  }
+}
+
+cudaError_t launch_panel_counts(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                                int32_t n_panels, int32_t width, int64_t *cnt, cudaStream_t s) {
+  if (n_rows <= 0) return cudaSuccess;
+  k_panel_counts<<<blocks_for(n_rows), kT, 0, s>>>(n_rows, rowptr, colind, n_panels, width,
+                                                     cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_panel_fill(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,
+                              const void *val, int val_bytes, int32_t n_panels,
+                              const int64_t *off, int32_t *pnl_rowptr, int32_t *pnl_col,
+                              void *pnl_val, cudaStream_t s) {
+  if (n_rows < 0) return cudaErrorInvalidValue;
+  const unsigned g = blocks_for((n_rows + 1) * 32);
+  switch (val_bytes) {
+    case 8:
+      k_panel_fill<uint64_t><<<g, kT, 0, s>>>(n_rows, rowptr, colind,
+                                              static_cast<const uint64_t *>(val), n_panels, off,
+                                              pnl_rowptr, pnl_col, static_cast<uint64_t *>(pnl_val));
+      break;
+    case 4:
+      k_panel_fill<uint32_t><<<g, kT, 0, s>>>(n_rows, rowptr, colind,
+                                              static_cast<const uint32_t *>(val), n_panels, off,
+                                              pnl_rowptr, pnl_col, static_cast<uint32_t *>(pnl_val));
+      break;
+    case 2:
+      k_panel_fill<uint16_t><<<g, kT, 0, s>>>(n_rows, rowptr, colind,
+                                              static_cast<const uint16_t *>(val), n_panels, off,
+                                              pnl_rowptr, pnl_col, static_cast<uint16_t *>(pnl_val));
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace spmv

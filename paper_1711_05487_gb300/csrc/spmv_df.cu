@@ -216,10 +216,12 @@ template <int DB, bool XL2> cudaError_t launch_rowtile_df_k(const RunArgs &a, cu
 }
 
 // Width-1 row variants run the double-float tile kernel (one tile per CTA, whatever
-// tile_pipe says); every other variant runs the native FP64 kernels on the FP64 values.
+// tile_pipe says); every other variant (column panels included) runs the native FP64
+// kernels on the FP64 values.
 cudaError_t launch_spmv_df(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
-  if (v.partition != 0 || v.vs != 1) return kernel_set_f64_dd()->spmv(v, a, s);
+  if (v.partition != 0 || v.vs != 1 || v.xpath >= 2)
+    return kernel_set_f64_dd()->spmv(v, a, s);
   const bool xl2 = v.xpath != 0;
   if (v.index == 1 && a.delta_bits == 8)
     return xl2 ? launch_rowtile_df_k<8, true>(a, s) : launch_rowtile_df_k<8, false>(a, s);

@@ -9,6 +9,8 @@
 //  k_rowtile - thread-per-row tiles staged by TMA bulk copies (spmv_tile.cuh).
 //  k_bins_*  - row decomposition: short rows by sub-warps, medium rows by warps, long rows
 //              split into chunks with a fixed-order FP64 fixup (IMB).
+//  k_panel   - one pass of the column-panel variant (ML, x larger than the L2): the rows'
+//              nonzeros in one L2-sized slice of x, from a panel-major copy of the matrix.
 //  k_merge   - merge-path tiles of equal (rows + nonzeros) work; rows longer than a tile
 //              are split over tiles and finished by k_merge_fixup (IMB: the decomposition
 //              of Fig. 4/5, long rows computed by many workers with a reduction).
@@ -211,6 +213,83 @@ __global__ void __launch_bounds__(kRowThreads) k_rowvec(const RunArgs a) {
   }
   sum = group_sum<VS>(sum, mask);
   if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)sum;
+}
+
+// ------------------------------------------------------------------------- k_panel ----
+// One streamed element of 4, 8 or 2 bytes: evict-first in L2, kept in L1 (the lanes of a
+// thread-per-row warp read neighbouring parts of the same sectors).
+__device__ __forceinline__ int32_t ld_stream_1(const int32_t *p, uint64_t pol) {
+  int32_t r;
+  asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;"
+               : "=r"(r) : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ double ld_stream_1(const double *p, uint64_t pol) {
+  double r;
+  asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;"
+               : "=d"(r) : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ float ld_stream_1(const float *p, uint64_t pol) {
+  float r;
+  asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;"
+               : "=f"(r) : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ __nv_bfloat16 ld_stream_1(const __nv_bfloat16 *p, uint64_t pol) {
+  unsigned short r;
+  asm volatile("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;"
+               : "=h"(r) : "l"(p), "l"(pol));
+  return __ushort_as_bfloat16(r);
+}
+
+
+// One pass of the column-panel variant (ML with x larger than the L2). The matrix is held
+// panel-major: panel p holds the nonzeros whose columns fall in the p-th slice of x, as a
+// CSR of its own with the rows in order. Pass p computes every row's sum over panel p, so
+// one pass gathers from one L2-sized slice of x (evict-last) while its panel streams past
+// (evict-first); pass 0 writes y, later passes add to it.
+template <typename ValT, typename VecT, typename AccT, int VS, bool VEC>
+__global__ void __launch_bounds__(kRowThreads) k_panel(const RunArgs a,
+                                                       const int32_t *__restrict__ prow,
+                                                       int add) {
+  constexpr int GROUPS = kRowThreads / VS;
+  const int lane = threadIdx.x & (VS - 1);
+  const int64_t row = (int64_t)blockIdx.x * GROUPS + threadIdx.x / VS;
+  if (row >= a.n_rows) return;  // the whole sub-warp leaves together
+  const unsigned mask = group_mask<VS>();
+  const uint64_t pol_s = policy_evict_first(), pol_x = policy_evict_last();
+  const int s = __ldg(prow + row), e = __ldg(prow + row + 1);
+  AccT sum = 0;
+  if constexpr (VEC) {
+    sum = vec_range_dot<ValT, VecT, AccT, VS, true>(a, s, e, lane, pol_s, pol_x);
+  } else {
+    // four of the lane's nonzeros per step: their columns and values are loaded first
+    // (evict-first), then their four x gathers are in flight together
+    const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
+    const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
+    for (int j0 = s + lane; j0 < e; j0 += 4 * VS) {
+      int c[4];
+      ValT v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = j0 + q * VS;
+        c[q] = j < e ? ld_stream_1(a.colind + j, pol_s) : -1;
+        v[q] = j < e ? ld_stream_1(val + j, pol_s) : ValT(0);
+      }
+      AccT xv[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) xv[q] = c[q] >= 0 ? (AccT)ldx<true>(x + c[q], pol_x) : AccT(0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c[q] >= 0) sum += widen<AccT>(v[q]) * xv[q];
+    }
+  }
+  sum = group_sum<VS>(sum, mask);
+  if (lane == 0) {
+    VecT *y = static_cast<VecT *>(a.y);
+    y[row] = add ? (VecT)((AccT)y[row] + sum) : (VecT)sum;
+  }
 }
 
 // ------------------------------------------------------------------------- k_merge ----
@@ -637,9 +716,37 @@ cudaError_t launch_rowvec_vs(const spmv_variant &v, const RunArgs &a, cudaStream
   return cudaGetLastError();
 }
 
+// The column-panel variant: one launch per panel, in panel order on one stream.
+template <typename ValT, typename VecT, typename AccT, int VS>
+cudaError_t launch_panels_vs(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
+  RunArgs pa = a;
+  pa.colind = a.pnl_col;
+  pa.val = a.pnl_val;
+  const unsigned g = grid_for_rows(a.n_rows, VS);
+  for (int p = 0; p < a.n_panels; ++p) {
+    const int32_t *prow = a.pnl_rowptr + (int64_t)p * (a.n_rows + 1);
+    if (v.vec) k_panel<ValT, VecT, AccT, VS, true><<<g, kRowThreads, 0, s>>>(pa, prow, p > 0);
+    else k_panel<ValT, VecT, AccT, VS, false><<<g, kRowThreads, 0, s>>>(pa, prow, p > 0);
+  }
+  return cudaGetLastError();
+}
+
+template <typename ValT, typename VecT, typename AccT>
+cudaError_t launch_panels(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
+  if (a.n_panels != v.xpath || !a.pnl_rowptr) return cudaErrorInvalidValue;
+  switch (v.vs) {
+    case 1: return launch_panels_vs<ValT, VecT, AccT, 1>(v, a, s);
+    case 2: return launch_panels_vs<ValT, VecT, AccT, 2>(v, a, s);
+    case 4: return launch_panels_vs<ValT, VecT, AccT, 4>(v, a, s);
+    case 8: return launch_panels_vs<ValT, VecT, AccT, 8>(v, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename ValT, typename VecT, typename AccT>
 cudaError_t launch_spmv_impl(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
+  if (v.xpath >= 2) return launch_panels<ValT, VecT, AccT>(v, a, s);
   if (v.partition == 2)
     return launch_bins<ValT, VecT, AccT>(v.index == 1 ? a.delta_bits : 0, v.xpath != 0, a, s);
   if (v.partition == 1) {

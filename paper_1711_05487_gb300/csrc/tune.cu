@@ -391,11 +391,53 @@ void run_profile(spmv_matrix *h, int reps, spmv_profile_report &o, cudaStream_t 
   }
 }
 
+// Column panels compete when the matrix is ML (v.xpath = 1) and x is larger than half the
+// L2: panel counts that cut x into slices of a half, a third and a quarter of the L2, each
+// with sub-warps of 1, 2, 4 and 8 lanes and scalar or 128-bit loads. The fastest replaces v
+// when it beats `best` (the time of v); otherwise the panel copy is freed.
+void sweep_panels(spmv_matrix *h, spmv_variant &v, float best, const void *x, void *y,
+                  int reps, cudaStream_t s) {
+  const DeviceInfo &d = device_info(h->device);
+  const double xb = (double)dtype_bytes(h->vec) * (double)h->n_cols;
+  if (v.xpath != 1 || d.l2_bytes <= 0 || xb <= 0.5 * (double)d.l2_bytes) return;
+  spmv_variant best_v = v;
+  bool found = false;
+  int last_p = 0;
+  for (int f = 2; f <= 4; ++f) {
+    const int p = std::min(kMaxPanels,
+                           std::max(2, (int)std::ceil(xb * f / (double)d.l2_bytes)));
+    if (p == last_p) continue;
+    last_p = p;
+    for (int w : {1, 2, 4, 8}) {
+      for (int vec = 0; vec <= 1; ++vec) {
+        spmv_variant t = v;
+        t.xpath = p;
+        t.vs = w;
+        t.vec = vec;
+        prepare_variant(h, t, s);
+        const float ms = time_launches([&]() { return launch_run(h, t, x, y, s); }, reps, s);
+        if (ms < best) {
+          best = ms;
+          best_v = t;
+          found = true;
+        }
+      }
+    }
+  }
+  if (found) {
+    v = best_v;
+    prepare_variant(h, v, s);
+  } else {
+    drop_panels(h);
+  }
+}
+
 // Sub-warp width sweep by timing (Section III-E "parameter tuning"; build addition). When
 // the thread-per-row kernel (width 1) wins, its geometry is swept too: 128 / 64 / 32 rows
 // per tile, one tile per CTA or persistent CTAs with two tiles in flight.
 // Called by spmv_tune for the routes that choose a variant (never for SPMV_TUNE_FIXED), so
-// the sub-warp width and, for width 1, the tile geometry are always swept.
+// the sub-warp width and, for width 1, the tile geometry are always swept; ML matrices
+// whose x exceeds half the L2 then try column panels (sweep_panels).
 void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, cudaStream_t s) {
   if (h->n_rows == 0) return;
   const size_t vb = dtype_bytes(h->vec);
@@ -441,27 +483,28 @@ void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, cudaStream_t s) {
   if (best_vs != 1) {
     v.tile_rows = 0;
     v.tile_pipe = 0;
-    return;
-  }
-  int best_rows = h->tile_rows, best_pipe = h->tile_pipe, best_cap = h->tile_cap;
-  const int max_pipe = h->storage == SPMV_DF64 ? 0 : 1;
-  for (int pipe = 0; pipe <= max_pipe; ++pipe) {
-    for (int rows = kTileRows; rows >= 32; rows /= 2) {
-      set_tile_geometry(h, v, rows, pipe != 0, s);
-      const float ms = time_launches([&]() { return launch_run(h, v, x.p, y.p, s); }, reps, s);
-      if (ms < best) {
-        best = ms;
-        best_rows = rows;
-        best_pipe = pipe;
-        best_cap = h->tile_cap;
+  } else {
+    int best_rows = h->tile_rows, best_pipe = h->tile_pipe, best_cap = h->tile_cap;
+    const int max_pipe = h->storage == SPMV_DF64 ? 0 : 1;
+    for (int pipe = 0; pipe <= max_pipe; ++pipe) {
+      for (int rows = kTileRows; rows >= 32; rows /= 2) {
+        set_tile_geometry(h, v, rows, pipe != 0, s);
+        const float ms = time_launches([&]() { return launch_run(h, v, x.p, y.p, s); }, reps, s);
+        if (ms < best) {
+          best = ms;
+          best_rows = rows;
+          best_pipe = pipe;
+          best_cap = h->tile_cap;
+        }
       }
     }
+    h->tile_rows = best_rows;
+    h->tile_pipe = best_pipe;
+    h->tile_cap = best_cap;
+    v.tile_rows = best_rows;
+    v.tile_pipe = best_pipe;
   }
-  h->tile_rows = best_rows;
-  h->tile_pipe = best_pipe;
-  h->tile_cap = best_cap;
-  v.tile_rows = best_rows;
-  v.tile_pipe = best_pipe;
+  sweep_panels(h, v, best, x.p, y.p, reps, s);
 }
 
 }  // namespace

@@ -44,6 +44,10 @@ RunArgs run_args(const spmv_matrix *h, const void *x, void *y) {
   a.bin_long_first = h->bin_long_first.as<int32_t>();
   a.bin_n_long = h->bin_n_long;
   a.bin_partials = h->bin_partials.as<double>();
+  a.pnl_rowptr = h->pnl_rowptr.as<int32_t>();
+  a.pnl_col = h->pnl_col.as<int32_t>();
+  a.pnl_val = h->pnl_val.p;
+  a.n_panels = h->pnl_count;
   return a;
 }
 
@@ -138,6 +142,40 @@ void build_bins(spmv_matrix *h, cudaStream_t s) {
   h->has_bins = true;
 }
 
+// Column panels (xpath = P >= 2): the panel-major copy of the columns and of the values
+// the kernels read (the storage copy, or the FP64 input for double-float storage), built
+// from per-row panel counts and one exclusive scan per panel. Panel p holds the columns
+// [p*w, (p+1)*w), w = ceil(n_cols / P) rounded up to a multiple of 32.
+void build_panels(spmv_matrix *h, int n_panels, cudaStream_t s) {
+  if (h->pnl_count == n_panels) return;
+  drop_panels(h);
+  const int64_t n = h->n_rows;
+  int64_t w = (h->n_cols + n_panels - 1) / n_panels;
+  w = std::max<int64_t>(32, (w + 31) / 32 * 32);
+  DevBuf cnt;
+  cnt.alloc(sizeof(int64_t) * (size_t)n_panels * (size_t)(n + 1), 8, s, true);
+  int64_t *c = cnt.as<int64_t>();
+  CK(launch_panel_counts(n, h->rowptr.as<int32_t>(), h->colind.as<int32_t>(), n_panels,
+                         (int32_t)w, c, s));
+  const int64_t se = scan_scratch_elems(n);
+  DevBuf scr;
+  scr.alloc(sizeof(int64_t) * (size_t)se, 8, s);
+  for (int p = 0; p < n_panels; ++p) {
+    int64_t *cp = c + (int64_t)p * (n + 1);
+    CK(launch_scan_i64(cp, n, cp + n, scr.as<int64_t>(), se, s));
+  }
+  const size_t vb = h->storage == SPMV_DF64 ? 8 : dtype_bytes(h->storage);
+  h->pnl_rowptr.alloc(4 * (size_t)n_panels * (size_t)(n + 1), 4, s);
+  h->pnl_col.alloc(4 * (size_t)h->nnz, 4, s);
+  h->pnl_val.alloc(vb * (size_t)h->nnz, vb, s);
+  CK(launch_panel_fill(n, h->rowptr.as<int32_t>(), h->colind.as<int32_t>(), h->val_ptr(),
+                       (int)vb, n_panels, c, h->pnl_rowptr.as<int32_t>(),
+                       h->pnl_col.as<int32_t>(), h->pnl_val.p, s));
+  CK(cudaStreamSynchronize(s));
+  h->pnl_count = n_panels;
+  h->pnl_width = (int32_t)w;
+}
+
 // Geometry of the thread-per-row kernel. A staged tile holds the values and columns of
 // `rows` consecutive rows; the staged capacity is the matrix's largest such tile, capped by
 // the shared-memory budget of one stage (48 KB for one tile per CTA, 56 KB per stage for
@@ -190,7 +228,25 @@ void compute_tile_cap(spmv_matrix *h, const spmv_variant &v, cudaStream_t s) {
   set_tile_geometry(h, v, kTileRows, false, s);
 }
 
+void drop_panels(spmv_matrix *h) {
+  h->pnl_rowptr.release();
+  h->pnl_col.release();
+  h->pnl_val.release();
+  h->pnl_count = 0;
+  h->pnl_width = 0;
+}
+
 void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
+  if (v.xpath >= 2) {
+    // column panels: rows on sub-warps of vs lanes over each panel's CSR, int32 columns
+    v.partition = 0;
+    v.index = 0;
+    v.tile_rows = 0;
+    v.tile_pipe = 0;
+    if (v.vs == 0) v.vs = std::min(8, pow2_ceil_clamped(h->nnz_avg() / v.xpath, 1, 8));
+    build_panels(h, v.xpath, s);
+    return;
+  }
   if (v.partition == 1) {
     v.index = 0;                 // the delta index is built for sub-warp rows only
     build_merge(h, s);
@@ -232,7 +288,9 @@ bool valid_variant(const spmv_variant &v) {
   if (v.partition < 0 || v.partition > 2) return false;
   if (v.partition == 2 && v.vs != 0 && v.vs != 2 && v.vs != 4 && v.vs != 8) return false;
   if (v.index != 0 && v.index != 1) return false;
-  if (v.xpath != 0 && v.xpath != 1) return false;
+  if (v.xpath < 0 || v.xpath > kMaxPanels) return false;
+  if (v.xpath >= 2 && v.vs != 0 && v.vs != 1 && v.vs != 2 && v.vs != 4 && v.vs != 8)
+    return false;
   if (v.vec != 0 && v.vec != 1) return false;
   if (v.partition == 0 && v.vs != 0 && v.vs != 1 && v.vs != 2 && v.vs != 4 && v.vs != 8 &&
       v.vs != 16 && v.vs != 32)
