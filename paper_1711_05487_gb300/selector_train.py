@@ -228,8 +228,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--count", type=int, default=2000)
     ap.add_argument("--seed", type=int, default=171105487 + 40)
-    ap.add_argument("--n-lo", type=int, default=10_000)
-    ap.add_argument("--n-hi", type=int, default=1_000_000)
+    ap.add_argument("--n-lo", type=int, default=1_000)
+    ap.add_argument("--n-hi", type=int, default=4_000_000)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--train-frac", type=float, default=0.8)
