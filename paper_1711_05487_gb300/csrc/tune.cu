@@ -392,9 +392,10 @@ void run_profile(spmv_matrix *h, int reps, spmv_profile_report &o, cudaStream_t 
 }
 
 // Column panels compete when the matrix is ML (v.xpath = 1) and x is larger than half the
-// L2: panel counts that cut x into slices of a half, a third and a quarter of the L2, each
-// with sub-warps of 1, 2, 4 and 8 lanes and scalar or 128-bit loads. The fastest replaces v
-// when it beats `best` (the time of v); otherwise the panel copy is freed.
+// L2: panel counts that cut x into slices of a half and a third of the L2, each with
+// sub-warps of 1 lane up to the width that covers a row's average share of one panel (at
+// most 8), scalar or 128-bit loads. The fastest replaces v when it beats `best` (the time of
+// v); otherwise the panel copy is freed.
 void sweep_panels(spmv_matrix *h, spmv_variant &v, float best, const void *x, void *y,
                   int reps, cudaStream_t s) {
   const DeviceInfo &d = device_info(h->device);
@@ -403,12 +404,13 @@ void sweep_panels(spmv_matrix *h, spmv_variant &v, float best, const void *x, vo
   spmv_variant best_v = v;
   bool found = false;
   int last_p = 0;
-  for (int f = 2; f <= 4; ++f) {
+  for (int f = 2; f <= 3; ++f) {
     const int p = std::min(kMaxPanels,
                            std::max(2, (int)std::ceil(xb * f / (double)d.l2_bytes)));
     if (p == last_p) continue;
     last_p = p;
-    for (int w : {1, 2, 4, 8}) {
+    const int w_max = pow2_ceil_clamped(h->nnz_avg() / p, 1, 8);
+    for (int w = 1; w <= w_max; w *= 2) {
       for (int vec = 0; vec <= 1; ++vec) {
         spmv_variant t = v;
         t.xpath = p;
