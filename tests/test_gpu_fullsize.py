@@ -84,13 +84,13 @@ def test_scattered_16m_tuned(api, torch):
     A = api.SpmvMatrix.from_csr(m)
     rep = A.tune("profile")
     # x (128 MB) exceeds the L2: the ML class's column panels beat every single-pass variant
-    assert rep.variant.xpath >= 2, rep.variant
+    assert rep.variant[2] >= 2, rep.variant
     x64 = synth.uniform_vector(m.n_cols, synth.SEED_BASE + 14)
     y = A.run(torch.from_numpy(x64).cuda()).cpu().numpy()
     _check_sampled(m, x64, y, m.val, TAU["f64"], f"scattered 16M {rep.variant}")
     # the panel copy of the full-size matrix equals the oracle's on a sample of rows
     prow, pcol, pval, w = (t.cpu().numpy() if hasattr(t, "cpu") else t for t in A.col_panels())
-    P = rep.variant.xpath
+    P = rep.variant[2]
     assert w == oracle.panel_width(m.n_cols, P)
     for r in _sample_rows(m, n_random=2000, n_long=1, seed=5):
         s, e = m.rowptr[r], m.rowptr[r + 1]
