@@ -291,6 +291,11 @@ def run_ours(args, rank, world):
             amort[route] = {"t_pre_ms": round(r_l.t_pre_ms, 2), "t_spmv_ms": round(t_l, 5),
                             "classes": r_l.class_names, "variant": list(r_l.variant),
                             "n_iters_min": n_iters(r_l.t_pre_ms, t_l)}
+            if route == "learned":
+                # margin -1: the matrix lies outside the selector's training range and the
+                # route profiled it instead
+                amort[route]["decided_by"] = ("mlp" if r_l.mode_used == 2 else "profile")
+                amort[route]["margin"] = round(r_l.margin, 4)
         # Section IV-D's trivial optimizers: try every single optimization (5) or also every
         # pair of them (15 in all), 64 timed SpMVs each, keep the fastest; t_pre is the whole
         # search including each candidate's preprocessing

@@ -105,7 +105,9 @@ typedef struct {
   int32_t reps;          /* timed repetitions per probe (default 8; the autotuner half) */
   spmv_variant fixed;    /* SPMV_TUNE_FIXED only                                         */
   spmv_selector_t selector; /* SPMV_TUNE_LEARNED only                                    */
-  double min_margin;     /* learned: smallest |logit| accepted, else profile (default 0) */
+  double min_margin;     /* learned: smallest |logit| accepted, else profile (default 0); a
+                            matrix outside the selector's training range (margin -1) always
+                            falls back to profiling                                       */
   int32_t second_pass;   /* profile: re-profile after the CMP optimization (default 1)   */
 } spmv_tune_opts;
 
@@ -453,8 +455,17 @@ spmv_status spmv_selector_create(spmv_selector_t *out, const int32_t *sizes,
                                  const float *inv_sigma);
 spmv_status spmv_selector_destroy(spmv_selector_t s);
 
+/* The training range of the selector's inputs: lo and hi (host, SPMV_MLP_INPUTS floats
+ * each, in the standardized input space, copied) bound every input over the training set.
+ * Afterwards spmv_selector_predict reports *margin = -1 for a feature vector any of whose
+ * inputs lies more than `slack` outside [lo, hi]: the matrix is outside the distribution the
+ * network learned from, and spmv_tune's learned route then falls back to profiling (any
+ * opts.min_margin >= 0). SPMV_ERR_ARG for null pointers, lo > hi or slack < 0. */
+spmv_status spmv_selector_set_range(spmv_selector_t s, const float *lo, const float *hi,
+                                    float slack);
+
 /* Class set predicted for a feature vector (16 doubles, host): logit > 0 per class.
- * *margin = smallest |logit|. */
+ * *margin = smallest |logit|, or -1 when a training range is set and the inputs leave it. */
 spmv_status spmv_selector_predict(spmv_selector_t s, const double *feat16, uint32_t *classes,
                                   double *margin, spmv_stream_t stream);
 

@@ -131,6 +131,7 @@ _DECL = {
     "spmv_selector_create": (_I32, [ctypes.POINTER(_P), _P, _P, _P, _P]),
     "spmv_selector_destroy": (_I32, [_P]),
     "spmv_selector_predict": (_I32, [_P, _P, ctypes.POINTER(_U32), ctypes.POINTER(_D), _P]),
+    "spmv_selector_set_range": (_I32, [_P, _P, _P, ctypes.c_float]),
     "spmv_batch_create": (_I32, [ctypes.POINTER(_P), _P, _I32, _P, _P, _P, _P]),
     "spmv_run_batched": (_I32, [_P, _P]),
     "spmv_run_batched_sequential": (_I32, [_P, _P]),
@@ -366,6 +367,10 @@ def spmv_selector_create(sizes_host, params_host, mu_host, inv_sigma_host):
 
 def spmv_selector_destroy(s):
     _call("spmv_selector_destroy", s)
+
+
+def spmv_selector_set_range(s, lo_host, hi_host, slack):
+    _call("spmv_selector_set_range", s, lo_host, hi_host, float(slack))
 
 
 def spmv_selector_predict(s, feat16_host, stream=0):

@@ -261,18 +261,27 @@ class SpmvMatrix:
 
 
 class Selector:
-    """A learned selector (MLP weights + input standardization) on the current device."""
+    """A learned selector (MLP weights + input standardization) on the current device, with
+    the training range of its standardized inputs when known: a matrix whose inputs leave
+    that range by more than `slack` gets margin -1, and the learned route profiles it."""
 
-    def __init__(self, sizes, params, mu=None, inv_sigma=None):
+    def __init__(self, sizes, params, mu=None, inv_sigma=None, in_lo=None, in_hi=None,
+                 slack=0.5):
         self.sizes = np.ascontiguousarray(sizes, dtype=np.int32)
         self.params = np.ascontiguousarray(params, dtype=np.float32)
         self.mu = None if mu is None else np.ascontiguousarray(mu, dtype=np.float32)
         self.inv_sigma = None if inv_sigma is None else np.ascontiguousarray(inv_sigma,
                                                                              dtype=np.float32)
+        self.in_lo = None if in_lo is None else np.ascontiguousarray(in_lo, dtype=np.float32)
+        self.in_hi = None if in_hi is None else np.ascontiguousarray(in_hi, dtype=np.float32)
+        self.slack = float(slack)
         self.handle = _abi.spmv_selector_create(
             self.sizes.ctypes.data, self.params.ctypes.data,
             None if self.mu is None else self.mu.ctypes.data,
             None if self.inv_sigma is None else self.inv_sigma.ctypes.data)
+        if self.in_lo is not None and self.in_hi is not None:
+            _abi.spmv_selector_set_range(self.handle, self.in_lo.ctypes.data,
+                                         self.in_hi.ctypes.data, self.slack)
 
     def predict(self, feat16, stream=None):
         f = np.ascontiguousarray(feat16, dtype=np.float64)
@@ -290,17 +299,22 @@ class Selector:
             pass
 
     def save(self, path: str):
+        empty = np.zeros(0, np.float32)
         np.savez(path, sizes=self.sizes, params=self.params,
-                 mu=self.mu if self.mu is not None else np.zeros(0, np.float32),
-                 inv_sigma=self.inv_sigma if self.inv_sigma is not None else np.zeros(0, np.float32),
-                 version=np.array([1]))
+                 mu=self.mu if self.mu is not None else empty,
+                 inv_sigma=self.inv_sigma if self.inv_sigma is not None else empty,
+                 in_lo=self.in_lo if self.in_lo is not None else empty,
+                 in_hi=self.in_hi if self.in_hi is not None else empty,
+                 slack=np.array([self.slack], np.float32), version=np.array([2]))
 
     @classmethod
     def load(cls, path: str) -> "Selector":
         z = np.load(path)
-        mu = z["mu"] if z["mu"].size else None
-        inv = z["inv_sigma"] if z["inv_sigma"].size else None
-        return cls(z["sizes"], z["params"], mu, inv)
+        opt = {k: (z[k] if k in z.files and z[k].size else None)
+               for k in ("mu", "inv_sigma", "in_lo", "in_hi")}
+        slack = float(z["slack"][0]) if "slack" in z.files else 0.5
+        return cls(z["sizes"], z["params"], opt["mu"], opt["inv_sigma"], opt["in_lo"],
+                   opt["in_hi"], slack)
 
 
 class Batch:

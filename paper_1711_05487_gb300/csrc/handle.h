@@ -196,6 +196,9 @@ struct spmv_selector {
   DevBuf params, mu, inv_sigma;
   DevBuf ws;                   // one sample: 16 features, inputs, hidden layers, logits
   bool has_norm = false;
+  bool has_range = false;      // training range of the standardized inputs
+  float in_lo[SPMV_MLP_INPUTS] = {}, in_hi[SPMV_MLP_INPUTS] = {};
+  float in_slack = 0.0f;
 };
 
 namespace spmv {

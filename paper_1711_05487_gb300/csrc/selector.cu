@@ -107,6 +107,18 @@ spmv_status spmv_selector_destroy(spmv_selector_t sel) {
   return SPMV_OK;
 }
 
+spmv_status spmv_selector_set_range(spmv_selector_t sel, const float *lo, const float *hi,
+                                    float slack) {
+  if (!sel || !lo || !hi || !(slack >= 0.0f)) return SPMV_ERR_ARG;
+  for (int k = 0; k < SPMV_MLP_INPUTS; ++k)
+    if (!(lo[k] <= hi[k])) return SPMV_ERR_ARG;
+  std::memcpy(sel->in_lo, lo, sizeof sel->in_lo);
+  std::memcpy(sel->in_hi, hi, sizeof sel->in_hi);
+  sel->in_slack = slack;
+  sel->has_range = true;
+  return SPMV_OK;
+}
+
 spmv_status spmv_selector_predict(spmv_selector_t sel, const double *feat16, uint32_t *classes,
                                   double *margin, spmv_stream_t stream) {
   if (!sel || !feat16 || !classes) return SPMV_ERR_ARG;
@@ -123,7 +135,15 @@ spmv_status spmv_selector_predict(spmv_selector_t sel, const double *feat16, uin
     CK(launch_mlp_logits_ws(sel->sizes, sel->params.as<float>(), 1, x, lg, hid, s));
     float h[64];
     CK(cudaMemcpyAsync(h, lg, sizeof(float) * (size_t)std::min(n3, 64), cudaMemcpyDeviceToHost, s));
+    float xin[SPMV_MLP_INPUTS];
+    if (sel->has_range)
+      CK(cudaMemcpyAsync(xin, x, sizeof xin, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    bool inside = true;
+    if (sel->has_range)
+      for (int k = 0; k < SPMV_MLP_INPUTS; ++k)
+        inside = inside && xin[k] >= sel->in_lo[k] - sel->in_slack &&
+                 xin[k] <= sel->in_hi[k] + sel->in_slack;
     uint32_t c = 0;
     double mg = 1e300;
     for (int o = 0; o < n3 && o < 4; ++o) {
@@ -131,7 +151,7 @@ spmv_status spmv_selector_predict(spmv_selector_t sel, const double *feat16, uin
       mg = std::min(mg, (double)std::fabs(h[o]));
     }
     *classes = c;
-    if (margin) *margin = mg;
+    if (margin) *margin = inside ? mg : -1.0;
     return SPMV_OK;
   });
 }

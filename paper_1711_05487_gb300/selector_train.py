@@ -228,8 +228,10 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--count", type=int, default=2000)
     ap.add_argument("--seed", type=int, default=171105487 + 40)
-    ap.add_argument("--n-lo", type=int, default=1_000)
-    ap.add_argument("--n-hi", type=int, default=4_000_000)
+    ap.add_argument("--n-lo", type=int, default=10_000)
+    ap.add_argument("--n-hi", type=int, default=1_000_000)
+    ap.add_argument("--slack", type=float, default=0.5,
+                    help="standardized units an input may leave the training range by")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--train-frac", type=float, default=0.8)
@@ -274,8 +276,13 @@ def main():
            "t_dataset_s": t_data, "t_train_s": t_train, "count": int(n),
            "t_pre_profile_ms_median": float(np.median(ds["t_pre_profile_ms"])),
            "t_features_ms_median": float(np.median(ds["t_features_ms"]))}
-    sel = Selector(SIZES, params, mu, inv)
+    # the training range of the standardized inputs: the learned route profiles matrices
+    # outside it instead of extrapolating
+    x_tr = _inputs(ds["feat16"][tr], mu, inv)
+    sel = Selector(SIZES, params, mu, inv, x_tr.min(axis=0), x_tr.max(axis=0), args.slack)
     sel.save(os.path.join(args.out, "selector_gb300.npz"))
+    te_in = np.array([sel.predict(f)[1] >= 0.0 for f in ds["feat16"][te]])
+    res["test_inside_training_range"] = float(np.mean(te_in))
     if cal is not None:
         with open(os.path.join(args.out, "calibration_gb300.json"), "w") as fh:
             json.dump({"t_imb": cal["best"][0], "t_ml": cal["best"][1], "t_mb": cal["best"][2],

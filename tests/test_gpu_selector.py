@@ -214,6 +214,34 @@ def test_learned_route_uses_selector_and_falls_back(api, torch):
     check_spmv(m, x64, A.run(_dev(torch, x64)).cpu().numpy(), TAU["f64"], "learned")
 
 
+def test_learned_route_profiles_matrices_outside_the_training_range(api, torch):
+    """With a training range set, a matrix whose standardized inputs leave it by more than
+    the slack gets margin -1 and is classified by profiling; inside the range the MLP
+    decides. The inputs are computed by the oracle to place the range around them."""
+    m = synth.stencil_27pt(30)
+    A = api.SpmvMatrix.from_csr(m)
+    w = np.zeros(oracle.mlp_nparams(SIZES), dtype=np.float32)
+    w[-4:] = [1.0, -1.0, -1.0, -1.0]           # biases of the logits: always {MB}
+    f16 = np.zeros((1, 16))
+    f16[0, :14] = A.features()[0]
+    f16[0, 14], f16[0, 15] = m.n_rows, m.nnz
+    x = oracle.mlp_inputs(f16, None, None)[0]
+    inside = api.Selector(SIZES, w, in_lo=x - 0.1, in_hi=x + 0.1, slack=0.0)
+    r = A.tune("learned", selector=inside, autotune=0)
+    assert r.mode_used == 2 and r.margin == 1.0 and r.classes == 1
+    lo, hi = x - 0.1, x + 0.1
+    lo[0], hi[0] = x[0] + 0.5, x[0] + 1.0     # n_rows input below the range by 0.5
+    outside = api.Selector(SIZES, w, in_lo=lo, in_hi=hi, slack=0.25)
+    assert outside.predict(f16[0])[1] == -1.0
+    r = A.tune("learned", selector=outside, autotune=0, reps=3)
+    assert r.mode_used == 0 and r.margin == -1.0
+    within_slack = api.Selector(SIZES, w, in_lo=lo, in_hi=hi, slack=0.6)
+    assert within_slack.predict(f16[0])[1] == 1.0
+    from paper_1711_05487_gb300._abi import SpmvError
+    with pytest.raises(SpmvError):
+        api.Selector(SIZES, w, in_lo=hi, in_hi=lo)
+
+
 # -------------------------------------------------------------------- batched --------
 def test_batched_persistent_matches_oracle(api, torch):
     specs = synth.batched_specs(24, n_lo=500, n_hi=30_000)
