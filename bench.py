@@ -342,8 +342,8 @@ def run_ours(args, rank, world):
     # reduced-precision value storage on the same matrix (FP64 originals rounded once)
     extra = {}
     if m.val.dtype == np.float64 and not args.quick:
-        for st, vt, at in (("df64", "f64", "df64"), ("f32", "f64", "f64"), ("f32", "f32", "f32"),
-                           ("bf16", "f32", "f32")):
+        for st, vt, at in (("df64", "f64", "df64"), ("f32", "f64", "f64"), ("f32", "f64", "df64"),
+                           ("bf16", "f64", "df64"), ("f32", "f32", "f32"), ("bf16", "f32", "f32")):
             A.set_precision(st, vt, at, stream=stream)
             r2 = A.tune("profile", stream=stream)
             xv = x.to(torch.float64 if vt == "f64" else torch.float32)

@@ -146,10 +146,14 @@ spmv_status spmv_create(spmv_handle_t *out, int64_t n_rows, int64_t n_cols, int6
 spmv_status spmv_destroy(spmv_handle_t h);
 
 /* Value storage precision (build addition): storage in F64 / F32 / BF16, x and y in
- * vec_type (F64 or F32), products accumulated in acc_type (F64 or F32). Conversion is
+ * vec_type (F64 or F32), products accumulated in acc_type (F64, F32 or DF64). Conversion is
  * round-to-nearest-even straight from the input values. Offered: storage F64 with
- * vec = acc = F64; storage F32 or BF16 with (vec, acc) in {(F64,F64),(F32,F32),(F32,F64)};
- * storage DF64 with vec = F64, acc = DF64 (FP64 input values only).
+ * vec = acc = F64; storage F32 or BF16 with (vec, acc) in {(F64,F64),(F32,F32),(F32,F64),
+ * (F64,DF64),(F32,DF64)}; storage DF64 with vec = F64, acc = DF64 (FP64 input values only).
+ * acc = DF64 with F32 / BF16 storage: width-1 row variants sum each row in double-float
+ * arithmetic on the FP32 pipe (a stored value and an FP32 x element are exact in the high
+ * part), within about 8e-13 of sum_j |a_ij x_j| against the stored values, the FP64 bound;
+ * other variants accumulate in FP64.
  * DF64 (a GB300 answer to the CMP class, not in the paper): GB300's FP64 pipe is about 1/64
  * of its FP32 pipe, so width-1 row variants (vs = 1) compute each product and the row sum
  * in double-float FP32 arithmetic from value pairs split once here and x elements split as

@@ -384,6 +384,11 @@ spmv_status handle_info(spmv_handle_t h, const int32_t **rowptr, const int32_t *
 const KernelSet *kernel_set(spmv_dtype val, spmv_dtype vec, spmv_dtype acc) {
   if (val == SPMV_F64) return (vec == SPMV_F64 && acc == SPMV_F64) ? kernel_set_f64_dd() : nullptr;
   if (val == SPMV_DF64) return (vec == SPMV_F64 && acc == SPMV_DF64) ? kernel_set_f64_df() : nullptr;
+  if (acc == SPMV_DF64 && (val == SPMV_F32 || val == SPMV_BF16)) {
+    if (vec == SPMV_F64) return val == SPMV_F32 ? kernel_set_f32_d_df() : kernel_set_bf16_d_df();
+    if (vec == SPMV_F32) return val == SPMV_F32 ? kernel_set_f32_f_df() : kernel_set_bf16_f_df();
+    return nullptr;
+  }
   const bool dd = vec == SPMV_F64 && acc == SPMV_F64;
   const bool ff = vec == SPMV_F32 && acc == SPMV_F32;
   const bool fd = vec == SPMV_F32 && acc == SPMV_F64;

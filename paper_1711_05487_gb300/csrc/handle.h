@@ -24,6 +24,14 @@
 #include "internal.h"
 
 namespace spmv {
+
+// Kernel sets whose thread-per-row tiles accumulate in double-float arithmetic on the FP32
+// pipe (spmv_df.cu): FP32 / BF16 storage with FP64 (d) or FP32 (f) x.
+const KernelSet *kernel_set_f32_d_df();
+const KernelSet *kernel_set_f32_f_df();
+const KernelSet *kernel_set_bf16_d_df();
+const KernelSet *kernel_set_bf16_f_df();
+
 namespace rt {
 
 typedef unsigned __int128 u128;

@@ -17,6 +17,12 @@
 // Rows longer than kDfMaxRow, and rows that meet a value or an x element outside
 // [2^-40, 2^41) (split to a NaN marker, so the double-float sum is not finite), are
 // recomputed with native FP64 FMAs from the original FP64 values.
+//
+// The same kernel serves FP32 and BF16 storage with double-float accumulation: such a value
+// is exact in the high part (low part zero), and so is an FP32 x element, so a product is
+// the exact FP32 product plus its rounding error (and the x split's cross term for FP64 x);
+// the sum is the same double-float recurrence. Against the stored values, rows keep the
+// FP64 bound above at FP32 instruction rates.
 #include "spmv_kernels.cuh"
 
 namespace spmv {
@@ -79,6 +85,27 @@ template <bool XL2> __device__ __forceinline__ uint2 ldx_pair(const uint2 *p, ui
   }
 }
 
+// A stored value as a double-float pair: DF64 storage holds the pair; an FP32 or BF16 value
+// is exact in the high part. A nonzero outside [2^-40, 2^41) becomes the NaN marker, as in
+// df_split, so that its row falls back to FP64.
+__device__ __forceinline__ uint2 df_pair(uint2 v) { return v; }
+__device__ __forceinline__ uint2 df_pair(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const uint32_t eb = (b >> 23) & 0xFFu;
+  const bool out = eb - 87u > 80u;                   // biased exponent outside [87, 167]
+  const bool zero = (b & 0x7FFFFFFFu) == 0u;
+  return make_uint2(out ? (zero ? (b & 0x80000000u) : kDfNanHi) : b, 0u);
+}
+__device__ __forceinline__ uint2 df_pair(__nv_bfloat16 v) { return df_pair(__bfloat162float(v)); }
+
+// An x element as a pair: FP64 x is split as gathered, FP32 x is exact in the high part.
+template <bool XL2> __device__ __forceinline__ uint2 df_x(const double *p, uint64_t pol) {
+  return df_split(ldx<XL2>(p, pol));
+}
+template <bool XL2> __device__ __forceinline__ uint2 df_x(const float *p, uint64_t pol) {
+  return df_pair(ldx<XL2>(p, pol));
+}
+
 // (s, t) += (p, q); the _rn intrinsics keep each operation as written.
 __device__ __forceinline__ void df_add(float &s, float &t, float p, float q) {
   const float S = __fadd_rn(s, p);
@@ -89,21 +116,36 @@ __device__ __forceinline__ void df_add(float &s, float &t, float p, float q) {
   t = __fsub_rn(e, __fsub_rn(s, S));
 }
 
-// v * x as (p, q): p = fl(hi_v hi_x), q = its rounding error + hi_v lo_x + lo_v hi_x.
+// v * x as (p, q): p = fl(hi_v hi_x), q = its rounding error + hi_v lo_x + lo_v hi_x; VLO /
+// XLO say whether v / x have a low part at all (a zero one contributes nothing).
+template <bool VLO, bool XLO>
 __device__ __forceinline__ void df_prod(uint2 v, uint2 xv, float &p, float &q) {
   const float vh = __uint_as_float(v.x), vl = __uint_as_float(v.y);
   const float xh = __uint_as_float(xv.x), xl = __uint_as_float(xv.y);
   p = __fmul_rn(vh, xh);
   const float pe = __fmaf_rn(vh, xh, -p);
-  q = __fadd_rn(__fmaf_rn(vh, xl, __fmul_rn(vl, xh)), pe);
+  if constexpr (VLO && XLO) q = __fadd_rn(__fmaf_rn(vh, xl, __fmul_rn(vl, xh)), pe);
+  else if constexpr (XLO) q = __fmaf_rn(vh, xl, pe);
+  else if constexpr (VLO) q = __fmaf_rn(vl, xh, pe);
+  else q = pe;
 }
+
+// The values a staged tile holds for the double-float kernel and the storage type the FP64
+// fallbacks read: DF64 stages pairs and falls back to the FP64 originals; FP32 / BF16 stage
+// and fall back to the stored values themselves.
+template <typename ValT> struct DfStore { using type = ValT; };
+template <> struct DfStore<uint2> { using type = double; };
 
 }  // namespace
 
-// Thread-per-row tiles as in the FP64 kernel: a tile's value pairs and column indices are
-// staged in shared memory by one bulk copy each; each thread then walks its row.
-template <int DB, bool XL2>
+// Thread-per-row tiles as in the FP64 kernel: a tile's values (pairs, or FP32 / BF16) and
+// column indices are staged in shared memory by one bulk copy each; each thread then walks
+// its row.
+template <typename ValT, typename VecT, int DB, bool XL2>
 __global__ void __launch_bounds__(kTileRows) k_rowtile_df(const RunArgs a) {
+  using StoreT = typename DfStore<ValT>::type;
+  constexpr bool VLO = std::is_same<ValT, uint2>::value;
+  constexpr bool XLO = std::is_same<VecT, double>::value;
   using IdxT = typename IdxOf<DB>::type;
   constexpr int AL = stage_align<DB>();
   extern __shared__ __align__(16) unsigned char smem[];
@@ -114,19 +156,20 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_df(const RunArgs a) {
   const int s0 = __ldg(a.rowptr + r0), s1 = __ldg(a.rowptr + r1);
   const int a0 = s0 & ~(AL - 1);
   const int nc = ((s1 - a0) + AL - 1) & ~(AL - 1);
-  const double *__restrict__ val = static_cast<const double *>(a.val);
-  const uint2 *__restrict__ vdf = static_cast<const uint2 *>(a.val_df);
-  const double *__restrict__ x = static_cast<const double *>(a.x);
-  double *__restrict__ y = static_cast<double *>(a.y);
+  const StoreT *__restrict__ val = static_cast<const StoreT *>(a.val);
+  const ValT *__restrict__ vdf =
+      static_cast<const ValT *>(VLO ? a.val_df : a.val);   // the staged values
+  const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
+  VecT *__restrict__ y = static_cast<VecT *>(a.y);
   uint64_t pol_x = 0;
   if constexpr (XL2) pol_x = policy_evict_last();
   const int64_t row = r0 + threadIdx.x;
   if (nc > a.tile_cap) {
-    tile_direct<double, double, double, DB, XL2>(a, r0, r1, x, y, pol_x);
+    tile_direct<StoreT, VecT, double, DB, XL2>(a, r0, r1, x, y, pol_x);
     return;
   }
-  uint2 *sval = reinterpret_cast<uint2 *>(smem + 16);
-  IdxT *sidx = reinterpret_cast<IdxT *>(smem + 16 + (size_t)a.tile_cap * sizeof(uint2));
+  ValT *sval = reinterpret_cast<ValT *>(smem + 16);
+  IdxT *sidx = reinterpret_cast<IdxT *>(smem + 16 + (size_t)a.tile_cap * sizeof(ValT));
   const IdxT *gidx;
   if constexpr (DB != 0) gidx = static_cast<const IdxT *>(a.delta);
   else gidx = a.colind;
@@ -134,7 +177,7 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_df(const RunArgs a) {
     mbar_init(bar, 1);
     if (nc > 0) {
       const uint64_t pol = policy_evict_first();
-      const uint32_t bv = (uint32_t)nc * 8u;
+      const uint32_t bv = (uint32_t)nc * (uint32_t)sizeof(ValT);
       const uint32_t bi = (uint32_t)nc * (uint32_t)sizeof(IdxT);
       mbar_expect_tx(bar, bv + bi);
       bulk_g2s(sval, vdf + a0, bv, bar, pol);
@@ -178,68 +221,114 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_df(const RunArgs a) {
     for (; k + 8 <= len; k += 8) {
       uint2 xv[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) xv[q] = df_split(ldx<XL2>(x + column(k + q), pol_x));
+      for (int q = 0; q < 8; ++q) xv[q] = df_x<XL2>(x + column(k + q), pol_x);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         float p, pq;
-        df_prod(sval[o + k + q], xv[q], p, pq);
+        df_prod<VLO, XLO>(df_pair(sval[o + k + q]), xv[q], p, pq);
         df_add(sh, sl, p, pq);
       }
     }
     for (; k < len; ++k) {
       float p, pq;
-      df_prod(sval[o + k], df_split(ldx<XL2>(x + column(k), pol_x)), p, pq);
+      df_prod<VLO, XLO>(df_pair(sval[o + k]), df_x<XL2>(x + column(k), pol_x), p, pq);
       df_add(sh, sl, p, pq);
     }
     if (isfinite(sh)) {
-      y[row] = (double)sh + (double)sl;
+      y[row] = (VecT)((double)sh + (double)sl);
       return;
     }
     c = base;   // restart the delta decode for the FP64 pass
   }
+  // FP64 FMAs in element order, as the FP64-accumulating tile kernel computes the row
   double acc = 0.0;
-  for (int k = 0; k < len; ++k) acc = fma(__ldg(val + s + k), ldx<XL2>(x + column(k), pol_x), acc);
-  y[row] = acc;
+  for (int k = 0; k < len; ++k)
+    acc = fma(widen<double>(val[s + k]), (double)ldx<XL2>(x + column(k), pol_x), acc);
+  y[row] = (VecT)acc;
 }
 
 namespace {
 
-template <int DB, bool XL2> cudaError_t launch_rowtile_df_k(const RunArgs &a, cudaStream_t s) {
+template <typename ValT, typename VecT, int DB, bool XL2>
+cudaError_t launch_rowtile_df_k(const RunArgs &a, cudaStream_t s) {
   static std::atomic<int> configured{0};
   const int rows = a.tile_rows > 0 ? a.tile_rows : kTileRows;
-  const size_t smem = 16 + (size_t)a.tile_cap * (8 + sizeof(typename IdxOf<DB>::type));
-  cudaError_t e = ensure_smem(k_rowtile_df<DB, XL2>, smem, configured);
+  const size_t smem = 16 + (size_t)a.tile_cap * (sizeof(ValT) + sizeof(typename IdxOf<DB>::type));
+  cudaError_t e = ensure_smem(k_rowtile_df<ValT, VecT, DB, XL2>, smem, configured);
   if (e != cudaSuccess) return e;
   const unsigned g = (unsigned)((a.n_rows + rows - 1) / rows);
-  k_rowtile_df<DB, XL2><<<g, rows, smem, s>>>(a);
+  k_rowtile_df<ValT, VecT, DB, XL2><<<g, rows, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 // Width-1 row variants run the double-float tile kernel (one tile per CTA, whatever
-// tile_pipe says); every other variant (column panels included) runs the native FP64
-// kernels on the FP64 values.
-cudaError_t launch_spmv_df(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
+// tile_pipe says); every other variant (column panels included) runs the FP64-accumulating
+// kernels of `base` (for DF64 storage on the FP64 originals).
+template <typename ValT, typename VecT>
+cudaError_t launch_spmv_df(const KernelSet *base, const spmv_variant &v, const RunArgs &a,
+                           cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
-  if (v.partition != 0 || v.vs != 1 || v.xpath >= 2)
-    return kernel_set_f64_dd()->spmv(v, a, s);
+  if (v.partition != 0 || v.vs != 1 || v.xpath >= 2) return base->spmv(v, a, s);
   const bool xl2 = v.xpath != 0;
   if (v.index == 1 && a.delta_bits == 8)
-    return xl2 ? launch_rowtile_df_k<8, true>(a, s) : launch_rowtile_df_k<8, false>(a, s);
+    return xl2 ? launch_rowtile_df_k<ValT, VecT, 8, true>(a, s)
+               : launch_rowtile_df_k<ValT, VecT, 8, false>(a, s);
   if (v.index == 1)
-    return xl2 ? launch_rowtile_df_k<16, true>(a, s) : launch_rowtile_df_k<16, false>(a, s);
-  return xl2 ? launch_rowtile_df_k<0, true>(a, s) : launch_rowtile_df_k<0, false>(a, s);
+    return xl2 ? launch_rowtile_df_k<ValT, VecT, 16, true>(a, s)
+               : launch_rowtile_df_k<ValT, VecT, 16, false>(a, s);
+  return xl2 ? launch_rowtile_df_k<ValT, VecT, 0, true>(a, s)
+             : launch_rowtile_df_k<ValT, VecT, 0, false>(a, s);
+}
+
+cudaError_t spmv_f64_df(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
+  return launch_spmv_df<uint2, double>(kernel_set_f64_dd(), v, a, s);
+}
+cudaError_t spmv_f32_d_df(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
+  return launch_spmv_df<float, double>(kernel_set_f32_dd(), v, a, s);
+}
+cudaError_t spmv_f32_f_df(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
+  return launch_spmv_df<float, float>(kernel_set_f32_fd(), v, a, s);
+}
+cudaError_t spmv_bf16_d_df(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
+  return launch_spmv_df<__nv_bfloat16, double>(kernel_set_bf16_dd(), v, a, s);
+}
+cudaError_t spmv_bf16_f_df(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
+  return launch_spmv_df<__nv_bfloat16, float>(kernel_set_bf16_fd(), v, a, s);
+}
+
+// The base set with its SpMV launcher replaced (profiling, SpMM as in the base set).
+const KernelSet *df_set(const KernelSet *base, spmv_launch_fn fn, KernelSet *slot) {
+  *slot = *base;
+  slot->spmv = fn;
+  return slot;
 }
 
 }  // namespace
 
 const KernelSet *kernel_set_f64_df() {
-  static const KernelSet ks = [] {
-    const KernelSet *f64 = kernel_set_f64_dd();
-    KernelSet k = *f64;
-    k.spmv = &launch_spmv_df;
-    return k;
-  }();
-  return &ks;
+  static KernelSet ks;
+  static const KernelSet *p = df_set(kernel_set_f64_dd(), &spmv_f64_df, &ks);
+  return p;
+}
+const KernelSet *kernel_set_f32_d_df() {
+  static KernelSet ks;
+  static const KernelSet *p = df_set(kernel_set_f32_dd(), &spmv_f32_d_df, &ks);
+  return p;
+}
+const KernelSet *kernel_set_f32_f_df() {
+  static KernelSet ks;
+  static const KernelSet *p = df_set(kernel_set_f32_fd(), &spmv_f32_f_df, &ks);
+  return p;
+}
+const KernelSet *kernel_set_bf16_d_df() {
+  static KernelSet ks;
+  static const KernelSet *p = df_set(kernel_set_bf16_dd(), &spmv_bf16_d_df, &ks);
+  return p;
+}
+const KernelSet *kernel_set_bf16_f_df() {
+  static KernelSet ks;
+  static const KernelSet *p = df_set(kernel_set_bf16_fd(), &spmv_bf16_f_df, &ks);
+  return p;
 }
 
 }  // namespace spmv

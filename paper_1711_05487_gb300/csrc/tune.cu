@@ -487,7 +487,7 @@ void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, cudaStream_t s) {
     v.tile_pipe = 0;
   } else {
     int best_rows = h->tile_rows, best_pipe = h->tile_pipe, best_cap = h->tile_cap;
-    const int max_pipe = h->storage == SPMV_DF64 ? 0 : 1;
+    const int max_pipe = h->acc == SPMV_DF64 ? 0 : 1;
     for (int pipe = 0; pipe <= max_pipe; ++pipe) {
       for (int rows = kTileRows; rows >= 32; rows /= 2) {
         set_tile_geometry(h, v, rows, pipe != 0, s);

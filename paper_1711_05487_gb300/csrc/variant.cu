@@ -267,7 +267,7 @@ void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
       v.vs = (v.vec || v.index == 1) ? pool_vs(h->nnz_avg(), v.index == 1 ? 8 : 4)
                                      : heuristic_vs(h->nnz_avg(), 1);
     }
-    if (h->storage == SPMV_DF64) v.tile_pipe = 0;   // the double-float kernel: one tile per CTA
+    if (h->acc == SPMV_DF64) v.tile_pipe = 0;   // the double-float kernel: one tile per CTA
     if (v.vs == 1 && v.tile_rows != 0) {
       set_tile_geometry(h, v, v.tile_rows, v.tile_pipe != 0, s);
     } else {

@@ -120,7 +120,8 @@ def test_empty_matrix_and_zero_rows(api, torch):
 
 PRECISIONS = [("f32", "f64", "f64"), ("f32", "f32", "f64"), ("bf16", "f64", "f64"),
               ("bf16", "f32", "f64"), ("bf16", "f32", "f32"), ("f32", "f32", "f32"),
-              ("df64", "f64", "df64")]
+              ("df64", "f64", "df64"), ("f32", "f64", "df64"), ("f32", "f32", "df64"),
+              ("bf16", "f64", "df64"), ("bf16", "f32", "df64")]
 
 
 @pytest.mark.parametrize("storage,vec,acc", PRECISIONS)
@@ -147,6 +148,10 @@ def test_precisions(api, torch, name, storage, vec, acc):
         A.set_variant(**v)
         y = A.run(x).double().cpu().numpy()
         check_spmv(m, x64, y, TAU[storage], f"{name} {storage}/{vec}/{acc} {v}")
+        if acc in ("f64", "df64") and vec == "f64":
+            # the accumulation itself: FP64 bound against the values as stored
+            check_spmv(m, x64, y, TAU["f64"], f"{name} {storage}/{vec}/{acc} {v} (stored)",
+                       values=stored_values(m.val, storage))
 
 
 def test_unsupported_precision_rejected(api):
@@ -274,6 +279,42 @@ def test_df64_rows_that_do_not_split_fall_back_to_fp64(api, torch):
     for (yd, y64), v in zip(_df_runs(api, torch, m, x64, DF_VARIANTS), DF_VARIANTS):
         assert np.array_equal(yd[bad].view(np.uint64), y64[bad].view(np.uint64)), v
         check_spmv(m, x64, yd, TAU["df64"], f"df64 {v}")
+
+
+def test_double_float_accumulation_on_fp32_storage_falls_back_like_fp64(api, torch):
+    """FP32 storage with double-float accumulation: rows meeting a value or x element outside
+    [2^-40, 2^41) are recomputed with FP64 FMAs, bit-identical to the FP64-accumulating tile
+    kernel on the same FP32 values; every row is within the FP64 bound of the oracle on the
+    stored values."""
+    m = synth.uniform_random(20_000, 20, seed=24, min_per_row=0, n_cols=30_000)
+    rng = np.random.default_rng(25)
+    val = m.val.copy()
+    for r in rng.choice(m.n_rows, 150, replace=False):
+        s, e = m.rowptr[r], m.rowptr[r + 1]
+        if e > s:
+            val[s] = 1e-14 if r % 2 else 3e13
+    m = synth.Csr(m.n_rows, m.n_cols, m.rowptr, m.colind, val, "df_f32_edges")
+    x64 = synth.uniform_vector(m.n_cols, 26)
+    x64[rng.choice(m.n_cols, 200, replace=False)] = 0.0
+    x64[rng.choice(m.n_cols, 50, replace=False)] = 1e-13
+    v32 = stored_values(val, "f32")
+    xb = (x64 != 0) & ((np.abs(x64) < 2.0 ** -40) | (np.abs(x64) >= 2.0 ** 41))
+    vb = (v32 != 0) & ((np.abs(v32) < 2.0 ** -40) | (np.abs(v32) >= 2.0 ** 41))
+    bad = np.zeros(m.n_rows, bool)
+    row_of = np.repeat(np.arange(m.n_rows), np.diff(m.rowptr))
+    bad[row_of[vb | xb[m.colind]]] = True
+    assert bad.sum() > 100
+    D = api.SpmvMatrix.from_csr(m)
+    D.set_precision("f32", "f64", "df64")
+    F = api.SpmvMatrix.from_csr(m)
+    F.set_precision("f32", "f64", "f64")
+    x = _dev(torch, x64)
+    for v in DF_VARIANTS:
+        D.set_variant(**v)
+        F.set_variant(**v)
+        yd, yf = D.run(x).cpu().numpy(), F.run(x).cpu().numpy()
+        assert np.array_equal(yd[bad].view(np.uint64), yf[bad].view(np.uint64)), v
+        check_spmv(m, x64, yd, TAU["f64"], f"f32/df64 {v}", values=v32)
 
 
 def test_df64_long_rows_and_ragged(api, torch):
