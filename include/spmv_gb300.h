@@ -186,10 +186,12 @@ spmv_status spmv_run(spmv_handle_t h, const void *x, void *y, spmv_stream_t stre
 
 /* y = A x with HOST buffers: copies x to a handle-owned device buffer, runs, copies y
  * back; returns when y is on the host (the end-to-end path). Row variants whose x and y
- * together reach 8 MB compute in eight row chunks: chunk c waits only for the prefix of x up to the largest column of chunks
- * 0..c (uploaded piece by piece on a handle-owned stream), consecutive chunks' kernels run
- * on two alternating handle-owned streams, and each finished chunk of y is downloaded on
- * another while the next computes. With page-locked x and y the whole pipeline is captured
+ * together reach 8 MB compute in eight row chunks: chunk c waits only for the prefix of x
+ * up to the largest column of chunks 0..c (uploaded piece by piece on a handle-owned
+ * stream), consecutive chunks' kernels run on two alternating handle-owned streams, and
+ * each finished chunk of y is downloaded on another while the next computes. Column
+ * panels (up to 8) upload x slice by slice, each pass waiting only for its slice, and run
+ * their last pass in the eight row chunks. With page-locked x and y the whole pipeline is captured
  * once into a CUDA graph (kept per handle for the last pair of host pointers until the
  * precision or variant changes) and replayed with one launch; pageable buffers take the
  * same pipeline without a graph, with slower, staged copies. Host buffers must stay valid

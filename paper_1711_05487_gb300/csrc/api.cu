@@ -121,6 +121,7 @@ spmv_status spmv_destroy(spmv_handle_t h) {
     }
     for (auto e : h->joined)
       if (e) cudaEventDestroy(e);
+    if (h->pass_done) cudaEventDestroy(h->pass_done);
     cudaStreamDestroy(h->copy_stream);
     cudaStreamDestroy(h->upload_stream);
     cudaStreamDestroy(h->capture_stream);

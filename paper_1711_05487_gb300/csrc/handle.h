@@ -179,6 +179,7 @@ struct spmv_matrix {
   cudaStream_t capture_stream = nullptr;  // host-buffer runs: graph capture
   cudaStream_t chunk_stream[2] = {};    // host-buffer runs: alternate chunks' kernels
   cudaEvent_t joined[5] = {};           // host-buffer runs: fork from / rejoin the origin
+  cudaEvent_t pass_done = nullptr;      // host-buffer runs: column panels' passes before the last
   cudaGraph_t host_graph = nullptr;     // host-buffer pipeline for (host_x, host_y, epoch)
   cudaGraphExec_t host_exec = nullptr;
   const void *host_x = nullptr;

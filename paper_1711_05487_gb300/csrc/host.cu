@@ -56,13 +56,16 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
         CK(cudaEventCreateWithFlags(&h->x_ready[c], cudaEventDisableTiming));
       }
       for (auto &e : h->joined) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&h->pass_done, cudaEventDisableTiming));
     }
     // pipelining pays once the copies take longer than a few chunk launches (x and y of at
     // least 8 MB together)
-    const bool chunked = h->variant.partition == 0 && h->variant.xpath < 2 &&
-                         h->n_rows >= 4 * kHostChunks * kTileRows &&
-                         (int64_t)vb * (h->n_rows + h->n_cols) >= 8000000;
-    const int nch = chunked ? kHostChunks : 1;
+    const bool big = h->n_rows >= 4 * kHostChunks * kTileRows &&
+                     (int64_t)vb * (h->n_rows + h->n_cols) >= 8000000;
+    const int n_pass = h->variant.xpath >= 2 ? h->variant.xpath : 0;
+    const bool panels = n_pass >= 2 && n_pass <= kHostChunks && big;
+    const bool chunked = h->variant.partition == 0 && h->variant.xpath < 2 && big;
+    const int nch = (chunked || panels) ? kHostChunks : 1;
     // chunk row boundaries: equal parts aligned to 128 rows
     int64_t per = (h->n_rows + nch - 1) / nch;
     per = ((per + kTileRows - 1) / kTileRows) * kTileRows;
@@ -91,8 +94,7 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
     // its piece, and each finished chunk of y is downloaded on another stream. Consecutive
     // chunks' kernels go to two alternating streams, so one chunk's last partial wave of CTAs
     // overlaps the next chunk's first; all side streams join back into `origin` at the end.
-    // Merge-path tiles and column panels span the whole matrix: one upload, one run, one
-    // download.
+    // Merge-path tiles span the whole matrix: one upload, one launch, one download.
     const KernelSet *ks = set_for(h);
     auto enqueue = [&](cudaStream_t origin) {
       cudaStream_t side[4] = {h->upload_stream, h->copy_stream, h->chunk_stream[0],
@@ -134,6 +136,61 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
         CK(cudaStreamWaitEvent(origin, h->joined[k], 0));
       }
     };
+    // Column panels: pass p reads only slice p of x, so x goes up in slice order on the
+    // upload stream and pass p waits for its slice (the next slices upload during the
+    // passes before); the last pass runs in row chunks on the two alternating streams, each
+    // finished chunk of y downloaded while the next computes.
+    auto enqueue_panels = [&](cudaStream_t origin) {
+      cudaStream_t side[4] = {h->upload_stream, h->copy_stream, h->chunk_stream[0],
+                              h->chunk_stream[1]};
+      CK(cudaEventRecord(h->joined[4], origin));
+      for (cudaStream_t st : side) CK(cudaStreamWaitEvent(st, h->joined[4], 0));
+      const int64_t w = h->pnl_width;
+      for (int p = 0; p < n_pass; ++p) {
+        const int64_t c0 = std::min<int64_t>(h->n_cols, (int64_t)p * w);
+        const int64_t c1 = p == n_pass - 1 ? h->n_cols : std::min<int64_t>(h->n_cols, c0 + w);
+        if (c1 > c0)
+          CK(cudaMemcpyAsync(static_cast<char *>(h->x_stage.p) + vb * (size_t)c0,
+                             static_cast<const char *>(x_host) + vb * (size_t)c0,
+                             vb * (size_t)(c1 - c0), cudaMemcpyHostToDevice, h->upload_stream));
+        CK(cudaEventRecord(h->x_ready[p], h->upload_stream));
+      }
+      for (int p = 0; p + 1 < n_pass; ++p) {
+        CK(cudaStreamWaitEvent(h->chunk_stream[0], h->x_ready[p], 0));
+        RunArgs a = run_args(h, h->x_stage.p, h->y_stage.p);
+        a.pnl_first = p;
+        a.n_panels = 1;
+        CK(ks->spmv(h->variant, a, h->chunk_stream[0]));
+      }
+      CK(cudaEventRecord(h->pass_done, h->chunk_stream[0]));
+      CK(cudaStreamWaitEvent(h->chunk_stream[1], h->pass_done, 0));
+      for (cudaStream_t cs : {h->chunk_stream[0], h->chunk_stream[1]})
+        CK(cudaStreamWaitEvent(cs, h->x_ready[n_pass - 1], 0));
+      for (int c = 0; c < nch; ++c) {
+        const int64_t r0 = bounds[c], r1 = bounds[c + 1];
+        if (r1 <= r0) continue;
+        cudaStream_t cs = h->chunk_stream[c & 1];
+        RunArgs a = run_args(h, h->x_stage.p, static_cast<char *>(h->y_stage.p) + vb * (size_t)r0);
+        a.n_rows = r1 - r0;
+        a.pnl_rowptr += r0;
+        a.pnl_first = n_pass - 1;
+        a.n_panels = 1;
+        CK(ks->spmv(h->variant, a, cs));
+        CK(cudaEventRecord(h->chunk_done[c], cs));
+        CK(cudaStreamWaitEvent(h->copy_stream, h->chunk_done[c], 0));
+        CK(cudaMemcpyAsync(static_cast<char *>(y_host) + vb * (size_t)r0,
+                           static_cast<char *>(h->y_stage.p) + vb * (size_t)r0,
+                           vb * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, h->copy_stream));
+      }
+      for (int k = 0; k < 4; ++k) {
+        CK(cudaEventRecord(h->joined[k], side[k]));
+        CK(cudaStreamWaitEvent(origin, h->joined[k], 0));
+      }
+    };
+    auto run = [&](cudaStream_t origin) {
+      if (panels) enqueue_panels(origin);
+      else enqueue(origin);
+    };
     if (is_page_locked(x_host) && is_page_locked(y_host)) {
       // Page-locked buffers: the whole pipeline (uploads, chunk kernels, downloads and the
       // events between the three streams) is captured once into a CUDA graph per pair of
@@ -143,7 +200,7 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
         drop_host_graph(h);
         CK(cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeRelaxed));
         try {
-          enqueue(h->capture_stream);
+          run(h->capture_stream);
         } catch (...) {
           cudaGraph_t g = nullptr;
           cudaStreamEndCapture(h->capture_stream, &g);
@@ -158,7 +215,7 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
       }
       CK(cudaGraphLaunch(h->host_exec, s));
     } else {
-      enqueue(s);
+      run(s);
     }
     CK(cudaStreamSynchronize(s));
     return SPMV_OK;

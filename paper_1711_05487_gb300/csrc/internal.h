@@ -66,10 +66,13 @@ struct RunArgs {
   int64_t bin_n_long = 0;
   double *bin_partials = nullptr;
   // column panels (xpath >= 2): a panel-major copy of the matrix; panel p's row pointers
-  // are pnl_rowptr + p * (n_rows + 1), absolute positions into pnl_col / pnl_val
+  // are pnl_rowptr + p * pnl_stride, absolute positions into pnl_col / pnl_val. A launch runs
+  // the passes pnl_first .. pnl_first + n_panels - 1; pass 0 writes y, later passes add.
   const int32_t *pnl_rowptr = nullptr;
   const int32_t *pnl_col = nullptr;
   const void *pnl_val = nullptr;
+  int64_t pnl_stride = 0;
+  int32_t pnl_first = 0;
   int32_t n_panels = 0;
 };
 

@@ -716,15 +716,15 @@ cudaError_t launch_rowvec_vs(const spmv_variant &v, const RunArgs &a, cudaStream
   return cudaGetLastError();
 }
 
-// The column-panel variant: one launch per panel, in panel order on one stream.
+// The column-panel variant: one launch per pass, in panel order on one stream.
 template <typename ValT, typename VecT, typename AccT, int VS>
 cudaError_t launch_panels_vs(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
   RunArgs pa = a;
   pa.colind = a.pnl_col;
   pa.val = a.pnl_val;
   const unsigned g = grid_for_rows(a.n_rows, VS);
-  for (int p = 0; p < a.n_panels; ++p) {
-    const int32_t *prow = a.pnl_rowptr + (int64_t)p * (a.n_rows + 1);
+  for (int p = a.pnl_first; p < a.pnl_first + a.n_panels; ++p) {
+    const int32_t *prow = a.pnl_rowptr + (int64_t)p * a.pnl_stride;
     if (v.vec) k_panel<ValT, VecT, AccT, VS, true><<<g, kRowThreads, 0, s>>>(pa, prow, p > 0);
     else k_panel<ValT, VecT, AccT, VS, false><<<g, kRowThreads, 0, s>>>(pa, prow, p > 0);
   }
@@ -733,7 +733,9 @@ cudaError_t launch_panels_vs(const spmv_variant &v, const RunArgs &a, cudaStream
 
 template <typename ValT, typename VecT, typename AccT>
 cudaError_t launch_panels(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
-  if (a.n_panels != v.xpath || !a.pnl_rowptr) return cudaErrorInvalidValue;
+  if (!a.pnl_rowptr || a.pnl_first < 0 || a.n_panels < 1 ||
+      a.pnl_first + a.n_panels > v.xpath || a.pnl_stride < a.n_rows + 1)
+    return cudaErrorInvalidValue;
   switch (v.vs) {
     case 1: return launch_panels_vs<ValT, VecT, AccT, 1>(v, a, s);
     case 2: return launch_panels_vs<ValT, VecT, AccT, 2>(v, a, s);

@@ -47,6 +47,8 @@ RunArgs run_args(const spmv_matrix *h, const void *x, void *y) {
   a.pnl_rowptr = h->pnl_rowptr.as<int32_t>();
   a.pnl_col = h->pnl_col.as<int32_t>();
   a.pnl_val = h->pnl_val.p;
+  a.pnl_stride = h->n_rows + 1;
+  a.pnl_first = 0;
   a.n_panels = h->pnl_count;
   return a;
 }

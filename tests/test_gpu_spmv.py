@@ -183,7 +183,9 @@ def test_spmm(api, torch, name, k):
 
 
 @pytest.mark.parametrize("gen", [lambda: synth.stencil_27pt(30),       # one launch
-                                 lambda: synth.stencil_27pt(80),       # eight row chunks
+                                 lambda: synth.stencil_27pt(80),       # eight row chunks;
+                                                                       # panels: slices, then
+                                                                       # last-pass chunks
                                  lambda: synth.power_law(30_000, seed=14, dtype=np.float64)])
 def test_run_host_equals_device_run(api, torch, gen):
     m = gen()
@@ -192,7 +194,8 @@ def test_run_host_equals_device_run(api, torch, gen):
     xh = torch.from_numpy(x64).pin_memory()
     yh = torch.empty(m.n_rows, dtype=torch.float64).pin_memory()
     for v in (dict(index=1, vec=1), dict(vec=1, vs=1, tile_rows=64, tile_pipe=1),
-              dict(vec=1, vs=4), dict(partition=1), dict(xpath=2, vs=4)):
+              dict(vec=1, vs=4), dict(partition=1), dict(xpath=2, vs=4),
+              dict(xpath=3, vs=1, vec=1)):
         A.set_variant(**v)
         yd = A.run(torch.from_numpy(x64).cuda()).cpu()
         yh.fill_(float("nan"))
