@@ -218,6 +218,17 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_df(const RunArgs a) {
   if (len <= kDfMaxRow) {
     float sh = 0.0f, sl = 0.0f;
     int k = 0;
+    for (; k + 16 <= len; k += 16) {
+      uint2 xv[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) xv[q] = df_x<XL2>(x + column(k + q), pol_x);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        float p, pq;
+        df_prod<VLO, XLO>(df_pair(sval[o + k + q]), xv[q], p, pq);
+        df_add(sh, sl, p, pq);
+      }
+    }
     for (; k + 8 <= len; k += 8) {
       uint2 xv[8];
 #pragma unroll

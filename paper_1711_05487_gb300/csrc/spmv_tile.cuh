@@ -32,8 +32,8 @@ __host__ __device__ constexpr int tile_elem_bytes() {
 }
 
 // Dot product of one row whose values and columns sit in shared memory at offset o (the
-// row's first element) of a staged tile: 8 gathers of x in flight per thread, then 8 FMAs;
-// the exact trip count keeps the FP64 pipe free of masked-off work.
+// row's first element) of a staged tile: 16 (then 8) gathers of x in flight per thread
+// before their FMAs; exact trip counts keep the FP64 pipe free of masked-off work.
 template <typename ValT, typename VecT, typename AccT, int DB, bool XL2, typename IdxT>
 __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
                                              const IdxT *sidx, int o, int len, int32_t base,
@@ -56,6 +56,13 @@ __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
     }
   };
   int k = 0;
+  for (; k + 16 <= len; k += 16) {
+    AccT xv[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) xv[q] = (AccT)ldx<XL2>(x + column(k + q), pol_x);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc = fma(widen<AccT>(sval[o + k + q]), xv[q], acc);
+  }
   for (; k + 8 <= len; k += 8) {
     AccT xv[8];
 #pragma unroll
