@@ -638,7 +638,8 @@ def run_reference(args):
     v = 2.0 * m.nnz / dt / 1e9
     return {
         "impl": "reference", "metric": "SpMV GFLOP/s (2*nnz/t), adaptive (profile-guided) vs "
-        "plain CSR-vector", "value": round(v, 4), "unit": "GFLOP/s", "n_gpus": 0,
+        "plain CSR-vector", "value": round(v, 4), "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "device": "host CPU (the oracle; no GPU work)",
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded)",
