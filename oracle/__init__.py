@@ -94,6 +94,8 @@ def _declare(L):
     L.oracle_delta8_decode.restype = None
     L.oracle_delta_width.argtypes = [_I64, _P, _P]
     L.oracle_delta_width.restype = ctypes.c_int32
+    L.oracle_sell32.argtypes = [_I64, _P, _P, _P]
+    L.oracle_sell32.restype = _I64
     L.oracle_panel_width.argtypes = [_I64, ctypes.c_int32]
     L.oracle_panel_width.restype = ctypes.c_int32
     L.oracle_col_panels.argtypes = [_I64, _I64, _P, _P, ctypes.c_int32, _P, _P]
@@ -211,6 +213,22 @@ def row_bins(rowptr, colind, l_med=64, chunk=4096):
                           _p(counts))
     a, b, c = (int(v) for v in counts)
     return med[:a], lng[:b], first[:b + 1], ch[:c]
+
+
+def sell32(rowptr):
+    """(soff, perm) of the sliced-row layout: slice s spans positions [soff[s], soff[s+1]),
+    element k of row 32 s + l at soff[s] + 32 k + l; perm = CSR position or -1 (padding)."""
+    rp = _c(rowptr, np.int32)
+    n = rp.shape[0] - 1
+    ns = (n + 31) // 32
+    lens = np.diff(rp.astype(np.int64))
+    bound = 0
+    for s in range(0, n, 32):
+        bound += 32 * int(lens[s:s + 32].max()) if lens[s:s + 32].size else 0
+    soff = np.empty(ns + 1, np.int64)
+    perm = np.empty(max(bound, 1), np.int32)
+    tot = lib().oracle_sell32(n, _p(rp), _p(soff), _p(perm))
+    return soff, perm[:tot]
 
 
 def panel_width(n_cols: int, n_panels: int) -> int:

@@ -335,6 +335,35 @@ void oracle_row_bins(int64_t n_rows, const int32_t *rowptr, const int32_t *colin
 }
 
 /* ---------------------------------------------------------------------------------- */
+/* Sliced rows (SELL-32; a GB300 layout for the CMP class, not in the paper): rows are taken
+ * in slices of 32 consecutive rows (the last slice may hold fewer); slice s holds w_s = the
+ * longest row length in the slice elements per row, stored column-major: element k of row
+ * 32 s + l sits at soff[s] + 32 k + l, where soff[0] = 0 and soff[s+1] = soff[s] + 32 w_s.
+ * Positions past a row's length (and the lanes of missing rows in the last slice) are
+ * padding. perm[p] is the CSR position of the element at p, or -1 for padding. Returns the
+ * number of positions soff[n_slices].                                                    */
+int64_t oracle_sell32(int64_t n_rows, const int32_t *rowptr, int64_t *soff, int32_t *perm) {
+  const int64_t ns = (n_rows + 31) / 32;
+  soff[0] = 0;
+  for (int64_t s = 0; s < ns; ++s) {
+    int64_t w = 0;
+    for (int64_t r = 32 * s; r < 32 * s + 32 && r < n_rows; ++r)
+      if (rowptr[r + 1] - rowptr[r] > w) w = rowptr[r + 1] - rowptr[r];
+    soff[s + 1] = soff[s] + 32 * w;
+  }
+  for (int64_t s = 0; s < ns; ++s) {
+    const int64_t w = (soff[s + 1] - soff[s]) / 32;
+    for (int64_t l = 0; l < 32; ++l) {
+      const int64_t r = 32 * s + l;
+      const int64_t len = r < n_rows ? rowptr[r + 1] - rowptr[r] : 0;
+      for (int64_t k = 0; k < w; ++k)
+        perm[soff[s] + 32 * k + l] = k < len ? (int32_t)(rowptr[r] + k) : -1;
+    }
+  }
+  return soff[ns];
+}
+
+/* ---------------------------------------------------------------------------------- */
 /* Column panels (Section III-E, ML: make the irregular accesses to x hit in cache; read on
  * GB300 as cutting x into P slices that each fit in the L2 and running the SpMV as one pass
  * per slice). Panel p holds the columns [p*w, (p+1)*w), w = oracle_panel_width(n_cols, P):

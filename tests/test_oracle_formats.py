@@ -353,3 +353,57 @@ def test_col_panels_spmv_by_passes_is_exact_on_integers():
                             val[perm][prow[p][0]:prow[p][-1]], x)
         acc += yp
     assert np.array_equal(acc, y)
+
+
+# ------------------------------------------------------------------ sliced rows (SELL-32)
+def test_sell32_hand_example():
+    # 3 rows of lengths 2, 0, 3 in one slice of width 3: element k of row l at 32 k + l
+    rp = np.array([0, 2, 2, 5], np.int32)
+    soff, perm = oracle.sell32(rp)
+    assert soff.tolist() == [0, 96]
+    want = np.full(96, -1)
+    want[[0, 32]] = [0, 1]
+    want[[2, 34, 66]] = [2, 3, 4]
+    assert perm.tolist() == want.tolist()
+
+
+@pytest.mark.parametrize("gen", [lambda: synth.uniform_random(1000, 40, seed=41, min_per_row=0),
+                                 lambda: synth.stencil_27pt(9),
+                                 lambda: synth.power_law(3000, alpha=1.6, clip=500, seed=42,
+                                                         dtype=np.float64),
+                                 lambda: synth.dense_random(70, 50, 0.1, seed=43),
+                                 lambda: synth.Csr(0, 4, np.zeros(1, np.int32),
+                                                   np.zeros(0, np.int32), np.zeros(0), "empty")])
+def test_sell32_against_dense_and_widths(gen):
+    """Reading every slice position back (value and column of perm, zero for padding)
+    rebuilds A; each slice is as wide as its longest row; every CSR element appears once,
+    rows in order down their lane."""
+    m = gen()
+    soff, perm = oracle.sell32(m.rowptr)
+    ns = (m.n_rows + 31) // 32
+    lens = np.diff(m.rowptr)
+    assert soff.shape == (ns + 1,) and soff[0] == 0
+    for s in range(ns):
+        assert soff[s + 1] - soff[s] == 32 * lens[32 * s:32 * s + 32].max()
+    real = perm[perm >= 0]
+    assert np.array_equal(np.sort(real), np.arange(m.nnz))
+    dense = np.zeros((m.n_rows, m.n_cols))
+    for s in range(ns):
+        w = (soff[s + 1] - soff[s]) // 32
+        for lane in range(32):
+            r = 32 * s + lane
+            ks = [perm[soff[s] + 32 * k + lane] for k in range(w)]
+            n_real = sum(1 for j in ks if j >= 0)
+            assert all(j >= 0 for j in ks[:n_real]) and all(j < 0 for j in ks[n_real:])
+            if r < m.n_rows:
+                assert n_real == lens[r]
+                assert ks[:n_real] == list(range(m.rowptr[r], m.rowptr[r + 1]))
+                for j in ks[:n_real]:
+                    dense[r, m.colind[j]] += m.val[j]
+            else:
+                assert n_real == 0
+    want = np.zeros((m.n_rows, m.n_cols))
+    for r in range(m.n_rows):
+        for j in range(m.rowptr[r], m.rowptr[r + 1]):
+            want[r, m.colind[j]] += m.val[j]
+    assert np.array_equal(dense, want)
