@@ -73,7 +73,11 @@ typedef struct {
                         64 nonzeros on sub-warps of vs lanes (2, 4 or 8), rows under
                         4096 on one warp each, longer rows in 4096-nonzero chunks summed
                         in FP64 in chunk order. 1 and 2 are the decompositions of
-                        Section III-E (IMB); the autotuner picks between them         */
+                        Section III-E (IMB); the autotuner picks between them;
+                        3: sliced rows (SELL-32, a GB300 layout for short rows; see
+                        spmv_get_sell): one thread per row over 32-row slices stored
+                        column-major, coalesced loads without a shared-memory stage, int32
+                        columns or (index 1) the delta index's deltas; vs is 1          */
   int32_t index;     /* 0: int32 columns; 1: 8- or 16-bit column deltas (one width per
                         matrix, see spmv_get_delta) with escape rows (MB); merge-path
                         tiles (partition 1) always read int32 columns                     */
@@ -222,6 +226,18 @@ spmv_status spmv_export_csr(spmv_handle_t h, int32_t *row_ptr, int32_t *col_ind,
  * *bits. SPMV_ERR_NOT_TUNED if no delta index has been built. */
 spmv_status spmv_get_delta(spmv_handle_t h, int32_t *base, void *delta, int32_t *esc_col,
                            int64_t *n_esc, int32_t *bits, spmv_stream_t stream);
+
+/* Copies the sliced-row copy of the matrix (variant partition 3): rows in slices of 32
+ * consecutive rows (the last may hold fewer); slice s is as wide as its longest row and
+ * stores element k of row 32 s + l at position slice_off[s] + 32 k + l (slice_off: device,
+ * int64[ceil(n_rows / 32) + 1], slice_off[0] = 0). val (device, *n_positions values of the
+ * storage dtype; FP64 for SPMV_DF64 storage) and idx (device, *n_positions int32 columns when
+ * *idx_bits = 0, else column deltas of *idx_bits bits, as spmv_get_delta describes them)
+ * hold the slices; positions past a row's length are padding (zero). Any of the arrays may
+ * be NULL; all NULL queries *n_positions and *idx_bits. SPMV_ERR_NOT_TUNED if no slices have
+ * been built. */
+spmv_status spmv_get_sell(spmv_handle_t h, int64_t *slice_off, void *val, void *idx,
+                          int64_t *n_positions, int32_t *idx_bits, spmv_stream_t stream);
 
 /* Copies the column-panel copy of the matrix (variant xpath = P >= 2; Section III-E, ML,
  * with x cut into P slices that each fit in the L2): panel p holds the columns

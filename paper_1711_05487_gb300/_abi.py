@@ -107,6 +107,7 @@ _DECL = {
     "spmv_get_row_bins": (_I32, [_P, _P, _P, _P, _P, _P, _P]),
     "spmv_get_col_panels": (_I32, [_P, _P, _P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_I32),
                                    _P]),
+    "spmv_get_sell": (_I32, [_P, _P, _P, _P, ctypes.POINTER(_I64), ctypes.POINTER(_I32), _P]),
     "spmv_features": (_I32, [_P, _I32, _P, _P, _P]),
     "spmv_profile": (_I32, [_P, _I32, ctypes.POINTER(spmv_profile_report), _P]),
     "spmv_profile_cta_times": (_I32, [_P, _P, _P, ctypes.POINTER(_I32), _P]),
@@ -244,6 +245,13 @@ def spmv_get_row_bins(h, med_rows=None, long_rows=None, long_first=None, chunks=
     _call("spmv_get_row_bins", h, med_rows, long_rows, long_first, chunks,
           ctypes.cast(counts, _P), stream)
     return int(counts[0]), int(counts[1]), int(counts[2])
+
+
+def spmv_get_sell(h, slice_off=None, val=None, idx=None, stream=0):
+    """Returns (n_positions, idx_bits); copies the sliced rows when the pointers are given."""
+    n, b = _I64(), _I32()
+    _call("spmv_get_sell", h, slice_off, val, idx, ctypes.byref(n), ctypes.byref(b), stream)
+    return n.value, b.value
 
 
 def spmv_get_col_panels(h, panel_rowptr=None, panel_col=None, panel_val=None, stream=0):

@@ -239,6 +239,18 @@ class SpmvMatrix:
                                ch.data_ptr(), _stream(stream))
         return med[:n_med], lng[:n_long], first, ch[:n_ch]
 
+    def sell(self, device="cuda", stream=None):
+        """The sliced-row copy (partition 3): (slice offsets, values, columns or deltas,
+        delta bits or 0)."""
+        n, bits = _abi.spmv_get_sell(self._h)
+        ns = (self.n_rows + 31) // 32
+        off = torch.empty(ns + 1, dtype=torch.int64, device=device)
+        v = torch.empty(max(n, 1), dtype=TORCH_DTYPE[self.storage], device=device)
+        it = {0: torch.int32, 16: torch.int16, 8: torch.uint8}[bits]
+        ix = torch.empty(max(n, 1), dtype=it, device=device)
+        _abi.spmv_get_sell(self._h, off.data_ptr(), v.data_ptr(), ix.data_ptr(), _stream(stream))
+        return off, v[:n], ix[:n], bits
+
     def col_panels(self, device="cuda", stream=None):
         """The column-panel copy (variant xpath = P >= 2): (row pointers (P, n_rows + 1),
         columns, values, panel width)."""

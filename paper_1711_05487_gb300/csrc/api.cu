@@ -27,7 +27,8 @@ void default_types(spmv_dtype in, spmv_dtype *st, spmv_dtype *vec, spmv_dtype *a
 void install_storage(spmv_matrix *h, cudaStream_t s) {
   h->val_store.release();
   h->val_df.release();
-  drop_panels(h);   // the panel copy holds values of the previous storage dtype
+  drop_panels(h);   // the panel and slice copies hold values of the previous storage dtype
+  drop_sell(h);
   if (h->storage == SPMV_DF64) {
     // the FP64 input values stay the values of every non-double-float kernel
     h->val_df.alloc(8 * (size_t)h->nnz, 8, s);
@@ -262,6 +263,29 @@ spmv_status spmv_get_row_bins(spmv_handle_t h, int32_t *med_rows, int32_t *long_
   });
 }
 
+spmv_status spmv_get_sell(spmv_handle_t h, int64_t *slice_off, void *val, void *idx,
+                          int64_t *n_positions, int32_t *idx_bits, spmv_stream_t stream) {
+  if (!h || !n_positions || !idx_bits) return SPMV_ERR_ARG;
+  if (h->sell_bits < 0) return SPMV_ERR_NOT_TUNED;
+  *n_positions = h->sell_total;
+  *idx_bits = h->sell_bits;
+  if (!slice_off && !val && !idx) return SPMV_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return guarded([&]() -> spmv_status {
+    const size_t vb = h->storage == SPMV_DF64 ? 8 : dtype_bytes(h->storage);
+    const size_t ib = h->sell_bits ? (size_t)(h->sell_bits / 8) : 4;
+    const int64_t ns = (h->n_rows + 31) / 32;
+    if (slice_off)
+      CK(cudaMemcpyAsync(slice_off, h->sell_off.p, 8 * (size_t)(ns + 1), cudaMemcpyDeviceToDevice, s));
+    if (val && h->sell_total)
+      CK(cudaMemcpyAsync(val, h->sell_val.p, vb * (size_t)h->sell_total, cudaMemcpyDeviceToDevice, s));
+    if (idx && h->sell_total)
+      CK(cudaMemcpyAsync(idx, h->sell_idx.p, ib * (size_t)h->sell_total, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return SPMV_OK;
+  });
+}
+
 spmv_status spmv_get_col_panels(spmv_handle_t h, int32_t *panel_rowptr, int32_t *panel_col,
                                 void *panel_val, int32_t *n_panels, int32_t *panel_cols,
                                 spmv_stream_t stream) {
@@ -357,7 +381,8 @@ spmv_status spmv_get_device_bytes(spmv_handle_t h, int64_t *bytes) {
                           &h->esc, &h->coord, &h->tail_row, &h->tail_val, &h->head_val,
                           &h->x_stage, &h->y_stage, &h->scratch, &h->val_df, &h->bin_rows,
                           &h->bin_long_rows, &h->bin_long_first, &h->bin_chunks,
-                          &h->bin_partials, &h->pnl_rowptr, &h->pnl_col, &h->pnl_val})
+                          &h->bin_partials, &h->pnl_rowptr, &h->pnl_col, &h->pnl_val,
+                          &h->sell_off, &h->sell_val, &h->sell_idx})
     t += (int64_t)b->bytes;
   *bytes = t;
   return SPMV_OK;

@@ -163,6 +163,9 @@ struct spmv_matrix {
   int64_t bin_n_med = 0, bin_n_long = 0, bin_n_chunks = 0;
   int32_t bin_vs_short = 4;
   bool has_bins = false;
+  DevBuf sell_off, sell_val, sell_idx;   // sliced rows: column-major 32-row slices
+  int32_t sell_bits = -1;      // column representation of the built slices (0 = int32; -1 none)
+  int64_t sell_total = 0;      // slice positions, padding included
   DevBuf pnl_rowptr, pnl_col, pnl_val;   // column panels: panel-major copy of the matrix
   int32_t pnl_count = 0;       // panels of the built copy (0: none)
   int32_t pnl_width = 0;       // columns per panel
@@ -229,6 +232,10 @@ cudaError_t launch_run(const spmv_matrix *h, const spmv_variant &v, const void *
                        cudaStream_t s);
 // Frees the column-panel copy (its values follow the storage dtype).
 void drop_panels(spmv_matrix *h);
+// Frees the sliced-row copy (its values follow the storage dtype).
+void drop_sell(spmv_matrix *h);
+// Positions of the sliced-row layout of the matrix, padding included (no copy is built).
+int64_t sell_positions(spmv_matrix *h, cudaStream_t s);
 // Frees the captured host-buffer pipeline.
 void drop_host_graph(spmv_matrix *h);
 

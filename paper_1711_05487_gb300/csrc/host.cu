@@ -64,7 +64,8 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
                      (int64_t)vb * (h->n_rows + h->n_cols) >= 8000000;
     const int n_pass = h->variant.xpath >= 2 ? h->variant.xpath : 0;
     const bool panels = n_pass >= 2 && n_pass <= kHostChunks && big;
-    const bool chunked = h->variant.partition == 0 && h->variant.xpath < 2 && big;
+    const bool chunked = (h->variant.partition == 0 || h->variant.partition == 3) &&
+                         h->variant.xpath < 2 && big;
     const int nch = (chunked || panels) ? kHostChunks : 1;
     // chunk row boundaries: equal parts aligned to 128 rows
     int64_t per = (h->n_rows + nch - 1) / nch;
@@ -123,6 +124,7 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
           a.n_rows = r1 - r0;
           a.rowptr += r0;
           if (a.dbase) a.dbase += r0;
+          if (a.sell_off) a.sell_off += r0 / 32;   // chunks start on 128-row boundaries
           CK(ks->spmv(h->variant, a, cs));
         }
         CK(cudaEventRecord(h->chunk_done[c], cs));

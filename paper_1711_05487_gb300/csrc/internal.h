@@ -74,6 +74,12 @@ struct RunArgs {
   int64_t pnl_stride = 0;
   int32_t pnl_first = 0;
   int32_t n_panels = 0;
+  // sliced rows (partition 3): 32-row slices stored column-major; element k of row r at
+  // sell_off[r / 32] + 32 k + r % 32 of sell_val and sell_idx (int32 columns, or column
+  // deltas of delta_bits bits with dbase / esc as for the delta index)
+  const int64_t *sell_off = nullptr;
+  const void *sell_val = nullptr;
+  const void *sell_idx = nullptr;
 };
 
 // Column panels: at most this many slices of x (variant field xpath = panel count).
@@ -234,6 +240,16 @@ cudaError_t launch_panel_fill(int64_t n_rows, const int32_t *rowptr, const int32
                               const void *val, int val_bytes, int32_t n_panels,
                               const int64_t *off, int32_t *pnl_rowptr, int32_t *pnl_col,
                               void *pnl_val, cudaStream_t s);
+
+// Sliced rows: 32 x (the longest row) of every 32-row slice (int64, for the scan into slice
+// offsets), then the column-major copy of the values (val_bytes 2, 4 or 8) and of the column
+// representation (idx_bytes 4: int32 columns; 2 or 1: column deltas), padding left as it is.
+cudaError_t launch_sell_widths(int64_t n_rows, const int32_t *rowptr, int64_t *w32,
+                               cudaStream_t s);
+cudaError_t launch_sell_fill(int64_t n_rows, const int32_t *rowptr, const void *val,
+                             int val_bytes, const void *idx, int idx_bytes,
+                             const int64_t *soff, void *sell_val, void *sell_idx,
+                             cudaStream_t s);
 
 // Largest column of each row chunk (host-buffer pipelining)
 cudaError_t launch_chunk_colmax(int64_t n_rows, const int32_t *rowptr, const int32_t *colind,

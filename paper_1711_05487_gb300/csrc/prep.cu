@@ -729,6 +729,76 @@ cudaError_t launch_bin_fill(int64_t n_rows, const int32_t *rowptr, const int32_t
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------- sliced rows ----
+__global__ void k_sell_widths(int64_t n_rows, const int32_t *rowptr, int64_t *w32) {
+  const int64_t sl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= (n_rows + 31) / 32) return;
+  const int64_t r1 = min(32 * sl + 32, n_rows);
+  int w = 0;
+  for (int64_t r = 32 * sl; r < r1; ++r) w = max(w, rowptr[r + 1] - rowptr[r]);
+  w32[sl] = 32 * (int64_t)w;
+}
+
+// Thread per row: element k of row r goes to soff[r / 32] + 32 k + r % 32.
+template <typename VT, typename IT>
+__global__ void k_sell_fill(int64_t n_rows, const int32_t *rowptr, const VT *val, const IT *idx,
+                            const int64_t *soff, VT *sval, IT *sidx) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_rows) return;
+  const int64_t p0 = soff[r >> 5] + (r & 31);
+  const int s = rowptr[r], len = rowptr[r + 1] - s;
+  for (int k = 0; k < len; ++k) {
+    sval[p0 + 32 * (int64_t)k] = val[s + k];
+    sidx[p0 + 32 * (int64_t)k] = idx[s + k];
+  }
+}
+
+cudaError_t launch_sell_widths(int64_t n_rows, const int32_t *rowptr, int64_t *w32,
+                               cudaStream_t s) {
+  if (n_rows <= 0) return cudaSuccess;
+  k_sell_widths<<<blocks_for((n_rows + 31) / 32), kT, 0, s>>>(n_rows, rowptr, w32);
+  return cudaGetLastError();
+}
+
+template <typename VT>
+static cudaError_t sell_fill_v(int64_t n, const int32_t *rowptr, const void *val, const void *idx,
+                               int idx_bytes, const int64_t *soff, void *sv, void *si,
+                               cudaStream_t s) {
+  const unsigned g = blocks_for(n);
+  const VT *v = static_cast<const VT *>(val);
+  VT *o = static_cast<VT *>(sv);
+  switch (idx_bytes) {
+    case 4:
+      k_sell_fill<VT, int32_t><<<g, kT, 0, s>>>(n, rowptr, v, static_cast<const int32_t *>(idx),
+                                                soff, o, static_cast<int32_t *>(si));
+      break;
+    case 2:
+      k_sell_fill<VT, uint16_t><<<g, kT, 0, s>>>(n, rowptr, v, static_cast<const uint16_t *>(idx),
+                                                 soff, o, static_cast<uint16_t *>(si));
+      break;
+    case 1:
+      k_sell_fill<VT, uint8_t><<<g, kT, 0, s>>>(n, rowptr, v, static_cast<const uint8_t *>(idx),
+                                                soff, o, static_cast<uint8_t *>(si));
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sell_fill(int64_t n_rows, const int32_t *rowptr, const void *val,
+                             int val_bytes, const void *idx, int idx_bytes,
+                             const int64_t *soff, void *sell_val, void *sell_idx,
+                             cudaStream_t s) {
+  if (n_rows <= 0) return cudaSuccess;
+  switch (val_bytes) {
+    case 8: return sell_fill_v<uint64_t>(n_rows, rowptr, val, idx, idx_bytes, soff, sell_val, sell_idx, s);
+    case 4: return sell_fill_v<uint32_t>(n_rows, rowptr, val, idx, idx_bytes, soff, sell_val, sell_idx, s);
+    case 2: return sell_fill_v<uint16_t>(n_rows, rowptr, val, idx, idx_bytes, soff, sell_val, sell_idx, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // ------------------------------------------------------------------ column panels ----
 // Thread per row: the row's columns are sorted, so its part in panel b starts at the first
 // column >= b * width (binary search between the previous boundary and the row's end).

@@ -9,6 +9,8 @@
 //  k_rowtile - thread-per-row tiles staged by TMA bulk copies (spmv_tile.cuh).
 //  k_bins_*  - row decomposition: short rows by sub-warps, medium rows by warps, long rows
 //              split into chunks with a fixed-order FP64 fixup (IMB).
+//  k_sell    - sliced rows (SELL-32): thread per row over 32-row slices stored column-major,
+//              coalesced loads without a shared-memory stage (CMP, with or without deltas).
 //  k_panel   - one pass of the column-panel variant (ML, x larger than the L2): the rows'
 //              nonzeros in one L2-sized slice of x, from a panel-major copy of the matrix.
 //  k_merge   - merge-path tiles of equal (rows + nonzeros) work; rows longer than a tile
@@ -290,6 +292,85 @@ __global__ void __launch_bounds__(kRowThreads) k_panel(const RunArgs a,
     VecT *y = static_cast<VecT *>(a.y);
     y[row] = add ? (VecT)((AccT)y[row] + sum) : (VecT)sum;
   }
+}
+
+// -------------------------------------------------------------------------- k_sell ----
+// Sliced rows (SELL-32, partition 3): one thread per row over a layout in which the 32 rows of
+// a slice lie column-major, so that the k-th elements of a warp's rows are one contiguous
+// 256-byte (FP64) run: every value and column load is coalesced without a shared-memory
+// stage, and the occupancy is set by registers alone. 16 (then 8) x gathers in flight per
+// thread before their FMAs, one FMA per nonzero, exact trip counts (padding is never read).
+constexpr int kSellThreads = 128;
+
+template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
+__global__ void __launch_bounds__(kSellThreads) k_sell(const RunArgs a) {
+  using IdxT = typename IdxOf<DB>::type;
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= a.n_rows) return;
+  const int64_t p0 = __ldg(a.sell_off + (row >> 5)) + (row & 31);
+  const int len = __ldg(a.rowptr + row + 1) - __ldg(a.rowptr + row);
+  const ValT *__restrict__ sv = static_cast<const ValT *>(a.sell_val) + p0;
+  const IdxT *__restrict__ si = static_cast<const IdxT *>(a.sell_idx) + p0;
+  const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
+  uint64_t pol_x = 0;
+  if constexpr (XL2) pol_x = policy_evict_last();
+  int c = 0;
+  const int32_t *ec = nullptr;
+  if constexpr (DB != 0) {
+    const int32_t base = __ldg(a.dbase + row);
+    if (base < 0) ec = a.esc + (-(int64_t)base - 1);
+    else c = base;
+  }
+  auto column = [&](int k) -> int {
+    if constexpr (DB != 0) {
+      if (ec) return __ldg(ec + k);
+      c += (int)__ldg(si + 32 * (int64_t)k);
+      return c;
+    } else {
+      return __ldg(si + 32 * (int64_t)k);
+    }
+  };
+  AccT acc = 0;
+  int k = 0;
+  for (; k + 16 <= len; k += 16) {
+    AccT xv[16], v[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      xv[q] = (AccT)ldx<XL2>(x + column(k + q), pol_x);
+      v[q] = widen<AccT>(__ldg(sv + 32 * (int64_t)(k + q)));
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) acc = fma(v[q], xv[q], acc);
+  }
+  for (; k + 8 <= len; k += 8) {
+    AccT xv[8], v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      xv[q] = (AccT)ldx<XL2>(x + column(k + q), pol_x);
+      v[q] = widen<AccT>(__ldg(sv + 32 * (int64_t)(k + q)));
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc = fma(v[q], xv[q], acc);
+  }
+  for (; k < len; ++k)
+    acc = fma(widen<AccT>(__ldg(sv + 32 * (int64_t)k)), (AccT)ldx<XL2>(x + column(k), pol_x), acc);
+  static_cast<VecT *>(a.y)[row] = (VecT)acc;
+}
+
+template <typename ValT, typename VecT, typename AccT>
+cudaError_t launch_sell(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
+  if (!a.sell_off || !a.sell_val || !a.sell_idx) return cudaErrorInvalidValue;
+  const unsigned g = (unsigned)((a.n_rows + kSellThreads - 1) / kSellThreads);
+  const bool xl2 = v.xpath != 0;
+  const int db = v.index == 1 ? a.delta_bits : 0;
+#define SPMV_SELL(DB_)                                                                \
+  (xl2 ? k_sell<ValT, VecT, AccT, DB_, true><<<g, kSellThreads, 0, s>>>(a)           \
+       : k_sell<ValT, VecT, AccT, DB_, false><<<g, kSellThreads, 0, s>>>(a))
+  if (db == 16) SPMV_SELL(16);
+  else if (db == 8) SPMV_SELL(8);
+  else SPMV_SELL(0);
+#undef SPMV_SELL
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------- k_merge ----
@@ -749,6 +830,7 @@ template <typename ValT, typename VecT, typename AccT>
 cudaError_t launch_spmv_impl(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
   if (a.n_rows == 0) return cudaSuccess;
   if (v.xpath >= 2) return launch_panels<ValT, VecT, AccT>(v, a, s);
+  if (v.partition == 3) return launch_sell<ValT, VecT, AccT>(v, a, s);
   if (v.partition == 2)
     return launch_bins<ValT, VecT, AccT>(v.index == 1 ? a.delta_bits : 0, v.xpath != 0, a, s);
   if (v.partition == 1) {

@@ -438,8 +438,9 @@ void sweep_panels(spmv_matrix *h, spmv_variant &v, float best, const void *x, vo
 // the thread-per-row kernel (width 1) wins, its geometry is swept too: 128 / 64 / 32 rows
 // per tile, one tile per CTA or persistent CTAs with two tiles in flight.
 // Called by spmv_tune for the routes that choose a variant (never for SPMV_TUNE_FIXED), so
-// the sub-warp width and, for width 1, the tile geometry are always swept; ML matrices
-// whose x exceeds half the L2 then try column panels (sweep_panels).
+// the sub-warp width and, for width 1, the tile geometry are always swept; then sliced rows
+// (short rows, little padding) and, for ML matrices whose x exceeds half the L2, column
+// panels (sweep_panels) compete with the winner.
 void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, cudaStream_t s) {
   if (h->n_rows == 0) return;
   const size_t vb = dtype_bytes(h->vec);
@@ -506,7 +507,24 @@ void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, cudaStream_t s) {
     v.tile_rows = best_rows;
     v.tile_pipe = best_pipe;
   }
+  // Sliced rows (thread per row without a shared-memory stage) compete with the best row
+  // variant when rows are short and the slices pad the matrix by at most an eighth.
+  if (h->nnz_avg() <= 64.0 && v.xpath < 2 &&
+      sell_positions(h, s) <= h->nnz + h->nnz / 8 + 32 * ((h->n_rows + 31) / 32)) {
+    spmv_variant t = v;
+    t.partition = 3;
+    t.vs = 1;
+    prepare_variant(h, t, s);
+    const float ms = time_launches([&]() { return launch_run(h, t, x.p, y.p, s); }, reps, s);
+    if (ms < best) {
+      best = ms;
+      v = t;
+    } else {
+      drop_sell(h);
+    }
+  }
   sweep_panels(h, v, best, x.p, y.p, reps, s);
+  if (v.partition != 3) drop_sell(h);
 }
 
 }  // namespace

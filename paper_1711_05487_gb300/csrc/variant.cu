@@ -47,6 +47,9 @@ RunArgs run_args(const spmv_matrix *h, const void *x, void *y) {
   a.pnl_rowptr = h->pnl_rowptr.as<int32_t>();
   a.pnl_col = h->pnl_col.as<int32_t>();
   a.pnl_val = h->pnl_val.p;
+  a.sell_off = h->sell_off.as<int64_t>();
+  a.sell_val = h->sell_val.p;
+  a.sell_idx = h->sell_idx.p;
   a.pnl_stride = h->n_rows + 1;
   a.pnl_first = 0;
   a.n_panels = h->pnl_count;
@@ -178,6 +181,42 @@ void build_panels(spmv_matrix *h, int n_panels, cudaStream_t s) {
   h->pnl_width = (int32_t)w;
 }
 
+// Slice offsets of the sliced-row layout: 32 x the longest row of each 32-row slice, scanned
+// (n_slices + 1 entries, the last one the total).
+DevBuf sell_offsets(spmv_matrix *h, int64_t *total, cudaStream_t s) {
+  const int64_t ns = (h->n_rows + 31) / 32;
+  DevBuf off;
+  off.alloc(sizeof(int64_t) * (size_t)(ns + 1), 8, s, true);
+  CK(launch_sell_widths(h->n_rows, h->rowptr.as<int32_t>(), off.as<int64_t>(), s));
+  const int64_t se = scan_scratch_elems(ns);
+  DevBuf scr;
+  scr.alloc(sizeof(int64_t) * (size_t)se, 8, s);
+  CK(launch_scan_i64(off.as<int64_t>(), ns, off.as<int64_t>() + ns, scr.as<int64_t>(), se, s));
+  CK(cudaMemcpyAsync(total, off.as<int64_t>() + ns, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return off;
+}
+
+// Sliced rows (partition 3): the column-major copy of the values the kernels read and of the
+// columns (bits = 0) or of the delta index's deltas (bits = 8 or 16).
+void build_sell(spmv_matrix *h, int bits, cudaStream_t s) {
+  if (h->sell_bits == bits) return;
+  drop_sell(h);
+  int64_t total = 0;
+  DevBuf off = sell_offsets(h, &total, s);
+  const size_t vb = h->storage == SPMV_DF64 ? 8 : dtype_bytes(h->storage);
+  const size_t ib = bits ? (size_t)(bits / 8) : 4;
+  h->sell_val.alloc(vb * (size_t)total, vb, s, true);
+  h->sell_idx.alloc(ib * (size_t)total, ib, s, true);
+  CK(launch_sell_fill(h->n_rows, h->rowptr.as<int32_t>(), h->val_ptr(), (int)vb,
+                      bits ? h->delta.p : (const void *)h->colind.p, (int)ib,
+                      off.as<int64_t>(), h->sell_val.p, h->sell_idx.p, s));
+  CK(cudaStreamSynchronize(s));
+  h->sell_off = std::move(off);
+  h->sell_total = total;
+  h->sell_bits = bits;
+}
+
 // Geometry of the thread-per-row kernel. A staged tile holds the values and columns of
 // `rows` consecutive rows; the staged capacity is the matrix's largest such tile, capped by
 // the shared-memory budget of one stage (48 KB for one tile per CTA, 56 KB per stage for
@@ -230,6 +269,20 @@ void compute_tile_cap(spmv_matrix *h, const spmv_variant &v, cudaStream_t s) {
   set_tile_geometry(h, v, kTileRows, false, s);
 }
 
+void drop_sell(spmv_matrix *h) {
+  h->sell_off.release();
+  h->sell_val.release();
+  h->sell_idx.release();
+  h->sell_bits = -1;
+  h->sell_total = 0;
+}
+
+int64_t sell_positions(spmv_matrix *h, cudaStream_t s) {
+  int64_t total = 0;
+  sell_offsets(h, &total, s);
+  return total;
+}
+
 void drop_panels(spmv_matrix *h) {
   h->pnl_rowptr.release();
   h->pnl_col.release();
@@ -247,6 +300,16 @@ void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
     v.tile_pipe = 0;
     if (v.vs == 0) v.vs = std::min(8, pow2_ceil_clamped(h->nnz_avg() / v.xpath, 1, 8));
     build_panels(h, v.xpath, s);
+    return;
+  }
+  if (v.partition == 3) {
+    // sliced rows: thread per row, int32 columns or the delta index's deltas
+    if (v.index == 1) build_delta(h, s);
+    v.vec = 1;
+    v.vs = 1;
+    v.tile_rows = 0;
+    v.tile_pipe = 0;
+    build_sell(h, v.index == 1 ? h->delta_bits : 0, s);
     return;
   }
   if (v.partition == 1) {
@@ -287,7 +350,8 @@ void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
 }
 
 bool valid_variant(const spmv_variant &v) {
-  if (v.partition < 0 || v.partition > 2) return false;
+  if (v.partition < 0 || v.partition > 3) return false;
+  if (v.partition == 3 && v.vs != 0 && v.vs != 1) return false;
   if (v.partition == 2 && v.vs != 0 && v.vs != 2 && v.vs != 4 && v.vs != 8) return false;
   if (v.index != 0 && v.index != 1) return false;
   if (v.xpath < 0 || v.xpath > kMaxPanels) return false;

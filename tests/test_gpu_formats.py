@@ -59,6 +59,39 @@ def test_delta_index_bit_exact_and_round_trip(api, name):
     assert np.array_equal(v.cpu().numpy().view(np.uint64), m.val.view(np.uint64))
 
 
+@pytest.mark.parametrize("index", [0, 1])
+@pytest.mark.parametrize("name", ["st27_14", "lap2d_200", "scattered_escape", "ragged_empty",
+                                  "identity1"])
+def test_sell_bit_exact(api, name, index):
+    """The sliced-row copy equals the oracle's layout: slice offsets, the stored values at
+    their positions, the columns (index 0) or the delta index's deltas (index 1, 8 or 16
+    bits, escape rows included), zero padding; FP32 storage keeps its own values."""
+    m = FORMAT_MATS[name]()
+    soff, perm = oracle.sell32(m.rowptr)
+    pad = perm < 0
+    src = np.where(pad, 0, perm)
+    for storage in ("f64", "f32"):
+        A = api.SpmvMatrix.from_csr(m)
+        if storage == "f32":
+            A.set_precision("f32", "f32", "f32")
+        A.set_variant(partition=3, index=index)
+        off, v, ix, bits = A.sell()
+        assert np.array_equal(off.cpu().numpy(), soff)
+        want_v = np.where(pad, 0.0, stored_values(m.val, storage)[src] if m.nnz else 0.0)
+        assert np.array_equal(v.cpu().numpy().astype(np.float64), want_v)
+        if index == 0:
+            assert bits == 0
+            want_i = np.where(pad, 0, m.colind[src] if m.nnz else 0)
+            assert np.array_equal(ix.cpu().numpy(), want_i)
+        else:
+            assert bits == oracle.delta_width(m.rowptr, m.colind)
+            enc = oracle.delta8_encode if bits == 8 else oracle.delta16_encode
+            _, od, _ = enc(m.rowptr, m.colind)
+            want_d = np.where(pad, 0, od[src] if m.nnz else 0)
+            got = ix.cpu().numpy().view(np.uint8 if bits == 8 else np.uint16)
+            assert np.array_equal(got, want_d)
+
+
 @pytest.mark.parametrize("name", list(FORMAT_MATS))
 def test_merge_path_table_bit_exact(api, name):
     m = FORMAT_MATS[name]()

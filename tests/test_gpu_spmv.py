@@ -55,6 +55,8 @@ VARIANTS = (
        for p in (0, 1)]                                                # width-1 tiles
     + [dict(xpath=p, vs=w, vec=c) for p, w, c in ((2, 1, 0), (2, 4, 1), (3, 2, 0), (5, 8, 1),
                                                   (16, 1, 1))]         # ML: column panels
+    + [dict(partition=3), dict(partition=3, index=1), dict(partition=3, xpath=1),
+       dict(partition=3, index=1, xpath=1)]                            # sliced rows
 )
 
 
@@ -143,7 +145,8 @@ def test_precisions(api, torch, name, storage, vec, acc):
                 dict(vec=1, xpath=1, vs=8), dict(vec=1, vs=1),
                 dict(index=1, vec=1, vs=1, tile_rows=64, tile_pipe=1),
                 dict(vec=1, vs=1, tile_rows=32, xpath=1),
-                dict(xpath=2, vs=2), dict(xpath=3, vs=1, vec=1)]
+                dict(xpath=2, vs=2), dict(xpath=3, vs=1, vec=1),
+                dict(partition=3, index=1), dict(partition=3)]
     for v in variants:
         A.set_variant(**v)
         y = A.run(x).double().cpu().numpy()
@@ -195,7 +198,7 @@ def test_run_host_equals_device_run(api, torch, gen):
     yh = torch.empty(m.n_rows, dtype=torch.float64).pin_memory()
     for v in (dict(index=1, vec=1), dict(vec=1, vs=1, tile_rows=64, tile_pipe=1),
               dict(vec=1, vs=4), dict(partition=1), dict(xpath=2, vs=4),
-              dict(xpath=3, vs=1, vec=1)):
+              dict(xpath=3, vs=1, vec=1), dict(partition=3, index=1)):
         A.set_variant(**v)
         yd = A.run(torch.from_numpy(x64).cuda()).cpu()
         yh.fill_(float("nan"))
