@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kRowThreads) k_panel(const RunArgs a,
 constexpr int kSellThreads = 128;
 
 template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
-__global__ void __launch_bounds__(kSellThreads) k_sell(const RunArgs a) {
+__global__ void __launch_bounds__(kSellThreads, 10) k_sell(const RunArgs a) {
   using IdxT = typename IdxOf<DB>::type;
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= a.n_rows) return;
