@@ -158,11 +158,20 @@ def dtype_bytes(code):
     return {0: 8, 1: 4, 2: 2, 3: 8}[code]
 
 
-def alg_bytes(n_rows, n_cols, nnz, variant, storage, vec):
+def alg_bytes(n_rows, n_cols, nnz, variant, storage, vec, handle=None):
     """Compulsory traffic of one SpMV with the variant's own format (P_MB's M_min):
     row pointers, column indices (int32 or 16-bit deltas + per-row base), values, x, y.
     Column panels (xpath = P >= 2) read P sets of row pointers and pass over y 2P - 1 times
-    (written once, then read and written by every later pass)."""
+    (written once, then read and written by every later pass). Sliced rows (partition 3)
+    read their padded positions and one 8-byte offset per 32-row slice."""
+    if variant[0] == 3 and handle is not None:
+        from paper_1711_05487_gb300 import _abi
+        positions, bits = _abi.spmv_get_sell(handle)
+        vb = 8 if storage == 3 else dtype_bytes(storage)
+        ib = bits // 8 if bits else 4
+        extra = 4 * n_rows if bits else 0
+        return (4 * (n_rows + 1) + 8 * ((n_rows + 31) // 32 + 1) + (ib + vb) * positions
+                + extra + dtype_bytes(vec) * (n_rows + n_cols))
     if len(variant) > 2 and variant[2] >= 2:
         p = variant[2]
         vb = 8 if storage == 3 else dtype_bytes(storage)
@@ -262,7 +271,7 @@ def run_ours(args, rank, world):
     storage = A.storage
     traffic = measured_traffic(args.workload + ("" if args.precision == "native"
                                                  else "/" + args.precision), rep.variant)
-    ab = alg_bytes(m.n_rows, m.n_cols, m.nnz, rep.variant, storage, A.vec)
+    ab = alg_bytes(m.n_rows, m.n_cols, m.nnz, rep.variant, storage, A.vec, A.handle)
     achieved = ab / (ms * 1e-3) / 1e9
     csr_bytes = alg_bytes(m.n_rows, m.n_cols, m.nnz, (0, 0, 0, 0, 0), storage, A.vec)
     value = whole_job_rate(flops, ms, world)
@@ -352,7 +361,7 @@ def run_ours(args, rank, world):
             x, y = xv, yv
             t2 = timed(args.steps, args.warmup)
             x, y = x_old, y_old
-            b2 = alg_bytes(m.n_rows, m.n_cols, m.nnz, r2.variant, A.storage, A.vec)
+            b2 = alg_bytes(m.n_rows, m.n_cols, m.nnz, r2.variant, A.storage, A.vec, A.handle)
             extra[f"{st}/{vt}/{at}"] = {
                 "gflops": round(flops / (t2 * 1e-3) / 1e9, 1),
                 "variant": list(r2.variant), "classes": r2.class_names,
@@ -561,7 +570,7 @@ def run_cg(args, rank, world):
     clocks.stop()
     t, rep, tr = tuned
     it = max(1, rep["iters"])
-    spmv_b = alg_bytes(m.n_rows, m.n_cols, m.nnz, tr.variant, 0, 0)
+    spmv_b = alg_bytes(m.n_rows, m.n_cols, m.nnz, tr.variant, 0, 0, A.handle)
     iter_b = spmv_b + 88 * m.n_rows     # + dot(p,Ap) 16N, x/r update 48N, p update 24N
     achieved = iter_b / (t / it * 1e-3) / 1e9
     return {
