@@ -166,7 +166,10 @@ def alg_bytes(n_rows, n_cols, nnz, variant, storage, vec, handle=None):
     read their padded positions and one 8-byte offset per 32-row slice."""
     if variant[0] == 3 and handle is not None:
         from paper_1711_05487_gb300 import _abi
-        positions, bits = _abi.spmv_get_sell(handle)
+        try:
+            positions, bits = _abi.spmv_get_sell(handle)
+        except _abi.SpmvError:      # the handle has since been re-tuned without slices
+            positions, bits = nnz, (16 if variant[1] == 1 else 0)
         vb = 8 if storage == 3 else dtype_bytes(storage)
         ib = bits // 8 if bits else 4
         extra = 4 * n_rows if bits else 0
@@ -570,7 +573,7 @@ def run_cg(args, rank, world):
     clocks.stop()
     t, rep, tr = tuned
     it = max(1, rep["iters"])
-    spmv_b = alg_bytes(m.n_rows, m.n_cols, m.nnz, tr.variant, 0, 0, A.handle)
+    spmv_b = alg_bytes(m.n_rows, m.n_cols, m.nnz, tr.variant, 0, 0)
     iter_b = spmv_b + 88 * m.n_rows     # + dot(p,Ap) 16N, x/r update 48N, p update 24N
     achieved = iter_b / (t / it * 1e-3) / 1e9
     return {
