@@ -341,7 +341,7 @@ def run_ours(args, rank, world):
                 "tile_i32": dict(vec=1, vs=1), "tile_delta16": dict(index=1, vec=1, vs=1),
                 "tile_i32_xl2": dict(vec=1, vs=1, xpath=1),
                 "subwarp_delta16": dict(index=1, vec=1, vs=4), "merge_path": dict(partition=1),
-                "col_panels_2": dict(xpath=2, vs=2)}
+                "col_panels_2": dict(xpath=2, vs=2), "sliced_delta16": dict(partition=3, index=1)}
         for name, knobs in pool.items():
             A.set_variant(stream=stream, **knobs)
             t_v = timed(max(8, args.steps // 4), args.warmup)
