@@ -459,6 +459,10 @@ def run_batched(args, rank, world):
         flops += 2.0 * m.nnz * k
         nbytes += 4 * (m.n_rows + 1) + 8 * m.nnz + 4 * k * (m.n_rows + m.n_cols)
     B = api.Batch(As, Xs, Ys, ks, stream=stream)
+    # the batch's work plan (items per warp, chunk length of split rows) by its autotuner
+    t0 = time.perf_counter()
+    plan = B.tune(reps=5, stream=stream)
+    t_plan = (time.perf_counter() - t0) * 1e3
 
     def timed(fn, K, W, tag):
         with torch.cuda.stream(stream):
@@ -506,7 +510,9 @@ def run_batched(args, rank, world):
                                 "ms": round(seq_ms, 4)},
         "speedup_vs_sequential": round(seq_ms / ms, 3),
         "tune": {"route": "learned" if sel is not None else "fixed",
-                 "t_pre_ms_total": round(t_tune, 1)},
+                 "t_pre_ms_total": round(t_tune, 1),
+                 "plan": {"item_nnz": plan[0], "chunk_nnz": plan[1],
+                          "t_tune_ms": round(t_plan, 1)}},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
                      "peak_kind": peak_kind, "alg_bytes": nbytes},

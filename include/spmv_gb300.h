@@ -504,6 +504,21 @@ spmv_status spmv_batch_create(spmv_batch_t *out, const spmv_handle_t *handles, i
  * counter) plus a fixup launch, replayed from a CUDA graph captured on the first call. */
 spmv_status spmv_run_batched(spmv_batch_t b, spmv_stream_t stream);
 
+/* The batch's work plan: row blocks of about item_nnz nonzeros per warp (at most 1024 rows),
+ * rows longer than item_nnz split into chunks of chunk_nnz nonzeros whose FP64 partials the
+ * fixup adds in chunk order (defaults 1024 and 2048). Rebuilds the items and drops the
+ * captured graph; synchronizes the device. SPMV_ERR_ARG unless 32 <= item_nnz <= 65536 and
+ * item_nnz <= chunk_nnz <= 2^20. */
+spmv_status spmv_batch_set_plan(spmv_batch_t b, int32_t item_nnz, int32_t chunk_nnz,
+                                spmv_stream_t stream);
+
+/* Autotuner of the batch plan: times `reps` replays (after two warm-ups) of each plan with
+ * item_nnz in {256, 512, 1024, 2048} and chunk_nnz = 2 or 4 x item_nnz, keeps the fastest
+ * and returns it in *item_nnz / *chunk_nnz (either may be NULL). Runs the batch, so X must
+ * hold valid inputs and Y is overwritten. */
+spmv_status spmv_batch_tune(spmv_batch_t b, int32_t reps, int32_t *item_nnz, int32_t *chunk_nnz,
+                            spmv_stream_t stream);
+
 /* The same work as plain per-matrix launches (no graph, no persistence), for comparison. */
 spmv_status spmv_run_batched_sequential(spmv_batch_t b, spmv_stream_t stream);
 

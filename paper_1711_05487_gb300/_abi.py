@@ -135,6 +135,8 @@ _DECL = {
     "spmv_selector_set_range": (_I32, [_P, _P, _P, ctypes.c_float]),
     "spmv_batch_create": (_I32, [ctypes.POINTER(_P), _P, _I32, _P, _P, _P, _P]),
     "spmv_run_batched": (_I32, [_P, _P]),
+    "spmv_batch_set_plan": (_I32, [_P, _I32, _I32, _P]),
+    "spmv_batch_tune": (_I32, [_P, _I32, ctypes.POINTER(_I32), ctypes.POINTER(_I32), _P]),
     "spmv_run_batched_sequential": (_I32, [_P, _P]),
     "spmv_batch_destroy": (_I32, [_P]),
     "spmv_run_noalloc": (_I32, [_I64, _I64, _I64, _P, _P, _P, _P, _P, _P]),
@@ -396,6 +398,17 @@ def spmv_batch_create(handles, X, Y, k, stream=0):
     b = _P()
     _call("spmv_batch_create", ctypes.byref(b), H, n, XX, YY, KK, stream)
     return b.value
+
+
+def spmv_batch_set_plan(b, item_nnz, chunk_nnz, stream=0):
+    _call("spmv_batch_set_plan", b, int(item_nnz), int(chunk_nnz), stream)
+
+
+def spmv_batch_tune(b, reps=5, stream=0):
+    """Returns the (item_nnz, chunk_nnz) plan the autotuner kept."""
+    i, c = _I32(), _I32()
+    _call("spmv_batch_tune", b, int(reps), ctypes.byref(i), ctypes.byref(c), stream)
+    return i.value, c.value
 
 
 def spmv_run_batched(b, stream=0):

@@ -343,6 +343,13 @@ class Batch:
     def run(self, stream=None):
         _abi.spmv_run_batched(self.handle, _stream(stream))
 
+    def set_plan(self, item_nnz, chunk_nnz, stream=None):
+        _abi.spmv_batch_set_plan(self.handle, item_nnz, chunk_nnz, _stream(stream))
+
+    def tune(self, reps=5, stream=None):
+        """Times the candidate work plans and keeps the fastest: (item_nnz, chunk_nnz)."""
+        return _abi.spmv_batch_tune(self.handle, reps, _stream(stream))
+
     def run_sequential(self, stream=None):
         _abi.spmv_run_batched_sequential(self.handle, _stream(stream))
 

@@ -10,8 +10,9 @@
 using namespace spmv;
 
 namespace {
-// Target nonzeros per row-block item (a warp's work); rows longer than this are split into
-// chunks of kChunkNnz nonzeros (the matrix decomposition applied per item).
+// Default plan: target nonzeros per row-block item (a warp's work); rows longer than this
+// are split into chunks of kChunkNnz nonzeros (the matrix decomposition applied per item).
+// spmv_batch_tune picks both by timing.
 constexpr int32_t kItemNnz = 1024;
 constexpr int32_t kChunkNnz = 2048;
 constexpr int32_t kItemRowsMax = 1024;
@@ -41,6 +42,9 @@ struct spmv_batch {
   std::vector<const void *> X;
   std::vector<void *> Y;
   std::vector<int32_t> k;
+  std::vector<BatchMat> mats;            // per matrix: arrays, k and sub-warp width
+  std::vector<std::vector<int32_t>> rowptr;   // host copies, for re-planning
+  int32_t item_nnz = kItemNnz, chunk_nnz = kChunkNnz;
   BatchMat *d_mats = nullptr;
   BatchItem *d_items = nullptr;          // items of k = 1, then k = 4, then k = 16
   BatchFix *d_fix = nullptr;
@@ -74,6 +78,101 @@ static void batch_free(spmv_batch *b) {
   delete b;
 }
 
+// The work plan for (item_nnz, chunk_nnz): row blocks of about item_nnz nonzeros per warp,
+// rows longer than item_nnz split into chunks of chunk_nnz nonzeros with FP64 partials,
+// longest items first; uploads the items, the fixups and the partial slots, sizes the
+// persistent grids and drops the captured graph.
+static void batch_plan(spmv_batch *b, int32_t item_nnz, int32_t chunk_nnz, cudaStream_t s) {
+  std::vector<BatchItem> items_k[3];
+  std::vector<BatchFix> fix;
+  int32_t chunks = 0;
+  for (int32_t m = 0; m < b->count; ++m) {
+    const std::vector<int32_t> &hrp = b->rowptr[(size_t)m];
+    const int32_t n_rows = (int32_t)hrp.size() - 1;
+    std::vector<BatchItem> &items = items_k[k_slot(b->k[(size_t)m])];
+    int32_t r = 0;
+    while (r < n_rows) {
+      const int32_t len = hrp[(size_t)r + 1] - hrp[(size_t)r];
+      if (len > item_nnz) {
+        const int32_t first = chunks;
+        int32_t cnt = 0;
+        for (int32_t z = hrp[(size_t)r]; z < hrp[(size_t)r + 1]; z += chunk_nnz) {
+          const int32_t ze = std::min(z + chunk_nnz, hrp[(size_t)r + 1]);
+          items.push_back(BatchItem{m, r, r + 1, z, ze, chunks++});
+          ++cnt;
+        }
+        fix.push_back(BatchFix{m, r, first, cnt});
+        ++r;
+        continue;
+      }
+      int32_t e = r;
+      int64_t acc = 0;
+      while (e < n_rows && e - r < kItemRowsMax) {
+        const int32_t l = hrp[(size_t)e + 1] - hrp[(size_t)e];
+        if (l > item_nnz || (acc + l > item_nnz && e > r)) break;
+        acc += l;
+        ++e;
+      }
+      items.push_back(BatchItem{m, r, e, 0, (int32_t)acc, -1});   // nz_end: the block's nnz
+      r = e;
+    }
+  }
+  // Longest items first (chunks of split rows, then full row blocks, then the short
+  // remainders), so that the last items the warps take are the cheapest; the sort is
+  // stable, so items of one matrix stay together within a class (x rows stay L2-hot).
+  auto item_class = [&](const BatchItem &it) -> int {
+    if (it.chunk >= 0) return 0;
+    return it.nz_end >= item_nnz / 2 ? 1 : 2;
+  };
+  std::vector<BatchItem> items;
+  for (int q = 0; q < 3; ++q) {
+    std::stable_sort(items_k[q].begin(), items_k[q].end(),
+                     [&](const BatchItem &a, const BatchItem &c) {
+                       return item_class(a) < item_class(c);
+                     });
+    b->item_off[q] = (int32_t)items.size();
+    items.insert(items.end(), items_k[q].begin(), items_k[q].end());
+  }
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  BK(cudaDeviceSynchronize());   // no launch of the previous plan is still running
+  cudaFree(b->d_items);
+  cudaFree(b->d_fix);
+  cudaFree(b->d_partials);
+  b->d_items = nullptr;
+  b->d_fix = nullptr;
+  b->d_partials = nullptr;
+  b->item_off[3] = (int32_t)items.size();
+  b->n_items = (int32_t)items.size();
+  b->n_fix = (int32_t)fix.size();
+  b->n_chunks = chunks;
+  BK(cudaMalloc(&b->d_items, sizeof(BatchItem) * std::max<size_t>(items.size(), 1)));
+  BK(cudaMalloc(&b->d_fix, sizeof(BatchFix) * std::max<size_t>(fix.size(), 1)));
+  BK(cudaMalloc(&b->d_partials, sizeof(double) * 16 * (size_t)std::max(chunks, 1)));
+  if (!items.empty())
+    BK(cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, s));
+  if (!fix.empty())
+    BK(cudaMemcpyAsync(b->d_fix, fix.data(), sizeof(BatchFix) * fix.size(), cudaMemcpyHostToDevice, s));
+  BK(cudaStreamSynchronize(s));
+  int sms = 0;
+  BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+  for (int q = 0; q < 3; ++q) {
+    const int64_t warps = b->item_off[q + 1] - b->item_off[q];
+    const int64_t ctas = (warps + 7) / 8;     // 8 warps per CTA
+    b->grid[q] = (int)std::min<int64_t>((int64_t)sms * batch_blocks_per_sm_k(kKs[q]), ctas);
+  }
+  b->item_nnz = item_nnz;
+  b->chunk_nnz = chunk_nnz;
+}
+
+static spmv_status batch_status(cudaError_t e) {
+  return e == cudaErrorMemoryAllocation ? SPMV_ERR_OOM
+         : e == cudaErrorInvalidValue  ? SPMV_ERR_ARG
+                                       : SPMV_ERR_CUDA;
+}
+
 extern "C" {
 
 spmv_status spmv_batch_create(spmv_batch_t *out, const spmv_handle_t *handles, int32_t count,
@@ -87,10 +186,8 @@ spmv_status spmv_batch_create(spmv_batch_t *out, const spmv_handle_t *handles, i
   try {
     BK(cudaGetDevice(&b->device));
     b->count = count;
-    std::vector<BatchMat> mats((size_t)count);
-    std::vector<BatchItem> items_k[3];
-    std::vector<BatchFix> fix;
-    int32_t chunks = 0;
+    b->mats.resize((size_t)count);
+    b->rowptr.resize((size_t)count);
     for (int32_t m = 0; m < count; ++m) {
       if (!handles[m] || k[m] < 1 || (k[m] != 1 && k[m] != 4 && k[m] != 16)) throw Fail{cudaErrorInvalidValue};
       const int32_t *rp = nullptr, *ci = nullptr;
@@ -106,95 +203,93 @@ spmv_status spmv_batch_create(spmv_batch_t *out, const spmv_handle_t *handles, i
         batch_free(b);
         return SPMV_ERR_UNSUPPORTED_DTYPE;
       }
-      std::vector<int32_t> hrp((size_t)n_rows + 1);
+      std::vector<int32_t> &hrp = b->rowptr[(size_t)m];
+      hrp.resize((size_t)n_rows + 1);
       BK(cudaMemcpyAsync(hrp.data(), rp, 4 * ((size_t)n_rows + 1), cudaMemcpyDeviceToHost, s));
       BK(cudaStreamSynchronize(s));
       const double avg = n_rows ? (double)hrp[(size_t)n_rows] / (double)n_rows : 0.0;
-      mats[(size_t)m] = BatchMat{rp, ci, static_cast<const float *>(v),
-                                 static_cast<const float *>(X[m]), static_cast<float *>(Y[m]),
-                                 k[m], vs > 0 ? vs : heuristic_vs(avg)};
+      b->mats[(size_t)m] = BatchMat{rp, ci, static_cast<const float *>(v),
+                                    static_cast<const float *>(X[m]), static_cast<float *>(Y[m]),
+                                    k[m], vs > 0 ? vs : heuristic_vs(avg)};
       b->handles.push_back(handles[m]);
       b->X.push_back(X[m]);
       b->Y.push_back(Y[m]);
       b->k.push_back(k[m]);
-      // row blocks of about kItemNnz nonzeros; long rows split into chunks
-      std::vector<BatchItem> &items = items_k[k_slot(k[m])];
-      int32_t r = 0;
-      while (r < (int32_t)n_rows) {
-        const int32_t len = hrp[(size_t)r + 1] - hrp[(size_t)r];
-        if (len > kItemNnz) {
-          const int32_t first = chunks;
-          int32_t cnt = 0;
-          for (int32_t z = hrp[(size_t)r]; z < hrp[(size_t)r + 1]; z += kChunkNnz) {
-            const int32_t ze = std::min(z + kChunkNnz, hrp[(size_t)r + 1]);
-            items.push_back(BatchItem{m, r, r + 1, z, ze, chunks++});
-            ++cnt;
-          }
-          fix.push_back(BatchFix{m, r, first, cnt});
-          ++r;
-          continue;
-        }
-        int32_t e = r;
-        int64_t acc = 0;
-        while (e < (int32_t)n_rows && e - r < kItemRowsMax) {
-          const int32_t l = hrp[(size_t)e + 1] - hrp[(size_t)e];
-          if (l > kItemNnz || (acc + l > kItemNnz && e > r)) break;
-          acc += l;
-          ++e;
-        }
-        items.push_back(BatchItem{m, r, e, 0, (int32_t)acc, -1});   // nz_end: the block's nnz
-        r = e;
-      }
     }
-    // Longest items first (chunks of split rows, then full row blocks, then the short
-    // remainders), so that the last items the warps take are the cheapest; the sort is
-    // stable, so items of one matrix stay together within a class (x rows stay L2-hot).
-    auto item_class = [&](const BatchItem &it) -> int {
-      if (it.chunk >= 0) return 0;
-      return it.nz_end >= kItemNnz / 2 ? 1 : 2;
-    };
-    std::vector<BatchItem> items;
-    for (int q = 0; q < 3; ++q) {
-      std::stable_sort(items_k[q].begin(), items_k[q].end(),
-                       [&](const BatchItem &a, const BatchItem &c) {
-                         return item_class(a) < item_class(c);
-                       });
-      b->item_off[q] = (int32_t)items.size();
-      items.insert(items.end(), items_k[q].begin(), items_k[q].end());
-    }
-    b->item_off[3] = (int32_t)items.size();
-    b->n_items = (int32_t)items.size();
-    b->n_fix = (int32_t)fix.size();
-    b->n_chunks = chunks;
-    BK(cudaMalloc(&b->d_mats, sizeof(BatchMat) * mats.size()));
-    BK(cudaMalloc(&b->d_items, sizeof(BatchItem) * std::max<size_t>(items.size(), 1)));
-    BK(cudaMalloc(&b->d_fix, sizeof(BatchFix) * std::max<size_t>(fix.size(), 1)));
-    BK(cudaMalloc(&b->d_partials, sizeof(double) * 16 * (size_t)std::max(chunks, 1)));
+    BK(cudaMalloc(&b->d_mats, sizeof(BatchMat) * b->mats.size()));
     BK(cudaMalloc(&b->d_counter, 3 * sizeof(int32_t)));
-    BK(cudaMemcpyAsync(b->d_mats, mats.data(), sizeof(BatchMat) * mats.size(), cudaMemcpyHostToDevice, s));
-    if (!items.empty())
-      BK(cudaMemcpyAsync(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, s));
-    if (!fix.empty())
-      BK(cudaMemcpyAsync(b->d_fix, fix.data(), sizeof(BatchFix) * fix.size(), cudaMemcpyHostToDevice, s));
-    BK(cudaStreamSynchronize(s));
-    int sms = 0;
-    BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
-    for (int q = 0; q < 3; ++q) {
-      const int64_t warps = b->item_off[q + 1] - b->item_off[q];
-      const int64_t ctas = (warps + 7) / 8;     // 8 warps per CTA
-      b->grid[q] = (int)std::min<int64_t>((int64_t)sms * batch_blocks_per_sm_k(kKs[q]), ctas);
-    }
+    BK(cudaMemcpyAsync(b->d_mats, b->mats.data(), sizeof(BatchMat) * b->mats.size(),
+                       cudaMemcpyHostToDevice, s));
+    batch_plan(b, kItemNnz, kChunkNnz, s);
     BK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
     for (auto &st : b->side) BK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     for (auto &e : b->ev) BK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   } catch (const Fail &f) {
     cudaGetLastError();
     batch_free(b);
-    return f.e == cudaErrorMemoryAllocation ? SPMV_ERR_OOM
-           : f.e == cudaErrorInvalidValue  ? SPMV_ERR_ARG
-                                           : SPMV_ERR_CUDA;
+    return batch_status(f.e);
   }
   *out = b;
+  return SPMV_OK;
+}
+
+spmv_status spmv_batch_set_plan(spmv_batch_t b, int32_t item_nnz, int32_t chunk_nnz,
+                                spmv_stream_t stream) {
+  if (!b || item_nnz < 32 || item_nnz > 65536 || chunk_nnz < item_nnz || chunk_nnz > (1 << 20))
+    return SPMV_ERR_ARG;
+  try {
+    batch_plan(b, item_nnz, chunk_nnz, static_cast<cudaStream_t>(stream));
+  } catch (const Fail &f) {
+    cudaGetLastError();
+    return batch_status(f.e);
+  }
+  return SPMV_OK;
+}
+
+spmv_status spmv_batch_tune(spmv_batch_t b, int32_t reps, int32_t *item_nnz,
+                            int32_t *chunk_nnz, spmv_stream_t stream) {
+  if (!b || reps < 1) return SPMV_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  try {
+    BK(cudaEventCreate(&e0));
+    BK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int32_t bi = b->item_nnz, bc = b->chunk_nnz;
+    for (int32_t item : {256, 512, 1024, 2048}) {
+      for (int32_t mult : {2, 4}) {
+        batch_plan(b, item, item * mult, s);
+        for (int w = 0; w < 2; ++w) {
+          const spmv_status q = spmv_run_batched(b, stream);
+          if (q != SPMV_OK) throw Fail{cudaErrorLaunchFailure};
+        }
+        BK(cudaEventRecord(e0, s));
+        for (int r = 0; r < reps; ++r) {
+          const spmv_status q = spmv_run_batched(b, stream);
+          if (q != SPMV_OK) throw Fail{cudaErrorLaunchFailure};
+        }
+        BK(cudaEventRecord(e1, s));
+        BK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          bi = item;
+          bc = item * mult;
+        }
+      }
+    }
+    batch_plan(b, bi, bc, s);
+  } catch (const Fail &f) {
+    cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return batch_status(f.e);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (item_nnz) *item_nnz = b->item_nnz;
+  if (chunk_nnz) *chunk_nnz = b->chunk_nnz;
   return SPMV_OK;
 }
 

@@ -269,14 +269,29 @@ def test_batched_persistent_matches_oracle(api, torch):
         X64.append(X)
     assert max(np.diff(m.rowptr).max() for m in mats) > 4096
     b = api.Batch(As, Xs, Ys, ks)
-    for rep in range(2):
+    from paper_1711_05487_gb300._abi import SpmvError
+    with pytest.raises(SpmvError):
+        b.set_plan(16, 64)                        # item below the 32-nonzero minimum
+    with pytest.raises(SpmvError):
+        b.set_plan(1024, 512)                     # chunks shorter than items
+    # the default plan, two explicit plans (small items with short chunks; large items with
+    # long chunks) and the autotuner's pick all give the oracle's products
+    plans = [None, (256, 512), (2048, 8192), "tune"]
+    for rep, plan in enumerate(plans):
+        if plan == "tune":
+            item, chunk = b.tune(reps=2)
+            assert item in (256, 512, 1024, 2048) and chunk in (2 * item, 4 * item)
+        elif plan is not None:
+            b.set_plan(*plan)
+        for Y in Ys:
+            Y.fill_(np.nan)
         b.run()
         torch.cuda.synchronize()
         for m, X, Y in zip(mats, X64, Ys):
             Yr, Sr = oracle.spmm(m.rowptr, m.colind, m.val, X)
             tau = TAU["f32"] if np.diff(m.rowptr).max() <= 27 else 2e-5
             check_rows(Y.cpu().numpy().astype(np.float64).ravel(), Yr.ravel(), Sr.ravel(), tau,
-                       f"batched {m.name} rep {rep}")
+                       f"batched {m.name} plan {plan}")
     for Y in Ys:
         Y.fill_(np.nan)
     b.run_sequential()
