@@ -391,6 +391,24 @@ void run_profile(spmv_matrix *h, int reps, spmv_profile_report &o, cudaStream_t 
   }
 }
 
+// Device bytes of a second copy of the matrix: panel-major (n_panels row-pointer sets) or
+// sliced rows (`positions` slots).
+size_t panel_bytes(const spmv_matrix *h, int n_panels) {
+  const size_t vb = h->storage == SPMV_DF64 ? 8 : dtype_bytes(h->storage);
+  return (4 + vb) * (size_t)h->nnz + 4 * (size_t)n_panels * (size_t)(h->n_rows + 1);
+}
+
+// An optional copy is tried only when the device has room for it and a quarter to spare.
+bool optional_fits(size_t bytes, cudaStream_t s) {
+  size_t free_b = 0, total_b = 0;
+  CK(cudaStreamSynchronize(s));
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return bytes + bytes / 4 < free_b;
+}
+
 // Column panels compete when the matrix is ML (v.xpath = 1) and x is larger than half the
 // L2: panel counts that cut x into slices of a half and a third of the L2, each with
 // sub-warps of 1 lane up to the width that covers a row's average share of one panel (at
@@ -404,6 +422,8 @@ void sweep_panels(spmv_matrix *h, spmv_variant &v, float best, const void *x, vo
   spmv_variant best_v = v;
   bool found = false;
   int last_p = 0;
+  // the panel copy doubles the matrix in device memory: without room for it, panels sit out
+  if (!optional_fits(panel_bytes(h, 2), s)) return;
   for (int f = 2; f <= 3; ++f) {
     const int p = std::min(kMaxPanels,
                            std::max(2, (int)std::ceil(xb * f / (double)d.l2_bytes)));
@@ -510,8 +530,10 @@ void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, cudaStream_t s) {
   // Sliced rows (thread per row without a shared-memory stage) compete with the best row
   // variant when rows are short and the slices pad the matrix by at most an eighth; their
   // times vary more from run to run, so they replace the incumbent only when 5 % faster.
-  if (h->nnz_avg() <= 64.0 && v.xpath < 2 &&
-      sell_positions(h, s) <= h->nnz + h->nnz / 8 + 32 * ((h->n_rows + 31) / 32)) {
+  const int64_t sell_pos = h->nnz_avg() <= 64.0 && v.xpath < 2 ? sell_positions(h, s) : -1;
+  const size_t sell_vb = h->storage == SPMV_DF64 ? 8 : dtype_bytes(h->storage);
+  if (sell_pos >= 0 && sell_pos <= h->nnz + h->nnz / 8 + 32 * ((h->n_rows + 31) / 32) &&
+      optional_fits((sell_vb + 4) * (size_t)sell_pos, s)) {
     spmv_variant t = v;
     t.partition = 3;
     t.vs = 1;
