@@ -714,7 +714,7 @@ def main():
         return
     out, m = run_ours(args, rank, world)
     if rank == 0:
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:      # the oracle baseline: N = 1 only
             wl = WORKLOADS[args.workload]
             out["cpu_baseline"] = cpu_baseline(m, synth.uniform_vector(m.n_cols, wl["x_seed"]))
         print(json.dumps(out), flush=True)
