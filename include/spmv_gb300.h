@@ -149,7 +149,7 @@ spmv_status spmv_create(spmv_handle_t *out, int64_t n_rows, int64_t n_cols, int6
 /* Frees every device buffer of the handle (synchronizes the device first). */
 spmv_status spmv_destroy(spmv_handle_t h);
 
-/* Value storage precision (build addition): storage in F64 / F32 / BF16, x and y in
+/* Value storage precision (not in the paper): storage in F64 / F32 / BF16, x and y in
  * vec_type (F64 or F32), products accumulated in acc_type (F64, F32 or DF64). Conversion is
  * round-to-nearest-even straight from the input values. Offered: storage F64 with
  * vec = acc = F64; storage F32 or BF16 with (vec, acc) in {(F64,F64),(F32,F32),(F32,F64),

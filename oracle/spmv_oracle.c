@@ -691,7 +691,7 @@ uint32_t oracle_classify(const double *p /* csr, mb, ml, imb, cmp, peak */, doub
   return cls;
 }
 
-/* Second profiling pass, this build's GB300 reading of Section III-C: a compute-bound
+/* Second profiling pass, a GB300 reading of Section III-C: a compute-bound
  * baseline (CMP) hides the memory bottlenecks, so after the CMP optimization the profile is
  * repeated with the optimized kernel as the baseline, p2 = (P_CSR', P_ML'): ML joins the
  * class set when P_ML' / P_CSR' > t_ml and MB when P_CSR' / P_MB >= t_mb. Without p2, or
@@ -893,7 +893,7 @@ void oracle_log2p1_f32_array(const float *in, float *out, int64_t n) {
 
 /* ---------------------------------------------------------------------------------- */
 /* Feature route (Section III-D). The paper trains a decision tree on Table I features;
- * this build reads the route as fixed rules over the same features:
+ * the route is read here as fixed rules over the same features:
  *   IMB  highly uneven rows, nnz_max > long_ratio * nnz_avg (the IMB sub-class test of
  *        Section III-E);
  *   ML   most elements open a new cache line (misses_avg >= nnz_avg / 2) and x does not

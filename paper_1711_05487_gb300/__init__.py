@@ -16,7 +16,7 @@ __all__ = ["build", "SpmvError", "spmv_variant", "SPMV_F64", "SPMV_F32", "SPMV_B
 def __getattr__(name):
     # the torch-based layer is imported lazily so that the ABI can be inspected without torch
     if name in ("SpmvMatrix", "Selector", "Batch", "variant", "class_names", "TuneResult",
-                "BASELINE"):
+                "CSR_VECTOR"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

@@ -45,7 +45,7 @@ def variant(partition=0, index=0, xpath=0, vec=0, vs=0, tile_rows=0, tile_pipe=0
     return spmv_variant(partition, index, xpath, vec, vs, tile_rows, tile_pipe)
 
 
-BASELINE = dict(partition=0, index=0, xpath=0, vec=0, vs=0, tile_rows=0, tile_pipe=0)
+CSR_VECTOR = dict(partition=0, index=0, xpath=0, vec=0, vs=0, tile_rows=0, tile_pipe=0)
 
 
 def _as_torch(a, dtype=None) -> torch.Tensor:
@@ -150,7 +150,7 @@ class SpmvMatrix:
         return self.report
 
     def set_variant(self, stream=None, **knobs):
-        v = variant(**{**BASELINE, **knobs})
+        v = variant(**{**CSR_VECTOR, **knobs})
         _abi.spmv_set_variant(self._h, v, _stream(stream))
 
     # ----------------------------------------------------------------------- running

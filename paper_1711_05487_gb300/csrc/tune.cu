@@ -454,7 +454,7 @@ void sweep_panels(spmv_matrix *h, spmv_variant &v, float best, const void *x, vo
   }
 }
 
-// Sub-warp width sweep by timing (Section III-E "parameter tuning"; build addition). When
+// Sub-warp width sweep by timing (Section III-E "parameter tuning"; not in the paper). When
 // the thread-per-row kernel (width 1) wins, its geometry is swept too: 128 / 64 / 32 rows
 // per tile, one tile per CTA or persistent CTAs with two tiles in flight.
 // Called by spmv_tune for the routes that choose a variant (never for SPMV_TUNE_FIXED), so
