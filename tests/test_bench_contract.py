@@ -26,3 +26,39 @@ def test_reference_arm_json_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_algorithmic_bytes_closed_forms():
+    """The roofline's algorithmic bytes: P_MB's compulsory traffic per variant."""
+    b = _bench_module()
+    n, c, z = 1000, 1200, 7000
+    # plain CSR, FP64 values and vectors: 4(N+1) + (4 + 8) NNZ + 8 (N + N_cols)
+    assert b.alg_bytes(n, c, z, (0, 0, 0, 0, 0, 0, 0), 0, 0) == 4 * (n + 1) + 12 * z + 8 * (n + c)
+    # 16-bit deltas: 2 bytes per column index plus a 4-byte base per row
+    assert (b.alg_bytes(n, c, z, (0, 1, 0, 1, 1, 32, 0), 0, 0)
+            == 4 * (n + 1) + 10 * z + 4 * n + 8 * (n + c))
+    # FP32 storage and vectors
+    assert b.alg_bytes(n, c, z, (0, 0, 0, 0, 0, 0, 0), 1, 1) == 4 * (n + 1) + 8 * z + 4 * (n + c)
+    # column panels: P row-pointer sets, y passed over 2P - 1 times
+    p = 3
+    assert (b.alg_bytes(n, c, z, (0, 0, p, 0, 2, 0, 0), 0, 0)
+            == 4 * p * (n + 1) + 12 * z + 8 * c + 8 * n * (2 * p - 1))
+    # double-float storage moves 8 bytes per value
+    assert b.alg_bytes(n, c, z, (0, 0, 0, 0, 0, 0, 0), 3, 0) == b.alg_bytes(
+        n, c, z, (0, 0, 0, 0, 0, 0, 0), 0, 0)
+
+
+def test_whole_job_rate_and_dtype_sizes():
+    b = _bench_module()
+    assert b.dtype_bytes(0) == 8 and b.dtype_bytes(1) == 4 and b.dtype_bytes(2) == 2
+    assert b.dtype_bytes(3) == 8
+    # N replicas of the same work in the max-over-ranks time
+    assert b.whole_job_rate(2e9, 1.0, 4) == 4 * 2e9 / 1e-3 / 1e9
