@@ -100,6 +100,45 @@ def test_bandwidth_probe_is_plausible(abi):
     assert 1000 < hbm < 20000 and l2 > hbm
 
 
+def test_profile_report_and_cta_times(api, torch):
+    """spmv_profile: P_MB and P_peak equal the oracle's bounds at the reported B_max (the
+    L2 rate for a cache-fitting working set, else HBM: the footnote's reading), the timed
+    rates are 2 NNZ / t of their own timings, P_IMB follows t_imb, and every static-partition
+    CTA of the CTA-time probe reports a plausible SM and a non-negative time."""
+    m = synth.stencil_27pt(40)
+    A = api.SpmvMatrix.from_csr(m)
+    r = A.profile(reps=5)
+    p = r["p"]
+    ws = oracle.bounds(m.n_rows, m.n_cols, m.nnz, 4, 8, 8, 1.0)[2]
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    assert r["b_max_gbs"] == oracle.select_bmax(int(ws), l2, r["b_hbm_gbs"], r["b_l2_gbs"])
+    p_mb, p_peak, _ = oracle.bounds(m.n_rows, m.n_cols, m.nnz, 4, 8, 8, r["b_max_gbs"])
+    assert p["P_MB"] == pytest.approx(p_mb, rel=1e-12)
+    assert p["P_peak"] == pytest.approx(p_peak, rel=1e-12)
+    flops = 2.0 * m.nnz
+    for key, t in (("P_CSR", "t_csr_ms"), ("P_ML", "t_ml_ms"), ("P_CMP", "t_cmp_ms"),
+                   ("P_IMB", "t_imb_ms")):
+        assert r[t] > 0 and p[key] == pytest.approx(flops / (r[t] * 1e-3) / 1e9, rel=1e-9)
+    assert r["t_median_ms"] <= r["t_span_ms"] + 1e-9 and r["n_ctas"] > 0
+    el, sm = A.profile_cta_times()
+    assert el.shape == (r["n_ctas"],) and sm.shape == (r["n_ctas"],)
+    assert np.all(el >= 0) and np.all((sm >= 0) & (sm < 1024)) and el.max() > 0
+
+
+def test_device_bytes_follow_the_pool_data(api, torch):
+    """The handle's device footprint: the CSR arrays at creation, more once a variant builds
+    its data (delta index, sliced-row copy)."""
+    m = synth.stencil_27pt(30)
+    A = api.SpmvMatrix.from_csr(m)
+    b0 = A.device_bytes()
+    assert b0 >= 4 * (m.n_rows + 1) + 12 * m.nnz
+    A.set_variant(index=1, vec=1)
+    b1 = A.device_bytes()
+    assert b1 >= b0 + 2 * m.nnz + 4 * m.n_rows
+    A.set_variant(partition=3, index=1)
+    assert A.device_bytes() >= b1 + 10 * m.nnz
+
+
 # ------------------------------------------------------------------------ MLP --------
 SIZES = np.array([12, 32, 32, 4], dtype=np.int32)
 
