@@ -124,6 +124,7 @@ spmv_status spmv_destroy(spmv_handle_t h) {
       if (e) cudaEventDestroy(e);
     if (h->pass_done) cudaEventDestroy(h->pass_done);
     cudaStreamDestroy(h->copy_stream);
+    cudaStreamDestroy(h->copy_stream2);
     cudaStreamDestroy(h->upload_stream);
     cudaStreamDestroy(h->capture_stream);
     for (auto st : h->chunk_stream)

@@ -177,11 +177,12 @@ struct spmv_matrix {
   int32_t tile_pipe = 0;       // 1: persistent CTAs with two tiles in flight
   DevBuf d_err;                // device error word of bounded waits
   DevBuf small;                // 256 bytes for single-value reductions (maxima, codes)
-  cudaStream_t copy_stream = nullptr;   // host-buffer runs: device-to-host copies of y
+  cudaStream_t copy_stream = nullptr;   // host-buffer runs: device-to-host copies of y (even
+  cudaStream_t copy_stream2 = nullptr;  // and odd chunks: two copies in flight)
   cudaStream_t upload_stream = nullptr; // host-buffer runs: host-to-device copies of x
   cudaStream_t capture_stream = nullptr;  // host-buffer runs: graph capture
   cudaStream_t chunk_stream[2] = {};    // host-buffer runs: alternate chunks' kernels
-  cudaEvent_t joined[5] = {};           // host-buffer runs: fork from / rejoin the origin
+  cudaEvent_t joined[6] = {};           // host-buffer runs: fork from / rejoin the origin
   cudaEvent_t pass_done = nullptr;      // host-buffer runs: column panels' passes before the last
   cudaGraph_t host_graph = nullptr;     // host-buffer pipeline for (host_x, host_y, epoch)
   cudaGraphExec_t host_exec = nullptr;

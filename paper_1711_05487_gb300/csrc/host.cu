@@ -48,6 +48,7 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
     if (!h->y_stage.p) h->y_stage.alloc(vb * (size_t)std::max<int64_t>(h->n_rows, 1), vb, s);
     if (!h->copy_stream) {
       CK(cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+      CK(cudaStreamCreateWithFlags(&h->copy_stream2, cudaStreamNonBlocking));
       CK(cudaStreamCreateWithFlags(&h->upload_stream, cudaStreamNonBlocking));
       CK(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
       for (auto &st : h->chunk_stream) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -97,11 +98,29 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
     // overlaps the next chunk's first; all side streams join back into `origin` at the end.
     // Merge-path tiles span the whole matrix: one upload, one launch, one download.
     const KernelSet *ks = set_for(h);
+    cudaStream_t side[5] = {h->upload_stream, h->copy_stream, h->copy_stream2,
+                            h->chunk_stream[0], h->chunk_stream[1]};
+    auto fork = [&](cudaStream_t origin) {
+      CK(cudaEventRecord(h->joined[5], origin));
+      for (cudaStream_t st : side) CK(cudaStreamWaitEvent(st, h->joined[5], 0));
+    };
+    auto join = [&](cudaStream_t origin) {
+      for (int k = 0; k < 5; ++k) {
+        CK(cudaEventRecord(h->joined[k], side[k]));
+        CK(cudaStreamWaitEvent(origin, h->joined[k], 0));
+      }
+    };
+    // downloads of consecutive chunks alternate between two streams (two copies in flight)
+    auto download = [&](int c, int64_t r0, int64_t r1, cudaStream_t after) {
+      cudaStream_t cp = (c & 1) ? h->copy_stream2 : h->copy_stream;
+      CK(cudaEventRecord(h->chunk_done[c], after));
+      CK(cudaStreamWaitEvent(cp, h->chunk_done[c], 0));
+      CK(cudaMemcpyAsync(static_cast<char *>(y_host) + vb * (size_t)r0,
+                         static_cast<char *>(h->y_stage.p) + vb * (size_t)r0,
+                         vb * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, cp));
+    };
     auto enqueue = [&](cudaStream_t origin) {
-      cudaStream_t side[4] = {h->upload_stream, h->copy_stream, h->chunk_stream[0],
-                              h->chunk_stream[1]};
-      CK(cudaEventRecord(h->joined[4], origin));
-      for (cudaStream_t st : side) CK(cudaStreamWaitEvent(st, h->joined[4], 0));
+      fork(origin);
       int64_t uploaded = 0;
       for (int c = 0; c < nch; ++c) {
         const int64_t need = chunked ? h->x_need[c] : h->n_cols;
@@ -127,26 +146,16 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
           if (a.sell_off) a.sell_off += r0 / 32;   // chunks start on 128-row boundaries
           CK(ks->spmv(h->variant, a, cs));
         }
-        CK(cudaEventRecord(h->chunk_done[c], cs));
-        CK(cudaStreamWaitEvent(h->copy_stream, h->chunk_done[c], 0));
-        CK(cudaMemcpyAsync(static_cast<char *>(y_host) + vb * (size_t)r0,
-                           static_cast<char *>(h->y_stage.p) + vb * (size_t)r0,
-                           vb * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, h->copy_stream));
+        download(c, r0, r1, cs);
       }
-      for (int k = 0; k < 4; ++k) {
-        CK(cudaEventRecord(h->joined[k], side[k]));
-        CK(cudaStreamWaitEvent(origin, h->joined[k], 0));
-      }
+      join(origin);
     };
     // Column panels: pass p reads only slice p of x, so x goes up in slice order on the
     // upload stream and pass p waits for its slice (the next slices upload during the
     // passes before); the last pass runs in row chunks on the two alternating streams, each
     // finished chunk of y downloaded while the next computes.
     auto enqueue_panels = [&](cudaStream_t origin) {
-      cudaStream_t side[4] = {h->upload_stream, h->copy_stream, h->chunk_stream[0],
-                              h->chunk_stream[1]};
-      CK(cudaEventRecord(h->joined[4], origin));
-      for (cudaStream_t st : side) CK(cudaStreamWaitEvent(st, h->joined[4], 0));
+      fork(origin);
       const int64_t w = h->pnl_width;
       for (int p = 0; p < n_pass; ++p) {
         const int64_t c0 = std::min<int64_t>(h->n_cols, (int64_t)p * w);
@@ -178,16 +187,9 @@ spmv_status spmv_run_host(spmv_handle_t h, const void *x_host, void *y_host,
         a.pnl_first = n_pass - 1;
         a.n_panels = 1;
         CK(ks->spmv(h->variant, a, cs));
-        CK(cudaEventRecord(h->chunk_done[c], cs));
-        CK(cudaStreamWaitEvent(h->copy_stream, h->chunk_done[c], 0));
-        CK(cudaMemcpyAsync(static_cast<char *>(y_host) + vb * (size_t)r0,
-                           static_cast<char *>(h->y_stage.p) + vb * (size_t)r0,
-                           vb * (size_t)(r1 - r0), cudaMemcpyDeviceToHost, h->copy_stream));
+        download(c, r0, r1, cs);
       }
-      for (int k = 0; k < 4; ++k) {
-        CK(cudaEventRecord(h->joined[k], side[k]));
-        CK(cudaStreamWaitEvent(origin, h->joined[k], 0));
-      }
+      join(origin);
     };
     auto run = [&](cudaStream_t origin) {
       if (panels) enqueue_panels(origin);
