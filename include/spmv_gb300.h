@@ -167,7 +167,8 @@ spmv_status spmv_destroy(spmv_handle_t h);
  * every other variant runs the FP64 kernels on the FP64 values. Width-1 variants run one
  * tile per CTA (tile_pipe is set to 0). The handle keeps the pairs (8 bytes per nonzero)
  * beside the FP64 values.
- * Invalidates the tuned variant (spmv_tune or spmv_set_variant must follow). */
+ * Invalidates the tuned variant (spmv_tune or spmv_set_variant must follow). On failure
+ * (SPMV_ERR_OOM, CUDA) the handle is back at the input dtype's defaults and untuned. */
 spmv_status spmv_set_precision(spmv_handle_t h, spmv_dtype storage, spmv_dtype vec_type,
                                spmv_dtype acc_type, spmv_stream_t stream);
 
@@ -175,11 +176,15 @@ spmv_status spmv_set_precision(spmv_handle_t h, spmv_dtype storage, spmv_dtype v
  * (Table II), build the variant's data (delta index, merge-path table) and, if
  * opts->autotune, pick the sub-warp width by timing. opts and report may be NULL
  * (defaults / no report). Synchronizes the stream (the profile route times kernels).
- * Errors: SPMV_ERR_NO_SELECTOR (learned without opts->selector), SPMV_ERR_OOM, CUDA. */
+ * Errors: SPMV_ERR_NO_SELECTOR (learned without opts->selector), SPMV_ERR_OOM, CUDA; an
+ * error met after argument checks leaves the handle untuned (runs answer
+ * SPMV_ERR_NOT_TUNED until a tune or spmv_set_variant succeeds). */
 spmv_status spmv_tune(spmv_handle_t h, spmv_mode mode, const spmv_tune_opts *opts,
                       spmv_tune_report *report, spmv_stream_t stream);
 
-/* Installs a variant directly (same preprocessing as spmv_tune, no classification). */
+/* Installs a variant directly (same preprocessing as spmv_tune, no classification).
+ * Errors: SPMV_ERR_ARG (invalid variant; the installed one stays), SPMV_ERR_OOM, CUDA
+ * (the handle is left untuned). */
 spmv_status spmv_set_variant(spmv_handle_t h, const spmv_variant *v, spmv_stream_t stream);
 
 /* Fig. 1: y = A x (y overwritten), asynchronous on stream, no host synchronization.
@@ -193,7 +198,8 @@ spmv_status spmv_run(spmv_handle_t h, const void *x, void *y, spmv_stream_t stre
  * together reach 8 MB compute in eight row chunks: chunk c waits only for the prefix of x
  * up to the largest column of chunks 0..c (uploaded piece by piece on a handle-owned
  * stream), consecutive chunks' kernels run on two alternating handle-owned streams, and
- * each finished chunk of y is downloaded on another while the next computes. Column
+ * each finished chunk of y is downloaded while the next computes (consecutive chunks'
+ * downloads alternate between two more streams). Column
  * panels (up to 8) upload x slice by slice, each pass waiting only for its slice, and run
  * their last pass in the eight row chunks. With page-locked x and y the whole pipeline is captured
  * once into a CUDA graph (kept per handle for the last pair of host pointers until the
@@ -495,7 +501,9 @@ spmv_status spmv_selector_predict(spmv_selector_t s, const double *feat16, uint3
 /* A batch of `count` tuned handles with FP32 storage, FP32 x/y and FP32 accumulation;
  * X[i] (n_cols_i x k[i]) and Y[i] (n_rows_i x k[i]) are row-major device arrays, k[i] in
  * {1, 4, 16}. The batch plans row-block work items (long rows split, partials summed in
- * FP64) and owns a CUDA graph of its launches. */
+ * FP64) and owns a CUDA graph of its launches. It reads the handles' device arrays in
+ * place: the handles must outlive the batch, and a batched run answers SPMV_ERR_ARG once a
+ * handle's precision has changed since the batch was created. */
 spmv_status spmv_batch_create(spmv_batch_t *out, const spmv_handle_t *handles, int32_t count,
                               const void *const *X, void *const *Y, const int32_t *k,
                               spmv_stream_t stream);

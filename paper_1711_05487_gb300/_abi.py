@@ -29,6 +29,8 @@ STATUS = {0: "SPMV_OK", 1: "SPMV_ERR_INVALID_CSR", 2: "SPMV_ERR_UNSUPPORTED_DTYP
           3: "SPMV_ERR_OOM", 4: "SPMV_ERR_NOT_TUNED", 5: "SPMV_ERR_CUDA",
           6: "SPMV_ERR_TIMEOUT", 7: "SPMV_ERR_ARG", 8: "SPMV_ERR_NO_SELECTOR",
           9: "SPMV_ERR_TOO_LARGE"}
+(SPMV_OK, SPMV_ERR_INVALID_CSR, SPMV_ERR_UNSUPPORTED_DTYPE, SPMV_ERR_OOM, SPMV_ERR_NOT_TUNED,
+ SPMV_ERR_CUDA, SPMV_ERR_TIMEOUT, SPMV_ERR_ARG, SPMV_ERR_NO_SELECTOR, SPMV_ERR_TOO_LARGE) = range(10)
 
 
 class SpmvError(RuntimeError):

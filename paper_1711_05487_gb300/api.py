@@ -129,7 +129,15 @@ class SpmvMatrix:
     # ----------------------------------------------------------------- configuration
     def set_precision(self, storage="f64", vec="f64", acc="f64", stream=None):
         s, v, a = DTYPE_CODE[storage], DTYPE_CODE[vec], DTYPE_CODE[acc]
-        _abi.spmv_set_precision(self._h, s, v, a, _stream(stream))
+        try:
+            _abi.spmv_set_precision(self._h, s, v, a, _stream(stream))
+        except _abi.SpmvError as e:
+            if e.status not in (_abi.SPMV_ERR_ARG, _abi.SPMV_ERR_UNSUPPORTED_DTYPE):
+                # a failure while converting leaves the handle at the input dtype's defaults
+                self.storage = self.in_type
+                self.vec = SPMV_F64 if self.in_type == SPMV_F64 else SPMV_F32
+                self.acc = self.vec
+            raise
         self.storage, self.vec, self.acc = s, v, a
 
     @property

@@ -130,13 +130,7 @@ spmv_status spmv_destroy(spmv_handle_t h) {
     for (auto st : h->chunk_stream)
       if (st) cudaStreamDestroy(st);
   }
-  for (DevBuf *b : {&h->rowptr, &h->colind, &h->val_in, &h->val_store, &h->dbase, &h->delta,
-                    &h->esc, &h->coord, &h->tail_row, &h->tail_val, &h->head_val, &h->x_stage,
-                    &h->y_stage, &h->scratch, &h->d_err, &h->small, &h->feat_part,
-                    &h->feat_fin, &h->val_df, &h->cg_ws, &h->bin_rows, &h->bin_long_rows,
-                    &h->bin_long_first, &h->bin_chunks, &h->bin_partials})
-    b->release();
-  delete h;
+  delete h;   // every device buffer of the handle is a DevBuf and frees itself
   return SPMV_OK;
 }
 
@@ -151,9 +145,22 @@ spmv_status spmv_set_precision(spmv_handle_t h, spmv_dtype storage, spmv_dtype v
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return guarded([&]() -> spmv_status {
     if (storage != h->storage) {
+      // no run until a variant is installed for the new storage
+      h->tuned = false;
+      ++h->epoch;
       h->storage = storage;
-      install_storage(h, s);
-      CK(cudaStreamSynchronize(s));
+      try {
+        install_storage(h, s);
+        CK(cudaStreamSynchronize(s));
+      } catch (...) {
+        // back to the input dtype's defaults, whose values are always resident
+        h->val_store.release();
+        h->val_df.release();
+        h->x_stage.release();
+        h->y_stage.release();
+        default_types(h->in_type, &h->storage, &h->vec, &h->acc);
+        throw;
+      }
     }
     if (vec_type != h->vec) {
       h->x_stage.release();
@@ -171,6 +178,10 @@ spmv_status spmv_set_variant(spmv_handle_t h, const spmv_variant *v, spmv_stream
   if (!h || !v || !valid_variant(*v)) return SPMV_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   return guarded([&]() -> spmv_status {
+    // untuned while the variant's buffers are rebuilt: a failure part way leaves no
+    // installed variant pointing at released buffers
+    h->tuned = false;
+    ++h->epoch;
     spmv_variant w = *v;
     prepare_variant(h, w, s);
     h->variant = w;

@@ -167,6 +167,23 @@ static void batch_plan(spmv_batch *b, int32_t item_nnz, int32_t chunk_nnz, cudaS
   b->chunk_nnz = chunk_nnz;
 }
 
+// The batch reads its handles' device arrays through the pointers taken at creation: a
+// handle whose precision changed since (its value array reallocated) no longer matches.
+static bool batch_current(const spmv_batch *b) {
+  for (int32_t m = 0; m < b->count; ++m) {
+    const int32_t *rp = nullptr, *ci = nullptr;
+    const void *v = nullptr;
+    int64_t n_rows = 0;
+    int32_t st = 0, ve = 0, ac = 0, vs = 0;
+    const BatchMat &bm = b->mats[(size_t)m];
+    if (handle_info(b->handles[(size_t)m], &rp, &ci, &v, &n_rows, &st, &ve, &ac, &vs) != SPMV_OK ||
+        rp != bm.rowptr || ci != bm.colind || v != static_cast<const void *>(bm.val) ||
+        st != SPMV_F32 || ve != SPMV_F32 || ac != SPMV_F32)
+      return false;
+  }
+  return true;
+}
+
 static spmv_status batch_status(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? SPMV_ERR_OOM
          : e == cudaErrorInvalidValue  ? SPMV_ERR_ARG
@@ -294,7 +311,7 @@ spmv_status spmv_batch_tune(spmv_batch_t b, int32_t reps, int32_t *item_nnz,
 }
 
 spmv_status spmv_run_batched(spmv_batch_t b, spmv_stream_t stream) {
-  if (!b) return SPMV_ERR_ARG;
+  if (!b || !batch_current(b)) return SPMV_ERR_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   try {
     if (!b->exec) {

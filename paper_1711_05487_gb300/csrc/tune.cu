@@ -582,6 +582,10 @@ spmv_status spmv_tune(spmv_handle_t h, spmv_mode mode, const spmv_tune_opts *opt
   spmv_tune_report rep;
   std::memset(&rep, 0, sizeof rep);
   spmv_status st = guarded([&]() -> spmv_status {
+    // untuned while probes and candidates rebuild the variant buffers: a failure part way
+    // leaves no installed variant pointing at released buffers
+    h->tuned = false;
+    ++h->epoch;
     const double t0 = now_ms();
     uint32_t cls = 0;
     spmv_variant v{};

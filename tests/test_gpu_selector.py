@@ -339,3 +339,38 @@ def test_batched_persistent_matches_oracle(api, torch):
         Yr, Sr = oracle.spmm(m.rowptr, m.colind, m.val, X)
         check_rows(Y.cpu().numpy().astype(np.float64).ravel(), Yr.ravel(), Sr.ravel(), 2e-5,
                    f"sequential {m.name}")
+
+
+def test_batch_refuses_handles_whose_precision_changed(api, torch):
+    """The batch reads its handles' arrays in place: once a handle's precision changes (its
+    value array reallocated) a batched run answers SPMV_ERR_ARG instead of reading freed
+    memory; a handle whose variant change is refused keeps the variant it had."""
+    from paper_1711_05487_gb300 import _abi
+    mats = [synth.laplacian_2d(40), synth.uniform_random(3000, 12, seed=5)]
+    As, Xs, Ys = [], [], []
+    for m in mats:
+        A = api.SpmvMatrix.from_csr(synth.Csr(m.n_rows, m.n_cols, m.rowptr, m.colind,
+                                              m.val.astype(np.float32), m.name))
+        A.set_variant()
+        As.append(A)
+        Xs.append(torch.ones((m.n_cols, 1), dtype=torch.float32, device="cuda"))
+        Ys.append(torch.zeros((m.n_rows, 1), dtype=torch.float32, device="cuda"))
+    b = api.Batch(As, Xs, Ys, [1, 1])
+    b.run()
+    torch.cuda.synchronize()
+    As[1].set_precision("bf16", "f32", "f32")
+    with pytest.raises(_abi.SpmvError) as ei:
+        b.run()
+    assert ei.value.status == _abi.SPMV_ERR_ARG
+    b.close()
+    # an invalid variant is refused before anything changes: the installed one still runs
+    A = As[0]
+    with pytest.raises(_abi.SpmvError):
+        A.set_variant(partition=9)
+    x = torch.ones(mats[0].n_cols, dtype=torch.float32, device="cuda")
+    y = torch.zeros(mats[0].n_rows, dtype=torch.float32, device="cuda")
+    A.run(x, y)
+    torch.cuda.synchronize()
+    yr, sr = oracle.spmv(mats[0].rowptr, mats[0].colind,
+                         mats[0].val.astype(np.float32).astype(np.float64), np.ones(mats[0].n_cols))
+    check_rows(y.cpu().numpy().astype(np.float64), yr, sr, TAU["f32"], "after refused variant")
