@@ -244,6 +244,18 @@ __device__ __forceinline__ __nv_bfloat16 ld_stream_1(const __nv_bfloat16 *p, uin
                : "=h"(r) : "l"(p), "l"(pol));
   return __ushort_as_bfloat16(r);
 }
+__device__ __forceinline__ uint16_t ld_stream_1(const uint16_t *p, uint64_t pol) {
+  unsigned short r;
+  asm volatile("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;"
+               : "=h"(r) : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ uint8_t ld_stream_1(const uint8_t *p, uint64_t pol) {
+  unsigned short r;
+  asm volatile("ld.global.nc.L2::cache_hint.u8 %0, [%1], %2;"
+               : "=h"(r) : "l"(p), "l"(pol));
+  return (uint8_t)r;
+}
 
 
 // One pass of the column-panel variant (ML with x larger than the L2). The matrix is held
@@ -312,6 +324,8 @@ __global__ void __launch_bounds__(kSellThreads, 10) k_sell(const RunArgs a) {
   const ValT *__restrict__ sv = static_cast<const ValT *>(a.sell_val) + p0;
   const IdxT *__restrict__ si = static_cast<const IdxT *>(a.sell_idx) + p0;
   const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
+  // the slices stream past once (evict-first) so that they do not push x out of the L2
+  const uint64_t pol_s = policy_evict_first();
   uint64_t pol_x = 0;
   if constexpr (XL2) pol_x = policy_evict_last();
   int c = 0;
@@ -324,10 +338,10 @@ __global__ void __launch_bounds__(kSellThreads, 10) k_sell(const RunArgs a) {
   auto column = [&](int k) -> int {
     if constexpr (DB != 0) {
       if (ec) return __ldg(ec + k);
-      c += (int)__ldg(si + 32 * (int64_t)k);
+      c += (int)ld_stream_1(si + 32 * (int64_t)k, pol_s);
       return c;
     } else {
-      return __ldg(si + 32 * (int64_t)k);
+      return ld_stream_1(si + 32 * (int64_t)k, pol_s);
     }
   };
   AccT acc = 0;
@@ -337,7 +351,7 @@ __global__ void __launch_bounds__(kSellThreads, 10) k_sell(const RunArgs a) {
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       xv[q] = (AccT)ldx<XL2>(x + column(k + q), pol_x);
-      v[q] = widen<AccT>(__ldg(sv + 32 * (int64_t)(k + q)));
+      v[q] = widen<AccT>(ld_stream_1(sv + 32 * (int64_t)(k + q), pol_s));
     }
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc = fma(v[q], xv[q], acc);
@@ -347,13 +361,14 @@ __global__ void __launch_bounds__(kSellThreads, 10) k_sell(const RunArgs a) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       xv[q] = (AccT)ldx<XL2>(x + column(k + q), pol_x);
-      v[q] = widen<AccT>(__ldg(sv + 32 * (int64_t)(k + q)));
+      v[q] = widen<AccT>(ld_stream_1(sv + 32 * (int64_t)(k + q), pol_s));
     }
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc = fma(v[q], xv[q], acc);
   }
   for (; k < len; ++k)
-    acc = fma(widen<AccT>(__ldg(sv + 32 * (int64_t)k)), (AccT)ldx<XL2>(x + column(k), pol_x), acc);
+    acc = fma(widen<AccT>(ld_stream_1(sv + 32 * (int64_t)k, pol_s)), (AccT)ldx<XL2>(x + column(k), pol_x),
+              acc);
   static_cast<VecT *>(a.y)[row] = (VecT)acc;
 }
 
