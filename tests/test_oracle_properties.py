@@ -226,3 +226,42 @@ def test_f32_rounding_matches_numpy_and_is_idempotent(a):
         want = np.array([a]).astype(np.float32)
     assert r.view(np.uint32)[0] == want.view(np.uint32)[0]
     assert oracle.round_f32(r.astype(np.float64)).view(np.uint32)[0] == r.view(np.uint32)[0]
+
+
+@settings(**SETTINGS)
+@given(**csr_args, line=st.sampled_from([2, 16, 32]), fits=st.booleans())
+def test_table1_features_against_a_direct_computation(seed, n_rows, n_cols, max_len, gap_scale,
+                                                      line, fits):
+    """Table I per row: nnz, bandwidth (last - first + 1), scatter nnz/bw, clustering (runs
+    of consecutive columns / nnz) and misses (the first element and every gap larger than a
+    cache line); averages and population deviations over all N rows (empty rows count as
+    zeros); size = working set within the last-level cache, density = NNZ / (N N_cols).
+    Ratios are compared within the oracle's 2^-24 quantization."""
+    n_rows = max(n_rows, 1)
+    rp, ci = random_csr(seed, n_rows, n_cols, max_len, gap_scale)
+    f, _ = oracle.features(n_rows, n_cols, rp, ci, line_elems=line,
+                           ws_bytes=100 if fits else 1000, llc_bytes=500)
+    d = dict(zip(oracle.FEATURE_NAMES, f))
+    nnz, bw, sc, cl, ms = (np.zeros(n_rows) for _ in range(5))
+    for i in range(n_rows):
+        c = ci[rp[i]:rp[i + 1]].astype(np.int64)
+        if c.size == 0:
+            continue
+        g = np.diff(c)
+        nnz[i] = c.size
+        bw[i] = c[-1] - c[0] + 1
+        sc[i] = c.size / bw[i]
+        cl[i] = (1 + np.count_nonzero(g != 1)) / c.size
+        ms[i] = 1 + np.count_nonzero(g > line)
+    assert d["size"] == (1.0 if fits else 0.0)
+    assert d["density"] == pytest.approx(rp[-1] / (n_rows * n_cols), rel=1e-15)
+    assert (d["nnz_min"], d["nnz_max"]) == (nnz.min(), nnz.max())
+    assert d["nnz_avg"] == pytest.approx(nnz.mean(), rel=1e-15)
+    assert d["nnz_sd"] == pytest.approx(nnz.std(), rel=1e-12, abs=1e-12)
+    assert (d["bw_min"], d["bw_max"]) == (bw.min(), bw.max())
+    assert d["bw_avg"] == pytest.approx(bw.mean(), rel=1e-15)
+    assert d["bw_sd"] == pytest.approx(bw.std(), rel=1e-12, abs=1e-9)
+    assert abs(d["scatter_avg"] - sc.mean()) <= 2 ** -24
+    assert abs(d["scatter_sd"] - sc.std()) <= 2 ** -20
+    assert abs(d["clustering_avg"] - cl.mean()) <= 2 ** -24
+    assert d["misses_avg"] == pytest.approx(ms.mean(), rel=1e-15)
