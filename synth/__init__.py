@@ -21,7 +21,7 @@ import numpy as np
 
 __all__ = [
     "Csr", "laplacian_2d", "stencil_27pt", "stencil_7pt", "power_law", "scattered",
-    "banded", "uniform_random", "dense_random", "identity", "permutation",
+    "banded", "uniform_random", "dense_random", "identity", "permutation", "random_gaps",
     "uniform_vector", "mixed_spec", "make_from_spec", "batched_specs",
     "SEED_BASE",
 ]
@@ -275,6 +275,33 @@ def dense_random(n_rows: int, n_cols: int, density: float, seed: int,
 def identity(n: int) -> Csr:
     return Csr(n, n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32),
                np.ones(n, dtype=np.float64), f"identity_{n}")
+
+
+def random_gaps(n_rows: int, n_cols: int, max_len: int, gap_scale: float, seed: int,
+                dtype=np.float64) -> Csr:
+    """Rows of 0..max_len sorted unique columns whose gaps are drawn geometrically around
+    gap_scale times a per-row factor of 0.01, 1 or 100, so one matrix mixes rows with small
+    gaps, gaps of thousands and gaps past 65,536; in about 30 % of rows one gap is set to
+    exactly 255, 256, 65,535 or 65,536. Values U[-1, 1]."""
+    rng = _rng(seed)
+    rows = []
+    for _ in range(n_rows):
+        length = int(rng.integers(0, max_len + 1))
+        if length == 0:
+            rows.append(np.zeros(0, np.int64))
+            continue
+        scale = gap_scale * float(rng.choice([0.01, 1.0, 100.0]))
+        gaps = rng.geometric(min(1.0, 1.0 / max(scale, 1.0)), length - 1)
+        if gaps.size and rng.random() < 0.3:
+            gaps[rng.integers(0, gaps.size)] = rng.choice([255, 256, 65535, 65536])
+        start = int(rng.integers(0, n_cols))
+        cols = start + np.concatenate([[0], np.cumsum(gaps)])
+        rows.append(cols[cols < n_cols])
+    counts = np.array([r.size for r in rows], np.int64)
+    colind = (np.concatenate(rows) if rows else np.zeros(0)).astype(np.int32)
+    val = rng.uniform(-1, 1, colind.size).astype(dtype)
+    return Csr(n_rows, n_cols, _rowptr_from_counts(counts), colind, val,
+               f"random_gaps_{n_rows}x{n_cols}_s{seed}")
 
 
 def permutation(n: int, seed: int) -> Csr:

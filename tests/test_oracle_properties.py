@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
+import synth
 
 hyp = pytest.importorskip("hypothesis")
 st = pytest.importorskip("hypothesis.strategies")
@@ -16,29 +17,8 @@ SETTINGS = dict(max_examples=60, deadline=None)
 
 
 def random_csr(seed, n_rows, n_cols, max_len, gap_scale):
-    """Sorted unique columns per row; gaps drawn geometrically around gap_scale, so that one
-    matrix mixes rows whose gaps fit 8 bits, 16 bits, or neither, some rows holding a gap
-    exactly at a width's limit."""
-    rng = np.random.default_rng(seed)
-    rows = []
-    for _ in range(n_rows):
-        length = int(rng.integers(0, max_len + 1))
-        if length == 0:
-            rows.append(np.zeros(0, np.int64))
-            continue
-        scale = gap_scale * float(rng.choice([0.01, 1.0, 100.0]))
-        gaps = rng.geometric(min(1.0, 1.0 / max(scale, 1.0)), length - 1)
-        if gaps.size and rng.random() < 0.3:
-            # a gap right at or just past an index width's limit
-            gaps[rng.integers(0, gaps.size)] = rng.choice([255, 256, 65535, 65536])
-        start = int(rng.integers(0, n_cols))
-        cols = start + np.concatenate([[0], np.cumsum(gaps)])
-        rows.append(cols[cols < n_cols])
-    lens = np.array([r.size for r in rows], np.int64)
-    rowptr = np.zeros(n_rows + 1, np.int32)
-    rowptr[1:] = np.cumsum(lens)
-    colind = (np.concatenate(rows) if rows else np.zeros(0)).astype(np.int32)
-    return rowptr, colind
+    m = synth.random_gaps(n_rows, n_cols, max_len, gap_scale, seed)
+    return m.rowptr, m.colind
 
 
 csr_args = dict(seed=st.integers(0, 2**31 - 1), n_rows=st.integers(0, 64),
