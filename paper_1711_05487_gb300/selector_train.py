@@ -8,7 +8,7 @@ trained on the GPU by the library's own kernels:
 
   1. for each seeded mixed matrix: Table I features (GPU), the profile route's class set (the
      label), and the time of every pool variant the class sets can select (the exhaustive
-     sweep that judges regret);
+     sweep that measures regret);
   2. standardize the MLP inputs on the training split and train with full-batch Adam
      (spmv_mlp_train: forward, backward and update kernels);
   3. on the held-out split: match ratios against the profile labels, and the geometric means
