@@ -644,10 +644,87 @@ def cpu_baseline(m, x_host, budget_s=8.0):
 
 
 # ---------------------------------------------------------------------- reference ----
+def _reference_line(args, metric, value, unit, higher, ms, config, cores, sample):
+    return {
+        "impl": "reference", "metric": metric, "value": value, "unit": unit,
+        "n_gpus": args.gpus, "device": "host CPU (the oracle; no GPU work)",
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": higher, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)", "config": config,
+        "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def run_reference_batched(args):
+    """The batched workload on the oracle: each step is one pass of FP64 SpMM products over
+    all matrices (FP32 values and X widened exactly), matrices spread over the host cores."""
+    import concurrent.futures as cf
+
+    import oracle
+    oracle.lib()
+    specs = synth.batched_specs(args.batch_count)
+    cores = os.cpu_count() or 1
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        mats = list(ex.map(lambda sp: synth.make_from_spec(sp, dtype=np.float32), specs))
+    Xs = [synth.uniform_vector(m.n_cols * sp["k"], sp["seed"], np.float32).reshape(m.n_cols, sp["k"])
+          for sp, m in zip(specs, mats)]
+    flops = sum(2.0 * m.nnz * sp["k"] for sp, m in zip(specs, mats))
+    work = list(zip(mats, Xs))
+
+    def one_pass(ex):
+        list(ex.map(lambda mx: oracle.spmm(mx[0].rowptr, mx[0].colind, mx[0].val, mx[1]), work))
+
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        for _ in range(args.warmup):
+            one_pass(ex)
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            one_pass(ex)
+        dt = (time.perf_counter() - t) / args.steps
+    v = round(flops / dt / 1e9, 4)
+    return _reference_line(
+        args, "batched SpMV/SpMM GFLOP/s (sum of 2*nnz*k / t), one persistent launch", v,
+        "GFLOP/s", True, round(dt * 1e3, 3),
+        {"workload": f"batched_{len(mats)}", "matrices": len(mats), "flops_per_step": flops},
+        cores, f"all {len(mats)} matrices per step, one FP64 SpMM per matrix, matrices spread "
+               f"over {cores} threads")
+
+
+def run_reference_cg(args):
+    """Conjugate gradients on the oracle (single-threaded plain C): the iterations to rtol
+    1e-8 come from one full solve; each step is a bounded sample of 25 iterations, and the
+    reported time per solve is the sample's time per iteration times that count."""
+    import oracle
+    oracle.lib()
+    m = synth.laplacian_27pt(160)
+    b = synth.uniform_vector(m.n_rows, synth.SEED_BASE + 15)
+    rtol, sample = 1e-8, 25
+    _, iters, conv, _ = oracle.cg(m.rowptr, m.colind, m.val, b, max_iters=5000, rtol=rtol)
+    for _ in range(args.warmup):
+        oracle.cg(m.rowptr, m.colind, m.val, b, max_iters=sample, rtol=0.0)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.cg(m.rowptr, m.colind, m.val, b, max_iters=sample, rtol=0.0)
+    per_iter = (time.perf_counter() - t) / (args.steps * sample)
+    ms = round(per_iter * iters * 1e3, 3)
+    return _reference_line(
+        args, "CG solve time to rtol 1e-8, SPD 27-point operator 160^3, tuned handle", ms, "ms",
+        False, ms, {"workload": "cg27_160", "n_rows": m.n_rows, "nnz": m.nnz, "rtol": rtol,
+                    "iters": iters, "converged": bool(conv)},
+        1, f"{sample} CG iterations per step, scaled to the {iters} iterations the oracle "
+           f"needs to reach rtol {rtol}")
+
+
 def run_reference(args):
     """The oracle (plain FP64 CPU CSR SpMV over the paper's static nnz-balanced row
     partition, one range per host core), timed on the host: --steps SpMVs of the same
     workload after --warmup untimed ones."""
+    if args.workload == "batched_512":
+        return run_reference_batched(args)
+    if args.workload == "cg27_160":
+        return run_reference_cg(args)
     import oracle
     oracle.lib()
     wl = WORKLOADS[args.workload]
@@ -705,8 +782,10 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         if rank == 0:
-            if args.steps > 20:
-                args.steps = 20
+            # bounded samples: the default run ends within a few minutes on the host cores
+            cap = 3 if args.workload == "batched_512" else (5 if args.workload == "cg27_160"
+                                                            else 20)
+            args.steps = max(1, min(args.steps, cap))
             print(json.dumps(run_reference(args)), flush=True)
         return
     if world > 1:

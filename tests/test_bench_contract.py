@@ -62,3 +62,20 @@ def test_whole_job_rate_and_dtype_sizes():
     assert b.dtype_bytes(3) == 8
     # N replicas of the same work in the max-over-ranks time
     assert b.whole_job_rate(2e9, 1.0, 4) == 4 * 2e9 / 1e-3 / 1e9
+
+
+def test_reference_arm_batched_line():
+    """The batched workload's reference arm: the oracle's SpMM over every matrix of the batch,
+    with the GPU arm's metric and unit."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "batched_512", "--batch-count", "6", "--steps", "2",
+                        "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "GFLOP/s" and d["higher_is_better"] is True
+    assert d["metric"].startswith("batched SpMV/SpMM GFLOP/s")
+    assert d["config"]["workload"] == "batched_6" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
