@@ -481,6 +481,9 @@ spmv_status spmv_mlp_train(const int32_t *sizes, float *params, float *m, float 
 spmv_status spmv_selector_create(spmv_selector_t *out, const int32_t *sizes,
                                  const float *params, const float *mu,
                                  const float *inv_sigma);
+
+/* Frees the selector's device buffers (synchronizes the device first). SPMV_ERR_ARG for
+ * NULL. A handle tuned through the selector keeps its variant. */
 spmv_status spmv_selector_destroy(spmv_selector_t s);
 
 /* The training range of the selector's inputs: lo and hi (host, SPMV_MLP_INPUTS floats
@@ -530,6 +533,8 @@ spmv_status spmv_batch_tune(spmv_batch_t b, int32_t reps, int32_t *item_nnz, int
 /* The same work as plain per-matrix launches (no graph, no persistence), for comparison. */
 spmv_status spmv_run_batched_sequential(spmv_batch_t b, spmv_stream_t stream);
 
+/* Frees the batch's plan, graph, streams and device buffers (synchronizes the device first);
+ * the handles and the caller's X / Y are not touched. SPMV_ERR_ARG for NULL. */
 spmv_status spmv_batch_destroy(spmv_batch_t b);
 
 #ifdef __cplusplus
