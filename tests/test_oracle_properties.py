@@ -245,3 +245,29 @@ def test_table1_features_against_a_direct_computation(seed, n_rows, n_cols, max_
     assert abs(d["scatter_sd"] - sc.std()) <= 2 ** -20
     assert abs(d["clustering_avg"] - cl.mean()) <= 2 ** -24
     assert d["misses_avg"] == pytest.approx(ms.mean(), rel=1e-15)
+
+
+@settings(**SETTINGS)
+@given(**csr_args, l_med=st.integers(1, 10), extra=st.integers(1, 14))
+def test_row_decomposition_bins_and_chunks(seed, n_rows, n_cols, max_len, gap_scale, l_med,
+                                           extra):
+    """Fig. 5's A = A_short + A_long with a medium bin: rows shorter than l_med are short,
+    rows of l_med..chunk-1 nonzeros medium (listed in order), longer rows long (listed in
+    order) and cut into consecutive chunks of `chunk` nonzeros, the last one the remainder;
+    a chunk's start column is the row's first column for its first chunk, else the column
+    before the chunk (the base its deltas start from)."""
+    chunk = l_med + extra
+    rp, ci = random_csr(seed, n_rows, n_cols, max_len, gap_scale)
+    lens = np.diff(rp.astype(np.int64))
+    med, lng, first, ch = oracle.row_bins(rp, ci, l_med=l_med, chunk=chunk)
+    assert np.array_equal(med, np.flatnonzero((lens >= l_med) & (lens < chunk)))
+    assert np.array_equal(lng, np.flatnonzero(lens >= chunk))
+    assert first.size == lng.size + 1 and first[0] == 0 and first[-1] == ch.shape[0]
+    for i, r in enumerate(lng):
+        cs = ch[first[i]:first[i + 1]].astype(np.int64)
+        starts = np.arange(rp[r], rp[r + 1], chunk)
+        assert np.array_equal(cs[:, 0], np.full(starts.size, r))
+        assert np.array_equal(cs[:, 1], starts)
+        assert np.array_equal(cs[:, 2], np.minimum(starts + chunk, rp[r + 1]))
+        want_c0 = np.where(starts > rp[r], ci[np.maximum(starts - 1, 0)], ci[rp[r]])
+        assert np.array_equal(cs[:, 3], want_c0)
