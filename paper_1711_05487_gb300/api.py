@@ -30,6 +30,7 @@ FEATURE_NAMES = ("size", "density", "nnz_min", "nnz_max", "nnz_avg", "nnz_sd", "
 
 
 def class_names(mask: int) -> list[str]:
+    """Names of the bottleneck classes (Fig. 3: MB, ML, IMB, CMP) set in a class mask."""
     return [n for b, n in CLASS_NAMES if mask & b]
 
 
@@ -42,6 +43,10 @@ def _stream(stream) -> int:
 
 
 def variant(partition=0, index=0, xpath=0, vec=0, vs=0, tile_rows=0, tile_pipe=0) -> spmv_variant:
+    """A pool variant (Table II knobs): partition 0 rows, 1 merge-path tiles, 2 row
+    decomposition, 3 sliced rows; index 1 delta columns; xpath 1 x evict-last in the L2,
+    P >= 2 P column panels; vec vector loads; vs sub-warp width (1: thread per row);
+    tile_rows / tile_pipe the width-1 tile geometry (0: chosen by the library)."""
     return spmv_variant(partition, index, xpath, vec, vs, tile_rows, tile_pipe)
 
 
@@ -72,10 +77,12 @@ class TuneResult:
 
     @property
     def class_names(self):
+        """Names of the classes the route found."""
         return class_names(self.classes)
 
     @staticmethod
     def from_report(r: _abi.spmv_tune_report) -> "TuneResult":
+        """Converts the C tune report."""
         return TuneResult(int(r.classes), int(r.mode_used), r.variant.as_tuple(),
                           dict(zip(P_NAMES, list(r.p))), list(r.p2), float(r.b_max_gbs),
                           dict(zip(FEATURE_NAMES, list(r.features))), float(r.margin),
@@ -109,13 +116,16 @@ class SpmvMatrix:
 
     @classmethod
     def from_csr(cls, m, stream=None) -> "SpmvMatrix":
+        """Copies a CSR matrix (n_rows, n_cols, rowptr, colind, val) into the library."""
         return cls(m.n_rows, m.n_cols, m.rowptr, m.colind, m.val, stream)
 
     @property
     def handle(self) -> int:
+        """The C handle, for calls through the ctypes binding."""
         return self._h
 
     def close(self):
+        """Destroys the C handle and frees its device memory."""
         if self._h:
             _abi.spmv_destroy(self._h)
             self._h = None
@@ -128,6 +138,8 @@ class SpmvMatrix:
 
     # ----------------------------------------------------------------- configuration
     def set_precision(self, storage="f64", vec="f64", acc="f64", stream=None):
+        """Value storage ('f64', 'f32', 'bf16', 'df64'), x / y dtype and accumulation;
+        the handle must be tuned again afterwards."""
         s, v, a = DTYPE_CODE[storage], DTYPE_CODE[vec], DTYPE_CODE[acc]
         try:
             _abi.spmv_set_precision(self._h, s, v, a, _stream(stream))
@@ -142,9 +154,13 @@ class SpmvMatrix:
 
     @property
     def vec_dtype(self) -> torch.dtype:
+        """torch dtype of x and y."""
         return TORCH_DTYPE[self.vec]
 
     def tune(self, mode="profile", stream=None, selector=None, fixed=None, **kw) -> TuneResult:
+        """Section III: classify with `mode` ('profile', 'features', 'learned' with a
+        `selector`, or 'fixed' with a `fixed` variant), then build and autotune the variant;
+        other keywords set fields of the tune options. Synchronizes."""
         opts = _abi.spmv_tune_opts_default()
         for k, val in kw.items():
             setattr(opts, k, val)
@@ -158,21 +174,27 @@ class SpmvMatrix:
         return self.report
 
     def set_variant(self, stream=None, **knobs):
+        """Installs a variant by hand (the knobs of `variant`; none: plain CSR-vector)."""
         v = variant(**{**CSR_VECTOR, **knobs})
         _abi.spmv_set_variant(self._h, v, _stream(stream))
 
     # ----------------------------------------------------------------------- running
     def run(self, x: torch.Tensor, y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """y = A x (Fig. 1) on device tensors, asynchronous on `stream`; allocates y when
+        it is not given."""
         if y is None:
             y = torch.empty(self.n_rows, dtype=self.vec_dtype, device=x.device)
         _abi.spmv_run(self._h, x.data_ptr(), y.data_ptr(), _stream(stream))
         return y
 
     def run_host(self, x: torch.Tensor, y: torch.Tensor, stream=None) -> torch.Tensor:
+        """y = A x with host tensors (page-locked ones replay a captured pipeline of
+        uploads, chunk kernels and downloads); returns when y is on the host."""
         _abi.spmv_run_host(self._h, x.data_ptr(), y.data_ptr(), _stream(stream))
         return y
 
     def spmm(self, X: torch.Tensor, Y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Y = A X for row-major X of shape (n_cols, k)."""
         k = X.shape[1]
         if Y is None:
             Y = torch.empty((self.n_rows, k), dtype=self.vec_dtype, device=X.device)
@@ -181,6 +203,8 @@ class SpmvMatrix:
 
     # ---------------------------------------------------------------- inspection
     def features(self, line_bytes=128, stream=None):
+        """Table I features computed on the GPU (14, FEATURE_NAMES order) and their 12 exact
+        integer sums."""
         f = np.zeros(14)
         isum = np.zeros(12, dtype=np.uint64)
         _abi.spmv_features(self._h, line_bytes, f.ctypes.data, isum.ctypes.data, _stream(stream))
@@ -201,6 +225,8 @@ class SpmvMatrix:
         return el, sm
 
     def profile_kernel(self, which: int, x: torch.Tensor, y: torch.Tensor, stream=None):
+        """Runs one profiling kernel once into y: 0 the static-partition baseline, 1 the
+        P_ML kernel, 2 the P_CMP kernel."""
         _abi.spmv_profile_kernel(self._h, which, x.data_ptr(), y.data_ptr(), _stream(stream))
         return y
 
@@ -217,6 +243,8 @@ class SpmvMatrix:
         return x, rep
 
     def export_csr(self, device="cuda", stream=None):
+        """The matrix as CSR with its stored values (columns decoded from the delta index
+        when the installed variant uses one)."""
         rp = torch.empty(self.n_rows + 1, dtype=torch.int32, device=device)
         ci = torch.empty(max(self.nnz, 1), dtype=torch.int32, device=device)
         v = torch.empty(max(self.nnz, 1), dtype=TORCH_DTYPE[self.storage], device=device)
@@ -271,12 +299,15 @@ class SpmvMatrix:
         return rp, ci[:self.nnz], v[:self.nnz], w
 
     def merge_path(self, device="cuda", stream=None):
+        """The merge-path table (rows ended, nonzeros consumed) at every tile boundary, and
+        the merge items per tile."""
         n_tiles, items = _abi.spmv_get_merge_path(self._h)
         c = torch.empty((n_tiles + 1, 2), dtype=torch.int32, device=device)
         _abi.spmv_get_merge_path(self._h, c.data_ptr(), _stream(stream))
         return c, items
 
     def device_bytes(self) -> int:
+        """Device memory held by the handle, in bytes."""
         return _abi.spmv_get_device_bytes(self._h)
 
 
@@ -304,10 +335,12 @@ class Selector:
                                          self.in_hi.ctypes.data, self.slack)
 
     def predict(self, feat16, stream=None):
+        """(class mask, margin) for 16 feature values; margin -1 outside the training range."""
         f = np.ascontiguousarray(feat16, dtype=np.float64)
         return _abi.spmv_selector_predict(self.handle, f.ctypes.data, _stream(stream))
 
     def close(self):
+        """Frees the selector's device buffers."""
         if self.handle:
             _abi.spmv_selector_destroy(self.handle)
             self.handle = None
@@ -319,6 +352,7 @@ class Selector:
             pass
 
     def save(self, path: str):
+        """Writes the weights, standardization and training range to an .npz file."""
         empty = np.zeros(0, np.float32)
         np.savez(path, sizes=self.sizes, params=self.params,
                  mu=self.mu if self.mu is not None else empty,
@@ -329,6 +363,7 @@ class Selector:
 
     @classmethod
     def load(cls, path: str) -> "Selector":
+        """Reads a selector written by `save`."""
         z = np.load(path)
         opt = {k: (z[k] if k in z.files and z[k].size else None)
                for k in ("mu", "inv_sigma", "in_lo", "in_hi")}
@@ -349,9 +384,11 @@ class Batch:
                                              _stream(stream))
 
     def run(self, stream=None):
+        """All products of the batch: one persistent launch replayed from a CUDA graph."""
         _abi.spmv_run_batched(self.handle, _stream(stream))
 
     def set_plan(self, item_nnz, chunk_nnz, stream=None):
+        """Sets the work plan: nonzeros per warp item and the chunk length of split rows."""
         _abi.spmv_batch_set_plan(self.handle, item_nnz, chunk_nnz, _stream(stream))
 
     def tune(self, reps=5, stream=None):
@@ -359,9 +396,11 @@ class Batch:
         return _abi.spmv_batch_tune(self.handle, reps, _stream(stream))
 
     def run_sequential(self, stream=None):
+        """The same products launched matrix by matrix, for comparison."""
         _abi.spmv_run_batched_sequential(self.handle, _stream(stream))
 
     def close(self):
+        """Frees the batch (its plan, graph and buffers; not the handles)."""
         if self.handle:
             _abi.spmv_batch_destroy(self.handle)
             self.handle = None
