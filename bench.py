@@ -717,6 +717,34 @@ def run_reference_cg(args):
            f"needs to reach rtol {rtol}")
 
 
+def cpu_baseline_batched(args):
+    """The oracle's side of the batched line: two timed passes of FP64 SpMM products over the
+    whole batch on the host cores (the reference arm's computation)."""
+    import argparse as _ap
+    ref = run_reference_batched(_ap.Namespace(batch_count=args.batch_count, warmup=1, steps=2,
+                                              gpus=1))
+    cb = dict(ref["cpu_baseline"])
+    cb["sample"] = "whole batch, 2 passes: " + cb["sample"]
+    return cb
+
+
+def cpu_baseline_cg(iters, sample=25):
+    """The oracle's side of the CG line: time per iteration of the oracle's conjugate
+    gradients (single-threaded) over `sample` iterations, times the timed solve's count."""
+    import oracle
+    oracle.lib()
+    m = synth.laplacian_27pt(160)
+    b = synth.uniform_vector(m.n_rows, synth.SEED_BASE + 15)
+    oracle.cg(m.rowptr, m.colind, m.val, b, max_iters=2, rtol=0.0)          # warm-up
+    t = time.perf_counter()
+    oracle.cg(m.rowptr, m.colind, m.val, b, max_iters=sample, rtol=0.0)
+    per_iter = (time.perf_counter() - t) / sample
+    return {"value": round(per_iter * iters * 1e3, 3), "unit": "ms", "cores": 1,
+            "kind": "oracle",
+            "sample": f"{sample} CG iterations of the oracle on the same operator, scaled to "
+                      f"the {iters} iterations of the timed solve"}
+
+
 def run_reference(args):
     """The oracle (plain FP64 CPU CSR SpMV over the paper's static nnz-balanced row
     partition, one range per host core), timed on the host: --steps SpMVs of the same
@@ -796,6 +824,10 @@ def main():
     if args.workload in ("batched_512", "cg27_160"):
         out = (run_batched if args.workload == "batched_512" else run_cg)(args, rank, world)
         if rank == 0:
+            if not args.no_cpu_baseline and world == 1:      # the oracle baseline: N = 1 only
+                out["cpu_baseline"] = (
+                    cpu_baseline_batched(args) if args.workload == "batched_512"
+                    else cpu_baseline_cg(out["solves"]["tuned_f64"]["iters"]))
             print(json.dumps(out), flush=True)
         return
     out, m = run_ours(args, rank, world)

@@ -79,3 +79,22 @@ def test_reference_arm_batched_line():
     assert d["config"]["workload"] == "batched_6" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_batched_and_cg_lines_carry_the_oracle_baseline(monkeypatch, capsys):
+    """main() attaches the oracle's cpu_baseline to the batched and CG lines at N = 1 (the
+    GPU runs are replaced by stubs here; the baselines themselves run on the host)."""
+    b = _bench_module()
+    monkeypatch.setattr(b, "run_batched", lambda args, rank, world: {"metric": "batched"})
+    monkeypatch.setattr(b, "run_cg", lambda args, rank, world:
+                        {"metric": "cg", "solves": {"tuned_f64": {"iters": 300}}})
+    small = b.synth.laplacian_27pt
+    monkeypatch.setattr(b.synth, "laplacian_27pt", lambda n: small(24))
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    for wl, unit in (("batched_512", "GFLOP/s"), ("cg27_160", "ms")):
+        monkeypatch.setattr(sys, "argv", ["bench.py", "--workload", wl, "--batch-count", "4"])
+        b.main()
+        d = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+        cb = d["cpu_baseline"]
+        assert cb["kind"] == "oracle" and cb["unit"] == unit and cb["value"] > 0
+        assert cb["cores"] >= 1 and cb["sample"]
