@@ -46,6 +46,14 @@ def test_library_exports_every_declared_symbol(abi):
     assert declared == set(abi.DECLARED)
 
 
+def test_binding_has_one_function_per_declared_call():
+    """The Python binding is argument marshalling with the header's names: one function per
+    declared entry point, and nothing else named like one."""
+    src = open(os.path.join(ROOT, "paper_1711_05487_gb300", "_abi.py")).read()
+    bound = set(re.findall(r"^def (spmv_[a-z0-9_]+)\(", src, flags=re.M))
+    assert bound == _declared_functions()
+
+
 def test_status_strings(abi):
     for s in range(10):
         assert abi.spmv_status_string(s)
