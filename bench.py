@@ -636,7 +636,7 @@ def cpu_baseline(m, x_host, budget_s=8.0):
     rates = _time_rates(par, m.nnz, budget_s)
     rates1 = _time_rates(lambda: oracle.spmv(m.rowptr, m.colind, m.val, x_host), m.nnz, budget_s)
     return {"value": round(oracle.harmonic_mean(rates), 4), "unit": "GFLOP/s",
-            "cores": used[0], "kind": "oracle",
+            "cores": used[0], "kind": "oracle", "build": "gcc " + " ".join(oracle.BUILD_FLAGS),
             "sample": f"full matrix, {len(rates)} SpMVs, harmonic mean of per-SpMV rates; "
                       "static nnz-balanced row partition, one range per thread",
             "single_thread": {"value": round(oracle.harmonic_mean(rates1), 4), "cores": 1,
@@ -644,6 +644,11 @@ def cpu_baseline(m, x_host, budget_s=8.0):
 
 
 # ---------------------------------------------------------------------- reference ----
+def _oracle_build_flags():
+    import oracle
+    return "gcc " + " ".join(oracle.BUILD_FLAGS)
+
+
 def _reference_line(args, metric, value, unit, higher, ms, config, cores, sample):
     return {
         "impl": "reference", "metric": metric, "value": value, "unit": unit,
@@ -652,7 +657,7 @@ def _reference_line(args, metric, value, unit, higher, ms, config, cores, sample
         "higher_is_better": higher, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded)", "config": config,
         "cpu_baseline": {"value": value, "unit": unit, "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "build": _oracle_build_flags()},
         "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -740,7 +745,7 @@ def cpu_baseline_cg(iters, sample=25):
     oracle.cg(m.rowptr, m.colind, m.val, b, max_iters=sample, rtol=0.0)
     per_iter = (time.perf_counter() - t) / sample
     return {"value": round(per_iter * iters * 1e3, 3), "unit": "ms", "cores": 1,
-            "kind": "oracle",
+            "kind": "oracle", "build": _oracle_build_flags(),
             "sample": f"{sample} CG iterations of the oracle on the same operator, scaled to "
                       f"the {iters} iterations of the timed solve"}
 
@@ -777,7 +782,7 @@ def run_reference(args):
         "config": {"workload": args.workload, "desc": wl["desc"], "n_rows": m.n_rows,
                    "nnz": m.nnz},
         "cpu_baseline": {"value": round(v, 4), "unit": "GFLOP/s", "cores": used,
-                         "kind": "oracle",
+                         "kind": "oracle", "build": _oracle_build_flags(),
                          "sample": f"full matrix, {args.steps} SpMVs, static nnz-balanced "
                                    "row partition, one range per thread"},
         "e2e": {"value": round(v, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0,

@@ -154,6 +154,10 @@ spmv_status spmv_destroy(spmv_handle_t h);
  * round-to-nearest-even straight from the input values. Offered: storage F64 with
  * vec = acc = F64; storage F32 or BF16 with (vec, acc) in {(F64,F64),(F32,F32),(F32,F64),
  * (F64,DF64),(F32,DF64)}; storage DF64 with vec = F64, acc = DF64 (FP64 input values only).
+ * acc = F32 keeps every FP32 running sum within the FP32-storage bound (2e-6 of
+ * sum_j |a_ij x_j| against the FP64 values): a thread sums at most 30 products of a row in
+ * FP32 alone, and a longer chain (a long row, or a lane's share of one) is summed in runs of
+ * 16 FP32 products whose sums, and the lanes' reduction, are added in FP64.
  * acc = DF64 with F32 / BF16 storage: width-1 row variants sum each row in double-float
  * arithmetic on the FP32 pipe (a stored value and an FP32 x element are exact in the high
  * part), within about 8e-13 of sum_j |a_ij x_j| against the stored values, the FP64 bound;
@@ -400,8 +404,10 @@ const char *spmv_status_string(spmv_status s);
  * merge items) are rejected with SPMV_ERR_TOO_LARGE before any work is queued.
  *
  * The first call on each device looks up the array's device address (a runtime call that
- * may synchronize); make that first call before any stream capture. Asynchronous on
- * stream otherwise. All calls share the one array and each call's scratch contents stay
+ * may synchronize, and that creates the device's context if needed); make that first call
+ * before any stream capture. The address is kept per CUDA context: after cudaDeviceReset
+ * (a new context, in which the array may sit elsewhere) the next call looks it up again, so
+ * it too should come before any capture. Asynchronous on stream otherwise. All calls share the one array and each call's scratch contents stay
  * there until the next call overwrites them, so calls whose work overlaps on the GPU (on
  * different streams, or from different host threads, without ordering between them) race
  * and give wrong results; serialize them on one stream or with events. Errors:
@@ -501,7 +507,9 @@ spmv_status spmv_selector_predict(spmv_selector_t s, const double *feat16, uint3
                                   double *margin, spmv_stream_t stream);
 
 /* ----------------------------------------------------------------- batched SpMM ---- */
-/* A batch of `count` tuned handles with FP32 storage, FP32 x/y and FP32 accumulation;
+/* A batch of `count` tuned handles with FP32 storage, FP32 x/y and FP32 accumulation
+ * (runs of at most 16 FP32 products per lane, summed in FP64 on long rows, so every row
+ * stays within 2e-6 of sum_j |a_ij x_j|);
  * X[i] (n_cols_i x k[i]) and Y[i] (n_rows_i x k[i]) are row-major device arrays, k[i] in
  * {1, 4, 16}. The batch plans row-block work items (long rows split, partials summed in
  * FP64) and owns a CUDA graph of its launches. It reads the handles' device arrays in

@@ -32,19 +32,30 @@ FEATURE_NAMES = ("size", "density", "nnz_min", "nnz_max", "nnz_avg", "nnz_sd", "
                  "clustering_avg", "misses_avg")
 
 
+# Compiler flags. -ffp-contract=off keeps every FP64 operation rounded as written (no fused
+# multiply-adds), which the fixed-order MLP inference and the exact pins rely on; -O3 is the
+# optimisation level of the timed CPU baseline. No -march=native: the same flags build the
+# same arithmetic on the x86 and Arm hosts.
+BUILD_FLAGS = ("-O3", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp")
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc into oracle/_build/liboracle.so."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+    stamp = os.path.join(_BUILD, "flags.txt")
+    flags = " ".join(BUILD_FLAGS)
+    if (not force and os.path.exists(_LIB_PATH) and os.path.exists(stamp)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)
+            and open(stamp).read() == flags):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared",
-           "-fPIC", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", *BUILD_FLAGS, "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
     # OpenMP only serves the static-partition baseline; without it that runs on one thread
-    if subprocess.run(cmd[:-1] + ["-fopenmp", "-lm"], capture_output=True).returncode != 0:
-        subprocess.run(cmd, check=True)
+    if subprocess.run(cmd, capture_output=True).returncode != 0:
+        subprocess.run([c for c in cmd if c != "-fopenmp"], check=True)
     os.replace(tmp, _LIB_PATH)
+    with open(stamp, "w") as fh:
+        fh.write(flags)
     return _LIB_PATH
 
 

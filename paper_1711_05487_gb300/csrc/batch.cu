@@ -6,8 +6,10 @@
 // items: every warp takes the next item from a device counter with atomicAdd (no warp or CTA
 // ever waits on another), a row-block item is computed by sub-warps of the matrix's width,
 // a chunk of a long row by the whole warp into an FP64 partial slot, and k_batch_fixup adds
-// the chunks of each split row in chunk order, in FP64. Storage, x/y and accumulation are
-// FP32; X and Y are row-major (n x k).
+// the chunks of each split row in chunk order, in FP64. Storage and x/y are FP32; the
+// accumulation is FP32 in runs of at most kF32Run products per lane, whose sums add in FP64
+// wherever a lane's chain would be longer, so every row stays within the FP32 bound; X and
+// Y are row-major (n x k).
 #include "common.cuh"
 
 namespace spmv {
@@ -36,6 +38,77 @@ __device__ __forceinline__ void load_xrow(const float *p, float *o) {
 // sub-warp at a time. The U rows' bounds, values, columns and x rows are loaded together
 // before any multiply-add, so U chains of dependent loads are in flight per lane instead of
 // one. Each row's lane sums and their reduction keep the order of a single-row walk.
+// FOLD (rows longer than kF32Run products per lane): every lane's FP32 sums are moved to
+// FP64 after each run of kF32Run products and the lane reduction is in FP64, which keeps a
+// long row within the FP32 bound; short rows stay in FP32 throughout.
+template <int K, int VS, int U, bool FOLD>
+__device__ __forceinline__ void warp_rows_group(const BatchMat &m, int row0, int r1, int sl,
+                                                unsigned mask, const int (&s)[U],
+                                                const int (&e)[U], int maxlen) {
+  constexpr int GROUPS = 32 / VS;
+  float acc[U][K];
+  double tot[FOLD ? U : 1][FOLD ? K : 1];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+#pragma unroll
+    for (int q = 0; q < K; ++q) acc[u][q] = 0.0f;
+  if constexpr (FOLD) {
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int q = 0; q < K; ++q) tot[u][q] = 0.0;
+  }
+  int steps = 0;
+  for (int off = sl; off < maxlen; off += VS) {
+    float v[U];
+    int c[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = s[u] + off;
+      const bool ok = j < e[u];
+      v[u] = ok ? __ldg(m.val + j) : 0.0f;
+      c[u] = ok ? __ldg(m.colind + j) : -1;
+    }
+    float xr[U][K];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (c[u] >= 0) {
+        load_xrow<K>(m.X + (int64_t)c[u] * K, xr[u]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < K; ++q) xr[u][q] = 0.0f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int q = 0; q < K; ++q) acc[u][q] = fmaf(v[u], xr[u][q], acc[u][q]);
+    if constexpr (FOLD) {
+      if (++steps == kF32Run) {
+        steps = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int q = 0; q < K; ++q) {
+            tot[u][q] += (double)acc[u][q];
+            acc[u][q] = 0.0f;
+          }
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int row = row0 + u * GROUPS;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      float r;
+      if constexpr (FOLD) r = (float)group_sum<VS>(tot[u][q] + (double)acc[u][q], mask);
+      else r = group_sum<VS>(acc[u][q], mask);
+      if (sl == 0 && row < r1) m.Y[(int64_t)row * K + q] = r;
+    }
+  }
+}
+
 template <int K, int VS, int U>
 __device__ void warp_rows(const BatchMat &m, int r0, int r1, int lane) {
   constexpr int GROUPS = 32 / VS;
@@ -55,44 +128,17 @@ __device__ void warp_rows(const BatchMat &m, int r0, int r1, int lane) {
       }
       maxlen = max(maxlen, e[u] - s[u]);
     }
-    float acc[U][K];
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int q = 0; q < K; ++q) acc[u][q] = 0.0f;
-    for (int off = sl; off < maxlen; off += VS) {
-      float v[U];
-      int c[U];
+    // uniform over the sub-warp: the U rows' lengths are the same in all its lanes. Rows
+    // long enough to fold have work enough per lane to go one at a time (fewer registers).
+    if (maxlen > kF32Run * VS) {
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int j = s[u] + off;
-        const bool ok = j < e[u];
-        v[u] = ok ? __ldg(m.val + j) : 0.0f;
-        c[u] = ok ? __ldg(m.colind + j) : -1;
+        const int su[1] = {s[u]}, eu[1] = {e[u]};
+        warp_rows_group<K, VS, 1, true>(m, row0 + u * GROUPS, r1, sl, mask, su, eu,
+                                        e[u] - s[u]);
       }
-      float xr[U][K];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (c[u] >= 0) {
-          load_xrow<K>(m.X + (int64_t)c[u] * K, xr[u]);
-        } else {
-#pragma unroll
-          for (int q = 0; q < K; ++q) xr[u][q] = 0.0f;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int q = 0; q < K; ++q) acc[u][q] = fmaf(v[u], xr[u][q], acc[u][q]);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int row = row0 + u * GROUPS;
-#pragma unroll
-      for (int q = 0; q < K; ++q) {
-        const float r = group_sum<VS>(acc[u][q], mask);
-        if (sl == 0 && row < r1) m.Y[(int64_t)row * K + q] = r;
-      }
+    } else {
+      warp_rows_group<K, VS, U, false>(m, row0, r1, sl, mask, s, e, maxlen);
     }
   }
 }
@@ -101,6 +147,66 @@ __device__ void warp_rows(const BatchMat &m, int r0, int r1, int lane) {
 // its x row and keeping 4 accumulators, so a sub-warp of VS lanes has VS / 4 nonzeros of its
 // row in flight (two per quad per step) instead of one 64-byte gather per lane. The quads'
 // sums of one row are added with a fixed shuffle tree; the quad of slot 0 writes the row.
+// FOLD (rows of more than kF32Run products per lane): FP32 sums of kF32Run products (eight
+// steps) are moved to FP64 and the quads' sums are added in FP64.
+template <int VS, bool FOLD>
+__device__ __forceinline__ void row_k16(const BatchMat &m, int row, int s, int e, int slot,
+                                        int quad, unsigned mask) {
+  constexpr int SLOTS = VS / 4;
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  double tot[4] = {0.0, 0.0, 0.0, 0.0};
+  int steps = 0;
+  int j = s + slot;
+  for (; j + SLOTS < e; j += 2 * SLOTS) {
+    const float v0 = __ldg(m.val + j), v1 = __ldg(m.val + j + SLOTS);
+    const int c0 = __ldg(m.colind + j), c1 = __ldg(m.colind + j + SLOTS);
+    const uint4 x0 = ld_nc_u4(m.X + (int64_t)c0 * 16 + quad * 4);
+    const uint4 x1 = ld_nc_u4(m.X + (int64_t)c1 * 16 + quad * 4);
+    acc[0] = fmaf(v1, __uint_as_float(x1.x), fmaf(v0, __uint_as_float(x0.x), acc[0]));
+    acc[1] = fmaf(v1, __uint_as_float(x1.y), fmaf(v0, __uint_as_float(x0.y), acc[1]));
+    acc[2] = fmaf(v1, __uint_as_float(x1.z), fmaf(v0, __uint_as_float(x0.z), acc[2]));
+    acc[3] = fmaf(v1, __uint_as_float(x1.w), fmaf(v0, __uint_as_float(x0.w), acc[3]));
+    if constexpr (FOLD) {
+      if (++steps == kF32Run / 2) {
+        steps = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          tot[q] += (double)acc[q];
+          acc[q] = 0.0f;
+        }
+      }
+    }
+  }
+  if (j < e) {
+    const float v0 = __ldg(m.val + j);
+    const uint4 x0 = ld_nc_u4(m.X + (int64_t)__ldg(m.colind + j) * 16 + quad * 4);
+    acc[0] = fmaf(v0, __uint_as_float(x0.x), acc[0]);
+    acc[1] = fmaf(v0, __uint_as_float(x0.y), acc[1]);
+    acc[2] = fmaf(v0, __uint_as_float(x0.z), acc[2]);
+    acc[3] = fmaf(v0, __uint_as_float(x0.w), acc[3]);
+  }
+  float r[4];
+  if constexpr (FOLD) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double t = tot[q] + (double)acc[q];
+#pragma unroll
+      for (int off = 4; off < VS; off <<= 1) t += __shfl_xor_sync(mask, t, off, VS);
+      r[q] = (float)t;
+    }
+  } else {
+#pragma unroll
+    for (int off = 4; off < VS; off <<= 1)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += __shfl_xor_sync(mask, acc[q], off, VS);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) r[q] = acc[q];
+  }
+  if (slot == 0)
+    *reinterpret_cast<float4 *>(m.Y + (int64_t)row * 16 + quad * 4) =
+        make_float4(r[0], r[1], r[2], r[3]);
+}
+
 template <int VS>
 __device__ void warp_rows_k16(const BatchMat &m, int r0, int r1, int lane) {
   static_assert(VS >= 4, "a quad per nonzero");
@@ -109,33 +215,8 @@ __device__ void warp_rows_k16(const BatchMat &m, int r0, int r1, int lane) {
   const unsigned mask = group_mask<VS>();
   for (int row = r0 + lane / VS; row < r1; row += GROUPS) {
     const int s = __ldg(m.rowptr + row), e = __ldg(m.rowptr + row + 1);
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    int j = s + slot;
-    for (; j + SLOTS < e; j += 2 * SLOTS) {
-      const float v0 = __ldg(m.val + j), v1 = __ldg(m.val + j + SLOTS);
-      const int c0 = __ldg(m.colind + j), c1 = __ldg(m.colind + j + SLOTS);
-      const uint4 x0 = ld_nc_u4(m.X + (int64_t)c0 * 16 + quad * 4);
-      const uint4 x1 = ld_nc_u4(m.X + (int64_t)c1 * 16 + quad * 4);
-      acc[0] = fmaf(v1, __uint_as_float(x1.x), fmaf(v0, __uint_as_float(x0.x), acc[0]));
-      acc[1] = fmaf(v1, __uint_as_float(x1.y), fmaf(v0, __uint_as_float(x0.y), acc[1]));
-      acc[2] = fmaf(v1, __uint_as_float(x1.z), fmaf(v0, __uint_as_float(x0.z), acc[2]));
-      acc[3] = fmaf(v1, __uint_as_float(x1.w), fmaf(v0, __uint_as_float(x0.w), acc[3]));
-    }
-    if (j < e) {
-      const float v0 = __ldg(m.val + j);
-      const uint4 x0 = ld_nc_u4(m.X + (int64_t)__ldg(m.colind + j) * 16 + quad * 4);
-      acc[0] = fmaf(v0, __uint_as_float(x0.x), acc[0]);
-      acc[1] = fmaf(v0, __uint_as_float(x0.y), acc[1]);
-      acc[2] = fmaf(v0, __uint_as_float(x0.z), acc[2]);
-      acc[3] = fmaf(v0, __uint_as_float(x0.w), acc[3]);
-    }
-#pragma unroll
-    for (int off = 4; off < VS; off <<= 1)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] += __shfl_xor_sync(mask, acc[q], off, VS);
-    if (slot == 0)
-      *reinterpret_cast<float4 *>(m.Y + (int64_t)row * 16 + quad * 4) =
-          make_float4(acc[0], acc[1], acc[2], acc[3]);
+    if (e - s > kF32Run * SLOTS) row_k16<VS, true>(m, row, s, e, slot, quad, mask);
+    else row_k16<VS, false>(m, row, s, e, slot, quad, mask);
   }
 }
 
@@ -166,14 +247,17 @@ __device__ void warp_rows_vs(const BatchMat &m, int r0, int r1, int lane) {
   }
 }
 
-// Nonzeros [z0, z1) of one long row by one warp: FP32 lane sums, then a fixed shuffle tree
-// in FP64 into partial slot `chunk` (16 doubles per slot, k used).
+// Nonzeros [z0, z1) of one long row by one warp: FP32 lane sums of at most kF32Run
+// products at a time, moved to FP64, then a fixed shuffle tree in FP64 into partial slot
+// `chunk` (16 doubles per slot, k used).
 // K = 16: eight slots of a quad each (as in warp_rows_k16); the slots' sums are added in
 // FP64 with a fixed shuffle tree and the quad of slot 0 writes the 16 partials.
 __device__ void warp_chunk_k16(const BatchMat &m, int z0, int z1, int chunk, double *partials,
                                int lane) {
   const int slot = lane >> 2, quad = lane & 3;
   float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  int steps = 0;
   int j = z0 + slot;
   for (; j + 8 < z1; j += 16) {
     const float v0 = __ldg(m.val + j), v1 = __ldg(m.val + j + 8);
@@ -184,6 +268,14 @@ __device__ void warp_chunk_k16(const BatchMat &m, int z0, int z1, int chunk, dou
     acc[1] = fmaf(v1, __uint_as_float(x1.y), fmaf(v0, __uint_as_float(x0.y), acc[1]));
     acc[2] = fmaf(v1, __uint_as_float(x1.z), fmaf(v0, __uint_as_float(x0.z), acc[2]));
     acc[3] = fmaf(v1, __uint_as_float(x1.w), fmaf(v0, __uint_as_float(x0.w), acc[3]));
+    if (++steps == kF32Run / 2) {
+      steps = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        t[q] += (double)acc[q];
+        acc[q] = 0.0f;
+      }
+    }
   }
   if (j < z1) {
     const float v0 = __ldg(m.val + j);
@@ -193,10 +285,9 @@ __device__ void warp_chunk_k16(const BatchMat &m, int z0, int z1, int chunk, dou
     acc[2] = fmaf(v0, __uint_as_float(x0.z), acc[2]);
     acc[3] = fmaf(v0, __uint_as_float(x0.w), acc[3]);
   }
-  double t[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    t[q] = (double)acc[q];
+    t[q] += (double)acc[q];
 #pragma unroll
     for (int off = 4; off < 32; off <<= 1) t[q] += __shfl_xor_sync(0xffffffffu, t[q], off);
   }
@@ -214,8 +305,13 @@ __device__ void warp_chunk(const BatchMat &m, int z0, int z1, int chunk, double 
     return;
   }
   float acc[K];
+  double t[K];
 #pragma unroll
-  for (int q = 0; q < K; ++q) acc[q] = 0.0f;
+  for (int q = 0; q < K; ++q) {
+    acc[q] = 0.0f;
+    t[q] = 0.0;
+  }
+  int steps = 0;
   // two elements per lane per step: both loads issue before the multiply-adds, which then
   // run in element order
   int j = z0 + lane;
@@ -227,6 +323,14 @@ __device__ void warp_chunk(const BatchMat &m, int z0, int z1, int chunk, double 
     load_xrow<K>(m.X + (int64_t)c1 * K, x1);
 #pragma unroll
     for (int q = 0; q < K; ++q) acc[q] = fmaf(v1, x1[q], fmaf(v0, x0[q], acc[q]));
+    if (++steps == kF32Run / 2) {
+      steps = 0;
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        t[q] += (double)acc[q];
+        acc[q] = 0.0f;
+      }
+    }
   }
   if (j < z1) {
     const float v = __ldg(m.val + j);
@@ -237,7 +341,7 @@ __device__ void warp_chunk(const BatchMat &m, int z0, int z1, int chunk, double 
   }
 #pragma unroll
   for (int q = 0; q < K; ++q) {
-    const double r = group_sum<32>((double)acc[q], 0xffffffffu);
+    const double r = group_sum<32>(t[q] + (double)acc[q], 0xffffffffu);
     if (lane == 0) partials[(int64_t)chunk * 16 + q] = r;
   }
 }

@@ -22,6 +22,20 @@ template <typename AccT> __device__ __forceinline__ AccT widen(__nv_bfloat16 v) 
   return (AccT)__bfloat162float(v);
 }
 
+// ------------------------------------------------- FP32 accumulation within its bound ----
+// With FP32 accumulation a row's result must stay within 2e-6 of sum_j |a_ij x_j| (the
+// FP32-storage tolerance). Every FP32 addition rounds the running sum by at most
+// u = 2^-24 of its magnitude, which is at most sum_j |a_ij x_j|, so a value that went
+// through n roundings errs by at most n u. No FP32 running sum therefore takes more than
+// about 30 roundings (its products, its share of a lane reduction, the final store, and
+// one for values rounded to FP32 from FP64): a row whose chain would be longer is summed
+// in runs of kF32Run products whose FP32 sums are added in FP64 (at most 16 u + the
+// final store).
+constexpr int kF32Run = 16;     // products per FP32 run before its sum moves to FP64
+constexpr int kF32Chain = 30;   // longest row one thread sums in FP32 alone
+template <typename AccT> struct IsF32 { static constexpr bool value = false; };
+template <> struct IsF32<float> { static constexpr bool value = true; };
+
 // bf16 held in the low / high half of a 32-bit word -> float (exact)
 __device__ __forceinline__ float bf16lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }

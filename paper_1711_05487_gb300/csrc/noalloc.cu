@@ -24,24 +24,68 @@ constexpr long long kMaxItems = kMaxTiles * spmv::kMergeItems;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch per device, looked up once (the name of the array in
-// host code is only a stand-in for the symbol, not a device address).
+// Device address of g_noalloc_scratch per device, looked up once per CUDA context (the name
+// of the array in host code is only a stand-in for the symbol, not a device address). The
+// cache is keyed by the context's unique id: after cudaDeviceReset the runtime creates a new
+// context and loads the kernels again, possibly at another address, so an address taken in
+// the old context is never reused.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+struct ScratchSlot {
+  unsigned long long ctx_id = 0;   // 0: not looked up yet
+  void *addr = nullptr;
+};
+
 std::mutex g_mu;
-void *g_scratch[128] = {};
+ScratchSlot g_scratch[128];
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+bool g_entry_points = false;
+
+// Id of the calling thread's current context, 0 if there is none yet (the runtime makes the
+// device's primary context current on its first use of the device). Holds g_mu.
+unsigned long long current_ctx_id() {
+  if (!g_entry_points) {
+    g_entry_points = true;
+    void *f = nullptr, *g = nullptr;
+    cudaDriverEntryPointQueryResult q1{}, q2{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1) ==
+            cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &g, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f);
+      g_ctx_id = reinterpret_cast<CtxGetIdFn>(g);
+    }
+    cudaGetLastError();
+  }
+  if (!g_ctx_current || !g_ctx_id) return 0;
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_current(&ctx) != 0 || !ctx) return 0;
+  if (g_ctx_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
 spmv_status scratch_address(int dev, unsigned char **out) {
   if (dev < 0 || dev >= 128) return SPMV_ERR_ARG;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch[dev]) {
+  ScratchSlot &slot = g_scratch[dev];
+  const unsigned long long id = current_ctx_id();
+  if (id == 0 || slot.ctx_id != id || !slot.addr) {
+    // set-up with the device current: the symbol lookup also creates the context (and
+    // loads the kernels) if this is the device's first use
     void *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
       cudaGetLastError();
       return SPMV_ERR_CUDA;
     }
-    g_scratch[dev] = p;
+    slot.addr = p;
+    slot.ctx_id = current_ctx_id();   // 0 (no driver entry points): looked up on every call
   }
-  *out = static_cast<unsigned char *>(g_scratch[dev]);
+  *out = static_cast<unsigned char *>(slot.addr);
   return SPMV_OK;
 }
 

@@ -184,6 +184,53 @@ __device__ __forceinline__ SumT delta_range_dot(const RunArgs &a, int s, int e, 
 }
 
 // ------------------------------------------------------------------------ k_rowvec ----
+// One lane's share of sum_{j in [s, e)} val[j] x[colind[j]], lanes strided by VS (Fig. 1's
+// inner loop spread over a sub-warp). With SumT wider than AccT the lane's products are
+// summed in runs of kF32Run in AccT and the run sums in SumT.
+template <typename ValT, typename VecT, typename AccT, int VS, bool XL2, typename SumT>
+__device__ __forceinline__ SumT strided_dot(const RunArgs &a, int s, int e, int lane,
+                                            uint64_t pol_x) {
+  const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
+  const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
+  const int32_t *__restrict__ col = a.colind;
+  if constexpr (std::is_same<SumT, AccT>::value) {
+    AccT sum = 0;
+    for (int j = s + lane; j < e; j += VS)
+      sum += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(col + j), pol_x);
+    return sum;
+  } else {
+    SumT sum = 0;
+    for (int j0 = s + lane; j0 < e; j0 += kF32Run * VS) {
+      const int j1 = min(e, j0 + kF32Run * VS);
+      AccT part = 0;
+      for (int j = j0; j < j1; j += VS)
+        part += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(col + j), pol_x);
+      sum += (SumT)part;
+    }
+    return sum;
+  }
+}
+
+// One lane's share of row `row` with the knobs of k_rowvec.
+template <typename ValT, typename VecT, typename AccT, int VS, bool VEC, int DB, bool XL2,
+          typename SumT>
+__device__ __forceinline__ SumT rowvec_dot(const RunArgs &a, int64_t row, int s, int e,
+                                           int lane, unsigned mask, uint64_t pol_s,
+                                           uint64_t pol_x) {
+  if constexpr (!VEC) {
+    return strided_dot<ValT, VecT, AccT, VS, XL2, SumT>(a, s, e, lane, pol_x);
+  } else if constexpr (DB == 0) {
+    return vec_range_dot<ValT, VecT, AccT, VS, XL2, SumT>(a, s, e, lane, pol_s, pol_x);
+  } else {
+    const int32_t base = __ldg(a.dbase + row);
+    if (base < 0)
+      return esc_range_dot<ValT, VecT, AccT, VS, XL2, SumT>(a, s, e, a.esc + (-(int64_t)base - 1),
+                                                            lane, pol_x);
+    return delta_range_dot<ValT, VecT, AccT, VS, DB, XL2, SumT>(a, s, e, base, lane, mask, pol_s,
+                                                                pol_x);
+  }
+}
+
 template <typename ValT, typename VecT, typename AccT, int VS, bool VEC, int DB, bool XL2>
 __global__ void __launch_bounds__(kRowThreads) k_rowvec(const RunArgs a) {
   constexpr int GROUPS = kRowThreads / VS;
@@ -191,30 +238,26 @@ __global__ void __launch_bounds__(kRowThreads) k_rowvec(const RunArgs a) {
   const int64_t row = (int64_t)blockIdx.x * GROUPS + threadIdx.x / VS;
   if (row >= a.n_rows) return;  // the whole sub-warp leaves together
   const unsigned mask = group_mask<VS>();
-  const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
-  const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
   uint64_t pol_s = 0, pol_x = 0;
   if constexpr (VEC) pol_s = policy_evict_first();
   if constexpr (XL2) pol_x = policy_evict_last();
   const int s = __ldg(a.rowptr + row), e = __ldg(a.rowptr + row + 1);
-  AccT sum = 0;
-  if constexpr (!VEC) {
-    const int32_t *__restrict__ col = a.colind;
-    for (int j = s + lane; j < e; j += VS)
-      sum += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(col + j), pol_x);
-  } else if constexpr (DB == 0) {
-    sum = vec_range_dot<ValT, VecT, AccT, VS, XL2>(a, s, e, lane, pol_s, pol_x);
-  } else {
-    const int32_t base = __ldg(a.dbase + row);
-    if (base < 0)
-      sum = esc_range_dot<ValT, VecT, AccT, VS, XL2>(a, s, e, a.esc + (-(int64_t)base - 1),
-                                                     lane, pol_x);
-    else
-      sum = delta_range_dot<ValT, VecT, AccT, VS, DB, XL2>(a, s, e, base, lane, mask, pol_s,
-                                                           pol_x);
+  VecT *__restrict__ y = static_cast<VecT *>(a.y);
+  if constexpr (IsF32<AccT>::value) {
+    // FP32 accumulation of a row longer than kF32Run products per lane: FP32 runs, FP64
+    // sums and an FP64 lane reduction (the branch is uniform over the sub-warp)
+    if (e - s > kF32Run * VS) {
+      double d = rowvec_dot<ValT, VecT, AccT, VS, VEC, DB, XL2, double>(a, row, s, e, lane, mask,
+                                                                        pol_s, pol_x);
+      d = group_sum<VS>(d, mask);
+      if (lane == 0) y[row] = (VecT)d;
+      return;
+    }
   }
+  AccT sum = rowvec_dot<ValT, VecT, AccT, VS, VEC, DB, XL2, AccT>(a, row, s, e, lane, mask, pol_s,
+                                                                  pol_x);
   sum = group_sum<VS>(sum, mask);
-  if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)sum;
+  if (lane == 0) y[row] = (VecT)sum;
 }
 
 // ------------------------------------------------------------------------- k_panel ----
@@ -258,30 +301,21 @@ __device__ __forceinline__ uint8_t ld_stream_1(const uint8_t *p, uint64_t pol) {
 }
 
 
-// One pass of the column-panel variant (ML with x larger than the L2). The matrix is held
-// panel-major: panel p holds the nonzeros whose columns fall in the p-th slice of x, as a
-// CSR of its own with the rows in order. Pass p computes every row's sum over panel p, so
-// one pass gathers from one L2-sized slice of x (evict-last) while its panel streams past
-// (evict-first); pass 0 writes y, later passes add to it.
-template <typename ValT, typename VecT, typename AccT, int VS, bool VEC>
-__global__ void __launch_bounds__(kRowThreads) k_panel(const RunArgs a,
-                                                       const int32_t *__restrict__ prow,
-                                                       int add) {
-  constexpr int GROUPS = kRowThreads / VS;
-  const int lane = threadIdx.x & (VS - 1);
-  const int64_t row = (int64_t)blockIdx.x * GROUPS + threadIdx.x / VS;
-  if (row >= a.n_rows) return;  // the whole sub-warp leaves together
-  const unsigned mask = group_mask<VS>();
-  const uint64_t pol_s = policy_evict_first(), pol_x = policy_evict_last();
-  const int s = __ldg(prow + row), e = __ldg(prow + row + 1);
-  AccT sum = 0;
+// One lane's share of a row's nonzeros in one panel (prow gives the panel's row bounds):
+// 128-bit loads (VEC), or four of the lane's nonzeros per step whose columns and values are
+// loaded first (evict-first), then their four x gathers in flight together. With SumT wider
+// than AccT, runs of kF32Run products are summed in AccT and the run sums in SumT.
+template <typename ValT, typename VecT, typename AccT, int VS, bool VEC, typename SumT>
+__device__ __forceinline__ SumT panel_dot(const RunArgs &a, int s, int e, int lane,
+                                          uint64_t pol_s, uint64_t pol_x) {
   if constexpr (VEC) {
-    sum = vec_range_dot<ValT, VecT, AccT, VS, true>(a, s, e, lane, pol_s, pol_x);
+    return vec_range_dot<ValT, VecT, AccT, VS, true, SumT>(a, s, e, lane, pol_s, pol_x);
   } else {
-    // four of the lane's nonzeros per step: their columns and values are loaded first
-    // (evict-first), then their four x gathers are in flight together
     const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
     const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
+    SumT sum = 0;
+    AccT part = 0;
+    int steps = 0;
     for (int j0 = s + lane; j0 < e; j0 += 4 * VS) {
       int c[4];
       ValT v[4];
@@ -296,13 +330,43 @@ __global__ void __launch_bounds__(kRowThreads) k_panel(const RunArgs a,
       for (int q = 0; q < 4; ++q) xv[q] = c[q] >= 0 ? (AccT)ldx<true>(x + c[q], pol_x) : AccT(0);
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (c[q] >= 0) sum += widen<AccT>(v[q]) * xv[q];
+        if (c[q] >= 0) part += widen<AccT>(v[q]) * xv[q];
+      if constexpr (!std::is_same<SumT, AccT>::value) {
+        if (++steps == kF32Run / 4) {
+          sum += (SumT)part;
+          part = 0;
+          steps = 0;
+        }
+      }
     }
+    return sum + (SumT)part;
   }
+}
+
+// One pass of the column-panel variant (ML with x larger than the L2). The matrix is held
+// panel-major: panel p holds the nonzeros whose columns fall in the p-th slice of x, as a
+// CSR of its own with the rows in order. Pass p computes every row's sum over panel p, so
+// one pass gathers from one L2-sized slice of x (evict-last) while its panel streams past
+// (evict-first); pass 0 writes y, later passes add to it. With FP32 accumulation every
+// pass sums runs of kF32Run products in FP64 and rounds once into y, so a row through P
+// passes errs by at most (16 + P) u.
+template <typename ValT, typename VecT, typename AccT, int VS, bool VEC>
+__global__ void __launch_bounds__(kRowThreads) k_panel(const RunArgs a,
+                                                       const int32_t *__restrict__ prow,
+                                                       int add) {
+  constexpr int GROUPS = kRowThreads / VS;
+  using SumT = typename std::conditional<IsF32<AccT>::value, double, AccT>::type;
+  const int lane = threadIdx.x & (VS - 1);
+  const int64_t row = (int64_t)blockIdx.x * GROUPS + threadIdx.x / VS;
+  if (row >= a.n_rows) return;  // the whole sub-warp leaves together
+  const unsigned mask = group_mask<VS>();
+  const uint64_t pol_s = policy_evict_first(), pol_x = policy_evict_last();
+  const int s = __ldg(prow + row), e = __ldg(prow + row + 1);
+  SumT sum = panel_dot<ValT, VecT, AccT, VS, VEC, SumT>(a, s, e, lane, pol_s, pol_x);
   sum = group_sum<VS>(sum, mask);
   if (lane == 0) {
     VecT *y = static_cast<VecT *>(a.y);
-    y[row] = add ? (VecT)((AccT)y[row] + sum) : (VecT)sum;
+    y[row] = add ? (VecT)((SumT)y[row] + sum) : (VecT)sum;
   }
 }
 
@@ -345,6 +409,9 @@ __global__ void __launch_bounds__(kSellThreads, 10) k_sell(const RunArgs a) {
     }
   };
   AccT acc = 0;
+  // FP32 accumulation of a row longer than kF32Chain: each 16-product run's sum moves to FP64
+  double tot = 0.0;
+  const bool fold = IsF32<AccT>::value && len > kF32Chain;
   int k = 0;
   for (; k + 16 <= len; k += 16) {
     AccT xv[16], v[16];
@@ -355,6 +422,12 @@ __global__ void __launch_bounds__(kSellThreads, 10) k_sell(const RunArgs a) {
     }
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc = fma(v[q], xv[q], acc);
+    if constexpr (IsF32<AccT>::value) {
+      if (fold) {
+        tot += (double)acc;
+        acc = 0;
+      }
+    }
   }
   for (; k + 8 <= len; k += 8) {
     AccT xv[8], v[8];
@@ -369,6 +442,9 @@ __global__ void __launch_bounds__(kSellThreads, 10) k_sell(const RunArgs a) {
   for (; k < len; ++k)
     acc = fma(widen<AccT>(ld_stream_1(sv + 32 * (int64_t)k, pol_s)), (AccT)ldx<XL2>(x + column(k), pol_x),
               acc);
+  if constexpr (IsF32<AccT>::value) {
+    if (fold) acc = (AccT)(tot + (double)acc);
+  }
   static_cast<VecT *>(a.y)[row] = (VecT)acc;
 }
 
@@ -653,9 +729,40 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm(const RunArgs a, int off, 
   const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
   const VecT *__restrict__ X = static_cast<const VecT *>(a.x);
   const int s = __ldg(a.rowptr + row), e = __ldg(a.rowptr + row + 1);
+  VecT *__restrict__ Y = static_cast<VecT *>(a.y) + row * ldk + off;
   AccT acc[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) acc[q] = 0;
+  if constexpr (IsF32<AccT>::value) {
+    if (e - s > kF32Run * VS) {
+      // FP32 accumulation of a long row: every lane sums runs of kF32Run products per column
+      // in FP32 and the run sums in FP64; the lane reduction is in FP64 (sub-warp uniform)
+      double tot[K];
+#pragma unroll
+      for (int q = 0; q < K; ++q) tot[q] = 0.0;
+      for (int j0 = s + lane; j0 < e; j0 += kF32Run * VS) {
+        const int j1 = min(e, j0 + kF32Run * VS);
+        for (int j = j0; j < j1; j += VS) {
+          const AccT v = widen<AccT>(val[j]);
+          VecT xr[K];
+          XRow<VecT, K>::load(X + (int64_t)__ldg(a.colind + j) * ldk + off, xr);
+#pragma unroll
+          for (int q = 0; q < K; ++q) acc[q] += v * (AccT)xr[q];
+        }
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+          tot[q] += (double)acc[q];
+          acc[q] = 0;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        const double r = group_sum<VS>(tot[q], mask);
+        if (lane == 0) Y[q] = (VecT)r;
+      }
+      return;
+    }
+  }
   for (int j = s + lane; j < e; j += VS) {
     const AccT v = widen<AccT>(val[j]);
     VecT xr[K];
@@ -663,7 +770,6 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm(const RunArgs a, int off, 
 #pragma unroll
     for (int q = 0; q < K; ++q) acc[q] += v * (AccT)xr[q];
   }
-  VecT *__restrict__ Y = static_cast<VecT *>(a.y) + row * ldk + off;
 #pragma unroll
   for (int q = 0; q < K; ++q) {
     const AccT r = group_sum<VS>(acc[q], mask);
@@ -711,6 +817,15 @@ __global__ void __launch_bounds__(kRowThreads) k_bins_short(const RunArgs a) {
   uint64_t pol_s = policy_evict_first(), pol_x = 0;
   if constexpr (XL2) pol_x = policy_evict_last();
   const int running = DB != 0 ? __ldg(a.dbase + row) : 0;
+  if constexpr (IsF32<AccT>::value) {
+    if (e - s > kF32Run * VS) {   // FP32 runs, FP64 sums (uniform over the sub-warp)
+      double d = bins_range_dot<ValT, VecT, AccT, VS, DB, XL2, double>(a, row, s, e, running,
+                                                                       lane, pol_s, pol_x);
+      d = group_sum<VS>(d, group_mask<VS>());
+      if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)d;
+      return;
+    }
+  }
   AccT sum = bins_range_dot<ValT, VecT, AccT, VS, DB, XL2, AccT>(a, row, s, e, running, lane,
                                                                   pol_s, pol_x);
   sum = group_sum<VS>(sum, group_mask<VS>());

@@ -55,6 +55,9 @@ __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
       return (int)sidx[o + k];
     }
   };
+  // FP32 accumulation of a row longer than kF32Chain: each 16-product run's sum moves to FP64
+  double tot = 0.0;
+  const bool fold = IsF32<AccT>::value && len > kF32Chain;
   int k = 0;
   for (; k + 16 <= len; k += 16) {
     AccT xv[16];
@@ -62,6 +65,12 @@ __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
     for (int q = 0; q < 16; ++q) xv[q] = (AccT)ldx<XL2>(x + column(k + q), pol_x);
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc = fma(widen<AccT>(sval[o + k + q]), xv[q], acc);
+    if constexpr (IsF32<AccT>::value) {
+      if (fold) {
+        tot += (double)acc;
+        acc = 0;
+      }
+    }
   }
   for (; k + 8 <= len; k += 8) {
     AccT xv[8];
@@ -71,7 +80,58 @@ __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
     for (int q = 0; q < 8; ++q) acc = fma(widen<AccT>(sval[o + k + q]), xv[q], acc);
   }
   for (; k < len; ++k) acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2>(x + column(k), pol_x), acc);
+  if constexpr (IsF32<AccT>::value) {
+    if (fold) acc = (AccT)(tot + (double)acc);
+  }
   return acc;
+}
+
+// One lane's share of row r (nonzeros [s, e)) straight from global memory, lanes strided
+// by 32. With SumT wider than AccT each lane sums runs of kF32Run products in AccT and the
+// run sums in SumT.
+template <typename ValT, typename VecT, typename AccT, int DB, bool XL2, typename SumT>
+__device__ __forceinline__ SumT warp_row_dot(const RunArgs &a, int64_t r, int s, int e,
+                                             int lane, const VecT *__restrict__ x,
+                                             uint64_t pol_x) {
+  constexpr bool RUNS = !std::is_same<SumT, AccT>::value;
+  const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
+  SumT sum = 0;
+  AccT part = 0;
+  int steps = 0;
+  auto add = [&](AccT p) {
+    part += p;
+    if constexpr (RUNS) {
+      if (++steps == kF32Run) {
+        sum += (SumT)part;
+        part = 0;
+        steps = 0;
+      }
+    }
+  };
+  if constexpr (DB != 0) {
+    const int32_t base = __ldg(a.dbase + r);
+    if (base < 0) {
+      const int32_t *ec = a.esc + (-(int64_t)base - 1) - s;
+      for (int j = s + lane; j < e; j += 32)
+        add(widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(ec + j), pol_x));
+    } else {
+      // decode the row's deltas: the lane sums its own and its predecessors' deltas
+      using DT = typename IdxOf<DB>::type;
+      const DT *__restrict__ dl = static_cast<const DT *>(a.delta);
+      int run = base;
+      for (int j0 = s; j0 < e; j0 += 32) {
+        const int j = j0 + lane;
+        const int d = j < e ? (int)dl[j] : 0;
+        const int incl = group_incl_scan<32>(d, lane, 0xffffffffu);
+        if (j < e) add(widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + (run + incl), pol_x));
+        run += __shfl_sync(0xffffffffu, incl, 31);
+      }
+    }
+  } else {
+    for (int j = s + lane; j < e; j += 32)
+      add(widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(a.colind + j), pol_x));
+  }
+  return sum + (SumT)part;
 }
 
 // Rows [r0, r1) straight from global memory, a warp per row (tiles larger than the staged
@@ -80,34 +140,18 @@ template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
 __device__ __forceinline__ void tile_direct(const RunArgs &a, int64_t r0, int64_t r1,
                                             const VecT *__restrict__ x, VecT *__restrict__ y,
                                             uint64_t pol_x) {
-  const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t r = r0 + warp; r < r1; r += blockDim.x / 32) {
     const int s = __ldg(a.rowptr + r), e = __ldg(a.rowptr + r + 1);
-    AccT acc = 0;
-    if constexpr (DB != 0) {
-      const int32_t base = __ldg(a.dbase + r);
-      if (base < 0) {
-        const int32_t *ec = a.esc + (-(int64_t)base - 1) - s;
-        for (int j = s + lane; j < e; j += 32)
-          acc += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(ec + j), pol_x);
-      } else {
-        // decode the row's deltas: the lane sums its own and its predecessors' deltas
-        using DT = typename IdxOf<DB>::type;
-        const DT *__restrict__ dl = static_cast<const DT *>(a.delta);
-        int run = base;
-        for (int j0 = s; j0 < e; j0 += 32) {
-          const int j = j0 + lane;
-          const int d = j < e ? (int)dl[j] : 0;
-          const int incl = group_incl_scan<32>(d, lane, 0xffffffffu);
-          if (j < e) acc += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + (run + incl), pol_x);
-          run += __shfl_sync(0xffffffffu, incl, 31);
-        }
+    if constexpr (IsF32<AccT>::value) {
+      if (e - s > kF32Run * 32) {   // long row in FP32: runs summed in FP64 (warp-uniform)
+        double d = warp_row_dot<ValT, VecT, AccT, DB, XL2, double>(a, r, s, e, lane, x, pol_x);
+        d = group_sum<32>(d, 0xffffffffu);
+        if (lane == 0) y[r] = (VecT)d;
+        continue;
       }
-    } else {
-      for (int j = s + lane; j < e; j += 32)
-        acc += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(a.colind + j), pol_x);
     }
+    AccT acc = warp_row_dot<ValT, VecT, AccT, DB, XL2, AccT>(a, r, s, e, lane, x, pol_x);
     acc = group_sum<32>(acc, 0xffffffffu);
     if (lane == 0) y[r] = (VecT)acc;
   }

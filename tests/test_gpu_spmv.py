@@ -130,10 +130,6 @@ PRECISIONS = [("f32", "f64", "f64"), ("f32", "f32", "f64"), ("bf16", "f64", "f64
 @pytest.mark.parametrize("name", ["lap64", "st27_12", "powerlaw", "ragged_empty", "scattered"])
 def test_precisions(api, torch, name, storage, vec, acc):
     m = MATS[name]
-    if acc == "f32" and np.diff(m.rowptr).max() > 27:
-        # FP32 accumulation is only offered against the FP32-storage bound for short rows:
-        # n products and n-1 sums in FP32 stay within (n + 1) 2^-24 <= 2e-6 for n <= 30.
-        pytest.skip("FP32 accumulation on long rows is outside the stated bound")
     A = api.SpmvMatrix.from_csr(m)
     A.set_precision(storage, vec, acc)
     x64 = synth.uniform_vector(m.n_cols, 101)
@@ -181,8 +177,7 @@ def test_spmm(api, torch, name, k):
     X32 = X64.astype(np.float32)
     Y32 = A32.spmm(_dev(torch, X32)).double().cpu().numpy()
     Yr, Sr = oracle.spmm(m.rowptr, m.colind, m.val.astype(np.float32), X32)
-    tau = TAU["f32"] if np.diff(m.rowptr).max() <= 27 else 2e-5
-    check_rows(Y32.ravel(), Yr.ravel(), Sr.ravel(), tau, f"spmm32 {name} k={k}")
+    check_rows(Y32.ravel(), Yr.ravel(), Sr.ravel(), TAU["f32"], f"spmm32 {name} k={k}")
 
 
 @pytest.mark.parametrize("gen", [lambda: synth.stencil_27pt(30),       # one launch
