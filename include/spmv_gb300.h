@@ -70,9 +70,9 @@ typedef struct {
   int32_t partition; /* 0: one sub-warp per row, rows handed to CTAs by the hardware
                         scheduler; 1: merge-path tiles, long rows split across tiles;
                         2: row decomposition (A = A_short + A_long, Fig. 5): rows under
-                        64 nonzeros on sub-warps of vs lanes (2, 4 or 8), rows under
-                        4096 on one warp each, longer rows in 4096-nonzero chunks summed
-                        in FP64 in chunk order. 1 and 2 are the decompositions of
+                        bin_med nonzeros on sub-warps of vs lanes (2, 4 or 8), rows under
+                        bin_chunk on one warp each, longer rows in bin_chunk-nonzero
+                        chunks summed in FP64 in chunk order. 1 and 2 are the decompositions of
                         Section III-E (IMB); the autotuner picks between them;
                         3: sliced rows (SELL-32, a GB300 layout for short rows; see
                         spmv_get_sell): one thread per row over 32-row slices stored
@@ -94,6 +94,11 @@ typedef struct {
   int32_t tile_rows; /* width 1: rows per staged tile, 32 / 64 / 128; 0 = automatic       */
   int32_t tile_pipe; /* width 1: 0 = one tile per CTA, 1 = persistent CTAs keeping the next
                         tile's bulk copy in flight (two shared-memory stages)               */
+  int32_t bin_med;   /* partition 2: rows under bin_med nonzeros go to sub-warps; 0 = 64   */
+  int32_t bin_chunk; /* partition 2: rows under bin_chunk nonzeros take one warp, longer
+                        rows are cut into bin_chunk-nonzero chunks; 0 = 4096. Needs
+                        2 <= bin_med <= bin_chunk <= 2^20. Neither limit is in the paper;
+                        the grid search of Section III-C tunes them with the thresholds  */
 } spmv_variant;
 
 #define SPMV_NUM_FEATURES 14
@@ -113,6 +118,8 @@ typedef struct {
                             matrix outside the selector's training range (margin -1) always
                             falls back to profiling                                       */
   int32_t second_pass;   /* profile: re-profile after the CMP optimization (default 1)   */
+  int32_t bin_med;       /* row decomposition limits of a tuned IMB variant (see          */
+  int32_t bin_chunk;     /* spmv_variant); 0 = the defaults 64 and 4096                    */
 } spmv_tune_opts;
 
 typedef struct {

@@ -41,22 +41,25 @@ class SpmvError(RuntimeError):
 
 class spmv_variant(ctypes.Structure):
     _fields_ = [("partition", _I32), ("index", _I32), ("xpath", _I32), ("vec", _I32),
-                ("vs", _I32), ("tile_rows", _I32), ("tile_pipe", _I32)]
+                ("vs", _I32), ("tile_rows", _I32), ("tile_pipe", _I32), ("bin_med", _I32),
+                ("bin_chunk", _I32)]
 
     def as_tuple(self):
         return (self.partition, self.index, self.xpath, self.vec, self.vs, self.tile_rows,
-                self.tile_pipe)
+                self.tile_pipe, self.bin_med, self.bin_chunk)
 
     def __repr__(self):
         return (f"spmv_variant(partition={self.partition}, index={self.index}, "
                 f"xpath={self.xpath}, vec={self.vec}, vs={self.vs}, "
-                f"tile_rows={self.tile_rows}, tile_pipe={self.tile_pipe})")
+                f"tile_rows={self.tile_rows}, tile_pipe={self.tile_pipe}, "
+                f"bin_med={self.bin_med}, bin_chunk={self.bin_chunk})")
 
 
 class spmv_tune_opts(ctypes.Structure):
     _fields_ = [("t_imb", _D), ("t_ml", _D), ("t_mb", _D), ("long_row_ratio", _D),
                 ("autotune", _I32), ("reps", _I32), ("fixed", spmv_variant),
-                ("selector", _P), ("min_margin", _D), ("second_pass", _I32)]
+                ("selector", _P), ("min_margin", _D), ("second_pass", _I32),
+                ("bin_med", _I32), ("bin_chunk", _I32)]
 
 
 class spmv_tune_report(ctypes.Structure):

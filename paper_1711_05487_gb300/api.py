@@ -42,15 +42,19 @@ def _stream(stream) -> int:
     return int(stream)
 
 
-def variant(partition=0, index=0, xpath=0, vec=0, vs=0, tile_rows=0, tile_pipe=0) -> spmv_variant:
+def variant(partition=0, index=0, xpath=0, vec=0, vs=0, tile_rows=0, tile_pipe=0,
+            bin_med=0, bin_chunk=0) -> spmv_variant:
     """A pool variant (Table II knobs): partition 0 rows, 1 merge-path tiles, 2 row
     decomposition, 3 sliced rows; index 1 delta columns; xpath 1 x evict-last in the L2,
     P >= 2 P column panels; vec vector loads; vs sub-warp width (1: thread per row);
-    tile_rows / tile_pipe the width-1 tile geometry (0: chosen by the library)."""
-    return spmv_variant(partition, index, xpath, vec, vs, tile_rows, tile_pipe)
+    tile_rows / tile_pipe the width-1 tile geometry (0: chosen by the library); bin_med /
+    bin_chunk the row decomposition's limits (0: 64 and 4096)."""
+    return spmv_variant(partition, index, xpath, vec, vs, tile_rows, tile_pipe, bin_med,
+                        bin_chunk)
 
 
-CSR_VECTOR = dict(partition=0, index=0, xpath=0, vec=0, vs=0, tile_rows=0, tile_pipe=0)
+CSR_VECTOR = dict(partition=0, index=0, xpath=0, vec=0, vs=0, tile_rows=0, tile_pipe=0,
+                  bin_med=0, bin_chunk=0)
 
 
 def _as_torch(a, dtype=None) -> torch.Tensor:

@@ -7,15 +7,24 @@
 // ever waits on another), a row-block item is computed by sub-warps of the matrix's width,
 // a chunk of a long row by the whole warp into an FP64 partial slot, and k_batch_fixup adds
 // the chunks of each split row in chunk order, in FP64. Storage and x/y are FP32; the
-// accumulation is FP32 in runs of at most kF32Run products per lane, whose sums add in FP64
-// wherever a lane's chain would be longer, so every row stays within the FP32 bound; X and
-// Y are row-major (n x k).
+// accumulation is FP32, in runs of at most kF32Run products per lane added into FP32 pairs
+// wherever a lane's chain would pass kF32Chain roundings, so every row stays within the
+// FP32 bound; X and Y are row-major (n x k).
 #include "common.cuh"
 
 namespace spmv {
 
 namespace {
 constexpr int kBT = 256;
+}
+
+// True when a lane's FP32 chain over a row of len products spread over `lanes` lanes (its
+// products plus the log2(LANES) levels of the lane reduction) would pass kF32Chain roundings.
+template <int LANES>
+__device__ __forceinline__ bool f32_chain_too_long(int len, int lanes) {
+  constexpr int levels = LANES >= 32 ? 5 : LANES >= 16 ? 4 : LANES >= 8 ? 3 : LANES >= 4 ? 2
+                                                                             : LANES >= 2 ? 1 : 0;
+  return (len + lanes - 1) / lanes + levels > kF32Chain;
 }
 
 template <int K>
@@ -38,26 +47,20 @@ __device__ __forceinline__ void load_xrow(const float *p, float *o) {
 // sub-warp at a time. The U rows' bounds, values, columns and x rows are loaded together
 // before any multiply-add, so U chains of dependent loads are in flight per lane instead of
 // one. Each row's lane sums and their reduction keep the order of a single-row walk.
-// FOLD (rows longer than kF32Run products per lane): every lane's FP32 sums are moved to
-// FP64 after each run of kF32Run products and the lane reduction is in FP64, which keeps a
-// long row within the FP32 bound; short rows stay in FP32 throughout.
+// FOLD (rows whose FP32 chain per lane would pass kF32Chain roundings): every lane adds its
+// FP32 sum into an FP32 pair after each run of kF32Run products and the lane reduction adds
+// the pairs, which keeps a long row within the FP32 bound; short rows stay in plain FP32.
 template <int K, int VS, int U, bool FOLD>
 __device__ __forceinline__ void warp_rows_group(const BatchMat &m, int row0, int r1, int sl,
                                                 unsigned mask, const int (&s)[U],
                                                 const int (&e)[U], int maxlen) {
   constexpr int GROUPS = 32 / VS;
   float acc[U][K];
-  double tot[FOLD ? U : 1][FOLD ? K : 1];
+  FPair tot[FOLD ? U : 1][FOLD ? K : 1];
 #pragma unroll
   for (int u = 0; u < U; ++u)
 #pragma unroll
     for (int q = 0; q < K; ++q) acc[u][q] = 0.0f;
-  if constexpr (FOLD) {
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int q = 0; q < K; ++q) tot[u][q] = 0.0;
-  }
   int steps = 0;
   for (int off = sl; off < maxlen; off += VS) {
     float v[U];
@@ -90,7 +93,7 @@ __device__ __forceinline__ void warp_rows_group(const BatchMat &m, int row0, int
         for (int u = 0; u < U; ++u)
 #pragma unroll
           for (int q = 0; q < K; ++q) {
-            tot[u][q] += (double)acc[u][q];
+            wadd(tot[u][q], acc[u][q]);
             acc[u][q] = 0.0f;
           }
       }
@@ -102,8 +105,12 @@ __device__ __forceinline__ void warp_rows_group(const BatchMat &m, int row0, int
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       float r;
-      if constexpr (FOLD) r = (float)group_sum<VS>(tot[u][q] + (double)acc[u][q], mask);
-      else r = group_sum<VS>(acc[u][q], mask);
+      if constexpr (FOLD) {
+        wadd(tot[u][q], acc[u][q]);
+        r = wvalue(group_sum<VS>(tot[u][q], mask));
+      } else {
+        r = group_sum<VS>(acc[u][q], mask);
+      }
       if (sl == 0 && row < r1) m.Y[(int64_t)row * K + q] = r;
     }
   }
@@ -128,14 +135,20 @@ __device__ void warp_rows(const BatchMat &m, int r0, int r1, int lane) {
       }
       maxlen = max(maxlen, e[u] - s[u]);
     }
-    // uniform over the sub-warp: the U rows' lengths are the same in all its lanes. Rows
-    // long enough to fold have work enough per lane to go one at a time (fewer registers).
-    if (maxlen > kF32Run * VS) {
+    // uniform over the sub-warp (its lanes share the U rows): a lane's FP32 chain is its
+    // products plus the log2(VS) levels of the lane reduction
+    if (f32_chain_too_long<VS>(maxlen, VS)) {
+      if constexpr (K == 1) {
+        warp_rows_group<K, VS, U, true>(m, row0, r1, sl, mask, s, e, maxlen);
+      } else {
+        // wider right-hand sides fold one row at a time (the pairs of U rows would cost
+        // occupancy); such a row has more than kF32Chain / 2 products per lane anyway
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int su[1] = {s[u]}, eu[1] = {e[u]};
-        warp_rows_group<K, VS, 1, true>(m, row0 + u * GROUPS, r1, sl, mask, su, eu,
-                                        e[u] - s[u]);
+        for (int u = 0; u < U; ++u) {
+          const int su[1] = {s[u]}, eu[1] = {e[u]};
+          warp_rows_group<K, VS, 1, true>(m, row0 + u * GROUPS, r1, sl, mask, su, eu,
+                                          e[u] - s[u]);
+        }
       }
     } else {
       warp_rows_group<K, VS, U, false>(m, row0, r1, sl, mask, s, e, maxlen);
@@ -147,14 +160,14 @@ __device__ void warp_rows(const BatchMat &m, int r0, int r1, int lane) {
 // its x row and keeping 4 accumulators, so a sub-warp of VS lanes has VS / 4 nonzeros of its
 // row in flight (two per quad per step) instead of one 64-byte gather per lane. The quads'
 // sums of one row are added with a fixed shuffle tree; the quad of slot 0 writes the row.
-// FOLD (rows of more than kF32Run products per lane): FP32 sums of kF32Run products (eight
-// steps) are moved to FP64 and the quads' sums are added in FP64.
+// FOLD (rows whose FP32 chain per lane would pass kF32Chain roundings): FP32 sums of
+// kF32Run products (eight steps) are added into FP32 pairs, and the quads' pairs are added.
 template <int VS, bool FOLD>
 __device__ __forceinline__ void row_k16(const BatchMat &m, int row, int s, int e, int slot,
                                         int quad, unsigned mask) {
   constexpr int SLOTS = VS / 4;
   float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  double tot[4] = {0.0, 0.0, 0.0, 0.0};
+  FPair tot[4];
   int steps = 0;
   int j = s + slot;
   for (; j + SLOTS < e; j += 2 * SLOTS) {
@@ -171,7 +184,7 @@ __device__ __forceinline__ void row_k16(const BatchMat &m, int row, int s, int e
         steps = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          tot[q] += (double)acc[q];
+          wadd(tot[q], acc[q]);
           acc[q] = 0.0f;
         }
       }
@@ -189,10 +202,16 @@ __device__ __forceinline__ void row_k16(const BatchMat &m, int row, int s, int e
   if constexpr (FOLD) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      double t = tot[q] + (double)acc[q];
+      FPair t = tot[q];
+      wadd(t, acc[q]);
 #pragma unroll
-      for (int off = 4; off < VS; off <<= 1) t += __shfl_xor_sync(mask, t, off, VS);
-      r[q] = (float)t;
+      for (int off = 4; off < VS; off <<= 1) {
+        FPair o;
+        o.hi = __shfl_xor_sync(mask, t.hi, off, VS);
+        o.lo = __shfl_xor_sync(mask, t.lo, off, VS);
+        wadd(t, o);
+      }
+      r[q] = wvalue(t);
     }
   } else {
 #pragma unroll
@@ -215,7 +234,7 @@ __device__ void warp_rows_k16(const BatchMat &m, int r0, int r1, int lane) {
   const unsigned mask = group_mask<VS>();
   for (int row = r0 + lane / VS; row < r1; row += GROUPS) {
     const int s = __ldg(m.rowptr + row), e = __ldg(m.rowptr + row + 1);
-    if (e - s > kF32Run * SLOTS) row_k16<VS, true>(m, row, s, e, slot, quad, mask);
+    if (f32_chain_too_long<SLOTS>(e - s, SLOTS)) row_k16<VS, true>(m, row, s, e, slot, quad, mask);
     else row_k16<VS, false>(m, row, s, e, slot, quad, mask);
   }
 }
@@ -248,15 +267,15 @@ __device__ void warp_rows_vs(const BatchMat &m, int r0, int r1, int lane) {
 }
 
 // Nonzeros [z0, z1) of one long row by one warp: FP32 lane sums of at most kF32Run
-// products at a time, moved to FP64, then a fixed shuffle tree in FP64 into partial slot
-// `chunk` (16 doubles per slot, k used).
+// products at a time, added into FP32 pairs, then (once per lane) a fixed shuffle tree in
+// FP64 into partial slot `chunk` (16 doubles per slot, k used).
 // K = 16: eight slots of a quad each (as in warp_rows_k16); the slots' sums are added in
 // FP64 with a fixed shuffle tree and the quad of slot 0 writes the 16 partials.
 __device__ void warp_chunk_k16(const BatchMat &m, int z0, int z1, int chunk, double *partials,
                                int lane) {
   const int slot = lane >> 2, quad = lane & 3;
   float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  double t[4] = {0.0, 0.0, 0.0, 0.0};
+  FPair w[4];
   int steps = 0;
   int j = z0 + slot;
   for (; j + 8 < z1; j += 16) {
@@ -272,7 +291,7 @@ __device__ void warp_chunk_k16(const BatchMat &m, int z0, int z1, int chunk, dou
       steps = 0;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        t[q] += (double)acc[q];
+        wadd(w[q], acc[q]);
         acc[q] = 0.0f;
       }
     }
@@ -286,8 +305,10 @@ __device__ void warp_chunk_k16(const BatchMat &m, int z0, int z1, int chunk, dou
     acc[3] = fmaf(v0, __uint_as_float(x0.w), acc[3]);
   }
 #pragma unroll
+  double t[4];
   for (int q = 0; q < 4; ++q) {
-    t[q] += (double)acc[q];
+    wadd(w[q], acc[q]);
+    t[q] = wdouble(w[q]);
 #pragma unroll
     for (int off = 4; off < 32; off <<= 1) t[q] += __shfl_xor_sync(0xffffffffu, t[q], off);
   }
@@ -305,12 +326,9 @@ __device__ void warp_chunk(const BatchMat &m, int z0, int z1, int chunk, double 
     return;
   }
   float acc[K];
-  double t[K];
+  FPair w[K];
 #pragma unroll
-  for (int q = 0; q < K; ++q) {
-    acc[q] = 0.0f;
-    t[q] = 0.0;
-  }
+  for (int q = 0; q < K; ++q) acc[q] = 0.0f;
   int steps = 0;
   // two elements per lane per step: both loads issue before the multiply-adds, which then
   // run in element order
@@ -327,7 +345,7 @@ __device__ void warp_chunk(const BatchMat &m, int z0, int z1, int chunk, double 
       steps = 0;
 #pragma unroll
       for (int q = 0; q < K; ++q) {
-        t[q] += (double)acc[q];
+        wadd(w[q], acc[q]);
         acc[q] = 0.0f;
       }
     }
@@ -341,7 +359,8 @@ __device__ void warp_chunk(const BatchMat &m, int z0, int z1, int chunk, double 
   }
 #pragma unroll
   for (int q = 0; q < K; ++q) {
-    const double r = group_sum<32>(t[q] + (double)acc[q], 0xffffffffu);
+    wadd(w[q], acc[q]);
+    const double r = group_sum<32>(wdouble(w[q]), 0xffffffffu);
     if (lane == 0) partials[(int64_t)chunk * 16 + q] = r;
   }
 }

@@ -29,12 +29,46 @@ template <typename AccT> __device__ __forceinline__ AccT widen(__nv_bfloat16 v) 
 // through n roundings errs by at most n u. No FP32 running sum therefore takes more than
 // about 30 roundings (its products, its share of a lane reduction, the final store, and
 // one for values rounded to FP32 from FP64): a row whose chain would be longer is summed
-// in runs of kF32Run products whose FP32 sums are added in FP64 (at most 16 u + the
+// in runs of kF32Run products whose sums are added into an FP32 pair (at most 16 u + the
 // final store).
-constexpr int kF32Run = 16;     // products per FP32 run before its sum moves to FP64
-constexpr int kF32Chain = 30;   // longest row one thread sums in FP32 alone
+constexpr int kF32Run = 16;     // products per FP32 run before its sum is set aside
+constexpr int kF32Chain = 30;   // most roundings one FP32 running sum may take
 template <typename AccT> struct IsF32 { static constexpr bool value = false; };
 template <> struct IsF32<float> { static constexpr bool value = true; };
+
+// The run sums are added into an FP32 pair hi + lo with Knuth's two-sum (the addition
+// hi + a = s + e is exact in FP32, e goes to lo), so their total carries an error of order
+// u^2 and stays on the FP32 pipe (GB300's FP64 pipe runs at 1/64 of its FP32 rate).
+struct FPair {
+  float hi = 0.0f, lo = 0.0f;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+// Wide sums: FPair for FP32 runs, the type itself otherwise.
+__device__ __forceinline__ void wadd(FPair &w, float a) {
+  float s, e;
+  two_sum(w.hi, a, s, e);
+  w.hi = s;
+  w.lo += e;
+}
+__device__ __forceinline__ void wadd(FPair &w, const FPair &o) {
+  float s, e;
+  two_sum(w.hi, o.hi, s, e);
+  w.hi = s;
+  w.lo += o.lo + e;
+}
+__device__ __forceinline__ void wadd(double &w, double a) { w += a; }
+__device__ __forceinline__ void wadd(float &w, float a) { w += a; }
+__device__ __forceinline__ float wvalue(const FPair &w) { return w.hi + w.lo; }
+__device__ __forceinline__ double wvalue(double w) { return w; }
+__device__ __forceinline__ float wvalue(float w) { return w; }
+__device__ __forceinline__ double wdouble(const FPair &w) { return (double)w.hi + (double)w.lo; }
+__device__ __forceinline__ double wdouble(double w) { return w; }
+template <typename AccT> struct WideOf { using type = AccT; };
+template <> struct WideOf<float> { using type = FPair; };
 
 // bf16 held in the low / high half of a 32-bit word -> float (exact)
 __device__ __forceinline__ float bf16lo(uint32_t w) { return __uint_as_float(w << 16); }
@@ -165,6 +199,17 @@ template <int VS> __device__ __forceinline__ unsigned group_mask() {
 template <int VS, typename T> __device__ __forceinline__ T group_sum(T v, unsigned mask) {
 #pragma unroll
   for (int off = VS / 2; off > 0; off >>= 1) v += __shfl_xor_sync(mask, v, off, VS);
+  return v;
+}
+// The same tree over FP32 pairs (both halves shuffled, high parts added by two-sum).
+template <int VS> __device__ __forceinline__ FPair group_sum(FPair v, unsigned mask) {
+#pragma unroll
+  for (int off = VS / 2; off > 0; off >>= 1) {
+    FPair o;
+    o.hi = __shfl_xor_sync(mask, v.hi, off, VS);
+    o.lo = __shfl_xor_sync(mask, v.lo, off, VS);
+    wadd(v, o);
+  }
   return v;
 }
 

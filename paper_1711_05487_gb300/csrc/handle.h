@@ -162,6 +162,7 @@ struct spmv_matrix {
   DevBuf bin_rows, bin_long_rows, bin_long_first, bin_chunks, bin_partials;
   int64_t bin_n_med = 0, bin_n_long = 0, bin_n_chunks = 0;
   int32_t bin_vs_short = 4;
+  int32_t bin_med = spmv::kBinMed, bin_chunk = spmv::kBinChunk;   // limits of the built tables
   bool has_bins = false;
   DevBuf sell_off, sell_val, sell_idx;   // sliced rows: column-major 32-row slices
   int32_t sell_bits = -1;      // column representation of the built slices (0 = int32; -1 none)

@@ -53,7 +53,7 @@ struct RunArgs {
   const void *val_df = nullptr;      // storage SPMV_DF64: double-float value pairs
   // row decomposition (partition 2): rows with length < bin_l_med go to sub-warps of
   // bin_vs_short lanes; medium rows (bin_rows) to a warp each; long rows (bin_long_rows,
-  // length >= kBinChunk) in chunks (row, first, end nonzero, the column a delta decode of
+  // length >= the chunk limit) in chunks (row, first, end nonzero, the column a delta decode of
   // the chunk starts from) whose FP64 partials are added per long row over
   // [bin_long_first[i], bin_long_first[i + 1])
   int32_t bin_l_med = 0, bin_vs_short = 4;
@@ -85,10 +85,12 @@ struct RunArgs {
 // Column panels: at most this many slices of x (variant field xpath = panel count).
 constexpr int kMaxPanels = 16;
 
-// Row decomposition thresholds: rows of at least kBinMed nonzeros get a warp; rows of at
-// least kBinChunk nonzeros are split into chunks of kBinChunk nonzeros.
+// Default row decomposition limits (a variant may set its own): rows of at least kBinMed
+// nonzeros get a warp; rows of at least kBinChunk nonzeros are split into chunks of
+// kBinChunk nonzeros.
 constexpr int kBinMed = 64;
 constexpr int kBinChunk = 4096;
+constexpr int kBinLimitMax = 1 << 20;
 
 // Thread-per-row tile kernel geometry: at most this many rows (= threads) per CTA.
 constexpr int kTileRows = 128;

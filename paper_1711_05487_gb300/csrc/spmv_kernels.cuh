@@ -44,7 +44,7 @@ __device__ __forceinline__ SumT vec_range_dot(const RunArgs &a, int s, int e, in
   const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
   const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
   const int32_t *__restrict__ col = a.colind;
-  SumT sum = 0;
+  SumT sum{};
   AccT part = 0;
   int steps = 0;
   const int a0 = s & ~3;
@@ -73,13 +73,13 @@ __device__ __forceinline__ SumT vec_range_dot(const RunArgs &a, int s, int e, in
         if (j >= s && j < e) part += v[q] * xv[q];
       }
       if (++steps == 4) {
-        sum += (SumT)part;
+        wadd(sum, part);
         part = 0;
         steps = 0;
       }
     }
   }
-  if constexpr (!std::is_same<SumT, AccT>::value) sum += (SumT)part;
+  if constexpr (!std::is_same<SumT, AccT>::value) wadd(sum, part);
   return sum;
 }
 
@@ -90,9 +90,9 @@ __device__ __forceinline__ SumT esc_range_dot(const RunArgs &a, int s, int e,
                                               const int32_t *ec, int lane, uint64_t pol_x) {
   const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
   const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
-  SumT sum = 0;
+  SumT sum{};
   for (int j = s + lane; j < e; j += VS)
-    sum += (SumT)(widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(ec + (j - s)), pol_x));
+    wadd(sum, (AccT)(widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(ec + (j - s)), pol_x)));
   return sum;
 }
 
@@ -124,7 +124,7 @@ __device__ __forceinline__ SumT delta_range_dot(const RunArgs &a, int s, int e, 
                                                 uint64_t pol_x) {
   const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
   const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
-  SumT sum = 0;
+  SumT sum{};
   AccT part = 0;
   const int a0 = s & ~7;
   const int n_it = (e - a0 + VS * 8 - 1) / (VS * 8);
@@ -173,13 +173,13 @@ __device__ __forceinline__ SumT delta_range_dot(const RunArgs &a, int s, int e, 
         if (j >= s && j < e) part += v[q] * xv[q];
       }
       if (it & 1) {           // runs of 16 products (two steps) summed in AccT
-        sum += (SumT)part;
+        wadd(sum, part);
         part = 0;
       }
     }
     running += tot;
   }
-  if constexpr (!std::is_same<SumT, AccT>::value) sum += (SumT)part;
+  if constexpr (!std::is_same<SumT, AccT>::value) wadd(sum, part);
   return sum;
 }
 
@@ -199,13 +199,13 @@ __device__ __forceinline__ SumT strided_dot(const RunArgs &a, int s, int e, int 
       sum += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(col + j), pol_x);
     return sum;
   } else {
-    SumT sum = 0;
+    SumT sum{};
     for (int j0 = s + lane; j0 < e; j0 += kF32Run * VS) {
       const int j1 = min(e, j0 + kF32Run * VS);
       AccT part = 0;
       for (int j = j0; j < j1; j += VS)
         part += widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(col + j), pol_x);
-      sum += (SumT)part;
+      wadd(sum, part);
     }
     return sum;
   }
@@ -244,13 +244,13 @@ __global__ void __launch_bounds__(kRowThreads) k_rowvec(const RunArgs a) {
   const int s = __ldg(a.rowptr + row), e = __ldg(a.rowptr + row + 1);
   VecT *__restrict__ y = static_cast<VecT *>(a.y);
   if constexpr (IsF32<AccT>::value) {
-    // FP32 accumulation of a row longer than kF32Run products per lane: FP32 runs, FP64
-    // sums and an FP64 lane reduction (the branch is uniform over the sub-warp)
+    // FP32 accumulation of a row longer than kF32Run products per lane: FP32 runs added
+    // into FP32 pairs, and a lane reduction over the pairs (uniform over the sub-warp)
     if (e - s > kF32Run * VS) {
-      double d = rowvec_dot<ValT, VecT, AccT, VS, VEC, DB, XL2, double>(a, row, s, e, lane, mask,
-                                                                        pol_s, pol_x);
+      FPair d = rowvec_dot<ValT, VecT, AccT, VS, VEC, DB, XL2, FPair>(a, row, s, e, lane, mask,
+                                                                      pol_s, pol_x);
       d = group_sum<VS>(d, mask);
-      if (lane == 0) y[row] = (VecT)d;
+      if (lane == 0) y[row] = (VecT)wvalue(d);
       return;
     }
   }
@@ -313,7 +313,7 @@ __device__ __forceinline__ SumT panel_dot(const RunArgs &a, int s, int e, int la
   } else {
     const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
     const VecT *__restrict__ x = static_cast<const VecT *>(a.x);
-    SumT sum = 0;
+    SumT sum{};
     AccT part = 0;
     int steps = 0;
     for (int j0 = s + lane; j0 < e; j0 += 4 * VS) {
@@ -333,13 +333,14 @@ __device__ __forceinline__ SumT panel_dot(const RunArgs &a, int s, int e, int la
         if (c[q] >= 0) part += widen<AccT>(v[q]) * xv[q];
       if constexpr (!std::is_same<SumT, AccT>::value) {
         if (++steps == kF32Run / 4) {
-          sum += (SumT)part;
+          wadd(sum, part);
           part = 0;
           steps = 0;
         }
       }
     }
-    return sum + (SumT)part;
+    wadd(sum, part);
+    return sum;
   }
 }
 
@@ -348,14 +349,14 @@ __device__ __forceinline__ SumT panel_dot(const RunArgs &a, int s, int e, int la
 // CSR of its own with the rows in order. Pass p computes every row's sum over panel p, so
 // one pass gathers from one L2-sized slice of x (evict-last) while its panel streams past
 // (evict-first); pass 0 writes y, later passes add to it. With FP32 accumulation every
-// pass sums runs of kF32Run products in FP64 and rounds once into y, so a row through P
-// passes errs by at most (16 + P) u.
+// pass sums runs of kF32Run products into an FP32 pair and rounds once into y, so a row
+// through P passes errs by at most (16 + P) u.
 template <typename ValT, typename VecT, typename AccT, int VS, bool VEC>
 __global__ void __launch_bounds__(kRowThreads) k_panel(const RunArgs a,
                                                        const int32_t *__restrict__ prow,
                                                        int add) {
   constexpr int GROUPS = kRowThreads / VS;
-  using SumT = typename std::conditional<IsF32<AccT>::value, double, AccT>::type;
+  using SumT = typename WideOf<AccT>::type;
   const int lane = threadIdx.x & (VS - 1);
   const int64_t row = (int64_t)blockIdx.x * GROUPS + threadIdx.x / VS;
   if (row >= a.n_rows) return;  // the whole sub-warp leaves together
@@ -366,7 +367,8 @@ __global__ void __launch_bounds__(kRowThreads) k_panel(const RunArgs a,
   sum = group_sum<VS>(sum, mask);
   if (lane == 0) {
     VecT *y = static_cast<VecT *>(a.y);
-    y[row] = add ? (VecT)((SumT)y[row] + sum) : (VecT)sum;
+    if (add) wadd(sum, (AccT)y[row]);
+    y[row] = (VecT)wvalue(sum);
   }
 }
 
@@ -409,8 +411,9 @@ __global__ void __launch_bounds__(kSellThreads, 10) k_sell(const RunArgs a) {
     }
   };
   AccT acc = 0;
-  // FP32 accumulation of a row longer than kF32Chain: each 16-product run's sum moves to FP64
-  double tot = 0.0;
+  // FP32 accumulation of a row longer than kF32Chain: each 16-product run's sum is added
+  // into an FP32 pair
+  FPair tot;
   const bool fold = IsF32<AccT>::value && len > kF32Chain;
   int k = 0;
   for (; k + 16 <= len; k += 16) {
@@ -424,7 +427,7 @@ __global__ void __launch_bounds__(kSellThreads, 10) k_sell(const RunArgs a) {
     for (int q = 0; q < 16; ++q) acc = fma(v[q], xv[q], acc);
     if constexpr (IsF32<AccT>::value) {
       if (fold) {
-        tot += (double)acc;
+        wadd(tot, (float)acc);
         acc = 0;
       }
     }
@@ -443,7 +446,10 @@ __global__ void __launch_bounds__(kSellThreads, 10) k_sell(const RunArgs a) {
     acc = fma(widen<AccT>(ld_stream_1(sv + 32 * (int64_t)k, pol_s)), (AccT)ldx<XL2>(x + column(k), pol_x),
               acc);
   if constexpr (IsF32<AccT>::value) {
-    if (fold) acc = (AccT)(tot + (double)acc);
+    if (fold) {
+      wadd(tot, (float)acc);
+      acc = (AccT)wvalue(tot);
+    }
   }
   static_cast<VecT *>(a.y)[row] = (VecT)acc;
 }
@@ -736,10 +742,8 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm(const RunArgs a, int off, 
   if constexpr (IsF32<AccT>::value) {
     if (e - s > kF32Run * VS) {
       // FP32 accumulation of a long row: every lane sums runs of kF32Run products per column
-      // in FP32 and the run sums in FP64; the lane reduction is in FP64 (sub-warp uniform)
-      double tot[K];
-#pragma unroll
-      for (int q = 0; q < K; ++q) tot[q] = 0.0;
+      // in FP32 and adds the run sums into FP32 pairs, reduced over the lanes as pairs
+      FPair tot[K];
       for (int j0 = s + lane; j0 < e; j0 += kF32Run * VS) {
         const int j1 = min(e, j0 + kF32Run * VS);
         for (int j = j0; j < j1; j += VS) {
@@ -751,14 +755,14 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm(const RunArgs a, int off, 
         }
 #pragma unroll
         for (int q = 0; q < K; ++q) {
-          tot[q] += (double)acc[q];
+          wadd(tot[q], (float)acc[q]);
           acc[q] = 0;
         }
       }
 #pragma unroll
       for (int q = 0; q < K; ++q) {
-        const double r = group_sum<VS>(tot[q], mask);
-        if (lane == 0) Y[q] = (VecT)r;
+        const FPair r = group_sum<VS>(tot[q], mask);
+        if (lane == 0) Y[q] = (VecT)wvalue(r);
       }
       return;
     }
@@ -783,8 +787,8 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm(const RunArgs a, int off, 
 //                  (longer rows are skipped: the sub-warp reads their bounds only);
 //  k_bins_warp   - one warp per work item: a medium row (l_med <= length < kBinChunk, from
 //                  the row list) written directly, or a chunk of at most kBinChunk nonzeros
-//                  of a long row whose sum goes to an FP64 partial slot; the lanes add
-//                  runs of 16 products in FP64 (FP32 accumulation stays within 16);
+//                  of a long row whose sum goes to an FP64 partial slot; with FP32
+//                  accumulation the lanes add runs of 16 products into FP32 pairs;
 //  k_bins_fixup  - each long row's partials added in chunk order (reproducible, no atomics).
 // One sub-warp's share of elements [s, e) of row `row`, whose decode (delta columns of DB
 // bits) starts from column `running`.
@@ -818,11 +822,11 @@ __global__ void __launch_bounds__(kRowThreads) k_bins_short(const RunArgs a) {
   if constexpr (XL2) pol_x = policy_evict_last();
   const int running = DB != 0 ? __ldg(a.dbase + row) : 0;
   if constexpr (IsF32<AccT>::value) {
-    if (e - s > kF32Run * VS) {   // FP32 runs, FP64 sums (uniform over the sub-warp)
-      double d = bins_range_dot<ValT, VecT, AccT, VS, DB, XL2, double>(a, row, s, e, running,
-                                                                       lane, pol_s, pol_x);
+    if (e - s > kF32Run * VS) {   // FP32 runs summed in pairs (uniform over the sub-warp)
+      FPair d = bins_range_dot<ValT, VecT, AccT, VS, DB, XL2, FPair>(a, row, s, e, running,
+                                                                     lane, pol_s, pol_x);
       d = group_sum<VS>(d, group_mask<VS>());
-      if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)d;
+      if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)wvalue(d);
       return;
     }
   }
@@ -834,6 +838,7 @@ __global__ void __launch_bounds__(kRowThreads) k_bins_short(const RunArgs a) {
 
 template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
 __global__ void __launch_bounds__(kRowThreads) k_bins_warp(const RunArgs a) {
+  using WS = typename WideOf<AccT>::type;   // FP32 runs are summed in FP32 pairs
   const int lane = threadIdx.x & 31;
   const int64_t item = ((int64_t)blockIdx.x * kRowThreads + threadIdx.x) / 32;
   if (item >= a.bin_n_med + a.bin_n_chunks) return;
@@ -842,18 +847,18 @@ __global__ void __launch_bounds__(kRowThreads) k_bins_warp(const RunArgs a) {
   if (item < a.bin_n_chunks) {
     // (row, first nonzero, end nonzero, the column the delta decode starts from)
     const int4 c = a.bin_chunks[item];
-    const double sum = bins_range_dot<ValT, VecT, AccT, 32, DB, XL2, double>(
-        a, c.x, c.y, c.z, c.w, lane, pol_s, pol_x);
-    const double t = group_sum<32>(sum, 0xffffffffu);
-    if (lane == 0) a.bin_partials[item] = t;
+    const WS sum = bins_range_dot<ValT, VecT, AccT, 32, DB, XL2, WS>(a, c.x, c.y, c.z, c.w,
+                                                                    lane, pol_s, pol_x);
+    const WS t = group_sum<32>(sum, 0xffffffffu);
+    if (lane == 0) a.bin_partials[item] = wdouble(t);
   } else {
     const int row = __ldg(a.bin_rows + (item - a.bin_n_chunks));
     const int s = __ldg(a.rowptr + row), e = __ldg(a.rowptr + row + 1);
     const int running = DB != 0 ? __ldg(a.dbase + row) : 0;
-    double sum = bins_range_dot<ValT, VecT, AccT, 32, DB, XL2, double>(a, row, s, e, running,
-                                                                        lane, pol_s, pol_x);
+    WS sum = bins_range_dot<ValT, VecT, AccT, 32, DB, XL2, WS>(a, row, s, e, running, lane,
+                                                              pol_s, pol_x);
     sum = group_sum<32>(sum, 0xffffffffu);
-    if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)sum;
+    if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)wvalue(sum);
   }
 }
 

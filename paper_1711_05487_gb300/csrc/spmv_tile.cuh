@@ -55,8 +55,9 @@ __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
       return (int)sidx[o + k];
     }
   };
-  // FP32 accumulation of a row longer than kF32Chain: each 16-product run's sum moves to FP64
-  double tot = 0.0;
+  // FP32 accumulation of a row longer than kF32Chain: each 16-product run's sum is added
+  // into an FP32 pair
+  FPair tot;
   const bool fold = IsF32<AccT>::value && len > kF32Chain;
   int k = 0;
   for (; k + 16 <= len; k += 16) {
@@ -67,7 +68,7 @@ __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
     for (int q = 0; q < 16; ++q) acc = fma(widen<AccT>(sval[o + k + q]), xv[q], acc);
     if constexpr (IsF32<AccT>::value) {
       if (fold) {
-        tot += (double)acc;
+        wadd(tot, (float)acc);
         acc = 0;
       }
     }
@@ -81,28 +82,31 @@ __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
   }
   for (; k < len; ++k) acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2>(x + column(k), pol_x), acc);
   if constexpr (IsF32<AccT>::value) {
-    if (fold) acc = (AccT)(tot + (double)acc);
+    if (fold) {
+      wadd(tot, (float)acc);
+      acc = (AccT)wvalue(tot);
+    }
   }
   return acc;
 }
 
 // One lane's share of row r (nonzeros [s, e)) straight from global memory, lanes strided
-// by 32. With SumT wider than AccT each lane sums runs of kF32Run products in AccT and the
-// run sums in SumT.
+// by 32. With SumT wider than AccT (FP32 pairs) each lane sums runs of kF32Run products in
+// AccT and adds the run sums into SumT.
 template <typename ValT, typename VecT, typename AccT, int DB, bool XL2, typename SumT>
 __device__ __forceinline__ SumT warp_row_dot(const RunArgs &a, int64_t r, int s, int e,
                                              int lane, const VecT *__restrict__ x,
                                              uint64_t pol_x) {
   constexpr bool RUNS = !std::is_same<SumT, AccT>::value;
   const ValT *__restrict__ val = static_cast<const ValT *>(a.val);
-  SumT sum = 0;
+  SumT sum{};
   AccT part = 0;
   int steps = 0;
   auto add = [&](AccT p) {
     part += p;
     if constexpr (RUNS) {
       if (++steps == kF32Run) {
-        sum += (SumT)part;
+        wadd(sum, part);
         part = 0;
         steps = 0;
       }
@@ -131,7 +135,8 @@ __device__ __forceinline__ SumT warp_row_dot(const RunArgs &a, int64_t r, int s,
     for (int j = s + lane; j < e; j += 32)
       add(widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(a.colind + j), pol_x));
   }
-  return sum + (SumT)part;
+  wadd(sum, part);
+  return sum;
 }
 
 // Rows [r0, r1) straight from global memory, a warp per row (tiles larger than the staged
@@ -144,10 +149,10 @@ __device__ __forceinline__ void tile_direct(const RunArgs &a, int64_t r0, int64_
   for (int64_t r = r0 + warp; r < r1; r += blockDim.x / 32) {
     const int s = __ldg(a.rowptr + r), e = __ldg(a.rowptr + r + 1);
     if constexpr (IsF32<AccT>::value) {
-      if (e - s > kF32Run * 32) {   // long row in FP32: runs summed in FP64 (warp-uniform)
-        double d = warp_row_dot<ValT, VecT, AccT, DB, XL2, double>(a, r, s, e, lane, x, pol_x);
+      if (e - s > kF32Run * 32) {   // long row in FP32: runs summed in pairs (warp-uniform)
+        FPair d = warp_row_dot<ValT, VecT, AccT, DB, XL2, FPair>(a, r, s, e, lane, x, pol_x);
         d = group_sum<32>(d, 0xffffffffu);
-        if (lane == 0) y[r] = (VecT)d;
+        if (lane == 0) y[r] = (VecT)wvalue(d);
         continue;
       }
     }

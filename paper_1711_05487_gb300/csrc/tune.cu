@@ -461,7 +461,8 @@ void sweep_panels(spmv_matrix *h, spmv_variant &v, float best, const void *x, vo
 // the sub-warp width and, for width 1, the tile geometry are always swept; then sliced rows
 // (short rows, little padding) and, for ML matrices whose x exceeds half the L2, column
 // panels (sweep_panels) compete with the winner.
-void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, cudaStream_t s) {
+void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, int32_t bin_med, int32_t bin_chunk,
+                 cudaStream_t s) {
   if (h->n_rows == 0) return;
   const size_t vb = dtype_bytes(h->vec);
   DevBuf x, y;
@@ -478,6 +479,8 @@ void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, cudaStream_t s) {
       spmv_variant t = v;
       t.partition = c[0];
       t.vs = c[1];
+      t.bin_med = bin_med;
+      t.bin_chunk = bin_chunk;
       prepare_variant(h, t, s);
       const float ms = time_launches([&]() { return launch_run(h, t, x.p, y.p, s); }, reps, s);
       if (ms < best_t) {
@@ -578,6 +581,12 @@ spmv_status spmv_tune(spmv_handle_t h, spmv_mode mode, const spmv_tune_opts *opt
   if (mode == SPMV_TUNE_LEARNED && !opts.selector) return SPMV_ERR_NO_SELECTOR;
   if (mode < SPMV_TUNE_PROFILE || mode > SPMV_TUNE_FIXED) return SPMV_ERR_ARG;
   if (mode == SPMV_TUNE_FIXED && !valid_variant(opts.fixed)) return SPMV_ERR_ARG;
+  {
+    spmv_variant lim{};
+    lim.bin_med = opts.bin_med;
+    lim.bin_chunk = opts.bin_chunk;
+    if (!valid_variant(lim)) return SPMV_ERR_ARG;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   spmv_tune_report rep;
   std::memset(&rep, 0, sizeof rep);
@@ -640,12 +649,15 @@ spmv_status spmv_tune(spmv_handle_t h, spmv_mode mode, const spmv_tune_opts *opt
         }
       }
       v = variant_for_classes(cls, h->nnz_avg(), nnz_max, opts.long_row_ratio);
+      v.bin_med = opts.bin_med;
+      v.bin_chunk = opts.bin_chunk;
     }
     const double t1 = now_ms();
     prepare_variant(h, v, s);
     CK(cudaStreamSynchronize(s));
     const double t2 = now_ms();
-    if (opts.autotune && mode != SPMV_TUNE_FIXED) autotune_vs(h, v, std::max(3, opts.reps / 2), s);
+    if (opts.autotune && mode != SPMV_TUNE_FIXED)
+      autotune_vs(h, v, std::max(3, opts.reps / 2), opts.bin_med, opts.bin_chunk, s);
     CK(cudaStreamSynchronize(s));
     const double t3 = now_ms();
     h->variant = v;

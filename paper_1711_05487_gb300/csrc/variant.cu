@@ -34,7 +34,7 @@ RunArgs run_args(const spmv_matrix *h, const void *x, void *y) {
   a.tile_pipe = h->tile_pipe;
   a.err = h->d_err.as<int32_t>();
   a.val_df = h->val_df.p;
-  a.bin_l_med = kBinMed;
+  a.bin_l_med = h->bin_med;
   a.bin_vs_short = h->bin_vs_short;
   a.bin_rows = h->bin_rows.as<int32_t>();
   a.bin_n_med = h->bin_n_med;
@@ -113,13 +113,17 @@ void build_merge(spmv_matrix *h, cudaStream_t s) {
 
 // Row decomposition tables (partition 2): three exclusive scans over per-row counts place
 // each medium row in the row list and each long row's chunks in the chunk table.
-void build_bins(spmv_matrix *h, cudaStream_t s) {
-  if (h->has_bins) return;
+void build_bins(spmv_matrix *h, int32_t l_med, int32_t chunk, cudaStream_t s) {
+  if (h->has_bins && h->bin_med == l_med && h->bin_chunk == chunk) return;
+  h->has_bins = false;
+  for (DevBuf *b : {&h->bin_rows, &h->bin_long_rows, &h->bin_long_first, &h->bin_chunks,
+                    &h->bin_partials})
+    b->release();
   const int64_t n = h->n_rows;
   DevBuf cnt;
   cnt.alloc(sizeof(int64_t) * 3 * (size_t)(n + 1), 8, s, true);
   int64_t *med = cnt.as<int64_t>(), *lng = med + (n + 1), *nch = lng + (n + 1);
-  CK(launch_bin_counts(n, h->rowptr.as<int32_t>(), kBinMed, kBinChunk, med, lng, nch, s));
+  CK(launch_bin_counts(n, h->rowptr.as<int32_t>(), l_med, chunk, med, lng, nch, s));
   const int64_t se = scan_scratch_elems(n);
   DevBuf scr;
   scr.alloc(sizeof(int64_t) * (size_t)se, 8, s);
@@ -136,7 +140,7 @@ void build_bins(spmv_matrix *h, cudaStream_t s) {
   h->bin_partials.alloc(8 * (size_t)std::max<int64_t>(tot[2], 1), 8, s);
   const int32_t last = (int32_t)tot[2];
   CK(cudaMemcpyAsync(h->bin_long_first.as<int32_t>() + tot[1], &last, 4, cudaMemcpyHostToDevice, s));
-  CK(launch_bin_fill(n, h->rowptr.as<int32_t>(), h->colind.as<int32_t>(), kBinMed, kBinChunk,
+  CK(launch_bin_fill(n, h->rowptr.as<int32_t>(), h->colind.as<int32_t>(), l_med, chunk,
                      med, lng, nch,
                      h->bin_rows.as<int32_t>(), h->bin_long_rows.as<int32_t>(),
                      h->bin_long_first.as<int32_t>(), h->bin_chunks.as<int4>(), s));
@@ -144,6 +148,8 @@ void build_bins(spmv_matrix *h, cudaStream_t s) {
   h->bin_n_med = tot[0];
   h->bin_n_long = tot[1];
   h->bin_n_chunks = tot[2];
+  h->bin_med = l_med;
+  h->bin_chunk = chunk;
   h->has_bins = true;
 }
 
@@ -292,6 +298,10 @@ void drop_panels(spmv_matrix *h) {
 }
 
 void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
+  if (v.partition != 2 || v.xpath >= 2) {   // the limits belong to the row decomposition
+    v.bin_med = 0;
+    v.bin_chunk = 0;
+  }
   if (v.xpath >= 2) {
     // column panels: rows on sub-warps of vs lanes over each panel's CSR, int32 columns
     v.partition = 0;
@@ -322,7 +332,9 @@ void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
     v.tile_rows = 0;
     v.tile_pipe = 0;
     h->bin_vs_short = v.vs;
-    build_bins(h, s);
+    if (v.bin_med == 0) v.bin_med = kBinMed;
+    if (v.bin_chunk == 0) v.bin_chunk = kBinChunk;
+    build_bins(h, v.bin_med, v.bin_chunk, s);
   } else {
     if (v.index == 1) {
       v.vec = 1;
@@ -364,6 +376,9 @@ bool valid_variant(const spmv_variant &v) {
   if (v.tile_rows != 0 && v.tile_rows != 32 && v.tile_rows != 64 && v.tile_rows != 128)
     return false;
   if (v.tile_pipe != 0 && v.tile_pipe != 1) return false;
+  const int32_t med = v.bin_med ? v.bin_med : kBinMed, chunk = v.bin_chunk ? v.bin_chunk : kBinChunk;
+  if (v.bin_med < 0 || v.bin_chunk < 0 || med < 2 || med > chunk || chunk > kBinLimitMax)
+    return false;
   return true;
 }
 

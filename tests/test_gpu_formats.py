@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_util import stored_values, torch_cuda
+from gpu_util import TAU, check_spmv, stored_values, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -130,6 +130,39 @@ def test_row_bins_bit_exact(api, torch):
         om, ol, of, oc = oracle.row_bins(m.rowptr, m.colind, l_med=64, chunk=4096)
         assert np.array_equal(med, om) and np.array_equal(lng, ol)
         assert np.array_equal(first, of) and np.array_equal(ch, oc)
+
+
+@pytest.mark.parametrize("l_med,chunk", [(2, 2), (32, 2048), (128, 8192), (64, 300),
+                                         (1000, 1000)])
+def test_row_bins_at_other_limits(api, torch, l_med, chunk):
+    """A variant's own row decomposition limits: the tables equal the oracle's at those
+    limits bit for bit (rebuilt when the limits change), and the SpMV stays within the FP64
+    bound (FP32 too, for FP32 storage)."""
+    m = synth.power_law(30_000, alpha=1.5, clip=30_000, seed=20, dtype=np.float64)
+    x64 = synth.uniform_vector(m.n_cols, 21)
+    A = api.SpmvMatrix.from_csr(m)
+    for index in (0, 1):
+        A.set_variant(partition=2, index=index, bin_med=l_med, bin_chunk=chunk)
+        med, lng, first, ch = (t.cpu().numpy() for t in A.row_bins())
+        om, ol, of, oc = oracle.row_bins(m.rowptr, m.colind, l_med=l_med, chunk=chunk)
+        assert np.array_equal(med, om) and np.array_equal(lng, ol)
+        assert np.array_equal(first, of) and np.array_equal(ch, oc)
+        y = A.run(torch.from_numpy(x64).cuda()).cpu().numpy()
+        check_spmv(m, x64, y, TAU["f64"], f"bins {l_med}/{chunk} index {index}")
+    A32 = api.SpmvMatrix.from_csr(m.astype(np.float32))
+    A32.set_variant(partition=2, bin_med=l_med, bin_chunk=chunk)
+    x32 = x64.astype(np.float32)
+    y = A32.run(torch.from_numpy(x32).cuda()).double().cpu().numpy()
+    check_spmv(m.astype(np.float32), x32.astype(np.float64), y, TAU["f32"],
+               f"bins f32 {l_med}/{chunk}")
+
+
+def test_row_bin_limits_rejected(api):
+    from paper_1711_05487_gb300._abi import SpmvError
+    A = api.SpmvMatrix.from_csr(synth.laplacian_2d(20))
+    for med, chunk in ((1, 0), (100, 50), (0, 1 << 21), (-3, 0)):
+        with pytest.raises(SpmvError):
+            A.set_variant(partition=2, bin_med=med, bin_chunk=chunk)
 
 
 @pytest.mark.parametrize("n_panels", [2, 3, 7, 16])
