@@ -314,6 +314,7 @@ def run_ours(args, rank, world):
                 # route profiled it instead
                 amort[route]["decided_by"] = ("mlp" if r_l.mode_used == 2 else "profile")
                 amort[route]["margin"] = round(r_l.margin, 4)
+                amort[route]["t_learned_over_t_profile"] = round(t_l / ms, 4)
         # Section IV-D's trivial optimizers: try every single optimization (5) or also every
         # pair of them (15 in all), 64 timed SpMVs each, keep the fastest; t_pre is the whole
         # search including each candidate's preprocessing
@@ -399,6 +400,7 @@ def run_ours(args, rank, world):
         "speedup_vs_csr_vector": round(base_ms / ms, 3),
         "paper_protocol": protocol,
         "tune": {"classes": rep.class_names, "variant": list(rep.variant),
+                 "classes_fig3_one_pass": fig3_one_pass(rep.p) if rep.p["P_CSR"] > 0 else None,
                  "p_gflops": {k: round(v, 1) for k, v in rep.p.items()},
                  "b_max_gbs": round(rep.b_max_gbs, 1), "t_pre_ms": round(rep.t_pre_ms, 2)},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
@@ -450,11 +452,14 @@ def run_batched(args, rank, world):
     flops = 0.0
     nbytes = 0
     t_tune = 0.0
+    by_mlp = 0
     for sp, m in zip(specs, mats):
         A = api.SpmvMatrix.from_csr(m, stream=stream)
         A.set_precision("f32", "f32", "f32", stream=stream)
         if sel is not None:
-            t_tune += A.tune("learned", stream=stream, selector=sel).t_pre_ms
+            r = A.tune("learned", stream=stream, selector=sel)
+            t_tune += r.t_pre_ms
+            by_mlp += r.mode_used == 2
         else:
             A.set_variant(stream=stream)
         k = sp["k"]
@@ -503,6 +508,22 @@ def run_batched(args, rank, world):
     clocks.stop()
     achieved = nbytes / (ms * 1e-3) / 1e9
     total_nnz = sum(m.nnz for m in mats)
+    learned = None
+    if sel is not None:
+        # the same batch with every matrix tuned by the profile route instead (the learned
+        # route's judge), at the same work plan
+        t_prof = 0.0
+        for A in As:
+            t_prof += A.tune("profile", stream=stream).t_pre_ms
+        B.close()
+        B = api.Batch(As, Xs, Ys, ks, stream=stream)
+        B.set_plan(*plan)
+        ms_p = timed(B.run, args.steps, args.warmup, "batched_profile_route")
+        learned = {"decided_by_mlp": int(by_mlp), "matrices": len(As),
+                   "t_pre_ms_total": round(t_tune, 1),
+                   "profile_route": {"gflops": round(flops / (ms_p * 1e-3) / 1e9, 2),
+                                     "ms": round(ms_p, 5), "t_pre_ms_total": round(t_prof, 1)},
+                   "t_learned_over_t_profile": round(ms / ms_p, 4)}
     out = {
         "metric": "batched SpMV/SpMM GFLOP/s (sum of 2*nnz*k / t), one persistent launch",
         "value": round(whole_job_rate(flops, ms, world), 2), "unit": "GFLOP/s",
@@ -525,9 +546,110 @@ def run_batched(args, rank, world):
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
                      "peak_kind": peak_kind, "alg_bytes": nbytes},
         "gpu_launches": args.steps * 2,
+        "learned": learned,
         "clocks": clocks.summary(),
         "gen_s": round(gen_s, 1),
     }
+    B.close()
+    return out
+
+
+# The other full-size workloads of the method, measured in the same run as the headline so
+# that one line carries them all: each matrix is generated, tuned by the profile route and
+# timed like the headline, then tuned again by the learned route and timed.
+OTHER_WORKLOADS = ("powerlaw_4m", "scattered_16m", "batched_512")
+CLASS_NAMES = ("MB", "ML", "IMB", "CMP")
+
+
+def _names(mask):
+    return [n for b, n in enumerate(CLASS_NAMES) if mask >> b & 1]
+
+
+def time_spmv(A, x, y, stream, K, W, world):
+    """Milliseconds per SpMV over K back-to-back runs between CUDA events on `stream`, after W
+    untimed ones (the slowest rank's time)."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(W):
+            A.run(x, y, stream=stream)
+        stream.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            A.run(x, y, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+    return max_over_ranks(e0.elapsed_time(e1), world) / K
+
+
+def fig3_one_pass(p: dict) -> list:
+    """The class set of Fig. 3's rules on the first profiling pass alone (the paper's
+    classifier), beside the two-pass set the profile route installs."""
+    from paper_1711_05487_gb300 import _abi
+    v = np.array([p[k] for k in ("P_CSR", "P_MB", "P_ML", "P_IMB", "P_CMP", "P_peak")])
+    return _names(_abi.spmv_classify(v.ctypes.data))
+
+
+def workload_summary(name, args, world, peak, sel):
+    """One of the other full-size workloads: GFLOP/s, variant and classes of the profile
+    route, algorithmic bytes and HBM roofline fraction, and the learned route beside it."""
+    import torch
+
+    from paper_1711_05487_gb300 import api
+    if name == "batched_512":
+        b = run_batched(args, 0, world)
+        return {"desc": "512 mixed FP32 matrices, N log-uniform in [1e3, 2e5], k in {1, 4, 16}",
+                "gflops": b["value"], "ms_per_step": b["ms_per_step"],
+                "alg_bytes": b["roofline"]["alg_bytes"], "roofline_frac": b["roofline"]["frac"],
+                "total_nnz": b["config"]["total_nnz"], "k_hist": b["config"]["k_hist"],
+                "sequential_launches": b["sequential_launches"],
+                "speedup_vs_sequential": b["speedup_vs_sequential"], "plan": b["tune"]["plan"],
+                "learned": b["learned"], "gpu_launches": b["gpu_launches"],
+                "clocks": b["clocks"], "gen_s": b["gen_s"]}
+    wl = WORKLOADS[name]
+    t0 = time.time()
+    m = wl["make"]()
+    gen_s = time.time() - t0
+    stream = torch.cuda.Stream()
+    A = api.SpmvMatrix.from_csr(m, stream=stream)
+    vec_t = torch.float64 if m.val.dtype == np.float64 else torch.float32
+    if m.val.dtype != np.float64:
+        A.set_precision("f32", "f32", "f32", stream=stream)
+    x = torch.from_numpy(synth.uniform_vector(m.n_cols, wl["x_seed"])).to(vec_t).cuda()
+    y = torch.empty(m.n_rows, dtype=vec_t, device="cuda")
+    flops = 2.0 * m.nnz
+    A.set_variant(stream=stream)
+    base_ms = time_spmv(A, x, y, stream, args.steps, args.warmup, world)
+    rep = A.tune("profile", stream=stream)
+    ms = time_spmv(A, x, y, stream, args.steps, args.warmup, world)
+    ab = alg_bytes(m.n_rows, m.n_cols, m.nnz, rep.variant, A.storage, A.vec, A.handle)
+    out = {"desc": wl["desc"], "n_rows": m.n_rows, "nnz": m.nnz,
+           "dtype": {0: "f64", 1: "f32", 2: "bf16", 3: "df64"}[A.storage],
+           "gflops": round(flops / (ms * 1e-3) / 1e9, 2), "ms_per_step": round(ms, 5),
+           "variant": list(rep.variant), "classes": rep.class_names,
+           "classes_fig3_one_pass": fig3_one_pass(rep.p), "t_pre_ms": round(rep.t_pre_ms, 2),
+           "alg_bytes": ab, "achieved_gbs": round(ab / (ms * 1e-3) / 1e9, 1),
+           "roofline_frac": round(ab / (ms * 1e-3) / 1e9 / peak, 4),
+           "csr_vector": {"gflops": round(flops / (base_ms * 1e-3) / 1e9, 2),
+                          "ms": round(base_ms, 5)},
+           "speedup_vs_csr_vector": round(base_ms / ms, 3),
+           "gpu_launches": args.steps * launches_per_spmv(A, rep.variant),
+           "gen_s": round(gen_s, 1)}
+    if sel is not None:
+        r_l = A.tune("learned", stream=stream, selector=sel)
+        t_l = time_spmv(A, x, y, stream, args.steps, args.warmup, world)
+        out["learned"] = {"decided_by": "mlp" if r_l.mode_used == 2 else "profile",
+                          "margin": round(r_l.margin, 4), "classes": r_l.class_names,
+                          "variant": list(r_l.variant), "t_pre_ms": round(r_l.t_pre_ms, 2),
+                          "gflops": round(flops / (t_l * 1e-3) / 1e9, 2),
+                          "ms_per_step": round(t_l, 5),
+                          "t_learned_over_t_profile": round(t_l / ms, 4)}
+    A.close()
+    del x, y
+    torch.cuda.synchronize()
     return out
 
 
@@ -836,10 +958,18 @@ def main():
             print(json.dumps(out), flush=True)
         return
     out, m = run_ours(args, rank, world)
+    if rank == 0 and not args.no_cpu_baseline and world == 1:   # the oracle: N = 1 only
+        wl = WORKLOADS[args.workload]
+        out["cpu_baseline"] = cpu_baseline(m, synth.uniform_vector(m.n_cols, wl["x_seed"]))
+    del m
+    if args.workload == "stencil27_160" and not args.quick and not args.fixed_variant:
+        from paper_1711_05487_gb300 import api
+        sel_path = os.path.join(ROOT, "paper_1711_05487_gb300", "data", "selector_gb300.npz")
+        sel = api.Selector.load(sel_path) if os.path.exists(sel_path) else None
+        peak, _ = _peaks()
+        out["workloads"] = {name: workload_summary(name, args, world, peak, sel)
+                            for name in OTHER_WORKLOADS}
     if rank == 0:
-        if not args.no_cpu_baseline and world == 1:      # the oracle baseline: N = 1 only
-            wl = WORKLOADS[args.workload]
-            out["cpu_baseline"] = cpu_baseline(m, synth.uniform_vector(m.n_cols, wl["x_seed"]))
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -1,11 +1,17 @@
 """Calibration of the profile route's thresholds on the target GPU.
 
 The paper sets T_ML and T_IMB by an exhaustive grid search that maximizes the average
-performance gain of the optimizations selected on a large matrix set (Section III-C). With
-the per-matrix P-vectors (both profiling passes) and the measured time of every candidate
-variant, each threshold triple (T_IMB, T_ML, T_MB) is scored by classifying every matrix with
-the library's own classifier (spmv_classify2), mapping the class set to its variant (Table
-II) and averaging t(plain CSR-vector) / t(selected variant).
+performance gain of the optimizations selected on a large matrix set (Section III-C). This
+module runs that search over six constants: the three thresholds of Fig. 3 (T_IMB, T_ML and
+T_MB, the reading of "P_CSR close to P_MB"), the uneven-rows ratio that sends an IMB matrix
+to the matrix decomposition (nnz_max > ratio * nnz_avg, Section III-E), and the two limits
+of the row decomposition (rows under l_med nonzeros on sub-warps, rows of at least `chunk`
+nonzeros cut into chunks). With the per-matrix P-vectors (both profiling passes) and the
+measured time of every candidate variant (the row decomposition timed at every pair of
+limits), each setting is scored by classifying every matrix with the library's own
+classifier (spmv_classify2), mapping the class set to its variant (Table II) and averaging
+t(plain CSR-vector) / t(selected variant). The setting is chosen on a training split and
+its gain is reported on a held-out split, next to the paper's thresholds on the same split.
 """
 from __future__ import annotations
 
@@ -15,16 +21,23 @@ import numpy as np
 
 from . import _abi
 
-PAPER = (1.24, 1.25, 0.75)
+# The paper's T_IMB and T_ML, this library's T_MB reading, its uneven-rows ratio and its
+# row decomposition limits.
+PAPER = (1.24, 1.25, 0.75, 32.0, 64, 4096)
 GRID = {
     "t_imb": (1.05, 1.1, 1.15, 1.24, 1.35, 1.5, 2.0, 3.0),
     "t_ml": (1.02, 1.05, 1.1, 1.15, 1.25, 1.4, 1.6, 2.0),
     "t_mb": (0.4, 0.5, 0.6, 0.7, 0.75, 0.8, 0.9, 1.01),
+    "long_ratio": (8.0, 16.0, 32.0, 64.0),
 }
+# (l_med, chunk) pairs at which the row decomposition is timed; (64, 4096) is the default.
+BIN_GRID = tuple((m, c) for m in (32, 64, 128) for c in (2048, 4096, 8192))
+KEYS = ("t_imb", "t_ml", "t_mb", "long_ratio", "bin_med", "bin_chunk")
 
 
 def classes_for(ds: dict, idx, thr) -> np.ndarray:
-    t_imb, t_ml, t_mb = thr
+    """Fig. 3 class sets (both passes) of the matrices idx under thresholds thr[:3]."""
+    t_imb, t_ml, t_mb = thr[:3]
     out = np.zeros(len(idx), dtype=np.int32)
     for k, i in enumerate(idx):
         p = np.ascontiguousarray(ds["p"][i], dtype=np.float64)
@@ -33,28 +46,80 @@ def classes_for(ds: dict, idx, thr) -> np.ndarray:
     return out
 
 
-def _candidate(cls, nnz_avg, nnz_max):
+def _candidate(cls, nnz_avg, nnz_max, ratio=32.0):
     from .selector_train import candidate_of
-    return candidate_of(int(cls), float(nnz_avg), float(nnz_max))
+    return candidate_of(int(cls), float(nnz_avg), float(nnz_max), ratio)
+
+
+def times_at(ds: dict, idx, bins=(64, 4096)) -> np.ndarray:
+    """Candidate times of the matrices idx with the row decomposition timed at `bins`,
+    each merge-path candidate replaced by the faster decomposition (the autotuner's pick)."""
+    from .selector_train import CANDIDATES, family_times
+    t = np.array(ds["times"][idx], dtype=np.float64, copy=True)
+    if "times_bins" in ds and tuple(bins) in BIN_GRID:
+        b = BIN_GRID.index(tuple(bins))
+        for xp in (0, 1):
+            t[:, CANDIDATES.index((2, 0, xp, 1))] = ds["times_bins"][idx, xp, b]
+    return family_times(t)
 
 
 def mean_gain(ds: dict, idx, thr) -> float:
+    """Mean t(plain CSR-vector) / t(selected variant) over idx under the setting thr
+    (t_imb, t_ml, t_mb[, long_ratio, bin_med, bin_chunk])."""
+    thr = tuple(thr) + PAPER[len(thr):]
     idx = np.asarray(idx)
     cls = classes_for(ds, idx, thr)
-    ch = np.array([_candidate(c, a, m) for c, a, m in
-                   zip(cls, ds["nnz_avg"][idx], ds["nnz_max"][idx])])
-    from .selector_train import family_times
-    t = family_times(ds["times"][idx])
+    ch = np.array([_candidate(c, a, m, thr[3]) for c, a, m in
+                   zip(cls, ds["nnz_avg"][idx], ds["nnz_max"][idx])], dtype=np.int64)
+    t = times_at(ds, idx, thr[4:6])
     return float(np.mean(t[:, 0] / t[np.arange(len(idx)), ch]))
 
 
 def grid_search(ds: dict, idx) -> dict:
-    best, best_gain = PAPER, -1.0
-    table = []
-    for thr in itertools.product(GRID["t_imb"], GRID["t_ml"], GRID["t_mb"]):
-        g = mean_gain(ds, idx, thr)
-        table.append((thr, g))
-        if g > best_gain + 1e-12:
-            best, best_gain = thr, g
-    return {"best": tuple(float(v) for v in best), "best_gain": best_gain,
-            "paper_gain": mean_gain(ds, idx, PAPER), "table": table}
+    """The exhaustive search on the matrices idx. Class sets depend only on the three
+    thresholds and candidates only on the class set and the ratio, so both are computed once
+    per value and every setting is scored with array operations."""
+    idx = np.asarray(idx)
+    thr3 = list(itertools.product(GRID["t_imb"], GRID["t_ml"], GRID["t_mb"]))
+    cls = np.stack([classes_for(ds, idx, t) for t in thr3])            # (T3, n)
+    avg, mx = ds["nnz_avg"][idx], ds["nnz_max"][idx]
+    ratios = GRID["long_ratio"]
+    # candidate of every (ratio, class set, matrix) that occurs
+    cand = {}
+    for r in ratios:
+        for c in np.unique(cls):
+            cand[(r, int(c))] = np.array([_candidate(c, a, m, r) for a, m in zip(avg, mx)])
+    bins = BIN_GRID if "times_bins" in ds else ((64, 4096),)
+    r_n = np.arange(len(idx))
+    best, best_gain, table = None, -1.0, []
+    for bi, b in enumerate(bins):
+        t = times_at(ds, idx, b)
+        speed = t[:, :1] / t                                           # (n, candidates)
+        for r in ratios:
+            ch = np.zeros_like(cls, dtype=np.int64)
+            for c in np.unique(cls):
+                sel = cls == c
+                ch[sel] = np.broadcast_to(cand[(r, int(c))], cls.shape)[sel]
+            gains = speed[r_n[None, :], ch].mean(axis=1)               # (T3,)
+            for k, g in enumerate(gains):
+                setting = (*thr3[k], r, b[0], b[1])
+                table.append((setting, float(g)))
+                if g > best_gain + 1e-12:
+                    best, best_gain = setting, float(g)
+    return {"best": tuple(float(v) if i < 4 else int(v) for i, v in enumerate(best)),
+            "best_gain": best_gain, "paper_gain": mean_gain(ds, idx, PAPER), "table": table}
+
+
+def calibrate(ds: dict, train_idx, test_idx) -> dict:
+    """Grid search on the training split, scored on the held-out split beside the paper's
+    setting: the record stored with a calibrated selector."""
+    res = grid_search(ds, train_idx)
+    best = res["best"]
+    return {**dict(zip(KEYS, best)), "second_pass": 1,
+            "train_mean_gain": res["best_gain"],
+            "paper_train_mean_gain": res["paper_gain"],
+            "test_mean_gain": mean_gain(ds, test_idx, best),
+            "paper_test_mean_gain": mean_gain(ds, test_idx, PAPER),
+            "n_train": int(len(train_idx)), "n_test": int(len(test_idx)),
+            "grid": {k: list(v) for k, v in GRID.items()},
+            "bin_grid": [list(b) for b in BIN_GRID]}

@@ -41,8 +41,11 @@ CANDIDATES = ((0, 0, 0, 0), (0, 0, 0, 1), (0, 1, 0, 1), (0, 0, 1, 0), (0, 0, 1, 
 SIZES = (12, 32, 32, 4)
 
 
-def _time_variant(A: SpmvMatrix, x, y, knobs, reps: int) -> float:
-    A.set_variant(partition=knobs[0], index=knobs[1], xpath=knobs[2], vec=knobs[3])
+def _time_variant(A: SpmvMatrix, x, y, knobs, reps: int, bin_med: int = 0,
+                  bin_chunk: int = 0) -> float:
+    A.set_variant(partition=knobs[0], index=knobs[1], xpath=knobs[2], vec=knobs[3],
+                  bin_med=bin_med if knobs[0] == 2 else 0,
+                  bin_chunk=bin_chunk if knobs[0] == 2 else 0)
     for _ in range(2):
         A.run(x, y)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -66,10 +69,21 @@ def measure_matrix(m, reps: int = 5) -> dict:
     x = torch.ones(m.n_cols, dtype=A.vec_dtype, device="cuda")
     y = torch.empty(m.n_rows, dtype=A.vec_dtype, device="cuda")
     times = [_time_variant(A, x, y, c, reps) for c in CANDIDATES]
-    feat16 = np.concatenate([f, [float(m.n_rows), float(m.nnz)]])
     lens = np.diff(m.rowptr)
+    # the row decomposition at every pair of limits the grid search tries, for matrices
+    # uneven enough that some ratio of the grid sends them to the decomposition
+    from .calibrate import BIN_GRID, GRID
+    t_bins = np.zeros((2, len(BIN_GRID)))
+    uneven = lens.size and lens.max() > min(GRID["long_ratio"]) * lens.mean()
+    for xp in (0, 1):
+        base = times[CANDIDATES.index((2, 0, xp, 1))]
+        for b, (l_med, chunk) in enumerate(BIN_GRID):
+            t_bins[xp, b] = (_time_variant(A, x, y, (2, 0, xp, 1), reps, l_med, chunk)
+                             if uneven else base)
+    feat16 = np.concatenate([f, [float(m.n_rows), float(m.nnz)]])
     out = {"feat16": feat16, "classes": rep.classes, "p": [rep.p[k] for k in rep.p],
-           "p2": list(rep.p2), "times": times, "t_pre_profile_ms": rep.t_pre_ms, "t_features_ms": t_feat,
+           "p2": list(rep.p2), "times": times, "times_bins": t_bins,
+           "t_pre_profile_ms": rep.t_pre_ms, "t_features_ms": t_feat,
            "nnz_avg": float(lens.mean()) if lens.size else 0.0,
            "nnz_max": float(lens.max()) if lens.size else 0.0, "name": m.name}
     A.close()
@@ -104,6 +118,7 @@ def build_dataset(count: int, seed: int, n_lo: int, n_hi: int, reps: int = 5,
         "p": np.array([r["p"] for r in rows]),
         "p2": np.array([r["p2"] for r in rows]),
         "times": np.array([r["times"] for r in rows]),
+        "times_bins": np.stack([r["times_bins"] for r in rows]),
         "t_pre_profile_ms": np.array([r["t_pre_profile_ms"] for r in rows]),
         "t_features_ms": np.array([r["t_features_ms"] for r in rows]),
         "nnz_avg": np.array([r["nnz_avg"] for r in rows]),
@@ -190,8 +205,9 @@ def family_times(t: np.ndarray) -> np.ndarray:
     return t
 
 
-def candidate_of(classes: int, nnz_avg: float, nnz_max: float) -> int:
-    v = _abi.spmv_variant_for_classes(int(classes), nnz_avg, nnz_max, 32.0)
+def candidate_of(classes: int, nnz_avg: float, nnz_max: float, long_ratio: float = 32.0) -> int:
+    """Index in CANDIDATES of the variant Table II maps the class set to."""
+    v = _abi.spmv_variant_for_classes(int(classes), nnz_avg, nnz_max, long_ratio)
     if v.partition == 1:          # merge-path tiles use neither the delta index nor widths
         return CANDIDATES.index((1, 0, v.xpath, 0))
     return CANDIDATES.index((v.partition, v.index, v.xpath, v.vec))
@@ -202,24 +218,60 @@ def _gmean(a) -> float:
     return float(np.exp(np.mean(np.log(a)))) if a.size else float("nan")
 
 
+def match_ratios(pred: np.ndarray, lab: np.ndarray, bits: int = 0xF) -> tuple[float, float]:
+    """Section IV-B: exact match ratio (every class of the set right) and partial match
+    ratio (at least one class in common, or both sets empty), over the class bits in
+    `bits`."""
+    p, q = np.asarray(pred) & bits, np.asarray(lab) & bits
+    emr = float(np.mean(p == q)) if p.size else float("nan")
+    pmr = float(np.mean(((p & q) != 0) | ((p == 0) & (q == 0)))) if p.size else float("nan")
+    return emr, pmr
+
+
+def varying_bits(lab: np.ndarray) -> int:
+    """The class bits that are not the same in every label (a bit every label carries, or
+    none does, makes every prediction that copies it match trivially)."""
+    lab = np.asarray(lab)
+    bits = 0
+    for b in range(4):
+        v = (lab >> b) & 1
+        if v.size and v.min() != v.max():
+            bits |= 1 << b
+    return bits
+
+
 def evaluate(ds: dict, idx: np.ndarray, pred: np.ndarray) -> dict:
-    """Section IV-B match ratios and Section IV-C speed of the selected variants."""
+    """Section IV-B match ratios (over all four classes, and over the classes whose bit
+    varies among the labels) and Section IV-C speed of the selected variants: regret of the
+    profile route's and of the MLP's choice against the best candidate."""
+    from .calibrate import times_at
     lab = ds["classes"][idx]
-    emr = float(np.mean(pred == lab))
-    pmr = float(np.mean(((pred & lab) != 0) | ((pred == 0) & (lab == 0))))
-    t = family_times(ds["times"][idx])
-    ch_ml = np.array([candidate_of(c, a, mx) for c, a, mx in
+    ratio = float(ds.get("long_ratio", 32.0))
+    emr, pmr = match_ratios(pred, lab)
+    vb = varying_bits(ds["classes"])
+    emr_v, pmr_v = match_ratios(pred, lab, vb)
+    t = times_at(ds, idx, tuple(ds.get("bins", (64, 4096))))
+    ch_ml = np.array([candidate_of(c, a, mx, ratio) for c, a, mx in
                       zip(pred, ds["nnz_avg"][idx], ds["nnz_max"][idx])])
-    ch_pr = np.array([candidate_of(c, a, mx) for c, a, mx in
+    ch_pr = np.array([candidate_of(c, a, mx, ratio) for c, a, mx in
                       zip(lab, ds["nnz_avg"][idx], ds["nnz_max"][idx])])
     r = np.arange(len(idx))
     t_ml, t_pr, t_best, t_base = t[r, ch_ml], t[r, ch_pr], t.min(axis=1), t[:, 0]
+    names = ("MB", "ML", "IMB", "CMP")
     return {"n": int(len(idx)), "exact_match_ratio": emr, "partial_match_ratio": pmr,
+            "varying_classes": [names[b] for b in range(4) if vb >> b & 1],
+            "exact_match_ratio_varying": emr_v, "partial_match_ratio_varying": pmr_v,
+            "class_accuracy": {names[b]: float(np.mean(((pred >> b) & 1) == ((lab >> b) & 1)))
+                               for b in range(4)},
             "gmean_t_mlp_over_t_profile": _gmean(t_ml / t_pr),
             "gmean_t_mlp_over_t_best": _gmean(t_ml / t_best),
             "gmean_t_profile_over_t_best": _gmean(t_pr / t_best),
+            "frac_mlp_within_5pct_of_best": float(np.mean(t_ml <= 1.05 * t_best)),
+            "frac_profile_within_5pct_of_best": float(np.mean(t_pr <= 1.05 * t_best)),
+            "max_t_mlp_over_t_profile": float(np.max(t_ml / t_pr)) if len(idx) else float("nan"),
             "gmean_speedup_mlp_vs_csr_vector": _gmean(t_base / t_ml),
             "gmean_speedup_profile_vs_csr_vector": _gmean(t_base / t_pr),
+            "gmean_speedup_best_vs_csr_vector": _gmean(t_base / t_best),
             "label_histogram": {int(k): int(v) for k, v in
                                 zip(*np.unique(lab, return_counts=True))}}
 
@@ -228,9 +280,9 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--count", type=int, default=2000)
     ap.add_argument("--seed", type=int, default=171105487 + 40)
-    ap.add_argument("--n-lo", type=int, default=10_000)
-    ap.add_argument("--n-hi", type=int, default=1_000_000)
-    ap.add_argument("--slack", type=float, default=0.5,
+    ap.add_argument("--n-lo", type=int, default=1_000)
+    ap.add_argument("--n-hi", type=int, default=4_000_000)
+    ap.add_argument("--slack", type=float, default=1.0,
                     help="standardized units an input may leave the training range by")
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--steps", type=int, default=3000)
@@ -257,21 +309,20 @@ def main():
     cal = None
     if "p2" in ds:
         from . import calibrate
-        cal = calibrate.grid_search(ds, tr)
+        cal = calibrate.calibrate(ds, tr, te)
         ds = dict(ds)
         ds["classes_paper"] = ds["classes"]
-        ds["classes"] = calibrate.classes_for(ds, np.arange(n), cal["best"])
+        ds["classes"] = calibrate.classes_for(ds, np.arange(n),
+                                              [cal[k] for k in calibrate.KEYS])
+        ds["long_ratio"] = cal["long_ratio"]
+        ds["bins"] = (cal["bin_med"], cal["bin_chunk"])
     t1 = time.time()
     params, mu, inv, hist = train(ds["feat16"][tr], ds["classes"][tr], steps=args.steps)
     t_train = time.time() - t1
     pred_te, _ = predict(params, mu, inv, ds["feat16"][te])
     pred_tr, _ = predict(params, mu, inv, ds["feat16"][tr])
     res = {"train": evaluate(ds, tr, pred_tr), "test": evaluate(ds, te, pred_te),
-           "calibration": None if cal is None else {
-               "thresholds": cal["best"], "train_mean_gain": cal["best_gain"],
-               "paper_thresholds_train_mean_gain": cal["paper_gain"],
-               "test_mean_gain": calibrate.mean_gain(ds, te, cal["best"]),
-               "paper_thresholds_test_mean_gain": calibrate.mean_gain(ds, te, calibrate.PAPER)},
+           "calibration": cal,
            "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
            "t_dataset_s": t_data, "t_train_s": t_train, "count": int(n),
            "t_pre_profile_ms_median": float(np.median(ds["t_pre_profile_ms"])),
@@ -285,8 +336,7 @@ def main():
     res["test_inside_training_range"] = float(np.mean(te_in))
     if cal is not None:
         with open(os.path.join(args.out, "calibration_gb300.json"), "w") as fh:
-            json.dump({"t_imb": cal["best"][0], "t_ml": cal["best"][1], "t_mb": cal["best"][2],
-                       "second_pass": 1}, fh, indent=1)
+            json.dump(cal, fh, indent=1)
     with open(os.path.join(args.out, "selector_metrics.json"), "w") as fh:
         json.dump(res, fh, indent=1)
     print(json.dumps(res))
