@@ -638,6 +638,14 @@ def workload_summary(name, args, world, peak, sel):
            "speedup_vs_csr_vector": round(base_ms / ms, 3),
            "gpu_launches": args.steps * launches_per_spmv(A, rep.variant),
            "gen_s": round(gen_s, 1)}
+    # the measured ceiling of this matrix's random x gathers: as many gathers, uniform over
+    # an x of the same size (no index stream); ceiling_frac = probe time / SpMV time
+    if name in ("powerlaw_4m", "scattered_16m"):
+        from paper_1711_05487_gb300 import _abi
+        t_g = _abi.spmv_probe_gather(m.n_cols, 8 if vec_t == torch.float64 else 4, m.nnz, 5)
+        out["gather_ceiling"] = {"probe_ms": round(t_g, 5),
+                                 "g_gathers_per_s": round(m.nnz / (t_g * 1e-3) / 1e9, 1),
+                                 "frac": round(t_g / ms, 4)}
     if sel is not None:
         r_l = A.tune("learned", stream=stream, selector=sel)
         t_l = time_spmv(A, x, y, stream, args.steps, args.warmup, world)

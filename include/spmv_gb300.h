@@ -339,6 +339,14 @@ spmv_status spmv_profile_kernel(spmv_handle_t h, int32_t which, const void *x, v
  * footnote. Measured once per device and cached. */
 spmv_status spmv_probe_bandwidth(double *hbm_gbs, double *l2_gbs);
 
+/* Ceiling of random x gathers (not in the paper; the measured bound of an SpMV whose column
+ * indices are uniform random): the time in ms (best of three runs of reps launches) of
+ * `count` gathers of elem_bytes (4 or 8) elements at uniform pseudo-random positions of an
+ * n_x-element array, 8 in flight per thread, no index array streamed. Allocates and frees
+ * its array (n_x < 2^32). Synchronizes. Errors: SPMV_ERR_ARG, SPMV_ERR_OOM, SPMV_ERR_CUDA. */
+spmv_status spmv_probe_gather(int64_t n_x, int32_t elem_bytes, int64_t count, int32_t reps,
+                              double *ms, spmv_stream_t stream);
+
 /* Fig. 3 on a P-vector (csr, mb, ml, imb, cmp, peak); pure function. */
 uint32_t spmv_classify(const double *p, double t_imb, double t_ml, double t_mb);
 

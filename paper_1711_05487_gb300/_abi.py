@@ -118,6 +118,7 @@ _DECL = {
     "spmv_profile_cta_times": (_I32, [_P, _P, _P, ctypes.POINTER(_I32), _P]),
     "spmv_profile_kernel": (_I32, [_P, _I32, _P, _P, _P]),
     "spmv_probe_bandwidth": (_I32, [ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "spmv_probe_gather": (_I32, [_I64, _I32, _I64, _I32, ctypes.POINTER(_D), _P]),
     "spmv_classify": (_U32, [_P, _D, _D, _D]),
     "spmv_classify2": (_U32, [_P, _P, _D, _D, _D]),
     "spmv_variant_for_classes": (None, [_U32, _D, _D, _D, ctypes.POINTER(spmv_variant)]),
@@ -299,6 +300,14 @@ def spmv_probe_bandwidth():
     a, b = _D(), _D()
     _call("spmv_probe_bandwidth", ctypes.byref(a), ctypes.byref(b))
     return a.value, b.value
+
+
+def spmv_probe_gather(n_x, elem_bytes, count, reps=5, stream=0):
+    """Milliseconds of `count` random gathers from an n_x-element array (the ceiling of an
+    SpMV with uniform random columns)."""
+    ms = _D()
+    _call("spmv_probe_gather", n_x, elem_bytes, count, reps, ctypes.byref(ms), stream)
+    return ms.value
 
 
 def spmv_classify(p_host, t_imb=1.24, t_ml=1.25, t_mb=0.75) -> int:

@@ -2,10 +2,11 @@
 //
 // The host plans work items (row blocks of about equal nonzero counts; rows longer than a
 // chunk are split into nonzero chunks, the matrix decomposition of Fig. 4/5) and sorts them
-// by the matrices' right-hand-side count k in {1, 4, 16}. One resident kernel per k walks its
-// items: every warp takes the next item from a device counter with atomicAdd (no warp or CTA
-// ever waits on another), a row-block item is computed by sub-warps of the matrix's width,
-// a chunk of a long row by the whole warp into an FP64 partial slot, and k_batch_fixup adds
+// longest first. One resident kernel walks them all: every warp takes the next item from a
+// device counter with atomicAdd (no warp or CTA ever waits on another) and runs the code of
+// its matrix's right-hand-side count k in {1, 4, 16}; a row-block item is computed by
+// sub-warps of the matrix's width, a chunk of a long row by the whole warp into an FP64
+// partial slot, and k_batch_fixup adds
 // the chunks of each split row in chunk order, in FP64. Storage and x/y are FP32; the
 // accumulation is FP32, in runs of at most kF32Run products per lane added into FP32 pairs
 // wherever a lane's chain would pass kF32Chain roundings, so every row stays within the
@@ -366,6 +367,15 @@ __device__ void warp_chunk(const BatchMat &m, int z0, int z1, int chunk, double 
 }
 
 template <int K>
+__device__ __forceinline__ void run_item(const BatchMat &m, const BatchItem &item,
+                                         double *partials, int lane) {
+  if (item.chunk < 0) warp_rows_vs<K>(m, item.row_begin, item.row_end, lane);
+  else warp_chunk<K>(m, item.nz_begin, item.nz_end, item.chunk, partials, lane);
+}
+
+// The whole batch in one persistent launch: a resident grid whose warps take the next work
+// item from one device counter (atomicAdd; no warp or CTA ever waits on another) and run it
+// with the code of its matrix's right-hand-side count.
 __global__ void __launch_bounds__(kBT)
 k_batch_persistent(const BatchMat *mats, const BatchItem *items, int32_t n_items,
                    int32_t *counter, double *partials) {
@@ -377,22 +387,10 @@ k_batch_persistent(const BatchMat *mats, const BatchItem *items, int32_t n_items
     if (it >= n_items) break;
     const BatchItem item = items[it];
     const BatchMat m = mats[item.mat];
-    if (item.chunk < 0) warp_rows_vs<K>(m, item.row_begin, item.row_end, lane);
-    else warp_chunk<K>(m, item.nz_begin, item.nz_end, item.chunk, partials, lane);
+    if (m.k == 1) run_item<1>(m, item, partials, lane);
+    else if (m.k == 4) run_item<4>(m, item, partials, lane);
+    else run_item<16>(m, item, partials, lane);
   }
-}
-
-// One warp per item (the same work without persistence).
-template <int K>
-__global__ void __launch_bounds__(kBT)
-k_batch_items(const BatchMat *mats, const BatchItem *items, int32_t n_items, double *partials) {
-  const int lane = threadIdx.x & 31;
-  const int64_t it = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-  if (it >= n_items) return;
-  const BatchItem item = items[it];
-  const BatchMat m = mats[item.mat];
-  if (item.chunk < 0) warp_rows_vs<K>(m, item.row_begin, item.row_end, lane);
-  else warp_chunk<K>(m, item.nz_begin, item.nz_end, item.chunk, partials, lane);
 }
 
 __global__ void k_batch_fixup(const BatchMat *mats, const BatchFix *fix, int32_t n_fix,
@@ -408,33 +406,17 @@ __global__ void k_batch_fixup(const BatchMat *mats, const BatchFix *fix, int32_t
   m.Y[(int64_t)f.row * m.k + q] = (float)tot;
 }
 
-int batch_blocks_per_sm_k(int k) {
+int batch_blocks_per_sm() {
   int b = 0;
-  if (k == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_persistent<1>, kBT, 0);
-  else if (k == 4) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_persistent<4>, kBT, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_persistent<16>, kBT, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_persistent, kBT, 0);
   return b > 0 ? b : 1;
 }
 
-int batch_blocks_per_sm() { return batch_blocks_per_sm_k(16); }
-
-cudaError_t launch_batch_persistent_k(int k, const BatchMat *mats, const BatchItem *items,
-                                      int32_t n_items, int32_t *counter, double *partials,
-                                      int grid, cudaStream_t s) {
+cudaError_t launch_batch_persistent(const BatchMat *mats, const BatchItem *items,
+                                    int32_t n_items, int32_t *counter, double *partials,
+                                    int grid, cudaStream_t s) {
   if (n_items <= 0 || grid <= 0) return cudaSuccess;
-  if (k == 1) k_batch_persistent<1><<<grid, kBT, 0, s>>>(mats, items, n_items, counter, partials);
-  else if (k == 4) k_batch_persistent<4><<<grid, kBT, 0, s>>>(mats, items, n_items, counter, partials);
-  else k_batch_persistent<16><<<grid, kBT, 0, s>>>(mats, items, n_items, counter, partials);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_batch_items_k(int k, const BatchMat *mats, const BatchItem *items,
-                                 int32_t n_items, double *partials, cudaStream_t s) {
-  if (n_items <= 0) return cudaSuccess;
-  const unsigned g = (unsigned)(((int64_t)n_items * 32 + kBT - 1) / kBT);
-  if (k == 1) k_batch_items<1><<<g, kBT, 0, s>>>(mats, items, n_items, partials);
-  else if (k == 4) k_batch_items<4><<<g, kBT, 0, s>>>(mats, items, n_items, partials);
-  else k_batch_items<16><<<g, kBT, 0, s>>>(mats, items, n_items, partials);
+  k_batch_persistent<<<grid, kBT, 0, s>>>(mats, items, n_items, counter, partials);
   return cudaGetLastError();
 }
 

@@ -16,7 +16,6 @@ namespace {
 constexpr int32_t kItemNnz = 1024;
 constexpr int32_t kChunkNnz = 2048;
 constexpr int32_t kItemRowsMax = 1024;
-constexpr int kKs[3] = {1, 4, 16};
 inline int k_slot(int k) { return k == 1 ? 0 : (k == 4 ? 1 : 2); }
 
 struct Fail {
@@ -46,16 +45,13 @@ struct spmv_batch {
   std::vector<std::vector<int32_t>> rowptr;   // host copies, for re-planning
   int32_t item_nnz = kItemNnz, chunk_nnz = kChunkNnz;
   BatchMat *d_mats = nullptr;
-  BatchItem *d_items = nullptr;          // items of k = 1, then k = 4, then k = 16
+  BatchItem *d_items = nullptr;          // every matrix's items, costliest first
   BatchFix *d_fix = nullptr;
   double *d_partials = nullptr;
-  int32_t *d_counter = nullptr;          // one work counter per k
+  int32_t *d_counter = nullptr;          // the work counter of the persistent kernel
   int32_t n_items = 0, n_fix = 0, n_chunks = 0;
-  int32_t item_off[4] = {0, 0, 0, 0};    // item range of each k
-  int grid[3] = {0, 0, 0};
+  int grid = 0;
   cudaStream_t cap = nullptr;
-  cudaStream_t side[2] = {nullptr, nullptr};
-  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -66,10 +62,6 @@ static void batch_free(spmv_batch *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->cap) cudaStreamDestroy(b->cap);
-  for (auto st : b->side)
-    if (st) cudaStreamDestroy(st);
-  for (auto e : b->ev)
-    if (e) cudaEventDestroy(e);
   cudaFree(b->d_mats);
   cudaFree(b->d_items);
   cudaFree(b->d_fix);
@@ -80,10 +72,10 @@ static void batch_free(spmv_batch *b) {
 
 // The work plan for (item_nnz, chunk_nnz): row blocks of about item_nnz nonzeros per warp,
 // rows longer than item_nnz split into chunks of chunk_nnz nonzeros with FP64 partials,
-// longest items first; uploads the items, the fixups and the partial slots, sizes the
-// persistent grids and drops the captured graph.
+// costliest items first; uploads the items, the fixups and the partial slots, sizes the
+// persistent grid and drops the captured graph.
 static void batch_plan(spmv_batch *b, int32_t item_nnz, int32_t chunk_nnz, cudaStream_t s) {
-  std::vector<BatchItem> items_k[3];
+  std::vector<BatchItem> items_k[3];   // per k in {1, 4, 16}
   std::vector<BatchFix> fix;
   int32_t chunks = 0;
   for (int32_t m = 0; m < b->count; ++m) {
@@ -117,22 +109,19 @@ static void batch_plan(spmv_batch *b, int32_t item_nnz, int32_t chunk_nnz, cudaS
       r = e;
     }
   }
-  // Longest items first (chunks of split rows, then full row blocks, then the short
-  // remainders), so that the last items the warps take are the cheapest; the sort is
-  // stable, so items of one matrix stay together within a class (x rows stay L2-hot).
+  // Costliest items first (chunks of split rows, then full row blocks, then the short
+  // remainders; within each, the widest right-hand sides first), so that the last items
+  // the warps take are the cheapest; the sort is stable, so items of one matrix stay
+  // together (their x rows stay L2-hot).
   auto item_class = [&](const BatchItem &it) -> int {
     if (it.chunk >= 0) return 0;
     return it.nz_end >= item_nnz / 2 ? 1 : 2;
   };
   std::vector<BatchItem> items;
-  for (int q = 0; q < 3; ++q) {
-    std::stable_sort(items_k[q].begin(), items_k[q].end(),
-                     [&](const BatchItem &a, const BatchItem &c) {
-                       return item_class(a) < item_class(c);
-                     });
-    b->item_off[q] = (int32_t)items.size();
-    items.insert(items.end(), items_k[q].begin(), items_k[q].end());
-  }
+  for (int q = 2; q >= 0; --q) items.insert(items.end(), items_k[q].begin(), items_k[q].end());
+  std::stable_sort(items.begin(), items.end(), [&](const BatchItem &a, const BatchItem &c) {
+    return item_class(a) < item_class(c);
+  });
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;
@@ -144,7 +133,6 @@ static void batch_plan(spmv_batch *b, int32_t item_nnz, int32_t chunk_nnz, cudaS
   b->d_items = nullptr;
   b->d_fix = nullptr;
   b->d_partials = nullptr;
-  b->item_off[3] = (int32_t)items.size();
   b->n_items = (int32_t)items.size();
   b->n_fix = (int32_t)fix.size();
   b->n_chunks = chunks;
@@ -158,11 +146,8 @@ static void batch_plan(spmv_batch *b, int32_t item_nnz, int32_t chunk_nnz, cudaS
   BK(cudaStreamSynchronize(s));
   int sms = 0;
   BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
-  for (int q = 0; q < 3; ++q) {
-    const int64_t warps = b->item_off[q + 1] - b->item_off[q];
-    const int64_t ctas = (warps + 7) / 8;     // 8 warps per CTA
-    b->grid[q] = (int)std::min<int64_t>((int64_t)sms * batch_blocks_per_sm_k(kKs[q]), ctas);
-  }
+  const int64_t ctas = ((int64_t)b->n_items + 7) / 8;     // 8 warps per CTA
+  b->grid = (int)std::min<int64_t>((int64_t)sms * batch_blocks_per_sm(), ctas);
   b->item_nnz = item_nnz;
   b->chunk_nnz = chunk_nnz;
 }
@@ -234,13 +219,11 @@ spmv_status spmv_batch_create(spmv_batch_t *out, const spmv_handle_t *handles, i
       b->k.push_back(k[m]);
     }
     BK(cudaMalloc(&b->d_mats, sizeof(BatchMat) * b->mats.size()));
-    BK(cudaMalloc(&b->d_counter, 3 * sizeof(int32_t)));
+    BK(cudaMalloc(&b->d_counter, sizeof(int32_t)));
     BK(cudaMemcpyAsync(b->d_mats, b->mats.data(), sizeof(BatchMat) * b->mats.size(),
                        cudaMemcpyHostToDevice, s));
     batch_plan(b, kItemNnz, kChunkNnz, s);
     BK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
-    for (auto &st : b->side) BK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    for (auto &e : b->ev) BK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   } catch (const Fail &f) {
     cudaGetLastError();
     batch_free(b);
@@ -315,22 +298,14 @@ spmv_status spmv_run_batched(spmv_batch_t b, spmv_stream_t stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   try {
     if (!b->exec) {
-      // Capture on the batch's own streams (the legacy default stream cannot be captured):
-      // reset the counters, fork the three persistent kernels (k = 1, 4, 16) onto parallel
-      // branches, join, then the fixup of split rows.
+      // Capture on the batch's own stream (the legacy default stream cannot be captured):
+      // reset the work counter, the persistent kernel over every item, then the fixup of
+      // split rows.
       BK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = cudaMemsetAsync(b->d_counter, 0, 3 * sizeof(int32_t), b->cap);
-      cudaStream_t st[3] = {b->cap, b->side[0], b->side[1]};
-      if (e == cudaSuccess) e = cudaEventRecord(b->ev[0], b->cap);
-      for (int q = 1; q < 3 && e == cudaSuccess; ++q) e = cudaStreamWaitEvent(st[q], b->ev[0], 0);
-      for (int q = 0; q < 3 && e == cudaSuccess; ++q)
-        e = launch_batch_persistent_k(kKs[q], b->d_mats, b->d_items + b->item_off[q],
-                                      b->item_off[q + 1] - b->item_off[q], b->d_counter + q,
-                                      b->d_partials, b->grid[q], st[q]);
-      for (int q = 1; q < 3 && e == cudaSuccess; ++q) {
-        e = cudaEventRecord(b->ev[q], st[q]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, b->ev[q], 0);
-      }
+      cudaError_t e = cudaMemsetAsync(b->d_counter, 0, sizeof(int32_t), b->cap);
+      if (e == cudaSuccess)
+        e = launch_batch_persistent(b->d_mats, b->d_items, b->n_items, b->d_counter,
+                                    b->d_partials, b->grid, b->cap);
       if (e == cudaSuccess) e = launch_batch_fixup(b->d_mats, b->d_fix, b->n_fix, b->d_partials, b->cap);
       cudaGraph_t g = nullptr;
       cudaError_t e3 = cudaStreamEndCapture(b->cap, &g);

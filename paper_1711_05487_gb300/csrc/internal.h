@@ -262,6 +262,8 @@ cudaError_t launch_chunk_colmax(int64_t n_rows, const int32_t *rowptr, const int
 cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t *err, cudaStream_t s);
 
 // Bandwidth probe
+cudaError_t launch_gather_probe(const void *x, int32_t elem_bytes, int64_t n_x, int64_t count,
+                                unsigned long long *sink, cudaStream_t s);
 cudaError_t launch_read_probe(const void *buf, int64_t bytes, int reps,
                               unsigned long long *sink, cudaStream_t s);
 
@@ -281,15 +283,13 @@ int64_t mlp_param_count(const int32_t *sizes);
 cudaError_t launch_adam(int64_t n, float *p, const float *g, float *m, float *v, float lr,
                         float b1, float b2, float eps, int32_t t, cudaStream_t s);
 
-// Batched (batch.cu): one persistent kernel per right-hand-side count k in {1, 4, 16}
-cudaError_t launch_batch_persistent_k(int k, const BatchMat *mats, const BatchItem *items,
-                                      int32_t n_items, int32_t *counter, double *partials,
-                                      int grid, cudaStream_t s);
-cudaError_t launch_batch_items_k(int k, const BatchMat *mats, const BatchItem *items,
-                                 int32_t n_items, double *partials, cudaStream_t s);
+// Batched (batch.cu): one persistent kernel over the work items of every matrix (each
+// item run with the code of its matrix's k in {1, 4, 16}), then the fixup of split rows
+cudaError_t launch_batch_persistent(const BatchMat *mats, const BatchItem *items,
+                                    int32_t n_items, int32_t *counter, double *partials,
+                                    int grid, cudaStream_t s);
 cudaError_t launch_batch_fixup(const BatchMat *mats, const BatchFix *fix, int32_t n_fix,
                                const double *partials, cudaStream_t s);
-int batch_blocks_per_sm_k(int k);
 int batch_blocks_per_sm();
 
 // Conjugate gradients (cg.cu): deterministic FP64 vector kernels; each reduction writes

@@ -673,6 +673,57 @@ cudaError_t launch_read_probe(const void *buf, int64_t bytes, int reps,
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ gather probe -----
+// `count` gathers of one element each from x[0, n_x) at pseudo-random positions: gather j
+// reads x[(h(j) >> 32) * n_x >> 32], h the splitmix64 finalizer (Steele, Lea and Flood) of
+// seed + j, so no index array is streamed and the positions are uniform over x. Each thread
+// keeps 8 gathers in flight before summing them; the sum is stored only if it equals an
+// impossible value, so the loads stay. The gather rate is the ceiling of an SpMV whose x
+// accesses are uniform random over an x of the same size.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void k_gather_probe(const T *__restrict__ x, int64_t n_x, int64_t count,
+                               uint64_t seed, unsigned long long *sink) {
+  T acc = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * 8;
+  for (int64_t j0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 8; j0 < count;
+       j0 += stride) {
+    T v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const uint64_t h = mix64(seed + (uint64_t)(j0 + q));
+      const int64_t i = (int64_t)(((h >> 32) * (uint64_t)n_x) >> 32);
+      v[q] = j0 + q < count ? __ldg(x + i) : (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc += v[q];
+  }
+  if (acc == (T)-1234.5) *sink = 1;
+}
+
+cudaError_t launch_gather_probe(const void *x, int32_t elem_bytes, int64_t n_x, int64_t count,
+                                unsigned long long *sink, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t g = (int64_t)sms * 8;
+  const int64_t need = (count / 8 + kT - 1) / kT;
+  if (g > need) g = need;
+  if (g < 1) g = 1;
+  if (elem_bytes == 8)
+    k_gather_probe<double><<<(unsigned)g, kT, 0, s>>>(static_cast<const double *>(x), n_x, count,
+                                                      0x9E3779B97F4A7C15ull, sink);
+  else
+    k_gather_probe<float><<<(unsigned)g, kT, 0, s>>>(static_cast<const float *>(x), n_x, count,
+                                                     0x9E3779B97F4A7C15ull, sink);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ row decomposition ------
 // Per row: med = 1 if l_med <= length < chunk, lng = 1 if length >= chunk, nch = the long
 // row's chunk count. Exclusive scans of the three give each row's place in the lists.

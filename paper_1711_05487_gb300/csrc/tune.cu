@@ -762,6 +762,29 @@ spmv_status spmv_probe_bandwidth(double *hbm_gbs, double *l2_gbs) {
   });
 }
 
+spmv_status spmv_probe_gather(int64_t n_x, int32_t elem_bytes, int64_t count, int32_t reps,
+                              double *ms, spmv_stream_t stream) {
+  if (!ms || n_x < 1 || n_x >= ((int64_t)1 << 32) || count < 1 || reps < 1 ||
+      (elem_bytes != 4 && elem_bytes != 8))
+    return SPMV_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return guarded([&]() -> spmv_status {
+    DevBuf x, sink;
+    x.alloc((size_t)elem_bytes * (size_t)n_x, 16, s);
+    sink.alloc(8, 8, s, true);
+    CK(launch_fill_const(x.p, elem_bytes == 8 ? SPMV_F64 : SPMV_F32, n_x, 1.0, s));
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r)
+      best = std::min(best, time_launches([&]() {
+        return launch_gather_probe(x.p, elem_bytes, n_x, count,
+                                   sink.as<unsigned long long>(), s);
+      }, reps, s));
+    CK(cudaStreamSynchronize(s));
+    *ms = best;
+    return SPMV_OK;
+  });
+}
+
 uint32_t spmv_classify(const double *p, double t_imb, double t_ml, double t_mb) {
   if (!p) return 0;
   return classify(p, t_imb, t_ml, t_mb);

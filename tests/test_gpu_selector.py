@@ -100,6 +100,20 @@ def test_bandwidth_probe_is_plausible(abi):
     assert 1000 < hbm < 20000 and l2 > hbm
 
 
+def test_gather_probe_is_plausible(abi):
+    """Random gathers: an L2-resident x (16 MB) serves them faster than one far larger than
+    the L2 (2 GB), where every gather misses to DRAM; the L2 rate is above 10 G gathers/s and
+    each DRAM-bound gather moves at least a 32-byte sector within the HBM bound."""
+    n = 1 << 26
+    t_l2 = abi.spmv_probe_gather(4 << 20, 4, n, reps=3)
+    t_dram = abi.spmv_probe_gather(1 << 29, 4, n, reps=3)
+    assert 0 < t_l2 < t_dram
+    assert n / (t_l2 * 1e-3) > 10e9
+    assert 32 * n / (t_dram * 1e-3) / 1e9 < 20000
+    with pytest.raises(abi.SpmvError):
+        abi.spmv_probe_gather(1 << 32, 4, n)
+
+
 def test_profile_report_and_cta_times(api, torch):
     """spmv_profile: P_MB and P_peak equal the oracle's bounds at the reported B_max (the
     L2 rate for a cache-fitting working set, else HBM: the footnote's reading), the timed
