@@ -936,11 +936,28 @@ def main():
                          "and arithmetic, or FP32 / BF16 value storage with FP32 x and "
                          "accumulation, for the timed line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--probe-gather", action="store_true",
+                    help="print the random-gather ceiling for x sizes from 4 MB to 1 GB (one "
+                         "JSON line per size) and exit")
     ap.add_argument("--fixed-variant", default=None,
                     help="install this variant instead of tuning: partition,index,xpath,vec,"
                          "vs,tile_rows,tile_pipe")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.probe_gather:
+        import torch
+
+        from paper_1711_05487_gb300 import _abi
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        count = 1 << 27
+        for n_x, eb in ((1 << 20, 4), (4 << 20, 4), (16 << 20, 4), (4 << 20, 8), (8 << 20, 8),
+                        (12 << 20, 8), (16 << 20, 8), (64 << 20, 8), (1 << 28, 4)):
+            ms = _abi.spmv_probe_gather(n_x, eb, count, 5)
+            print(json.dumps({"n_x": n_x, "elem_bytes": eb, "x_mb": n_x * eb / 2 ** 20,
+                              "gathers": count, "ms": round(ms, 5),
+                              "g_gathers_per_s": round(count / (ms * 1e-3) / 1e9, 1)}),
+                  flush=True)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -170,6 +170,7 @@ struct spmv_matrix {
   DevBuf pnl_rowptr, pnl_col, pnl_val;   // column panels: panel-major copy of the matrix
   int32_t pnl_count = 0;       // panels of the built copy (0: none)
   int32_t pnl_width = 0;       // columns per panel
+  int32_t pnl_tile_rows = 0, pnl_tile_cap = 0;   // staged tiles of one-thread-per-row passes
   // run state
   spmv_variant variant{};
   bool tuned = false;

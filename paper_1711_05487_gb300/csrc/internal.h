@@ -49,6 +49,9 @@ struct RunArgs {
   int32_t tile_cap = 0;              // staged elements per row tile (thread-per-row kernel)
   int32_t tile_rows = 0;             // rows (= threads) per tile: 32, 64 or 128
   int32_t tile_pipe = 0;             // 1: persistent CTAs with two staged tiles in flight
+  int32_t y_add = 0;                 // 1: row sums are added to y (later column-panel passes)
+  int32_t f32_chain = 30;            // FP32 accumulation: longest row a thread sums in FP32
+                                     // alone (16 when passes add into y: one rounding each)
   int32_t *err = nullptr;            // device error word (bounded waits)
   const void *val_df = nullptr;      // storage SPMV_DF64: double-float value pairs
   // row decomposition (partition 2): rows with length < bin_l_med go to sub-warps of
@@ -74,6 +77,8 @@ struct RunArgs {
   int64_t pnl_stride = 0;
   int32_t pnl_first = 0;
   int32_t n_panels = 0;
+  int32_t pnl_tile_cap = 0;          // one thread per row (vs = 1): staged tiles of the passes
+  int32_t pnl_tile_rows = 0;         // rows per staged tile of the passes
   // sliced rows (partition 3): 32-row slices stored column-major; element k of row r at
   // sell_off[r / 32] + 32 k + r % 32 of sell_val and sell_idx (int32 columns, or column
   // deltas of delta_bits bits with dbase / esc as for the delta index)

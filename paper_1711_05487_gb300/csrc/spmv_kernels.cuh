@@ -932,7 +932,10 @@ cudaError_t launch_rowvec_vs(const spmv_variant &v, const RunArgs &a, cudaStream
   return cudaGetLastError();
 }
 
-// The column-panel variant: one launch per pass, in panel order on one stream.
+// The column-panel variant: one launch per pass, in panel order on one stream. With one
+// thread per row (VS = 1) every pass is the thread-per-row tile kernel on the panel's CSR
+// (its tiles staged by bulk copies, x gathered evict-last), adding into y after the first
+// pass; wider sub-warps run k_panel.
 template <typename ValT, typename VecT, typename AccT, int VS>
 cudaError_t launch_panels_vs(const spmv_variant &v, const RunArgs &a, cudaStream_t s) {
   RunArgs pa = a;
@@ -941,8 +944,21 @@ cudaError_t launch_panels_vs(const spmv_variant &v, const RunArgs &a, cudaStream
   const unsigned g = grid_for_rows(a.n_rows, VS);
   for (int p = a.pnl_first; p < a.pnl_first + a.n_panels; ++p) {
     const int32_t *prow = a.pnl_rowptr + (int64_t)p * a.pnl_stride;
-    if (v.vec) k_panel<ValT, VecT, AccT, VS, true><<<g, kRowThreads, 0, s>>>(pa, prow, p > 0);
-    else k_panel<ValT, VecT, AccT, VS, false><<<g, kRowThreads, 0, s>>>(pa, prow, p > 0);
+    if constexpr (VS == 1) {
+      if (a.pnl_tile_rows <= 0) return cudaErrorInvalidValue;
+      RunArgs ta = pa;
+      ta.rowptr = prow;
+      ta.y_add = p > 0;
+      ta.f32_chain = kF32Run;          // each pass also rounds once into y
+      ta.tile_cap = a.pnl_tile_cap;
+      ta.tile_rows = a.pnl_tile_rows;
+      ta.tile_pipe = 0;
+      const cudaError_t e = launch_rowtile_k<ValT, VecT, AccT, 0, true>(ta, s);
+      if (e != cudaSuccess) return e;
+    } else {
+      if (v.vec) k_panel<ValT, VecT, AccT, VS, true><<<g, kRowThreads, 0, s>>>(pa, prow, p > 0);
+      else k_panel<ValT, VecT, AccT, VS, false><<<g, kRowThreads, 0, s>>>(pa, prow, p > 0);
+    }
   }
   return cudaGetLastError();
 }

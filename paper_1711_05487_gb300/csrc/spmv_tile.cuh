@@ -55,10 +55,10 @@ __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
       return (int)sidx[o + k];
     }
   };
-  // FP32 accumulation of a row longer than kF32Chain: each 16-product run's sum is added
+  // FP32 accumulation of a row longer than a.f32_chain: each 16-product run's sum is added
   // into an FP32 pair
   FPair tot;
-  const bool fold = IsF32<AccT>::value && len > kF32Chain;
+  const bool fold = IsF32<AccT>::value && len > a.f32_chain;
   int k = 0;
   for (; k + 16 <= len; k += 16) {
     AccT xv[16];
@@ -139,6 +139,14 @@ __device__ __forceinline__ SumT warp_row_dot(const RunArgs &a, int64_t r, int s,
   return sum;
 }
 
+// Stores a row's sum, or adds it to y (the later passes of column panels).
+template <typename VecT, typename AccT>
+__device__ __forceinline__ void store_y(const RunArgs &a, VecT *__restrict__ y, int64_t row,
+                                        AccT v) {
+  if (a.y_add) y[row] = (VecT)((AccT)y[row] + v);
+  else y[row] = (VecT)v;
+}
+
 // Rows [r0, r1) straight from global memory, a warp per row (tiles larger than the staged
 // capacity).
 template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
@@ -152,13 +160,13 @@ __device__ __forceinline__ void tile_direct(const RunArgs &a, int64_t r0, int64_
       if (e - s > kF32Run * 32) {   // long row in FP32: runs summed in pairs (warp-uniform)
         FPair d = warp_row_dot<ValT, VecT, AccT, DB, XL2, FPair>(a, r, s, e, lane, x, pol_x);
         d = group_sum<32>(d, 0xffffffffu);
-        if (lane == 0) y[r] = (VecT)wvalue(d);
+        if (lane == 0) store_y<VecT, AccT>(a, y, r, (AccT)wvalue(d));
         continue;
       }
     }
     AccT acc = warp_row_dot<ValT, VecT, AccT, DB, XL2, AccT>(a, r, s, e, lane, x, pol_x);
     acc = group_sum<32>(acc, 0xffffffffu);
-    if (lane == 0) y[r] = (VecT)acc;
+    if (lane == 0) store_y<VecT, AccT>(a, y, r, acc);
   }
 }
 
@@ -214,8 +222,8 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile(const RunArgs a) {
       }
     }
     if (row >= r1) return;
-    y[row] = (VecT)tile_row_dot<ValT, VecT, AccT, DB, XL2>(a, sval, sidx, s - a0, e - s, base,
-                                                           x, pol_x);
+    store_y<VecT, AccT>(a, y, row, tile_row_dot<ValT, VecT, AccT, DB, XL2>(a, sval, sidx, s - a0,
+                                                                           e - s, base, x, pol_x));
   } else {
     // oversize tile: a warp per row straight from global memory
     tile_direct<ValT, VecT, AccT, DB, XL2>(a, r0, r1, x, y, pol_x);
@@ -311,8 +319,8 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_pipe(const RunArgs a) {
       const ValT *sval = reinterpret_cast<const ValT *>(stage0 + (size_t)st * stage_bytes);
       const IdxT *sidx = reinterpret_cast<const IdxT *>(stage0 + (size_t)st * stage_bytes + vbytes);
       if (row < r1)
-        y[row] = (VecT)tile_row_dot<ValT, VecT, AccT, DB, XL2>(a, sval, sidx, s - a0, e - s,
-                                                               base, x, pol_x);
+        store_y<VecT, AccT>(a, y, row, tile_row_dot<ValT, VecT, AccT, DB, XL2>(
+                                           a, sval, sidx, s - a0, e - s, base, x, pol_x));
     } else {
       tile_direct<ValT, VecT, AccT, DB, XL2>(a, r0, r1, x, y, pol_x);
     }

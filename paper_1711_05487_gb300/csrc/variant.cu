@@ -53,6 +53,8 @@ RunArgs run_args(const spmv_matrix *h, const void *x, void *y) {
   a.pnl_stride = h->n_rows + 1;
   a.pnl_first = 0;
   a.n_panels = h->pnl_count;
+  a.pnl_tile_cap = h->pnl_tile_cap;
+  a.pnl_tile_rows = h->pnl_tile_rows;
   return a;
 }
 
@@ -153,6 +155,10 @@ void build_bins(spmv_matrix *h, int32_t l_med, int32_t chunk, cudaStream_t s) {
   h->has_bins = true;
 }
 
+int32_t max_tile_elems(spmv_matrix *h, const int32_t *rowptr, int rows, int align,
+                       cudaStream_t s);
+int32_t tile_limit(const spmv_matrix *h, const spmv_variant &v, bool pipe);
+
 // Column panels (xpath = P >= 2): the panel-major copy of the columns and of the values
 // the kernels read (the storage copy, or the FP64 input for double-float storage), built
 // from per-row panel counts and one exclusive scan per panel. Panel p holds the columns
@@ -185,6 +191,22 @@ void build_panels(spmv_matrix *h, int n_panels, cudaStream_t s) {
   CK(cudaStreamSynchronize(s));
   h->pnl_count = n_panels;
   h->pnl_width = (int32_t)w;
+  // staged tiles of the one-thread-per-row passes: the largest of 128, 64, 32 rows whose
+  // largest tile over all panels fits one 48 KB stage (int32 columns)
+  spmv_variant pv{};
+  const int32_t limit = tile_limit(h, pv, false);
+  h->pnl_tile_rows = 0;
+  for (int rows = kTileRows; rows >= 32; rows /= 2) {
+    int32_t m = 0;
+    for (int p = 0; p < n_panels; ++p)
+      m = std::max(m, max_tile_elems(h, h->pnl_rowptr.as<int32_t>() + (int64_t)p * (n + 1), rows,
+                                     8, s));
+    if (m <= limit || rows == 32) {
+      h->pnl_tile_rows = rows;
+      h->pnl_tile_cap = std::min(m, limit);
+      break;
+    }
+  }
 }
 
 // Slice offsets of the sliced-row layout: 32 x the longest row of each 32-row slice, scanned
@@ -232,8 +254,9 @@ int tile_align(const spmv_matrix *h, const spmv_variant &v) {
   return v.index == 1 ? stage_align_bits(h->delta_bits) : 8;
 }
 
-int32_t max_tile_elems(spmv_matrix *h, int rows, int align, cudaStream_t s) {
-  CK(launch_tile_max(h->n_rows, h->rowptr.as<int32_t>(), rows, align, h->small.as<int32_t>(), s));
+int32_t max_tile_elems(spmv_matrix *h, const int32_t *rowptr, int rows, int align,
+                       cudaStream_t s) {
+  CK(launch_tile_max(h->n_rows, rowptr, rows, align, h->small.as<int32_t>(), s));
   int32_t m = 0;
   CK(cudaMemcpyAsync(&m, h->small.p, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -256,7 +279,8 @@ void set_tile_geometry(spmv_matrix *h, const spmv_variant &v, int rows, bool pip
                        cudaStream_t s) {
   h->tile_rows = rows;
   h->tile_pipe = pipe ? 1 : 0;
-  h->tile_cap = std::min(max_tile_elems(h, rows, tile_align(h, v), s), tile_limit(h, v, pipe));
+  h->tile_cap = std::min(max_tile_elems(h, h->rowptr.as<int32_t>(), rows, tile_align(h, v), s),
+                         tile_limit(h, v, pipe));
 }
 
 // Default geometry: the largest of 128, 64, 32 rows per tile whose largest tile fits one
@@ -264,7 +288,7 @@ void set_tile_geometry(spmv_matrix *h, const spmv_variant &v, int rows, bool pip
 void compute_tile_cap(spmv_matrix *h, const spmv_variant &v, cudaStream_t s) {
   const int32_t limit = tile_limit(h, v, false);
   for (int rows = kTileRows; rows >= 32; rows /= 2) {
-    const int32_t m = max_tile_elems(h, rows, tile_align(h, v), s);
+    const int32_t m = max_tile_elems(h, h->rowptr.as<int32_t>(), rows, tile_align(h, v), s);
     if (m <= limit) {
       h->tile_rows = rows;
       h->tile_pipe = 0;
