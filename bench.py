@@ -121,6 +121,23 @@ WORKLOADS = {
 }
 
 
+CALIBRATION = os.path.join(ROOT, "paper_1711_05487_gb300", "data", "calibration_gb300.json")
+
+
+def route_opts() -> dict:
+    """Tune options of the grid-searched setting (Section III-C: thresholds tuned on the target
+    platform, here with the uneven-rows ratio and the row decomposition limits) when the
+    calibration file is present; the library's defaults otherwise."""
+    try:
+        with open(CALIBRATION) as fh:
+            c = json.load(fh)
+        return {"t_imb": float(c["t_imb"]), "t_ml": float(c["t_ml"]), "t_mb": float(c["t_mb"]),
+                "long_row_ratio": float(c["long_ratio"]), "bin_med": int(c["bin_med"]),
+                "bin_chunk": int(c["bin_chunk"])}
+    except (OSError, KeyError, ValueError):
+        return {}
+
+
 def max_over_ranks(ms: float, world: int) -> float:
     """The slowest rank's time (the timed region ends when every replica is done)."""
     if world <= 1:
@@ -257,7 +274,7 @@ def run_ours(args, rank, world):
         knobs = [int(v) for v in args.fixed_variant.split(",")]
         rep = A.tune("fixed", stream=stream, fixed=api.variant(*knobs))
     else:
-        rep = A.tune("profile", stream=stream)
+        rep = A.tune("profile", stream=stream, **route_opts())
     peak, peak_kind = _peaks()
     clocks = ClockSampler(dev)
     clocks.start()
@@ -304,7 +321,7 @@ def run_ours(args, rank, world):
     if not args.quick and os.path.exists(sel_path) and not args.fixed_variant:
         sel = api.Selector.load(sel_path)
         for route, kw in (("learned", dict(selector=sel)), ("features", {})):
-            r_l = A.tune(route, stream=stream, **kw)
+            r_l = A.tune(route, stream=stream, **kw, **route_opts())
             t_l = timed(max(8, args.steps // 4), args.warmup)
             amort[route] = {"t_pre_ms": round(r_l.t_pre_ms, 2), "t_spmv_ms": round(t_l, 5),
                             "classes": r_l.class_names, "variant": list(r_l.variant),
@@ -364,7 +381,7 @@ def run_ours(args, rank, world):
         for st, vt, at in (("df64", "f64", "df64"), ("f32", "f64", "f64"), ("f32", "f64", "df64"),
                            ("bf16", "f64", "df64"), ("f32", "f32", "f32"), ("bf16", "f32", "f32")):
             A.set_precision(st, vt, at, stream=stream)
-            r2 = A.tune("profile", stream=stream)
+            r2 = A.tune("profile", stream=stream, **route_opts())
             xv = x.to(torch.float64 if vt == "f64" else torch.float32)
             yv = torch.empty(m.n_rows, dtype=xv.dtype, device="cuda")
             x_old, y_old = x, y
@@ -400,6 +417,8 @@ def run_ours(args, rank, world):
         "speedup_vs_csr_vector": round(base_ms / ms, 3),
         "paper_protocol": protocol,
         "tune": {"classes": rep.class_names, "variant": list(rep.variant),
+                 "setting": {"source": "calibrated" if route_opts() else "library defaults",
+                             **route_opts()},
                  "classes_fig3_one_pass": fig3_one_pass(rep.p) if rep.p["P_CSR"] > 0 else None,
                  "p_gflops": {k: round(v, 1) for k, v in rep.p.items()},
                  "b_max_gbs": round(rep.b_max_gbs, 1), "t_pre_ms": round(rep.t_pre_ms, 2)},
@@ -457,7 +476,7 @@ def run_batched(args, rank, world):
         A = api.SpmvMatrix.from_csr(m, stream=stream)
         A.set_precision("f32", "f32", "f32", stream=stream)
         if sel is not None:
-            r = A.tune("learned", stream=stream, selector=sel)
+            r = A.tune("learned", stream=stream, selector=sel, **route_opts())
             t_tune += r.t_pre_ms
             by_mlp += r.mode_used == 2
         else:
@@ -514,7 +533,7 @@ def run_batched(args, rank, world):
         # route's judge), at the same work plan
         t_prof = 0.0
         for A in As:
-            t_prof += A.tune("profile", stream=stream).t_pre_ms
+            t_prof += A.tune("profile", stream=stream, **route_opts()).t_pre_ms
         B.close()
         B = api.Batch(As, Xs, Ys, ks, stream=stream)
         B.set_plan(*plan)
@@ -623,7 +642,7 @@ def workload_summary(name, args, world, peak, sel):
     flops = 2.0 * m.nnz
     A.set_variant(stream=stream)
     base_ms = time_spmv(A, x, y, stream, args.steps, args.warmup, world)
-    rep = A.tune("profile", stream=stream)
+    rep = A.tune("profile", stream=stream, **route_opts())
     ms = time_spmv(A, x, y, stream, args.steps, args.warmup, world)
     ab = alg_bytes(m.n_rows, m.n_cols, m.nnz, rep.variant, A.storage, A.vec, A.handle)
     out = {"desc": wl["desc"], "n_rows": m.n_rows, "nnz": m.nnz,
@@ -647,7 +666,7 @@ def workload_summary(name, args, world, peak, sel):
                                  "g_gathers_per_s": round(m.nnz / (t_g * 1e-3) / 1e9, 1),
                                  "frac": round(t_g / ms, 4)}
     if sel is not None:
-        r_l = A.tune("learned", stream=stream, selector=sel)
+        r_l = A.tune("learned", stream=stream, selector=sel, **route_opts())
         t_l = time_spmv(A, x, y, stream, args.steps, args.warmup, world)
         out["learned"] = {"decided_by": "mlp" if r_l.mode_used == 2 else "profile",
                           "margin": round(r_l.margin, 4), "classes": r_l.class_names,
@@ -703,7 +722,7 @@ def run_cg(args, rank, world):
     for name, prec in (("tuned_f64", None), ("tuned_df64", "df64")):
         if prec:
             A.set_precision(prec, "f64", prec)
-        tr = A.tune("profile")
+        tr = A.tune("profile", **route_opts())
         t, rep = solve_runs(A)
         it = max(1, rep["iters"])
         gain = t_plain / max(1, rep_plain["iters"]) - t / it

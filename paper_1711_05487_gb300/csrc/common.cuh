@@ -145,6 +145,30 @@ template <bool XL2> __device__ __forceinline__ float ldx(const float *p, uint64_
   }
 }
 
+// Read-modify-write data touched once (y of a column-panel pass): a coherent load and a
+// store, both with an L2 eviction policy.
+__device__ __forceinline__ double ld_hint(const double *p, uint64_t pol) {
+  double r;
+  asm volatile("ld.global.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ float ld_hint(const float *p, uint64_t pol) {
+  float r;
+  asm volatile("ld.global.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ void st_hint(double *p, double v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_hint(float *p, float v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ int32_t ld_hint_nc(const int32_t *p, uint64_t pol) {
+  int32_t r;
+  asm volatile("ld.global.nc.L2::cache_hint.s32 %0, [%1], %2;" : "=r"(r) : "l"(p), "l"(pol));
+  return r;
+}
+
 // ---------------------------------------------------- vector loads of E values --------
 // Loads E consecutive values starting at an E-aligned index into AccT registers.
 template <typename AccT, bool HINT, int E> struct VLoad;

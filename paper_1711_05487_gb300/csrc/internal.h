@@ -50,6 +50,9 @@ struct RunArgs {
   int32_t tile_rows = 0;             // rows (= threads) per tile: 32, 64 or 128
   int32_t tile_pipe = 0;             // 1: persistent CTAs with two staged tiles in flight
   int32_t y_add = 0;                 // 1: row sums are added to y (later column-panel passes)
+  int32_t rows_once = 0;             // 1: row pointers and y are touched once (column-panel
+                                     // passes): loaded and stored evict-first in the L2, so
+                                     // that the slice of x stays resident
   int32_t f32_chain = 30;            // FP32 accumulation: longest row a thread sums in FP32
                                      // alone (16 when passes add into y: one rounding each)
   int32_t *err = nullptr;            // device error word (bounded waits)

@@ -949,6 +949,7 @@ cudaError_t launch_panels_vs(const spmv_variant &v, const RunArgs &a, cudaStream
       RunArgs ta = pa;
       ta.rowptr = prow;
       ta.y_add = p > 0;
+      ta.rows_once = 1;
       ta.f32_chain = kF32Run;          // each pass also rounds once into y
       ta.tile_cap = a.pnl_tile_cap;
       ta.tile_rows = a.pnl_tile_rows;

@@ -139,12 +139,25 @@ __device__ __forceinline__ SumT warp_row_dot(const RunArgs &a, int64_t r, int s,
   return sum;
 }
 
-// Stores a row's sum, or adds it to y (the later passes of column panels).
+// Stores a row's sum, or adds it to y (the later passes of column panels); a panel pass
+// reads and writes y evict-first.
 template <typename VecT, typename AccT>
 __device__ __forceinline__ void store_y(const RunArgs &a, VecT *__restrict__ y, int64_t row,
                                         AccT v) {
+  if (a.rows_once) {
+    const uint64_t pol = policy_evict_first();
+    if (a.y_add) v = (AccT)ld_hint(y + row, pol) + v;
+    st_hint(y + row, (VecT)v, pol);
+    return;
+  }
   if (a.y_add) y[row] = (VecT)((AccT)y[row] + v);
   else y[row] = (VecT)v;
+}
+
+// A row pointer: read-only path, evict-first in the L2 for a panel pass.
+__device__ __forceinline__ int32_t ld_rowptr(const RunArgs &a, int64_t i) {
+  if (a.rows_once) return ld_hint_nc(a.rowptr + i, policy_evict_first());
+  return __ldg(a.rowptr + i);
 }
 
 // Rows [r0, r1) straight from global memory, a warp per row (tiles larger than the staged
@@ -178,7 +191,7 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile(const RunArgs a) {
   const int rows = (int)blockDim.x;
   const int64_t r0 = (int64_t)blockIdx.x * rows;
   const int64_t r1 = min(r0 + (int64_t)rows, a.n_rows);
-  const int s0 = __ldg(a.rowptr + r0), s1 = __ldg(a.rowptr + r1);
+  const int s0 = ld_rowptr(a, r0), s1 = ld_rowptr(a, r1);
   constexpr int AL = stage_align<DB>();
   const int a0 = s0 & ~(AL - 1);                 // aligned start: the copies are 16-byte units
   const int nc = ((s1 - a0) + AL - 1) & ~(AL - 1);   // staged elements
@@ -209,8 +222,8 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile(const RunArgs a) {
     int s = 0, e = 0;
     int32_t base = 0;
     if (row < r1) {
-      s = __ldg(a.rowptr + row);
-      e = __ldg(a.rowptr + row + 1);
+      s = ld_rowptr(a, row);
+      e = ld_rowptr(a, row + 1);
       if constexpr (DB != 0) base = __ldg(a.dbase + row);
     }
     __syncthreads();   // the barrier is initialised before anyone waits on it
