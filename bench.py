@@ -527,6 +527,12 @@ def run_batched(args, rank, world):
     clocks.stop()
     achieved = nbytes / (ms * 1e-3) / 1e9
     total_nnz = sum(m.nnz for m in mats)
+    # the measured ceiling of the x-row gathers: one 32-byte L2 sector per nonzero for k = 1
+    # and k = 4 (4- and 16-byte rows), two for k = 16 (64-byte rows), at the random-gather
+    # rate of an L2-resident array
+    from paper_1711_05487_gb300 import _abi
+    sectors = sum(m.nnz * (2 if k == 16 else 1) for m, k in zip(mats, ks))
+    t_g = _abi.spmv_probe_gather(4 << 20, 4, sectors, 5)
     learned = None
     if sel is not None:
         # the same batch with every matrix tuned by the profile route instead (the learned
@@ -565,6 +571,8 @@ def run_batched(args, rank, world):
                      "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
                      "peak_kind": peak_kind, "alg_bytes": nbytes},
         "gpu_launches": args.steps * 2,
+        "gather_ceiling": {"x_row_sectors": int(sectors), "probe_ms": round(t_g, 5),
+                           "frac": round(t_g / ms, 4)},
         "learned": learned,
         "clocks": clocks.summary(),
         "gen_s": round(gen_s, 1),
@@ -627,6 +635,7 @@ def workload_summary(name, args, world, peak, sel):
                 "sequential_launches": b["sequential_launches"],
                 "speedup_vs_sequential": b["speedup_vs_sequential"], "plan": b["tune"]["plan"],
                 "learned": b["learned"], "gpu_launches": b["gpu_launches"],
+                "gather_ceiling": b["gather_ceiling"],
                 "clocks": b["clocks"], "gen_s": b["gen_s"]}
     wl = WORKLOADS[name]
     t0 = time.time()

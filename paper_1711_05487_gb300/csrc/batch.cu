@@ -159,15 +159,17 @@ __device__ void warp_rows(const BatchMat &m, int r0, int r1, int lane) {
 
 // K = 16: the four lanes of a quad share a nonzero, each gathering one 16-byte quarter of
 // its x row and keeping 4 accumulators, so a sub-warp of VS lanes has VS / 4 nonzeros of its
-// row in flight (two per quad per step) instead of one 64-byte gather per lane. The quads'
-// sums of one row are added with a fixed shuffle tree; the quad of slot 0 writes the row.
-// FOLD (rows whose FP32 chain per lane would pass kF32Chain roundings): FP32 sums of
-// kF32Run products (eight steps) are added into FP32 pairs, and the quads' pairs are added.
+// row in flight (two per quad per step) instead of one 64-byte gather per lane. The two
+// nonzeros of a step go to two accumulator sets (even and odd steps' halves of the lane's
+// share), two independent FMA chains of half the length; their sum and the quads' sums of
+// one row are added with a fixed shuffle tree; the quad of slot 0 writes the row.
+// FOLD (rows whose chains would pass kF32Chain roundings): each chain's FP32 sums of kF32Run
+// products are added into FP32 pairs, and the quads' pairs are added.
 template <int VS, bool FOLD>
 __device__ __forceinline__ void row_k16(const BatchMat &m, int row, int s, int e, int slot,
                                         int quad, unsigned mask) {
   constexpr int SLOTS = VS / 4;
-  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  float a0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, a1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
   FPair tot[4];
   int steps = 0;
   int j = s + slot;
@@ -176,17 +178,23 @@ __device__ __forceinline__ void row_k16(const BatchMat &m, int row, int s, int e
     const int c0 = __ldg(m.colind + j), c1 = __ldg(m.colind + j + SLOTS);
     const uint4 x0 = ld_nc_u4(m.X + (int64_t)c0 * 16 + quad * 4);
     const uint4 x1 = ld_nc_u4(m.X + (int64_t)c1 * 16 + quad * 4);
-    acc[0] = fmaf(v1, __uint_as_float(x1.x), fmaf(v0, __uint_as_float(x0.x), acc[0]));
-    acc[1] = fmaf(v1, __uint_as_float(x1.y), fmaf(v0, __uint_as_float(x0.y), acc[1]));
-    acc[2] = fmaf(v1, __uint_as_float(x1.z), fmaf(v0, __uint_as_float(x0.z), acc[2]));
-    acc[3] = fmaf(v1, __uint_as_float(x1.w), fmaf(v0, __uint_as_float(x0.w), acc[3]));
+    a0[0] = fmaf(v0, __uint_as_float(x0.x), a0[0]);
+    a0[1] = fmaf(v0, __uint_as_float(x0.y), a0[1]);
+    a0[2] = fmaf(v0, __uint_as_float(x0.z), a0[2]);
+    a0[3] = fmaf(v0, __uint_as_float(x0.w), a0[3]);
+    a1[0] = fmaf(v1, __uint_as_float(x1.x), a1[0]);
+    a1[1] = fmaf(v1, __uint_as_float(x1.y), a1[1]);
+    a1[2] = fmaf(v1, __uint_as_float(x1.z), a1[2]);
+    a1[3] = fmaf(v1, __uint_as_float(x1.w), a1[3]);
     if constexpr (FOLD) {
-      if (++steps == kF32Run / 2) {
+      if (++steps == kF32Run) {
         steps = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          wadd(tot[q], acc[q]);
-          acc[q] = 0.0f;
+          wadd(tot[q], a0[q]);
+          wadd(tot[q], a1[q]);
+          a0[q] = 0.0f;
+          a1[q] = 0.0f;
         }
       }
     }
@@ -194,17 +202,18 @@ __device__ __forceinline__ void row_k16(const BatchMat &m, int row, int s, int e
   if (j < e) {
     const float v0 = __ldg(m.val + j);
     const uint4 x0 = ld_nc_u4(m.X + (int64_t)__ldg(m.colind + j) * 16 + quad * 4);
-    acc[0] = fmaf(v0, __uint_as_float(x0.x), acc[0]);
-    acc[1] = fmaf(v0, __uint_as_float(x0.y), acc[1]);
-    acc[2] = fmaf(v0, __uint_as_float(x0.z), acc[2]);
-    acc[3] = fmaf(v0, __uint_as_float(x0.w), acc[3]);
+    a0[0] = fmaf(v0, __uint_as_float(x0.x), a0[0]);
+    a0[1] = fmaf(v0, __uint_as_float(x0.y), a0[1]);
+    a0[2] = fmaf(v0, __uint_as_float(x0.z), a0[2]);
+    a0[3] = fmaf(v0, __uint_as_float(x0.w), a0[3]);
   }
   float r[4];
   if constexpr (FOLD) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       FPair t = tot[q];
-      wadd(t, acc[q]);
+      wadd(t, a0[q]);
+      wadd(t, a1[q]);
 #pragma unroll
       for (int off = 4; off < VS; off <<= 1) {
         FPair o;
@@ -216,11 +225,11 @@ __device__ __forceinline__ void row_k16(const BatchMat &m, int row, int s, int e
     }
   } else {
 #pragma unroll
+    for (int q = 0; q < 4; ++q) r[q] = a0[q] + a1[q];
+#pragma unroll
     for (int off = 4; off < VS; off <<= 1)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] += __shfl_xor_sync(mask, acc[q], off, VS);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) r[q] = acc[q];
+      for (int q = 0; q < 4; ++q) r[q] += __shfl_xor_sync(mask, r[q], off, VS);
   }
   if (slot == 0)
     *reinterpret_cast<float4 *>(m.Y + (int64_t)row * 16 + quad * 4) =
@@ -235,8 +244,13 @@ __device__ void warp_rows_k16(const BatchMat &m, int r0, int r1, int lane) {
   const unsigned mask = group_mask<VS>();
   for (int row = r0 + lane / VS; row < r1; row += GROUPS) {
     const int s = __ldg(m.rowptr + row), e = __ldg(m.rowptr + row + 1);
-    if (f32_chain_too_long<SLOTS>(e - s, SLOTS)) row_k16<VS, true>(m, row, s, e, slot, quad, mask);
-    else row_k16<VS, false>(m, row, s, e, slot, quad, mask);
+    // a lane's two chains hold about half of its ceil(len / SLOTS) products each, plus the
+    // sum of the two and the levels of the lane reduction
+    const int per_lane = (e - s + SLOTS - 1) / SLOTS;
+    if (f32_chain_too_long<SLOTS>((per_lane + 1) / 2 + 1, 1))
+      row_k16<VS, true>(m, row, s, e, slot, quad, mask);
+    else
+      row_k16<VS, false>(m, row, s, e, slot, quad, mask);
   }
 }
 
