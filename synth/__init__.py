@@ -255,6 +255,17 @@ def uniform_random(n: int, max_per_row: int, seed: int, dtype=np.float64,
     return Csr(n, n_cols, rowptr, colind, val, f"uniform_{max_per_row}_{n}")
 
 
+def same_sign_rows(lengths, n_cols: int, seed: int, dtype=np.float64) -> Csr:
+    """Rows of the given lengths, distinct uniform columns, values uniform in [0.5, 1]: with a
+    positive x every product of a row has the same sign (no cancellation)."""
+    rng = _rng(seed)
+    counts = np.minimum(np.asarray(lengths, dtype=np.int64), n_cols)
+    rowptr = _rowptr_from_counts(counts)
+    colind = _sorted_distinct_columns(counts, n_cols, rng)
+    val = rng.uniform(0.5, 1.0, size=colind.shape[0]).astype(dtype)
+    return Csr(int(counts.shape[0]), n_cols, rowptr, colind, val, f"same_sign_{counts.shape[0]}")
+
+
 def dense_random(n_rows: int, n_cols: int, density: float, seed: int,
                  integer_values: bool = True) -> Csr:
     """Small matrix drawn as a dense mask; integer values keep FP64 sums exact."""

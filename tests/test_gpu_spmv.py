@@ -153,6 +153,61 @@ def test_precisions(api, torch, name, storage, vec, acc):
                        values=stored_values(m.val, storage))
 
 
+SAME_SIGN_LENGTHS = ([0, 1, 15, 16, 17, 29, 30, 31, 33, 63, 64, 65, 127, 129, 500, 2047, 2049,
+                      5000, 40_000] * 4)
+
+
+def test_fp32_accumulation_bound_on_same_sign_long_rows(api, torch):
+    """FP32 accumulation on rows whose products all have one sign and x > 0: the running sum
+    grows with every product, so a plain FP32 chain's roundings add up (a sequential FP32 sum
+    of a 40,000-product row errs by about 4e-6 of the row's sum, outside the 2e-6 bound;
+    checked below with numpy). Every variant keeps every row within the FP32 bound, as do SpMM (k = 4, 16) and
+    the batched launch (k = 1, 4, 16): long chains are summed in runs of 16 FP32 products."""
+    m = synth.same_sign_rows(SAME_SIGN_LENGTHS, 60_000, seed=51, dtype=np.float32)
+    x32 = np.random.default_rng(52).uniform(0.5, 1.0, m.n_cols).astype(np.float32)
+    x64 = x32.astype(np.float64)
+    # the plain FP32 chain this test guards against
+    r = int(np.argmax(np.diff(m.rowptr)))
+    s0, s1 = m.rowptr[r], m.rowptr[r + 1]
+    prod = m.val[s0:s1] * x32[m.colind[s0:s1]]
+    exact = float(np.sum(m.val[s0:s1].astype(np.float64) * x64[m.colind[s0:s1]]))
+    seq = float(np.add.accumulate(prod, dtype=np.float32)[-1])
+    assert abs(seq - exact) / exact > TAU["f32"]
+    A = api.SpmvMatrix.from_csr(m)
+    A.set_precision("f32", "f32", "f32")
+    x = _dev(torch, x32)
+    for v in VARIANTS:
+        A.set_variant(**v)
+        y = A.run(x).double().cpu().numpy()
+        check_spmv(m, x64, y, TAU["f32"], f"same-sign rows {v}")
+    for k in (4, 16):
+        X32 = np.random.default_rng(53 + k).uniform(0.5, 1.0, (m.n_cols, k)).astype(np.float32)
+        A.set_variant(vec=1, vs=4)
+        Y = A.spmm(_dev(torch, X32)).double().cpu().numpy()
+        Yr, Sr = oracle.spmm(m.rowptr, m.colind, m.val, X32.astype(np.float64))
+        check_rows(Y.ravel(), Yr.ravel(), Sr.ravel(), TAU["f32"], f"same-sign spmm k={k}")
+    As, Xs, Ys, X64 = [], [], [], []
+    for k, vs in ((1, 1), (4, 2), (16, 4), (16, 32)):
+        B = api.SpmvMatrix.from_csr(m)
+        B.set_precision("f32", "f32", "f32")
+        B.set_variant(vec=1, vs=vs)
+        X = np.random.default_rng(60 + k + vs).uniform(0.5, 1.0, (m.n_cols, k)).astype(np.float32)
+        As.append(B)
+        Xs.append(_dev(torch, X))
+        Ys.append(torch.full((m.n_rows, k), float("nan"), dtype=torch.float32, device="cuda"))
+        X64.append(X.astype(np.float64))
+    b = api.Batch(As, Xs, Ys, [1, 4, 16, 16])
+    for plan in ((256, 512), (2048, 8192)):
+        b.set_plan(*plan)
+        b.run()
+        torch.cuda.synchronize()
+        for X, Y, k in zip(X64, Ys, (1, 4, 16, 16)):
+            Yr, Sr = oracle.spmm(m.rowptr, m.colind, m.val, X)
+            check_rows(Y.cpu().numpy().astype(np.float64).ravel(), Yr.ravel(), Sr.ravel(),
+                       TAU["f32"], f"same-sign batched k={k} plan {plan}")
+    b.close()
+
+
 def test_unsupported_precision_rejected(api):
     from paper_1711_05487_gb300._abi import SpmvError
     A = api.SpmvMatrix.from_csr(MATS["lap64"])
