@@ -70,7 +70,7 @@ typedef struct {
   int32_t partition; /* 0: one sub-warp per row, rows handed to CTAs by the hardware
                         scheduler; 1: merge-path tiles, long rows split across tiles;
                         2: row decomposition (A = A_short + A_long, Fig. 5): rows under
-                        bin_med nonzeros on sub-warps of vs lanes (2, 4 or 8), rows under
+                        bin_med nonzeros on sub-warps of vs lanes (1, 2, 4 or 8), rows under
                         bin_chunk on one warp each, longer rows in bin_chunk-nonzero
                         chunks summed in FP64 in chunk order. 1 and 2 are the decompositions of
                         Section III-E (IMB); the autotuner picks between them;

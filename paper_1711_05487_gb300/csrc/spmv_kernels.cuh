@@ -783,13 +783,14 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm(const RunArgs a, int off, 
 
 // -------------------------------------------------------------------- k_bins_* ------
 // Row decomposition (IMB, Section III-E's matrix decomposition A = A_short + A_long; Fig. 5):
-//  k_bins_short  - rows shorter than l_med, a sub-warp of VS lanes each, over all rows
+//  k_bins_short  - rows shorter than l_med, a sub-warp of VS lanes (1: a thread) each, over all rows
 //                  (longer rows are skipped: the sub-warp reads their bounds only);
 //  k_bins_warp   - one warp per work item: a medium row (l_med <= length < kBinChunk, from
 //                  the row list) written directly, or a chunk of at most kBinChunk nonzeros
 //                  of a long row whose sum goes to an FP64 partial slot; with FP32
 //                  accumulation the lanes add runs of 16 products into FP32 pairs;
-//  k_bins_fixup  - each long row's partials added in chunk order (reproducible, no atomics).
+//  k_bins_fixup  - each long row's partials added by one warp in a fixed order
+//                  (reproducible, no atomics).
 // One sub-warp's share of elements [s, e) of row `row`, whose decode (delta columns of DB
 // bits) starts from column `running`.
 template <typename ValT, typename VecT, typename AccT, int VS, int DB, bool XL2, typename SumT>
@@ -862,18 +863,26 @@ __global__ void __launch_bounds__(kRowThreads) k_bins_warp(const RunArgs a) {
   }
 }
 
+// One warp per long row: the lanes read the row's partials 32 at a time (lane j takes chunks
+// j, j + 32, ... in order), then a fixed shuffle tree adds the lanes' sums; FP64 throughout,
+// the same order on every run.
 template <typename VecT>
 __global__ void k_bins_fixup(const RunArgs a) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.bin_n_long) return;
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x & 31;
+  if (i >= a.bin_n_long) return;                  // uniform over the warp
   double t = 0.0;
-  for (int c = a.bin_long_first[i]; c < a.bin_long_first[i + 1]; ++c) t += a.bin_partials[c];
-  static_cast<VecT *>(a.y)[a.bin_long_rows[i]] = (VecT)t;
+  for (int c = a.bin_long_first[i] + lane; c < a.bin_long_first[i + 1]; c += 32)
+    t += a.bin_partials[c];
+  t = group_sum<32>(t, 0xffffffffu);
+  if (lane == 0) static_cast<VecT *>(a.y)[a.bin_long_rows[i]] = (VecT)t;
 }
 
 template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
 void launch_bins_k(const RunArgs &a, cudaStream_t s) {
   switch (a.bin_vs_short) {
+    case 1: k_bins_short<ValT, VecT, AccT, 1, DB, XL2><<<(unsigned)((a.n_rows + 255) / 256),
+                                                         kRowThreads, 0, s>>>(a); break;
     case 2: k_bins_short<ValT, VecT, AccT, 2, DB, XL2><<<(unsigned)((a.n_rows + 127) / 128),
                                                          kRowThreads, 0, s>>>(a); break;
     case 8: k_bins_short<ValT, VecT, AccT, 8, DB, XL2><<<(unsigned)((a.n_rows + 31) / 32),
@@ -902,7 +911,7 @@ cudaError_t launch_bins(int db, bool xl2, const RunArgs &a, cudaStream_t s) {
     else launch_bins_k<ValT, VecT, AccT, 0, false>(a, s);
   }
   if (a.bin_n_long > 0)
-    k_bins_fixup<VecT><<<(unsigned)((a.bin_n_long + 255) / 256), 256, 0, s>>>(a);
+    k_bins_fixup<VecT><<<(unsigned)((a.bin_n_long * 32 + 255) / 256), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -471,10 +471,10 @@ void autotune_vs(spmv_matrix *h, spmv_variant &v, int reps, int32_t bin_med, int
   CK(launch_fill_const(x.p, h->vec, h->n_cols, 1.0, s));
   if (v.partition != 0) {
     // IMB's decomposition family: merge-path tiles, or the row decomposition with short
-    // rows on sub-warps of 2, 4 or 8 lanes; the fastest is kept
+    // rows on one thread or sub-warps of 2, 4 or 8 lanes; the fastest is kept
     spmv_variant best_v = v;
     float best_t = 1e30f;
-    const int cand[4][2] = {{1, 0}, {2, 2}, {2, 4}, {2, 8}};
+    const int cand[5][2] = {{1, 0}, {2, 1}, {2, 2}, {2, 4}, {2, 8}};
     for (const auto &c : cand) {
       spmv_variant t = v;
       t.partition = c[0];

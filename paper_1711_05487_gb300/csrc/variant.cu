@@ -352,7 +352,7 @@ void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
   } else if (v.partition == 2) {
     if (v.index == 1) build_delta(h, s);
     v.vec = 1;
-    if (v.vs != 2 && v.vs != 4 && v.vs != 8) v.vs = 4;   // short rows' sub-warp width
+    if (v.vs != 1 && v.vs != 2 && v.vs != 4 && v.vs != 8) v.vs = 4;   // short rows' width
     v.tile_rows = 0;
     v.tile_pipe = 0;
     h->bin_vs_short = v.vs;
@@ -388,7 +388,8 @@ void prepare_variant(spmv_matrix *h, spmv_variant &v, cudaStream_t s) {
 bool valid_variant(const spmv_variant &v) {
   if (v.partition < 0 || v.partition > 3) return false;
   if (v.partition == 3 && v.vs != 0 && v.vs != 1) return false;
-  if (v.partition == 2 && v.vs != 0 && v.vs != 2 && v.vs != 4 && v.vs != 8) return false;
+  if (v.partition == 2 && v.vs != 0 && v.vs != 1 && v.vs != 2 && v.vs != 4 && v.vs != 8)
+    return false;
   if (v.index != 0 && v.index != 1) return false;
   if (v.xpath < 0 || v.xpath > kMaxPanels) return false;
   if (v.xpath >= 2 && v.vs != 0 && v.vs != 1 && v.vs != 2 && v.vs != 4 && v.vs != 8)

@@ -47,8 +47,8 @@ VARIANTS = (
     + [dict(xpath=1, vs=8), dict(vec=1, xpath=1, vs=4),
        dict(index=1, vec=1, xpath=1, vs=4)]                            # ML (+ joint)
     + [dict(partition=1), dict(partition=1, xpath=1)]                  # IMB
-    + [dict(partition=2, vs=w) for w in (2, 4, 8)] + [dict(partition=2, xpath=1)]
-    + [dict(partition=2, index=1, vs=w) for w in (2, 8)]                # MB + IMB
+    + [dict(partition=2, vs=w) for w in (1, 2, 4, 8)] + [dict(partition=2, xpath=1)]
+    + [dict(partition=2, index=1, vs=w) for w in (1, 2, 8)]             # MB + IMB
     + [dict(partition=2, index=1, xpath=1)]
     + [dict(vec=1, vs=1, tile_rows=r, tile_pipe=p) for r in (32, 64, 128) for p in (0, 1)]
     + [dict(index=1, vec=1, vs=1, tile_rows=r, tile_pipe=p, xpath=p) for r in (32, 128)
