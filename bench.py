@@ -213,7 +213,7 @@ def launches_per_spmv(A, variant) -> int:
         return 1 + (n_tiles > 1)                           # tiles, then the carry fixup
     if variant[0] == 2:
         n_med, n_long, n_ch = _abi.spmv_get_row_bins(A.handle)
-        return 1 + (n_med + n_ch > 0) + (n_long > 0)       # short rows, warps, fixup
+        return 1 + (n_long > 0)                            # rows and warp items, fixup
     return 1
 
 

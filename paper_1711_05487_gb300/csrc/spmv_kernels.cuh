@@ -783,9 +783,10 @@ __global__ void __launch_bounds__(kRowThreads) k_spmm(const RunArgs a, int off, 
 
 // -------------------------------------------------------------------- k_bins_* ------
 // Row decomposition (IMB, Section III-E's matrix decomposition A = A_short + A_long; Fig. 5):
-//  k_bins_short  - rows shorter than l_med, a sub-warp of VS lanes (1: a thread) each, over all rows
-//                  (longer rows are skipped: the sub-warp reads their bounds only);
-//  k_bins_warp   - one warp per work item: a medium row (l_med <= length < kBinChunk, from
+//  k_bins        - one launch of two kinds of blocks: short rows (shorter than l_med), a
+//                  sub-warp of VS lanes (1: a thread) each, over all rows (longer rows are
+//                  skipped: the sub-warp reads their bounds only), and warp items,
+//                  one warp per work item: a medium row (l_med <= length < kBinChunk, from
 //                  the row list) written directly, or a chunk of at most kBinChunk nonzeros
 //                  of a long row whose sum goes to an FP64 partial slot; with FP32
 //                  accumulation the lanes add runs of 16 products into FP32 pairs;
@@ -811,11 +812,12 @@ __device__ __forceinline__ SumT bins_range_dot(const RunArgs &a, int64_t row, in
   }
 }
 
+// Short rows of row block `blk` (kRowThreads / VS rows).
 template <typename ValT, typename VecT, typename AccT, int VS, int DB, bool XL2>
-__global__ void __launch_bounds__(kRowThreads) k_bins_short(const RunArgs a) {
+__device__ __forceinline__ void bins_short_block(const RunArgs &a, int64_t blk) {
   constexpr int GROUPS = kRowThreads / VS;
   const int lane = threadIdx.x & (VS - 1);
-  const int64_t row = (int64_t)blockIdx.x * GROUPS + threadIdx.x / VS;
+  const int64_t row = blk * GROUPS + threadIdx.x / VS;
   if (row >= a.n_rows) return;
   const int s = __ldg(a.rowptr + row), e = __ldg(a.rowptr + row + 1);
   if (e - s >= a.bin_l_med) return;
@@ -837,11 +839,12 @@ __global__ void __launch_bounds__(kRowThreads) k_bins_short(const RunArgs a) {
   if (lane == 0) static_cast<VecT *>(a.y)[row] = (VecT)sum;
 }
 
+// Warp items of block `blk` (kRowThreads / 32 items: long-row chunks first, then medium rows).
 template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
-__global__ void __launch_bounds__(kRowThreads) k_bins_warp(const RunArgs a) {
+__device__ __forceinline__ void bins_warp_block(const RunArgs &a, int64_t blk) {
   using WS = typename WideOf<AccT>::type;   // FP32 runs are summed in FP32 pairs
   const int lane = threadIdx.x & 31;
-  const int64_t item = ((int64_t)blockIdx.x * kRowThreads + threadIdx.x) / 32;
+  const int64_t item = (blk * kRowThreads + threadIdx.x) / 32;
   if (item >= a.bin_n_med + a.bin_n_chunks) return;
   uint64_t pol_s = policy_evict_first(), pol_x = 0;
   if constexpr (XL2) pol_x = policy_evict_last();
@@ -863,6 +866,19 @@ __global__ void __launch_bounds__(kRowThreads) k_bins_warp(const RunArgs a) {
   }
 }
 
+// The row decomposition in one launch: g_warp blocks of warp items and g_short blocks of
+// short rows, the short blocks spread evenly among the others (block b is short block j
+// when floor((b + 1) g_short / B) > floor(b g_short / B) = j, B = g_warp + g_short), so that
+// the latency-bound short rows run beside the gather-bound long ones instead of after them.
+template <typename ValT, typename VecT, typename AccT, int VS, int DB, bool XL2>
+__global__ void __launch_bounds__(kRowThreads) k_bins(const RunArgs a, int64_t g_warp,
+                                                      int64_t g_short) {
+  const int64_t B = g_warp + g_short, b = blockIdx.x;
+  const int64_t j0 = b * g_short / B, j1 = (b + 1) * g_short / B;
+  if (j1 > j0) bins_short_block<ValT, VecT, AccT, VS, DB, XL2>(a, j0);
+  else bins_warp_block<ValT, VecT, AccT, DB, XL2>(a, b - j0);
+}
+
 // One warp per long row: the lanes read the row's partials 32 at a time (lane j takes chunks
 // j, j + 32, ... in order), then a fixed shuffle tree adds the lanes' sums; FP64 throughout,
 // the same order on every run.
@@ -878,22 +894,23 @@ __global__ void k_bins_fixup(const RunArgs a) {
   if (lane == 0) static_cast<VecT *>(a.y)[a.bin_long_rows[i]] = (VecT)t;
 }
 
+template <typename ValT, typename VecT, typename AccT, int VS, int DB, bool XL2>
+void launch_bins_vs(const RunArgs &a, cudaStream_t s) {
+  constexpr int GROUPS = kRowThreads / VS;
+  const int64_t items = a.bin_n_med + a.bin_n_chunks;
+  const int64_t g_warp = (items * 32 + kRowThreads - 1) / kRowThreads;
+  const int64_t g_short = (a.n_rows + GROUPS - 1) / GROUPS;
+  k_bins<ValT, VecT, AccT, VS, DB, XL2><<<(unsigned)(g_warp + g_short), kRowThreads, 0, s>>>(
+      a, g_warp, g_short);
+}
+
 template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
 void launch_bins_k(const RunArgs &a, cudaStream_t s) {
   switch (a.bin_vs_short) {
-    case 1: k_bins_short<ValT, VecT, AccT, 1, DB, XL2><<<(unsigned)((a.n_rows + 255) / 256),
-                                                         kRowThreads, 0, s>>>(a); break;
-    case 2: k_bins_short<ValT, VecT, AccT, 2, DB, XL2><<<(unsigned)((a.n_rows + 127) / 128),
-                                                         kRowThreads, 0, s>>>(a); break;
-    case 8: k_bins_short<ValT, VecT, AccT, 8, DB, XL2><<<(unsigned)((a.n_rows + 31) / 32),
-                                                         kRowThreads, 0, s>>>(a); break;
-    default: k_bins_short<ValT, VecT, AccT, 4, DB, XL2><<<(unsigned)((a.n_rows + 63) / 64),
-                                                          kRowThreads, 0, s>>>(a); break;
-  }
-  const int64_t items = a.bin_n_med + a.bin_n_chunks;
-  if (items > 0) {
-    const unsigned g = (unsigned)((items * 32 + kRowThreads - 1) / kRowThreads);
-    k_bins_warp<ValT, VecT, AccT, DB, XL2><<<g, kRowThreads, 0, s>>>(a);
+    case 1: launch_bins_vs<ValT, VecT, AccT, 1, DB, XL2>(a, s); break;
+    case 2: launch_bins_vs<ValT, VecT, AccT, 2, DB, XL2>(a, s); break;
+    case 8: launch_bins_vs<ValT, VecT, AccT, 8, DB, XL2>(a, s); break;
+    default: launch_bins_vs<ValT, VecT, AccT, 4, DB, XL2>(a, s); break;
   }
 }
 
