@@ -614,10 +614,12 @@ def time_spmv(A, x, y, stream, K, W, world):
 
 def fig3_one_pass(p: dict) -> list:
     """The class set of Fig. 3's rules on the first profiling pass alone (the paper's
-    classifier), beside the two-pass set the profile route installs."""
+    classifier), beside the two-pass set the profile route installs; same thresholds."""
     from paper_1711_05487_gb300 import _abi
     v = np.array([p[k] for k in ("P_CSR", "P_MB", "P_ML", "P_IMB", "P_CMP", "P_peak")])
-    return _names(_abi.spmv_classify(v.ctypes.data))
+    o = route_opts()
+    thr = (o["t_imb"], o["t_ml"], o["t_mb"]) if o else (1.24, 1.25, 0.75)
+    return _names(_abi.spmv_classify(v.ctypes.data, *thr))
 
 
 def workload_summary(name, args, world, peak, sel):

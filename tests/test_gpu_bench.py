@@ -40,6 +40,13 @@ def test_gpu_arm_json_line():
     assert 0 < e2e["value"]
     assert d["gpu_launches"] >= d["steps"]
     assert "sm_mhz" in d["clocks"] and "reasons" in d["clocks"]
+    t = d["tune"]
+    # the grid-searched setting the profile route ran with, and Fig. 3's one-pass class set
+    # beside the two-pass one
+    assert t["setting"]["source"] in ("calibrated", "library defaults")
+    assert set(t["classes_fig3_one_pass"]) <= {"MB", "ML", "IMB", "CMP"}
+    # the second pass only adds classes to the first pass's set
+    assert set(t["classes"]) >= set(t["classes_fig3_one_pass"])
     pp = d["paper_protocol"]
     assert pp["runs"] == 5 and pp["spmvs_per_run"] == 128 and len(pp["gflops_per_run"]) == 5
     assert min(pp["gflops_per_run"]) - 0.1 <= pp["gflops_harmonic_mean"] <= \
