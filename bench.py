@@ -394,6 +394,23 @@ def run_ours(args, rank, world):
                 "variant": list(r2.variant), "classes": r2.class_names,
                 "frac_hbm": round(b2 / (t2 * 1e-3) / 1e9 / peak, 3)}
         A.set_precision("f64", "f64", "f64", stream=stream)
+    fp64_pipe = None
+    if storage == 0:
+        # the FP64 pipe's ceiling measured now by the register-only FMA probe (4 chains per
+        # thread, 32 warps per SM); the SpMV spends one FMA per nonzero, plus one add per row
+        # where delta-coded tile rows are summed in two chains
+        from paper_1711_05487_gb300 import _abi
+        r_fma = _abi.spmv_probe_fma(8, 4, 32, 5, stream.cuda_stream)
+        v = rep.variant
+        adds = m.n_rows if (v[0] == 0 and v[1] != 0 and v[4] == 1) else 0
+        ops = m.nnz + adds
+        fp64_pipe = {"probe_gfma_per_s": round(r_fma / 1e9, 1),
+                     "probe": "spmv_probe_fma(8 bytes, 4 chains, 32 warps per SM)",
+                     "fp64_ops_per_spmv": int(ops), "dfma": int(m.nnz), "dadd": int(adds),
+                     "achieved_g_ops_per_s": round(ops / (ms * 1e-3) / 1e9, 1),
+                     "t_min_ms": round(ops / r_fma * 1e3, 5),
+                     "frac": round(ops / (ms * 1e-3) / r_fma, 4),
+                     "frac_of_nominal_625_gfma": round(ops / (ms * 1e-3) / 625e9, 4)}
     out = {
         "metric": "SpMV GFLOP/s (2*nnz/t), adaptive (profile-guided) vs plain CSR-vector",
         "value": round(value, 2),
@@ -437,10 +454,7 @@ def run_ours(args, rank, world):
         "precision_variants": extra,
         "variant_sweep": sweep,
         "amortization": amort,
-        "fp64_pipe": None if storage != 0 else {
-            "gfma_per_s": round(m.nnz / (ms * 1e-3) / 1e9, 1),
-            "frac_of_nominal_625_gfma": round(m.nnz / (ms * 1e-3) / 625e9, 3),
-            "frac_of_measured_597_gfma": round(m.nnz / (ms * 1e-3) / 597e9, 3)},
+        "fp64_pipe": fp64_pipe,
         "clocks": clocks.summary(),
         "gen_s": round(gen_s, 1),
     }
@@ -975,6 +989,9 @@ def main():
     ap.add_argument("--probe-gather", action="store_true",
                     help="print the random-gather ceiling for x sizes from 4 MB to 1 GB (one "
                          "JSON line per size) and exit")
+    ap.add_argument("--probe-fma", action="store_true",
+                    help="print the FP64 and FP32 FMA rates of register-only chains by chains "
+                         "per thread and warps per SM (one JSON line each) and exit")
     ap.add_argument("--fixed-variant", default=None,
                     help="install this variant instead of tuning: partition,index,xpath,vec,"
                          "vs,tile_rows,tile_pipe")
@@ -993,6 +1010,18 @@ def main():
                               "gathers": count, "ms": round(ms, 5),
                               "g_gathers_per_s": round(count / (ms * 1e-3) / 1e9, 1)}),
                   flush=True)
+        return
+    if args.probe_fma:
+        import torch
+
+        from paper_1711_05487_gb300 import _abi
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        for eb in (8, 4):
+            for w in (4, 8, 16, 24, 32, 48, 64):
+                for c in (1, 2, 4):
+                    r = _abi.spmv_probe_fma(eb, c, w, 5)
+                    print(json.dumps({"elem_bytes": eb, "chains": c, "warps_per_sm": w,
+                                      "g_fma_per_s": round(r / 1e9, 1)}), flush=True)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

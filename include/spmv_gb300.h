@@ -347,6 +347,15 @@ spmv_status spmv_probe_bandwidth(double *hbm_gbs, double *l2_gbs);
 spmv_status spmv_probe_gather(int64_t n_x, int32_t elem_bytes, int64_t count, int32_t reps,
                               double *ms, spmv_stream_t stream);
 
+/* FMA throughput of the current device (not in the paper; the measured bound of a kernel
+ * that spends one FMA per nonzero, which on GB300's narrow FP64 pipe is the native-FP64
+ * SpMV's bound): fused multiply-adds per second, best of three runs of reps launches, of a
+ * register-only kernel in which every thread runs `chains` independent FMA chains (1, 2, 4
+ * or 8) of elem_bytes (8: FP64, 4: FP32) with warps_per_sm warps on each SM (1 to 32, or an
+ * even count up to 64). Synchronizes. Errors: SPMV_ERR_ARG, SPMV_ERR_CUDA. */
+spmv_status spmv_probe_fma(int32_t elem_bytes, int32_t chains, int32_t warps_per_sm,
+                           int32_t reps, double *fma_per_s, spmv_stream_t stream);
+
 /* Fig. 3 on a P-vector (csr, mb, ml, imb, cmp, peak); pure function. */
 uint32_t spmv_classify(const double *p, double t_imb, double t_ml, double t_mb);
 

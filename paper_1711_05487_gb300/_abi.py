@@ -119,6 +119,7 @@ _DECL = {
     "spmv_profile_kernel": (_I32, [_P, _I32, _P, _P, _P]),
     "spmv_probe_bandwidth": (_I32, [ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "spmv_probe_gather": (_I32, [_I64, _I32, _I64, _I32, ctypes.POINTER(_D), _P]),
+    "spmv_probe_fma": (_I32, [_I32, _I32, _I32, _I32, ctypes.POINTER(_D), _P]),
     "spmv_classify": (_U32, [_P, _D, _D, _D]),
     "spmv_classify2": (_U32, [_P, _P, _D, _D, _D]),
     "spmv_variant_for_classes": (None, [_U32, _D, _D, _D, ctypes.POINTER(spmv_variant)]),
@@ -308,6 +309,14 @@ def spmv_probe_gather(n_x, elem_bytes, count, reps=5, stream=0):
     ms = _D()
     _call("spmv_probe_gather", n_x, elem_bytes, count, reps, ctypes.byref(ms), stream)
     return ms.value
+
+
+def spmv_probe_fma(elem_bytes, chains, warps_per_sm, reps=5, stream=0):
+    """Fused multiply-adds per second of a register-only kernel with `chains` independent
+    chains per thread and warps_per_sm warps per SM (elem_bytes 8: FP64, 4: FP32)."""
+    r = _D()
+    _call("spmv_probe_fma", elem_bytes, chains, warps_per_sm, reps, ctypes.byref(r), stream)
+    return r.value
 
 
 def spmv_classify(p_host, t_imb=1.24, t_ml=1.25, t_mb=0.75) -> int:

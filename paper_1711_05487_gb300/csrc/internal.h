@@ -272,6 +272,9 @@ cudaError_t launch_selftest_wait(uint64_t limit_ns, int32_t *err, cudaStream_t s
 // Bandwidth probe
 cudaError_t launch_gather_probe(const void *x, int32_t elem_bytes, int64_t n_x, int64_t count,
                                 unsigned long long *sink, cudaStream_t s);
+cudaError_t launch_fma_probe(int32_t elem_bytes, int32_t chains, int32_t warps_per_sm,
+                             int32_t fmas_per_thread, int64_t *n_threads,
+                             unsigned long long *sink, cudaStream_t s);
 cudaError_t launch_read_probe(const void *buf, int64_t bytes, int reps,
                               unsigned long long *sink, cudaStream_t s);
 

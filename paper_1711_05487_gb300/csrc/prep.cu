@@ -724,6 +724,52 @@ cudaError_t launch_gather_probe(const void *x, int32_t elem_bytes, int64_t n_x, 
   return cudaGetLastError();
 }
 
+// FMA throughput probe: every thread runs C independent chains a <- fma(a, b, c) from
+// registers (b and c are kernel arguments, so nothing folds); the chains' sum is stored
+// only if it equals an impossible value. Blocks of 32 threads (64 above 32 warps per SM)
+// so that warps_per_sm warps land on each SM.
+template <typename T, int C>
+__global__ void k_fma_probe(T b, T c, int32_t iters, unsigned long long *sink) {
+  T a[C];
+  const T t = (T)(blockIdx.x * blockDim.x + threadIdx.x) * (T)1e-9;
+#pragma unroll
+  for (int i = 0; i < C; ++i) a[i] = t + (T)i;
+  for (int32_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < C; ++i) a[i] = fma(a[i], b, c);
+  }
+  T sum = 0;
+#pragma unroll
+  for (int i = 0; i < C; ++i) sum += a[i];
+  if (sum == (T)-1234.5) *sink = 1;
+}
+
+template <typename T>
+cudaError_t launch_fma_probe_t(int32_t chains, int64_t blocks, int threads, int32_t fmas,
+                               unsigned long long *sink, cudaStream_t s) {
+  const T b = (T)0.999999, c = (T)1e-7;
+  switch (chains) {
+    case 1: k_fma_probe<T, 1><<<(unsigned)blocks, threads, 0, s>>>(b, c, fmas, sink); break;
+    case 2: k_fma_probe<T, 2><<<(unsigned)blocks, threads, 0, s>>>(b, c, fmas / 2, sink); break;
+    case 4: k_fma_probe<T, 4><<<(unsigned)blocks, threads, 0, s>>>(b, c, fmas / 4, sink); break;
+    default: k_fma_probe<T, 8><<<(unsigned)blocks, threads, 0, s>>>(b, c, fmas / 8, sink); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fma_probe(int32_t elem_bytes, int32_t chains, int32_t warps_per_sm,
+                             int32_t fmas_per_thread, int64_t *n_threads,
+                             unsigned long long *sink, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = warps_per_sm <= 32 ? 32 : 64;
+  const int64_t blocks = (int64_t)sms * warps_per_sm * 32 / threads;
+  *n_threads = blocks * threads;
+  return elem_bytes == 8 ? launch_fma_probe_t<double>(chains, blocks, threads, fmas_per_thread, sink, s)
+                         : launch_fma_probe_t<float>(chains, blocks, threads, fmas_per_thread, sink, s);
+}
+
 // ------------------------------------------------------------ row decomposition ------
 // Per row: med = 1 if l_med <= length < chunk, lng = 1 if length >= chunk, nch = the long
 // row's chunk count. Exclusive scans of the three give each row's place in the lists.

@@ -251,11 +251,15 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile_df(const RunArgs a) {
     }
     c = base;   // restart the delta decode for the FP64 pass
   }
-  // FP64 FMAs in element order, as the FP64-accumulating tile kernel computes the row
-  double acc = 0.0;
-  for (int k = 0; k < len; ++k)
-    acc = fma(widen<double>(val[s + k]), (double)ldx<XL2>(x + column(k), pol_x), acc);
-  y[row] = (VecT)acc;
+  // FP64 FMAs in the FP64-accumulating tile kernel's order: element order, in the two
+  // chains of fp64_chain_of when the columns are delta-coded
+  double acc = 0.0, acc1 = 0.0;
+  for (int k = 0; k < len; ++k) {
+    const double p = widen<double>(val[s + k]), xk = (double)ldx<XL2>(x + column(k), pol_x);
+    if (DB != 0 && fp64_chain_of(k, len)) acc1 = fma(p, xk, acc1);
+    else acc = fma(p, xk, acc);
+  }
+  y[row] = (VecT)(DB != 0 ? acc + acc1 : acc);
 }
 
 namespace {

@@ -785,6 +785,30 @@ spmv_status spmv_probe_gather(int64_t n_x, int32_t elem_bytes, int64_t count, in
   });
 }
 
+spmv_status spmv_probe_fma(int32_t elem_bytes, int32_t chains, int32_t warps_per_sm,
+                           int32_t reps, double *fma_per_s, spmv_stream_t stream) {
+  if (!fma_per_s || (elem_bytes != 4 && elem_bytes != 8) || reps < 1 ||
+      (chains != 1 && chains != 2 && chains != 4 && chains != 8) || warps_per_sm < 1 ||
+      warps_per_sm > 64 || (warps_per_sm > 32 && warps_per_sm % 2 != 0))
+    return SPMV_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  return guarded([&]() -> spmv_status {
+    constexpr int32_t kFmas = 16384;   // per thread and launch
+    DevBuf sink;
+    sink.alloc(8, 8, s, true);
+    int64_t n_threads = 0;
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r)
+      best = std::min(best, time_launches([&]() {
+        return launch_fma_probe(elem_bytes, chains, warps_per_sm, kFmas, &n_threads,
+                                sink.as<unsigned long long>(), s);
+      }, reps, s));
+    CK(cudaStreamSynchronize(s));
+    *fma_per_s = (double)n_threads * kFmas / (best * 1e-3);
+    return SPMV_OK;
+  });
+}
+
 uint32_t spmv_classify(const double *p, double t_imb, double t_ml, double t_mb) {
   if (!p) return 0;
   return classify(p, t_imb, t_ml, t_mb);

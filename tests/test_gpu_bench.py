@@ -47,6 +47,11 @@ def test_gpu_arm_json_line():
     assert set(t["classes_fig3_one_pass"]) <= {"MB", "ML", "IMB", "CMP"}
     # the second pass only adds classes to the first pass's set
     assert set(t["classes"]) >= set(t["classes_fig3_one_pass"])
+    # FP64 arithmetic: the FP64 pipe's ceiling measured by the FMA probe in the same run
+    fp = d["fp64_pipe"]
+    assert fp["probe_gfma_per_s"] > 0 and fp["fp64_ops_per_spmv"] >= nnz
+    assert fp["frac"] == pytest.approx(fp["achieved_g_ops_per_s"] / fp["probe_gfma_per_s"],
+                                       rel=2e-2)
     pp = d["paper_protocol"]
     assert pp["runs"] == 5 and pp["spmvs_per_run"] == 128 and len(pp["gflops_per_run"]) == 5
     assert min(pp["gflops_per_run"]) - 0.1 <= pp["gflops_harmonic_mean"] <= \

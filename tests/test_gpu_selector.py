@@ -114,6 +114,24 @@ def test_gather_probe_is_plausible(abi):
         abi.spmv_probe_gather(1 << 32, 4, n)
 
 
+def test_fma_probe_is_plausible(abi):
+    """Register-only FMA chains: FP32 FMAs retire faster than FP64 ones, each rate stays
+    below what the device's SMs could issue at 128 FMA lanes per clock at 2.5 GHz, and the
+    FP64 rate with one chain and 16 warps per SM is within a third of the rate with four
+    chains and 32 warps (the narrow FP64 pipe needs little parallelism to fill)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    f64 = abi.spmv_probe_fma(8, 4, 32, reps=3)
+    f64_1 = abi.spmv_probe_fma(8, 1, 16, reps=3)
+    f32 = abi.spmv_probe_fma(4, 4, 32, reps=3)
+    cap = sms * 128 * 2.5e9
+    assert 1e9 < f64 < f32 < cap
+    assert f64_1 > 0.67 * f64
+    for bad in ((8, 3, 32), (8, 4, 0), (8, 4, 65), (8, 4, 33), (2, 4, 32)):
+        with pytest.raises(abi.SpmvError):
+            abi.spmv_probe_fma(*bad)
+
+
 def test_profile_report_and_cta_times(api, torch):
     """spmv_profile: P_MB and P_peak equal the oracle's bounds at the reported B_max (the
     L2 rate for a cache-fitting working set, else HBM: the footnote's reading), the timed
