@@ -111,9 +111,6 @@ def _declare(L):
     L.oracle_panel_width.restype = ctypes.c_int32
     L.oracle_col_panels.argtypes = [_I64, _I64, _P, _P, ctypes.c_int32, _P, _P]
     L.oracle_col_panels.restype = None
-    L.oracle_panel_stage_order.argtypes = [_I64, ctypes.c_int32, _P, ctypes.c_int32,
-                                           ctypes.c_int32, _P]
-    L.oracle_panel_stage_order.restype = None
     L.oracle_merge_path.argtypes = [_I64, _I64, _P, _I64, _P]
     L.oracle_merge_path.restype = None
     L.oracle_features.argtypes = [_I64, _I64, _P, _P, _I64, _I64, _I64, _P, _P]
@@ -259,18 +256,6 @@ def col_panels(rowptr, colind, n_cols: int, n_panels: int):
     perm = np.empty(max(ci.shape[0], 1), np.int32)
     lib().oracle_col_panels(n, int(n_cols), _p(rp), _p(ci), int(n_panels), _p(prow), _p(perm))
     return prow, perm[:ci.shape[0]], panel_width(n_cols, n_panels)
-
-
-def panel_stage_order(prow, tile_rows: int, tile_cap: int):
-    """src_of of the staged order of a column-panel copy with row pointers prow (n_panels,
-    n_rows + 1): the element stored at j is the CSR-order copy's element src_of[j]."""
-    pr = _c(prow, np.int32)
-    n_panels, n1 = pr.shape
-    total = int(pr[-1, -1]) if n_panels else 0
-    src = np.empty(max(total, 1), np.int64)
-    lib().oracle_panel_stage_order(n1 - 1, n_panels, _p(pr), int(tile_rows), int(tile_cap),
-                                   _p(src))
-    return src[:total]
 
 
 def spmv_static(rowptr, colind, val, x, n_threads: int):

@@ -21,8 +21,6 @@
  *     nnz-balanced work split)
  *   - row decomposition into short, medium and chunked long rows (Section III-E, IMB:
  *     the matrix decomposition of Fig. 5)
- *   - column panels of x and the panel copy's staged order (Section III-E, ML: make the
- *     x accesses hit in cache; the staged order is a layout of this library)
  *   - Table I matrix features                (Section III-D)
  *   - P_MB and P_peak bounds                 (Section III-B)
  *   - Classify rule set                      (Section III-C, Fig. 3)
@@ -392,43 +390,6 @@ void oracle_col_panels(int64_t n_rows, int64_t n_cols, const int32_t *rowptr,
         if (colind[j] >= lo && colind[j] < hi) perm[k++] = (int32_t)j;
     }
     prow[(int64_t)p * (n_rows + 1) + n_rows] = (int32_t)k;
-  }
-}
-
-/* Stored order of a column-panel copy that the one-thread-per-row passes stage tile by tile
- * (a layout of this library, not of the paper: it changes where elements sit, not which
- * products are summed or in which order). Rows are cut into tiles of tile_rows rows (a
- * multiple of 32). A tile is staged when its span, counted in whole 8-element units from
- * its first element rounded down to a multiple of 8, holds at most tile_cap elements.
- * Inside a staged tile each group of 32 consecutive rows (lane = row - group start) keeps
- * its elements in the group's range of the copy, ordered by element index k within the
- * row first and lane second: all k = 0 elements of the group's rows in lane order, then all
- * k = 1 elements, and so on. Every other tile, and every tile when tile_rows = 0, keeps the
- * CSR order. src_of[j] is the CSR-order position (in the panel copy) of the element stored
- * at j. */
-void oracle_panel_stage_order(int64_t n_rows, int32_t n_panels, const int32_t *prow,
-                              int32_t tile_rows, int32_t tile_cap, int64_t *src_of) {
-  const int64_t total = n_panels > 0 ? prow[(int64_t)(n_panels - 1) * (n_rows + 1) + n_rows] : 0;
-  for (int64_t j = 0; j < total; ++j) src_of[j] = j;
-  if (tile_rows <= 0) return;
-  for (int32_t p = 0; p < n_panels; ++p) {
-    const int32_t *rp = prow + (int64_t)p * (n_rows + 1);
-    for (int64_t r0 = 0; r0 < n_rows; r0 += tile_rows) {
-      const int64_t r1 = r0 + tile_rows < n_rows ? r0 + tile_rows : n_rows;
-      const int64_t a0 = rp[r0] - rp[r0] % 8;
-      const int64_t span = (rp[r1] - a0 + 7) / 8 * 8;
-      if (span > tile_cap) continue;
-      for (int64_t g0 = r0; g0 < r1; g0 += 32) {
-        const int64_t g1 = g0 + 32 < r1 ? g0 + 32 : r1;
-        int64_t longest = 0;
-        for (int64_t r = g0; r < g1; ++r)
-          if (rp[r + 1] - rp[r] > longest) longest = rp[r + 1] - rp[r];
-        int64_t j = rp[g0];
-        for (int64_t k = 0; k < longest; ++k)
-          for (int64_t r = g0; r < g1; ++r)
-            if (rp[r + 1] - rp[r] > k) src_of[j++] = rp[r] + k;
-      }
-    }
   }
 }
 

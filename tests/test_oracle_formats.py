@@ -338,74 +338,6 @@ def test_col_panels_against_dense_masks(gen, n_panels):
         assert np.array_equal(prow[0], m.rowptr) and np.array_equal(perm, np.arange(m.nnz))
 
 
-def test_panel_stage_order_hand_example():
-    # one panel, 3 rows of lengths 2, 0, 3 in one 32-row group: k = 0 elements of rows 0 and
-    # 2, then k = 1 of rows 0 and 2, then k = 2 of row 2
-    prow = np.array([[0, 2, 2, 5]], np.int32)
-    assert oracle.panel_stage_order(prow, 32, 8).tolist() == [0, 2, 1, 3, 4]
-    # a capacity below the tile's span (5 elements occupy one 8-element unit) keeps CSR order
-    assert oracle.panel_stage_order(prow, 32, 7).tolist() == [0, 1, 2, 3, 4]
-    assert oracle.panel_stage_order(prow, 0, 8).tolist() == [0, 1, 2, 3, 4]
-
-
-def test_panel_stage_order_equal_rows_is_column_major():
-    # every row of length L: inside a staged group the stored order is the 32 x L block read
-    # column by column (the ELL layout of the group), row r's element k at 32 k + lane
-    L, n = 5, 96
-    prow = (np.arange(n + 1, dtype=np.int32) * L)[None, :]
-    src = oracle.panel_stage_order(prow, 64, 10_000)
-    for g0 in range(0, n, 32):
-        base = g0 * L
-        for lane in range(32):
-            for k in range(L):
-                assert src[base + 32 * k + lane] == base + lane * L + k
-
-
-def _stage_order_by_sorting(prow, tile_rows, tile_cap):
-    """The same order from a sort: inside each staged group, elements sorted by (k, row)."""
-    n_panels, n1 = prow.shape
-    n = n1 - 1
-    total = int(prow[-1, -1])
-    src = np.arange(total, dtype=np.int64)
-    for p in range(n_panels):
-        rp = prow[p].astype(np.int64)
-        for r0 in range(0, n, tile_rows):
-            r1 = min(r0 + tile_rows, n)
-            a0 = rp[r0] - rp[r0] % 8
-            if -(-(rp[r1] - a0) // 8) * 8 > tile_cap:
-                continue
-            for g0 in range(r0, r1, 32):
-                g1 = min(g0 + 32, r1)
-                keys = [(k, r, rp[r] + k) for r in range(g0, g1) for k in range(rp[r + 1] - rp[r])]
-                keys.sort()
-                src[rp[g0]:rp[g1]] = [j for _, _, j in keys]
-    return src
-
-
-@pytest.mark.parametrize("tile_rows", [32, 64, 128])
-@pytest.mark.parametrize("seed", [41, 42, 43])
-def test_panel_stage_order_against_sorting(seed, tile_rows):
-    """Against a sort-based statement of the same order, on panel copies with empty rows,
-    ragged groups, a ragged last tile and tiles above the capacity; src_of is a bijection
-    that moves elements only inside their own 32-row group."""
-    m = synth.uniform_random(1000 + seed, 12, seed=seed, min_per_row=0, n_cols=5000)
-    prow, perm, _ = oracle.col_panels(m.rowptr, m.colind, m.n_cols, 3)
-    lens = np.diff(prow, axis=1)
-    cap = int(np.quantile([lens[:, i:i + tile_rows].sum(axis=1).max()
-                           for i in range(0, m.n_rows, tile_rows)], 0.7))
-    src = oracle.panel_stage_order(prow, tile_rows, cap)
-    assert np.array_equal(src, _stage_order_by_sorting(prow, tile_rows, cap))
-    assert np.array_equal(np.sort(src), np.arange(m.nnz))
-    moved = src != np.arange(m.nnz)
-    assert moved.any() and not moved.all()
-    group_of = np.empty(m.nnz, np.int64)
-    for p in range(3):
-        for g0 in range(0, m.n_rows, 32):
-            g1 = min(g0 + 32, m.n_rows)
-            group_of[prow[p, g0]:prow[p, g1]] = p * 10 ** 6 + g0
-    assert np.array_equal(group_of[src], group_of)
-
-
 def test_col_panels_spmv_by_passes_is_exact_on_integers():
     # integer values and x: every partial sum is exact, so summing the passes in order
     # equals the one-pass product bit for bit
