@@ -139,6 +139,9 @@ typedef struct {
 
 /* ---------------------------------------------------------------- matrix handles ---- */
 
+/* Largest nonzero count a handle accepts: 2^31 - 2^21 - 1 (see spmv_create). */
+#define SPMV_MAX_NNZ 2145386495LL
+
 /* Fills opts with the defaults listed above. */
 spmv_status spmv_tune_opts_default(spmv_tune_opts *opts);
 
@@ -147,8 +150,11 @@ spmv_status spmv_tune_opts_default(spmv_tune_opts *opts);
  * pointers (device_ptrs = 0) or device pointers (device_ptrs = 1); the caller keeps
  * ownership and may free them when the call returns. Storage, x/y and accumulation
  * dtypes start as val_type / F64 / F64 (F32 / F32 / F32 for F32 and BF16 input).
- * Errors: SPMV_ERR_ARG (null out or arrays, negative sizes), SPMV_ERR_INVALID_CSR,
- * SPMV_ERR_OOM, SPMV_ERR_CUDA. The call synchronizes the stream. */
+ * Sizes: n_rows and n_cols below 2^31 - 1, nnz at most SPMV_MAX_NNZ = 2^31 - 2^21 - 1
+ * (offsets are int32, and the kernels step through a row's nonzeros in strides of up to
+ * 2^20, the longest row-decomposition chunk, which must not pass 2^31 - 1).
+ * Errors: SPMV_ERR_ARG (null out or arrays, negative or oversized sizes),
+ * SPMV_ERR_INVALID_CSR, SPMV_ERR_OOM, SPMV_ERR_CUDA. The call synchronizes the stream. */
 spmv_status spmv_create(spmv_handle_t *out, int64_t n_rows, int64_t n_cols, int64_t nnz,
                         const int32_t *row_ptr, const int32_t *col_ind, const void *val,
                         spmv_dtype val_type, int32_t device_ptrs, spmv_stream_t stream);

@@ -66,7 +66,7 @@ spmv_status spmv_create(spmv_handle_t *out, int64_t n_rows, int64_t n_cols, int6
                         spmv_dtype val_type, int32_t device_ptrs, spmv_stream_t stream) {
   if (!out || !row_ptr || (nnz > 0 && (!col_ind || !val))) return SPMV_ERR_ARG;
   if (n_rows < 0 || n_cols < 0 || nnz < 0 || n_rows >= INT32_MAX || n_cols >= INT32_MAX ||
-      nnz >= INT32_MAX)
+      nnz > SPMV_MAX_NNZ)
     return SPMV_ERR_ARG;
   if (!valid_dtype(val_type)) return SPMV_ERR_UNSUPPORTED_DTYPE;
   *out = nullptr;

@@ -23,7 +23,7 @@ __all__ = [
     "Csr", "laplacian_2d", "stencil_27pt", "stencil_7pt", "power_law", "scattered",
     "banded", "uniform_random", "dense_random", "identity", "permutation", "random_gaps",
     "uniform_vector", "mixed_spec", "make_from_spec", "batched_specs",
-    "SEED_BASE",
+    "SEED_BASE", "MAX_NNZ", "max_nnz_lengths", "max_nnz_rows", "max_nnz_x", "max_nnz_device",
 ]
 
 # Seeds are derived from the arXiv number so that every run draws the same inputs.
@@ -325,6 +325,99 @@ def permutation(n: int, seed: int) -> Csr:
 # ---------------------------------------------------------------------------------------
 # Mixed matrix sets (learned-selector training set, batched workload)
 # ---------------------------------------------------------------------------------------
+
+# --------------------------------------------------------------------------------------
+# The largest matrix a handle accepts: nnz just under 2^31 - 2^21 - 1, so that row offsets
+# near the top of int32 are exercised. Too large to build on the host, it is given in closed
+# form: max_nnz_device builds the whole CSR on a CUDA device with torch, max_nnz_rows any set
+# of its rows with numpy, both from the same formulas.
+#   rows 2^25, columns 2^20; row lengths 64, except a band of rows of 32 starting at row 2^24
+#   (sized so that the total lands just under the limit), rows 1,000,003 k (k >= 1) of 16
+#   whose columns are 65,536 apart (delta-index escape rows), and the last three rows of
+#   300,000 (long rows, chunked by the row decomposition);
+#   column k of row i: 4096 k + (i mod 4096), for the rows of 16: 65536 k + (i mod 4096),
+#   for the rows of 300,000: 3 k + (i mod 3);
+#   value at position j: ((j * 2654435761) mod 2^31) / 2^30 - 1; x[c]: ((c * 40503) mod
+#   65536) / 32768 - 1 (both exact in FP64, in [-1, 1)).
+
+MAX_NNZ = 2 ** 31 - 2 ** 21 - 1
+MAX_NNZ_ROWS = 1 << 25
+MAX_NNZ_COLS = 1 << 20
+
+
+def max_nnz_lengths() -> np.ndarray:
+    """Row lengths (int64) of the maximum-size matrix."""
+    n = MAX_NNZ_ROWS
+    lens = np.full(n, 64, np.int64)
+    lens[np.arange(1_000_003, n, 1_000_003)] = 16
+    lens[-3:] = 300_000
+    excess = int(lens.sum()) - (MAX_NNZ - 128)
+    band = np.arange(1 << 24, n)
+    band = band[lens[band] == 64][: -(-excess // 32)]
+    lens[band] = 32
+    assert MAX_NNZ - 1024 < lens.sum() <= MAX_NNZ
+    return lens
+
+
+def _max_nnz_stride_offset(i, lens, xp):
+    """Per row: the column stride and first column (numpy or torch arrays)."""
+    stride = xp.where(lens == 16, 65536, xp.where(lens == 300_000, 3, 4096))
+    off = xp.where(lens == 300_000, i % 3, i % 4096)
+    return stride, off
+
+
+def _max_nnz_hash(j):
+    return (j * 2654435761) % 2 ** 31   # j < 2^31: the product stays below 2^63
+
+
+def max_nnz_x() -> np.ndarray:
+    c = np.arange(MAX_NNZ_COLS, dtype=np.int64)
+    return ((c * 40503) % 65536) / 32768.0 - 1.0
+
+
+def max_nnz_rows(rows) -> Csr:
+    """The given rows of the maximum-size matrix, in the order given, as a CSR of their own
+    (FP64 values)."""
+    lens = max_nnz_lengths()
+    rp_full = np.zeros(MAX_NNZ_ROWS + 1, np.int64)
+    np.cumsum(lens, out=rp_full[1:])
+    rows = np.asarray(rows, np.int64)
+    counts = lens[rows]
+    rp = _rowptr_from_counts(counts)
+    row_of = np.repeat(rows, counts)
+    k = np.arange(int(counts.sum()), dtype=np.int64) - np.repeat(rp[:-1].astype(np.int64), counts)
+    stride, off = _max_nnz_stride_offset(row_of, lens[row_of], np)
+    cols = (k * stride + off).astype(np.int32)
+    vals = _max_nnz_hash(rp_full[row_of] + k).astype(np.float64) / 2.0 ** 30 - 1.0
+    return Csr(len(rows), MAX_NNZ_COLS, rp, cols, vals, "max_nnz_rows")
+
+
+def max_nnz_device(torch, device="cuda"):
+    """(rowptr int32, colind int32, val float64) of the whole maximum-size matrix as tensors
+    on the device (about 26 GB), built from the closed form in bounded pieces."""
+    lens_h = max_nnz_lengths()
+    n = MAX_NNZ_ROWS
+    rp64 = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    rp64[1:] = torch.cumsum(torch.from_numpy(lens_h).to(device), 0)
+    nnz = int(rp64[-1])
+    col = torch.empty(nnz, dtype=torch.int32, device=device)
+    val = torch.empty(nnz, dtype=torch.float64, device=device)
+    lens = torch.from_numpy(lens_h).to(device)
+    piece = 1 << 21   # rows per piece (about 134 M nonzeros)
+    for r0 in range(0, n, piece):
+        r1 = min(r0 + piece, n)
+        rows = torch.arange(r0, r1, dtype=torch.int64, device=device)
+        ln = lens[r0:r1]
+        s0, s1 = int(rp64[r0]), int(rp64[r1])
+        row_of = torch.repeat_interleave(rows, ln)
+        j = torch.arange(s0, s1, dtype=torch.int64, device=device)
+        k = j - rp64[row_of]
+        stride, off = _max_nnz_stride_offset(row_of, lens[row_of], torch)
+        col[s0:s1] = (k * stride + off).to(torch.int32)
+        val[s0:s1] = _max_nnz_hash(j).to(torch.float64) / 2.0 ** 30 - 1.0
+        del row_of, j, k, stride, off
+    return rp64.to(torch.int32), col, val
+
 
 FAMILIES = ("stencil", "powerlaw", "banded", "random")
 

@@ -60,6 +60,23 @@ def test_status_strings(abi):
     assert "invalid argument" in abi.spmv_status_string(7)
 
 
+def test_create_rejects_nnz_past_the_int32_headroom(abi):
+    """spmv_create takes at most SPMV_MAX_NNZ = 2^31 - 2^21 - 1 nonzeros (int32 offsets with
+    room for the kernels' widest stride through a row, a 2^20-nonzero chunk) and refuses one
+    more with SPMV_ERR_ARG before it reads any array or touches the GPU."""
+    import ctypes
+    hdr = open(os.path.join(ROOT, "include", "spmv_gb300.h")).read()
+    lim = int(re.search(r"#define SPMV_MAX_NNZ (\d+)LL", hdr).group(1))
+    assert lim == 2 ** 31 - 2 ** 21 - 1
+    dummy = ctypes.c_int64(0)
+    p = ctypes.addressof(dummy)
+    for n_rows, n_cols, nnz in ((10, 10, lim + 1), (10, 10, 2 ** 31 - 1), (2 ** 31 - 1, 10, 0),
+                                (10, 2 ** 31 - 1, 0), (-1, 10, 0)):
+        with pytest.raises(abi.SpmvError) as e:
+            abi.spmv_create(n_rows, n_cols, nnz, p, p, p, abi.SPMV_F64, 0)
+        assert e.value.status == 7
+
+
 def _p_vector(bits):
     imb, ml, mb, cmp_ = bits
     p_imb = 200.0 if imb else 110.0
