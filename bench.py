@@ -549,8 +549,8 @@ def run_batched(args, rank, world):
     t_g = _abi.spmv_probe_gather(4 << 20, 4, sectors, 5)
     learned = None
     if sel is not None:
-        # the same batch with every matrix tuned by the profile route instead (the learned
-        # route's judge), at the same work plan
+        # the same batch with every matrix tuned by the profile route instead (what the
+        # learned route is compared with), at the same work plan
         t_prof = 0.0
         for A in As:
             t_prof += A.tune("profile", stream=stream, **route_opts()).t_pre_ms
