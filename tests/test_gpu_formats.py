@@ -132,6 +132,24 @@ def test_row_bins_bit_exact(api, torch):
         assert np.array_equal(first, of) and np.array_equal(ch, oc)
 
 
+def test_row_bins_long_rows_repeatable(api, torch):
+    """Long rows split into many chunks (up to 67): their partials are added in chunk order,
+    so ten SpMVs in a row, on two handles, give the same bits, within the FP64 bound of the
+    oracle."""
+    m = synth.power_law(20_000, alpha=1.5, clip=20_000, seed=22, dtype=np.float64)
+    x = torch.from_numpy(synth.uniform_vector(m.n_cols, 23)).cuda()
+    ys = []
+    for _ in range(2):
+        A = api.SpmvMatrix.from_csr(m)
+        A.set_variant(partition=2, bin_med=16, bin_chunk=300)
+        for _ in range(10):
+            ys.append(A.run(x).cpu().numpy())
+    assert all(np.array_equal(y.view(np.uint64), ys[0].view(np.uint64)) for y in ys)
+    check_spmv(m, x.cpu().numpy(), ys[0], TAU["f64"], "bins repeat")
+    _, lng, first, _ = (t.cpu().numpy() for t in A.row_bins())
+    assert lng.size > 50 and np.diff(first).max() > 20   # many long rows, some of many chunks
+
+
 @pytest.mark.parametrize("l_med,chunk", [(2, 2), (32, 2048), (128, 8192), (64, 300),
                                          (1000, 1000)])
 def test_row_bins_at_other_limits(api, torch, l_med, chunk):
