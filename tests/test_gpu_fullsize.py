@@ -66,6 +66,27 @@ def test_stencil_160_tuned_all_precisions(api, torch, stencil160, storage, vec, 
                    f"stencil 160^3 {storage}/{vec}/{acc} {rep.variant}")
 
 
+# the pool the benchmark times on the full stencil (its variant sweep), plus the tuned
+# geometry of the thread-per-row tile with 16-bit deltas
+STENCIL_POOL = [dict(), dict(vec=1, vs=4), dict(vec=1, vs=1), dict(index=1, vec=1, vs=1),
+                dict(vec=1, vs=1, xpath=1), dict(index=1, vec=1, vs=4), dict(partition=1),
+                dict(xpath=2, vs=2), dict(partition=3, index=1),
+                dict(index=1, vec=1, vs=1, xpath=1, tile_rows=32), dict(partition=2, index=1)]
+
+
+def test_stencil_160_every_timed_variant(api, torch, stencil160):
+    """Every variant the benchmark times on the 160^3 stencil (FP64), at full size, within
+    the FP64 bound of the oracle on sampled rows."""
+    m = stencil160
+    A = api.SpmvMatrix.from_csr(m)
+    x64 = synth.uniform_vector(m.n_cols, synth.SEED_BASE + 12)
+    x = torch.from_numpy(x64).cuda()
+    for v in STENCIL_POOL:
+        A.set_variant(**v)
+        y = A.run(x).cpu().numpy()
+        _check_sampled(m, x64, y, m.val, TAU["f64"], f"stencil 160^3 {v}")
+
+
 def test_powerlaw_4m_tuned(api, torch):
     m = synth.power_law(4_000_000)
     A = api.SpmvMatrix.from_csr(m)
@@ -77,6 +98,12 @@ def test_powerlaw_4m_tuned(api, torch):
     # carry scan, each tile's part added in FP64 -- within the FP32-storage bound
     _check_sampled(m, x32.astype(np.float64), y, m.val.astype(np.float64), TAU["f32"],
                    f"powerlaw 4M {rep.variant}")
+    # the decomposition the autotuner weighs against it, and thread-per-row short rows
+    for v in (dict(partition=1), dict(partition=2, vs=1), dict(partition=2, vs=8, xpath=1)):
+        A.set_variant(**v)
+        y = A.run(torch.from_numpy(x32).cuda()).double().cpu().numpy()
+        _check_sampled(m, x32.astype(np.float64), y, m.val.astype(np.float64), TAU["f32"],
+                       f"powerlaw 4M {v}")
 
 
 def test_scattered_16m_tuned(api, torch):
@@ -100,6 +127,11 @@ def test_scattered_16m_tuned(api, torch):
             a, b = prow[p, r], prow[p, r + 1]
             assert np.array_equal(pcol[a:b], cols[inside])
             assert np.array_equal(pval[a:b], m.val[s:e][inside])
+    # the single-pass variant with x evict-last and the three-panel copy it competes with
+    for v in (dict(vec=1, vs=4, xpath=1), dict(xpath=3, vs=1)):
+        A.set_variant(**v)
+        y = A.run(torch.from_numpy(x64).cuda()).cpu().numpy()
+        _check_sampled(m, x64, y, m.val, TAU["f64"], f"scattered 16M {v}")
 
 
 def test_batched_512_sampled(api, torch):
