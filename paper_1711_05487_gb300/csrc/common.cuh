@@ -126,8 +126,16 @@ template <bool HINT> __device__ __forceinline__ uint2 ld8(const void *p, uint64_
 }
 
 // x gathers: evict-last keeps x resident in L2 while the matrix streams past it.
-template <bool XL2> __device__ __forceinline__ double ldx(const double *p, uint64_t pol) {
-  if constexpr (XL2) {
+// NA: the gather allocates no L1 line (x gathers of a column-panel pass, which land on an
+// L2-sized slice at random and are almost never reused from L1).
+template <bool XL2, bool NA = false>
+__device__ __forceinline__ double ldx(const double *p, uint64_t pol) {
+  if constexpr (XL2 && NA) {
+    double r;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;"
+                 : "=d"(r) : "l"(p), "l"(pol));
+    return r;
+  } else if constexpr (XL2) {
     double r;
     asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(p), "l"(pol));
     return r;
@@ -135,8 +143,14 @@ template <bool XL2> __device__ __forceinline__ double ldx(const double *p, uint6
     return __ldg(p);
   }
 }
-template <bool XL2> __device__ __forceinline__ float ldx(const float *p, uint64_t pol) {
-  if constexpr (XL2) {
+template <bool XL2, bool NA = false>
+__device__ __forceinline__ float ldx(const float *p, uint64_t pol) {
+  if constexpr (XL2 && NA) {
+    float r;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;"
+                 : "=f"(r) : "l"(p), "l"(pol));
+    return r;
+  } else if constexpr (XL2) {
     float r;
     asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(pol));
     return r;

@@ -44,7 +44,8 @@ __device__ __forceinline__ int fp64_chain_of(int k, int len) {
 // Dot product of one row whose values and columns sit in shared memory at offset o (the
 // row's first element) of a staged tile: 16 (then 8) gathers of x in flight per thread
 // before their FMAs; exact trip counts keep the FP64 pipe free of masked-off work.
-template <typename ValT, typename VecT, typename AccT, int DB, bool XL2, typename IdxT>
+template <typename ValT, typename VecT, typename AccT, int DB, bool XL2, bool NA = false,
+          typename IdxT>
 __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
                                              const IdxT *sidx, int o, int len, int32_t base,
                                              const VecT *__restrict__ x, uint64_t pol_x) {
@@ -75,7 +76,7 @@ __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
     for (; k + 16 <= len; k += 16) {
       AccT xv[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) xv[q] = (AccT)ldx<XL2>(x + column(k + q), pol_x);
+      for (int q = 0; q < 16; ++q) xv[q] = (AccT)ldx<XL2, NA>(x + column(k + q), pol_x);
 #pragma unroll
       for (int q = 0; q < 16; q += 2) {
         acc = fma(widen<AccT>(sval[o + k + q]), xv[q], acc);
@@ -85,7 +86,7 @@ __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
     for (; k + 8 <= len; k += 8) {
       AccT xv[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) xv[q] = (AccT)ldx<XL2>(x + column(k + q), pol_x);
+      for (int q = 0; q < 8; ++q) xv[q] = (AccT)ldx<XL2, NA>(x + column(k + q), pol_x);
 #pragma unroll
       for (int q = 0; q < 8; q += 2) {
         acc = fma(widen<AccT>(sval[o + k + q]), xv[q], acc);
@@ -93,13 +94,13 @@ __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
       }
     }
     for (; k < len; ++k)
-      acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2>(x + column(k), pol_x), acc);
+      acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2, NA>(x + column(k), pol_x), acc);
     return acc + acc1;
   }
   for (; k + 16 <= len; k += 16) {
     AccT xv[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) xv[q] = (AccT)ldx<XL2>(x + column(k + q), pol_x);
+    for (int q = 0; q < 16; ++q) xv[q] = (AccT)ldx<XL2, NA>(x + column(k + q), pol_x);
 #pragma unroll
     for (int q = 0; q < 16; ++q) acc = fma(widen<AccT>(sval[o + k + q]), xv[q], acc);
     if constexpr (IsF32<AccT>::value) {
@@ -112,11 +113,11 @@ __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
   for (; k + 8 <= len; k += 8) {
     AccT xv[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) xv[q] = (AccT)ldx<XL2>(x + column(k + q), pol_x);
+    for (int q = 0; q < 8; ++q) xv[q] = (AccT)ldx<XL2, NA>(x + column(k + q), pol_x);
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc = fma(widen<AccT>(sval[o + k + q]), xv[q], acc);
   }
-  for (; k < len; ++k) acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2>(x + column(k), pol_x), acc);
+  for (; k < len; ++k) acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2, NA>(x + column(k), pol_x), acc);
   if constexpr (IsF32<AccT>::value) {
     if (fold) {
       wadd(tot, (float)acc);
@@ -129,7 +130,8 @@ __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
 // One lane's share of row r (nonzeros [s, e)) straight from global memory, lanes strided
 // by 32. With SumT wider than AccT (FP32 pairs) each lane sums runs of kF32Run products in
 // AccT and adds the run sums into SumT.
-template <typename ValT, typename VecT, typename AccT, int DB, bool XL2, typename SumT>
+template <typename ValT, typename VecT, typename AccT, int DB, bool XL2, typename SumT,
+          bool NA = false>
 __device__ __forceinline__ SumT warp_row_dot(const RunArgs &a, int64_t r, int s, int e,
                                              int lane, const VecT *__restrict__ x,
                                              uint64_t pol_x) {
@@ -153,7 +155,7 @@ __device__ __forceinline__ SumT warp_row_dot(const RunArgs &a, int64_t r, int s,
     if (base < 0) {
       const int32_t *ec = a.esc + (-(int64_t)base - 1) - s;
       for (int j = s + lane; j < e; j += 32)
-        add(widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(ec + j), pol_x));
+        add(widen<AccT>(val[j]) * (AccT)ldx<XL2, NA>(x + __ldg(ec + j), pol_x));
     } else {
       // decode the row's deltas: the lane sums its own and its predecessors' deltas
       using DT = typename IdxOf<DB>::type;
@@ -163,13 +165,13 @@ __device__ __forceinline__ SumT warp_row_dot(const RunArgs &a, int64_t r, int s,
         const int j = j0 + lane;
         const int d = j < e ? (int)dl[j] : 0;
         const int incl = group_incl_scan<32>(d, lane, 0xffffffffu);
-        if (j < e) add(widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + (run + incl), pol_x));
+        if (j < e) add(widen<AccT>(val[j]) * (AccT)ldx<XL2, NA>(x + (run + incl), pol_x));
         run += __shfl_sync(0xffffffffu, incl, 31);
       }
     }
   } else {
     for (int j = s + lane; j < e; j += 32)
-      add(widen<AccT>(val[j]) * (AccT)ldx<XL2>(x + __ldg(a.colind + j), pol_x));
+      add(widen<AccT>(val[j]) * (AccT)ldx<XL2, NA>(x + __ldg(a.colind + j), pol_x));
   }
   wadd(sum, part);
   return sum;
@@ -198,7 +200,7 @@ __device__ __forceinline__ int32_t ld_rowptr(const RunArgs &a, int64_t i) {
 
 // Rows [r0, r1) straight from global memory, a warp per row (tiles larger than the staged
 // capacity).
-template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
+template <typename ValT, typename VecT, typename AccT, int DB, bool XL2, bool NA = false>
 __device__ __forceinline__ void tile_direct(const RunArgs &a, int64_t r0, int64_t r1,
                                             const VecT *__restrict__ x, VecT *__restrict__ y,
                                             uint64_t pol_x) {
@@ -207,19 +209,19 @@ __device__ __forceinline__ void tile_direct(const RunArgs &a, int64_t r0, int64_
     const int s = __ldg(a.rowptr + r), e = __ldg(a.rowptr + r + 1);
     if constexpr (IsF32<AccT>::value) {
       if (e - s > kF32Run * 32) {   // long row in FP32: runs summed in pairs (warp-uniform)
-        FPair d = warp_row_dot<ValT, VecT, AccT, DB, XL2, FPair>(a, r, s, e, lane, x, pol_x);
+        FPair d = warp_row_dot<ValT, VecT, AccT, DB, XL2, FPair, NA>(a, r, s, e, lane, x, pol_x);
         d = group_sum<32>(d, 0xffffffffu);
         if (lane == 0) store_y<VecT, AccT>(a, y, r, (AccT)wvalue(d));
         continue;
       }
     }
-    AccT acc = warp_row_dot<ValT, VecT, AccT, DB, XL2, AccT>(a, r, s, e, lane, x, pol_x);
+    AccT acc = warp_row_dot<ValT, VecT, AccT, DB, XL2, AccT, NA>(a, r, s, e, lane, x, pol_x);
     acc = group_sum<32>(acc, 0xffffffffu);
     if (lane == 0) store_y<VecT, AccT>(a, y, r, acc);
   }
 }
 
-template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
+template <typename ValT, typename VecT, typename AccT, int DB, bool XL2, bool NA = false>
 __global__ void __launch_bounds__(kTileRows) k_rowtile(const RunArgs a) {
   using IdxT = typename IdxOf<DB>::type;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -271,11 +273,12 @@ __global__ void __launch_bounds__(kTileRows) k_rowtile(const RunArgs a) {
       }
     }
     if (row >= r1) return;
-    store_y<VecT, AccT>(a, y, row, tile_row_dot<ValT, VecT, AccT, DB, XL2>(a, sval, sidx, s - a0,
-                                                                           e - s, base, x, pol_x));
+    store_y<VecT, AccT>(a, y, row,
+                        tile_row_dot<ValT, VecT, AccT, DB, XL2, NA>(a, sval, sidx, s - a0, e - s,
+                                                                    base, x, pol_x));
   } else {
     // oversize tile: a warp per row straight from global memory
-    tile_direct<ValT, VecT, AccT, DB, XL2>(a, r0, r1, x, y, pol_x);
+    tile_direct<ValT, VecT, AccT, DB, XL2, NA>(a, r0, r1, x, y, pol_x);
   }
 }
 
@@ -401,7 +404,7 @@ cudaError_t ensure_smem(K kernel, size_t smem, std::atomic<int> &configured) {
   return e;
 }
 
-template <typename ValT, typename VecT, typename AccT, int DB, bool XL2>
+template <typename ValT, typename VecT, typename AccT, int DB, bool XL2, bool NA = false>
 cudaError_t launch_rowtile_k(const RunArgs &a, cudaStream_t s) {
   using IdxT = typename IdxOf<DB>::type;
   const int rows = a.tile_rows > 0 ? a.tile_rows : kTileRows;
@@ -424,10 +427,10 @@ cudaError_t launch_rowtile_k(const RunArgs &a, cudaStream_t s) {
   }
   static std::atomic<int> configured{0};
   const size_t smem = 16 + per_stage;
-  cudaError_t e = ensure_smem(k_rowtile<ValT, VecT, AccT, DB, XL2>, smem, configured);
+  cudaError_t e = ensure_smem(k_rowtile<ValT, VecT, AccT, DB, XL2, NA>, smem, configured);
   if (e != cudaSuccess) return e;
   const unsigned g = (unsigned)((a.n_rows + rows - 1) / rows);
-  k_rowtile<ValT, VecT, AccT, DB, XL2><<<g, rows, smem, s>>>(a);
+  k_rowtile<ValT, VecT, AccT, DB, XL2, NA><<<g, rows, smem, s>>>(a);
   return cudaGetLastError();
 }
 
