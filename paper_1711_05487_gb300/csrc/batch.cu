@@ -319,8 +319,8 @@ __device__ void warp_chunk_k16(const BatchMat &m, int z0, int z1, int chunk, dou
     acc[2] = fmaf(v0, __uint_as_float(x0.z), acc[2]);
     acc[3] = fmaf(v0, __uint_as_float(x0.w), acc[3]);
   }
-#pragma unroll
   double t[4];
+#pragma unroll
   for (int q = 0; q < 4; ++q) {
     wadd(w[q], acc[q]);
     t[q] = wdouble(w[q]);

@@ -96,35 +96,37 @@ __device__ __forceinline__ AccT tile_row_dot(const RunArgs &a, const ValT *sval,
     for (; k < len; ++k)
       acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2, NA>(x + column(k), pol_x), acc);
     return acc + acc1;
-  }
-  for (; k + 16 <= len; k += 16) {
-    AccT xv[16];
+  } else {
+    for (; k + 16 <= len; k += 16) {
+      AccT xv[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) xv[q] = (AccT)ldx<XL2, NA>(x + column(k + q), pol_x);
+      for (int q = 0; q < 16; ++q) xv[q] = (AccT)ldx<XL2, NA>(x + column(k + q), pol_x);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) acc = fma(widen<AccT>(sval[o + k + q]), xv[q], acc);
+      for (int q = 0; q < 16; ++q) acc = fma(widen<AccT>(sval[o + k + q]), xv[q], acc);
+      if constexpr (IsF32<AccT>::value) {
+        if (fold) {
+          wadd(tot, (float)acc);
+          acc = 0;
+        }
+      }
+    }
+    for (; k + 8 <= len; k += 8) {
+      AccT xv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) xv[q] = (AccT)ldx<XL2, NA>(x + column(k + q), pol_x);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc = fma(widen<AccT>(sval[o + k + q]), xv[q], acc);
+    }
+    for (; k < len; ++k)
+      acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2, NA>(x + column(k), pol_x), acc);
     if constexpr (IsF32<AccT>::value) {
       if (fold) {
         wadd(tot, (float)acc);
-        acc = 0;
+        acc = (AccT)wvalue(tot);
       }
     }
+    return acc;
   }
-  for (; k + 8 <= len; k += 8) {
-    AccT xv[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) xv[q] = (AccT)ldx<XL2, NA>(x + column(k + q), pol_x);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc = fma(widen<AccT>(sval[o + k + q]), xv[q], acc);
-  }
-  for (; k < len; ++k) acc = fma(widen<AccT>(sval[o + k]), (AccT)ldx<XL2, NA>(x + column(k), pol_x), acc);
-  if constexpr (IsF32<AccT>::value) {
-    if (fold) {
-      wadd(tot, (float)acc);
-      acc = (AccT)wvalue(tot);
-    }
-  }
-  return acc;
 }
 
 // One lane's share of row r (nonzeros [s, e)) straight from global memory, lanes strided
